@@ -1,0 +1,731 @@
+"""FP64 CPU oracle of the local level-set grain-growth step.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously-correct
+restatement of the method that the CUDA path is checked against.  Only the
+tests, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import it.  It shares no code with the CUDA path; the only
+module both use is ``paper_1701_06658_gb300.inputs`` (seeded random numbers).
+
+Source: C. Miessen, N. Velinov, G. Gottstein, L.A. Barrales-Mora, "A highly
+efficient 3D level-set grain growth algorithm tailored for ccNUMA
+architecture" (arXiv:1701.06658).  Every function cites the section /
+equation it restates; equations are numbered in order of appearance:
+(1) zero level set, (2) |grad phi| = 1, (7) heat equation, (8) Gaussian
+kernel, (9) d(t) = G(t) * d(0), (10) velocity correction, (13) bulk
+normalisation, (14)-(15) time map, (16) comparison step, (18) magnetic
+energy, (19) magnetic pressure, (20) GB mobility.
+
+Conventions (grid units, h = 1, M_max * gamma_max = 1):
+  * arrays are indexed (z, y, x) (x fastest); a domain has shape (Nz, Ny, Nx);
+    Nz == 1 is a 2D domain, whose z axis is never convolved, searched or
+    resized;
+  * the domain is periodic; a grain owns a box with origin o (in [0, N)) and
+    dims n <= N per axis; box cell l sits at global cell (o + l) mod N;
+  * an axis with n == N is "full": it wraps onto itself;
+  * outside its box a grain's function is -eps (Fig. 1 caption: "outside it
+    was restricted to eps = -7h").
+
+Readings of points where the paper is silent or garbled (each named in the
+code where it applies):
+  R1 Eq. (8) prints (4 pi t)^(-1/D) exp(-|x|^2 / 4 pi); we use the heat kernel
+     of Eq. (7), exp(-|x|^2 / (4 t)), sampled at integer offsets |k| <= R,
+     normalised to sum 1 and applied separably.
+  R2 values are clamped to [-eps, eps] after the predictor and redistancing.
+  R3 Eq. (10): phi_p = phi + w (G*phi - phi) + M (e_j - e_i) dt, with the
+     pair (i, j) taken per cell from the ID-field of the previous step.  With
+     no physics (w = 1, no bulk term) phi_p = G*phi.
+  R4 Eq. (16): the max runs over all other grains (-eps outside their boxes);
+     all grains compare predicted values of the same step (Jacobi); the
+     ID-field is the argmax over grains whose value exceeds -eps, lowest id on
+     ties, -1 when none does.
+  R5 Sec. 2.1.6 (Zhao's scheme, taxicab metric): a cell whose face neighbour
+     (outside the box: -eps) has the opposite sign is a reference cell and
+     gets the planar-exact distance s / sqrt(sum_a delta_a^-2), delta_a the
+     nearest linear zero crossing along axis a; every other cell gets
+     s * min(eps, min over same-sign face neighbours |d| + 1), iterated to the
+     fixed point.  sign(0) = -1.
+  R6 Sec. 2.1.3 / 3.1 (size-adaptive grids): after every step the box becomes
+     the bounding box of {phi > 0} grown by the halo; an axis whose extent
+     reaches N becomes full (and keeps its origin if it was full already).
+     Values move with their global cell; new cells get -eps.  A grain with no
+     positive cell is extinct.
+  R7 initial functions (Sec. 2.1.3, "initialized to fulfill Eq. (2)"): the
+     minimum over face-adjacent cells of the signed distance to the power
+     bisector plane, clamped to [-eps, eps].
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# geometry helpers
+# --------------------------------------------------------------------------
+
+
+def spatial_axes(shape):
+    """Axes that carry space: (0, 1, 2) in 3D, (1, 2) in 2D."""
+    return (1, 2) if shape[0] == 1 else (0, 1, 2)
+
+
+@dataclass
+class Grain:
+    """Grain object of Sec. 3.1: its id, its box Omega_i and its function."""
+    gid: int
+    origin: tuple            # (oz, oy, ox), each in [0, N)
+    phi: np.ndarray          # float64, shape (nz, ny, nx)
+    idf: np.ndarray | None = None   # ID-field, int64, same shape (R3/R4)
+    alive: bool = True
+
+    @property
+    def dims(self):
+        return self.phi.shape
+
+
+def full_axes(grain: Grain, shape):
+    return tuple(grain.dims[a] == shape[a] for a in range(3))
+
+
+def box_positions(grain: Grain, shape):
+    """Global cell index along each axis for every local index of the box."""
+    return tuple((grain.origin[a] + np.arange(grain.dims[a])) % shape[a] for a in range(3))
+
+
+def sample(grain: Grain, pos, shape, fill):
+    """Values of the grain's function at the outer product of the global
+    positions ``pos`` = (pz, py, px); ``fill`` where the box does not reach."""
+    loc = []
+    inside = []
+    for a in range(3):
+        l = (pos[a] - grain.origin[a]) % shape[a]
+        ok = l < grain.dims[a]
+        loc.append(np.where(ok, l, 0))
+        inside.append(ok)
+    vals = grain.phi[np.ix_(loc[0], loc[1], loc[2])]
+    mask = inside[0][:, None, None] & inside[1][None, :, None] & inside[2][None, None, :]
+    return np.where(mask, vals, fill), mask
+
+
+def boxes_intersect(gi: Grain, gj: Grain, shape):
+    """True when the two boxes share a cell of the periodic domain."""
+    for a in range(3):
+        n, oi, ni, oj, nj = shape[a], gi.origin[a], gi.dims[a], gj.origin[a], gj.dims[a]
+        if ni == n or nj == n:
+            continue
+        # j starts inside i's interval, or i starts inside j's interval
+        if not ((oj - oi) % n < ni or (oi - oj) % n < nj):
+            return False
+    return True
+
+
+def _shift(a, axis, k, wrap, fill):
+    """b[x] = a[x + k] along ``axis`` (k = +-1); periodic when ``wrap``."""
+    if wrap:
+        return np.roll(a, -k, axis=axis)
+    b = np.full_like(a, fill)
+    src = [slice(None)] * a.ndim
+    dst = [slice(None)] * a.ndim
+    if k > 0:
+        src[axis] = slice(k, None)
+        dst[axis] = slice(None, -k)
+    else:
+        src[axis] = slice(None, k)
+        dst[axis] = slice(-k, None)
+    b[tuple(dst)] = a[tuple(src)]
+    return b
+
+
+# --------------------------------------------------------------------------
+# predictor: Eqs. (7)-(10), Sec. 2.1.4
+# --------------------------------------------------------------------------
+
+
+def heat_kernel_taps(dt: float, radius: int) -> np.ndarray:
+    """1D taps of the heat kernel for time dt (reading R1): G(dt, k) is
+    proportional to exp(-k^2 / (4 dt)), |k| <= radius, normalised to sum 1.
+    Its second moment is 2 dt (up to truncation), the variance of the
+    Green's function of Eq. (7)."""
+    k = np.arange(-radius, radius + 1, dtype=np.float64)
+    g = np.exp(-k * k / (4.0 * dt))
+    return g / g.sum()
+
+
+def extend(phi: np.ndarray, full, radius: int, eps: float, axes) -> np.ndarray:
+    """Pad the box by ``radius`` cells per spatial axis: periodic copies on a
+    full axis, -eps elsewhere (Fig. 1 caption)."""
+    out = phi
+    for a in axes:
+        pad = [(0, 0)] * 3
+        pad[a] = (radius, radius)
+        if full[a]:
+            out = np.pad(out, pad, mode="wrap")
+        else:
+            out = np.pad(out, pad, mode="constant", constant_values=-eps)
+    return out
+
+
+def convolve(phi: np.ndarray, full, taps: np.ndarray, eps: float, axes) -> np.ndarray:
+    """G * phi on the box (Eq. (9)), the 3D (2D) kernel being the outer
+    product of ``taps``; applied one axis after the other."""
+    radius = (len(taps) - 1) // 2
+    c = extend(phi, full, radius, eps, axes)
+    for a in axes:
+        n = c.shape[a] - 2 * radius
+        acc = np.zeros(c.shape[:a] + (n,) + c.shape[a + 1:])
+        for t in range(2 * radius + 1):
+            sl = [slice(None)] * 3
+            sl[a] = slice(t, t + n)
+            acc += taps[t] * c[tuple(sl)]
+        c = acc
+    return c
+
+
+def predict(grain: Grain, shape, taps, eps, physics=None, dt=1.0) -> np.ndarray:
+    """Predictor of Algorithm 1 (Sec. 2.1.4): convolution with the heat
+    kernel (Eq. (9)) and, with physics, the velocity correction of Eq. (10)
+    (reading R3).  Clamped to [-eps, eps] (reading R2)."""
+    axes = spatial_axes(shape)
+    c = convolve(grain.phi, full_axes(grain, shape), taps, eps, axes)
+    if physics is None:
+        phip = c
+    else:
+        w, bulk = physics.blend_terms(grain.gid, grain.idf, dt)
+        phip = grain.phi + w * (c - grain.phi) + bulk
+    return np.clip(phip, -eps, eps)
+
+
+# --------------------------------------------------------------------------
+# corrector: Eq. (16), Sec. 2.1.5 and the ID-field of Sec. 3.1
+# --------------------------------------------------------------------------
+
+
+def neighbour_max(i: int, grains, phip: dict, shape, eps, candidates=None):
+    """max_{j != i} phi_p_j over the cells of box i, and its argmax (R4).
+
+    ``candidates`` restricts j to a superset of the grains whose boxes meet
+    box i (the neighbour preselection of Sec. 3.1); it cannot change the
+    result because every other grain contributes -eps."""
+    gi = grains[i]
+    pos = box_positions(gi, shape)
+    m = np.full(gi.dims, -eps)
+    idm = np.full(gi.dims, -1, dtype=np.int64)
+    js = range(len(grains)) if candidates is None else sorted(candidates)
+    for j in js:
+        gj = grains[j]
+        if j == i or not gj.alive:
+            continue
+        view = Grain(gj.gid, gj.origin, phip[j])
+        v, _ = sample(view, pos, shape, -eps)
+        better = v > m          # strict: ascending j keeps the lowest id on ties
+        m = np.where(better, v, m)
+        idm = np.where(better, j, idm)
+    return m, idm
+
+
+def compare(phip_i: np.ndarray, m: np.ndarray) -> np.ndarray:
+    """Eq. (16): d_c = (d_p - max_{j != i} d_p_j) / 2."""
+    return 0.5 * (phip_i - m)
+
+
+# --------------------------------------------------------------------------
+# re-initialisation: Sec. 2.1.6 (Zhao's fast sweeping, taxicab metric)
+# --------------------------------------------------------------------------
+
+
+def reference_values(phic: np.ndarray, full, eps, axes):
+    """Reference cells and their planar-exact distances (reading R5).
+
+    Returns (is_ref, |d_ref|)."""
+    pos = phic > 0
+    a = np.abs(phic)
+    is_ref = np.zeros(phic.shape, dtype=bool)
+    inv2 = np.zeros(phic.shape)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for ax in axes:
+            dmin = np.full(phic.shape, np.inf)
+            for k in (1, -1):
+                nb = _shift(phic, ax, k, full[ax], -eps)
+                opp = (nb > 0) != pos
+                delta = a / (a + np.abs(nb))
+                dmin = np.where(opp, np.minimum(dmin, delta), dmin)
+            has = np.isfinite(dmin)
+            is_ref |= has
+            inv2 = inv2 + np.where(has, 1.0 / (dmin * dmin), 0.0)
+        dref = np.where(is_ref, 1.0 / np.sqrt(inv2), 0.0)
+    return is_ref, dref
+
+
+def redistance(phic: np.ndarray, full, eps, axes) -> np.ndarray:
+    """Taxicab signed distance to the zero level of phic (reading R5):
+    reference values held fixed, d = s * min(eps, min_{same-sign face
+    neighbour y} |d(y)| + 1) iterated until nothing changes."""
+    pos = phic > 0
+    is_ref, dref = reference_values(phic, full, eps, axes)
+    mag = np.where(is_ref, dref, eps)
+    exists = np.ones(phic.shape, dtype=bool)
+    while True:
+        cand = np.full(phic.shape, np.inf)
+        for ax in axes:
+            for k in (1, -1):
+                nb_mag = _shift(mag, ax, k, full[ax], np.inf)
+                nb_pos = _shift(pos, ax, k, full[ax], False)
+                nb_ok = _shift(exists, ax, k, full[ax], False)
+                same = nb_ok & (nb_pos == pos)
+                cand = np.where(same, np.minimum(cand, nb_mag + 1.0), cand)
+        new = np.where(is_ref, dref, np.minimum(eps, cand))
+        if np.array_equal(new, mag):
+            break
+        mag = new
+    return np.where(pos, mag, -mag)
+
+
+# --------------------------------------------------------------------------
+# box update: Secs. 2.1.3 and 3.1 (size-adaptive local grids)
+# --------------------------------------------------------------------------
+
+
+def box_update(grain: Grain, shape, halo: int, eps: float) -> Grain:
+    """New box = bbox{phi > 0} grown by ``halo`` (reading R6)."""
+    pos = grain.phi > 0
+    if not pos.any():
+        return Grain(grain.gid, grain.origin, grain.phi, grain.idf, alive=False)
+    axes = spatial_axes(shape)
+    origin = list(grain.origin)
+    dims = list(grain.dims)
+    for a in axes:
+        other = tuple(b for b in range(3) if b != a)
+        occ = np.nonzero(pos.any(axis=other))[0]
+        lmin, lmax = int(occ[0]), int(occ[-1])
+        n = lmax - lmin + 1 + 2 * halo
+        was_full = grain.dims[a] == shape[a]
+        if n >= shape[a]:
+            dims[a] = shape[a]
+            origin[a] = grain.origin[a] if was_full else (grain.origin[a] + lmin - halo) % shape[a]
+        else:
+            dims[a] = n
+            origin[a] = (grain.origin[a] + lmin - halo) % shape[a]
+    new = Grain(grain.gid, tuple(origin), np.zeros(tuple(dims)))
+    pos_new = box_positions(new, shape)
+    new.phi, _ = sample(grain, pos_new, shape, -eps)
+    if grain.idf is not None:
+        idv = Grain(grain.gid, grain.origin, grain.idf)
+        new.idf, _ = sample(idv, pos_new, shape, -1)
+        new.idf = new.idf.astype(np.int64)
+    return new
+
+
+# --------------------------------------------------------------------------
+# physics of the velocity correction: Eqs. (10), (13)-(15), (18)-(20), Sec. 4.3
+# --------------------------------------------------------------------------
+
+
+def _qmul(a, b):
+    aw, ax, ay, az = a
+    bw, bx, by, bz = b
+    return np.array([aw * bw - ax * bx - ay * by - az * bz,
+                     aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx,
+                     aw * bz + ax * by - ay * bx + az * bw])
+
+
+def cubic_symmetry_quaternions() -> np.ndarray:
+    """The 24 proper rotations of the cube as unit quaternions (w, x, y, z):
+    identity, 3 half turns about the axes, 6 quarter turns about the axes,
+    8 third turns about the body diagonals, 6 half turns about the face
+    diagonals."""
+    c = 1.0 / math.sqrt(2.0)
+    ops = [(1, 0, 0, 0), (0, 1, 0, 0), (0, 0, 1, 0), (0, 0, 0, 1)]
+    for ax in range(3):
+        for s in (1, -1):
+            v = [c, 0.0, 0.0, 0.0]
+            v[1 + ax] = s * c
+            ops.append(tuple(v))
+    for sx in (1, -1):
+        for sy in (1, -1):
+            for sz in (1, -1):
+                ops.append((0.5, 0.5 * sx, 0.5 * sy, 0.5 * sz))
+    for (p, q) in ((1, 2), (1, 3), (2, 3)):
+        for s in (1, -1):
+            v = [0.0, 0.0, 0.0, 0.0]
+            v[p] = c
+            v[q] = s * c
+            ops.append(tuple(v))
+    return np.array(ops, dtype=np.float64)
+
+
+_CUBIC = cubic_symmetry_quaternions()
+
+
+def disorientation_cubic(qa, qb) -> float:
+    """Smallest rotation angle (radians) taking crystal a to crystal b under
+    cubic symmetry: 2 acos(max_k |w(conj(qa) qb S_k)|)."""
+    qa = np.asarray(qa, dtype=np.float64)
+    conj = qa * np.array([1.0, -1.0, -1.0, -1.0])
+    dq = _qmul(conj, np.asarray(qb, dtype=np.float64))
+    best = max(abs(_qmul(dq, s)[0]) for s in _CUBIC)
+    return 2.0 * math.acos(min(1.0, best))
+
+
+def read_shockley(theta: float, theta_max: float) -> float:
+    """Normalised Read-Shockley energy (Sec. 4.3): (t)(1 - ln t) with
+    t = theta / theta_max below theta_max, 1 above."""
+    if theta >= theta_max:
+        return 1.0
+    if theta <= 0.0:
+        return 0.0
+    t = theta / theta_max
+    return t * (1.0 - math.log(t))
+
+
+def mobility_step(theta: float, theta_max: float, low: float) -> float:
+    """Normalised mobility: ``low`` below theta_max, 1 above."""
+    return low if theta < theta_max else 1.0
+
+
+def mobility_eq20(theta: float) -> float:
+    """Eq. (20): mu = 1 - 0.99 exp(-5 (theta / 15 deg)^9)."""
+    return 1.0 - 0.99 * math.exp(-5.0 * (theta / math.radians(15.0)) ** 9)
+
+
+MU0 = 4.0e-7 * math.pi
+
+
+def magnetic_energy_density(b_tesla: float, dchi: float, cos2: float) -> float:
+    """Eqs. (18)-(19): orientation-dependent part of mu0 H^2 chi / 2 with
+    H = B / mu0, chi = chi_perp + dchi cos^2(theta); chi_perp cancels in
+    every difference, so E = B^2 dchi cos^2 / (2 mu0) in J/m^3."""
+    return b_tesla * b_tesla * dchi * cos2 / (2.0 * MU0)
+
+
+def c_axis(q) -> np.ndarray:
+    """Crystal [001] direction rotated by the unit quaternion q = (w, x, y, z)."""
+    w, x, y, z = q
+    return np.array([2.0 * (x * z + w * y), 2.0 * (y * z - w * x), 1.0 - 2.0 * (x * x + y * y)])
+
+
+@dataclass
+class Physics:
+    """Per-pair weights and per-grain bulk energies of Eq. (10).
+
+    weight(i, j) -> (w_ij, M_ij): w = M* gamma* in (0, 1] scales the
+    curvature flow, M* in (0, 1] the bulk term.  ``energy[i]`` is the bulk
+    energy of grain i in grid units (E_i h / gamma_max, Eq. (13))."""
+    weight: callable
+    energy: np.ndarray
+    _cache: dict = field(default_factory=dict)
+
+    def pair(self, i, j):
+        key = (i, j)
+        if key not in self._cache:
+            self._cache[key] = self.weight(i, j)
+        return self._cache[key]
+
+    def blend_terms(self, gid, idf, dt):
+        """Per-cell w and bulk = M (e_j - e_i) dt for pair (gid, ID(x));
+        w = 1 and bulk = 0 where the ID-field is -1."""
+        w = np.ones(idf.shape)
+        bulk = np.zeros(idf.shape)
+        for j in np.unique(idf):
+            if j < 0:
+                continue
+            wij, mij = self.pair(gid, int(j))
+            sel = idf == j
+            w[sel] = wij
+            bulk[sel] = mij * (self.energy[int(j)] - self.energy[gid]) * dt
+        return w, bulk
+
+
+def isotropic_physics(energy) -> Physics:
+    """w = M = 1 for every pair, per-grain bulk energies (Sec. 4.1 / 4.3)."""
+    return Physics(weight=lambda i, j: (1.0, 1.0), energy=np.asarray(energy, dtype=np.float64))
+
+
+def read_shockley_physics(quats, theta_max_deg=15.0, mob_low=0.1, mobility="step",
+                          w_floor=1e-3) -> Physics:
+    """Read-Shockley energy and low/high-angle mobility per pair (Sec. 4.3),
+    cubic disorientation; w = max(w_floor, M* gamma*)."""
+    qs = np.asarray(quats, dtype=np.float64)
+    tm = math.radians(theta_max_deg)
+
+    def weight(i, j):
+        th = disorientation_cubic(qs[i], qs[j])
+        m = mobility_step(th, tm, mob_low) if mobility == "step" else mobility_eq20(th)
+        return max(w_floor, m * read_shockley(th, tm)), m
+    return Physics(weight=weight, energy=np.zeros(len(qs)))
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Microstructure:
+    shape: tuple                 # (Nz, Ny, Nx)
+    grains: list
+    eps: float = 7.0
+    halo: int = 5
+    radius: int = 5
+    physics: Physics | None = None
+    time: float = 0.0
+
+
+def box_candidates(ms: Microstructure):
+    """Grains whose boxes meet each box (Sec. 3.1's neighbour preselection)."""
+    alive = [g for g in ms.grains if g.alive]
+    out = {g.gid: set() for g in ms.grains}
+    for a_i, gi in enumerate(alive):
+        for gj in alive[a_i + 1:]:
+            if boxes_intersect(gi, gj, ms.shape):
+                out[gi.gid].add(gj.gid)
+                out[gj.gid].add(gi.gid)
+    return out
+
+
+@dataclass
+class StepParts:
+    """Intermediate results of one step, per grain id."""
+    phip: dict
+    m: dict
+    idm: dict
+    phic: dict
+    phi: dict
+
+
+def step_parts(ms: Microstructure, dt: float, brute_force: bool = False) -> StepParts:
+    """Predictor, corrector and re-initialisation of Algorithm 1 on the
+    current boxes, without the box update."""
+    taps = heat_kernel_taps(dt, ms.radius)
+    axes = spatial_axes(ms.shape)
+    phip = {}
+    for g in ms.grains:
+        if g.alive:
+            phip[g.gid] = predict(g, ms.shape, taps, ms.eps, ms.physics, dt)
+    cand = None if brute_force else box_candidates(ms)
+    parts = StepParts(phip, {}, {}, {}, {})
+    for g in ms.grains:
+        if not g.alive:
+            continue
+        m, idm = neighbour_max(g.gid, ms.grains, phip, ms.shape, ms.eps,
+                               None if cand is None else cand[g.gid])
+        parts.m[g.gid] = m
+        parts.idm[g.gid] = idm
+        parts.phic[g.gid] = compare(phip[g.gid], m)
+        parts.phi[g.gid] = np.clip(redistance(parts.phic[g.gid], full_axes(g, ms.shape), ms.eps, axes),
+                                   -ms.eps, ms.eps)
+    return parts
+
+
+def step(ms: Microstructure, dt: float, brute_force: bool = False) -> Microstructure:
+    """One pass of Algorithm 1's loop body plus the box update (R6)."""
+    parts = step_parts(ms, dt, brute_force)
+    grains = []
+    for g in ms.grains:
+        if not g.alive:
+            grains.append(g)
+            continue
+        idf = parts.idm[g.gid] if ms.physics is not None else None
+        upd = Grain(g.gid, g.origin, parts.phi[g.gid], idf)
+        grains.append(box_update(upd, ms.shape, ms.halo, ms.eps))
+    return Microstructure(ms.shape, grains, ms.eps, ms.halo, ms.radius, ms.physics, ms.time + dt)
+
+
+def run(ms: Microstructure, n: int, dt: float) -> Microstructure:
+    for _ in range(n):
+        ms = step(ms, dt)
+    return ms
+
+
+# --------------------------------------------------------------------------
+# outputs
+# --------------------------------------------------------------------------
+
+
+def owner_map(ms: Microstructure) -> np.ndarray:
+    """owner(x) = argmax_i phi_i(x) over the boxes that cover x, lowest id on
+    ties, -1 where no box covers x."""
+    Nz, Ny, Nx = ms.shape
+    best = np.full(ms.shape, -np.inf)
+    own = np.full(ms.shape, -1, dtype=np.int64)
+    allpos = (np.arange(Nz), np.arange(Ny), np.arange(Nx))
+    for g in ms.grains:
+        if not g.alive:
+            continue
+        v, _ = sample(g, allpos, ms.shape, -np.inf)
+        better = v > best
+        best = np.where(better, v, best)
+        own = np.where(better, g.gid, own)
+    return own
+
+
+def volumes(ms: Microstructure) -> np.ndarray:
+    """V_i = sum_x H(phi_i(x)), H(phi) = clamp(phi + 1/2, 0, 1) (a unit ramp
+    across the zero level); 0 for extinct grains."""
+    out = np.zeros(len(ms.grains))
+    for g in ms.grains:
+        if g.alive:
+            out[g.gid] = float(np.clip(g.phi + 0.5, 0.0, 1.0).sum())
+    return out
+
+
+def voxel_counts(ms: Microstructure) -> np.ndarray:
+    own = owner_map(ms)
+    return np.bincount(own[own >= 0].ravel(), minlength=len(ms.grains))
+
+
+# --------------------------------------------------------------------------
+# initial microstructure: Sec. 2.1.3 (tessellation S, local grids Omega_i)
+# --------------------------------------------------------------------------
+
+
+def power_distance(cells_xyz: np.ndarray, s, w, n_xyz) -> np.ndarray:
+    """|x - s|^2 - w with the minimum-image displacement per axis:
+    d = x - s; d = d - N rint(d / N); (dx^2 + dy^2) + dz^2 - w."""
+    d = []
+    for a in range(3):
+        da = cells_xyz[..., a] - s[a]
+        da = da - n_xyz[a] * np.rint(da / n_xyz[a])
+        d.append(da)
+    r = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+    return r - w if w is not None else r
+
+
+def labels_at(cells_xyz: np.ndarray, seeds, weights, n_xyz) -> np.ndarray:
+    """Voronoi (power) label of each cell: argmin_i of power_distance, lowest
+    id on ties."""
+    best = np.full(cells_xyz.shape[:-1], np.inf)
+    lab = np.full(cells_xyz.shape[:-1], -1, dtype=np.int64)
+    for i in range(len(seeds)):
+        d = power_distance(cells_xyz, seeds[i], None if weights is None else weights[i], n_xyz)
+        better = d < best
+        best = np.where(better, d, best)
+        lab = np.where(better, i, lab)
+    return lab
+
+
+def domain_cells(shape) -> np.ndarray:
+    """Integer cell coordinates (x, y, z) of the whole domain, shape (Nz, Ny, Nx, 3)."""
+    Nz, Ny, Nx = shape
+    z, y, x = np.meshgrid(np.arange(Nz), np.arange(Ny), np.arange(Nx), indexing="ij")
+    return np.stack([x, y, z], axis=-1).astype(np.float64)
+
+
+def face_neighbours(labels: np.ndarray, n_grains: int):
+    """Nb(i): grains whose cells touch grain i's cells across a face (periodic)."""
+    nb = [set() for _ in range(n_grains)]
+    axes = spatial_axes(labels.shape)
+    for a in axes:
+        other = np.roll(labels, -1, axis=a)
+        diff = labels != other
+        for p, q in set(zip(labels[diff].ravel().tolist(), other[diff].ravel().tolist())):
+            nb[p].add(q)
+            nb[q].add(p)
+    return nb
+
+
+def minimum_image_offset(x: np.ndarray, r: int, n: int) -> np.ndarray:
+    """Integer offset e of cell x from cell r on a ring of n cells, chosen in
+    (-n/2, n/2] for even n ([-(n-1)/2, (n-1)/2] for odd n)."""
+    e = (x - r) % n
+    return np.where(e > n // 2, e - n, e)
+
+
+def initial_box(cells_xyz_int: np.ndarray, seed_xyz, n_xyz, halo: int):
+    """Box of one grain: bbox of its label cells (offsets from the rounded
+    seed by minimum image) grown by ``halo``; returns origin (z, y, x) and
+    dims (z, y, x)."""
+    origin = [0, 0, 0]
+    dims = [1, 1, 1]
+    for a in range(3):
+        n = int(n_xyz[a])
+        if n == 1:
+            continue
+        r = int(np.rint(seed_xyz[a])) % n
+        e = minimum_image_offset(cells_xyz_int[:, a], r, n)
+        lo, hi = int(e.min()), int(e.max())
+        ext = hi - lo + 1 + 2 * halo
+        za = 2 - a   # (z, y, x) index of axis a of (x, y, z)
+        dims[za] = min(ext, n)
+        origin[za] = (r + lo - halo) % n
+    return tuple(origin), tuple(dims)
+
+
+def bisector_sdf(pos_xyz: np.ndarray, i: int, nbs, seeds, weights, n_xyz, eps):
+    """Reading R7: phi_i(x) = clamp(min_{j in Nb(i)} ((|b|^2 - w_j) - (|a|^2 - w_i))
+    / (2 |b - a|), -eps, eps), a = x - s_i, b = x - s_j (minimum images), and the
+    minimising j (lowest id on ties; -1 when Nb(i) is empty)."""
+    def disp(s):
+        out = []
+        for a in range(3):
+            d = pos_xyz[..., a] - s[a]
+            out.append(d - n_xyz[a] * np.rint(d / n_xyz[a]))
+        return out
+    a_ = disp(seeds[i])
+    wi = 0.0 if weights is None else weights[i]
+    pa = (a_[0] * a_[0] + a_[1] * a_[1]) + a_[2] * a_[2] - wi
+    best = np.full(pos_xyz.shape[:-1], np.inf)
+    arg = np.full(pos_xyz.shape[:-1], -1, dtype=np.int64)
+    for j in sorted(nbs):
+        b_ = disp(seeds[j])
+        wj = 0.0 if weights is None else weights[j]
+        pb = (b_[0] * b_[0] + b_[1] * b_[1]) + b_[2] * b_[2] - wj
+        dx, dy, dz = b_[0] - a_[0], b_[1] - a_[1], b_[2] - a_[2]
+        den = 2.0 * np.sqrt((dx * dx + dy * dy) + dz * dz)
+        v = (pb - pa) / den
+        better = v < best
+        best = np.where(better, v, best)
+        arg = np.where(better, j, arg)
+    best = np.where(np.isfinite(best), best, eps)
+    return np.clip(best, -eps, eps), arg
+
+
+def tessellate(shape, seeds, weights=None, eps=7.0, halo=5, radius=5, physics=None,
+               with_idf=False) -> Microstructure:
+    """Initialisation of Algorithm 1: one grain per (power) Voronoi cell of
+    the seeds, its box (R6's rule applied to the label cells) and its
+    initial function (R7).  Grains with no cell are extinct from the start."""
+    Nz, Ny, Nx = shape
+    n_xyz = (Nx, Ny, Nz)
+    seeds = np.asarray(seeds, dtype=np.float64)
+    cells = domain_cells(shape)
+    lab = labels_at(cells, seeds, weights, n_xyz)
+    G = len(seeds)
+    nbs = face_neighbours(lab, G)
+    grains = []
+    for i in range(G):
+        sel = lab == i
+        if not sel.any():
+            grains.append(Grain(i, (0, 0, 0), np.full((1, 1, 1), -eps), None, alive=False))
+            continue
+        pts = cells[sel].astype(np.int64)
+        origin, dims = initial_box(pts, seeds[i], n_xyz, halo)
+        g = Grain(i, origin, np.zeros(dims))
+        pz, py, px = box_positions(g, shape)
+        z, y, x = np.meshgrid(pz, py, px, indexing="ij")
+        pos = np.stack([x, y, z], axis=-1).astype(np.float64)
+        g.phi, arg = bisector_sdf(pos, i, nbs[i], seeds, weights, n_xyz, eps)
+        if with_idf or physics is not None:
+            g.idf = arg
+        grains.append(g)
+    return Microstructure(tuple(shape), grains, eps, halo, radius, physics)
+
+
+def labels_of_tessellation(shape, seeds, weights=None) -> np.ndarray:
+    Nz, Ny, Nx = shape
+    return labels_at(domain_cells(shape), np.asarray(seeds, dtype=np.float64), weights, (Nx, Ny, Nz))
+
+
+def single_grain_state(shape, phi_fn, eps=7.0, halo=5, radius=5):
+    """Two-grain state for analytic tests: grain 0 has phi = clamp(phi_fn(x), +-eps)
+    on the bbox of its positive set grown by the halo; grain 1 is the
+    complement (-phi_fn) on the whole domain.  ``phi_fn`` maps (z, y, x) index
+    grids to signed distances."""
+    Nz, Ny, Nx = shape
+    z, y, x = np.meshgrid(np.arange(Nz), np.arange(Ny), np.arange(Nx), indexing="ij")
+    d = phi_fn(z.astype(np.float64), y.astype(np.float64), x.astype(np.float64))
+    full = Grain(0, (0, 0, 0), np.clip(d, -eps, eps))
+    g0 = box_update(full, shape, halo, eps)
+    g1 = Grain(1, (0, 0, 0), np.clip(-d, -eps, eps))
+    return Microstructure(tuple(shape), [g0, g1], eps, halo, radius)
