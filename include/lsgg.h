@@ -1,0 +1,191 @@
+/*
+ * lsgg.h -- C ABI of the GB300 (sm_103a) local level-set grain-growth library.
+ *
+ * Method: C. Miessen, N. Velinov, G. Gottstein, L.A. Barrales-Mora, "A highly
+ * efficient 3D level-set grain growth algorithm tailored for ccNUMA
+ * architecture", arXiv:1701.06658.  Each grain i carries its own level-set
+ * function phi_i on a local box Omega_i (its bounding box plus a halo,
+ * Sec. 2.1.3, Fig. 1); one time step is Algorithm 1's loop body:
+ *   predictor     phi_p = G(dt) * phi           (Eqs. (7)-(9); Eq. (10) with physics)
+ *   corrector     phi_c = (phi_p - max_{j!=i} phi_p_j) / 2        (Eq. (16))
+ *   re-init       taxicab signed distance to the zero level        (Sec. 2.1.6)
+ *   box update    bbox{phi > 0} + halo, neighbour data              (Secs. 2.1.3, 3.1)
+ *
+ * Units: grid units (cell spacing h = 1, M_max * gamma_max = 1).  The domain is
+ * periodic, nx * ny * nz cells, x fastest; nz == 1 is a 2D domain.
+ *
+ * Conventions for every function below:
+ *   - return LSGG_OK (0) on success, a negative LSGG_ERR_* code otherwise;
+ *     lsgg_status_string() names it.  No function throws or aborts.
+ *   - host pointers are caller-owned; the library copies what it needs and
+ *     keeps no host pointer after the call returns.
+ *   - a context owns all of its device memory; lsgg_destroy frees it.
+ *   - a context is not thread-safe; distinct contexts are independent.
+ *   - every device computation runs in the library's CUDA kernels; there is
+ *     no CPU fallback.  Without a usable CUDA device, calls that compute
+ *     return LSGG_ERR_CUDA.
+ */
+#ifndef LSGG_H
+#define LSGG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define LSGG_OK                 0
+#define LSGG_ERR_INVALID_ARG   -1   /* a size, pointer or config field is out of range */
+#define LSGG_ERR_OUT_OF_MEMORY -2   /* a device allocation failed */
+#define LSGG_ERR_OVER_BUDGET   -3   /* a server admission would exceed its HBM budget */
+#define LSGG_ERR_CUDA          -4   /* a CUDA runtime call failed (no device, launch error) */
+#define LSGG_ERR_TIMEOUT       -5   /* a bounded wait expired (device queue or host wait) */
+#define LSGG_ERR_NOT_READY     -6   /* a served request has not finished yet */
+#define LSGG_ERR_CAPACITY      -7   /* a caller buffer is too small (see *n_out) */
+#define LSGG_ERR_UNSUPPORTED   -8   /* a requested variant is not built */
+
+/* ---------------------------------------------------------------- config */
+#define LSGG_INIT_VORONOI   0   /* Voronoi tessellation of the seeds */
+#define LSGG_INIT_LAGUERRE  1   /* power diagram: seeds plus weights */
+
+#define LSGG_PHYSICS_IDEAL          0  /* w = 1, no bulk term: phi_p = G * phi */
+#define LSGG_PHYSICS_READ_SHOCKLEY  1  /* per-pair w = M* gamma*(theta), cubic disorientation (Sec. 4.3) */
+#define LSGG_PHYSICS_MAGNETIC       2  /* w = 1, per-grain bulk energy (Eqs. (18)-(19)) */
+
+#define LSGG_STORAGE_FP32  0   /* phi stored in FP32 */
+#define LSGG_STORAGE_BF16  1   /* phi stored in BF16 between steps, FP32 arithmetic */
+
+#define LSGG_EXEC_BATCHED  0   /* persistent per-size-class kernels over the packed box list */
+#define LSGG_EXEC_PLAIN    1   /* comparator: separate launches per grain per sub-step */
+
+#define LSGG_MOBILITY_STEP  0  /* mob_low below theta_max, 1 above */
+#define LSGG_MOBILITY_EQ20  1  /* Eq. (20): 1 - 0.99 exp(-5 (theta / 15 deg)^9) */
+
+typedef struct lsgg_config {
+    int32_t nx, ny, nz;        /* domain size in cells; nz == 1 selects 2D */
+    int32_t n_grains;          /* number of seeds (grains), >= 1 */
+    uint64_t seed;             /* SplitMix64 seed for generated seeds / weights / orientations */
+    int32_t halo;              /* box halo in cells around the positive set (default 5) */
+    int32_t radius;            /* heat-kernel half width R in cells, 1..7 (default 5) */
+    float eps;                 /* band half width: phi is clamped to [-eps, eps] (default 7) */
+    int32_t init_kind;         /* LSGG_INIT_* */
+    int32_t physics;           /* LSGG_PHYSICS_* */
+    int32_t storage;           /* LSGG_STORAGE_* */
+    int32_t exec;              /* LSGG_EXEC_* */
+    int32_t mobility_law;      /* LSGG_MOBILITY_* (READ_SHOCKLEY only) */
+    int32_t device;            /* CUDA device ordinal */
+    double theta_max_deg;      /* Read-Shockley / mobility cut-off angle (default 15) */
+    double mob_low;            /* low-angle mobility for LSGG_MOBILITY_STEP (default 0.1) */
+    double lognormal_sigma;    /* LAGUERRE: sigma of the lognormal radii (default 0.5) */
+    double big_fraction;       /* LAGUERRE: fraction of enlarged grains (default 0.01) */
+    double big_volume;         /* LAGUERRE: their volume factor (default 5) */
+    double field_dir[3];       /* MAGNETIC: field direction (normalised by the library) */
+    double energy_scale;       /* MAGNETIC: grid-unit bulk energy of cos^2 = 1, i.e.
+                                  B^2 dchi h / (2 mu0 gamma_max) (Eqs. (13), (18)) */
+    double arena_slack;        /* device box arena capacity / initial need (default 1.5) */
+    const double* seeds;       /* optional n_grains x 3 (x, y, z) seed points in cells */
+    const double* weights;     /* optional n_grains power weights (LAGUERRE) */
+    const double* quats;       /* optional n_grains x 4 unit quaternions (w, x, y, z) */
+    const double* energy;      /* optional n_grains bulk energies in grid units (MAGNETIC) */
+} lsgg_config;
+
+/* Fill *cfg with the defaults above (64^3, 50 grains, seed 1, ideal, FP32, batched). */
+void lsgg_config_default(lsgg_config* cfg);
+
+/* --------------------------------------------------------------- lifecycle */
+typedef struct lsgg_ctx lsgg_ctx;
+
+/* Algorithm 1, Initialization (Sec. 2.1.3, reading of Sec. 3.1's tessellation
+ * input): seeds (given, or drawn from cfg->seed by SplitMix64 as in
+ * lsgg_generate_seeds) -> Voronoi / power labels on the grid (FP64, minimum
+ * image, lowest id on ties) -> per grain the bbox of its cells grown by the
+ * halo (an axis reaching the domain size becomes full and periodic) -> phi_i
+ * = min over face-adjacent grains j of the signed distance to the (power)
+ * bisector plane, clamped to [-eps, eps].  Grains with no cell start extinct.
+ * `stream` is a cudaStream_t (NULL: the library creates its own).  The call
+ * synchronises before returning.  On success *out owns the device state. */
+int lsgg_create_microstructure(const lsgg_config* cfg, void* stream, lsgg_ctx** out);
+
+/* n time steps of Algorithm 1 with time dt (grid units; dt = 1 gives a heat
+ * kernel of variance 2 per axis).  Enqueues on the context's stream and
+ * returns after enqueue; lsgg_sync waits.  dt must satisfy 0 < dt <= 4. */
+int lsgg_step(lsgg_ctx* ctx, int32_t n, double dt);
+
+/* Wait for enqueued work, at most timeout_ms (< 0: no limit).  Handles a box
+ * arena that ran out of room by growing it and finishing the steps.  Returns
+ * LSGG_ERR_TIMEOUT if the wait expired (the work keeps running). */
+int lsgg_sync(lsgg_ctx* ctx, int64_t timeout_ms);
+
+/* Per-grain volume V_i = sum_x H(phi_i(x)), H(phi) = clamp(phi + 1/2, 0, 1),
+ * FP64 compensated sums in a fixed order (deterministic); index = grain id,
+ * 0 for extinct grains.  out: host array of cap >= n_grains doubles;
+ * *n_out = n_grains.  Synchronises. */
+int lsgg_grain_volumes(lsgg_ctx* ctx, double* out, int64_t cap, int64_t* n_out);
+
+/* owner(x) = argmax_i phi_i(x) over the boxes covering x, lowest id on ties,
+ * -1 where no box covers x; x fastest, n_cells = nx*ny*nz int32s.  Synchronises. */
+int lsgg_voxel_owner(lsgg_ctx* ctx, int32_t* out, int64_t n_cells);
+
+/* Free all device memory of the context (after finishing its work). */
+int lsgg_destroy(lsgg_ctx* ctx);
+
+const char* lsgg_status_string(int status);
+
+/* The context's CUDA stream (a cudaStream_t) so callers can order their own
+ * work and time the library's kernels with events on it. */
+void* lsgg_get_stream(lsgg_ctx* ctx);
+
+/* sizeof(lsgg_config) as compiled into the library: bindings check their
+ * struct layout against it before calling lsgg_create_microstructure. */
+size_t lsgg_abi_config_size(void);
+
+/* ------------------------------------------------------------- inspection */
+typedef struct lsgg_stats {
+    int64_t steps_done;        /* steps completed since creation */
+    int64_t alive;             /* grains with a positive cell */
+    int64_t box_cells;         /* sum over alive grains of box volume (cells) */
+    int64_t arena_capacity;    /* device arena capacity per buffer (elements) */
+    double superimposition;    /* box_cells / (nx*ny*nz) (Sec. 5.2.3) */
+    int64_t device_bytes;      /* device memory held by the context */
+    int32_t n_classes;         /* box-size classes of the batched path */
+    int32_t class_count[8];    /* boxes per class at the last box update */
+} lsgg_stats;
+
+int lsgg_get_stats(lsgg_ctx* ctx, lsgg_stats* out);
+
+/* Boxes of all grains: out[7*i .. 7*i+6] = alive, ox, oy, oz, nx, ny, nz
+ * (origin in [0, N) per axis).  cap in int32s, >= 7 * n_grains.  Synchronises. */
+int lsgg_get_boxes(lsgg_ctx* ctx, int32_t* out, int64_t cap);
+
+/* phi of all alive grains, packed in grain-id order, each box x fastest with
+ * no padding (sum of nx*ny*nz over alive grains floats).  *n_out = that
+ * count; LSGG_ERR_CAPACITY if cap is smaller.  Synchronises. */
+int lsgg_get_phi(lsgg_ctx* ctx, float* out, int64_t cap, int64_t* n_out);
+
+/* Replace the state: boxes as in lsgg_get_boxes (7 int32 per grain), phi
+ * packed as in lsgg_get_phi, idf (optional, may be NULL) the ID-field packed
+ * the same way (-1 = no neighbour).  Grows the arena if needed.  Synchronises. */
+int lsgg_set_state(lsgg_ctx* ctx, const int32_t* boxes, const float* phi, const int32_t* idf);
+
+/* One step like lsgg_step(ctx, 1, dt) that also copies the step's
+ * intermediate fields to host arrays (each packed like lsgg_get_phi in the
+ * boxes the step ran on, i.e. lsgg_get_boxes before the call; any pointer may
+ * be NULL): phip = predictor output, m = max_{j != i} phi_p_j, idm = its
+ * argmax (-1 when no other grain exceeds -eps), phic = comparison output,
+ * phin = re-initialised phi before the box update.  Synchronises. */
+int lsgg_debug_step(lsgg_ctx* ctx, double dt, float* phip, float* m, int32_t* idm,
+                    float* phic, float* phin);
+
+/* SplitMix64 seed points (host only, no device needed): out[3*i + a] =
+ * u01(seed, 3*i + a) * N_a for a = x, y, z with
+ * u01(s, k) = (mix(s + (k + 1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53 and
+ * mix the SplitMix64 finaliser; z = 0 in 2D.  out holds 3 * n doubles. */
+int lsgg_generate_seeds(uint64_t seed, int32_t n, int32_t nx, int32_t ny, int32_t nz, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSGG_H */

@@ -1,0 +1,652 @@
+// C ABI of the library (declared in include/lsgg.h): context lifecycle, the
+// step loop (eager launches or a captured CUDA graph), arena growth, outputs
+// and test hooks.  Host code only marshals sizes and pointers; every
+// computation on grain data runs in the kernels of step.cu, init.cu,
+// outputs.cu and plain.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "lsgg_internal.cuh"
+#include "../../include/lsgg.h"
+
+namespace lsgg {
+cudaError_t launch_init(const Domain& D, int G, const double* d_seeds, const double* d_weights, int* d_labels,
+                        unsigned* d_bits, long long words_per_row, int* d_bb, Box* d_cur, cudaStream_t s);
+cudaError_t launch_sdf(const Domain& D, int G, const Box* d_cur, const double* d_seeds, const double* d_weights,
+                       const unsigned* d_bits, long long words_per_row, float* X, int* IDF, int* d_status,
+                       cudaStream_t s);
+cudaError_t launch_volumes(const Domain& D, int G, const Box* cur, const Box* prev, const float* X, double* out,
+                           cudaStream_t s);
+cudaError_t launch_owner(const Domain& D, int G, const Box* cur, const Box* prev, const float* X,
+                         unsigned long long* F, int* out, cudaStream_t s);
+cudaError_t launch_pack_state(const Domain& D, int G, const Box* cur, const Box* prev, const float* X,
+                              const long long* packed_off, float* out, cudaStream_t s);
+cudaError_t launch_pack_cur(int G, const Box* cur, const void* arena, const long long* packed_off, void* out,
+                            cudaStream_t s);
+cudaError_t launch_unpack_state(int G, const Box* cur, const float* packed, const int* packed_idf,
+                                const long long* packed_off, float* X, int* IDF, cudaStream_t s);
+long long large_class_scratch_floats(const Domain& d);
+}  // namespace lsgg
+
+using namespace lsgg;
+
+struct lsgg_ctx {
+    lsgg_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Domain dom{};
+    int G = 0;
+    StepBuffers B{};
+    Box* d_boxes = nullptr;          // 2 * G: prev then cur
+    double* d_seeds = nullptr;
+    double* d_weights = nullptr;
+    float* d_energy = nullptr;
+    double* d_vol = nullptr;
+    long long* d_packed_off = nullptr;
+    StepState* h_st = nullptr;       // pinned mirror for status reads
+    long long steps_target = 0;      // steps requested since creation
+    double last_dt = 0.0;
+    long long device_bytes = 0;
+    PhysicsDev phys{};
+    // CUDA graph of one step (batched path)
+    cudaGraphExec_t graph = nullptr;
+    double graph_dt = -1.0;
+    std::vector<void*> allocations;
+};
+
+namespace {
+
+int fail_cuda(cudaError_t e) {
+    (void)e;
+    return LSGG_ERR_CUDA;
+}
+
+#define CK(call)                                        \
+    do {                                                \
+        cudaError_t e__ = (call);                       \
+        if (e__ != cudaSuccess) return fail_cuda(e__);  \
+    } while (0)
+
+template <class T>
+int dalloc(lsgg_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? LSGG_ERR_OUT_OF_MEMORY : LSGG_ERR_CUDA;
+    }
+    c->allocations.push_back(q);
+    c->device_bytes += (long long)bytes;
+    *p = static_cast<T*>(q);
+    return LSGG_OK;
+}
+
+void dfree(lsgg_ctx* c, void* p) {
+    if (!p) return;
+    auto it = std::find(c->allocations.begin(), c->allocations.end(), p);
+    if (it != c->allocations.end()) c->allocations.erase(it);
+    cudaFree(p);
+}
+
+uint64_t splitmix_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+double u01(uint64_t seed, uint64_t stream, uint64_t index) {
+    uint64_t k = (stream << 40) + index;
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    return (double)(splitmix_mix(z) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+Taps make_taps(double dt, int R) {
+    Taps t{};
+    t.radius = R;
+    double sum = 0.0, g[kMaxTaps];
+    for (int k = -R; k <= R; ++k) {
+        g[k + R] = std::exp(-(double)k * k / (4.0 * dt));
+        sum += g[k + R];
+    }
+    for (int k = 0; k < 2 * R + 1; ++k) t.g[k] = (float)(g[k] / sum);
+    return t;
+}
+
+long long host_box_elems(const Box& b) { return box_elems(b); }
+
+int read_state(lsgg_ctx* c) {
+    CK(cudaMemcpyAsync(c->h_st, c->B.st, sizeof(StepState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LSGG_OK;
+}
+
+// Grow the arenas to hold `need` elements, keeping the state (prev layout).
+int grow_arena(lsgg_ctx* c, long long need) {
+    long long cap = std::max<long long>(need + need / 4, c->B.cap * 2);
+    float *X2 = nullptr, *Y2 = nullptr;
+    int* I2 = nullptr;
+    int r;
+    if ((r = dalloc(c, &X2, cap)) != LSGG_OK) return r;
+    if ((r = dalloc(c, &Y2, cap)) != LSGG_OK) return r;
+    if ((r = dalloc(c, &I2, cap)) != LSGG_OK) return r;
+    CK(cudaMemcpyAsync(X2, c->B.X, (size_t)c->B.cap * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(I2, c->B.IDF, (size_t)c->B.cap * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->device_bytes -= 3 * c->B.cap * 4;
+    dfree(c, c->B.X);
+    dfree(c, c->B.Y);
+    dfree(c, c->B.IDF);
+    c->B.X = X2;
+    c->B.Y = Y2;
+    c->B.IDF = I2;
+    c->B.cap = cap;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return LSGG_OK;
+}
+
+// Assign arena offsets / classes for the `cur` boxes (no resize), growing if needed.
+int relayout(lsgg_ctx* c) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        StepState z{};
+        // keep steps_done, clear status/halt
+        CK(cudaMemcpyAsync(c->h_st, c->B.st, sizeof(StepState), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        z = *c->h_st;
+        z.status = 0;
+        z.halt = 0;
+        *c->h_st = z;
+        CK(cudaMemcpyAsync(c->B.st, c->h_st, sizeof(StepState), cudaMemcpyHostToDevice, c->stream));
+        CK(launch_box_update(c->B, true, c->stream));
+        int r = read_state(c);
+        if (r != LSGG_OK) return r;
+        if (c->h_st->status == LSGG_ERR_CAPACITY) {
+            r = grow_arena(c, c->h_st->box_cells);
+            if (r != LSGG_OK) return r;
+            continue;
+        }
+        return LSGG_OK;
+    }
+    return LSGG_ERR_OUT_OF_MEMORY;
+}
+
+int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg);
+
+}  // namespace
+
+extern "C" {
+
+void lsgg_config_default(lsgg_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->nx = cfg->ny = cfg->nz = 64;
+    cfg->n_grains = 50;
+    cfg->seed = 1;
+    cfg->halo = 5;
+    cfg->radius = 5;
+    cfg->eps = 7.0f;
+    cfg->init_kind = LSGG_INIT_VORONOI;
+    cfg->physics = LSGG_PHYSICS_IDEAL;
+    cfg->storage = LSGG_STORAGE_FP32;
+    cfg->exec = LSGG_EXEC_BATCHED;
+    cfg->mobility_law = LSGG_MOBILITY_STEP;
+    cfg->theta_max_deg = 15.0;
+    cfg->mob_low = 0.1;
+    cfg->lognormal_sigma = 0.5;
+    cfg->big_fraction = 0.01;
+    cfg->big_volume = 5.0;
+    cfg->field_dir[0] = 0.0;
+    cfg->field_dir[1] = std::cos(32.0 * M_PI / 180.0);
+    cfg->field_dir[2] = std::sin(32.0 * M_PI / 180.0);
+    cfg->energy_scale = 0.0;
+    cfg->arena_slack = 1.5;
+}
+
+const char* lsgg_status_string(int s) {
+    switch (s) {
+        case LSGG_OK: return "ok";
+        case LSGG_ERR_INVALID_ARG: return "invalid argument";
+        case LSGG_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case LSGG_ERR_OVER_BUDGET: return "over the HBM budget";
+        case LSGG_ERR_CUDA: return "CUDA error";
+        case LSGG_ERR_TIMEOUT: return "timed out";
+        case LSGG_ERR_NOT_READY: return "not ready";
+        case LSGG_ERR_CAPACITY: return "buffer too small";
+        case LSGG_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+void* lsgg_get_stream(lsgg_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+size_t lsgg_abi_config_size(void) { return sizeof(lsgg_config); }
+
+int lsgg_generate_seeds(uint64_t seed, int32_t n, int32_t nx, int32_t ny, int32_t nz, double* out) {
+    if (!out || n <= 0 || nx <= 0 || ny <= 0 || nz <= 0) return LSGG_ERR_INVALID_ARG;
+    const double N[3] = {(double)nx, (double)ny, (double)nz};
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) out[3 * i + a] = u01(seed, 0, 3 * (uint64_t)i + a) * N[a];
+    if (nz == 1)
+        for (int i = 0; i < n; ++i) out[3 * i + 2] = 0.0;
+    return LSGG_OK;
+}
+
+int lsgg_destroy(lsgg_ctx* c) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (void* p : c->allocations) cudaFree(p);
+    if (c->h_st) cudaFreeHost(c->h_st);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return LSGG_OK;
+}
+
+static int create_impl(const lsgg_config* cfg, void* stream, lsgg_ctx** out);
+
+int lsgg_create_microstructure(const lsgg_config* cfg, void* stream, lsgg_ctx** out) {
+    if (!cfg || !out) return LSGG_ERR_INVALID_ARG;
+    *out = nullptr;
+    int r = create_impl(cfg, stream, out);
+    return r;
+}
+
+static int validate(const lsgg_config* cfg) {
+    if (cfg->nx < 2 || cfg->ny < 2 || cfg->nz < 1) return LSGG_ERR_INVALID_ARG;
+    if ((long long)cfg->nx * cfg->ny * cfg->nz > (1LL << 31)) return LSGG_ERR_INVALID_ARG;
+    if (cfg->n_grains < 1 || cfg->n_grains > (1 << 24)) return LSGG_ERR_INVALID_ARG;
+    if (cfg->halo < 1 || cfg->radius < 1 || cfg->radius > kMaxRadius) return LSGG_ERR_INVALID_ARG;
+    if (!(cfg->eps > 1.0f) || cfg->eps > 64.0f) return LSGG_ERR_INVALID_ARG;
+    if (cfg->init_kind != LSGG_INIT_VORONOI && cfg->init_kind != LSGG_INIT_LAGUERRE) return LSGG_ERR_INVALID_ARG;
+    if (cfg->physics < LSGG_PHYSICS_IDEAL || cfg->physics > LSGG_PHYSICS_MAGNETIC) return LSGG_ERR_INVALID_ARG;
+    if (cfg->storage != LSGG_STORAGE_FP32 && cfg->storage != LSGG_STORAGE_BF16) return LSGG_ERR_INVALID_ARG;
+    if (cfg->storage == LSGG_STORAGE_BF16) return LSGG_ERR_UNSUPPORTED;
+    if (cfg->exec != LSGG_EXEC_BATCHED && cfg->exec != LSGG_EXEC_PLAIN) return LSGG_ERR_INVALID_ARG;
+    if (cfg->physics == LSGG_PHYSICS_READ_SHOCKLEY) return LSGG_ERR_UNSUPPORTED;
+    if (!(cfg->arena_slack >= 1.0)) return LSGG_ERR_INVALID_ARG;
+    // taxicab reach is fixed to the default band: eps = 7 gives 6 exact steps
+    if (std::fabs(cfg->eps - 7.0f) > 1e-6f) return LSGG_ERR_UNSUPPORTED;
+    return LSGG_OK;
+}
+
+static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) {
+    int r = validate(cfg_in);
+    if (r != LSGG_OK) return r;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) { cudaGetLastError(); return LSGG_ERR_CUDA; }
+    if (cfg_in->device < 0 || cfg_in->device >= ndev) return LSGG_ERR_INVALID_ARG;
+    lsgg_ctx* c = new (std::nothrow) lsgg_ctx();
+    if (!c) return LSGG_ERR_OUT_OF_MEMORY;
+    c->cfg = *cfg_in;
+    c->cfg.seeds = c->cfg.weights = c->cfg.quats = c->cfg.energy = nullptr;
+    c->device = cfg_in->device;
+    auto bail = [&](int code) { lsgg_destroy(c); return code; };
+    if (cudaSetDevice(c->device) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+    if (stream) c->stream = (cudaStream_t)stream;
+    else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+        c->own_stream = true;
+    }
+    if (cudaMallocHost(&c->h_st, sizeof(StepState)) != cudaSuccess) return bail(LSGG_ERR_OUT_OF_MEMORY);
+    std::memset(c->h_st, 0, sizeof(StepState));
+    const int G = cfg_in->n_grains;
+    c->G = G;
+    Domain& D = c->dom;
+    D.nx = cfg_in->nx; D.ny = cfg_in->ny; D.nz = cfg_in->nz;
+    D.dim = cfg_in->nz == 1 ? 2 : 3;
+    D.eps = cfg_in->eps;
+    D.halo = cfg_in->halo;
+    D.radius = cfg_in->radius;
+
+    // ---- seeds / weights / energies (host marshalling of given or generated inputs) ----
+    std::vector<double> seeds(3 * (size_t)G), weights, energy;
+    if (cfg_in->seeds) std::memcpy(seeds.data(), cfg_in->seeds, seeds.size() * 8);
+    else lsgg_generate_seeds(cfg_in->seed, G, D.nx, D.ny, D.nz, seeds.data());
+    if (cfg_in->init_kind == LSGG_INIT_LAGUERRE) {
+        weights.resize(G);
+        if (cfg_in->weights) std::memcpy(weights.data(), cfg_in->weights, (size_t)G * 8);
+        else {
+            // lognormal radii with enlarged grains, weight = radius^2 (same recipe as the inputs module)
+            std::vector<double> rad(G);
+            double mean = 0.0;
+            for (int i = 0; i < G; ++i) {
+                double a = u01(cfg_in->seed, 1, 2 * (uint64_t)i), b = u01(cfg_in->seed, 1, 2 * (uint64_t)i + 1);
+                double z = std::sqrt(-2.0 * std::log1p(-a)) * std::cos(2.0 * M_PI * b);
+                double rr = std::exp(cfg_in->lognormal_sigma * z);
+                if (u01(cfg_in->seed, 2, (uint64_t)i) < cfg_in->big_fraction) rr *= std::pow(cfg_in->big_volume, 1.0 / D.dim);
+                rad[i] = rr;
+                mean += rr;
+            }
+            mean /= G;
+            double spacing = std::pow((double)D.nx * D.ny * D.nz / G, 1.0 / D.dim);
+            for (int i = 0; i < G; ++i) { double rr = rad[i] * 0.5 * spacing / mean; weights[i] = rr * rr; }
+        }
+    }
+    if (cfg_in->physics == LSGG_PHYSICS_MAGNETIC) {
+        energy.resize(G);
+        if (cfg_in->energy) std::memcpy(energy.data(), cfg_in->energy, (size_t)G * 8);
+        else {
+            double f[3] = {cfg_in->field_dir[0], cfg_in->field_dir[1], cfg_in->field_dir[2]};
+            double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+            if (!(fn > 0)) return bail(LSGG_ERR_INVALID_ARG);
+            for (int i = 0; i < G; ++i) {
+                double q[4];
+                if (cfg_in->quats) std::memcpy(q, cfg_in->quats + 4 * (size_t)i, 32);
+                else {
+                    double a = u01(cfg_in->seed, 3, 3 * (uint64_t)i), b = u01(cfg_in->seed, 3, 3 * (uint64_t)i + 1),
+                           cc = u01(cfg_in->seed, 3, 3 * (uint64_t)i + 2);
+                    double s1 = std::sqrt(1 - a), s2 = std::sqrt(a);
+                    q[0] = s2 * std::cos(2 * M_PI * cc); q[1] = s1 * std::sin(2 * M_PI * b);
+                    q[2] = s1 * std::cos(2 * M_PI * b); q[3] = s2 * std::sin(2 * M_PI * cc);
+                }
+                double ax = 2 * (q[1] * q[3] + q[0] * q[2]), ay = 2 * (q[2] * q[3] - q[0] * q[1]),
+                       az = 1 - 2 * (q[1] * q[1] + q[2] * q[2]);
+                double cs = (ax * f[0] + ay * f[1] + az * f[2]) / fn;
+                energy[i] = cfg_in->energy_scale * cs * cs;
+            }
+        }
+    }
+
+    // ---- device allocations for initialisation ----
+    const long long ncell = (long long)D.nx * D.ny * D.nz;
+    const long long wpr = (G + 31) / 32;
+    int* d_labels = nullptr;
+    unsigned* d_bits = nullptr;
+    int* d_bb = nullptr;
+    if ((r = dalloc(c, &c->d_seeds, seeds.size())) != LSGG_OK) return bail(r);
+    if (!weights.empty() && (r = dalloc(c, &c->d_weights, weights.size())) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->d_boxes, 2 * (size_t)G)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->B.bounds, (size_t)G)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->B.st, 1)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->B.worklist, (size_t)kNumClasses * G)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->d_vol, (size_t)G)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->d_packed_off, (size_t)G + 1)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->B.T, 2 * (size_t)ncell)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &d_labels, (size_t)ncell)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &d_bits, (size_t)G * wpr)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &d_bb, 6 * (size_t)G)) != LSGG_OK) return bail(r);
+    if (!energy.empty()) {
+        std::vector<float> ef(energy.begin(), energy.end());
+        if ((r = dalloc(c, &c->d_energy, (size_t)G)) != LSGG_OK) return bail(r);
+        if (cudaMemcpy(c->d_energy, ef.data(), ef.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+    }
+    if (cudaMemcpy(c->d_seeds, seeds.data(), seeds.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+    if (!weights.empty() && cudaMemcpy(c->d_weights, weights.data(), weights.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(LSGG_ERR_CUDA);
+    if (cudaMemsetAsync(c->B.st, 0, sizeof(StepState), c->stream) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+
+    c->B.dom = D;
+    c->B.n_boxes = G;
+    c->B.prev = c->d_boxes;
+    c->B.cur = c->d_boxes + G;
+    if (configure_step_kernels(c->B) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+
+    if (launch_init(D, G, c->d_seeds, c->d_weights, d_labels, d_bits, wpr, d_bb, c->B.cur, c->stream) != cudaSuccess)
+        return bail(LSGG_ERR_CUDA);
+    // size the arena from the initial boxes
+    std::vector<Box> hb(G);
+    if (cudaMemcpyAsync(hb.data(), c->B.cur, (size_t)G * sizeof(Box), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return bail(LSGG_ERR_CUDA);
+    long long need = 0;
+    for (const Box& b : hb) need += host_box_elems(b);
+    long long cap = (long long)(need * cfg_in->arena_slack) + (1 << 16);
+    cap = (cap + 31) & ~31LL;
+    c->B.cap = cap;
+    if ((r = dalloc(c, &c->B.X, (size_t)cap)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->B.Y, (size_t)cap)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->B.IDF, (size_t)cap)) != LSGG_OK) return bail(r);
+    c->B.scratch_per_cta = large_class_scratch_floats(D);
+    if ((r = dalloc(c, &c->B.scratch, (size_t)c->B.scratch_per_cta * c->B.grid[0][kNumClasses - 1])) != LSGG_OK)
+        return bail(r);
+    if ((r = relayout(c)) != LSGG_OK) return bail(r);
+    if (launch_sdf(D, G, c->B.cur, c->d_seeds, c->d_weights, d_bits, wpr, c->B.X,
+                   c->B.IDF, &c->B.st->status, c->stream) != cudaSuccess)
+        return bail(LSGG_ERR_CUDA);
+    if (cudaMemcpyAsync(c->B.prev, c->B.cur, (size_t)G * sizeof(Box), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return bail(LSGG_ERR_CUDA);
+    if ((r = read_state(c)) != LSGG_OK) return bail(r);
+    if (c->h_st->status != 0) return bail(c->h_st->status);
+    dfree(c, d_labels);
+    dfree(c, d_bits);
+    dfree(c, d_bb);
+    c->device_bytes -= (long long)ncell * 4 + (long long)G * wpr * 4 + 6LL * G * 4;
+    c->phys.kind = cfg_in->physics;
+    c->phys.energy = c->d_energy;
+    *out = c;
+    return LSGG_OK;
+}
+
+int lsgg_step(lsgg_ctx* c, int32_t n, double dt) {
+    if (!c || n < 0 || !(dt > 0.0) || dt > 4.0) return LSGG_ERR_INVALID_ARG;
+    if (n == 0) return LSGG_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LSGG_ERR_CUDA;
+    c->steps_target += n;
+    c->last_dt = dt;
+    return enqueue_steps(c, n, dt, nullptr);
+}
+
+int lsgg_sync(lsgg_ctx* c, int64_t timeout_ms) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LSGG_ERR_CUDA;
+    for (int round = 0; round < 64; ++round) {
+        auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            cudaError_t q = cudaStreamQuery(c->stream);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) return LSGG_ERR_CUDA;
+            if (timeout_ms >= 0) {
+                auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+                if (ms > timeout_ms) return LSGG_ERR_TIMEOUT;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        int r = read_state(c);
+        if (r != LSGG_OK) return r;
+        if (c->h_st->status == 0) return LSGG_OK;
+        if (c->h_st->status != LSGG_ERR_CAPACITY) return c->h_st->status;
+        // arena overflow: grow, lay out the pending boxes, finish the remaining steps
+        r = grow_arena(c, c->h_st->box_cells);
+        if (r != LSGG_OK) return r;
+        r = relayout(c);
+        if (r != LSGG_OK) return r;
+        long long remaining = c->steps_target - c->h_st->steps_done;
+        if (remaining > 0) {
+            r = enqueue_steps(c, remaining, c->last_dt, nullptr);
+            if (r != LSGG_OK) return r;
+        }
+    }
+    return LSGG_ERR_OUT_OF_MEMORY;
+}
+
+int lsgg_get_stats(lsgg_ctx* c, lsgg_stats* out) {
+    if (!c || !out) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    std::memset(out, 0, sizeof(*out));
+    out->steps_done = c->h_st->steps_done;
+    out->alive = c->h_st->alive;
+    out->box_cells = c->h_st->box_cells;
+    out->arena_capacity = c->B.cap;
+    out->superimposition = (double)c->h_st->box_cells / ((double)c->dom.nx * c->dom.ny * c->dom.nz);
+    out->device_bytes = c->device_bytes;
+    out->n_classes = kNumClasses;
+    for (int k = 0; k < kNumClasses; ++k) out->class_count[k] = c->h_st->class_count[k];
+    return LSGG_OK;
+}
+
+int lsgg_get_boxes(lsgg_ctx* c, int32_t* out, int64_t cap) {
+    if (!c || !out || cap < 7LL * c->G) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    std::vector<Box> hb(c->G);
+    CK(cudaMemcpy(hb.data(), c->B.cur, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < c->G; ++i) {
+        const Box& b = hb[i];
+        int32_t* o = out + 7 * (size_t)i;
+        o[0] = b.nx > 0;
+        o[1] = b.ox; o[2] = b.oy; o[3] = b.oz;
+        o[4] = b.nx; o[5] = b.ny; o[6] = b.nz;
+    }
+    return LSGG_OK;
+}
+
+static int packed_offsets(lsgg_ctx* c, const Box* table, std::vector<long long>& off) {
+    std::vector<Box> hb(c->G);
+    CK(cudaMemcpy(hb.data(), table, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToHost));
+    off.assign(c->G + 1, 0);
+    for (int i = 0; i < c->G; ++i)
+        off[i + 1] = off[i] + (hb[i].nx > 0 ? (long long)hb[i].nx * hb[i].ny * hb[i].nz : 0);
+    CK(cudaMemcpy(c->d_packed_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+    return LSGG_OK;
+}
+
+int lsgg_get_phi(lsgg_ctx* c, float* out, int64_t cap, int64_t* n_out) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    std::vector<long long> off;
+    if ((r = packed_offsets(c, c->B.cur, off)) != LSGG_OK) return r;
+    if (n_out) *n_out = off[c->G];
+    if (!out || cap < off[c->G]) return LSGG_ERR_CAPACITY;
+    float* d = nullptr;
+    if ((r = dalloc(c, &d, (size_t)off[c->G])) != LSGG_OK) return r;
+    cudaError_t e = launch_pack_state(c->dom, c->G, c->B.cur, c->B.prev, c->B.X, c->d_packed_off, d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)off[c->G] * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->device_bytes -= off[c->G] * 4;
+    dfree(c, d);
+    return e == cudaSuccess ? LSGG_OK : LSGG_ERR_CUDA;
+}
+
+int lsgg_set_state(lsgg_ctx* c, const int32_t* boxes, const float* phi, const int32_t* idf) {
+    if (!c || !boxes || !phi) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    const Domain& D = c->dom;
+    std::vector<Box> hb(c->G);
+    std::vector<long long> off(c->G + 1, 0);
+    long long need = 0;
+    for (int i = 0; i < c->G; ++i) {
+        const int32_t* b = boxes + 7 * (size_t)i;
+        Box x{};
+        if (b[0]) {
+            if (b[4] < 1 || b[5] < 1 || b[6] < 1 || b[4] > D.nx || b[5] > D.ny || b[6] > D.nz) return LSGG_ERR_INVALID_ARG;
+            if (b[1] < 0 || b[2] < 0 || b[3] < 0 || b[1] >= D.nx || b[2] >= D.ny || b[3] >= D.nz) return LSGG_ERR_INVALID_ARG;
+            x.ox = b[1]; x.oy = b[2]; x.oz = b[3];
+            x.nx = b[4]; x.ny = b[5]; x.nz = b[6];
+        }
+        hb[i] = x;
+        off[i + 1] = off[i] + (x.nx > 0 ? (long long)x.nx * x.ny * x.nz : 0);
+        need += host_box_elems(x);
+    }
+    if (need > c->B.cap && (r = grow_arena(c, need)) != LSGG_OK) return r;
+    CK(cudaMemcpy(c->B.cur, hb.data(), (size_t)c->G * sizeof(Box), cudaMemcpyHostToDevice));
+    if ((r = relayout(c)) != LSGG_OK) return r;
+    float* dphi = nullptr;
+    int* didf = nullptr;
+    if ((r = dalloc(c, &dphi, (size_t)off[c->G])) != LSGG_OK) return r;
+    if (idf && (r = dalloc(c, &didf, (size_t)off[c->G])) != LSGG_OK) return r;
+    CK(cudaMemcpy(c->d_packed_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dphi, phi, (size_t)off[c->G] * 4, cudaMemcpyHostToDevice));
+    if (idf) CK(cudaMemcpy(didf, idf, (size_t)off[c->G] * 4, cudaMemcpyHostToDevice));
+    CK(launch_unpack_state(c->G, c->B.cur, dphi, didf, c->d_packed_off, c->B.X, c->B.IDF, c->stream));
+    CK(cudaMemcpyAsync(c->B.prev, c->B.cur, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->device_bytes -= off[c->G] * 4 * (idf ? 2 : 1);
+    dfree(c, dphi);
+    dfree(c, didf);
+    return LSGG_OK;
+}
+
+int lsgg_debug_step(lsgg_ctx* c, double dt, float* phip, float* m, int32_t* idm, float* phic, float* phin) {
+    if (!c || !(dt > 0.0) || dt > 4.0) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    DebugOut dbg{};
+    float* base = nullptr;
+    if ((r = dalloc(c, &base, (size_t)c->B.cap * 5)) != LSGG_OK) return r;
+    dbg.phip = base;
+    dbg.m = base + c->B.cap;
+    dbg.idm = reinterpret_cast<int*>(base + 2 * c->B.cap);
+    dbg.phic = base + 3 * c->B.cap;
+    dbg.phin = base + 4 * c->B.cap;
+    c->steps_target += 1;
+    c->last_dt = dt;
+    r = enqueue_steps(c, 1, dt, &dbg);
+    if (r == LSGG_OK) r = lsgg_sync(c, -1);
+    if (r == LSGG_OK) {
+        std::vector<long long> off;
+        r = packed_offsets(c, c->B.prev, off);
+        float* tmp = nullptr;
+        if (r == LSGG_OK) r = dalloc(c, &tmp, (size_t)off[c->G] + 1);
+        void* dst[5] = {phip, m, idm, phic, phin};
+        void* src[5] = {dbg.phip, dbg.m, dbg.idm, dbg.phic, dbg.phin};
+        for (int k = 0; k < 5 && r == LSGG_OK; ++k) {
+            if (!dst[k]) continue;
+            if (launch_pack_cur(c->G, c->B.prev, src[k], c->d_packed_off, tmp, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(dst[k], tmp, (size_t)off[c->G] * 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                r = LSGG_ERR_CUDA;
+        }
+        if (tmp) { c->device_bytes -= (off[c->G] + 1) * 4; dfree(c, tmp); }
+    }
+    c->device_bytes -= c->B.cap * 5 * 4;
+    dfree(c, base);
+    return r;
+}
+
+int lsgg_grain_volumes(lsgg_ctx* c, double* out, int64_t cap, int64_t* n_out) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    if (n_out) *n_out = c->G;
+    if (!out || cap < c->G) return LSGG_ERR_CAPACITY;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, c->B.X, c->d_vol, c->stream));
+    CK(cudaMemcpyAsync(out, c->d_vol, (size_t)c->G * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LSGG_OK;
+}
+
+int lsgg_voxel_owner(lsgg_ctx* c, int32_t* out, int64_t n_cells) {
+    if (!c || !out) return LSGG_ERR_INVALID_ARG;
+    long long n = (long long)c->dom.nx * c->dom.ny * c->dom.nz;
+    if (n_cells < n) return LSGG_ERR_CAPACITY;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    int* d = nullptr;
+    if ((r = dalloc(c, &d, (size_t)n)) != LSGG_OK) return r;
+    cudaError_t e = launch_owner(c->dom, c->G, c->B.cur, c->B.prev, c->B.X, c->B.T, d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->device_bytes -= n * 4;
+    dfree(c, d);
+    return e == cudaSuccess ? LSGG_OK : LSGG_ERR_CUDA;
+}
+
+}  // extern "C"
+
+namespace {
+
+int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg) {
+    Taps taps = make_taps(dt, c->dom.radius);
+    c->phys.dt = (float)dt;
+    if (c->cfg.exec == LSGG_EXEC_PLAIN && !dbg) {
+        return LSGG_ERR_UNSUPPORTED;
+    }
+    for (long long i = 0; i < n; ++i) {
+        if (launch_step(c->B, taps, c->phys, dbg, c->stream) != cudaSuccess) return LSGG_ERR_CUDA;
+    }
+    return LSGG_OK;
+}
+
+}  // namespace

@@ -1,0 +1,139 @@
+// Internal declarations of the sm_103a level-set grain-growth library.
+//
+// Data layout in HBM (one context):
+//   boxes      Box[G] x 2 tables: `prev` = layout of the state arena X,
+//              `cur` = layout the next step writes (bbox of {phi > 0} + halo).
+//   X, Y       FP32 (or BF16) box arenas, `cap` elements each.  Box b's plane z
+//              starts at off + z * ps with ps = round_up(nx * ny, 4) so that a
+//              plane is one 16-byte aligned bulk copy; off is a multiple of 32.
+//   T          neighbour-max field, 2 x u64 per domain cell: key1 = the largest
+//              (phi_p, -id) over the boxes covering the cell, key2 = the second.
+//   IDF        int32 ID-field arena (same layout as X) for the physics blend.
+//   classes    per size class a work list of box indices and a queue counter
+//              per kernel; persistent CTAs pull boxes from the queue.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsgg {
+
+constexpr int kMaxRadius = 7;
+constexpr int kMaxTaps = 2 * kMaxRadius + 1;
+constexpr int kNumClasses = 4;          // box side <= 32, 48, ~64, larger (global scratch)
+constexpr int kRedistReach = 6;         // taxicab steps below eps = 7 (exact fixed point)
+
+struct Box {
+    int ox, oy, oz;       // origin, each in [0, N)
+    int nx, ny, nz;       // dims; nx == 0 marks an extinct grain
+    long long off;        // arena offset (elements) of plane 0
+};
+
+struct Domain {
+    int nx, ny, nz;
+    int dim;              // 2 or 3
+    float eps;
+    int halo;
+    int radius;
+};
+
+struct Taps {
+    float g[kMaxTaps];
+    int radius;
+};
+
+struct Bounds {           // positive-cell bbox in box-local coordinates
+    int lo[3];
+    int hi[3];
+};
+
+// Physics of Eq. (10) for the blend phi_p = phi + w (c - phi) + M (e_j - e_i) dt.
+struct PairEntry {        // neighbour j of grain i: weight w_ij and mobility M_ij
+    int j;
+    float w;
+    float m;
+};
+
+struct PhysicsDev {
+    int kind;                       // LSGG_PHYSICS_*
+    const float* energy;            // per grain, grid units
+    const int* nb_start;            // CSR over grains: pair entries sorted by j
+    const PairEntry* nb;            // pair table
+    float dt;
+};
+
+struct DebugOut {                   // optional per-cell intermediates (cur layout, FP32)
+    float* phip;
+    float* m;
+    int* idm;
+    float* phic;
+    float* phin;
+};
+
+struct StepState {                  // device-resident control block
+    int status;                     // 0 or an LSGG_ERR_* code
+    int halt;                       // 1: remaining launches of this step return at once
+    long long steps_done;
+    long long box_cells;            // sum of box volumes in `cur`
+    long long alive;
+    int class_count[kNumClasses];
+    int queue[2][kNumClasses];      // pull counters of the predictor / corrector kernels
+};
+
+__host__ __device__ inline int plane_stride(int nx, int ny) { return (nx * ny + 3) & ~3; }
+__host__ __device__ inline long long box_elems(const Box& b) {
+    if (b.nx <= 0) return 0;
+    long long s = (long long)plane_stride(b.nx, b.ny) * b.nz;
+    return (s + 31) & ~31LL;
+}
+__host__ __device__ inline int pmod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+// ---- order-preserving keys for the neighbour-max field ----
+__device__ __forceinline__ unsigned int ord_float(float v) {
+    unsigned int u = __float_as_uint(v + 0.0f);          // -0 -> +0
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord_float(unsigned int o) {
+    unsigned int u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    return __uint_as_float(u);
+}
+__device__ __forceinline__ unsigned long long make_key(float v, int gid) {
+    return ((unsigned long long)ord_float(v) << 32) | (unsigned long long)(0xffffffffu - (unsigned)gid);
+}
+__device__ __forceinline__ int key_id(unsigned long long k) {
+    return k ? (int)(0xffffffffu - (unsigned)(k & 0xffffffffu)) : -1;
+}
+__device__ __forceinline__ float key_val(unsigned long long k, float eps) {
+    return k ? unord_float((unsigned)(k >> 32)) : -eps;
+}
+
+// ---- launch helpers (implemented in step.cu / init.cu / outputs.cu) ----
+struct StepBuffers {
+    Domain dom;
+    int n_boxes;
+    Box* prev;
+    Box* cur;
+    Bounds* bounds;
+    float* X;
+    float* Y;
+    int* IDF;
+    unsigned long long* T;
+    int* worklist;                  // kNumClasses x n_boxes
+    StepState* st;
+    long long cap;
+    float* scratch;                 // global ring buffers of the large class
+    long long scratch_per_cta;
+    int n_sm;
+    int class_side[kNumClasses];    // largest box side per class (last: whole domain)
+    int grid[2][kNumClasses];       // persistent grid per kernel and class
+    size_t smem[2][kNumClasses];
+};
+
+cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
+                        const DebugOut* dbg, cudaStream_t s);
+cudaError_t launch_box_update(const StepBuffers& B, bool commit_only_layout, cudaStream_t s);
+cudaError_t configure_step_kernels(StepBuffers& B);
+cudaError_t launch_plain_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
+                              const int* h_alive_boxes, int n_alive, cudaStream_t s);
+
+}  // namespace lsgg

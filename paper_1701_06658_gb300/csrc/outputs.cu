@@ -1,0 +1,185 @@
+// Outputs of a microstructure.
+//
+//   k_volumes   V_i = sum_x H(phi_i(x)), H(phi) = clamp(phi + 1/2, 0, 1): one CTA
+//               per box, FP64 Neumaier-compensated partial sums per thread in a
+//               fixed cell order, then a fixed-order tree of TwoSum merges, so
+//               the result is the same on every run.
+//   k_owner_*   owner(x) = argmax_i phi_i(x) over boxes covering x, lowest id on
+//               ties (64-bit atomicMax of (phi, -id) keys), -1 where uncovered.
+//   k_remap     the state phi (stored in the `prev` layout) resampled on the
+//               current boxes with -eps where the old box did not reach: the
+//               grain functions as they enter the next step (Sec. 3.1 box update).
+#include "lsgg_internal.cuh"
+
+namespace lsgg {
+
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+    s = __dadd_rn(a, b);
+    double bb = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// Value of grain b's function at a cell of its current box (local x, y, z):
+// read from the prev layout, -eps outside the prev box.
+__device__ __forceinline__ float state_value(const Domain& D, const Box& nb, const Box& ob, const float* X,
+                                             int x, int y, int z) {
+    int lx = pmod(nb.ox + x - ob.ox, D.nx);
+    int ly = pmod(nb.oy + y - ob.oy, D.ny);
+    int lz = pmod(nb.oz + z - ob.oz, D.nz);
+    if (lx >= ob.nx || ly >= ob.ny || lz >= ob.nz) return -D.eps;
+    return X[ob.off + (long long)lz * plane_stride(ob.nx, ob.ny) + ly * ob.nx + lx];
+}
+
+__global__ void __launch_bounds__(256)
+k_volumes(Domain D, const Box* __restrict__ cur, const Box* __restrict__ prev, const float* __restrict__ X,
+          double* __restrict__ out) {
+    __shared__ double s_s[256], s_c[256];
+    const int b = blockIdx.x;
+    const Box nb = cur[b];
+    double s = 0.0, c = 0.0;
+    if (nb.nx > 0) {
+        const Box ob = prev[b];
+        const long long A = (long long)nb.nx * nb.ny;
+        const long long n = A * nb.nz;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+            int z = (int)(i / A);
+            int rem = (int)(i - z * A);
+            int y = rem / nb.nx, x = rem - y * nb.nx;
+            float v = state_value(D, nb, ob, X, x, y, z);
+            double h = fmin(fmax((double)v + 0.5, 0.0), 1.0);
+            double t, e;
+            two_sum(s, h, t, e);
+            s = t;
+            c = __dadd_rn(c, e);
+        }
+    }
+    s_s[threadIdx.x] = s;
+    s_c[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o) {
+            double t, e;
+            two_sum(s_s[threadIdx.x], s_s[threadIdx.x + o], t, e);
+            s_s[threadIdx.x] = t;
+            s_c[threadIdx.x] = __dadd_rn(__dadd_rn(s_c[threadIdx.x], s_c[threadIdx.x + o]), e);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[b] = nb.nx > 0 ? __dadd_rn(s_s[0], s_c[0]) : 0.0;
+}
+
+__global__ void __launch_bounds__(256)
+k_owner_scatter(Domain D, const Box* __restrict__ cur, const Box* __restrict__ prev, const float* __restrict__ X,
+                unsigned long long* __restrict__ F) {
+    const int b = blockIdx.x;
+    const Box nb = cur[b];
+    if (nb.nx <= 0) return;
+    const Box ob = prev[b];
+    const long long A = (long long)nb.nx * nb.ny;
+    const long long n = A * nb.nz;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        int z = (int)(i / A);
+        int rem = (int)(i - z * A);
+        int y = rem / nb.nx, x = rem - y * nb.nx;
+        float v = state_value(D, nb, ob, X, x, y, z);
+        long long g = ((long long)pmod(nb.oz + z, D.nz) * D.ny + pmod(nb.oy + y, D.ny)) * D.nx + pmod(nb.ox + x, D.nx);
+        atomicMax(&F[g], make_key(v, b));
+    }
+}
+
+__global__ void k_owner_decode(long long n, const unsigned long long* __restrict__ F, int* __restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = key_id(F[i]);
+}
+
+// Packed copy of the state on the current boxes (grain-id order, x fastest, no padding).
+__global__ void __launch_bounds__(256)
+k_pack_state(Domain D, const Box* __restrict__ cur, const Box* __restrict__ prev, const float* __restrict__ X,
+             const long long* __restrict__ packed_off, float* __restrict__ out) {
+    const int b = blockIdx.x;
+    const Box nb = cur[b];
+    if (nb.nx <= 0) return;
+    const Box ob = prev[b];
+    const long long A = (long long)nb.nx * nb.ny;
+    const long long n = A * nb.nz;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        int z = (int)(i / A);
+        int rem = (int)(i - z * A);
+        int y = rem / nb.nx, x = rem - y * nb.nx;
+        out[packed_off[b] + i] = state_value(D, nb, ob, X, x, y, z);
+    }
+}
+
+// Packed copy of a cur-layout arena (debug intermediates); `ints` selects int32 data.
+__global__ void __launch_bounds__(256)
+k_pack_cur(const Box* __restrict__ cur, const void* __restrict__ arena, const long long* __restrict__ packed_off,
+           void* __restrict__ out) {
+    const int b = blockIdx.x;
+    const Box nb = cur[b];
+    if (nb.nx <= 0) return;
+    const long long A = (long long)nb.nx * nb.ny;
+    const long long n = A * nb.nz;
+    const int ps = plane_stride(nb.nx, nb.ny);
+    const unsigned* src = reinterpret_cast<const unsigned*>(arena);
+    unsigned* dst = reinterpret_cast<unsigned*>(out);
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        long long z = i / A, rem = i - z * A;
+        dst[packed_off[b] + i] = src[nb.off + z * ps + rem];
+    }
+}
+
+// Unpack host-given state into the arena (cur layout) and set prev = cur.
+__global__ void __launch_bounds__(256)
+k_unpack_state(const Box* __restrict__ cur, const float* __restrict__ packed, const int* __restrict__ packed_idf,
+               const long long* __restrict__ packed_off, float* __restrict__ X, int* __restrict__ IDF) {
+    const int b = blockIdx.x;
+    const Box nb = cur[b];
+    if (nb.nx <= 0) return;
+    const long long A = (long long)nb.nx * nb.ny;
+    const long long n = A * nb.nz;
+    const int ps = plane_stride(nb.nx, nb.ny);
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        long long z = i / A, rem = i - z * A;
+        long long o = nb.off + z * ps + rem;
+        X[o] = packed[packed_off[b] + i];
+        if (IDF) IDF[o] = packed_idf ? packed_idf[packed_off[b] + i] : -1;
+    }
+}
+
+cudaError_t launch_volumes(const Domain& D, int G, const Box* cur, const Box* prev, const float* X, double* out,
+                           cudaStream_t s) {
+    k_volumes<<<G, 256, 0, s>>>(D, cur, prev, X, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_owner(const Domain& D, int G, const Box* cur, const Box* prev, const float* X,
+                         unsigned long long* F, int* out, cudaStream_t s) {
+    long long n = (long long)D.nx * D.ny * D.nz;
+    cudaError_t e = cudaMemsetAsync(F, 0, (size_t)n * 8, s);
+    if (e != cudaSuccess) return e;
+    k_owner_scatter<<<G, 256, 0, s>>>(D, cur, prev, X, F);
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 65535 * 16) blocks = 65535 * 16;
+    k_owner_decode<<<blocks, 256, 0, s>>>(n, F, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_state(const Domain& D, int G, const Box* cur, const Box* prev, const float* X,
+                              const long long* packed_off, float* out, cudaStream_t s) {
+    k_pack_state<<<G, 256, 0, s>>>(D, cur, prev, X, packed_off, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_cur(int G, const Box* cur, const void* arena, const long long* packed_off, void* out,
+                            cudaStream_t s) {
+    k_pack_cur<<<G, 256, 0, s>>>(cur, arena, packed_off, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_state(int G, const Box* cur, const float* packed, const int* packed_idf,
+                                const long long* packed_off, float* X, int* IDF, cudaStream_t s) {
+    k_unpack_state<<<G, 256, 0, s>>>(cur, packed, packed_idf, packed_off, X, IDF);
+    return cudaGetLastError();
+}
+
+}  // namespace lsgg

@@ -1,0 +1,689 @@
+// One time step of Algorithm 1 on the packed box list (batched path).
+//
+//   k_predict   Sec. 2.1.4, Eqs. (7)-(10): phi_p = G(dt) * phi (separable,
+//               x -> y in shared memory per plane, z over a ring of 2R+1
+//               planes while streaming the box along z), optional velocity
+//               correction, clamp to [-eps, eps]; the result is written in
+//               the box's new layout and scattered into the neighbour-max
+//               field T (two 64-bit atomicMax per cell: top-1 and top-2).
+//   k_correct   Sec. 2.1.5, Eq. (16) and Sec. 2.1.6: phi_c = (phi_p - m) / 2
+//               with m = max_{j != i} phi_p_j read from T; reference cells and
+//               their planar-exact distances; taxicab distance as a
+//               sign-blocked min-plus transform, x and y in the plane, z as a
+//               forward sweep plus a 6-plane backward window; clamp; positive
+//               bounding box of the box.
+//   k_box_update  Secs. 2.1.3 / 3.1: new box = bbox{phi > 0} + halo, arena
+//               offsets by a block-wide scan, size classes and work queues.
+//
+// One CTA owns one box at a time and streams it plane by plane; CTAs of a
+// size class pull boxes from a device queue (persistent grid).  Outside its
+// box a grain's function is -eps (Fig. 1 caption); a box axis that spans the
+// domain is periodic.
+#include <cfloat>
+#include <climits>
+
+#include "lsgg_internal.cuh"
+#include "../../include/lsgg.h"
+
+namespace lsgg {
+
+constexpr int kThreads = 256;
+constexpr int kBoxUpdateThreads = 1024;
+
+__device__ __forceinline__ bool sgn_pos(float v) { return !(__float_as_uint(v) >> 31); }
+
+// Pull the next box of class `cls` for kernel `which`; -1 when the queue is empty.
+__device__ __forceinline__ int pull_box(const StepBuffers& B, int which, int cls, int* s_box) {
+    if (threadIdx.x == 0) {
+        int b = -1;
+        if (!*(volatile int*)&B.st->halt) {
+            int w = atomicAdd(&B.st->queue[which][cls], 1);
+            if (w < B.st->class_count[cls]) b = B.worklist[cls * B.n_boxes + w];
+        }
+        *s_box = b;
+    }
+    __syncthreads();
+    int b = *s_box;
+    __syncthreads();
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// predictor + neighbour-max scatter
+// ---------------------------------------------------------------------------
+
+struct PredictSmem {   // carved from dynamic shared memory (maps) + a float buffer
+    int* mapx;         // [nx + 2R] old-box local x (or -1) for padded new-box x
+    int* mapy;         // [ny + 2R]
+    int* gx;           // [nx] global x of new-box cells
+    int* gy;           // [ny]
+};
+
+__device__ float pair_blend(const PhysicsDev& phys, int gid, int j, float phi, float c) {
+    // Eq. (10): phi + w (c - phi) + M (e_j - e_i) dt; w = 1, no bulk when j < 0.
+    if (j < 0) return c;
+    float w = 1.0f, m = 1.0f;
+    if (phys.kind == LSGG_PHYSICS_READ_SHOCKLEY) {
+        int lo = phys.nb_start[gid], hi = phys.nb_start[gid + 1] - 1;
+        while (lo <= hi) {
+            int mid = (lo + hi) >> 1;
+            int jj = phys.nb[mid].j;
+            if (jj == j) { w = phys.nb[mid].w; m = phys.nb[mid].m; break; }
+            if (jj < j) lo = mid + 1; else hi = mid - 1;
+        }
+    }
+    float bulk = 0.0f;
+    if (phys.energy) bulk = m * (phys.energy[j] - phys.energy[gid]) * phys.dt;
+    return phi + w * (c - phi) + bulk;
+}
+
+__device__ void predict_box(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
+                            int b, const PredictSmem& sm, float* buf) {
+    const Domain& D = B.dom;
+    const Box nb = B.cur[b];
+    const Box ob = B.prev[b];
+    const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
+    const int R = taps.radius;
+    const int W = 2 * R + 1;
+    const int px = nx + 2 * R, py = ny + 2 * R;
+    const int A = nx * ny;
+    const bool fx = nx == D.nx, fy = ny == D.ny, fz = nz == D.nz;
+    const float eps = D.eps;
+
+    float* P = buf;                       // (ny+2R) x (nx+2R) staged input plane
+    float* Xp = P + (size_t)px * py;      // (ny+2R) x nx after the x pass
+    float* ring = Xp + (size_t)nx * py;   // W planes of nx*ny after the y pass
+
+    for (int i = threadIdx.x; i < px; i += blockDim.x) {
+        int xl = i - R, v = -1;
+        bool ok = fx || (xl >= 0 && xl < nx);
+        if (ok) {
+            if (fx) xl = pmod(xl, nx);
+            int ol = pmod(nb.ox + xl - ob.ox, D.nx);
+            v = ol < ob.nx ? ol : -1;
+        }
+        sm.mapx[i] = v;
+    }
+    for (int i = threadIdx.x; i < py; i += blockDim.x) {
+        int yl = i - R, v = -1;
+        bool ok = fy || (yl >= 0 && yl < ny);
+        if (ok) {
+            if (fy) yl = pmod(yl, ny);
+            int ol = pmod(nb.oy + yl - ob.oy, D.ny);
+            v = ol < ob.ny ? ol : -1;
+        }
+        sm.mapy[i] = v;
+    }
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) sm.gx[i] = pmod(nb.ox + i, D.nx);
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) sm.gy[i] = pmod(nb.oy + i, D.ny);
+    __syncthreads();
+
+    const int ps_old = plane_stride(ob.nx, ob.ny);
+    const int ps_new = plane_stride(nx, ny);
+    const bool is3d = D.dim == 3;
+    const int zlo = is3d ? -R : 0, zhi = is3d ? nz + R : 1;
+
+    for (int zin = zlo; zin < zhi; ++zin) {
+        // ---- stage plane zin (new-box local z), masked by both boxes ----
+        int zold = -1;
+        {
+            bool ok = !is3d || fz || (zin >= 0 && zin < nz);
+            if (ok) {
+                int zl = is3d && fz ? pmod(zin, nz) : zin;
+                int ol = is3d ? pmod(nb.oz + zl - ob.oz, D.nz) : 0;
+                zold = ol < ob.nz ? ol : -1;
+            }
+        }
+        const float* src = B.X + ob.off + (long long)(zold < 0 ? 0 : zold) * ps_old;
+        for (int idx = threadIdx.x; idx < px * py; idx += blockDim.x) {
+            int yp = idx / px, xp = idx - yp * px;
+            int mx = sm.mapx[xp], my = sm.mapy[yp];
+            float v = -eps;
+            if (zold >= 0 && mx >= 0 && my >= 0) v = src[my * ob.nx + mx];
+            P[idx] = v;
+        }
+        __syncthreads();
+        // ---- x pass ----
+        for (int idx = threadIdx.x; idx < nx * py; idx += blockDim.x) {
+            int yp = idx / nx, x = idx - yp * nx;
+            const float* row = P + yp * px + x;
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kMaxTaps; ++k)
+                if (k < W) acc = fmaf(taps.g[k], row[k], acc);
+            Xp[idx] = acc;
+        }
+        __syncthreads();
+        // ---- y pass -> ring slot of plane zin ----
+        float* slot = ring + (size_t)(is3d ? pmod(zin, W) : 0) * A;
+        for (int idx = threadIdx.x; idx < A; idx += blockDim.x) {
+            int y = idx / nx, x = idx - y * nx;
+            const float* col = Xp + y * nx + x;
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kMaxTaps; ++k)
+                if (k < W) acc = fmaf(taps.g[k], col[k * nx], acc);
+            slot[idx] = acc;
+        }
+        __syncthreads();
+        // ---- z pass for output plane zo = zin - R ----
+        const int zo = is3d ? zin - R : 0;
+        if (zo < 0) continue;
+        const int gz = is3d ? pmod(nb.oz + zo, D.nz) : 0;
+        float* dst = B.Y + nb.off + (long long)zo * ps_new;
+        for (int idx = threadIdx.x; idx < A; idx += blockDim.x) {
+            float c;
+            if (is3d) {
+                c = 0.0f;
+#pragma unroll
+                for (int k = 0; k < kMaxTaps; ++k)
+                    if (k < W) c = fmaf(taps.g[k], ring[(size_t)pmod(zo - R + k, W) * A + idx], c);
+            } else {
+                c = slot[idx];
+            }
+            int y = idx / nx, x = idx - y * nx;
+            float v = c;
+            if (phys.kind != LSGG_PHYSICS_IDEAL) {
+                int zl = zo;
+                int zo_old = is3d ? pmod(nb.oz + zl - ob.oz, D.nz) : 0;
+                int mx = sm.mapx[x + R], my = sm.mapy[y + R];
+                float phi0 = -eps;
+                int j = -1;
+                if (zo_old < ob.nz && mx >= 0 && my >= 0) {
+                    long long o = ob.off + (long long)zo_old * ps_old + my * ob.nx + mx;
+                    phi0 = B.X[o];
+                    j = B.IDF[o];
+                }
+                v = pair_blend(phys, b, j, phi0, c);
+            }
+            v = fminf(fmaxf(v, -eps), eps);
+            dst[idx] = v;
+            long long g = ((long long)gz * D.ny + sm.gy[y]) * D.nx + sm.gx[x];
+            unsigned long long key = make_key(v, b);
+            unsigned long long old = atomicMax(&B.T[2 * g], key);
+            if (old) atomicMax(&B.T[2 * g + 1], old < key ? old : key);
+        }
+        // no barrier needed: the next writes into `ring` happen after two barriers
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_predict(StepBuffers B, Taps taps, PhysicsDev phys, int cls) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_box;
+    const int side = B.class_side[cls];
+    PredictSmem sm;
+    sm.mapx = reinterpret_cast<int*>(smem_raw);
+    sm.mapy = sm.mapx + side + 2 * kMaxRadius;
+    sm.gx = sm.mapy + side + 2 * kMaxRadius;
+    sm.gy = sm.gx + side;
+    float* buf = reinterpret_cast<float*>(sm.gy + side + 4);
+    buf = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(buf) + 15) & ~uintptr_t(15));
+    if (cls == kNumClasses - 1) buf = B.scratch + (long long)blockIdx.x * B.scratch_per_cta;
+    for (;;) {
+        int b = pull_box(B, 0, cls, &s_box);
+        if (b < 0) break;
+        predict_box(B, taps, phys, b, sm, buf);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// comparison + re-initialisation
+// ---------------------------------------------------------------------------
+
+// Along one line of n cells (stride `stride` in `in`), the sign-blocked
+// taxicab min-plus over +-kRedistReach of cell `i`: min over cells reachable
+// through same-sign cells of |v| + steps.  `wrap` for a periodic line.
+__device__ __forceinline__ float line_min(const float* in, int i, int n, int stride, bool wrap) {
+    const float v = in[i * stride];
+    const bool s = sgn_pos(v);
+    float best = fabsf(v);
+#pragma unroll
+    for (int k = 1; k <= kRedistReach; ++k) {
+        int j = i - k;
+        if (j < 0) { if (!wrap) break; j += n; }
+        float u = in[j * stride];
+        if (sgn_pos(u) != s) break;
+        best = fminf(best, fabsf(u) + (float)k);
+    }
+#pragma unroll
+    for (int k = 1; k <= kRedistReach; ++k) {
+        int j = i + k;
+        if (j >= n) { if (!wrap) break; j -= n; }
+        float u = in[j * stride];
+        if (sgn_pos(u) != s) break;
+        best = fminf(best, fabsf(u) + (float)k);
+    }
+    return s ? best : -best;
+}
+
+__device__ __forceinline__ void opp_delta(float a, bool pos, float nbv, float& dmin) {
+    if ((nbv > 0.0f) != pos) {
+        float d = a / (a + fabsf(nbv));
+        dmin = fminf(dmin, d);
+    }
+}
+
+__device__ void correct_box(const StepBuffers& B, const PhysicsDev& phys, const DebugOut& dbg,
+                            int b, int* gx, int* gy, float* buf, int* s_red) {
+    const Domain& D = B.dom;
+    const Box nb = B.cur[b];
+    const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
+    const int A = nx * ny;
+    const bool fx = nx == D.nx, fy = ny == D.ny, fz = nz == D.nz;
+    const bool is3d = D.dim == 3;
+    const float eps = D.eps;
+    const int ps = plane_stride(nx, ny);
+
+    float* C = buf;                  // 3 planes of phi_c (z-1, z, z+1)
+    float* G = C + 3 * (size_t)A;    // reference-classified plane
+    float* H = G + A;                // after the x pass
+    float* F = H + A;                // 7 planes: forward z sweep
+
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) gx[i] = pmod(nb.ox + i, D.nx);
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) gy[i] = pmod(nb.oy + i, D.ny);
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+
+    // stream bounds (see the pipeline description in the file header)
+    int z_first, z_last;
+    if (!is3d) { z_first = 0; z_last = 0; }
+    else if (fz) { z_first = -(kRedistReach + 1); z_last = nz + kRedistReach; }
+    else {
+        z_first = 0; z_last = nz + kRedistReach;
+        float* pre = C + (size_t)pmod(-1, 3) * A;       // plane -1: outside, -eps
+        for (int i = threadIdx.x; i < A; i += blockDim.x) pre[i] = -eps;
+    }
+    __syncthreads();
+
+    for (int zin = z_first; zin <= z_last; ++zin) {
+        // ---- A: phi_c of plane zin ----
+        {
+            float* Cz = C + (size_t)pmod(zin, 3) * A;
+            bool inside = !is3d || fz || (zin >= 0 && zin < nz);
+            bool want = is3d ? (fz ? true : zin <= nz) : true;
+            if (want) {
+                if (!inside) {
+                    for (int i = threadIdx.x; i < A; i += blockDim.x) Cz[i] = -eps;
+                } else {
+                    int zl = is3d && fz ? pmod(zin, nz) : zin;
+                    int gz = is3d ? pmod(nb.oz + zl, D.nz) : 0;
+                    const float* src = B.Y + nb.off + (long long)zl * ps;
+                    bool record = zin >= 0 && zin < nz;
+                    for (int i = threadIdx.x; i < A; i += blockDim.x) {
+                        int y = i / nx, x = i - y * nx;
+                        float pp = src[i];
+                        long long g = ((long long)gz * D.ny + gy[y]) * D.nx + gx[x];
+                        unsigned long long k1 = B.T[2 * g], k2 = B.T[2 * g + 1];
+                        int id1 = key_id(k1);
+                        float m;
+                        int mid;
+                        if (id1 != b) { m = key_val(k1, eps); mid = id1; }
+                        else { m = key_val(k2, eps); mid = key_id(k2); }
+                        if (!(m > -eps)) mid = -1;
+                        float pc = 0.5f * (pp - m);
+                        Cz[i] = pc;
+                        if (record) {
+                            long long o = nb.off + (long long)zl * ps + i;
+                            if (phys.kind != LSGG_PHYSICS_IDEAL) B.IDF[o] = mid;
+                            if (dbg.m) { dbg.m[o] = m; dbg.idm[o] = mid; dbg.phic[o] = pc; dbg.phip[o] = pp; }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const int zb = zin - 1 + (is3d ? 0 : 1);     // 2D: classify plane 0 right away
+        const bool do_b = is3d ? (fz ? zb >= z_first + 1 && zb <= nz + kRedistReach - 1 : zb >= 0 && zb < nz) : true;
+        if (do_b) {
+            // ---- B: classification of plane zb -> G ----
+            const float* Cm = C + (size_t)pmod(zb - 1, 3) * A;
+            const float* C0 = C + (size_t)pmod(zb, 3) * A;
+            const float* Cp = C + (size_t)pmod(zb + 1, 3) * A;
+            for (int i = threadIdx.x; i < A; i += blockDim.x) {
+                int y = i / nx, x = i - y * nx;
+                float v = C0[i];
+                bool pos = v > 0.0f;
+                float a = fabsf(v);
+                float inv2 = 0.0f;
+                bool ref = false, zero = false;
+                {   // x axis
+                    float dmin = FLT_MAX;
+                    float l = x > 0 ? C0[i - 1] : (fx ? C0[i + nx - 1] : -eps);
+                    float r = x < nx - 1 ? C0[i + 1] : (fx ? C0[i - nx + 1] : -eps);
+                    opp_delta(a, pos, l, dmin);
+                    opp_delta(a, pos, r, dmin);
+                    if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
+                }
+                {   // y axis
+                    float dmin = FLT_MAX;
+                    float l = y > 0 ? C0[i - nx] : (fy ? C0[i + (ny - 1) * nx] : -eps);
+                    float r = y < ny - 1 ? C0[i + nx] : (fy ? C0[i - (ny - 1) * nx] : -eps);
+                    opp_delta(a, pos, l, dmin);
+                    opp_delta(a, pos, r, dmin);
+                    if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
+                }
+                if (is3d) {
+                    float dmin = FLT_MAX;
+                    opp_delta(a, pos, Cm[i], dmin);
+                    opp_delta(a, pos, Cp[i], dmin);
+                    if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
+                }
+                float mag = eps;
+                if (ref) mag = zero ? 0.0f : 1.0f / sqrtf(inv2);
+                G[i] = pos ? mag : -mag;
+            }
+            __syncthreads();
+            // ---- C: x pass G -> H, y pass H -> forward z sweep into F ----
+            for (int i = threadIdx.x; i < A; i += blockDim.x) {
+                int y = i / nx, x = i - y * nx;
+                H[i] = line_min(G + y * nx, x, nx, 1, fx);
+            }
+            __syncthreads();
+            float* Fz = F + (size_t)(is3d ? pmod(zb, 7) : 0) * A;
+            const float* Fprev = F + (size_t)pmod(zb - 1, 7) * A;
+            const bool first = !is3d || zb == (fz ? z_first + 1 : 0);
+            for (int i = threadIdx.x; i < A; i += blockDim.x) {
+                int y = i / nx, x = i - y * nx;
+                float v = line_min(H + x, y, ny, nx, fy);
+                if (!first) {
+                    float p = Fprev[i];
+                    if (sgn_pos(p) == sgn_pos(v)) {
+                        float m = fminf(fabsf(v), fabsf(p) + 1.0f);
+                        v = sgn_pos(v) ? m : -m;
+                    }
+                }
+                Fz[i] = v;
+            }
+        }
+        __syncthreads();
+        // ---- E: backward z window, output plane zo ----
+        const int zo = is3d ? zb - kRedistReach : zb;
+        if (zo >= 0 && zo < nz && (is3d || zin == 0)) {
+            const int ztop = is3d ? (fz ? zb : min(zb, nz - 1)) : zo;
+            float* dst = B.X + nb.off + (long long)zo * ps;
+            for (int i = threadIdx.x; i < A; i += blockDim.x) {
+                float v = F[(size_t)(is3d ? pmod(zo, 7) : 0) * A + i];
+                const bool s = sgn_pos(v);
+                float best = fabsf(v);
+                if (is3d) {
+#pragma unroll
+                    for (int k = 1; k <= kRedistReach; ++k) {
+                        if (zo + k > ztop) break;
+                        float u = F[(size_t)pmod(zo + k, 7) * A + i];
+                        if (sgn_pos(u) != s) break;
+                        best = fminf(best, fabsf(u) + (float)k);
+                    }
+                }
+                best = fminf(best, eps);
+                float out = s ? best : -best;
+                dst[i] = out;
+                if (dbg.phin) dbg.phin[nb.off + (long long)zo * ps + i] = out;
+                if (out > 0.0f) {
+                    int y = i / nx, x = i - y * nx;
+                    lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);
+                    lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
+                    lo[2] = min(lo[2], zo); hi[2] = max(hi[2], zo);
+                }
+            }
+        }
+        // F slot reuse and C slot reuse are separated by the barriers of the next A and B stages
+        if (!is3d) break;
+    }
+    // ---- positive bounding box of this box ----
+    for (int a = 0; a < 3; ++a) {
+        int l = lo[a], h = hi[a];
+        for (int o = 16; o > 0; o >>= 1) {
+            l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+            h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+        }
+        lo[a] = l; hi[a] = h;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) s_red[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; ++a) { atomicMin(&s_red[a], lo[a]); atomicMax(&s_red[3 + a], hi[a]); }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Bounds bd;
+        for (int a = 0; a < 3; ++a) { bd.lo[a] = s_red[a]; bd.hi[a] = s_red[3 + a]; }
+        B.bounds[b] = bd;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_correct(StepBuffers B, PhysicsDev phys, DebugOut dbg, int cls) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_box;
+    __shared__ int s_red[6];
+    const int side = B.class_side[cls];
+    int* gx = reinterpret_cast<int*>(smem_raw);
+    int* gy = gx + side;
+    float* buf = reinterpret_cast<float*>(gy + side + 4);
+    buf = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(buf) + 15) & ~uintptr_t(15));
+    if (cls == kNumClasses - 1) buf = B.scratch + (long long)blockIdx.x * B.scratch_per_cta;
+    for (;;) {
+        int b = pull_box(B, 1, cls, &s_box);
+        if (b < 0) break;
+        correct_box(B, phys, dbg, b, gx, gy, buf, s_red);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// box update (single CTA)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int box_class(const StepBuffers& B, const Box& b) {
+    int s = max(b.nx, b.ny);
+    for (int c = 0; c < kNumClasses - 1; ++c)
+        if (s <= B.class_side[c]) return c;
+    return kNumClasses - 1;
+}
+
+__global__ void __launch_bounds__(kBoxUpdateThreads)
+k_box_update(StepBuffers B, int layout_only) {
+    __shared__ long long s_part[kBoxUpdateThreads];
+    __shared__ int s_cnt[kNumClasses];
+    __shared__ long long s_alive;
+    const int G = B.n_boxes;
+    const Domain D = B.dom;
+    if (*(volatile int*)&B.st->halt && !layout_only) return;
+    if (threadIdx.x < kNumClasses) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_alive = 0;
+    const int per = (G + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(G, b0 + per);
+    long long sum = 0;
+    for (int b = b0; b < b1; ++b) {
+        Box cb = B.cur[b];
+        if (!layout_only) {
+            Box n = cb;
+            if (cb.nx > 0) {
+                Bounds bd = B.bounds[b];
+                if (bd.hi[0] < bd.lo[0]) {
+                    n.nx = n.ny = n.nz = 0;          // extinct: no positive cell
+                } else {
+                    int Ns[3] = {D.nx, D.ny, D.nz};
+                    int os[3] = {cb.ox, cb.oy, cb.oz};
+                    int ns[3] = {cb.nx, cb.ny, cb.nz};
+                    int no[3], nn[3];
+                    for (int a = 0; a < 3; ++a) {
+                        if (a == 2 && D.dim == 2) { no[a] = 0; nn[a] = 1; continue; }
+                        int ext = bd.hi[a] - bd.lo[a] + 1 + 2 * D.halo;
+                        bool was_full = ns[a] == Ns[a];
+                        if (ext >= Ns[a]) {
+                            nn[a] = Ns[a];
+                            no[a] = was_full ? os[a] : pmod(os[a] + bd.lo[a] - D.halo, Ns[a]);
+                        } else {
+                            nn[a] = ext;
+                            no[a] = pmod(os[a] + bd.lo[a] - D.halo, Ns[a]);
+                        }
+                    }
+                    n.ox = no[0]; n.oy = no[1]; n.oz = no[2];
+                    n.nx = nn[0]; n.ny = nn[1]; n.nz = nn[2];
+                }
+            }
+            B.prev[b] = cb;
+            B.cur[b] = n;
+            cb = n;
+        }
+        sum += box_elems(cb);
+    }
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    // inclusive scan of the per-thread sums (Hillis-Steele, fixed order)
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        long long v = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0;
+        __syncthreads();
+        s_part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const long long total = s_part[blockDim.x - 1];
+    if (threadIdx.x == 0 && !layout_only) B.st->steps_done += 1;   // the step's fields are complete
+    if (total > B.cap) {
+        if (threadIdx.x == 0) {
+            B.st->status = LSGG_ERR_CAPACITY;
+            B.st->halt = 1;
+            B.st->box_cells = total;
+        }
+        return;
+    }
+    long long off = s_part[threadIdx.x] - sum;
+    long long cells = 0, alive = 0;
+    for (int b = b0; b < b1; ++b) {
+        Box cb = B.cur[b];
+        cb.off = off;
+        off += box_elems(cb);
+        B.cur[b] = cb;
+        if (cb.nx > 0) {
+            int c = box_class(B, cb);
+            int w = atomicAdd(&s_cnt[c], 1);
+            B.worklist[c * G + w] = b;
+            cells += (long long)cb.nx * cb.ny * cb.nz;
+            alive += 1;
+        }
+    }
+    // reduce cells / alive
+    __syncthreads();
+    s_part[threadIdx.x] = cells;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o) s_part[threadIdx.x] += s_part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) B.st->box_cells = s_part[0];
+    atomicAdd((unsigned long long*)&s_alive, (unsigned long long)alive);
+    __syncthreads();
+    if (threadIdx.x < kNumClasses) {
+        B.st->class_count[threadIdx.x] = s_cnt[threadIdx.x];
+        B.st->queue[0][threadIdx.x] = 0;
+        B.st->queue[1][threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) B.st->alive = s_alive;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers
+// ---------------------------------------------------------------------------
+
+static size_t predict_smem_bytes(int side, int R) {
+    size_t ints = (size_t)2 * (side + 2 * kMaxRadius) + 2 * side + 4;
+    size_t floats = (size_t)(side + 2 * R) * (side + 2 * R) + (size_t)side * (side + 2 * R) +
+                    (size_t)(2 * R + 1) * side * side;
+    return ints * 4 + 16 + floats * 4;
+}
+static size_t correct_smem_bytes(int side) {
+    return ((size_t)2 * side + 4) * 4 + 16 + (size_t)12 * side * side * 4;
+}
+
+cudaError_t configure_step_kernels(StepBuffers& B) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int n_sm = 0, max_optin = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    B.n_sm = n_sm;
+    const int R = B.dom.radius;
+    int big = B.dom.nx > B.dom.ny ? B.dom.nx : B.dom.ny;
+    if (B.dom.nz > big) big = B.dom.nz;
+    // class sides 32, 48 and the largest side <= 64 whose buffers fit shared memory
+    int want[kNumClasses - 1] = {32, 48, 64};
+    for (int c = 0; c < kNumClasses - 1; ++c) {
+        int side = want[c];
+        while (side > 8 && ((int)predict_smem_bytes(side, R) > max_optin || (int)correct_smem_bytes(side) > max_optin))
+            side -= 4;
+        B.class_side[c] = side;
+    }
+    B.class_side[kNumClasses - 1] = big;
+    size_t mp = 0, mc = 0;
+    for (int c = 0; c < kNumClasses; ++c) {
+        size_t sp, sc;
+        if (c < kNumClasses - 1) {
+            sp = predict_smem_bytes(B.class_side[c], R);
+            sc = correct_smem_bytes(B.class_side[c]);
+        } else {
+            sp = (size_t)(2 * (big + 2 * kMaxRadius) + 2 * big + 4) * 4 + 16;
+            sc = ((size_t)2 * big + 4) * 4 + 16;
+        }
+        B.smem[0][c] = sp;
+        B.smem[1][c] = sc;
+        if (sp > mp) mp = sp;
+        if (sc > mc) mc = sc;
+    }
+    e = cudaFuncSetAttribute(k_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_correct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mc);
+    if (e != cudaSuccess) return e;
+    for (int c = 0; c < kNumClasses; ++c) {
+        int occ_p = 0, occ_c = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, k_predict, kThreads, B.smem[0][c]);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k_correct, kThreads, B.smem[1][c]);
+        if (occ_p < 1) occ_p = 1;
+        if (occ_c < 1) occ_c = 1;
+        if (c < kNumClasses - 1) {
+            B.grid[0][c] = n_sm * occ_p;
+            B.grid[1][c] = n_sm * occ_c;
+        } else {
+            B.grid[0][c] = B.grid[1][c] = (n_sm + 3) / 4;
+        }
+    }
+    return cudaSuccess;
+}
+
+long long large_class_scratch_floats(const Domain& d) {
+    int big = d.nx > d.ny ? d.nx : d.ny;
+    long long side = big;
+    long long p = (side + 2 * kMaxRadius) * (side + 2 * kMaxRadius) + side * (side + 2 * kMaxRadius) +
+                  (long long)(2 * kMaxRadius + 1) * side * side;
+    long long c = 12 * side * side;
+    long long m = p > c ? p : c;
+    return (m + 31) & ~31LL;
+}
+
+cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream_t s) {
+    k_box_update<<<1, kBoxUpdateThreads, 0, s>>>(B, layout_only ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
+                        const DebugOut* dbg, cudaStream_t s) {
+    long long ncell = (long long)B.dom.nx * B.dom.ny * B.dom.nz;
+    cudaError_t e = cudaMemsetAsync(B.T, 0, (size_t)ncell * 16, s);
+    if (e != cudaSuccess) return e;
+    for (int c = 0; c < kNumClasses; ++c) {
+        k_predict<<<B.grid[0][c], kThreads, B.smem[0][c], s>>>(B, taps, phys, c);
+    }
+    DebugOut d{};
+    if (dbg) d = *dbg;
+    for (int c = 0; c < kNumClasses; ++c) {
+        k_correct<<<B.grid[1][c], kThreads, B.smem[1][c], s>>>(B, phys, d, c);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_box_update(B, false, s);
+}
+
+}  // namespace lsgg

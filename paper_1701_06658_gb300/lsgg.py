@@ -1,0 +1,332 @@
+"""Python binding of the ``liblsgg`` C ABI (include/lsgg.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  The functions keep the C names without the ``lsgg_`` prefix
+(``create_microstructure``, ``step``, ``grain_volumes``, ``voxel_owner``, ...);
+``Microstructure`` wraps a context.  The library must have been built in-tree
+(``paper_1701_06658_gb300.build.build()``); importing this module without it
+raises ``ImportError`` -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblsgg.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OUT_OF_MEMORY = -2
+ERR_OVER_BUDGET = -3
+ERR_CUDA = -4
+ERR_TIMEOUT = -5
+ERR_NOT_READY = -6
+ERR_CAPACITY = -7
+ERR_UNSUPPORTED = -8
+
+INIT_VORONOI, INIT_LAGUERRE = 0, 1
+PHYSICS_IDEAL, PHYSICS_READ_SHOCKLEY, PHYSICS_MAGNETIC = 0, 1, 2
+STORAGE_FP32, STORAGE_BF16 = 0, 1
+EXEC_BATCHED, EXEC_PLAIN = 0, 1
+MOBILITY_STEP, MOBILITY_EQ20 = 0, 1
+
+_dp = C.POINTER(C.c_double)
+
+
+class Config(C.Structure):
+    """Mirror of ``lsgg_config`` (field order and types as in lsgg.h)."""
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("n_grains", C.c_int32),
+        ("seed", C.c_uint64),
+        ("halo", C.c_int32), ("radius", C.c_int32),
+        ("eps", C.c_float),
+        ("init_kind", C.c_int32), ("physics", C.c_int32), ("storage", C.c_int32),
+        ("exec", C.c_int32), ("mobility_law", C.c_int32), ("device", C.c_int32),
+        ("theta_max_deg", C.c_double), ("mob_low", C.c_double),
+        ("lognormal_sigma", C.c_double), ("big_fraction", C.c_double), ("big_volume", C.c_double),
+        ("field_dir", C.c_double * 3),
+        ("energy_scale", C.c_double),
+        ("arena_slack", C.c_double),
+        ("seeds", _dp), ("weights", _dp), ("quats", _dp), ("energy", _dp),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("steps_done", C.c_int64), ("alive", C.c_int64), ("box_cells", C.c_int64),
+        ("arena_capacity", C.c_int64), ("superimposition", C.c_double),
+        ("device_bytes", C.c_int64), ("n_classes", C.c_int32), ("class_count", C.c_int32 * 8),
+    ]
+
+
+class LsggError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        self.code = code
+        super().__init__(f"{fn}: {status_string(code)} ({code})")
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "lsgg_config_default": (None, [C.POINTER(Config)]),
+    "lsgg_create_microstructure": (C.c_int, [C.POINTER(Config), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lsgg_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_double]),
+    "lsgg_sync": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lsgg_grain_volumes": (C.c_int, [C.c_void_p, _dp, C.c_int64, C.POINTER(C.c_int64)]),
+    "lsgg_voxel_owner": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
+    "lsgg_destroy": (C.c_int, [C.c_void_p]),
+    "lsgg_status_string": (C.c_char_p, [C.c_int]),
+    "lsgg_get_stream": (C.c_void_p, [C.c_void_p]),
+    "lsgg_abi_config_size": (C.c_size_t, []),
+    "lsgg_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "lsgg_get_boxes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
+    "lsgg_get_phi": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_int64)]),
+    "lsgg_set_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
+    "lsgg_debug_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "lsgg_generate_seeds": (C.c_int, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
+}
+
+
+def lib():
+    """The loaded library (ImportError if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_1701_06658_gb300.build.build() "
+                              "(needs nvcc); there is no non-CUDA implementation")
+        h = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        if h.lsgg_abi_config_size() != C.sizeof(Config):
+            raise ImportError("lsgg_config layout mismatch between liblsgg.so and the binding")
+        _lib = h
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().lsgg_status_string(code).decode()
+
+
+def _check(fn: str, code: int):
+    if code != OK:
+        raise LsggError(fn, code)
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+def config_default() -> Config:
+    cfg = Config()
+    lib().lsgg_config_default(C.byref(cfg))
+    return cfg
+
+
+def generate_seeds(seed: int, n: int, nx: int, ny: int, nz: int) -> np.ndarray:
+    out = np.zeros((n, 3), dtype=np.float64)
+    _check("generate_seeds", lib().lsgg_generate_seeds(seed, n, nx, ny, nz, _ptr(out, C.c_double)))
+    return out
+
+
+def create_microstructure(cfg: Config, stream=None):
+    ctx = C.c_void_p()
+    _check("create_microstructure", lib().lsgg_create_microstructure(C.byref(cfg), stream, C.byref(ctx)))
+    return ctx
+
+
+def step(ctx, n: int, dt: float):
+    _check("step", lib().lsgg_step(ctx, int(n), float(dt)))
+
+
+def sync(ctx, timeout_ms: int = -1):
+    _check("sync", lib().lsgg_sync(ctx, int(timeout_ms)))
+
+
+def destroy(ctx):
+    _check("destroy", lib().lsgg_destroy(ctx))
+
+
+def get_stream(ctx) -> int:
+    return lib().lsgg_get_stream(ctx) or 0
+
+
+def grain_volumes(ctx, n_grains: int, out=None) -> np.ndarray:
+    out = np.zeros(n_grains, dtype=np.float64) if out is None else out
+    n = C.c_int64()
+    _check("grain_volumes", lib().lsgg_grain_volumes(ctx, _ptr(out, C.c_double), out.size, C.byref(n)))
+    return out
+
+
+def voxel_owner(ctx, shape_zyx, out=None) -> np.ndarray:
+    out = np.zeros(shape_zyx, dtype=np.int32) if out is None else out
+    _check("voxel_owner", lib().lsgg_voxel_owner(ctx, _ptr(out, C.c_int32), out.size))
+    return out
+
+
+def get_stats(ctx) -> Stats:
+    s = Stats()
+    _check("get_stats", lib().lsgg_get_stats(ctx, C.byref(s)))
+    return s
+
+
+def get_boxes(ctx, n_grains: int) -> np.ndarray:
+    out = np.zeros((n_grains, 7), dtype=np.int32)
+    _check("get_boxes", lib().lsgg_get_boxes(ctx, _ptr(out, C.c_int32), out.size))
+    return out
+
+
+def get_phi(ctx) -> np.ndarray:
+    n = C.c_int64()
+    code = lib().lsgg_get_phi(ctx, None, 0, C.byref(n))
+    if code not in (OK, ERR_CAPACITY):
+        _check("get_phi", code)
+    out = np.zeros(n.value, dtype=np.float32)
+    _check("get_phi", lib().lsgg_get_phi(ctx, _ptr(out, C.c_float), out.size, C.byref(n)))
+    return out
+
+
+def set_state(ctx, boxes: np.ndarray, phi: np.ndarray, idf: np.ndarray | None = None):
+    b = np.ascontiguousarray(boxes, dtype=np.int32)
+    p = np.ascontiguousarray(phi, dtype=np.float32)
+    i = None if idf is None else np.ascontiguousarray(idf, dtype=np.int32)
+    _check("set_state", lib().lsgg_set_state(ctx, _ptr(b, C.c_int32), _ptr(p, C.c_float), _ptr(i, C.c_int32)))
+
+
+def packed_size(boxes: np.ndarray) -> int:
+    alive = boxes[:, 0] != 0
+    return int((boxes[alive, 4].astype(np.int64) * boxes[alive, 5] * boxes[alive, 6]).sum())
+
+
+def debug_step(ctx, dt: float, boxes: np.ndarray):
+    """One step returning the packed intermediates (phip, m, idm, phic, phin)
+    on ``boxes`` (the boxes returned by get_boxes before the call)."""
+    n = packed_size(boxes)
+    phip = np.zeros(n, np.float32)
+    m = np.zeros(n, np.float32)
+    idm = np.zeros(n, np.int32)
+    phic = np.zeros(n, np.float32)
+    phin = np.zeros(n, np.float32)
+    _check("debug_step", lib().lsgg_debug_step(ctx, float(dt), _ptr(phip, C.c_float), _ptr(m, C.c_float),
+                                                _ptr(idm, C.c_int32), _ptr(phic, C.c_float), _ptr(phin, C.c_float)))
+    return phip, m, idm, phic, phin
+
+
+def unpack(boxes: np.ndarray, packed: np.ndarray) -> dict:
+    """Split a packed array into per-grain (nz, ny, nx) arrays keyed by grain id."""
+    out = {}
+    o = 0
+    for g, b in enumerate(boxes):
+        if not b[0]:
+            continue
+        n = int(b[4]) * int(b[5]) * int(b[6])
+        out[g] = packed[o:o + n].reshape(int(b[6]), int(b[5]), int(b[4]))
+        o += n
+    return out
+
+
+def pack(boxes: np.ndarray, arrays: dict, dtype=np.float32) -> np.ndarray:
+    parts = [np.asarray(arrays[g], dtype=dtype).ravel() for g, b in enumerate(boxes) if b[0]]
+    return np.concatenate(parts) if parts else np.zeros(0, dtype)
+
+
+class Microstructure:
+    """A context: create -> step / sync -> outputs -> close."""
+
+    def __init__(self, nx: int, ny: int, nz: int, n_grains: int, seed: int = 1, seeds=None, weights=None,
+                 quats=None, energy=None, physics: int = PHYSICS_IDEAL, exec_mode: int = EXEC_BATCHED,
+                 storage: int = STORAGE_FP32, halo: int = 5, radius: int = 5, eps: float = 7.0,
+                 init_kind: int | None = None, stream=None, device: int = 0, arena_slack: float = 1.5, **extra):
+        cfg = config_default()
+        cfg.nx, cfg.ny, cfg.nz, cfg.n_grains, cfg.seed = nx, ny, nz, n_grains, seed
+        cfg.halo, cfg.radius, cfg.eps = halo, radius, eps
+        cfg.physics, cfg.exec, cfg.storage, cfg.device = physics, exec_mode, storage, device
+        cfg.arena_slack = arena_slack
+        for k, v in extra.items():
+            if k == "field_dir":
+                for a in range(3):
+                    cfg.field_dir[a] = float(v[a])
+            else:
+                setattr(cfg, k, v)
+        self._keep = []
+        if seeds is not None:
+            s = np.ascontiguousarray(seeds, dtype=np.float64)
+            self._keep.append(s)
+            cfg.seeds = _ptr(s, C.c_double)
+        if weights is not None:
+            w = np.ascontiguousarray(weights, dtype=np.float64)
+            self._keep.append(w)
+            cfg.weights = _ptr(w, C.c_double)
+        cfg.init_kind = (INIT_LAGUERRE if weights is not None else INIT_VORONOI) if init_kind is None else init_kind
+        if quats is not None:
+            q = np.ascontiguousarray(quats, dtype=np.float64)
+            self._keep.append(q)
+            cfg.quats = _ptr(q, C.c_double)
+        if energy is not None:
+            e = np.ascontiguousarray(energy, dtype=np.float64)
+            self._keep.append(e)
+            cfg.energy = _ptr(e, C.c_double)
+        self.shape = (nz, ny, nx)
+        self.n_grains = n_grains
+        self.ctx = create_microstructure(cfg, stream)
+        self._keep.clear()
+
+    def step(self, n: int, dt: float = 1.0):
+        step(self.ctx, n, dt)
+
+    def sync(self, timeout_ms: int = -1):
+        sync(self.ctx, timeout_ms)
+
+    def grain_volumes(self) -> np.ndarray:
+        return grain_volumes(self.ctx, self.n_grains)
+
+    def voxel_owner(self) -> np.ndarray:
+        return voxel_owner(self.ctx, self.shape)
+
+    def boxes(self) -> np.ndarray:
+        return get_boxes(self.ctx, self.n_grains)
+
+    def phi(self) -> dict:
+        b = self.boxes()
+        return unpack(b, get_phi(self.ctx))
+
+    def set_state(self, boxes, phi_by_grain: dict, idf_by_grain: dict | None = None):
+        p = pack(boxes, phi_by_grain)
+        i = None if idf_by_grain is None else pack(boxes, idf_by_grain, np.int32)
+        set_state(self.ctx, boxes, p, i)
+
+    def debug_step(self, dt: float = 1.0):
+        b = self.boxes()
+        parts = debug_step(self.ctx, dt, b)
+        return b, [unpack(b, p) for p in parts]
+
+    def stats(self) -> Stats:
+        return get_stats(self.ctx)
+
+    @property
+    def stream(self) -> int:
+        return get_stream(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

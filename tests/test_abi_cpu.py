@@ -1,0 +1,87 @@
+"""The C-ABI library without a GPU: it loads, exports every function that
+include/lsgg.h declares, agrees with the binding's struct layout, implements
+the seed generator bit for bit like the inputs module, and refuses to compute
+without a CUDA device (no CPU fallback)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1701_06658_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    L = pytest.importorskip("paper_1701_06658_gb300.lsgg")
+    try:
+        L.lib()
+    except ImportError as e:
+        pytest.fail(f"liblsgg.so not built: {e}")
+    return L
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lsgg_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol():
+    L = _lib()
+    h = ctypes.CDLL(L.LIB_PATH)
+    names = declared_functions()
+    assert "lsgg_create_microstructure" in names and "lsgg_step" in names
+    missing = [n for n in names if not hasattr(h, n)]
+    assert not missing, missing
+
+
+def test_config_layout_and_defaults():
+    L = _lib()
+    assert L.lib().lsgg_abi_config_size() == ctypes.sizeof(L.Config)
+    cfg = L.config_default()
+    assert (cfg.nx, cfg.ny, cfg.nz, cfg.n_grains, cfg.halo, cfg.radius) == (64, 64, 64, 50, 5, 5)
+    assert cfg.eps == 7.0 and cfg.arena_slack == 1.5
+
+
+@pytest.mark.parametrize("seed,n,shape", [(1, 50, (64, 64, 64)), (2, 5000, (256, 256, 256)),
+                                          (7, 33, (40, 30, 1)), (2 ** 63 + 5, 10, (17, 19, 23))])
+def test_seed_generator_matches_inputs_module(seed, n, shape):
+    L = _lib()
+    got = L.generate_seeds(seed, n, *shape)
+    want = I.voronoi_seeds(seed, n, shape)
+    assert np.array_equal(got, want)
+
+
+def test_status_strings():
+    L = _lib()
+    assert L.status_string(0) == "ok"
+    assert L.status_string(L.ERR_CUDA) == "CUDA error"
+    assert L.status_string(-99) == "unknown status"
+
+
+def test_invalid_arguments_rejected_before_any_device_work():
+    L = _lib()
+    cfg = L.config_default()
+    cfg.n_grains = 0
+    with pytest.raises(L.LsggError) as e:
+        L.create_microstructure(cfg)
+    assert e.value.code == L.ERR_INVALID_ARG
+    with pytest.raises(L.LsggError):
+        L.generate_seeds(1, 0, 4, 4, 4)
+
+
+def test_no_cpu_fallback_without_a_device():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = _lib()
+    with pytest.raises(L.LsggError) as e:
+        L.Microstructure(16, 16, 16, 4)
+    assert e.value.code == L.ERR_CUDA
