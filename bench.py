@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Benchmark of the local level-set grain-growth step on GB300.
+
+A "step" is one pass of the whole hot path over every grain box: heat-kernel
+predictor, comparison step, taxicab re-initialisation and box update.  The
+workload is a 256^3 periodic domain with 5000 Voronoi grains (seed 2), ideal
+growth, dt = 1 (kernel variance 2 per axis), FP32 -- the paper-like 3D shape
+(about 19 cells per grain diameter).
+
+Output: one JSON line on rank 0.  ``value`` = box cell-updates per second
+(box cells advanced by one full step, summed over grains and timed steps,
+divided by the device time of the timed steps, max over ranks, summed over
+ranks' work).  Multi-GPU runs are independent replicas (the step has no
+cross-replica exchange): weak scaling.
+
+--impl reference times the FP64 oracle on the host cores on a bounded sample
+of the same workload (a 64^3 periodic sub-domain at the same grain density).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {"n": 256, "grains": 5000, "seed": 2, "dt": 1.0}
+SAMPLE = {"n": 64, "grains": 78, "seed": 2}     # same density: 64^3 / 78 = 3361 cells per grain
+METRIC = "LS box cell-updates/s"
+UNIT = "cell-updates/s"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1701_06658_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(cs, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, units_per_launch: float):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to this launch by units processed; None if the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        k = d.get(kernel)
+        if not k or k.get("source_hash") != kernel_source_hash():
+            return None
+        return k["dram_bytes_per_launch"] * units_per_launch / k["units_per_launch"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        try:
+            self.fh.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and "Active" in r[4 + k]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+
+def oracle_sample_run(steps: int, warmup: int):
+    """The FP64 oracle on the bounded sample: 64^3 periodic domain, 78 Voronoi
+    grains (seed 2), dt = 1; returns (cell-updates/s, seconds, cell-updates)."""
+    from oracle import lsgg_oracle as O
+    from paper_1701_06658_gb300 import inputs as I
+    n, g = SAMPLE["n"], SAMPLE["grains"]
+    ms = O.tessellate((n, n, n), I.voronoi_seeds(SAMPLE["seed"], g, (n, n, n)))
+    for _ in range(warmup):
+        ms = O.step(ms, 1.0)
+    cells = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        cells += sum(int(np.prod(gr.dims)) for gr in ms.grains if gr.alive)
+        ms = O.step(ms, 1.0)
+    dt = time.perf_counter() - t0
+    return cells / dt, dt, cells
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    rate, secs, cells = oracle_sample_run(args.steps, args.warmup)
+    sample = (f"{SAMPLE['n']}^3 periodic sub-domain at the workload's grain density "
+              f"({SAMPLE['grains']} Voronoi grains, seed {SAMPLE['seed']}), {args.steps} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config():
+    return {"workload": f"{WORKLOAD['n']}^3 periodic, {WORKLOAD['grains']} Voronoi grains (seed {WORKLOAD['seed']}), "
+                        f"ideal growth, dt={WORKLOAD['dt']}, box halo 5, eps 7, FP32",
+            "domain": [WORKLOAD["n"]] * 3, "grains": WORKLOAD["grains"], "dt": WORKLOAD["dt"],
+            "l2": "inputs larger than L2: box arena ~0.8 GB per buffer and 268 MB field vs 129 MB L2"}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def gpu_arm(args):
+    import numpy as np  # noqa: F401
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1701_06658_gb300 import inputs as I
+    from paper_1701_06658_gb300 import lsgg as L
+    L.lib()
+    n, g, dt = WORKLOAD["n"], WORKLOAD["grains"], WORKLOAD["dt"]
+    seed = WORKLOAD["seed"] + 1000 * rank          # independent replica per rank
+    seeds = I.voronoi_seeds(seed, g, (n, n, n))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---------------- device-resident timing ----------------
+    ms = L.Microstructure(n, n, n, g, seeds=seeds, device=local)
+    stream = torch.cuda.ExternalStream(ms.stream)
+    ms.step(args.warmup, dt)
+    ms.sync()
+    s0 = ms.stats()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        ms.step(args.steps, dt)
+        ev1.record(stream)
+        ms.sync()
+        torch.cuda.synchronize()
+    barrier()
+    dev_ms = ev0.elapsed_time(ev1)
+    s1 = ms.stats()
+    cells = s1.cell_updates - s0.cell_updates
+    box_cells_mean = cells / args.steps
+
+    # ---------------- per-kernel event timing (separate pass) ----------------
+    L.profile(ms.ctx, True)
+    kprof = min(args.steps, 20)
+    ms.step(kprof, dt)
+    ktimes, kcount = L.kernel_times(ms.ctx)
+    L.profile(ms.ctx, False)
+    s2 = ms.stats()
+    cells_prof = s2.cell_updates - s1.cell_updates
+    ms.close()
+
+    # ---------------- end to end through the public API ----------------
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e = L.Microstructure(n, n, n, g, seeds=seeds, device=local)   # H2D of the seeds, init
+    d2h = 0
+    for _ in range(args.steps):
+        e2e.step(1, dt)
+        vol = e2e.grain_volumes()                                      # D2H of the step's result
+        d2h += vol.nbytes
+    own = e2e.voxel_owner()
+    d2h += own.nbytes
+    se = e2e.stats()
+    e2e.close()
+    e2e_s = time.perf_counter() - t0
+    e2e_cells = se.cell_updates
+
+    # ---------------- reduce over ranks ----------------
+    vals = [dev_ms, float(cells), e2e_s, float(e2e_cells)]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        dev_ms, cells_all, e2e_s, e2e_cells_all = mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
+    else:
+        cells_all, e2e_cells_all = float(cells), float(e2e_cells)
+    if rank != 0:
+        return 0
+
+    value = cells_all / (dev_ms * 1e-3)
+    # roofline of the dominant kernel (algorithmic bytes: 8 B per box cell + 16 B per domain cell)
+    peaks, src = measured_peaks()
+    dom_cells = n ** 3
+    per_launch_ms = {k: ktimes[k] / max(1, kprof) for k in ("k_predict", "k_correct")}
+    dominant = max(per_launch_ms, key=per_launch_ms.get)
+    box_cells_prof = cells_prof / kprof
+    alg_bytes = 8.0 * box_cells_prof + 16.0 * dom_cells
+    achieved = alg_bytes / (per_launch_ms[dominant] * 1e-3) / 1e9
+    traffic = profiled_traffic(dominant, box_cells_prof)
+    cpu_rate, cpu_s, cpu_cells = oracle_sample_run(steps=2, warmup=0) if not args.no_cpu else (None, 0, 0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(),
+        "domain_cell_updates_per_s": world * dom_cells * args.steps / (dev_ms * 1e-3),
+        "box_cells_per_step": box_cells_mean,
+        "superimposition": box_cells_mean / dom_cells,
+        "kernel_ms_per_step": {k: v / max(1, kprof) for k, v in ktimes.items()},
+        "gpu_launches": int(sum(kcount.values()) * args.steps / max(1, kprof)),
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
+                     "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": achieved / peaks.get("hbm_gbs"), "peak_source": src,
+                     "algorithmic_bytes_per_launch": alg_bytes, "traffic": traffic},
+        "e2e": {"value": e2e_cells_all / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * 3 * g / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "seconds": e2e_s, "includes": "create_microstructure from host seeds, steps, per-step volumes "
+                                               "to host, final owner map to host"},
+        "cpu_baseline": None if cpu_rate is None else {
+            "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"2 oracle steps of a {SAMPLE['n']}^3 periodic sub-domain at the workload's grain "
+                      f"density ({SAMPLE['grains']} grains), {cpu_s:.1f} s"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    import numpy as np
+    sys.exit(main())

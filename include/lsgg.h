@@ -144,6 +144,7 @@ size_t lsgg_abi_config_size(void);
 /* ------------------------------------------------------------- inspection */
 typedef struct lsgg_stats {
     int64_t steps_done;        /* steps completed since creation */
+    int64_t cell_updates;      /* box cells advanced, summed over completed steps */
     int64_t alive;             /* grains with a positive cell */
     int64_t box_cells;         /* sum over alive grains of box volume (cells) */
     int64_t arena_capacity;    /* device arena capacity per buffer (elements) */
@@ -154,6 +155,17 @@ typedef struct lsgg_stats {
 } lsgg_stats;
 
 int lsgg_get_stats(lsgg_ctx* ctx, lsgg_stats* out);
+
+/* Kernel timing with CUDA events on the context's stream.  While enabled,
+ * lsgg_step launches eagerly (no graph) and records events between the
+ * kernel groups of every step.  lsgg_kernel_times synchronises and writes,
+ * for groups 0 = neighbour-max field clear, 1 = predictor (k_predict),
+ * 2 = corrector + re-initialisation (k_correct), 3 = box update
+ * (k_box_update): out_ms[g] = summed device milliseconds and out_count[g] =
+ * kernel launches of the library in that group (any pointer may be NULL),
+ * over the steps since the previous call; then resets the sums. */
+int lsgg_profile(lsgg_ctx* ctx, int32_t enable);
+int lsgg_kernel_times(lsgg_ctx* ctx, double* out_ms, int64_t* out_count);
 
 /* Boxes of all grains: out[7*i .. 7*i+6] = alive, ox, oy, oz, nx, ny, nz
  * (origin in [0, N) per axis).  cap in int32s, >= 7 * n_grains.  Synchronises. */

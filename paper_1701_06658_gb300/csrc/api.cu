@@ -60,6 +60,12 @@ struct lsgg_ctx {
     cudaGraphExec_t graph = nullptr;
     double graph_dt = -1.0;
     std::vector<void*> allocations;
+    // kernel timing (lsgg_profile)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::vector<cudaEvent_t>> ev_pending;
+    double acc_ms[4] = {0, 0, 0, 0};
+    long long acc_cnt[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -244,6 +250,9 @@ int lsgg_destroy(lsgg_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (auto& v : c->ev_pending)
+        for (cudaEvent_t e : v) c->ev_pool.push_back(e);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (void* p : c->allocations) cudaFree(p);
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -474,6 +483,7 @@ int lsgg_get_stats(lsgg_ctx* c, lsgg_stats* out) {
     if (r != LSGG_OK) return r;
     std::memset(out, 0, sizeof(*out));
     out->steps_done = c->h_st->steps_done;
+    out->cell_updates = c->h_st->cell_updates;
     out->alive = c->h_st->alive;
     out->box_cells = c->h_st->box_cells;
     out->arena_capacity = c->B.cap;
@@ -481,6 +491,36 @@ int lsgg_get_stats(lsgg_ctx* c, lsgg_stats* out) {
     out->device_bytes = c->device_bytes;
     out->n_classes = kNumClasses;
     for (int k = 0; k < kNumClasses; ++k) out->class_count[k] = c->h_st->class_count[k];
+    return LSGG_OK;
+}
+
+int lsgg_profile(lsgg_ctx* c, int32_t enable) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    c->profiling = enable != 0;
+    return LSGG_OK;
+}
+
+int lsgg_kernel_times(lsgg_ctx* c, double* out_ms, int64_t* out_count) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    const long long per_step[4] = {0, kNumClasses, kNumClasses, 1};
+    for (auto& v : c->ev_pending) {
+        for (int g = 0; g < 4; ++g) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, v[g], v[g + 1]) != cudaSuccess) return LSGG_ERR_CUDA;
+            c->acc_ms[g] += ms;
+            c->acc_cnt[g] += per_step[g];
+        }
+        for (cudaEvent_t e : v) c->ev_pool.push_back(e);
+    }
+    c->ev_pending.clear();
+    for (int g = 0; g < 4; ++g) {
+        if (out_ms) out_ms[g] = c->acc_ms[g];
+        if (out_count) out_count[g] = c->acc_cnt[g];
+        c->acc_ms[g] = 0.0;
+        c->acc_cnt[g] = 0;
+    }
     return LSGG_OK;
 }
 
@@ -644,7 +684,17 @@ int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg) {
         return LSGG_ERR_UNSUPPORTED;
     }
     for (long long i = 0; i < n; ++i) {
-        if (launch_step(c->B, taps, c->phys, dbg, c->stream) != cudaSuccess) return LSGG_ERR_CUDA;
+        cudaEvent_t* ev = nullptr;
+        if (c->profiling) {
+            std::vector<cudaEvent_t> v(5);
+            for (auto& e : v) {
+                if (!c->ev_pool.empty()) { e = c->ev_pool.back(); c->ev_pool.pop_back(); }
+                else if (cudaEventCreate(&e) != cudaSuccess) return LSGG_ERR_CUDA;
+            }
+            c->ev_pending.push_back(v);
+            ev = c->ev_pending.back().data();
+        }
+        if (launch_step(c->B, taps, c->phys, dbg, c->stream, ev) != cudaSuccess) return LSGG_ERR_CUDA;
     }
     return LSGG_OK;
 }

@@ -76,6 +76,7 @@ struct StepState {                  // device-resident control block
     long long steps_done;
     long long box_cells;            // sum of box volumes in `cur`
     long long alive;
+    long long cell_updates;         // box cells advanced by completed steps (sum over steps)
     int class_count[kNumClasses];
     int queue[2][kNumClasses];      // pull counters of the predictor / corrector kernels
 };
@@ -129,8 +130,10 @@ struct StepBuffers {
     size_t smem[2][kNumClasses];
 };
 
+// ev (optional, 5 events): recorded before the field clear, after it, after the
+// predictor launches, after the corrector launches and after the box update.
 cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
-                        const DebugOut* dbg, cudaStream_t s);
+                        const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev = nullptr);
 cudaError_t launch_box_update(const StepBuffers& B, bool commit_only_layout, cudaStream_t s);
 cudaError_t configure_step_kernels(StepBuffers& B);
 cudaError_t launch_plain_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,

@@ -495,9 +495,10 @@ k_box_update(StepBuffers B, int layout_only) {
     if (threadIdx.x == 0) s_alive = 0;
     const int per = (G + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * per, b1 = min(G, b0 + per);
-    long long sum = 0;
+    long long sum = 0, done = 0;
     for (int b = b0; b < b1; ++b) {
         Box cb = B.cur[b];
+        if (cb.nx > 0) done += (long long)cb.nx * cb.ny * cb.nz;
         if (!layout_only) {
             Box n = cb;
             if (cb.nx > 0) {
@@ -541,6 +542,7 @@ k_box_update(StepBuffers B, int layout_only) {
         __syncthreads();
     }
     const long long total = s_part[blockDim.x - 1];
+    if (!layout_only && done) atomicAdd((unsigned long long*)&B.st->cell_updates, (unsigned long long)done);
     if (threadIdx.x == 0 && !layout_only) B.st->steps_done += 1;   // the step's fields are complete
     if (total > B.cap) {
         if (threadIdx.x == 0) {
@@ -669,21 +671,27 @@ cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream
 }
 
 cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
-                        const DebugOut* dbg, cudaStream_t s) {
+                        const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev) {
     long long ncell = (long long)B.dom.nx * B.dom.ny * B.dom.nz;
+    if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = cudaMemsetAsync(B.T, 0, (size_t)ncell * 16, s);
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
     for (int c = 0; c < kNumClasses; ++c) {
         k_predict<<<B.grid[0][c], kThreads, B.smem[0][c], s>>>(B, taps, phys, c);
     }
+    if (ev) cudaEventRecord(ev[2], s);
     DebugOut d{};
     if (dbg) d = *dbg;
     for (int c = 0; c < kNumClasses; ++c) {
         k_correct<<<B.grid[1][c], kThreads, B.smem[1][c], s>>>(B, phys, d, c);
     }
+    if (ev) cudaEventRecord(ev[3], s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_box_update(B, false, s);
+    e = launch_box_update(B, false, s);
+    if (ev) cudaEventRecord(ev[4], s);
+    return e;
 }
 
 }  // namespace lsgg

@@ -57,7 +57,7 @@ class Config(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [
-        ("steps_done", C.c_int64), ("alive", C.c_int64), ("box_cells", C.c_int64),
+        ("steps_done", C.c_int64), ("cell_updates", C.c_int64), ("alive", C.c_int64), ("box_cells", C.c_int64),
         ("arena_capacity", C.c_int64), ("superimposition", C.c_double),
         ("device_bytes", C.c_int64), ("n_classes", C.c_int32), ("class_count", C.c_int32 * 8),
     ]
@@ -90,6 +90,8 @@ _SIGS = {
     "lsgg_debug_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                   C.POINTER(C.c_int32), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "lsgg_generate_seeds": (C.c_int, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
+    "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
 }
 
 
@@ -175,6 +177,21 @@ def get_stats(ctx) -> Stats:
     s = Stats()
     _check("get_stats", lib().lsgg_get_stats(ctx, C.byref(s)))
     return s
+
+
+def profile(ctx, enable: bool):
+    _check("profile", lib().lsgg_profile(ctx, 1 if enable else 0))
+
+
+KERNEL_GROUPS = ("field_clear", "k_predict", "k_correct", "k_box_update")
+
+
+def kernel_times(ctx):
+    """(ms, launches) per kernel group since the previous call (see lsgg.h)."""
+    ms = np.zeros(4, np.float64)
+    cnt = np.zeros(4, np.int64)
+    _check("kernel_times", lib().lsgg_kernel_times(ctx, _ptr(ms, C.c_double), _ptr(cnt, C.c_int64)))
+    return dict(zip(KERNEL_GROUPS, ms.tolist())), dict(zip(KERNEL_GROUPS, cnt.tolist()))
 
 
 def get_boxes(ctx, n_grains: int) -> np.ndarray:

@@ -55,7 +55,9 @@ def _check_step(L, ms, dt=1.0, tol_p=2e-5):
             pos = O.box_positions(ref_ms.grains[g], shape)
             for (z, y, x) in zip(*np.nonzero(bad)):
                 j = int(idm[g][z, y, x])
-                assert j >= 0
+                if j < 0:     # GPU max rounded to -eps: a near-tie with "no neighbour"
+                    assert ref.m[g][z, y, x] < -7.0 + 1e-4
+                    continue
                 view = O.Grain(j, ref_ms.grains[j].origin, ref.phip[j])
                 v, _ = O.sample(view, (pos[0][[z]], pos[1][[y]], pos[2][[x]]), shape, -7.0)
                 assert abs(float(v.ravel()[0]) - ref.m[g][z, y, x]) < 1e-4
