@@ -127,7 +127,7 @@ class ClockSampler:
         reasons = set()
         for r in rows:
             for k, nm in enumerate(names):
-                if len(r) > 4 + k and "Active" in r[4 + k]:
+                if len(r) > 4 + k and r[4 + k].strip() == "Active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(rows)}

@@ -33,6 +33,9 @@ cudaError_t launch_pack_cur(int G, const Box* cur, const void* arena, const long
 cudaError_t launch_unpack_state(int G, const Box* cur, const float* packed, const int* packed_idf,
                                 const long long* packed_off, float* X, int* IDF, cudaStream_t s);
 long long large_class_scratch_floats(const Domain& d);
+cudaError_t launch_plain_step_impl(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
+                                   const Box* h_cur, const Box* h_prev, float* t1, float* t2, float* Cc,
+                                   float* Gg, float* Hh, cudaStream_t s);
 }  // namespace lsgg
 
 using namespace lsgg;
@@ -66,6 +69,9 @@ struct lsgg_ctx {
     std::vector<std::vector<cudaEvent_t>> ev_pending;
     double acc_ms[4] = {0, 0, 0, 0};
     long long acc_cnt[4] = {0, 0, 0, 0};
+    // plain (per-grain) comparator buffers
+    float *p_t1 = nullptr, *p_t2 = nullptr, *p_C = nullptr, *p_G = nullptr, *p_H = nullptr;
+    long long p_cap = 0;
 };
 
 namespace {
@@ -681,7 +687,70 @@ int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg) {
     Taps taps = make_taps(dt, c->dom.radius);
     c->phys.dt = (float)dt;
     if (c->cfg.exec == LSGG_EXEC_PLAIN && !dbg) {
-        return LSGG_ERR_UNSUPPORTED;
+        int r;
+        const Domain& D = c->dom;
+        if (!c->p_t1) {
+            long long R2 = 2 * c->dom.radius;
+            long long t = (long long)D.nx * (D.ny + R2) * (D.dim == 3 ? D.nz + R2 : 1);
+            if ((r = dalloc(c, &c->p_t1, (size_t)t)) != LSGG_OK) return r;
+            if ((r = dalloc(c, &c->p_t2, (size_t)t)) != LSGG_OK) return r;
+        }
+        if (c->p_cap != c->B.cap) {
+            dfree(c, c->p_C); dfree(c, c->p_G); dfree(c, c->p_H);
+            if ((r = dalloc(c, &c->p_C, (size_t)c->B.cap)) != LSGG_OK) return r;
+            if ((r = dalloc(c, &c->p_G, (size_t)c->B.cap)) != LSGG_OK) return r;
+            if ((r = dalloc(c, &c->p_H, (size_t)c->B.cap)) != LSGG_OK) return r;
+            c->p_cap = c->B.cap;
+        }
+        std::vector<Box> hc(c->G), hp(c->G);
+        for (long long i = 0; i < n; ++i) {
+            // the host loop over grains needs this step's boxes
+            if (cudaMemcpyAsync(hc.data(), c->B.cur, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(hp.data(), c->B.prev, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(c->h_st, c->B.st, sizeof(StepState), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return LSGG_ERR_CUDA;
+            if (c->h_st->halt) return LSGG_OK;         // arena overflow: lsgg_sync resumes
+            cudaEvent_t* ev = nullptr;
+            if (c->profiling) {
+                std::vector<cudaEvent_t> v(5);
+                for (auto& e : v) {
+                    if (!c->ev_pool.empty()) { e = c->ev_pool.back(); c->ev_pool.pop_back(); }
+                    else if (cudaEventCreate(&e) != cudaSuccess) return LSGG_ERR_CUDA;
+                }
+                c->ev_pending.push_back(v);
+                ev = c->ev_pending.back().data();
+                cudaEventRecord(ev[0], c->stream);
+                cudaEventRecord(ev[1], c->stream);
+            }
+            if (launch_plain_step_impl(c->B, taps, c->phys, hc.data(), hp.data(), c->p_t1, c->p_t2, c->p_C,
+                                       c->p_G, c->p_H, c->stream) != cudaSuccess)
+                return LSGG_ERR_CUDA;
+            if (ev) {
+                cudaEventRecord(ev[2], c->stream);
+                cudaEventRecord(ev[3], c->stream);
+                cudaEventRecord(ev[4], c->stream);
+            }
+        }
+        return LSGG_OK;
+    }
+    if (!dbg && !c->profiling) {
+        // CUDA graph of one step, captured once per dt and replayed n times
+        if (!c->graph || c->graph_dt != dt) {
+            if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LSGG_ERR_CUDA;
+            cudaError_t le = launch_step(c->B, taps, c->phys, nullptr, c->stream, nullptr);
+            cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+            if (le != cudaSuccess || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return LSGG_ERR_CUDA; }
+            cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) { c->graph = nullptr; return LSGG_ERR_CUDA; }
+            c->graph_dt = dt;
+        }
+        for (long long i = 0; i < n; ++i)
+            if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return LSGG_ERR_CUDA;
+        return LSGG_OK;
     }
     for (long long i = 0; i < n; ++i) {
         cudaEvent_t* ev = nullptr;
