@@ -190,6 +190,34 @@ int lsgg_set_state(lsgg_ctx* ctx, const int32_t* boxes, const float* phi, const 
 int lsgg_debug_step(lsgg_ctx* ctx, double dt, float* phip, float* m, int32_t* idm,
                     float* phic, float* phin);
 
+/* -------------------------------------------------- stateless device ops */
+/* A box of the packed layout used by the stateless ops: origin in [0, N) per
+ * axis, dims 1..N per axis (nx <= 0: an unused entry), and the element offset
+ * of the box's first cell in the packed per-cell arrays (x fastest, then y,
+ * then z, no padding). */
+typedef struct lsgg_box {
+    int32_t ox, oy, oz;
+    int32_t nx, ny, nz;
+    int64_t offset;
+} lsgg_box;
+
+/* Corrector, first part (Eq. (16), max over all other grains; Sec. 3.1
+ * ID-field): for every cell c of every box i,
+ *   m[c]  = max over boxes j != i that cover c's domain cell of phip_j there,
+ *           -eps where no other box covers it (outside its box a grain's
+ *           function is -eps),
+ *   id[c] = that j (lowest index on ties), -1 where m[c] == -eps.
+ * The domain is periodic, nx*ny*nz cells.  All array pointers are DEVICE
+ * pointers: boxes_dev (n_boxes entries), phip_dev / m_dev / id_dev (n_elems
+ * entries each, indexed by the boxes' offsets), scratch_dev (16 * nx*ny*nz
+ * bytes, 16-byte aligned, overwritten: the per-cell top-2 field).  Boxes
+ * with an origin or dims out of range, or reaching past n_elems, are skipped
+ * and their outputs left untouched.  Enqueued on `stream` (a cudaStream_t,
+ * NULL = legacy default stream); returns after enqueue. */
+int lsgg_neighbour_max(const lsgg_box* boxes_dev, int32_t n_boxes, const float* phip_dev, int64_t n_elems,
+                       int32_t nx, int32_t ny, int32_t nz, float eps, void* scratch_dev,
+                       float* m_dev, int32_t* id_dev, void* stream);
+
 /* SplitMix64 seed points (host only, no device needed): out[3*i + a] =
  * u01(seed, 3*i + a) * N_a for a = x, y, z with
  * u01(s, k) = (mix(s + (k + 1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53 and

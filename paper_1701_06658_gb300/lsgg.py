@@ -90,6 +90,8 @@ _SIGS = {
     "lsgg_debug_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                   C.POINTER(C.c_int32), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "lsgg_generate_seeds": (C.c_int, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
+    "lsgg_neighbour_max": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
+                                     C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
 }
@@ -192,6 +194,23 @@ def kernel_times(ctx):
     cnt = np.zeros(4, np.int64)
     _check("kernel_times", lib().lsgg_kernel_times(ctx, _ptr(ms, C.c_double), _ptr(cnt, C.c_int64)))
     return dict(zip(KERNEL_GROUPS, ms.tolist())), dict(zip(KERNEL_GROUPS, cnt.tolist()))
+
+
+class Box(C.Structure):
+    """Mirror of ``lsgg_box`` (stateless ops)."""
+    _fields_ = [("ox", C.c_int32), ("oy", C.c_int32), ("oz", C.c_int32),
+                ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("offset", C.c_int64)]
+
+
+BOX_DTYPE = np.dtype([("ox", "<i4"), ("oy", "<i4"), ("oz", "<i4"), ("nx", "<i4"), ("ny", "<i4"),
+                      ("nz", "<i4"), ("offset", "<i8")])
+
+
+def neighbour_max(boxes_dev: int, n_boxes: int, phip_dev: int, n_elems: int, nx: int, ny: int, nz: int,
+                  eps: float, scratch_dev: int, m_dev: int, id_dev: int, stream: int = 0):
+    """lsgg_neighbour_max on device pointers (ints, e.g. torch ``data_ptr()``)."""
+    _check("neighbour_max", lib().lsgg_neighbour_max(boxes_dev, n_boxes, phip_dev, n_elems, nx, ny, nz, eps,
+                                                      scratch_dev, m_dev, id_dev, stream or None))
 
 
 def get_boxes(ctx, n_grains: int) -> np.ndarray:
