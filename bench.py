@@ -33,7 +33,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = {"n": 256, "grains": 5000, "seed": 2, "dt": 1.0}
+WORKLOADS = {
+    "256": {"n": 256, "grains": 5000, "seed": 2, "dt": 1.0},
+    # small case for ncu captures: same grain density, state still larger than L2
+    "160": {"n": 160, "grains": 1221, "seed": 2, "dt": 1.0},
+}
+WORKLOAD = dict(WORKLOADS["256"])
 SAMPLE = {"n": 64, "grains": 78, "seed": 2}     # same density: 64^3 / 78 = 3361 cells per grain
 METRIC = "LS box cell-updates/s"
 UNIT = "cell-updates/s"
@@ -233,19 +238,20 @@ def gpu_arm(args):
     # ---------------- end to end through the public API ----------------
     torch.cuda.synchronize()
     barrier()
-    t0 = time.perf_counter()
-    e2e = L.Microstructure(n, n, n, g, seeds=seeds, device=local)   # H2D of the seeds, init
-    d2h = 0
-    for _ in range(args.steps):
-        e2e.step(1, dt)
-        vol = e2e.grain_volumes()                                      # D2H of the step's result
-        d2h += vol.nbytes
-    own = e2e.voxel_owner()
-    d2h += own.nbytes
-    se = e2e.stats()
-    e2e.close()
-    e2e_s = time.perf_counter() - t0
-    e2e_cells = se.cell_updates
+    e2e_s, e2e_cells, d2h = float("nan"), 0, 0
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        e2e = L.Microstructure(n, n, n, g, seeds=seeds, device=local)   # H2D of the seeds, init
+        for _ in range(args.steps):
+            e2e.step(1, dt)
+            vol = e2e.grain_volumes()                                      # D2H of the step's result
+            d2h += vol.nbytes
+        own = e2e.voxel_owner()
+        d2h += own.nbytes
+        se = e2e.stats()
+        e2e.close()
+        e2e_s = time.perf_counter() - t0
+        e2e_cells = se.cell_updates
 
     # ---------------- reduce over ranks ----------------
     vals = [dev_ms, float(cells), e2e_s, float(e2e_cells)]
@@ -287,7 +293,7 @@ def gpu_arm(args):
                      "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": achieved / peaks.get("hbm_gbs"), "peak_source": src,
                      "algorithmic_bytes_per_launch": alg_bytes, "traffic": traffic},
-        "e2e": {"value": e2e_cells_all / e2e_s, "unit": UNIT,
+        "e2e": None if args.no_e2e else {"value": e2e_cells_all / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * 3 * g / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "seconds": e2e_s, "includes": "create_microstructure from host seeds, steps, per-step volumes "
                                                "to host, final owner map to host"},
@@ -308,7 +314,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
+    ap.add_argument("--workload", default="256", choices=sorted(WORKLOADS),
+                    help="256: the benchmark workload; 160: a small case of the same density for profilers")
     args = ap.parse_args()
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[args.workload])
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
