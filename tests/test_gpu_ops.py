@@ -87,14 +87,13 @@ def test_neighbour_max_skips_invalid_boxes(env):
     torch, L = env
     shape = (10, 10, 10)
     boxes, phip = neighbour_max_case(4, shape, 5)
+    spans = [(int(b["offset"]), int(b["nx"] * b["ny"] * b["nz"])) for b in boxes]
     boxes[2]["offset"] = phip.size        # reaches past n_elems
     boxes[3]["nx"] = 11                   # wider than the domain
     m, idm = run_neighbour_max(torch, L, boxes, phip, shape)
-    for k in (2, 3):
-        b = boxes[k]
-        o = int(b["offset"])
-        n = int(abs(b["nx"]) * b["ny"] * b["nz"])
-        if o < phip.size:
-            assert np.all(m[o:o + min(n, phip.size - o)] == 123.0)
-    b = boxes[0]
-    assert np.all(m[:b["nx"] * b["ny"] * b["nz"]] != 123.0)
+    for k in (2, 3):                      # skipped: their original cells keep the fill value
+        o, n = spans[k]
+        assert np.all(m[o:o + n] == 123.0) and np.all(idm[o:o + n] == -99)
+    for k in (0, 1, 4):
+        o, n = spans[k]
+        assert np.all(m[o:o + n] != 123.0)
