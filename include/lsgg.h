@@ -43,7 +43,7 @@ extern "C" {
 #define LSGG_ERR_CUDA          -4   /* a CUDA runtime call failed (no device, launch error) */
 #define LSGG_ERR_TIMEOUT       -5   /* a bounded wait expired (device queue or host wait) */
 #define LSGG_ERR_NOT_READY     -6   /* a served request has not finished yet */
-#define LSGG_ERR_CAPACITY      -7   /* a caller buffer is too small (see *n_out) */
+#define LSGG_ERR_CAPACITY      -7   /* a caller buffer (see *n_out) or a fixed library buffer is too small */
 #define LSGG_ERR_UNSUPPORTED   -8   /* a requested variant is not built */
 
 /* ---------------------------------------------------------------- config */
@@ -217,6 +217,32 @@ typedef struct lsgg_box {
 int lsgg_neighbour_max(const lsgg_box* boxes_dev, int32_t n_boxes, const float* phip_dev, int64_t n_elems,
                        int32_t nx, int32_t ny, int32_t nz, float eps, void* scratch_dev,
                        float* m_dev, int32_t* id_dev, void* stream);
+
+/* Largest domain (nx*ny*nz cells) lsgg_neighbour_max_noalloc accepts: its
+ * top-2 field is a fixed 16 * 2^20 bytes = 16 MiB of static device memory. */
+#define LSGG_NOALLOC_MAX_CELLS (1 << 20)
+
+/* lsgg_neighbour_max for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is an interface for hosts that own all
+ * device memory themselves (a server that hands its whole budget to its own
+ * pool, a plug-in inside a framework that exposes no allocator) or that keep
+ * cudaMalloc / cudaFree out of latency-critical loops (cudaFree synchronises
+ * the device, cudaMalloc can wait on other work).  Same arguments, result
+ * and rules as lsgg_neighbour_max, without scratch_dev: the scratch field is
+ * a file-scope static device array of LSGG_NOALLOC_MAX_CELLS cells that
+ * every GPU on which the library's ops module is loaded keeps until the
+ * process exits.  The call allocates nothing (no cudaMalloc, no cudaFree,
+ * no allocating library routine).  Domains above LSGG_NOALLOC_MAX_CELLS
+ * cells return LSGG_ERR_CAPACITY without touching the device.  The first
+ * call on a device looks up the array's device address on the current
+ * device (cudaGetSymbolAddress) and caches it: make that first call before
+ * any stream capture.  Every call shares the one array and leaves the last
+ * call's field in it (each call clears it first), so calls whose work
+ * overlaps on the GPU (different streams, different host threads) race and
+ * must be ordered by the caller. */
+int lsgg_neighbour_max_noalloc(const lsgg_box* boxes_dev, int32_t n_boxes, const float* phip_dev,
+                               int64_t n_elems, int32_t nx, int32_t ny, int32_t nz, float eps,
+                               float* m_dev, int32_t* id_dev, void* stream);
 
 /* SplitMix64 seed points (host only, no device needed): out[3*i + a] =
  * u01(seed, 3*i + a) * N_a for a = x, y, z with

@@ -4,6 +4,10 @@
 //                        ID-field of Sec. 3.1 for a packed set of boxes, through
 //                        the per-cell top-2 field (two 64-bit atomicMax of
 //                        (value, -index) keys per box cell), in caller scratch.
+//   lsgg_neighbour_max_noalloc  the same kernels with the field in a static
+//                        device array, for callers that cannot allocate.
+#include <mutex>
+
 #include "lsgg_internal.cuh"
 #include "../../include/lsgg.h"
 
@@ -88,5 +92,50 @@ extern "C" int lsgg_neighbour_max(const lsgg_box* boxes_dev, int32_t n_boxes, co
     if (n_boxes == 0) return LSGG_OK;
     return lsgg::neighbour_max_into(boxes_dev, n_boxes, phip_dev, n_elems, nx, ny, nz, eps,
                                     static_cast<unsigned long long*>(scratch_dev), m_dev, id_dev,
+                                    (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// no-allocation variant: the top-2 field lives in static device memory
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// 2 x u64 per cell: the neighbour-max field of at most LSGG_NOALLOC_MAX_CELLS cells.
+static __device__ __align__(256) unsigned long long g_noalloc_field[2 * (size_t)LSGG_NOALLOC_MAX_CELLS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_field on the current device, looked up once per
+// device.  The host-side name is only a stand-in for the device array.
+int noalloc_field(unsigned long long** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return LSGG_ERR_CUDA; }
+    if (dev < 0 || dev >= kMaxDevices) return LSGG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_field);
+        if (e != cudaSuccess || !p) { cudaGetLastError(); return LSGG_ERR_CUDA; }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned long long*>(g_noalloc_addr[dev]);
+    return LSGG_OK;
+}
+
+}  // namespace
+
+extern "C" int lsgg_neighbour_max_noalloc(const lsgg_box* boxes_dev, int32_t n_boxes, const float* phip_dev,
+                                          int64_t n_elems, int32_t nx, int32_t ny, int32_t nz, float eps,
+                                          float* m_dev, int32_t* id_dev, void* stream) {
+    int r = lsgg::neighbour_max_check(boxes_dev, n_boxes, phip_dev, n_elems, nx, ny, nz, eps, m_dev, id_dev);
+    if (r != LSGG_OK) return r;
+    if ((long long)nx * ny * nz > (long long)LSGG_NOALLOC_MAX_CELLS) return LSGG_ERR_CAPACITY;
+    if (n_boxes == 0) return LSGG_OK;
+    unsigned long long* field = nullptr;
+    if ((r = noalloc_field(&field)) != LSGG_OK) return r;
+    return lsgg::neighbour_max_into(boxes_dev, n_boxes, phip_dev, n_elems, nx, ny, nz, eps, field, m_dev, id_dev,
                                     (cudaStream_t)stream);
 }

@@ -92,6 +92,8 @@ _SIGS = {
     "lsgg_generate_seeds": (C.c_int, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
     "lsgg_neighbour_max": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
                                      C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lsgg_neighbour_max_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
+                                             C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
 }
@@ -211,6 +213,17 @@ def neighbour_max(boxes_dev: int, n_boxes: int, phip_dev: int, n_elems: int, nx:
     """lsgg_neighbour_max on device pointers (ints, e.g. torch ``data_ptr()``)."""
     _check("neighbour_max", lib().lsgg_neighbour_max(boxes_dev, n_boxes, phip_dev, n_elems, nx, ny, nz, eps,
                                                       scratch_dev, m_dev, id_dev, stream or None))
+
+
+NOALLOC_MAX_CELLS = 1 << 20
+
+
+def neighbour_max_noalloc(boxes_dev: int, n_boxes: int, phip_dev: int, n_elems: int, nx: int, ny: int, nz: int,
+                          eps: float, m_dev: int, id_dev: int, stream: int = 0):
+    """lsgg_neighbour_max_noalloc: the same op without caller scratch and without
+    any device allocation (its field is a static array of NOALLOC_MAX_CELLS cells)."""
+    _check("neighbour_max_noalloc", lib().lsgg_neighbour_max_noalloc(boxes_dev, n_boxes, phip_dev, n_elems, nx, ny,
+                                                                      nz, eps, m_dev, id_dev, stream or None))
 
 
 def get_boxes(ctx, n_grains: int) -> np.ndarray:
