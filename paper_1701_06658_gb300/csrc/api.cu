@@ -380,6 +380,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if ((r = dalloc(c, &c->d_seeds, seeds.size())) != LSGG_OK) return bail(r);
     if (!weights.empty() && (r = dalloc(c, &c->d_weights, weights.size())) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->d_boxes, 2 * (size_t)G)) != LSGG_OK) return bail(r);
+    if (cudaMemset(c->d_boxes, 0, 2 * (size_t)G * sizeof(Box)) != cudaSuccess) return bail(LSGG_ERR_CUDA);
     if ((r = dalloc(c, &c->B.bounds, (size_t)G)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.st, 1)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.worklist, (size_t)kNumClasses * G)) != LSGG_OK) return bail(r);
@@ -421,8 +422,13 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if ((r = dalloc(c, &c->B.Y, (size_t)cap)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.IDF, (size_t)cap)) != LSGG_OK) return bail(r);
     c->B.scratch_per_cta = large_class_scratch_floats(D);
-    if ((r = dalloc(c, &c->B.scratch, (size_t)c->B.scratch_per_cta * c->B.grid[0][kNumClasses - 1])) != LSGG_OK)
-        return bail(r);
+    {
+        int ctas = 0;
+        for (int k = 0; k < kNumClasses; ++k)
+            if (c->B.mode[k] == 2) ctas = std::max(ctas, std::max(c->B.grid[0][k], c->B.grid[1][k]));
+        if ((r = dalloc(c, &c->B.scratch, (size_t)c->B.scratch_per_cta * std::max(ctas, 1))) != LSGG_OK)
+            return bail(r);
+    }
     if ((r = relayout(c)) != LSGG_OK) return bail(r);
     if (launch_sdf(D, G, c->B.cur, c->d_seeds, c->d_weights, d_bits, wpr, c->B.X,
                    c->B.IDF, &c->B.st->status, c->stream) != cudaSuccess)

@@ -60,4 +60,20 @@ __device__ __forceinline__ void opp_delta(float a, bool pos, float nbv, float& d
     }
 }
 
+// Pull the next box of class `cls` for kernel `which`; -1 when the queue is empty.
+__device__ __forceinline__ int pull_box(const StepBuffers& B, int which, int cls, int* s_box) {
+    if (threadIdx.x == 0) {
+        int b = -1;
+        if (!*(volatile int*)&B.st->halt) {
+            int w = atomicAdd(&B.st->queue[which][cls], 1);
+            if (w < B.st->class_count[cls]) b = B.worklist[cls * B.n_boxes + w];
+        }
+        *s_box = b;
+    }
+    __syncthreads();
+    int b = *s_box;
+    __syncthreads();
+    return b;
+}
+
 }  // namespace lsgg

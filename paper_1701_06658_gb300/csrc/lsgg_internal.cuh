@@ -20,7 +20,7 @@ namespace lsgg {
 
 constexpr int kMaxRadius = 7;
 constexpr int kMaxTaps = 2 * kMaxRadius + 1;
-constexpr int kNumClasses = 4;          // box side <= 32, 48, ~64, larger (global scratch)
+constexpr int kNumClasses = 5;          // box side <= 32, 40, 48, 64, larger (global scratch)
 constexpr int kRedistReach = 6;         // taxicab steps below eps = 7 (exact fixed point)
 
 struct Box {
@@ -126,6 +126,8 @@ struct StepBuffers {
     long long scratch_per_cta;
     int n_sm;
     int class_side[kNumClasses];    // largest box side per class (last: whole domain)
+    int mode[kNumClasses];          // 0: register-ring kernels, 1: shared-memory ring, 2: global scratch ring
+    int block[kNumClasses];         // threads per CTA
     int grid[2][kNumClasses];       // persistent grid per kernel and class
     size_t smem[2][kNumClasses];
 };

@@ -31,22 +31,6 @@ namespace lsgg {
 constexpr int kThreads = 256;
 constexpr int kBoxUpdateThreads = 1024;
 
-// Pull the next box of class `cls` for kernel `which`; -1 when the queue is empty.
-__device__ __forceinline__ int pull_box(const StepBuffers& B, int which, int cls, int* s_box) {
-    if (threadIdx.x == 0) {
-        int b = -1;
-        if (!*(volatile int*)&B.st->halt) {
-            int w = atomicAdd(&B.st->queue[which][cls], 1);
-            if (w < B.st->class_count[cls]) b = B.worklist[cls * B.n_boxes + w];
-        }
-        *s_box = b;
-    }
-    __syncthreads();
-    int b = *s_box;
-    __syncthreads();
-    return b;
-}
-
 // ---------------------------------------------------------------------------
 // predictor + neighbour-max scatter
 // ---------------------------------------------------------------------------
@@ -201,7 +185,7 @@ k_predict(StepBuffers B, Taps taps, PhysicsDev phys, int cls) {
     sm.gy = sm.gx + side;
     float* buf = reinterpret_cast<float*>(sm.gy + side + 4);
     buf = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(buf) + 15) & ~uintptr_t(15));
-    if (cls == kNumClasses - 1) buf = B.scratch + (long long)blockIdx.x * B.scratch_per_cta;
+    if (B.mode[cls] == 2) buf = B.scratch + (long long)blockIdx.x * B.scratch_per_cta;
     for (;;) {
         int b = pull_box(B, 0, cls, &s_box);
         if (b < 0) break;
@@ -412,7 +396,7 @@ k_correct(StepBuffers B, PhysicsDev phys, DebugOut dbg, int cls) {
     int* gy = gx + side;
     float* buf = reinterpret_cast<float*>(gy + side + 4);
     buf = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(buf) + 15) & ~uintptr_t(15));
-    if (cls == kNumClasses - 1) buf = B.scratch + (long long)blockIdx.x * B.scratch_per_cta;
+    if (B.mode[cls] == 2) buf = B.scratch + (long long)blockIdx.x * B.scratch_per_cta;
     for (;;) {
         int b = pull_box(B, 1, cls, &s_box);
         if (b < 0) break;
@@ -424,8 +408,10 @@ k_correct(StepBuffers B, PhysicsDev phys, DebugOut dbg, int cls) {
 // box update (single CTA)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int box_class(const StepBuffers& B, const Box& b) {
-    int s = max(b.nx, b.ny);
+// Size class of a box: the smallest class whose side holds the x and y extents
+// of both its new layout and the layout its state is read from.
+__device__ __forceinline__ int box_class(const StepBuffers& B, const Box& b, const Box& p) {
+    int s = max(max(b.nx, b.ny), max(p.nx, p.ny));
     for (int c = 0; c < kNumClasses - 1; ++c)
         if (s <= B.class_side[c]) return c;
     return kNumClasses - 1;
@@ -508,7 +494,7 @@ k_box_update(StepBuffers B, int layout_only) {
         off += box_elems(cb);
         B.cur[b] = cb;
         if (cb.nx > 0) {
-            int c = box_class(B, cb);
+            int c = box_class(B, cb, B.prev[b]);
             int w = atomicAdd(&s_cnt[c], 1);
             B.worklist[c * G + w] = b;
             cells += (long long)cb.nx * cb.ny * cb.nz;
@@ -548,6 +534,11 @@ static size_t correct_smem_bytes(int side) {
     return ((size_t)2 * side + 4) * 4 + 16 + (size_t)12 * side * side * 4;
 }
 
+int fast_class_side(int cls);
+cudaError_t configure_fast(StepBuffers& B, int cls, int n_sm);
+cudaError_t launch_fast(const StepBuffers& B, int which, int cls, const Taps& taps, const PhysicsDev& phys,
+                        const DebugOut& dbg, cudaStream_t s);
+
 cudaError_t configure_step_kernels(StepBuffers& B) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -559,46 +550,57 @@ cudaError_t configure_step_kernels(StepBuffers& B) {
     const int R = B.dom.radius;
     int big = B.dom.nx > B.dom.ny ? B.dom.nx : B.dom.ny;
     if (B.dom.nz > big) big = B.dom.nz;
-    // class sides 32, 48 and the largest side <= 64 whose buffers fit shared memory
-    int want[kNumClasses - 1] = {32, 48, 64};
-    for (int c = 0; c < kNumClasses - 1; ++c) {
-        int side = want[c];
-        while (side > 8 && ((int)predict_smem_bytes(side, R) > max_optin || (int)correct_smem_bytes(side) > max_optin))
-            side -= 4;
-        B.class_side[c] = side;
-    }
+    const bool fast_ok = B.dom.dim == 3 && R == 5;
+    const int sides[kNumClasses - 1] = {32, 40, 48, 64};
+    for (int c = 0; c < kNumClasses - 1; ++c) B.class_side[c] = sides[c];
     B.class_side[kNumClasses - 1] = big;
+    // register-ring kernels for the small classes, shared-memory rings where they fit, global otherwise
     size_t mp = 0, mc = 0;
     for (int c = 0; c < kNumClasses; ++c) {
-        size_t sp, sc;
-        if (c < kNumClasses - 1) {
+        B.block[c] = kThreads;
+        if (fast_ok && fast_class_side(c) == B.class_side[c]) {
+            e = configure_fast(B, c, n_sm);
+            if (e != cudaSuccess) return e;
+            B.mode[c] = 0;
+            continue;
+        }
+        size_t sp = 0, sc = 0;
+        bool fits = c < kNumClasses - 1 && (int)predict_smem_bytes(B.class_side[c], R) <= max_optin &&
+                    (int)correct_smem_bytes(B.class_side[c]) <= max_optin;
+        if (fits) {
+            B.mode[c] = 1;
             sp = predict_smem_bytes(B.class_side[c], R);
             sc = correct_smem_bytes(B.class_side[c]);
         } else {
-            sp = (size_t)(2 * (big + 2 * kMaxRadius) + 2 * big + 4) * 4 + 16;
-            sc = ((size_t)2 * big + 4) * 4 + 16;
+            B.mode[c] = 2;
+            int side = c < kNumClasses - 1 ? B.class_side[c] : big;
+            sp = (size_t)(2 * (side + 2 * kMaxRadius) + 2 * side + 4) * 4 + 16;
+            sc = ((size_t)2 * side + 4) * 4 + 16;
         }
         B.smem[0][c] = sp;
         B.smem[1][c] = sc;
         if (sp > mp) mp = sp;
         if (sc > mc) mc = sc;
     }
-    e = cudaFuncSetAttribute(k_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_correct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mc);
-    if (e != cudaSuccess) return e;
+    if (mp > 0) {
+        e = cudaFuncSetAttribute(k_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp);
+        if (e != cudaSuccess) return e;
+    }
+    if (mc > 0) {
+        e = cudaFuncSetAttribute(k_correct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mc);
+        if (e != cudaSuccess) return e;
+    }
     for (int c = 0; c < kNumClasses; ++c) {
+        if (B.mode[c] == 0) continue;
+        if (B.mode[c] == 2) {
+            B.grid[0][c] = B.grid[1][c] = (n_sm + 3) / 4;
+            continue;
+        }
         int occ_p = 0, occ_c = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, k_predict, kThreads, B.smem[0][c]);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k_correct, kThreads, B.smem[1][c]);
-        if (occ_p < 1) occ_p = 1;
-        if (occ_c < 1) occ_c = 1;
-        if (c < kNumClasses - 1) {
-            B.grid[0][c] = n_sm * occ_p;
-            B.grid[1][c] = n_sm * occ_c;
-        } else {
-            B.grid[0][c] = B.grid[1][c] = (n_sm + 3) / 4;
-        }
+        B.grid[0][c] = n_sm * (occ_p < 1 ? 1 : occ_p);
+        B.grid[1][c] = n_sm * (occ_c < 1 ? 1 : occ_c);
     }
     return cudaSuccess;
 }
@@ -625,18 +627,20 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
     cudaError_t e = cudaMemsetAsync(B.T, 0, (size_t)ncell * 16, s);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    for (int c = 0; c < kNumClasses; ++c) {
-        k_predict<<<B.grid[0][c], kThreads, B.smem[0][c], s>>>(B, taps, phys, c);
-    }
-    if (ev) cudaEventRecord(ev[2], s);
     DebugOut d{};
     if (dbg) d = *dbg;
     for (int c = 0; c < kNumClasses; ++c) {
-        k_correct<<<B.grid[1][c], kThreads, B.smem[1][c], s>>>(B, phys, d, c);
+        if (B.mode[c] == 0) e = launch_fast(B, 0, c, taps, phys, d, s);
+        else { k_predict<<<B.grid[0][c], kThreads, B.smem[0][c], s>>>(B, taps, phys, c); e = cudaGetLastError(); }
+        if (e != cudaSuccess) return e;
+    }
+    if (ev) cudaEventRecord(ev[2], s);
+    for (int c = 0; c < kNumClasses; ++c) {
+        if (B.mode[c] == 0) e = launch_fast(B, 1, c, taps, phys, d, s);
+        else { k_correct<<<B.grid[1][c], kThreads, B.smem[1][c], s>>>(B, phys, d, c); e = cudaGetLastError(); }
+        if (e != cudaSuccess) return e;
     }
     if (ev) cudaEventRecord(ev[3], s);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     e = launch_box_update(B, false, s);
     if (ev) cudaEventRecord(ev[4], s);
     return e;
