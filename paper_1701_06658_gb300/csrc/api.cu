@@ -52,6 +52,9 @@ struct lsgg_ctx {
     double* d_seeds = nullptr;
     double* d_weights = nullptr;
     float* d_energy = nullptr;
+    double* d_quats = nullptr;
+    int* d_nb_tab = nullptr;
+    int* d_nb_cnt = nullptr;
     double* d_vol = nullptr;
     long long* d_packed_off = nullptr;
     StepState* h_st = nullptr;       // pinned mirror for status reads
@@ -69,6 +72,8 @@ struct lsgg_ctx {
     std::vector<std::vector<cudaEvent_t>> ev_pending;
     double acc_ms[4] = {0, 0, 0, 0};
     long long acc_cnt[4] = {0, 0, 0, 0};
+    StepStreams ss{};
+    bool have_ss = false;
     // plain (per-grain) comparator buffers
     float *p_t1 = nullptr, *p_t2 = nullptr, *p_C = nullptr, *p_G = nullptr, *p_H = nullptr;
     long long p_cap = 0;
@@ -256,6 +261,13 @@ int lsgg_destroy(lsgg_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->have_ss) {
+        for (int k = 0; k < kNumClasses; ++k) {
+            cudaStreamDestroy(c->ss.side[k]);
+            cudaEventDestroy(c->ss.join[k]);
+        }
+        cudaEventDestroy(c->ss.fork);
+    }
     for (auto& v : c->ev_pending)
         for (cudaEvent_t e : v) c->ev_pool.push_back(e);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -286,7 +298,10 @@ static int validate(const lsgg_config* cfg) {
     if (cfg->storage != LSGG_STORAGE_FP32 && cfg->storage != LSGG_STORAGE_BF16) return LSGG_ERR_INVALID_ARG;
     if (cfg->storage == LSGG_STORAGE_BF16) return LSGG_ERR_UNSUPPORTED;
     if (cfg->exec != LSGG_EXEC_BATCHED && cfg->exec != LSGG_EXEC_PLAIN) return LSGG_ERR_INVALID_ARG;
-    if (cfg->physics == LSGG_PHYSICS_READ_SHOCKLEY) return LSGG_ERR_UNSUPPORTED;
+    if (cfg->physics == LSGG_PHYSICS_READ_SHOCKLEY &&
+        (!(cfg->theta_max_deg > 0.0) || !(cfg->mob_low > 0.0) ||
+         (cfg->mobility_law != LSGG_MOBILITY_STEP && cfg->mobility_law != LSGG_MOBILITY_EQ20)))
+        return LSGG_ERR_INVALID_ARG;
     if (!(cfg->arena_slack >= 1.0)) return LSGG_ERR_INVALID_ARG;
     // taxicab reach is fixed to the default band: eps = 7 gives 6 exact steps
     if (std::fabs(cfg->eps - 7.0f) > 1e-6f) return LSGG_ERR_UNSUPPORTED;
@@ -346,6 +361,22 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
             for (int i = 0; i < G; ++i) { double rr = rad[i] * 0.5 * spacing / mean; weights[i] = rr * rr; }
         }
     }
+    std::vector<double> quats;
+    if (cfg_in->physics != LSGG_PHYSICS_IDEAL) {
+        // unit quaternions: given, or Shoemake's method on SplitMix64 stream 3 (as the inputs module)
+        quats.resize(4 * (size_t)G);
+        for (int i = 0; i < G; ++i) {
+            double* q = quats.data() + 4 * (size_t)i;
+            if (cfg_in->quats) std::memcpy(q, cfg_in->quats + 4 * (size_t)i, 32);
+            else {
+                double a = u01(cfg_in->seed, 3, 3 * (uint64_t)i), b = u01(cfg_in->seed, 3, 3 * (uint64_t)i + 1),
+                       cc = u01(cfg_in->seed, 3, 3 * (uint64_t)i + 2);
+                double s1 = std::sqrt(1 - a), s2 = std::sqrt(a);
+                q[0] = s2 * std::cos(2 * M_PI * cc); q[1] = s1 * std::sin(2 * M_PI * b);
+                q[2] = s1 * std::cos(2 * M_PI * b); q[3] = s2 * std::sin(2 * M_PI * cc);
+            }
+        }
+    }
     if (cfg_in->physics == LSGG_PHYSICS_MAGNETIC) {
         energy.resize(G);
         if (cfg_in->energy) std::memcpy(energy.data(), cfg_in->energy, (size_t)G * 8);
@@ -354,15 +385,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
             double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
             if (!(fn > 0)) return bail(LSGG_ERR_INVALID_ARG);
             for (int i = 0; i < G; ++i) {
-                double q[4];
-                if (cfg_in->quats) std::memcpy(q, cfg_in->quats + 4 * (size_t)i, 32);
-                else {
-                    double a = u01(cfg_in->seed, 3, 3 * (uint64_t)i), b = u01(cfg_in->seed, 3, 3 * (uint64_t)i + 1),
-                           cc = u01(cfg_in->seed, 3, 3 * (uint64_t)i + 2);
-                    double s1 = std::sqrt(1 - a), s2 = std::sqrt(a);
-                    q[0] = s2 * std::cos(2 * M_PI * cc); q[1] = s1 * std::sin(2 * M_PI * b);
-                    q[2] = s1 * std::cos(2 * M_PI * b); q[3] = s2 * std::sin(2 * M_PI * cc);
-                }
+                const double* q = quats.data() + 4 * (size_t)i;
                 double ax = 2 * (q[1] * q[3] + q[0] * q[2]), ay = 2 * (q[2] * q[3] - q[0] * q[1]),
                        az = 1 - 2 * (q[1] * q[1] + q[2] * q[2]);
                 double cs = (ax * f[0] + ay * f[1] + az * f[2]) / fn;
@@ -395,6 +418,14 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
         if ((r = dalloc(c, &c->d_energy, (size_t)G)) != LSGG_OK) return bail(r);
         if (cudaMemcpy(c->d_energy, ef.data(), ef.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return bail(LSGG_ERR_CUDA);
     }
+    if (cfg_in->physics == LSGG_PHYSICS_READ_SHOCKLEY) {
+        if ((r = dalloc(c, &c->d_quats, quats.size())) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &c->d_nb_tab, (size_t)G * kNbCap)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &c->d_nb_cnt, (size_t)G)) != LSGG_OK) return bail(r);
+        if (cudaMemcpy(c->d_quats, quats.data(), quats.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(c->d_nb_cnt, 0, (size_t)G * 4) != cudaSuccess)
+            return bail(LSGG_ERR_CUDA);
+    }
     if (cudaMemcpy(c->d_seeds, seeds.data(), seeds.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) return bail(LSGG_ERR_CUDA);
     if (!weights.empty() && cudaMemcpy(c->d_weights, weights.data(), weights.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(LSGG_ERR_CUDA);
@@ -405,6 +436,14 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->B.prev = c->d_boxes;
     c->B.cur = c->d_boxes + G;
     if (configure_step_kernels(c->B) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+    {
+        bool ok = cudaEventCreateWithFlags(&c->ss.fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; k < kNumClasses && ok; ++k)
+            ok = cudaStreamCreateWithFlags(&c->ss.side[k], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->ss.join[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return bail(LSGG_ERR_CUDA);
+        c->have_ss = true;
+    }
 
     if (launch_init(D, G, c->d_seeds, c->d_weights, d_labels, d_bits, wpr, d_bb, c->B.cur, c->stream) != cudaSuccess)
         return bail(LSGG_ERR_CUDA);
@@ -423,11 +462,13 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if ((r = dalloc(c, &c->B.IDF, (size_t)cap)) != LSGG_OK) return bail(r);
     c->B.scratch_per_cta = large_class_scratch_floats(D);
     {
-        int ctas = 0;
-        for (int k = 0; k < kNumClasses; ++k)
-            if (c->B.mode[k] == 2) ctas = std::max(ctas, std::max(c->B.grid[0][k], c->B.grid[1][k]));
-        if ((r = dalloc(c, &c->B.scratch, (size_t)c->B.scratch_per_cta * std::max(ctas, 1))) != LSGG_OK)
-            return bail(r);
+        long long total = 0;
+        for (int k = 0; k < kNumClasses; ++k) {
+            c->B.scratch_class_off[k] = total;
+            if (c->B.mode[k] == 2)
+                total += c->B.scratch_per_cta * std::max(c->B.grid[0][k], c->B.grid[1][k]);
+        }
+        if ((r = dalloc(c, &c->B.scratch, (size_t)std::max(total, 32LL))) != LSGG_OK) return bail(r);
     }
     if ((r = relayout(c)) != LSGG_OK) return bail(r);
     if (launch_sdf(D, G, c->B.cur, c->d_seeds, c->d_weights, d_bits, wpr, c->B.X,
@@ -443,6 +484,12 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->device_bytes -= (long long)ncell * 4 + (long long)G * wpr * 4 + 6LL * G * 4;
     c->phys.kind = cfg_in->physics;
     c->phys.energy = c->d_energy;
+    c->phys.quats = c->d_quats;
+    c->phys.nb_tab = c->d_nb_tab;
+    c->phys.nb_cnt = c->d_nb_cnt;
+    c->phys.theta_max = cfg_in->theta_max_deg * M_PI / 180.0;
+    c->phys.mob_low = cfg_in->mob_low;
+    c->phys.mob_law = cfg_in->mobility_law;
     *out = c;
     return LSGG_OK;
 }
@@ -746,7 +793,7 @@ int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg) {
             if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
             cudaGraph_t g = nullptr;
             if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LSGG_ERR_CUDA;
-            cudaError_t le = launch_step(c->B, taps, c->phys, nullptr, c->stream, nullptr);
+            cudaError_t le = launch_step(c->B, taps, c->phys, nullptr, c->stream, nullptr, &c->ss);
             cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
             if (le != cudaSuccess || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return LSGG_ERR_CUDA; }
             cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
@@ -769,7 +816,7 @@ int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg) {
             c->ev_pending.push_back(v);
             ev = c->ev_pending.back().data();
         }
-        if (launch_step(c->B, taps, c->phys, dbg, c->stream, ev) != cudaSuccess) return LSGG_ERR_CUDA;
+        if (launch_step(c->B, taps, c->phys, dbg, c->stream, ev, &c->ss) != cudaSuccess) return LSGG_ERR_CUDA;
     }
     return LSGG_OK;
 }

@@ -9,22 +9,93 @@ namespace lsgg {
 
 __device__ __forceinline__ bool sgn_pos(float v) { return !(__float_as_uint(v) >> 31); }
 
-__device__ __forceinline__ float pair_blend(const PhysicsDev& phys, int gid, int j, float phi, float c) {
-    // Eq. (10): phi + w (c - phi) + M (e_j - e_i) dt; w = 1, no bulk when j < 0.
+// Disorientation angle (radians) of two cubic crystals: with q = conj(qa) qb
+// and |q| components sorted c0 >= c1 >= c2 >= c3, the largest |w| over the 24
+// proper rotations of the cube applied to q is max(c0, (c0 + c1)/sqrt 2,
+// (c0 + c1 + c2 + c3)/2) (identity and half turns about the axes; quarter
+// turns and half turns about face diagonals; third turns about body
+// diagonals); the angle is 2 acos of it.
+__device__ __forceinline__ double cubic_disorientation(const double* qa, const double* qb) {
+    const double aw = qa[0], ax = -qa[1], ay = -qa[2], az = -qa[3];
+    const double bw = qb[0], bx = qb[1], by = qb[2], bz = qb[3];
+    double c0 = fabs(aw * bw - ax * bx - ay * by - az * bz);
+    double c1 = fabs(aw * bx + ax * bw + ay * bz - az * by);
+    double c2 = fabs(aw * by - ax * bz + ay * bw + az * bx);
+    double c3 = fabs(aw * bz + ax * by - ay * bx + az * bw);
+    double t;
+    if (c0 < c1) { t = c0; c0 = c1; c1 = t; }
+    if (c2 < c3) { t = c2; c2 = c3; c3 = t; }
+    if (c0 < c2) { t = c0; c0 = c2; c2 = t; }
+    if (c1 < c3) { t = c1; c1 = c3; c3 = t; }
+    if (c1 < c2) { t = c1; c1 = c2; c2 = t; }
+    double m = fmax(c0, fmax((c0 + c1) * 0.70710678118654752440, 0.5 * (c0 + c1 + c2 + c3)));
+    return 2.0 * acos(fmin(1.0, m));
+}
+
+// Read-Shockley pair weight of Eq. (10) (Sec. 4.3): w = max(1e-3, M* gamma*)
+// with gamma* = t (1 - ln t), t = theta / theta_max below theta_max, 1 above;
+// M* = mob_low below theta_max (step law) or Eq. (20).
+__device__ __forceinline__ void rs_pair(const PhysicsDev& phys, int i, int j, float& w, float& m) {
+    const double th = cubic_disorientation(phys.quats + 4 * (size_t)i, phys.quats + 4 * (size_t)j);
+    double g;
+    if (th >= phys.theta_max) g = 1.0;
+    else if (th <= 0.0) g = 0.0;
+    else { const double t = th / phys.theta_max; g = t * (1.0 - log(t)); }
+    double mob;
+    if (phys.mob_law == LSGG_MOBILITY_STEP) mob = th < phys.theta_max ? phys.mob_low : 1.0;
+    else mob = 1.0 - 0.99 * exp(-5.0 * pow(th / (15.0 * 0.017453292519943295), 9.0));
+    const double ww = mob * g;
+    w = (float)(ww > 1e-3 ? ww : 1e-3);
+    m = (float)mob;
+}
+
+// Pair weights of one box, looked up from a shared-memory copy of its
+// neighbour table (tj ascending, n entries); computed directly on a miss.
+struct PairTable {
+    const int* tj;
+    const float* tw;
+    const float* tm;
+    int n;
+};
+
+// Eq. (10): phi + w (c - phi) + M (e_j - e_i) dt; w = 1, no bulk term when j < 0.
+__device__ __forceinline__ float pair_blend(const PhysicsDev& phys, const PairTable& tab, int gid, int j, float phi,
+                                            float c) {
     if (j < 0) return c;
     float w = 1.0f, m = 1.0f;
     if (phys.kind == LSGG_PHYSICS_READ_SHOCKLEY) {
-        int lo = phys.nb_start[gid], hi = phys.nb_start[gid + 1] - 1;
+        int lo = 0, hi = tab.n - 1;
+        bool hit = false;
         while (lo <= hi) {
-            int mid = (lo + hi) >> 1;
-            int jj = phys.nb[mid].j;
-            if (jj == j) { w = phys.nb[mid].w; m = phys.nb[mid].m; break; }
+            const int mid = (lo + hi) >> 1;
+            const int jj = tab.tj[mid];
+            if (jj == j) { w = tab.tw[mid]; m = tab.tm[mid]; hit = true; break; }
             if (jj < j) lo = mid + 1; else hi = mid - 1;
         }
+        if (!hit) rs_pair(phys, gid, j, w, m);
     }
     float bulk = 0.0f;
     if (phys.energy) bulk = m * (phys.energy[j] - phys.energy[gid]) * phys.dt;
     return phi + w * (c - phi) + bulk;
+}
+
+// Load box `gid`'s neighbour table into shared memory and evaluate its pair
+// weights (all threads of the CTA; caller synchronises afterwards).
+__device__ __forceinline__ PairTable load_pair_table(const PhysicsDev& phys, int gid, int* tj, float* tw, float* tm) {
+    PairTable t{tj, tw, tm, 0};
+    if (phys.kind != LSGG_PHYSICS_READ_SHOCKLEY) return t;
+    int n = phys.nb_cnt[gid];
+    if (n > kNbCap) n = kNbCap;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int j = phys.nb_tab[(size_t)gid * kNbCap + k];
+        float w, m;
+        rs_pair(phys, gid, j, w, m);
+        tj[k] = j;
+        tw[k] = w;
+        tm[k] = m;
+    }
+    t.n = n;
+    return t;
 }
 
 // Along one line of n cells (stride `stride` in `in`), the sign-blocked

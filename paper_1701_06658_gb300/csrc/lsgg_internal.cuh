@@ -54,11 +54,17 @@ struct PairEntry {        // neighbour j of grain i: weight w_ij and mobility M_
     float m;
 };
 
+constexpr int kNbCap = 96;          // neighbour-table entries per grain
+
 struct PhysicsDev {
     int kind;                       // LSGG_PHYSICS_*
-    const float* energy;            // per grain, grid units
-    const int* nb_start;            // CSR over grains: pair entries sorted by j
-    const PairEntry* nb;            // pair table
+    const float* energy;            // per grain bulk energy, grid units (MAGNETIC)
+    const double* quats;            // per grain unit quaternion (w, x, y, z) (READ_SHOCKLEY)
+    const int* nb_tab;              // per grain: ascending ids of the grains in its ID-field
+    const int* nb_cnt;              // per grain: entries (kNbCap + 1: the table overflowed)
+    double theta_max;               // radians
+    double mob_low;
+    int mob_law;                    // LSGG_MOBILITY_*
     float dt;
 };
 
@@ -122,8 +128,9 @@ struct StepBuffers {
     int* worklist;                  // kNumClasses x n_boxes
     StepState* st;
     long long cap;
-    float* scratch;                 // global ring buffers of the large class
+    float* scratch;                 // global ring buffers of the classes in mode 2
     long long scratch_per_cta;
+    long long scratch_class_off[kNumClasses];   // each mode-2 class owns a slice (classes run concurrently)
     int n_sm;
     int class_side[kNumClasses];    // largest box side per class (last: whole domain)
     int mode[kNumClasses];          // 0: register-ring kernels, 1: shared-memory ring, 2: global scratch ring
@@ -132,10 +139,20 @@ struct StepBuffers {
     size_t smem[2][kNumClasses];
 };
 
+// Side streams on which the size-class kernels of one phase run concurrently
+// (forked from and joined back into the step's stream by events).
+struct StepStreams {
+    cudaStream_t side[kNumClasses];
+    cudaEvent_t fork;
+    cudaEvent_t join[kNumClasses];
+};
+
 // ev (optional, 5 events): recorded before the field clear, after it, after the
 // predictor launches, after the corrector launches and after the box update.
+// ss (optional): run each phase's class kernels concurrently on side streams.
 cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
-                        const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev = nullptr);
+                        const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev = nullptr,
+                        const StepStreams* ss = nullptr);
 cudaError_t launch_box_update(const StepBuffers& B, bool commit_only_layout, cudaStream_t s);
 cudaError_t configure_step_kernels(StepBuffers& B);
 cudaError_t launch_plain_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,

@@ -1,0 +1,66 @@
+// Neighbour tables for the velocity correction of Eq. (10).
+//
+// The paper refreshes a grain's neighbourhood from its points of contact and
+// keeps, per cell, the nearest other grain in the ID-field (Sec. 3.1).  Here a
+// grain's table is exactly the set of grain ids present in its ID-field: the
+// pairs the next predictor can meet.  k_collect_neighbours rebuilds it from the
+// state's ID-field before every predictor of a READ_SHOCKLEY run; the
+// predictor evaluates the pair weights of a box once from it.
+#include "lsgg_internal.cuh"
+
+namespace lsgg {
+
+constexpr int kHashSlots = 512;
+
+__global__ void __launch_bounds__(256)
+k_collect_neighbours(const Box* __restrict__ prev, const int* __restrict__ IDF, int* __restrict__ tab,
+                     int* __restrict__ cnt) {
+    __shared__ int keys[kHashSlots];
+    __shared__ int n_keys, overflow;
+    const int b = blockIdx.x;
+    const Box ob = prev[b];
+    for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x) keys[k] = -1;
+    if (threadIdx.x == 0) { n_keys = 0; overflow = 0; }
+    __syncthreads();
+    if (ob.nx > 0) {
+        const long long A = (long long)ob.nx * ob.ny, n = A * ob.nz;
+        const int ps = plane_stride(ob.nx, ob.ny);
+        int last = -1;
+        for (long long c = threadIdx.x; c < n; c += blockDim.x) {
+            const long long z = c / A, rem = c - z * A;
+            const int j = IDF[ob.off + z * ps + rem];
+            if (j < 0 || j == last) continue;
+            last = j;
+            unsigned h = ((unsigned)j * 2654435761u) >> 23;   // 9 bits
+            for (int probe = 0; probe < kHashSlots; ++probe) {
+                const int slot = (int)((h + probe) & (kHashSlots - 1));
+                const int cur = keys[slot];
+                if (cur == j) break;
+                if (cur == -1) {
+                    const int prevk = atomicCAS(&keys[slot], -1, j);
+                    if (prevk == -1) { atomicAdd(&n_keys, 1); break; }
+                    if (prevk == j) break;
+                }
+                if (probe == kHashSlots - 1) overflow = 1;
+            }
+        }
+    }
+    __syncthreads();
+    // rank-sort the keys (ascending) and keep the first kNbCap
+    for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x) {
+        const int j = keys[k];
+        if (j < 0) continue;
+        int rank = 0;
+        for (int q = 0; q < kHashSlots; ++q) rank += (unsigned)keys[q] < (unsigned)j && keys[q] >= 0;
+        if (rank < kNbCap) tab[(size_t)b * kNbCap + rank] = j;
+    }
+    if (threadIdx.x == 0) cnt[b] = (overflow || n_keys > kNbCap) ? kNbCap + 1 : n_keys;
+}
+
+cudaError_t launch_collect_neighbours(const StepBuffers& B, const PhysicsDev& phys, cudaStream_t s) {
+    k_collect_neighbours<<<B.n_boxes, 256, 0, s>>>(B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
+                                                     const_cast<int*>(phys.nb_cnt));
+    return cudaGetLastError();
+}
+
+}  // namespace lsgg

@@ -95,7 +95,7 @@ __global__ void kp_conv_z(Domain D, PlainBox p, const float* __restrict__ t2, co
                 phi0 = X[o];
                 j = IDF[o];
             }
-            v = pair_blend(phys, p.gid, j, phi0, c);
+            v = pair_blend(phys, PairTable{nullptr, nullptr, nullptr, 0}, p.gid, j, phi0, c);
         }
         v = fminf(fmaxf(v, -D.eps), D.eps);
         Y[nb.off + (long long)z * ps + (long long)y * nx + x] = v;

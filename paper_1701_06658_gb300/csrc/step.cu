@@ -43,7 +43,7 @@ struct PredictSmem {   // carved from dynamic shared memory (maps) + a float buf
 };
 
 __device__ void predict_box(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
-                            int b, const PredictSmem& sm, float* buf) {
+                            int b, const PredictSmem& sm, float* buf, const PairTable& tab) {
     const Domain& D = B.dom;
     const Box nb = B.cur[b];
     const Box ob = B.prev[b];
@@ -159,7 +159,7 @@ __device__ void predict_box(const StepBuffers& B, const Taps& taps, const Physic
                     phi0 = B.X[o];
                     j = B.IDF[o];
                 }
-                v = pair_blend(phys, b, j, phi0, c);
+                v = pair_blend(phys, tab, b, j, phi0, c);
             }
             v = fminf(fmaxf(v, -eps), eps);
             dst[idx] = v;
@@ -185,11 +185,14 @@ k_predict(StepBuffers B, Taps taps, PhysicsDev phys, int cls) {
     sm.gy = sm.gx + side;
     float* buf = reinterpret_cast<float*>(sm.gy + side + 4);
     buf = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(buf) + 15) & ~uintptr_t(15));
-    if (B.mode[cls] == 2) buf = B.scratch + (long long)blockIdx.x * B.scratch_per_cta;
+    if (B.mode[cls] == 2) buf = B.scratch + B.scratch_class_off[cls] + (long long)blockIdx.x * B.scratch_per_cta;
+    __shared__ int s_tj[kNbCap];
+    __shared__ float s_tw[kNbCap], s_tm[kNbCap];
     for (;;) {
         int b = pull_box(B, 0, cls, &s_box);
         if (b < 0) break;
-        predict_box(B, taps, phys, b, sm, buf);
+        const PairTable tab = load_pair_table(phys, b, s_tj, s_tw, s_tm);
+        predict_box(B, taps, phys, b, sm, buf, tab);
     }
 }
 
@@ -396,7 +399,7 @@ k_correct(StepBuffers B, PhysicsDev phys, DebugOut dbg, int cls) {
     int* gy = gx + side;
     float* buf = reinterpret_cast<float*>(gy + side + 4);
     buf = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(buf) + 15) & ~uintptr_t(15));
-    if (B.mode[cls] == 2) buf = B.scratch + (long long)blockIdx.x * B.scratch_per_cta;
+    if (B.mode[cls] == 2) buf = B.scratch + B.scratch_class_off[cls] + (long long)blockIdx.x * B.scratch_per_cta;
     for (;;) {
         int b = pull_box(B, 1, cls, &s_box);
         if (b < 0) break;
@@ -535,6 +538,7 @@ static size_t correct_smem_bytes(int side) {
 }
 
 int fast_class_side(int cls);
+cudaError_t launch_collect_neighbours(const StepBuffers& B, const PhysicsDev& phys, cudaStream_t s);
 cudaError_t configure_fast(StepBuffers& B, int cls, int n_sm);
 cudaError_t launch_fast(const StepBuffers& B, int which, int cls, const Taps& taps, const PhysicsDev& phys,
                         const DebugOut& dbg, cudaStream_t s);
@@ -621,7 +625,7 @@ cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream
 }
 
 cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
-                        const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev) {
+                        const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev, const StepStreams* ss) {
     long long ncell = (long long)B.dom.nx * B.dom.ny * B.dom.nz;
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = cudaMemsetAsync(B.T, 0, (size_t)ncell * 16, s);
@@ -629,17 +633,44 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
     if (ev) cudaEventRecord(ev[1], s);
     DebugOut d{};
     if (dbg) d = *dbg;
-    for (int c = 0; c < kNumClasses; ++c) {
-        if (B.mode[c] == 0) e = launch_fast(B, 0, c, taps, phys, d, s);
-        else { k_predict<<<B.grid[0][c], kThreads, B.smem[0][c], s>>>(B, taps, phys, c); e = cudaGetLastError(); }
+    if (phys.kind == LSGG_PHYSICS_READ_SHOCKLEY) {
+        e = launch_collect_neighbours(B, phys, s);
         if (e != cudaSuccess) return e;
     }
+    auto run_phase = [&](int which) -> cudaError_t {
+        if (ss) {
+            cudaError_t r = cudaEventRecord(ss->fork, s);
+            if (r != cudaSuccess) return r;
+        }
+        for (int c = 0; c < kNumClasses; ++c) {
+            cudaStream_t cs = s;
+            if (ss) {
+                cs = ss->side[c];
+                cudaError_t r = cudaStreamWaitEvent(cs, ss->fork, 0);
+                if (r != cudaSuccess) return r;
+            }
+            cudaError_t r;
+            if (B.mode[c] == 0) r = launch_fast(B, which, c, taps, phys, d, cs);
+            else if (which == 0) { k_predict<<<B.grid[0][c], kThreads, B.smem[0][c], cs>>>(B, taps, phys, c); r = cudaGetLastError(); }
+            else { k_correct<<<B.grid[1][c], kThreads, B.smem[1][c], cs>>>(B, phys, d, c); r = cudaGetLastError(); }
+            if (r != cudaSuccess) return r;
+            if (ss) {
+                r = cudaEventRecord(ss->join[c], cs);
+                if (r != cudaSuccess) return r;
+            }
+        }
+        if (ss)
+            for (int c = 0; c < kNumClasses; ++c) {
+                cudaError_t r = cudaStreamWaitEvent(s, ss->join[c], 0);
+                if (r != cudaSuccess) return r;
+            }
+        return cudaSuccess;
+    };
+    e = run_phase(0);
+    if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
-    for (int c = 0; c < kNumClasses; ++c) {
-        if (B.mode[c] == 0) e = launch_fast(B, 1, c, taps, phys, d, s);
-        else { k_correct<<<B.grid[1][c], kThreads, B.smem[1][c], s>>>(B, phys, d, c); e = cudaGetLastError(); }
-        if (e != cudaSuccess) return e;
-    }
+    e = run_phase(1);
+    if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[3], s);
     e = launch_box_update(B, false, s);
     if (ev) cudaEventRecord(ev[4], s);

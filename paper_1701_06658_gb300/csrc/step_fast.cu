@@ -100,6 +100,8 @@ k_predict_fast(StepBuffers B, Taps taps, PhysicsDev phys, int cls) {
     int* gx = mapy + L::PX;
     int* gy = gx + SIDE;
     __shared__ int s_box;
+    __shared__ int s_tj[kNbCap];
+    __shared__ float s_tw[kNbCap], s_tm[kNbCap];
     const int tid = threadIdx.x;
     if (tid == 0) {
         for (int s = 0; s < kSlots; ++s) mbar_init(&bar[s], 1);
@@ -113,6 +115,7 @@ k_predict_fast(StepBuffers B, Taps taps, PhysicsDev phys, int cls) {
     for (;;) {
         const int b = pull_box(B, 0, cls, &s_box);
         if (b < 0) break;
+        const PairTable tab = load_pair_table(phys, b, s_tj, s_tw, s_tm);
         const Box nb = B.cur[b];
         const Box ob = B.prev[b];
         const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
@@ -167,105 +170,127 @@ k_predict_fast(StepBuffers B, Taps taps, PhysicsDev phys, int cls) {
         const bool own = y0 < ny;
         const int nxs = (nx + kVX - 1) / kVX;
         float ring[W][V];
+        // second-key atomics of the previous output plane, issued one plane late
+        // so the first atomics' return values arrive while this plane is computed
+        unsigned long long pend_old[V];
+        float pend_val[V];
+        int pend_g[V];            // domain cell index (< 2^31)
+#pragma unroll
+        for (int v = 0; v < V; ++v) { pend_old[v] = 0; pend_val[v] = 0.0f; pend_g[v] = 0; }
         int slot = 0;
-        for (int zb = zlo; zb < zhi; zb += W) {
-#pragma unroll
-            for (int s = 0; s < W; ++s) {
-                const int zin = zb + s;
-                if (zin >= zhi) break;
-                const int zl = zold_of(zin);
-                bool ok = true;
-                if (zl >= 0) {
-                    ok = mbar_wait(&bar[slot], (phase >> slot) & 1u);
-                    phase ^= 1u << slot;
-                }
-                const float* rs = raw + slot * L::PS;
-                for (int idx = tid; idx < PXa * PYa; idx += NT) {
-                    const int yp = idx / PXa, xp = idx - yp * PXa;
-                    const int mx = mapx[xp], my = mapy[yp];
-                    float v = -eps;
-                    if (zl >= 0 && mx >= 0 && my >= 0) v = rs[my * ob.nx + mx];
-                    P[idx] = v;
-                }
-                if (__syncthreads_or(!ok)) { give_up(B, bar, phase); return; }
-                if (tid == 0) {
-                    const int zn = zin + kSlots;
-                    if (zn < zhi) {
-                        const int zz = zold_of(zn);
-                        if (zz >= 0) {
-                            fence_async_smem();
-                            mbar_expect(&bar[slot], bytes);
-                            bulk_load(raw + slot * L::PS, Xold + (long long)zz * ps_old, bytes, &bar[slot]);
-                        }
+        for (int zin = zlo; zin < zhi; ++zin) {
+            const int zl = zold_of(zin);
+            bool ok = true;
+            if (zl >= 0) {
+                ok = mbar_wait(&bar[slot], (phase >> slot) & 1u);
+                phase ^= 1u << slot;
+            }
+            const float* rs = raw + slot * L::PS;
+            for (int idx = tid; idx < PXa * PYa; idx += NT) {
+                const int yp = idx / PXa, xp = idx - yp * PXa;
+                const int mx = mapx[xp], my = mapy[yp];
+                float v = -eps;
+                if (zl >= 0 && mx >= 0 && my >= 0) v = rs[my * ob.nx + mx];
+                P[idx] = v;
+            }
+            if (__syncthreads_or(!ok)) { give_up(B, bar, phase); return; }
+            if (tid == 0) {
+                const int zn = zin + kSlots;
+                if (zn < zhi) {
+                    const int zz = zold_of(zn);
+                    if (zz >= 0) {
+                        fence_async_smem();
+                        mbar_expect(&bar[slot], bytes);
+                        bulk_load(raw + slot * L::PS, Xold + (long long)zz * ps_old, bytes, &bar[slot]);
                     }
                 }
-                slot = slot + 1 == kSlots ? 0 : slot + 1;
-                // x pass: kVX outputs per thread from one window of the staged row
-                for (int t = tid; t < PYa * nxs; t += NT) {
-                    const int yp = t / nxs, x0 = (t - yp * nxs) * kVX;
-                    const float* row = P + yp * PXa + x0;
-                    float in[kVX + 2 * R];
+            }
+            slot = slot + 1 == kSlots ? 0 : slot + 1;
+            // x pass: kVX outputs per thread from one window of the staged row
+            for (int t = tid; t < PYa * nxs; t += NT) {
+                const int yp = t / nxs, x0 = (t - yp * nxs) * kVX;
+                const float* row = P + yp * PXa + x0;
+                float in[kVX + 2 * R];
 #pragma unroll
-                    for (int j = 0; j < kVX + 2 * R; ++j) in[j] = x0 + j < PXa ? row[j] : 0.0f;
+                for (int j = 0; j < kVX + 2 * R; ++j) in[j] = x0 + j < PXa ? row[j] : 0.0f;
 #pragma unroll
-                    for (int v = 0; v < kVX; ++v) {
-                        float acc = 0.0f;
+                for (int v = 0; v < kVX; ++v) {
+                    float acc = 0.0f;
 #pragma unroll
-                        for (int k = 0; k < W; ++k) acc = fmaf(taps.g[k], in[v + k], acc);
-                        if (x0 + v < nx) Xp[yp * nx + x0 + v] = acc;
-                    }
+                    for (int k = 0; k < W; ++k) acc = fmaf(taps.g[k], in[v + k], acc);
+                    if (x0 + v < nx) Xp[yp * nx + x0 + v] = acc;
                 }
-                __syncthreads();
-                // y pass into the register ring (slot s holds plane zin)
-                if (own) {
-                    float col[V + 2 * R];
+            }
+            __syncthreads();
+            // pending second keys of the previous plane (their first atomics have returned)
 #pragma unroll
-                    for (int j = 0; j < V + 2 * R; ++j) col[j] = y0 + j < PYa ? Xp[(y0 + j) * nx + sx] : 0.0f;
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        float acc = 0.0f;
-#pragma unroll
-                        for (int k = 0; k < W; ++k) acc = fmaf(taps.g[k], col[v + k], acc);
-                        ring[s][v] = acc;
-                    }
+            for (int v = 0; v < V; ++v)
+                if (pend_old[v]) {
+                    const unsigned long long k = make_key(pend_val[v], b);
+                    atomicMax(&B.T[2 * (long long)pend_g[v] + 1], pend_old[v] < k ? pend_old[v] : k);
                 }
-                // z pass for output plane zo = zin - R: ring slots of planes zo-R .. zo+R
-                const int zo = zin - R;
-                if (own && zo >= 0) {
-                    const int gz = pmod(nb.oz + zo, D.nz);
-                    float* dst = B.Y + nb.off + (long long)zo * ps_new;
-                    const long long grow = (long long)gz * D.ny;
+            // rotate the ring: ring[k] holds plane zin - (W - 1) + k
 #pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const int y = y0 + v;
-                        if (y < ny) {
-                            float c = 0.0f;
+            for (int k = 0; k < W - 1; ++k)
 #pragma unroll
-                            for (int k = 0; k < W; ++k) c = fmaf(taps.g[k], ring[(s + 1 + k) % W][v], c);
-                            float val = c;
-                            if (phys.kind != LSGG_PHYSICS_IDEAL) {
-                                const int ozz = pmod(nb.oz + zo - ob.oz, D.nz);
-                                const int mx = mapx[sx + R], my = mapy[y + R];
-                                float phi0 = -eps;
-                                int j = -1;
-                                if (ozz < ob.nz && mx >= 0 && my >= 0) {
-                                    const long long o = ob.off + (long long)ozz * ps_old + my * ob.nx + mx;
-                                    phi0 = B.X[o];
-                                    j = B.IDF[o];
-                                }
-                                val = pair_blend(phys, b, j, phi0, c);
+                for (int v = 0; v < V; ++v) ring[k][v] = ring[k + 1][v];
+            if (own) {
+                float col[V + 2 * R];
+#pragma unroll
+                for (int j = 0; j < V + 2 * R; ++j) col[j] = y0 + j < PYa ? Xp[(y0 + j) * nx + sx] : 0.0f;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < W; ++k) acc = fmaf(taps.g[k], col[v + k], acc);
+                    ring[W - 1][v] = acc;
+                }
+            }
+            // z pass for output plane zo = zin - R: ring[0 .. W-1] = planes zo-R .. zo+R
+            const int zo = zin - R;
+#pragma unroll
+            for (int v = 0; v < V; ++v) pend_old[v] = 0;
+            if (own && zo >= 0) {
+                const int gz = pmod(nb.oz + zo, D.nz);
+                float* dst = B.Y + nb.off + (long long)zo * ps_new;
+                const long long grow = (long long)gz * D.ny;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int y = y0 + v;
+                    if (y < ny) {
+                        float c = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < W; ++k) c = fmaf(taps.g[k], ring[k][v], c);
+                        float val = c;
+                        if (phys.kind != LSGG_PHYSICS_IDEAL) {
+                            const int ozz = pmod(nb.oz + zo - ob.oz, D.nz);
+                            const int mx = mapx[sx + R], my = mapy[y + R];
+                            float phi0 = -eps;
+                            int j = -1;
+                            if (ozz < ob.nz && mx >= 0 && my >= 0) {
+                                const long long o = ob.off + (long long)ozz * ps_old + my * ob.nx + mx;
+                                phi0 = B.X[o];
+                                j = B.IDF[o];
                             }
-                            val = fminf(fmaxf(val, -eps), eps);
-                            dst[y * nx + sx] = val;
-                            const long long g = (grow + gy[y]) * D.nx + gx[sx];
-                            const unsigned long long key = make_key(val, b);
-                            const unsigned long long old = atomicMax(&B.T[2 * g], key);
-                            if (old) atomicMax(&B.T[2 * g + 1], old < key ? old : key);
+                            val = pair_blend(phys, tab, b, j, phi0, c);
                         }
+                        val = fminf(fmaxf(val, -eps), eps);
+                        dst[y * nx + sx] = val;
+                        const long long g = (grow + gy[y]) * D.nx + gx[sx];
+                        const unsigned long long key = make_key(val, b);
+                        pend_old[v] = atomicMax(&B.T[2 * g], key);
+                        pend_val[v] = val;
+                        pend_g[v] = (int)g;
                     }
                 }
             }
         }
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (pend_old[v]) {
+                const unsigned long long k = make_key(pend_val[v], b);
+                atomicMax(&B.T[2 * (long long)pend_g[v] + 1], pend_old[v] < k ? pend_old[v] : k);
+            }
         __syncthreads();
     }
 }
@@ -377,142 +402,152 @@ k_correct_fast(StepBuffers B, PhysicsDev phys, DebugOut dbg, int cls) {
         int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
         const int zb_first = fzf ? z_first + 1 : 0;
         int slot = 0;
-        for (int zbase = z_first; zbase <= z_last; zbase += ZR) {
+        // field records of the owned cells of the next stage-A plane, loaded a plane early
+        ulonglong2 tk[V];
+        auto load_t = [&](int zin) {
+            const int zl = a_plane(zin);
+            if (!own || zl < 0 || zin > z_last || !a_wanted(zin)) return;
+            const long long grow = (long long)pmod(nb.oz + zl, D.nz) * D.ny;
 #pragma unroll
-            for (int s = 0; s < ZR; ++s) {
-                const int zin = zbase + s;
-                if (zin > z_last) break;
-                // ---- A: phi_c of plane zin for the owned cells ----
-                const bool want = a_wanted(zin);
-                const int zl = a_plane(zin);
-                bool ok = true;
-                if (want && zl >= 0) {
-                    ok = mbar_wait(&bar[slot], (phase >> slot) & 1u);
-                    phase ^= 1u << slot;
-                }
-                if (want) {
+            for (int v = 0; v < V; ++v) {
+                const int y = y0 + v;
+                if (y < ny) tk[v] = __ldg(reinterpret_cast<const ulonglong2*>(B.T) + (grow + gy[y]) * D.nx + gx[sx]);
+            }
+        };
+        load_t(z_first);
+        for (int zin = z_first; zin <= z_last; ++zin) {
+            // ---- A: phi_c of plane zin for the owned cells ----
+            const bool want = a_wanted(zin);
+            const int zl = a_plane(zin);
+            bool ok = true;
+            if (want && zl >= 0) {
+                ok = mbar_wait(&bar[slot], (phase >> slot) & 1u);
+                phase ^= 1u << slot;
+            }
+            if (want) {
 #pragma unroll
-                    for (int v = 0; v < V; ++v) { c_m[v] = c_0[v]; c_0[v] = c_p[v]; }
-                    if (own) {
-                        const float* rs = raw + slot * L::PS;
-                        const int gz = zl >= 0 ? pmod(nb.oz + zl, D.nz) : 0;
-                        float* Cz = Cs + (zin & 1) * A;
-                        const bool record = zin >= 0 && zin < nz;
+                for (int v = 0; v < V; ++v) { c_m[v] = c_0[v]; c_0[v] = c_p[v]; }
+                if (own) {
+                    const float* rs = raw + slot * L::PS;
+                    float* Cz = Cs + (zin & 1) * A;
+                    const bool record = zin >= 0 && zin < nz;
 #pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            const int y = y0 + v;
-                            float pc = -eps;
-                            if (y < ny && zl >= 0) {
-                                const int i = y * nx + sx;
-                                const float pp = rs[i];
-                                const long long g = ((long long)gz * D.ny + gy[y]) * D.nx + gx[sx];
-                                const ulonglong2 kk = __ldg(reinterpret_cast<const ulonglong2*>(B.T) + g);
-                                const int id1 = key_id(kk.x);
-                                float m;
-                                int mid;
-                                if (id1 != b) { m = key_val(kk.x, eps); mid = id1; }
-                                else { m = key_val(kk.y, eps); mid = key_id(kk.y); }
-                                if (!(m > -eps)) mid = -1;
-                                pc = 0.5f * (pp - m);
-                                Cz[i] = pc;
-                                if (record) {
-                                    const long long o = nb.off + (long long)zl * ps + i;
-                                    if (phys.kind != LSGG_PHYSICS_IDEAL) B.IDF[o] = mid;
-                                    if (dbg.m) { dbg.m[o] = m; dbg.idm[o] = mid; dbg.phic[o] = pc; dbg.phip[o] = pp; }
-                                }
-                            }
-                            c_p[v] = pc;
-                        }
-                    }
-                }
-                if (__syncthreads_or(!ok)) { give_up(B, bar, phase); return; }
-                if (tid == 0) {
-                    // refill this slot with the plane kSlots ahead (if it needs a copy)
-                    const int zn = zin + kSlots;
-                    const int zz = a_plane(zn);
-                    if (zn <= z_last && a_wanted(zn) && zz >= 0) {
-                        fence_async_smem();
-                        mbar_expect(&bar[slot], bytes);
-                        bulk_load(raw + slot * L::PS, Ybox + (long long)zz * ps, bytes, &bar[slot]);
-                    }
-                }
-                slot = slot + 1 == kSlots ? 0 : slot + 1;
-                // ---- B: classification of plane zb = zin - 1 ----
-                const int zb = zin - 1;
-                const bool do_b = zb >= zb_first && (fzf ? zb <= nz + kReach - 1 : zb < nz);
-                if (do_b) {
-                    const float* C0 = Cs + (zb & 1) * A;
-                    if (own) {
-#pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            const int y = y0 + v;
-                            if (y >= ny) continue;
+                    for (int v = 0; v < V; ++v) {
+                        const int y = y0 + v;
+                        float pc = -eps;
+                        if (y < ny && zl >= 0) {
                             const int i = y * nx + sx;
-                            const float val = c_0[v];
-                            const bool pos = val > 0.0f;
-                            const float a = fabsf(val);
-                            float inv2 = 0.0f;
-                            bool ref = false, zero = false;
-                            {
-                                float dmin = FLT_MAX;
-                                const float l = sx > 0 ? C0[i - 1] : (fx ? C0[i + nx - 1] : -eps);
-                                const float r = sx < nx - 1 ? C0[i + 1] : (fx ? C0[i - nx + 1] : -eps);
-                                opp_delta(a, pos, l, dmin);
-                                opp_delta(a, pos, r, dmin);
-                                if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
+                            const float pp = rs[i];
+                            const int id1 = key_id(tk[v].x);
+                            float m;
+                            int mid;
+                            if (id1 != b) { m = key_val(tk[v].x, eps); mid = id1; }
+                            else { m = key_val(tk[v].y, eps); mid = key_id(tk[v].y); }
+                            if (!(m > -eps)) mid = -1;
+                            pc = 0.5f * (pp - m);
+                            Cz[i] = pc;
+                            if (record) {
+                                const long long o = nb.off + (long long)zl * ps + i;
+                                if (phys.kind != LSGG_PHYSICS_IDEAL) B.IDF[o] = mid;
+                                if (dbg.m) { dbg.m[o] = m; dbg.idm[o] = mid; dbg.phic[o] = pc; dbg.phip[o] = pp; }
                             }
-                            {
-                                float dmin = FLT_MAX;
-                                const float l = y > 0 ? C0[i - nx] : (fy ? C0[i + (ny - 1) * nx] : -eps);
-                                const float r = y < ny - 1 ? C0[i + nx] : (fy ? C0[i - (ny - 1) * nx] : -eps);
-                                opp_delta(a, pos, l, dmin);
-                                opp_delta(a, pos, r, dmin);
-                                if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
-                            }
-                            {
-                                float dmin = FLT_MAX;
-                                opp_delta(a, pos, c_m[v], dmin);
-                                opp_delta(a, pos, c_p[v], dmin);
-                                if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
-                            }
-                            float mag = eps;
-                            if (ref) mag = zero ? 0.0f : 1.0f / sqrtf(inv2);
-                            G[i] = pos ? mag : -mag;
                         }
+                        c_p[v] = pc;
                     }
                 }
-                __syncthreads();
-                if (do_b) {
-                    // ---- x pass: G -> H, kVD outputs per thread ----
-                    const int nxs = (nx + kVD - 1) / kVD;
-                    for (int t = tid; t < ny * nxs; t += NT) {
-                        const int y = t / nxs, x0 = (t - y * nxs) * kVD;
-                        const float* row = G + y * nx;
-                        float w[NXW];
-                        bool valid[NXW];
-#pragma unroll
-                        for (int j = 0; j < NXW; ++j) {
-                            int x = x0 - kReach + j;
-                            bool ok2 = fx || (x >= 0 && x < nx);
-                            if (fx) x = pmod(x, nx);
-                            valid[j] = ok2;
-                            w[j] = ok2 ? row[x] : 0.0f;
-                        }
-                        window_sweep<NXW>(w, valid);
-#pragma unroll
-                        for (int v = 0; v < kVD; ++v)
-                            if (x0 + v < nx) H[y * nx + x0 + v] = w[kReach + v];
-                    }
+            }
+            load_t(zin + 1);
+            if (__syncthreads_or(!ok)) { give_up(B, bar, phase); return; }
+            if (tid == 0) {
+                // refill this slot with the plane kSlots ahead (if it needs a copy)
+                const int zn = zin + kSlots;
+                const int zz = a_plane(zn);
+                if (zn <= z_last && a_wanted(zn) && zz >= 0) {
+                    fence_async_smem();
+                    mbar_expect(&bar[slot], bytes);
+                    bulk_load(raw + slot * L::PS, Ybox + (long long)zz * ps, bytes, &bar[slot]);
                 }
-                __syncthreads();
-                // ---- y pass (owned column segment) + forward z sweep into fr[s] ----
-                if (do_b && own) {
+            }
+            slot = slot + 1 == kSlots ? 0 : slot + 1;
+            // ---- B: classification of plane zb = zin - 1 ----
+            const int zb = zin - 1;
+            const bool do_b = zb >= zb_first && (fzf ? zb <= nz + kReach - 1 : zb < nz);
+            if (do_b && own) {
+                const float* C0 = Cs + (zb & 1) * A;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int y = y0 + v;
+                    if (y >= ny) continue;
+                    const int i = y * nx + sx;
+                    const float val = c_0[v];
+                    const bool pos = val > 0.0f;
+                    const float a = fabsf(val);
+                    float inv2 = 0.0f;
+                    bool ref = false, zero = false;
+                    {
+                        float dmin = FLT_MAX;
+                        const float l = sx > 0 ? C0[i - 1] : (fx ? C0[i + nx - 1] : -eps);
+                        const float r = sx < nx - 1 ? C0[i + 1] : (fx ? C0[i - nx + 1] : -eps);
+                        opp_delta(a, pos, l, dmin);
+                        opp_delta(a, pos, r, dmin);
+                        if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
+                    }
+                    {
+                        float dmin = FLT_MAX;
+                        const float l = y > 0 ? C0[i - nx] : (fy ? C0[i + (ny - 1) * nx] : -eps);
+                        const float r = y < ny - 1 ? C0[i + nx] : (fy ? C0[i - (ny - 1) * nx] : -eps);
+                        opp_delta(a, pos, l, dmin);
+                        opp_delta(a, pos, r, dmin);
+                        if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
+                    }
+                    {
+                        float dmin = FLT_MAX;
+                        opp_delta(a, pos, c_m[v], dmin);
+                        opp_delta(a, pos, c_p[v], dmin);
+                        if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
+                    }
+                    float mag = eps;
+                    if (ref) mag = zero ? 0.0f : 1.0f / sqrtf(inv2);
+                    G[i] = pos ? mag : -mag;
+                }
+            }
+            __syncthreads();
+            if (do_b) {
+                // ---- x pass: G -> H, kVD outputs per thread ----
+                const int nxs = (nx + kVD - 1) / kVD;
+                for (int t = tid; t < ny * nxs; t += NT) {
+                    const int y = t / nxs, x0 = (t - y * nxs) * kVD;
+                    const float* row = G + y * nx;
+                    float w[NXW];
+                    bool valid[NXW];
+#pragma unroll
+                    for (int j = 0; j < NXW; ++j) {
+                        int x = x0 - kReach + j;
+                        const bool ok2 = fx || (x >= 0 && x < nx);
+                        if (fx) x = pmod(x, nx);
+                        valid[j] = ok2;
+                        w[j] = ok2 ? row[x] : 0.0f;
+                    }
+                    window_sweep<NXW>(w, valid);
+#pragma unroll
+                    for (int v = 0; v < kVD; ++v)
+                        if (x0 + v < nx) H[y * nx + x0 + v] = w[kReach + v];
+                }
+            }
+            __syncthreads();
+            // ---- y pass (owned column segment) + forward z sweep: fr[ZR-1] = plane zb ----
+            if (do_b) {
+#pragma unroll
+                for (int k = 0; k < ZR - 1; ++k)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) fr[k][v] = fr[k + 1][v];
+                if (own) {
                     float w[NY];
                     bool valid[NY];
 #pragma unroll
                     for (int j = 0; j < NY; ++j) {
                         int y = y0 - kReach + j;
-                        bool ok2 = fy || (y >= 0 && y < ny);
+                        const bool ok2 = fy || (y >= 0 && y < ny);
                         if (fy) y = pmod(y, ny);
                         valid[j] = ok2;
                         w[j] = ok2 ? H[y * nx + sx] : 0.0f;
@@ -522,43 +557,49 @@ k_correct_fast(StepBuffers B, PhysicsDev phys, DebugOut dbg, int cls) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         float val = w[kReach + v];
-                        const float p = fr[(s + ZR - 1) % ZR][v];
+                        const float p = fr[ZR - 2][v];
                         if (!first && sgn_pos(p) == sgn_pos(val)) {
                             const float mm = fminf(fabsf(val), fabsf(p) + 1.0f);
                             val = sgn_pos(val) ? mm : -mm;
                         }
-                        fr[s][v] = val;
+                        fr[ZR - 1][v] = val;
                     }
                 }
-                // ---- E: backward z window, output plane zo = zb - kReach ----
-                const int zo = zb - kReach;
-                if (own && zo >= 0 && zo < nz) {
-                    const int ztop = fzf ? zb : min(zb, nz - 1);
-                    float* dst = B.X + nb.off + (long long)zo * ps;
+            } else {
+                // planes past the box end: shift so that fr[0] stays plane zb - kReach
 #pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const int y = y0 + v;
-                        if (y >= ny) continue;
-                        const float val = fr[(s + 1) % ZR][v];
-                        const bool sg = sgn_pos(val);
-                        float best = fabsf(val);
-                        bool go = true;
+                for (int k = 0; k < ZR - 1; ++k)
 #pragma unroll
-                        for (int k = 1; k <= kReach; ++k) {
-                            const float u = fr[(s + 1 + k) % ZR][v];
-                            go = go && (zo + k <= ztop) && (sgn_pos(u) == sg);
-                            if (go) best = fminf(best, fabsf(u) + (float)k);
-                        }
-                        best = fminf(best, eps);
-                        const float out = sg ? best : -best;
-                        const int i = y * nx + sx;
-                        dst[i] = out;
-                        if (dbg.phin) dbg.phin[nb.off + (long long)zo * ps + i] = out;
-                        if (out > 0.0f) {
-                            lo[0] = min(lo[0], sx); hi[0] = max(hi[0], sx);
-                            lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
-                            lo[2] = min(lo[2], zo); hi[2] = max(hi[2], zo);
-                        }
+                    for (int v = 0; v < V; ++v) fr[k][v] = fr[k + 1][v];
+            }
+            // ---- E: backward z window over fr[0 .. 6] = planes zo .. zo + 6 ----
+            const int zo = zb - kReach;
+            if (own && zo >= 0 && zo < nz) {
+                const int ztop = fzf ? zb : min(zb, nz - 1);
+                float* dst = B.X + nb.off + (long long)zo * ps;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int y = y0 + v;
+                    if (y >= ny) continue;
+                    const float val = fr[0][v];
+                    const bool sg = sgn_pos(val);
+                    float best = fabsf(val);
+                    bool go = true;
+#pragma unroll
+                    for (int k = 1; k <= kReach; ++k) {
+                        const float u = fr[k][v];
+                        go = go && (zo + k <= ztop) && (sgn_pos(u) == sg);
+                        if (go) best = fminf(best, fabsf(u) + (float)k);
+                    }
+                    best = fminf(best, eps);
+                    const float out = sg ? best : -best;
+                    const int i = y * nx + sx;
+                    dst[i] = out;
+                    if (dbg.phin) dbg.phin[nb.off + (long long)zo * ps + i] = out;
+                    if (out > 0.0f) {
+                        lo[0] = min(lo[0], sx); hi[0] = max(hi[0], sx);
+                        lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
+                        lo[2] = min(lo[2], zo); hi[2] = max(hi[2], zo);
                     }
                 }
             }
