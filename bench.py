@@ -253,6 +253,11 @@ def gpu_arm(args):
         e2e_s = time.perf_counter() - t0
         e2e_cells = se.cell_updates
 
+    # ---------------- serving: continuous batching under an HBM budget ----------------
+    serving = None
+    if args.serve_requests > 0 and rank == 0:
+        serving = serving_run(L, I, args.serve_requests, local)
+
     # ---------------- reduce over ranks ----------------
     vals = [dev_ms, float(cells), e2e_s, float(e2e_cells)]
     if world > 1:
@@ -302,9 +307,49 @@ def gpu_arm(args):
             "sample": f"2 oracle steps of a {SAMPLE['n']}^3 periodic sub-domain at the workload's grain "
                       f"density ({SAMPLE['grains']} grains), {cpu_s:.1f} s"},
         "clocks": clk.summary(),
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def serving_run(L, I, n_requests, device):
+    """Requests drawn from the serving workload (cubic periodic domains 32..256,
+    grains = N^3/3355 clamped to [20, 5000], 10..200 steps), HBM budget 150 GB.
+    Closed loop first (all submitted at once) to measure capacity in requests/s,
+    then Poisson arrivals at 0.8 x capacity: latency = completion - arrival."""
+    budget = 150 << 30
+    probe = I.serving_requests(min(16, n_requests), 1.0, base_seed=5000)
+    with L.Server(budget, max_active=64, steps_per_round=4, device=device) as srv:
+        t0 = time.perf_counter()
+        tk = [srv.submit(r.n, r.n, r.n, r.n_grains, r.steps, seed=r.seed) for r in probe]
+        infos = [srv.wait(t) for t in tk]
+        closed_s = time.perf_counter() - t0
+        closed_cells = sum(i.cell_updates for i in infos)
+    capacity = len(probe) / closed_s
+    reqs = I.serving_requests(n_requests, 0.8 * capacity, base_seed=1000)
+    lat, cells = [], 0
+    with L.Server(budget, max_active=64, steps_per_round=4, device=device) as srv:
+        start = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            delay = start + r.arrival - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append((r, srv.submit(r.n, r.n, r.n, r.n_grains, r.steps, seed=r.seed)))
+        for r, t in tickets:
+            info = srv.wait(t)
+            lat.append(info.t_done - info.t_submit)
+            cells += info.cell_updates
+        wall = time.perf_counter() - start
+        peak = srv.stats().peak_bytes
+    lat = sorted(lat)
+    pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+    return {"requests": n_requests, "rate_per_s": 0.8 * capacity, "capacity_per_s": capacity,
+            "closed_loop_cell_updates_per_s": closed_cells / closed_s,
+            "p50_s": pct(0.50), "p99_s": pct(0.99), "mean_s": sum(lat) / len(lat),
+            "cell_updates_per_s": cells / wall, "wall_s": wall, "peak_admitted_bytes": peak,
+            "budget_bytes": budget}
 
 
 def main():
@@ -315,6 +360,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the serving measurement (0: skip; 256: the full serving workload)")
     ap.add_argument("--workload", default="256", choices=sorted(WORKLOADS),
                     help="256: the benchmark workload; 160: a small case of the same density for profilers")
     args = ap.parse_args()

@@ -190,6 +190,51 @@ int lsgg_set_state(lsgg_ctx* ctx, const int32_t* boxes, const float* phi, const 
 int lsgg_debug_step(lsgg_ctx* ctx, double dt, float* phip, float* m, int32_t* idm,
                     float* phic, float* phin);
 
+/* ------------------------------------------------------------- serving */
+/* A server runs independent simulations on one GPU with continuous batching
+ * (the paper has no serving layer; this is a request loop around Algorithm 1).
+ * Requests wait in FIFO order; a scheduler thread admits the head request when
+ * a slot is free and the HBM estimates of the running requests plus its own
+ * fit in budget_bytes, creates its microstructure (boxes resident on the
+ * device), and feeds every running request's stream with chunks of
+ * steps_per_round steps, so requests overlap on the device.  Finished requests
+ * keep their grain volumes on the host and release their device memory.
+ * Results are those of lsgg_create_microstructure + lsgg_step(n_steps, dt) +
+ * lsgg_grain_volumes run alone.  Times are seconds since lsgg_server_create. */
+typedef struct lsgg_server lsgg_server;
+
+typedef struct lsgg_request_info {
+    int32_t state;             /* 0 queued, 1 running, 2 done, < 0 failed with that status */
+    double t_submit, t_admit, t_done;
+    int64_t cell_updates;      /* box cell-updates of the request's steps */
+    int64_t device_bytes;      /* device memory its context held after creation */
+    int64_t estimate_bytes;    /* the admission estimate */
+} lsgg_request_info;
+
+typedef struct lsgg_server_stats {
+    int64_t queued, active, completed;
+    int64_t used_bytes, peak_bytes;   /* admission estimates in use / at most */
+    int64_t cell_updates;             /* summed over completed requests */
+} lsgg_server_stats;
+
+int lsgg_server_create(int64_t budget_bytes, int32_t max_active, int32_t steps_per_round, int32_t device,
+                       lsgg_server** out);
+/* Queue a request; cfg (and its arrays) are copied.  *ticket identifies it.
+ * A request whose estimate exceeds the whole budget fails with
+ * LSGG_ERR_OVER_BUDGET when it reaches the head of the queue. */
+int lsgg_server_submit(lsgg_server* s, const lsgg_config* cfg, int32_t n_steps, double dt, int64_t* ticket);
+/* LSGG_OK when done, LSGG_ERR_NOT_READY while queued or running, the failure status otherwise. */
+int lsgg_server_poll(lsgg_server* s, int64_t ticket, lsgg_request_info* info);
+/* Block until done (timeout_ms < 0: no limit; LSGG_ERR_TIMEOUT on expiry). */
+int lsgg_server_wait(lsgg_server* s, int64_t ticket, int64_t timeout_ms, lsgg_request_info* info);
+/* Grain volumes of a finished request (cap >= n_grains doubles). */
+int lsgg_server_volumes(lsgg_server* s, int64_t ticket, double* out, int64_t cap, int64_t* n_out);
+/* Forget a finished request's record. */
+int lsgg_server_release(lsgg_server* s, int64_t ticket);
+int lsgg_server_get_stats(lsgg_server* s, lsgg_server_stats* out);
+/* Stop the scheduler; running requests are abandoned and their memory freed. */
+int lsgg_server_destroy(lsgg_server* s);
+
 /* -------------------------------------------------- stateless device ops */
 /* A box of the packed layout used by the stateless ops: origin in [0, N) per
  * axis, dims 1..N per axis (nx <= 0: an unused entry), and the element offset

@@ -1,0 +1,318 @@
+// Serving: continuous batching of independent simulations on one GPU.
+//
+// A server owns a scheduler thread.  Submitted requests (a configuration,
+// a number of steps and dt) wait in a FIFO queue; the scheduler admits the
+// head of the queue as soon as the sum of the HBM estimates of the active
+// requests plus its own stays within the budget and a slot is free, creates
+// its microstructure (boxes resident on the device from then on), and keeps
+// every active request's stream fed with chunks of steps (CUDA-graph replays),
+// so work from different requests overlaps on the device.  A request that
+// has run all its steps has its grain volumes copied out and its device
+// memory released, which admits the next ones.  The paper has no serving
+// layer; this is the request loop around Algorithm 1.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lsgg.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    int64_t ticket = 0;
+    lsgg_config cfg{};
+    std::vector<double> seeds, weights, quats, energy;
+    int32_t n_steps = 0;
+    double dt = 1.0;
+    int64_t estimate = 0;
+    // progress
+    int32_t state = 0;                // 0 queued, 1 running, 2 done, < 0 failed (status code)
+    lsgg_ctx* ctx = nullptr;
+    int32_t enqueued = 0;
+    int64_t device_bytes = 0;
+    int64_t cell_updates = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    std::vector<double> volumes;
+};
+
+int64_t estimate_bytes(const lsgg_config& c) {
+    // arena X, Y, ID-field at ~12 box cells per domain cell with 1.5x slack, the
+    // 16-byte neighbour-max field, init temporaries (labels, neighbour bits)
+    const int64_t ncell = (int64_t)c.nx * c.ny * c.nz;
+    const int64_t g = c.n_grains;
+    return 3 * 4 * 18 * ncell + 16 * ncell + 4 * ncell + g * ((g + 31) / 32) * 4 + (64LL << 20);
+}
+
+double seconds_since(Clock::time_point t0) {
+    return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+}  // namespace
+
+struct lsgg_server {
+    int64_t budget = 0;
+    int32_t max_active = 0;
+    int32_t steps_per_round = 0;
+    int32_t device = 0;
+    Clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::vector<std::shared_ptr<Request>> active;
+    std::map<int64_t, std::shared_ptr<Request>> all;
+    int64_t next_ticket = 1;
+    int64_t used = 0;
+    int64_t peak_used = 0;
+    int64_t completed = 0;
+    int64_t cell_updates = 0;
+    bool stop = false;
+    std::thread worker;
+
+    void run();
+    bool admit_one(std::unique_lock<std::mutex>& lk);
+};
+
+bool lsgg_server::admit_one(std::unique_lock<std::mutex>& lk) {
+    if (queue.empty() || (int32_t)active.size() >= max_active) return false;
+    std::shared_ptr<Request> r = queue.front();
+    if (r->estimate > budget) {               // can never fit
+        queue.pop_front();
+        r->state = LSGG_ERR_OVER_BUDGET;
+        r->t_done = seconds_since(t0);
+        cv_done.notify_all();
+        return true;
+    }
+    if (used + r->estimate > budget) return false;
+    queue.pop_front();
+    used += r->estimate;
+    peak_used = std::max(peak_used, used);
+    lsgg_config cfg = r->cfg;
+    cfg.seeds = r->seeds.empty() ? nullptr : r->seeds.data();
+    cfg.weights = r->weights.empty() ? nullptr : r->weights.data();
+    cfg.quats = r->quats.empty() ? nullptr : r->quats.data();
+    cfg.energy = r->energy.empty() ? nullptr : r->energy.data();
+    cfg.device = device;
+    lk.unlock();
+    lsgg_ctx* ctx = nullptr;
+    int st = lsgg_create_microstructure(&cfg, nullptr, &ctx);
+    lk.lock();
+    if (st != LSGG_OK) {
+        used -= r->estimate;
+        r->state = st;
+        r->t_done = seconds_since(t0);
+        cv_done.notify_all();
+        return true;
+    }
+    r->ctx = ctx;
+    r->state = 1;
+    r->t_admit = seconds_since(t0);
+    lsgg_stats s{};
+    if (lsgg_get_stats(ctx, &s) == LSGG_OK) r->device_bytes = s.device_bytes;
+    active.push_back(r);
+    return true;
+}
+
+void lsgg_server::run() {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (!stop) {
+        bool progress = false;
+        while (admit_one(lk)) progress = true;
+        // feed idle streams, retire finished requests
+        for (size_t k = 0; k < active.size();) {
+            std::shared_ptr<Request> r = active[k];
+            cudaStream_t s = (cudaStream_t)lsgg_get_stream(r->ctx);
+            cudaError_t q = cudaStreamQuery(s);
+            if (q == cudaErrorNotReady) { ++k; continue; }
+            if (q != cudaSuccess) cudaGetLastError();
+            if (r->enqueued < r->n_steps) {
+                const int32_t chunk = std::min(steps_per_round, r->n_steps - r->enqueued);
+                int st = lsgg_step(r->ctx, chunk, r->dt);
+                if (st == LSGG_OK) {
+                    r->enqueued += chunk;
+                    progress = true;
+                    ++k;
+                    continue;
+                }
+                r->state = st;
+            }
+            // all steps enqueued and the stream is idle: finish (grows the arena if a step overflowed it)
+            lk.unlock();
+            int st = r->state < 0 ? r->state : lsgg_sync(r->ctx, -1);
+            std::vector<double> vol((size_t)r->cfg.n_grains);
+            int64_t n = 0;
+            lsgg_stats rs{};
+            if (st == LSGG_OK) st = lsgg_get_stats(r->ctx, &rs);
+            if (st == LSGG_OK && rs.steps_done < r->n_steps) {   // resumed after an arena overflow
+                lk.lock();
+                ++k;
+                continue;
+            }
+            if (st == LSGG_OK) st = lsgg_grain_volumes(r->ctx, vol.data(), (int64_t)vol.size(), &n);
+            lsgg_destroy(r->ctx);
+            lk.lock();
+            r->ctx = nullptr;
+            r->volumes.swap(vol);
+            r->cell_updates = rs.cell_updates;
+            r->state = st == LSGG_OK ? 2 : st;
+            r->t_done = seconds_since(t0);
+            used -= r->estimate;
+            ++completed;
+            cell_updates += rs.cell_updates;
+            active.erase(active.begin() + (long)k);
+            cv_done.notify_all();
+            progress = true;
+        }
+        if (!progress) cv_work.wait_for(lk, std::chrono::microseconds(200));
+    }
+    for (auto& r : active) {
+        lk.unlock();
+        lsgg_destroy(r->ctx);
+        lk.lock();
+        r->ctx = nullptr;
+        r->state = LSGG_ERR_NOT_READY;
+    }
+    active.clear();
+}
+
+extern "C" {
+
+int lsgg_server_create(int64_t budget_bytes, int32_t max_active, int32_t steps_per_round, int32_t device,
+                       lsgg_server** out) {
+    if (!out || budget_bytes <= 0 || max_active < 1 || steps_per_round < 1) return LSGG_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return LSGG_ERR_CUDA;
+    }
+    lsgg_server* s = new lsgg_server();
+    s->budget = budget_bytes;
+    s->max_active = max_active;
+    s->steps_per_round = steps_per_round;
+    s->device = device;
+    s->t0 = Clock::now();
+    s->worker = std::thread([s] { s->run(); });
+    *out = s;
+    return LSGG_OK;
+}
+
+int lsgg_server_submit(lsgg_server* s, const lsgg_config* cfg, int32_t n_steps, double dt, int64_t* ticket) {
+    if (!s || !cfg || !ticket || n_steps < 0 || !(dt > 0.0) || dt > 4.0) return LSGG_ERR_INVALID_ARG;
+    if (cfg->n_grains < 1 || cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return LSGG_ERR_INVALID_ARG;
+    auto r = std::make_shared<Request>();
+    r->cfg = *cfg;
+    const size_t g = (size_t)cfg->n_grains;
+    if (cfg->seeds) r->seeds.assign(cfg->seeds, cfg->seeds + 3 * g);
+    if (cfg->weights) r->weights.assign(cfg->weights, cfg->weights + g);
+    if (cfg->quats) r->quats.assign(cfg->quats, cfg->quats + 4 * g);
+    if (cfg->energy) r->energy.assign(cfg->energy, cfg->energy + g);
+    r->n_steps = n_steps;
+    r->dt = dt;
+    r->estimate = estimate_bytes(*cfg);
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->ticket = s->next_ticket++;
+    r->t_submit = seconds_since(s->t0);
+    s->queue.push_back(r);
+    s->all[r->ticket] = r;
+    *ticket = r->ticket;
+    s->cv_work.notify_all();
+    return LSGG_OK;
+}
+
+static void fill_info(const Request& r, lsgg_request_info* info) {
+    if (!info) return;
+    info->state = r.state;
+    info->t_submit = r.t_submit;
+    info->t_admit = r.t_admit;
+    info->t_done = r.t_done;
+    info->cell_updates = r.cell_updates;
+    info->device_bytes = r.device_bytes;
+    info->estimate_bytes = r.estimate;
+}
+
+int lsgg_server_wait(lsgg_server* s, int64_t ticket, int64_t timeout_ms, lsgg_request_info* info) {
+    if (!s) return LSGG_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return LSGG_ERR_INVALID_ARG;
+    std::shared_ptr<Request> r = it->second;
+    auto done = [&] { return r->state == 2 || r->state < 0; };
+    if (timeout_ms < 0) s->cv_done.wait(lk, done);
+    else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+        fill_info(*r, info);
+        return LSGG_ERR_TIMEOUT;
+    }
+    fill_info(*r, info);
+    return r->state < 0 ? r->state : LSGG_OK;
+}
+
+int lsgg_server_poll(lsgg_server* s, int64_t ticket, lsgg_request_info* info) {
+    if (!s) return LSGG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return LSGG_ERR_INVALID_ARG;
+    fill_info(*it->second, info);
+    if (it->second->state < 0) return it->second->state;
+    return it->second->state == 2 ? LSGG_OK : LSGG_ERR_NOT_READY;
+}
+
+int lsgg_server_volumes(lsgg_server* s, int64_t ticket, double* out, int64_t cap, int64_t* n_out) {
+    if (!s) return LSGG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return LSGG_ERR_INVALID_ARG;
+    const Request& r = *it->second;
+    if (r.state != 2) return r.state < 0 ? r.state : LSGG_ERR_NOT_READY;
+    if (n_out) *n_out = (int64_t)r.volumes.size();
+    if (!out || cap < (int64_t)r.volumes.size()) return LSGG_ERR_CAPACITY;
+    std::memcpy(out, r.volumes.data(), r.volumes.size() * sizeof(double));
+    return LSGG_OK;
+}
+
+int lsgg_server_release(lsgg_server* s, int64_t ticket) {
+    if (!s) return LSGG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return LSGG_ERR_INVALID_ARG;
+    if (it->second->state == 0 || it->second->state == 1) return LSGG_ERR_NOT_READY;
+    s->all.erase(it);
+    return LSGG_OK;
+}
+
+int lsgg_server_get_stats(lsgg_server* s, lsgg_server_stats* out) {
+    if (!s || !out) return LSGG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->queued = (int64_t)s->queue.size();
+    out->active = (int64_t)s->active.size();
+    out->completed = s->completed;
+    out->used_bytes = s->used;
+    out->peak_bytes = s->peak_used;
+    out->cell_updates = s->cell_updates;
+    return LSGG_OK;
+}
+
+int lsgg_server_destroy(lsgg_server* s) {
+    if (!s) return LSGG_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv_work.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    delete s;
+    return LSGG_OK;
+}
+
+}  // extern "C"

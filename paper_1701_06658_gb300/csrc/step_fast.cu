@@ -170,6 +170,10 @@ k_predict_fast(StepBuffers B, Taps taps, PhysicsDev phys, int cls) {
         const bool own = y0 < ny;
         const int nxs = (nx + kVX - 1) / kVX;
         float ring[W][V];
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+#pragma unroll
+            for (int v = 0; v < V; ++v) ring[k][v] = 0.0f;
         // second-key atomics of the previous output plane, issued one plane late
         // so the first atomics' return values arrive while this plane is computed
         unsigned long long pend_old[V];
@@ -404,6 +408,8 @@ k_correct_fast(StepBuffers B, PhysicsDev phys, DebugOut dbg, int cls) {
         int slot = 0;
         // field records of the owned cells of the next stage-A plane, loaded a plane early
         ulonglong2 tk[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) tk[v] = make_ulonglong2(0ull, 0ull);
         auto load_t = [&](int zin) {
             const int zl = a_plane(zin);
             if (!own || zl < 0 || zin > z_last || !a_wanted(zin)) return;
@@ -643,7 +649,7 @@ static FastInstance fast_instance(int cls) {
             return {(const void*)k_predict_fast<5, 4, 256, 32, 2>, (const void*)k_correct_fast<4, 256, 32, 2>,
                     PredictLayout<32, 5>::bytes, CorrectLayout<32>::bytes, 256};
         case 1:
-            return {(const void*)k_predict_fast<5, 5, 320, 40, 2>, (const void*)k_correct_fast<5, 320, 40, 1>,
+            return {(const void*)k_predict_fast<5, 5, 320, 40, 1>, (const void*)k_correct_fast<5, 320, 40, 1>,
                     PredictLayout<40, 5>::bytes, CorrectLayout<40>::bytes, 320};
         case 2:
             return {(const void*)k_predict_fast<5, 6, 384, 48, 1>, (const void*)k_correct_fast<6, 384, 48, 1>,

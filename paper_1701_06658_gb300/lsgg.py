@@ -94,6 +94,14 @@ _SIGS = {
                                      C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lsgg_neighbour_max_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
                                              C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lsgg_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
+    "lsgg_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Config), C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
+    "lsgg_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "lsgg_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]),
+    "lsgg_server_volumes": (C.c_int, [C.c_void_p, C.c_int64, _dp, C.c_int64, C.POINTER(C.c_int64)]),
+    "lsgg_server_release": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lsgg_server_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lsgg_server_destroy": (C.c_int, [C.c_void_p]),
     "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
 }
@@ -379,3 +387,78 @@ class Microstructure:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- serving
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("cell_updates", C.c_int64), ("device_bytes", C.c_int64), ("estimate_bytes", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("completed", C.c_int64),
+                ("used_bytes", C.c_int64), ("peak_bytes", C.c_int64), ("cell_updates", C.c_int64)]
+
+
+class Server:
+    """lsgg_server_*: continuous batching of independent simulations under an HBM budget."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 64, steps_per_round: int = 4, device: int = 0):
+        h = C.c_void_p()
+        _check("server_create", lib().lsgg_server_create(int(budget_bytes), max_active, steps_per_round, device,
+                                                          C.byref(h)))
+        self.h = h
+        self._n_grains = {}
+
+    def submit(self, nx: int, ny: int, nz: int, n_grains: int, n_steps: int, dt: float = 1.0, seed: int = 1,
+               seeds=None, **fields) -> int:
+        cfg = config_default()
+        cfg.nx, cfg.ny, cfg.nz, cfg.n_grains, cfg.seed = nx, ny, nz, n_grains, seed
+        for k, v in fields.items():
+            setattr(cfg, k, v)
+        keep = None
+        if seeds is not None:
+            keep = np.ascontiguousarray(seeds, dtype=np.float64)
+            cfg.seeds = _ptr(keep, C.c_double)
+        t = C.c_int64()
+        _check("server_submit", lib().lsgg_server_submit(self.h, C.byref(cfg), int(n_steps), float(dt), C.byref(t)))
+        self._n_grains[t.value] = n_grains
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> RequestInfo:
+        info = RequestInfo()
+        _check("server_wait", lib().lsgg_server_wait(self.h, ticket, timeout_ms, C.byref(info)))
+        return info
+
+    def poll(self, ticket: int):
+        info = RequestInfo()
+        code = lib().lsgg_server_poll(self.h, ticket, C.byref(info))
+        return code, info
+
+    def volumes(self, ticket: int) -> np.ndarray:
+        out = np.zeros(self._n_grains[ticket], np.float64)
+        n = C.c_int64()
+        _check("server_volumes", lib().lsgg_server_volumes(self.h, ticket, _ptr(out, C.c_double), out.size,
+                                                            C.byref(n)))
+        return out
+
+    def release(self, ticket: int):
+        _check("server_release", lib().lsgg_server_release(self.h, ticket))
+        self._n_grains.pop(ticket, None)
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        _check("server_get_stats", lib().lsgg_server_get_stats(self.h, C.byref(s)))
+        return s
+
+    def close(self):
+        if self.h is not None:
+            lib().lsgg_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

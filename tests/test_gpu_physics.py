@@ -1,0 +1,107 @@
+"""GPU parity of the physics variants of Eq. (10) and of the power-diagram
+initialisation against the FP64 oracle, on identical seeded inputs.
+
+Both sides start from their own initialisation of the same seeds (the GPU's
+initial phi equals the oracle's cast to FP32, and both take the initial
+ID-field as the minimising bisector neighbour), then advance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lsgg_oracle as O
+from paper_1701_06658_gb300 import inputs as I
+from tests.parity import box_full, sign_flip_exclusion
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1701_06658_gb300 import lsgg
+    lsgg.lib()
+    return lsgg
+
+
+def _compare_step(L, ms, ref_ms, dt=1.0, tol_p=3e-5):
+    ref = O.step_parts(ref_ms, dt)
+    b, (phip, m, idm, phic, phin) = ms.debug_step(dt)
+    for g in phin:
+        assert np.max(np.abs(phip[g] - ref.phip[g])) <= tol_p, g
+        assert np.max(np.abs(phic[g] - ref.phic[g])) <= tol_p, g
+        excl = sign_flip_exclusion(ref.phic[g], phic[g], box_full(b[g], ms.shape))
+        d = np.abs(phin[g] - ref.phi[g])
+        d[excl] = 0
+        assert d.max() <= 1e-4, g
+    return ref
+
+
+def test_read_shockley_step_matches_oracle(L):
+    """Read-Shockley energy, mobility 0.1 below 15 deg, cubic disorientation
+    from seeded random orientations: one step, every stage within tolerance."""
+    N, G = 40, 20
+    seeds = I.voronoi_seeds(31, G, (N, N, N))
+    quats = I.random_quaternions(31, G)
+    ref_ms = O.tessellate((N, N, N), seeds, physics=O.read_shockley_physics(quats))
+    with L.Microstructure(N, N, N, G, seeds=seeds, quats=quats, physics=L.PHYSICS_READ_SHOCKLEY) as ms:
+        _compare_step(L, ms, ref_ms)
+
+
+def test_read_shockley_eq20_mobility_step(L):
+    N, G = 32, 12
+    seeds = I.voronoi_seeds(32, G, (N, N, N))
+    quats = I.random_quaternions(32, G)
+    ref_ms = O.tessellate((N, N, N), seeds, physics=O.read_shockley_physics(quats, mobility="eq20"))
+    with L.Microstructure(N, N, N, G, seeds=seeds, quats=quats, physics=L.PHYSICS_READ_SHOCKLEY,
+                          mobility_law=L.MOBILITY_EQ20) as ms:
+        _compare_step(L, ms, ref_ms)
+
+
+def test_read_shockley_volumes_after_10_steps(L):
+    N, G, steps = 40, 20, 10
+    seeds = I.voronoi_seeds(33, G, (N, N, N))
+    quats = I.random_quaternions(33, G)
+    ref = O.run(O.tessellate((N, N, N), seeds, physics=O.read_shockley_physics(quats)), steps, 1.0)
+    with L.Microstructure(N, N, N, G, seeds=seeds, quats=quats, physics=L.PHYSICS_READ_SHOCKLEY) as ms:
+        ms.step(steps, 1.0)
+        vg = ms.grain_volumes()
+    vo = O.volumes(ref)
+    big = vo > 50
+    assert np.max(np.abs(vg - vo)[big] / vo[big]) <= 1e-3
+    assert np.all(np.abs(vg - vo)[~big] <= 0.05)
+
+
+def test_magnetic_step_matches_oracle(L):
+    """Per-grain bulk energies E_i = E_max h / gamma * cos^2(c-axis, field)
+    (Eqs. (13), (18)), field (0, cos 32 deg, sin 32 deg): one step."""
+    N, G = 40, 20
+    seeds = I.voronoi_seeds(34, G, (N, N, N))
+    quats = I.random_quaternions(34, G)
+    f = np.array([0.0, math.cos(math.radians(32)), math.sin(math.radians(32))])
+    scale = 0.05
+    energy = np.array([scale * float(np.dot(O.c_axis(q), f)) ** 2 for q in quats])
+    ref_ms = O.tessellate((N, N, N), seeds, physics=O.isotropic_physics(energy))
+    with L.Microstructure(N, N, N, G, seeds=seeds, quats=quats, physics=L.PHYSICS_MAGNETIC, energy_scale=scale,
+                          field_dir=f) as ms:
+        _compare_step(L, ms, ref_ms)
+
+
+def test_laguerre_init_matches_oracle(L):
+    """Power diagram of seeds with lognormal radii (5 % enlarged): boxes exact, phi = oracle in FP32."""
+    N, G = 48, 40
+    seeds = I.voronoi_seeds(35, G, (N, N, N))
+    w = I.laguerre_weights(35, G, (N, N, N), sigma=0.5, big_fraction=0.05)
+    ref = O.tessellate((N, N, N), seeds, weights=w)
+    with L.Microstructure(N, N, N, G, seeds=seeds, weights=w) as ms:
+        boxes = ms.boxes()
+        phi = ms.phi()
+    for g, gr in enumerate(ref.grains):
+        assert bool(boxes[g, 0]) == gr.alive
+        if gr.alive:
+            assert (boxes[g, 3], boxes[g, 2], boxes[g, 1]) == gr.origin
+            assert (boxes[g, 6], boxes[g, 5], boxes[g, 4]) == gr.dims
+            assert np.max(np.abs(phi[g] - gr.phi.astype(np.float32))) <= 1e-6

@@ -1,0 +1,71 @@
+"""GPU tests of the serving loop: continuous batching under an HBM budget.
+
+Each request's result must be the same alone and in a mix with others that
+overlap it on the device (bit for bit: the requests share no state and run
+the same kernels); requests larger than the budget are refused; a small
+budget serialises admissions without changing results.
+"""
+import numpy as np
+import pytest
+
+from paper_1701_06658_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1701_06658_gb300 import lsgg
+    lsgg.lib()
+    return lsgg
+
+
+MIX = [(48, 30, 7, 12), (32, 20, 8, 30), (64, 60, 9, 9), (40, 25, 10, 17), (56, 40, 11, 5), (32, 20, 12, 21)]
+
+
+def _direct(L, n, g, seed, steps):
+    with L.Microstructure(n, n, n, g, seeds=I.voronoi_seeds(seed, g, (n, n, n))) as ms:
+        ms.step(steps, 1.0)
+        return ms.grain_volumes()
+
+
+def test_result_alone_equals_result_in_the_mix(L):
+    n, g, seed, steps = MIX[0]
+    seeds = I.voronoi_seeds(seed, g, (n, n, n))
+    with L.Server(budget_bytes=8 << 30, max_active=8, steps_per_round=3) as srv:
+        t = srv.submit(n, n, n, g, steps, seeds=seeds)
+        srv.wait(t)
+        alone = srv.volumes(t)
+        tickets = []
+        for (nn, gg, sd, st) in MIX:
+            tickets.append(srv.submit(nn, nn, nn, gg, st, seeds=I.voronoi_seeds(sd, gg, (nn, nn, nn))))
+        infos = [srv.wait(tk) for tk in tickets]
+        mixed = srv.volumes(tickets[0])
+        # the requests did overlap: some were admitted before others finished
+        assert min(i.t_done for i in infos) > max(i.t_admit for i in infos[:3])
+        assert np.array_equal(alone, mixed)
+        assert np.array_equal(alone, _direct(L, n, g, seed, steps))
+        for (nn, gg, sd, st), tk in zip(MIX[1:3], tickets[1:3]):
+            assert np.array_equal(srv.volumes(tk), _direct(L, nn, gg, sd, st))
+        s = srv.stats()
+        assert s.completed == len(MIX) + 1 and s.active == 0 and s.queued == 0
+
+
+def test_budget_serialises_and_refuses(L):
+    n, g, seed, steps = MIX[1]
+    seeds = I.voronoi_seeds(seed, g, (n, n, n))
+    # room for about one 32^3 request at a time
+    with L.Server(budget_bytes=(64 << 20) + 3 * 4 * 18 * 32 ** 3 + 21 * 32 ** 3 + 4096, max_active=8,
+                  steps_per_round=5) as srv:
+        a = srv.submit(n, n, n, g, steps, seeds=seeds)
+        b = srv.submit(n, n, n, g, steps, seeds=seeds)
+        big = srv.submit(128, 128, 128, 200, 2)
+        ia, ib = srv.wait(a), srv.wait(b)
+        assert ib.t_admit >= ia.t_done          # the second waited for the first's memory
+        assert np.array_equal(srv.volumes(a), srv.volumes(b))
+        with pytest.raises(L.LsggError) as e:
+            srv.wait(big)
+        assert e.value.code == L.ERR_OVER_BUDGET
