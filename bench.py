@@ -209,6 +209,8 @@ def gpu_arm(args):
     stream = torch.cuda.ExternalStream(ms.stream)
     ms.step(args.warmup, dt)
     ms.sync()
+    tiles = L.autotune(ms.ctx, 2, dt) if not args.no_tune else None   # untimed: 6 real steps
+    ms.sync()
     s0 = ms.stats()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -293,6 +295,7 @@ def gpu_arm(args):
         "box_cells_per_step": box_cells_mean,
         "superimposition": box_cells_mean / dom_cells,
         "kernel_ms_per_step": {k: v / max(1, kprof) for k, v in ktimes.items()},
+        "tile_variants": tiles,
         "gpu_launches": int(sum(kcount.values()) * args.steps / max(1, kprof)),
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
                      "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
@@ -360,6 +363,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
+    ap.add_argument("--no-tune", action="store_true", help="skip the tile autotuner")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving measurement (0: skip; 256: the full serving workload)")
     ap.add_argument("--workload", default="256", choices=sorted(WORKLOADS),

@@ -165,7 +165,26 @@ int lsgg_get_stats(lsgg_ctx* ctx, lsgg_stats* out);
  * kernel launches of the library in that group (any pointer may be NULL),
  * over the steps since the previous call; then resets the sums. */
 int lsgg_profile(lsgg_ctx* ctx, int32_t enable);
+
+/* Tile autotuner of the batched path: for every box-size class served by the
+ * register-ring kernels, runs steps_per_trial real steps with each tile
+ * variant (cells per thread, threads per CTA), times each class's kernels
+ * with CUDA events on its stream, and keeps the fastest variant per class and
+ * kernel.  Variants give bit-identical results, so the tuning steps are
+ * ordinary steps of the simulation (3 * steps_per_trial of them, time dt).
+ * chosen (optional, 2 x 8 int32): variant per kernel (predictor, corrector)
+ * and class, -1 for classes not served by these kernels.  Synchronises. */
+int lsgg_autotune(lsgg_ctx* ctx, int32_t steps_per_trial, double dt, int32_t* chosen);
 int lsgg_kernel_times(lsgg_ctx* ctx, double* out_ms, int64_t* out_count);
+
+/* Contact neighbours of every grain after the last completed step (Sec. 3.1's
+ * neighbourhood from the points of contact): the distinct grains j != i that
+ * are the largest other function somewhere in grain i's box with a value above
+ * -eps -- the ids of its ID-field.  counts[i] = number of neighbours (at most
+ * cap_per_grain are stored, ascending, at ids[i * cap_per_grain ...]; a count
+ * above cap_per_grain means the list was cut).  Needs a step since creation
+ * or lsgg_set_state (else LSGG_ERR_NOT_READY).  Synchronises. */
+int lsgg_grain_neighbours(lsgg_ctx* ctx, int32_t* counts, int32_t* ids, int32_t cap_per_grain);
 
 /* Boxes of all grains: out[7*i .. 7*i+6] = alive, ox, oy, oz, nx, ny, nz
  * (origin in [0, N) per axis).  cap in int32s, >= 7 * n_grains.  Synchronises. */

@@ -33,6 +33,8 @@ cudaError_t launch_pack_cur(int G, const Box* cur, const void* arena, const long
 cudaError_t launch_unpack_state(int G, const Box* cur, const float* packed, const int* packed_idf,
                                 const long long* packed_off, float* X, int* IDF, cudaStream_t s);
 long long large_class_scratch_floats(const Domain& d);
+cudaError_t launch_field_neighbours(const StepBuffers& B, const Box* boxes, int cap, int* tab, int* cnt,
+                                    cudaStream_t s);
 cudaError_t launch_plain_step_impl(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
                                    const Box* h_cur, const Box* h_prev, float* t1, float* t2, float* Cc,
                                    float* Gg, float* Hh, cudaStream_t s);
@@ -58,6 +60,7 @@ struct lsgg_ctx {
     double* d_vol = nullptr;
     long long* d_packed_off = nullptr;
     StepState* h_st = nullptr;       // pinned mirror for status reads
+    bool field_valid = false;        // T holds the field of the last completed step
     long long steps_target = 0;      // steps requested since creation
     double last_dt = 0.0;
     long long device_bytes = 0;
@@ -500,6 +503,7 @@ int lsgg_step(lsgg_ctx* c, int32_t n, double dt) {
     if (cudaSetDevice(c->device) != cudaSuccess) return LSGG_ERR_CUDA;
     c->steps_target += n;
     c->last_dt = dt;
+    c->field_valid = true;
     return enqueue_steps(c, n, dt, nullptr);
 }
 
@@ -553,6 +557,60 @@ int lsgg_get_stats(lsgg_ctx* c, lsgg_stats* out) {
     return LSGG_OK;
 }
 
+int lsgg_autotune(lsgg_ctx* c, int32_t steps_per_trial, double dt, int32_t* chosen) {
+    if (!c || steps_per_trial < 1 || !(dt > 0.0) || dt > 4.0) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LSGG_ERR_CUDA;
+    const int nv = StepBuffers::kVariants;
+    const int ne = 4 * kNumClasses;
+    std::vector<cudaEvent_t> ev((size_t)ne * steps_per_trial);
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return LSGG_ERR_CUDA;
+    double best_ms[2][kNumClasses];
+    int best_v[2][kNumClasses];
+    for (int w = 0; w < 2; ++w)
+        for (int k = 0; k < kNumClasses; ++k) { best_ms[w][k] = 1e300; best_v[w][k] = c->B.variant[w][k]; }
+    Taps taps = make_taps(dt, c->dom.radius);
+    c->phys.dt = (float)dt;
+    int status = LSGG_OK;
+    for (int v = 0; v < nv && status == LSGG_OK; ++v) {
+        for (int w = 0; w < 2; ++w)
+            for (int k = 0; k < kNumClasses; ++k)
+                if (c->B.mode[k] == 0 && configure_fast_variant(c->B, w, k, v) != cudaSuccess) status = LSGG_ERR_CUDA;
+        if (status != LSGG_OK) break;
+        for (int sidx = 0; sidx < steps_per_trial; ++sidx) {
+            c->steps_target += 1;
+            if (launch_step(c->B, taps, c->phys, nullptr, c->stream, nullptr, &c->ss, ev.data() + (size_t)sidx * ne) !=
+                cudaSuccess) { status = LSGG_ERR_CUDA; break; }
+        }
+        if (status != LSGG_OK) break;
+        status = lsgg_sync(c, -1);
+        if (status != LSGG_OK) break;
+        for (int w = 0; w < 2; ++w)
+            for (int k = 0; k < kNumClasses; ++k) {
+                if (c->B.mode[k] != 0) continue;
+                double tot = 0.0;
+                for (int sidx = 0; sidx < steps_per_trial; ++sidx) {
+                    float ms = 0.0f;
+                    cudaEvent_t* e = ev.data() + (size_t)sidx * ne + (w * kNumClasses + k) * 2;
+                    if (cudaEventElapsedTime(&ms, e[0], e[1]) == cudaSuccess) tot += ms;
+                }
+                if (tot < best_ms[w][k]) { best_ms[w][k] = tot; best_v[w][k] = v; }
+            }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int w = 0; w < 2; ++w)
+        for (int k = 0; k < kNumClasses; ++k) {
+            if (c->B.mode[k] == 0 && configure_fast_variant(c->B, w, k, best_v[w][k]) != cudaSuccess) status = LSGG_ERR_CUDA;
+            if (chosen) chosen[w * kNumClasses + k] = c->B.mode[k] == 0 ? best_v[w][k] : -1;
+        }
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    c->field_valid = true;
+    c->last_dt = dt;
+    return status;
+}
+
 int lsgg_profile(lsgg_ctx* c, int32_t enable) {
     if (!c) return LSGG_ERR_INVALID_ARG;
     c->profiling = enable != 0;
@@ -581,6 +639,26 @@ int lsgg_kernel_times(lsgg_ctx* c, double* out_ms, int64_t* out_count) {
         c->acc_cnt[g] = 0;
     }
     return LSGG_OK;
+}
+
+int lsgg_grain_neighbours(lsgg_ctx* c, int32_t* counts, int32_t* ids, int32_t cap_per_grain) {
+    if (!c || !counts || !ids || cap_per_grain < 1) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    if (!c->field_valid) return LSGG_ERR_NOT_READY;
+    int *dt = nullptr, *dc = nullptr;
+    if ((r = dalloc(c, &dt, (size_t)c->G * cap_per_grain)) != LSGG_OK) return r;
+    if ((r = dalloc(c, &dc, (size_t)c->G)) != LSGG_OK) { dfree(c, dt); return r; }
+    // the boxes the last step ran on (its field covers them): the prev table
+    cudaError_t e = launch_field_neighbours(c->B, c->B.prev, cap_per_grain, dt, dc, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, dc, (size_t)c->G * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ids, dt, (size_t)c->G * cap_per_grain * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->device_bytes -= (long long)c->G * (cap_per_grain + 1) * 4;
+    dfree(c, dt);
+    dfree(c, dc);
+    return e == cudaSuccess ? LSGG_OK : LSGG_ERR_CUDA;
 }
 
 int lsgg_get_boxes(lsgg_ctx* c, int32_t* out, int64_t cap) {
@@ -661,6 +739,7 @@ int lsgg_set_state(lsgg_ctx* c, const int32_t* boxes, const float* phi, const in
     CK(launch_unpack_state(c->G, c->B.cur, dphi, didf, c->d_packed_off, c->B.X, c->B.IDF, c->stream));
     CK(cudaMemcpyAsync(c->B.prev, c->B.cur, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    c->field_valid = false;
     c->device_bytes -= off[c->G] * 4 * (idf ? 2 : 1);
     dfree(c, dphi);
     dfree(c, didf);
@@ -681,6 +760,7 @@ int lsgg_debug_step(lsgg_ctx* c, double dt, float* phip, float* m, int32_t* idm,
     dbg.phin = base + 4 * c->B.cap;
     c->steps_target += 1;
     c->last_dt = dt;
+    c->field_valid = true;
     r = enqueue_steps(c, 1, dt, &dbg);
     if (r == LSGG_OK) r = lsgg_sync(c, -1);
     if (r == LSGG_OK) {
@@ -725,6 +805,7 @@ int lsgg_voxel_owner(lsgg_ctx* c, int32_t* out, int64_t n_cells) {
     int* d = nullptr;
     if ((r = dalloc(c, &d, (size_t)n)) != LSGG_OK) return r;
     cudaError_t e = launch_owner(c->dom, c->G, c->B.cur, c->B.prev, c->B.X, c->B.T, d, c->stream);
+    c->field_valid = false;        // the owner map reused the field's memory
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     c->device_bytes -= n * 4;

@@ -134,7 +134,10 @@ struct StepBuffers {
     int n_sm;
     int class_side[kNumClasses];    // largest box side per class (last: whole domain)
     int mode[kNumClasses];          // 0: register-ring kernels, 1: shared-memory ring, 2: global scratch ring
-    int block[kNumClasses];         // threads per CTA
+    int block[kNumClasses];         // threads per CTA (shared-memory / global rings)
+    int fblock[2][kNumClasses];     // threads per CTA of the register-ring kernels
+    int variant[2][kNumClasses];    // tile variant of the register-ring kernels (autotuned)
+    static constexpr int kVariants = 3;
     int grid[2][kNumClasses];       // persistent grid per kernel and class
     size_t smem[2][kNumClasses];
 };
@@ -150,11 +153,15 @@ struct StepStreams {
 // ev (optional, 5 events): recorded before the field clear, after it, after the
 // predictor launches, after the corrector launches and after the box update.
 // ss (optional): run each phase's class kernels concurrently on side streams.
+// cls_ev (optional, 4 * kNumClasses events): start / end of each class kernel of
+// each phase, recorded on the class's stream: [(which * kNumClasses + c) * 2 + {0, 1}].
 cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
                         const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev = nullptr,
-                        const StepStreams* ss = nullptr);
+                        const StepStreams* ss = nullptr, cudaEvent_t* cls_ev = nullptr);
 cudaError_t launch_box_update(const StepBuffers& B, bool commit_only_layout, cudaStream_t s);
 cudaError_t configure_step_kernels(StepBuffers& B);
+cudaError_t configure_fast_variant(StepBuffers& B, int which, int cls, int variant);
+int fast_class_side(int cls);
 cudaError_t launch_plain_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
                               const int* h_alive_boxes, int n_alive, cudaStream_t s);
 

@@ -57,6 +57,65 @@ k_collect_neighbours(const Box* __restrict__ prev, const int* __restrict__ IDF, 
     if (threadIdx.x == 0) cnt[b] = (overflow || n_keys > kNbCap) ? kNbCap + 1 : n_keys;
 }
 
+// Contact neighbours of each box from the neighbour-max field of the last step:
+// per cell the largest other grain above -eps (the step's ID-field).
+__global__ void __launch_bounds__(256)
+k_field_neighbours(Domain D, const Box* __restrict__ boxes, const unsigned long long* __restrict__ T, int cap,
+                   int* __restrict__ tab, int* __restrict__ cnt) {
+    __shared__ int keys[kHashSlots];
+    __shared__ int n_keys, overflow;
+    const int b = blockIdx.x;
+    const Box nb = boxes[b];
+    for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x) keys[k] = -1;
+    if (threadIdx.x == 0) { n_keys = 0; overflow = 0; }
+    __syncthreads();
+    if (nb.nx > 0) {
+        const long long A = (long long)nb.nx * nb.ny, n = A * nb.nz;
+        int last = -1;
+        for (long long c = threadIdx.x; c < n; c += blockDim.x) {
+            const int z = (int)(c / A);
+            const int rem = (int)(c - (long long)z * A);
+            const int y = rem / nb.nx, x = rem - y * nb.nx;
+            const long long g = ((long long)pmod(nb.oz + z, D.nz) * D.ny + pmod(nb.oy + y, D.ny)) * D.nx +
+                                pmod(nb.ox + x, D.nx);
+            const unsigned long long k1 = T[2 * g], k2 = T[2 * g + 1];
+            const int id1 = key_id(k1);
+            const unsigned long long kk = id1 != b ? k1 : k2;
+            if (!kk || !(key_val(kk, D.eps) > -D.eps)) continue;
+            const int j = key_id(kk);
+            if (j == last) continue;
+            last = j;
+            unsigned h = ((unsigned)j * 2654435761u) >> 23;
+            for (int probe = 0; probe < kHashSlots; ++probe) {
+                const int slot = (int)((h + probe) & (kHashSlots - 1));
+                const int cur = keys[slot];
+                if (cur == j) break;
+                if (cur == -1) {
+                    const int prevk = atomicCAS(&keys[slot], -1, j);
+                    if (prevk == -1) { atomicAdd(&n_keys, 1); break; }
+                    if (prevk == j) break;
+                }
+                if (probe == kHashSlots - 1) overflow = 1;
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x) {
+        const int j = keys[k];
+        if (j < 0) continue;
+        int rank = 0;
+        for (int q = 0; q < kHashSlots; ++q) rank += (unsigned)keys[q] < (unsigned)j && keys[q] >= 0;
+        if (rank < cap) tab[(size_t)b * cap + rank] = j;
+    }
+    if (threadIdx.x == 0) cnt[b] = overflow ? cap + 1 : n_keys;
+}
+
+cudaError_t launch_field_neighbours(const StepBuffers& B, const Box* boxes, int cap, int* tab, int* cnt,
+                                    cudaStream_t s) {
+    k_field_neighbours<<<B.n_boxes, 256, 0, s>>>(B.dom, boxes, B.T, cap, tab, cnt);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_collect_neighbours(const StepBuffers& B, const PhysicsDev& phys, cudaStream_t s) {
     k_collect_neighbours<<<B.n_boxes, 256, 0, s>>>(B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
                                                      const_cast<int*>(phys.nb_cnt));

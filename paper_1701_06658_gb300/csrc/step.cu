@@ -537,7 +537,6 @@ static size_t correct_smem_bytes(int side) {
     return ((size_t)2 * side + 4) * 4 + 16 + (size_t)12 * side * side * 4;
 }
 
-int fast_class_side(int cls);
 cudaError_t launch_collect_neighbours(const StepBuffers& B, const PhysicsDev& phys, cudaStream_t s);
 cudaError_t configure_fast(StepBuffers& B, int cls, int n_sm);
 cudaError_t launch_fast(const StepBuffers& B, int which, int cls, const Taps& taps, const PhysicsDev& phys,
@@ -625,7 +624,8 @@ cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream
 }
 
 cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
-                        const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev, const StepStreams* ss) {
+                        const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev, const StepStreams* ss,
+                        cudaEvent_t* cls_ev) {
     long long ncell = (long long)B.dom.nx * B.dom.ny * B.dom.nz;
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = cudaMemsetAsync(B.T, 0, (size_t)ncell * 16, s);
@@ -650,10 +650,12 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
                 if (r != cudaSuccess) return r;
             }
             cudaError_t r;
+            if (cls_ev) cudaEventRecord(cls_ev[(which * kNumClasses + c) * 2], cs);
             if (B.mode[c] == 0) r = launch_fast(B, which, c, taps, phys, d, cs);
             else if (which == 0) { k_predict<<<B.grid[0][c], kThreads, B.smem[0][c], cs>>>(B, taps, phys, c); r = cudaGetLastError(); }
             else { k_correct<<<B.grid[1][c], kThreads, B.smem[1][c], cs>>>(B, phys, d, c); r = cudaGetLastError(); }
             if (r != cudaSuccess) return r;
+            if (cls_ev) cudaEventRecord(cls_ev[(which * kNumClasses + c) * 2 + 1], cs);
             if (ss) {
                 r = cudaEventRecord(ss->join[c], cs);
                 if (r != cudaSuccess) return r;

@@ -102,6 +102,8 @@ _SIGS = {
     "lsgg_server_release": (C.c_int, [C.c_void_p, C.c_int64]),
     "lsgg_server_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lsgg_server_destroy": (C.c_int, [C.c_void_p]),
+    "lsgg_grain_neighbours": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32]),
+    "lsgg_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_int32)]),
     "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
 }
@@ -191,6 +193,13 @@ def get_stats(ctx) -> Stats:
     return s
 
 
+def autotune(ctx, steps_per_trial: int = 2, dt: float = 1.0) -> dict:
+    """Run the tile autotuner; returns {"k_predict": [...], "k_correct": [...]} variant per class."""
+    chosen = np.full(16, -1, np.int32)
+    _check("autotune", lib().lsgg_autotune(ctx, steps_per_trial, float(dt), _ptr(chosen, C.c_int32)))
+    return {"k_predict": chosen[0:5].tolist(), "k_correct": chosen[5:10].tolist()}
+
+
 def profile(ctx, enable: bool):
     _check("profile", lib().lsgg_profile(ctx, 1 if enable else 0))
 
@@ -232,6 +241,14 @@ def neighbour_max_noalloc(boxes_dev: int, n_boxes: int, phip_dev: int, n_elems: 
     any device allocation (its field is a static array of NOALLOC_MAX_CELLS cells)."""
     _check("neighbour_max_noalloc", lib().lsgg_neighbour_max_noalloc(boxes_dev, n_boxes, phip_dev, n_elems, nx, ny,
                                                                       nz, eps, m_dev, id_dev, stream or None))
+
+
+def grain_neighbours(ctx, n_grains: int, cap: int = 96) -> list:
+    """Contact neighbours (ascending ids) of every grain after the last step."""
+    counts = np.zeros(n_grains, np.int32)
+    ids = np.zeros((n_grains, cap), np.int32)
+    _check("grain_neighbours", lib().lsgg_grain_neighbours(ctx, _ptr(counts, C.c_int32), _ptr(ids, C.c_int32), cap))
+    return [ids[g, :min(int(counts[g]), cap)].tolist() for g in range(n_grains)]
 
 
 def get_boxes(ctx, n_grains: int) -> np.ndarray:
