@@ -205,7 +205,8 @@ def gpu_arm(args):
             dist.barrier()
 
     # ---------------- device-resident timing ----------------
-    ms = L.Microstructure(n, n, n, g, seeds=seeds, device=local)
+    exec_mode = {"batched": L.EXEC_BATCHED, "streamed": L.EXEC_STREAMED}[args.exec]
+    ms = L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=exec_mode)
     stream = torch.cuda.ExternalStream(ms.stream)
     ms.step(args.warmup, dt)
     ms.sync()
@@ -232,8 +233,10 @@ def gpu_arm(args):
     kprof = min(args.steps, 20)
     ms.step(kprof, dt)
     ktimes, kcount = L.kernel_times(ms.ctx)
+    ptimes = L.pass_times(ms.ctx)
     L.profile(ms.ctx, False)
     s2 = ms.stats()
+    tier_cells = list(s2.pass_cells)
     cells_prof = s2.cell_updates - s1.cell_updates
     ms.close()
 
@@ -243,7 +246,8 @@ def gpu_arm(args):
     e2e_s, e2e_cells, d2h = float("nan"), 0, 0
     if not args.no_e2e:
         t0 = time.perf_counter()
-        e2e = L.Microstructure(n, n, n, g, seeds=seeds, device=local)   # H2D of the seeds, init
+        e2e = L.Microstructure(n, n, n, g, seeds=seeds, device=local,    # H2D of the seeds, init
+                               exec_mode=exec_mode)
         for _ in range(args.steps):
             e2e.step(1, dt)
             vol = e2e.grain_volumes()                                      # D2H of the step's result
@@ -279,12 +283,31 @@ def gpu_arm(args):
     # roofline of the dominant kernel (algorithmic bytes: 8 B per box cell + 16 B per domain cell)
     peaks, src = measured_peaks()
     dom_cells = n ** 3
-    per_launch_ms = {k: ktimes[k] / max(1, kprof) for k in ("k_predict", "k_correct")}
-    dominant = max(per_launch_ms, key=per_launch_ms.get)
     box_cells_prof = cells_prof / kprof
-    alg_bytes = 8.0 * box_cells_prof + 16.0 * dom_cells
-    achieved = alg_bytes / (per_launch_ms[dominant] * 1e-3) / 1e9
-    traffic = profiled_traffic(dominant, box_cells_prof)
+    pass_ms = {name: v[0] / max(1, v[1]) for name, v in ptimes.items() if v[1] > 0}
+    if pass_ms:
+        # pass path: the per-tier passes move 8 B per box cell of their tier (one
+        # FP32 read, one FP32 write); the field pass reads phi_p twice, writes
+        # phi_c (12 B per box cell) and stores the 16-byte field per domain cell
+        dominant = max(pass_ms, key=pass_ms.get)
+        if dominant == "p_field":
+            units = box_cells_prof
+            alg_bytes = 12.0 * units + 16.0 * dom_cells
+        elif dominant == "k_bin":
+            units, alg_bytes = float(g), 32.0 * g
+        else:
+            units = float(tier_cells[int(dominant[-2])])
+            alg_bytes = 8.0 * units
+        dom_ms = pass_ms[dominant]
+    else:
+        # box-streaming kernels: 8 B per box cell + the 16-byte field per domain cell
+        per_launch_ms = {k: ktimes[k] / max(1, kprof) for k in ("k_predict", "k_correct")}
+        dominant = max(per_launch_ms, key=per_launch_ms.get)
+        units = box_cells_prof
+        alg_bytes = 8.0 * box_cells_prof + 16.0 * dom_cells
+        dom_ms = per_launch_ms[dominant]
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(dominant, units)
     cpu_rate, cpu_s, cpu_cells = oracle_sample_run(steps=2, warmup=0) if not args.no_cpu else (None, 0, 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -295,6 +318,7 @@ def gpu_arm(args):
         "box_cells_per_step": box_cells_mean,
         "superimposition": box_cells_mean / dom_cells,
         "kernel_ms_per_step": {k: v / max(1, kprof) for k, v in ktimes.items()},
+        "pass_ms_per_step": pass_ms, "pass_cells_per_tier": tier_cells, "exec": args.exec,
         "tile_variants": tiles,
         "gpu_launches": int(sum(kcount.values()) * args.steps / max(1, kprof)),
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
@@ -364,6 +388,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
     ap.add_argument("--no-tune", action="store_true", help="skip the tile autotuner")
+    ap.add_argument("--exec", default="batched", choices=["batched", "streamed"],
+                    help="batched: pass path for boxes of side <= 64; streamed: box-streaming kernels only")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving measurement (0: skip; 256: the full serving workload)")
     ap.add_argument("--workload", default="256", choices=sorted(WORKLOADS),

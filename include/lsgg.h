@@ -40,7 +40,9 @@ extern "C" {
 #define LSGG_ERR_INVALID_ARG   -1   /* a size, pointer or config field is out of range */
 #define LSGG_ERR_OUT_OF_MEMORY -2   /* a device allocation failed */
 #define LSGG_ERR_OVER_BUDGET   -3   /* a server admission would exceed its HBM budget */
-#define LSGG_ERR_CUDA          -4   /* a CUDA runtime call failed (no device, launch error) */
+#define LSGG_ERR_CUDA          -4   /* a CUDA runtime call failed (no device, launch error); with
+                                       LSGG_TRACE_ERRORS set in the environment the runtime's
+                                       message is printed on stderr */
 #define LSGG_ERR_TIMEOUT       -5   /* a bounded wait expired (device queue or host wait) */
 #define LSGG_ERR_NOT_READY     -6   /* a served request has not finished yet */
 #define LSGG_ERR_CAPACITY      -7   /* a caller buffer (see *n_out) or a fixed library buffer is too small */
@@ -57,8 +59,12 @@ extern "C" {
 #define LSGG_STORAGE_FP32  0   /* phi stored in FP32 */
 #define LSGG_STORAGE_BF16  1   /* phi stored in BF16 between steps, FP32 arithmetic */
 
-#define LSGG_EXEC_BATCHED  0   /* persistent per-size-class kernels over the packed box list */
+#define LSGG_EXEC_BATCHED  0   /* all boxes at once: 3D boxes of x, y side <= 64 by five passes
+                                  over (box, plane) / (box, column) work items, larger boxes by
+                                  box-streaming kernels; persistent grids, one CUDA graph per step */
 #define LSGG_EXEC_PLAIN    1   /* comparator: separate launches per grain per sub-step */
+#define LSGG_EXEC_STREAMED 2   /* all boxes by box-streaming kernels: one CTA streams one box
+                                  along z (register-ring / shared-memory rings per size class) */
 
 #define LSGG_MOBILITY_STEP  0  /* mob_low below theta_max, 1 above */
 #define LSGG_MOBILITY_EQ20  1  /* Eq. (20): 1 - 0.99 exp(-5 (theta / 15 deg)^9) */
@@ -152,15 +158,22 @@ typedef struct lsgg_stats {
     int64_t device_bytes;      /* device memory held by the context */
     int32_t n_classes;         /* box-size classes of the batched path */
     int32_t class_count[8];    /* boxes per class at the last box update */
+    int64_t pass_cells[2];     /* box cells on the pass path per tier (x, y side <= 32,
+                                  <= 64) at the last box update; 0 off the pass path */
 } lsgg_stats;
 
 int lsgg_get_stats(lsgg_ctx* ctx, lsgg_stats* out);
 
 /* Kernel timing with CUDA events on the context's stream.  While enabled,
  * lsgg_step launches eagerly (no graph) and records events between the
- * kernel groups of every step.  lsgg_kernel_times synchronises and writes,
- * for groups 0 = neighbour-max field clear, 1 = predictor (k_predict),
- * 2 = corrector + re-initialisation (k_correct), 3 = box update
+ * kernel groups of every step, and runs the kernels of a step one after
+ * another on the context's stream (unprofiled steps run size classes and
+ * tiers concurrently), so each kernel's time is its own.
+ * lsgg_kernel_times synchronises and writes,
+ * for groups 0 = neighbour-max field clear (pass path: tile binning),
+ * 1 = predictor (k_predict; pass path: p_conv_xy, p_conv_z, p_field),
+ * 2 = corrector + re-initialisation (k_correct; pass path: p_redist_xy,
+ * p_redist_z), 3 = box update
  * (k_box_update): out_ms[g] = summed device milliseconds and out_count[g] =
  * kernel launches of the library in that group (any pointer may be NULL),
  * over the steps since the previous call; then resets the sums. */
@@ -176,6 +189,15 @@ int lsgg_profile(lsgg_ctx* ctx, int32_t enable);
  * and class, -1 for classes not served by these kernels.  Synchronises. */
 int lsgg_autotune(lsgg_ctx* ctx, int32_t steps_per_trial, double dt, int32_t* chosen);
 int lsgg_kernel_times(lsgg_ctx* ctx, double* out_ms, int64_t* out_count);
+
+/* Per-pass timing of the pass path (LSGG_EXEC_BATCHED, 3D), from the same
+ * profiled steps as lsgg_kernel_times (arrays of 10; NULL allowed):
+ * out_ms[t * 4 + k] / out_count[t * 4 + k] for tier t = 0 (boxes of x, y side
+ * <= 32), 1 (<= 64) and pass k = 0 p_conv_xy, 1 p_conv_z, 2 p_redist_xy,
+ * 3 p_redist_z; [8] the tile binning (k_bin), [9] the field pass (p_field,
+ * all boxes).  In lsgg_kernel_times the binning is group 0 and the field
+ * pass belongs to group 1.  Synchronises, then resets the sums. */
+int lsgg_pass_times(lsgg_ctx* ctx, double* out_ms, int64_t* out_count);
 
 /* Contact neighbours of every grain after the last completed step (Sec. 3.1's
  * neighbourhood from the points of contact): the distinct grains j != i that
@@ -307,6 +329,17 @@ int lsgg_neighbour_max(const lsgg_box* boxes_dev, int32_t n_boxes, const float* 
 int lsgg_neighbour_max_noalloc(const lsgg_box* boxes_dev, int32_t n_boxes, const float* phip_dev,
                                int64_t n_elems, int32_t nx, int32_t ny, int32_t nz, float eps,
                                float* m_dev, int32_t* id_dev, void* stream);
+
+/* Test hook: reallocate the context's box arenas to exactly `capacity`
+ * elements (at least what the current state needs), so that a later box update
+ * overflows and exercises the growth path of lsgg_sync.  Synchronises. */
+int lsgg_debug_set_capacity(lsgg_ctx* ctx, int64_t capacity);
+
+/* Test hook of the bounded device waits: one CTA initialises an mbarrier that
+ * nothing will complete and waits on it for at most `iterations` polls, the
+ * way the step kernels wait for their bulk copies; *timed_out = 1 when the
+ * wait gave up (the kernel then returns normally).  Synchronises. */
+int lsgg_debug_wait_timeout(int32_t device, int32_t iterations, int32_t* timed_out);
 
 /* SplitMix64 seed points (host only, no device needed): out[3*i + a] =
  * u01(seed, 3*i + a) * N_a for a = x, y, z with

@@ -75,24 +75,48 @@ struct lsgg_ctx {
     std::vector<std::vector<cudaEvent_t>> ev_pending;
     double acc_ms[4] = {0, 0, 0, 0};
     long long acc_cnt[4] = {0, 0, 0, 0};
+    double acc_pass_ms[kTiers * 4 + 2] = {};
+    long long acc_pass_cnt[kTiers * 4 + 2] = {};
     StepStreams ss{};
     bool have_ss = false;
+    bool separate_z = false;         // pass path with an ID-field: Z has its own arena
     // plain (per-grain) comparator buffers
     float *p_t1 = nullptr, *p_t2 = nullptr, *p_C = nullptr, *p_G = nullptr, *p_H = nullptr;
     long long p_cap = 0;
 };
 
+namespace lsgg {
+
+// With LSGG_TRACE_ERRORS set in the environment, CUDA failures are reported
+// on stderr with the runtime's message and where they were seen.
+bool trace_errors() {
+    static const bool on = std::getenv("LSGG_TRACE_ERRORS") != nullptr;
+    return on;
+}
+
+cudaError_t traced(cudaError_t e, const char* what) {
+    if (e != cudaSuccess && trace_errors()) std::fprintf(stderr, "lsgg: CUDA error '%s' in %s\n", cudaGetErrorString(e), what);
+    return e;
+}
+
+}  // namespace lsgg
+
 namespace {
 
-int fail_cuda(cudaError_t e) {
-    (void)e;
+
+int trace_cuda(cudaError_t e, int line) {
+    if (trace_errors()) std::fprintf(stderr, "lsgg: CUDA error '%s' (api.cu:%d)\n", cudaGetErrorString(e), line);
     return LSGG_ERR_CUDA;
 }
 
-#define CK(call)                                        \
-    do {                                                \
-        cudaError_t e__ = (call);                       \
-        if (e__ != cudaSuccess) return fail_cuda(e__);  \
+int fail_cuda(cudaError_t e) { return trace_cuda(e, 0); }
+
+#define CUDA_FAIL() trace_cuda(cudaPeekAtLastError(), __LINE__)
+
+#define CK(call)                                                 \
+    do {                                                         \
+        cudaError_t e__ = (call);                                \
+        if (e__ != cudaSuccess) return trace_cuda(e__, __LINE__); \
     } while (0)
 
 template <class T>
@@ -149,6 +173,20 @@ int read_state(lsgg_ctx* c) {
     return LSGG_OK;
 }
 
+// Point the pass path's Z arena at `cap` elements: its own arena when the
+// physics keeps an ID-field, else the (then unused) ID-field arena.
+int replace_z(lsgg_ctx* c, long long cap) {
+    if (!c->B.use_passes) return LSGG_OK;
+    if (!c->separate_z) { c->B.Z = reinterpret_cast<float*>(c->B.IDF); return LSGG_OK; }
+    float* Z2 = nullptr;
+    int r = dalloc(c, &Z2, (size_t)cap);
+    if (r != LSGG_OK) return r;
+    c->device_bytes -= c->B.cap * 4;
+    dfree(c, c->B.Z);
+    c->B.Z = Z2;
+    return LSGG_OK;
+}
+
 // Grow the arenas to hold `need` elements, keeping the state (prev layout).
 int grow_arena(lsgg_ctx* c, long long need) {
     long long cap = std::max<long long>(need + need / 4, c->B.cap * 2);
@@ -168,9 +206,10 @@ int grow_arena(lsgg_ctx* c, long long need) {
     c->B.X = X2;
     c->B.Y = Y2;
     c->B.IDF = I2;
+    r = replace_z(c, cap);
     c->B.cap = cap;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-    return LSGG_OK;
+    return r;
 }
 
 // Assign arena offsets / classes for the `cur` boxes (no resize), growing if needed.
@@ -300,7 +339,8 @@ static int validate(const lsgg_config* cfg) {
     if (cfg->physics < LSGG_PHYSICS_IDEAL || cfg->physics > LSGG_PHYSICS_MAGNETIC) return LSGG_ERR_INVALID_ARG;
     if (cfg->storage != LSGG_STORAGE_FP32 && cfg->storage != LSGG_STORAGE_BF16) return LSGG_ERR_INVALID_ARG;
     if (cfg->storage == LSGG_STORAGE_BF16) return LSGG_ERR_UNSUPPORTED;
-    if (cfg->exec != LSGG_EXEC_BATCHED && cfg->exec != LSGG_EXEC_PLAIN) return LSGG_ERR_INVALID_ARG;
+    if (cfg->exec != LSGG_EXEC_BATCHED && cfg->exec != LSGG_EXEC_PLAIN && cfg->exec != LSGG_EXEC_STREAMED)
+        return LSGG_ERR_INVALID_ARG;
     if (cfg->physics == LSGG_PHYSICS_READ_SHOCKLEY &&
         (!(cfg->theta_max_deg > 0.0) || !(cfg->mob_low > 0.0) ||
          (cfg->mobility_law != LSGG_MOBILITY_STEP && cfg->mobility_law != LSGG_MOBILITY_EQ20)))
@@ -315,7 +355,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     int r = validate(cfg_in);
     if (r != LSGG_OK) return r;
     int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) { cudaGetLastError(); return LSGG_ERR_CUDA; }
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) { cudaGetLastError(); return CUDA_FAIL(); }
     if (cfg_in->device < 0 || cfg_in->device >= ndev) return LSGG_ERR_INVALID_ARG;
     lsgg_ctx* c = new (std::nothrow) lsgg_ctx();
     if (!c) return LSGG_ERR_OUT_OF_MEMORY;
@@ -323,10 +363,10 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->cfg.seeds = c->cfg.weights = c->cfg.quats = c->cfg.energy = nullptr;
     c->device = cfg_in->device;
     auto bail = [&](int code) { lsgg_destroy(c); return code; };
-    if (cudaSetDevice(c->device) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+    if (cudaSetDevice(c->device) != cudaSuccess) return bail(CUDA_FAIL());
     if (stream) c->stream = (cudaStream_t)stream;
     else {
-        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(CUDA_FAIL());
         c->own_stream = true;
     }
     if (cudaMallocHost(&c->h_st, sizeof(StepState)) != cudaSuccess) return bail(LSGG_ERR_OUT_OF_MEMORY);
@@ -406,7 +446,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if ((r = dalloc(c, &c->d_seeds, seeds.size())) != LSGG_OK) return bail(r);
     if (!weights.empty() && (r = dalloc(c, &c->d_weights, weights.size())) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->d_boxes, 2 * (size_t)G)) != LSGG_OK) return bail(r);
-    if (cudaMemset(c->d_boxes, 0, 2 * (size_t)G * sizeof(Box)) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+    if (cudaMemset(c->d_boxes, 0, 2 * (size_t)G * sizeof(Box)) != cudaSuccess) return bail(CUDA_FAIL());
     if ((r = dalloc(c, &c->B.bounds, (size_t)G)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.st, 1)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.worklist, (size_t)kNumClasses * G)) != LSGG_OK) return bail(r);
@@ -419,7 +459,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if (!energy.empty()) {
         std::vector<float> ef(energy.begin(), energy.end());
         if ((r = dalloc(c, &c->d_energy, (size_t)G)) != LSGG_OK) return bail(r);
-        if (cudaMemcpy(c->d_energy, ef.data(), ef.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+        if (cudaMemcpy(c->d_energy, ef.data(), ef.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return bail(CUDA_FAIL());
     }
     if (cfg_in->physics == LSGG_PHYSICS_READ_SHOCKLEY) {
         if ((r = dalloc(c, &c->d_quats, quats.size())) != LSGG_OK) return bail(r);
@@ -427,34 +467,43 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
         if ((r = dalloc(c, &c->d_nb_cnt, (size_t)G)) != LSGG_OK) return bail(r);
         if (cudaMemcpy(c->d_quats, quats.data(), quats.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemset(c->d_nb_cnt, 0, (size_t)G * 4) != cudaSuccess)
-            return bail(LSGG_ERR_CUDA);
+            return bail(CUDA_FAIL());
     }
-    if (cudaMemcpy(c->d_seeds, seeds.data(), seeds.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+    if (cudaMemcpy(c->d_seeds, seeds.data(), seeds.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) return bail(CUDA_FAIL());
     if (!weights.empty() && cudaMemcpy(c->d_weights, weights.data(), weights.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
-        return bail(LSGG_ERR_CUDA);
-    if (cudaMemsetAsync(c->B.st, 0, sizeof(StepState), c->stream) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+        return bail(CUDA_FAIL());
+    if (cudaMemsetAsync(c->B.st, 0, sizeof(StepState), c->stream) != cudaSuccess) return bail(CUDA_FAIL());
 
     c->B.dom = D;
     c->B.n_boxes = G;
     c->B.prev = c->d_boxes;
     c->B.cur = c->d_boxes + G;
-    if (configure_step_kernels(c->B) != cudaSuccess) return bail(LSGG_ERR_CUDA);
+    c->B.use_passes = cfg_in->exec == LSGG_EXEC_BATCHED ? 1 : 0;
+    if (configure_step_kernels(c->B) != cudaSuccess) return bail(CUDA_FAIL());
+    if (c->B.use_passes) {
+        c->B.plane_item_cap = (long long)G * D.nz;
+        c->B.chunk_item_cap = (long long)G * ((64 * 64 + kPassChunk - 1) / kPassChunk);
+        if ((r = dalloc(c, &c->B.plane_items, (size_t)c->B.plane_item_cap)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &c->B.chunk_items, (size_t)c->B.chunk_item_cap)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &c->B.tile_cnt, (size_t)c->B.n_tiles)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &c->B.tile_list, (size_t)c->B.n_tiles * kTileCap)) != LSGG_OK) return bail(r);
+    }
     {
         bool ok = cudaEventCreateWithFlags(&c->ss.fork, cudaEventDisableTiming) == cudaSuccess;
         for (int k = 0; k < kNumClasses && ok; ++k)
             ok = cudaStreamCreateWithFlags(&c->ss.side[k], cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&c->ss.join[k], cudaEventDisableTiming) == cudaSuccess;
-        if (!ok) return bail(LSGG_ERR_CUDA);
+        if (!ok) return bail(CUDA_FAIL());
         c->have_ss = true;
     }
 
     if (launch_init(D, G, c->d_seeds, c->d_weights, d_labels, d_bits, wpr, d_bb, c->B.cur, c->stream) != cudaSuccess)
-        return bail(LSGG_ERR_CUDA);
+        return bail(CUDA_FAIL());
     // size the arena from the initial boxes
     std::vector<Box> hb(G);
     if (cudaMemcpyAsync(hb.data(), c->B.cur, (size_t)G * sizeof(Box), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return bail(LSGG_ERR_CUDA);
+        return bail(CUDA_FAIL());
     long long need = 0;
     for (const Box& b : hb) need += host_box_elems(b);
     long long cap = (long long)(need * cfg_in->arena_slack) + (1 << 16);
@@ -463,6 +512,9 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if ((r = dalloc(c, &c->B.X, (size_t)cap)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.Y, (size_t)cap)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.IDF, (size_t)cap)) != LSGG_OK) return bail(r);
+    c->separate_z = c->B.use_passes && cfg_in->physics != LSGG_PHYSICS_IDEAL;
+    if (c->separate_z && (r = dalloc(c, &c->B.Z, (size_t)cap)) != LSGG_OK) return bail(r);
+    if (c->B.use_passes && !c->separate_z) c->B.Z = reinterpret_cast<float*>(c->B.IDF);
     c->B.scratch_per_cta = large_class_scratch_floats(D);
     {
         long long total = 0;
@@ -476,9 +528,9 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if ((r = relayout(c)) != LSGG_OK) return bail(r);
     if (launch_sdf(D, G, c->B.cur, c->d_seeds, c->d_weights, d_bits, wpr, c->B.X,
                    c->B.IDF, &c->B.st->status, c->stream) != cudaSuccess)
-        return bail(LSGG_ERR_CUDA);
+        return bail(CUDA_FAIL());
     if (cudaMemcpyAsync(c->B.prev, c->B.cur, (size_t)G * sizeof(Box), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-        return bail(LSGG_ERR_CUDA);
+        return bail(CUDA_FAIL());
     if ((r = read_state(c)) != LSGG_OK) return bail(r);
     if (c->h_st->status != 0) return bail(c->h_st->status);
     dfree(c, d_labels);
@@ -500,7 +552,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
 int lsgg_step(lsgg_ctx* c, int32_t n, double dt) {
     if (!c || n < 0 || !(dt > 0.0) || dt > 4.0) return LSGG_ERR_INVALID_ARG;
     if (n == 0) return LSGG_OK;
-    if (cudaSetDevice(c->device) != cudaSuccess) return LSGG_ERR_CUDA;
+    if (cudaSetDevice(c->device) != cudaSuccess) return CUDA_FAIL();
     c->steps_target += n;
     c->last_dt = dt;
     c->field_valid = true;
@@ -509,13 +561,13 @@ int lsgg_step(lsgg_ctx* c, int32_t n, double dt) {
 
 int lsgg_sync(lsgg_ctx* c, int64_t timeout_ms) {
     if (!c) return LSGG_ERR_INVALID_ARG;
-    if (cudaSetDevice(c->device) != cudaSuccess) return LSGG_ERR_CUDA;
+    if (cudaSetDevice(c->device) != cudaSuccess) return CUDA_FAIL();
     for (int round = 0; round < 64; ++round) {
         auto t0 = std::chrono::steady_clock::now();
         for (;;) {
             cudaError_t q = cudaStreamQuery(c->stream);
             if (q == cudaSuccess) break;
-            if (q != cudaErrorNotReady) return LSGG_ERR_CUDA;
+            if (q != cudaErrorNotReady) return CUDA_FAIL();
             if (timeout_ms >= 0) {
                 auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
                 if (ms > timeout_ms) return LSGG_ERR_TIMEOUT;
@@ -554,6 +606,7 @@ int lsgg_get_stats(lsgg_ctx* c, lsgg_stats* out) {
     out->device_bytes = c->device_bytes;
     out->n_classes = kNumClasses;
     for (int k = 0; k < kNumClasses; ++k) out->class_count[k] = c->h_st->class_count[k];
+    for (int t = 0; t < kTiers; ++t) out->pass_cells[t] = c->B.use_passes ? c->h_st->tier_cells[t] : 0;
     return LSGG_OK;
 }
 
@@ -561,12 +614,12 @@ int lsgg_autotune(lsgg_ctx* c, int32_t steps_per_trial, double dt, int32_t* chos
     if (!c || steps_per_trial < 1 || !(dt > 0.0) || dt > 4.0) return LSGG_ERR_INVALID_ARG;
     int r = lsgg_sync(c, -1);
     if (r != LSGG_OK) return r;
-    if (cudaSetDevice(c->device) != cudaSuccess) return LSGG_ERR_CUDA;
+    if (cudaSetDevice(c->device) != cudaSuccess) return CUDA_FAIL();
     const int nv = StepBuffers::kVariants;
     const int ne = 4 * kNumClasses;
     std::vector<cudaEvent_t> ev((size_t)ne * steps_per_trial);
     for (auto& e : ev)
-        if (cudaEventCreate(&e) != cudaSuccess) return LSGG_ERR_CUDA;
+        if (cudaEventCreate(&e) != cudaSuccess) return CUDA_FAIL();
     double best_ms[2][kNumClasses];
     int best_v[2][kNumClasses];
     for (int w = 0; w < 2; ++w)
@@ -617,21 +670,57 @@ int lsgg_profile(lsgg_ctx* c, int32_t enable) {
     return LSGG_OK;
 }
 
-int lsgg_kernel_times(lsgg_ctx* c, double* out_ms, int64_t* out_count) {
-    if (!c) return LSGG_ERR_INVALID_ARG;
-    int r = lsgg_sync(c, -1);
-    if (r != LSGG_OK) return r;
-    const long long per_step[4] = {0, kNumClasses, kNumClasses, 1};
+}  // extern "C"
+
+namespace {
+
+// Fold the events of the profiled steps into the per-group and per-pass sums.
+int drain_profile_events(lsgg_ctx* c) {
+    int n_other = 0;
+    for (int k = 0; k < kNumClasses; ++k) n_other += c->B.mode[k] != 3;
+    const bool plain = c->cfg.exec == LSGG_EXEC_PLAIN;
+    const long long passes = c->B.use_passes ? kTiers : 0;
+    const long long per_step[4] = {passes ? 1 : 0, plain ? kNumClasses : n_other + 2 * passes + (passes ? 1 : 0),
+                                   plain ? kNumClasses : n_other + 2 * passes, 1};
     for (auto& v : c->ev_pending) {
         for (int g = 0; g < 4; ++g) {
             float ms = 0.0f;
-            if (cudaEventElapsedTime(&ms, v[g], v[g + 1]) != cudaSuccess) return LSGG_ERR_CUDA;
+            if (cudaEventElapsedTime(&ms, v[g], v[g + 1]) != cudaSuccess) return CUDA_FAIL();
             c->acc_ms[g] += ms;
             c->acc_cnt[g] += per_step[g];
+        }
+        if (v.size() == 5 + (size_t)kPassEvents) {
+            const cudaEvent_t* pe = v.data() + 5;
+            auto add = [&](int slot, int e0, int e1) -> bool {
+                float ms = 0.0f;
+                if (cudaEventElapsedTime(&ms, pe[e0], pe[e1]) != cudaSuccess) return false;
+                c->acc_pass_ms[slot] += ms;
+                c->acc_pass_cnt[slot] += 1;
+                return true;
+            };
+            bool ok = true;
+            for (int t = 0; t < kTiers; ++t) {
+                const int seg[4][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}};
+                for (int k = 0; k < 4; ++k) ok = ok && add(t * 4 + k, t * 6 + seg[k][0], t * 6 + seg[k][1]);
+            }
+            ok = ok && add(kTiers * 4, 6 * kTiers, 6 * kTiers + 1) && add(kTiers * 4 + 1, 6 * kTiers + 2, 6 * kTiers + 3);
+            if (!ok) return CUDA_FAIL();
         }
         for (cudaEvent_t e : v) c->ev_pool.push_back(e);
     }
     c->ev_pending.clear();
+    return LSGG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lsgg_kernel_times(lsgg_ctx* c, double* out_ms, int64_t* out_count) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    if ((r = drain_profile_events(c)) != LSGG_OK) return r;
     for (int g = 0; g < 4; ++g) {
         if (out_ms) out_ms[g] = c->acc_ms[g];
         if (out_count) out_count[g] = c->acc_cnt[g];
@@ -639,6 +728,55 @@ int lsgg_kernel_times(lsgg_ctx* c, double* out_ms, int64_t* out_count) {
         c->acc_cnt[g] = 0;
     }
     return LSGG_OK;
+}
+
+int lsgg_pass_times(lsgg_ctx* c, double* out_ms, int64_t* out_count) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    if ((r = drain_profile_events(c)) != LSGG_OK) return r;
+    for (int g = 0; g < kTiers * 4 + 2; ++g) {
+        if (out_ms) out_ms[g] = c->acc_pass_ms[g];
+        if (out_count) out_count[g] = c->acc_pass_cnt[g];
+        c->acc_pass_ms[g] = 0.0;
+        c->acc_pass_cnt[g] = 0;
+    }
+    return LSGG_OK;
+}
+
+int lsgg_debug_set_capacity(lsgg_ctx* c, int64_t capacity) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    std::vector<Box> hp(c->G), hc(c->G);
+    CK(cudaMemcpy(hp.data(), c->B.prev, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hc.data(), c->B.cur, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToHost));
+    long long need_prev = 0, need_cur = 0;
+    for (int i = 0; i < c->G; ++i) {
+        need_prev = std::max(need_prev, hp[i].nx > 0 ? hp[i].off + host_box_elems(hp[i]) : 0);
+        need_cur += host_box_elems(hc[i]);
+    }
+    capacity = (capacity + 31) & ~31LL;
+    if (capacity < need_prev || capacity < need_cur) return LSGG_ERR_INVALID_ARG;
+    float *X2 = nullptr, *Y2 = nullptr;
+    int* I2 = nullptr;
+    if ((r = dalloc(c, &X2, (size_t)capacity)) != LSGG_OK) return r;
+    if ((r = dalloc(c, &Y2, (size_t)capacity)) != LSGG_OK) return r;
+    if ((r = dalloc(c, &I2, (size_t)capacity)) != LSGG_OK) return r;
+    CK(cudaMemcpyAsync(X2, c->B.X, (size_t)need_prev * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(I2, c->B.IDF, (size_t)need_prev * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->device_bytes -= 3 * c->B.cap * 4;
+    dfree(c, c->B.X);
+    dfree(c, c->B.Y);
+    dfree(c, c->B.IDF);
+    c->B.X = X2;
+    c->B.Y = Y2;
+    c->B.IDF = I2;
+    if ((r = replace_z(c, capacity)) != LSGG_OK) return r;
+    c->B.cap = capacity;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return relayout(c);
 }
 
 int lsgg_grain_neighbours(lsgg_ctx* c, int32_t* counts, int32_t* ids, int32_t cap_per_grain) {
@@ -843,14 +981,14 @@ int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg) {
                 cudaMemcpyAsync(hp.data(), c->B.prev, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
                 cudaMemcpyAsync(c->h_st, c->B.st, sizeof(StepState), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
                 cudaStreamSynchronize(c->stream) != cudaSuccess)
-                return LSGG_ERR_CUDA;
+                return CUDA_FAIL();
             if (c->h_st->halt) return LSGG_OK;         // arena overflow: lsgg_sync resumes
             cudaEvent_t* ev = nullptr;
             if (c->profiling) {
                 std::vector<cudaEvent_t> v(5);
                 for (auto& e : v) {
                     if (!c->ev_pool.empty()) { e = c->ev_pool.back(); c->ev_pool.pop_back(); }
-                    else if (cudaEventCreate(&e) != cudaSuccess) return LSGG_ERR_CUDA;
+                    else if (cudaEventCreate(&e) != cudaSuccess) return CUDA_FAIL();
                 }
                 c->ev_pending.push_back(v);
                 ev = c->ev_pending.back().data();
@@ -859,7 +997,7 @@ int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg) {
             }
             if (launch_plain_step_impl(c->B, taps, c->phys, hc.data(), hp.data(), c->p_t1, c->p_t2, c->p_C,
                                        c->p_G, c->p_H, c->stream) != cudaSuccess)
-                return LSGG_ERR_CUDA;
+                return CUDA_FAIL();
             if (ev) {
                 cudaEventRecord(ev[2], c->stream);
                 cudaEventRecord(ev[3], c->stream);
@@ -873,31 +1011,43 @@ int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg) {
         if (!c->graph || c->graph_dt != dt) {
             if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
             cudaGraph_t g = nullptr;
-            if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LSGG_ERR_CUDA;
+            if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CUDA_FAIL();
             cudaError_t le = launch_step(c->B, taps, c->phys, nullptr, c->stream, nullptr, &c->ss);
             cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
-            if (le != cudaSuccess || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return LSGG_ERR_CUDA; }
-            cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+            if (le != cudaSuccess || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return CUDA_FAIL(); }
+            cudaGraphInstantiateParams ip{};
+            ip.flags = 0;
+            cudaError_t ie = cudaGraphInstantiateWithParams(&c->graph, g, &ip);
+            if (ie != cudaSuccess && trace_errors()) {
+                cudaGraphNodeType nt = cudaGraphNodeTypeEmpty;
+                if (ip.errNode_out) cudaGraphNodeGetType(ip.errNode_out, &nt);
+                std::fprintf(stderr, "lsgg: graph instantiation: result %d, failing node type %d\n", (int)ip.result_out,
+                             (int)nt);
+            }
             cudaGraphDestroy(g);
-            if (ie != cudaSuccess) { c->graph = nullptr; return LSGG_ERR_CUDA; }
+            if (ie != cudaSuccess) { c->graph = nullptr; return CUDA_FAIL(); }
             c->graph_dt = dt;
         }
         for (long long i = 0; i < n; ++i)
-            if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return LSGG_ERR_CUDA;
+            if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return CUDA_FAIL();
         return LSGG_OK;
     }
     for (long long i = 0; i < n; ++i) {
         cudaEvent_t* ev = nullptr;
         if (c->profiling) {
-            std::vector<cudaEvent_t> v(5);
+            std::vector<cudaEvent_t> v(c->B.use_passes ? 5 + kPassEvents : 5);
             for (auto& e : v) {
                 if (!c->ev_pool.empty()) { e = c->ev_pool.back(); c->ev_pool.pop_back(); }
-                else if (cudaEventCreate(&e) != cudaSuccess) return LSGG_ERR_CUDA;
+                else if (cudaEventCreate(&e) != cudaSuccess) return CUDA_FAIL();
             }
             c->ev_pending.push_back(v);
             ev = c->ev_pending.back().data();
         }
-        if (launch_step(c->B, taps, c->phys, dbg, c->stream, ev, &c->ss) != cudaSuccess) return LSGG_ERR_CUDA;
+        // profiled steps run every kernel on the context's stream, one after
+        // another, so that each kernel's event time is its own
+        if (launch_step(c->B, taps, c->phys, dbg, c->stream, ev, ev ? nullptr : &c->ss, nullptr,
+                        ev && c->B.use_passes ? ev + 5 : nullptr) != cudaSuccess)
+            return CUDA_FAIL();
     }
     return LSGG_OK;
 }

@@ -9,6 +9,14 @@ namespace lsgg {
 
 __device__ __forceinline__ bool sgn_pos(float v) { return !(__float_as_uint(v) >> 31); }
 
+// Division of non-negative ints below 2^16 by a divisor d set once: q = (t *
+// ceil(2^32 / d)) >> 32 is exact in that range (two instructions).
+struct Div16 {
+    unsigned m;
+    __device__ __forceinline__ explicit Div16(int d) : m((unsigned)((0x100000000ULL + d - 1) / d)) {}
+    __device__ __forceinline__ int operator()(int t) const { return (int)__umulhi((unsigned)t, m); }
+};
+
 // Disorientation angle (radians) of two cubic crystals: with q = conj(qa) qb
 // and |q| components sorted c0 >= c1 >= c2 >= c3, the largest |w| over the 24
 // proper rotations of the cube applied to q is max(c0, (c0 + c1)/sqrt 2,

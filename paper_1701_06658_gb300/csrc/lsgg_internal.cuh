@@ -8,9 +8,15 @@
 //              plane is one 16-byte aligned bulk copy; off is a multiple of 32.
 //   T          neighbour-max field, 2 x u64 per domain cell: key1 = the largest
 //              (phi_p, -id) over the boxes covering the cell, key2 = the second.
+//              Box-streaming kernels build it with 64-bit atomicMax; the pass
+//              path computes it per domain tile in registers and stores it.
 //   IDF        int32 ID-field arena (same layout as X) for the physics blend.
+//   Z          FP32 box arena (same layout) between the passes of the pass
+//              path; aliases IDF when the physics needs no ID-field.
 //   classes    per size class a work list of box indices and a queue counter
 //              per kernel; persistent CTAs pull boxes from the queue.
+//   items      pass path: per tier a list of (box, plane) and of (box, column
+//              chunk) work items, rebuilt by every box update.
 #pragma once
 
 #include <cstdint>
@@ -22,6 +28,10 @@ constexpr int kMaxRadius = 7;
 constexpr int kMaxTaps = 2 * kMaxRadius + 1;
 constexpr int kNumClasses = 5;          // box side <= 32, 40, 48, 64, larger (global scratch)
 constexpr int kRedistReach = 6;         // taxicab steps below eps = 7 (exact fixed point)
+constexpr int kTiers = 2;               // pass path: boxes with x, y sides <= 32 and <= 64
+constexpr int kPassChunk = 256;         // columns per column item of the pass path
+constexpr int kTileX = 32, kTileY = 8, kTileZ = 16;   // domain tiles of the field pass
+constexpr int kTileCap = 128;           // boxes listed per tile (more: the tile scans all boxes)
 
 struct Box {
     int ox, oy, oz;       // origin, each in [0, N)
@@ -85,6 +95,11 @@ struct StepState {                  // device-resident control block
     long long cell_updates;         // box cells advanced by completed steps (sum over steps)
     int class_count[kNumClasses];
     int queue[2][kNumClasses];      // pull counters of the predictor / corrector kernels
+    int n_planes[kTiers];           // pass path: work items per tier and their
+    int n_chunks[kTiers];           // first entry in the shared item lists
+    int plane_base[kTiers];
+    int chunk_base[kTiers];
+    long long tier_cells[kTiers];   // box cells per tier in `cur`
 };
 
 __host__ __device__ inline int plane_stride(int nx, int ny) { return (nx * ny + 3) & ~3; }
@@ -133,13 +148,31 @@ struct StepBuffers {
     long long scratch_class_off[kNumClasses];   // each mode-2 class owns a slice (classes run concurrently)
     int n_sm;
     int class_side[kNumClasses];    // largest box side per class (last: whole domain)
-    int mode[kNumClasses];          // 0: register-ring kernels, 1: shared-memory ring, 2: global scratch ring
+    int mode[kNumClasses];          // 0: register-ring kernels, 1: shared-memory ring, 2: global scratch ring,
+                                    // 3: pass path
     int block[kNumClasses];         // threads per CTA (shared-memory / global rings)
     int fblock[2][kNumClasses];     // threads per CTA of the register-ring kernels
     int variant[2][kNumClasses];    // tile variant of the register-ring kernels (autotuned)
     static constexpr int kVariants = 3;
     int grid[2][kNumClasses];       // persistent grid per kernel and class
     size_t smem[2][kNumClasses];
+    // pass path (mode 3 classes): tiers of box side <= tier_side[t]
+    float* Z;
+    int2* plane_items;              // (box, local z), tier 0 then tier 1
+    int2* chunk_items;              // (box, column chunk of kPassChunk columns)
+    long long plane_item_cap;       // entries (n_boxes * domain nz: a bound on sum nz)
+    long long chunk_item_cap;       // entries (n_boxes * 64 * 64 / kPassChunk)
+    int use_passes;
+    int tier_side[kTiers];
+    int tier_threads[kTiers];       // threads per CTA of the plane passes
+    int pgrid[kTiers][5];           // persistent grid per tier and pass (conv_xy, conv_z, -, redist_xy, redist_z)
+    size_t psmem[kTiers][2];        // dynamic shared memory of the two plane passes
+    // field pass: boxes overlapping each domain tile of kTileX x kTileY x kTileZ cells
+    int* tile_cnt;                  // [n_tiles]
+    int* tile_list;                 // [n_tiles * kTileCap]
+    int ntile[3];
+    int n_tiles;
+    int field_grid, bin_grid;
 };
 
 // Side streams on which the size-class kernels of one phase run concurrently
@@ -155,11 +188,27 @@ struct StepStreams {
 // ss (optional): run each phase's class kernels concurrently on side streams.
 // cls_ev (optional, 4 * kNumClasses events): start / end of each class kernel of
 // each phase, recorded on the class's stream: [(which * kNumClasses + c) * 2 + {0, 1}].
+// pass_ev (optional, 6 * kTiers + 4 events): per tier, around the pass-path kernels:
+// [t * 6 + 0..2] p_conv_xy, p_conv_z; [t * 6 + 3..5] p_redist_xy, p_redist_z;
+// [6 * kTiers + 0..1] around k_bin, [6 * kTiers + 2..3] around p_field.
 cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
                         const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev = nullptr,
-                        const StepStreams* ss = nullptr, cudaEvent_t* cls_ev = nullptr);
+                        const StepStreams* ss = nullptr, cudaEvent_t* cls_ev = nullptr,
+                        cudaEvent_t* pass_ev = nullptr);
 cudaError_t launch_box_update(const StepBuffers& B, bool commit_only_layout, cudaStream_t s);
 cudaError_t configure_step_kernels(StepBuffers& B);
+// Let `fn` take up to the device's opt-in shared memory per CTA (process-wide).
+cudaError_t allow_max_dynamic_smem(const void* fn);
+cudaError_t configure_passes(StepBuffers& B);
+cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps& taps, const PhysicsDev& phys,
+                          const DebugOut& dbg, cudaStream_t s, cudaEvent_t* pass_ev);
+cudaError_t launch_bin(const StepBuffers& B, cudaStream_t s);
+cudaError_t launch_field(const StepBuffers& B, const PhysicsDev& phys, const DebugOut& dbg, cudaStream_t s);
+constexpr int kPassEvents = 6 * kTiers + 4;
+// Error tracing (LSGG_TRACE_ERRORS in the environment): `traced` prints a
+// failing call's message and `what` on stderr and returns the error.
+bool trace_errors();
+cudaError_t traced(cudaError_t e, const char* what);
 cudaError_t configure_fast_variant(StepBuffers& B, int which, int cls, int variant);
 int fast_class_side(int cls);
 cudaError_t launch_plain_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,

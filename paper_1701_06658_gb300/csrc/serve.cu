@@ -48,11 +48,15 @@ struct Request {
 };
 
 int64_t estimate_bytes(const lsgg_config& c) {
-    // arena X, Y, ID-field at ~12 box cells per domain cell with 1.5x slack, the
-    // 16-byte neighbour-max field, init temporaries (labels, neighbour bits)
+    // arena X, Y, ID-field (and the pass path's Z when the physics keeps an
+    // ID-field) at ~12 box cells per domain cell with 1.5x slack, the 16-byte
+    // neighbour-max field, init temporaries (labels, neighbour bits), the pass
+    // path's work-item lists
     const int64_t ncell = (int64_t)c.nx * c.ny * c.nz;
     const int64_t g = c.n_grains;
-    return 3 * 4 * 18 * ncell + 16 * ncell + 4 * ncell + g * ((g + 31) / 32) * 4 + (64LL << 20);
+    const int64_t arenas = (c.exec == LSGG_EXEC_BATCHED && c.physics != LSGG_PHYSICS_IDEAL) ? 4 : 3;
+    const int64_t items = c.exec == LSGG_EXEC_BATCHED ? 8 * g * ((int64_t)c.nz + 16) : 0;
+    return arenas * 4 * 18 * ncell + 16 * ncell + 4 * ncell + g * ((g + 31) / 32) * 4 + items + (64LL << 20);
 }
 
 double seconds_since(Clock::time_point t0) {

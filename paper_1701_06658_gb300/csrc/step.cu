@@ -163,10 +163,12 @@ __device__ void predict_box(const StepBuffers& B, const Taps& taps, const Physic
             }
             v = fminf(fmaxf(v, -eps), eps);
             dst[idx] = v;
-            long long g = ((long long)gz * D.ny + sm.gy[y]) * D.nx + sm.gx[x];
-            unsigned long long key = make_key(v, b);
-            unsigned long long old = atomicMax(&B.T[2 * g], key);
-            if (old) atomicMax(&B.T[2 * g + 1], old < key ? old : key);
+            if (!B.use_passes) {        // the pass path's field pass builds T instead
+                long long g = ((long long)gz * D.ny + sm.gy[y]) * D.nx + sm.gx[x];
+                unsigned long long key = make_key(v, b);
+                unsigned long long old = atomicMax(&B.T[2 * g], key);
+                if (old) atomicMax(&B.T[2 * g + 1], old < key ? old : key);
+            }
         }
         // no barrier needed: the next writes into `ring` happen after two barriers
     }
@@ -420,15 +422,23 @@ __device__ __forceinline__ int box_class(const StepBuffers& B, const Box& b, con
     return kNumClasses - 1;
 }
 
+// Tier of a pass-path class: the smallest tier whose side holds the class's side.
+__device__ __forceinline__ int pass_tier(const StepBuffers& B, int c) {
+    return B.class_side[c] <= B.tier_side[0] ? 0 : 1;
+}
+
 __global__ void __launch_bounds__(kBoxUpdateThreads)
 k_box_update(StepBuffers B, int layout_only) {
     __shared__ long long s_part[kBoxUpdateThreads];
     __shared__ int s_cnt[kNumClasses];
     __shared__ long long s_alive;
+    __shared__ int s_np[kTiers], s_nc[kTiers], s_wp[kTiers], s_wc[kTiers];
+    __shared__ unsigned long long s_tc[kTiers];
     const int G = B.n_boxes;
     const Domain D = B.dom;
     if (*(volatile int*)&B.st->halt && !layout_only) return;
     if (threadIdx.x < kNumClasses) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x < kTiers) { s_np[threadIdx.x] = 0; s_nc[threadIdx.x] = 0; s_tc[threadIdx.x] = 0; }
     if (threadIdx.x == 0) s_alive = 0;
     const int per = (G + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * per, b1 = min(G, b0 + per);
@@ -499,10 +509,37 @@ k_box_update(StepBuffers B, int layout_only) {
         if (cb.nx > 0) {
             int c = box_class(B, cb, B.prev[b]);
             int w = atomicAdd(&s_cnt[c], 1);
-            B.worklist[c * G + w] = b;
+            if (B.mode[c] == 3) {
+                const int t = pass_tier(B, c);
+                atomicAdd(&s_np[t], cb.nz);
+                atomicAdd(&s_nc[t], (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk);
+                atomicAdd(&s_tc[t], (unsigned long long)cb.nx * cb.ny * cb.nz);
+            } else {
+                B.worklist[c * G + w] = b;
+            }
             cells += (long long)cb.nx * cb.ny * cb.nz;
             alive += 1;
         }
+    }
+    // pass-path work items: tier 0 first, then tier 1, each box's in a block
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_wp[0] = 0; s_wp[1] = s_np[0];
+        s_wc[0] = 0; s_wc[1] = s_nc[0];
+    }
+    __syncthreads();
+    const bool items_fit = (long long)s_np[0] + s_np[1] <= B.plane_item_cap &&
+                           (long long)s_nc[0] + s_nc[1] <= B.chunk_item_cap;
+    for (int b = b0; b < b1 && items_fit; ++b) {
+        const Box cb = B.cur[b];
+        if (cb.nx <= 0) continue;
+        const int c = box_class(B, cb, B.prev[b]);
+        if (B.mode[c] != 3) continue;
+        const int t = pass_tier(B, c);
+        const int nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
+        const int p0 = atomicAdd(&s_wp[t], cb.nz), c0 = atomicAdd(&s_wc[t], nch);
+        for (int z = 0; z < cb.nz; ++z) B.plane_items[p0 + z] = make_int2(b, z);
+        for (int k = 0; k < nch; ++k) B.chunk_items[c0 + k] = make_int2(b, k);
     }
     // reduce cells / alive
     __syncthreads();
@@ -520,7 +557,18 @@ k_box_update(StepBuffers B, int layout_only) {
         B.st->queue[0][threadIdx.x] = 0;
         B.st->queue[1][threadIdx.x] = 0;
     }
-    if (threadIdx.x == 0) B.st->alive = s_alive;
+    if (threadIdx.x < kTiers) {
+        const int t = threadIdx.x;
+        B.st->n_planes[t] = items_fit ? s_np[t] : 0;
+        B.st->n_chunks[t] = items_fit ? s_nc[t] : 0;
+        B.st->plane_base[t] = t ? s_np[0] : 0;
+        B.st->chunk_base[t] = t ? s_nc[0] : 0;
+        B.st->tier_cells[t] = (long long)s_tc[t];
+    }
+    if (threadIdx.x == 0) {
+        B.st->alive = s_alive;
+        if (!items_fit) { B.st->status = LSGG_ERR_UNSUPPORTED; B.st->halt = 1; }   // not reached: caps are bounds
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -542,6 +590,17 @@ cudaError_t configure_fast(StepBuffers& B, int cls, int n_sm);
 cudaError_t launch_fast(const StepBuffers& B, int which, int cls, const Taps& taps, const PhysicsDev& phys,
                         const DebugOut& dbg, cudaStream_t s);
 
+cudaError_t allow_max_dynamic_smem(const void* fn) {
+    int dev = 0, max_optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e == cudaSuccess)        // static shared memory counts against the same limit
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 cudaError_t configure_step_kernels(StepBuffers& B) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -559,8 +618,14 @@ cudaError_t configure_step_kernels(StepBuffers& B) {
     B.class_side[kNumClasses - 1] = big;
     // register-ring kernels for the small classes, shared-memory rings where they fit, global otherwise
     size_t mp = 0, mc = 0;
+    const bool passes = B.use_passes && B.dom.dim == 3;
+    B.use_passes = passes ? 1 : 0;
     for (int c = 0; c < kNumClasses; ++c) {
         B.block[c] = kThreads;
+        if (passes && c < kNumClasses - 1) {      // x, y sides <= 64: pass path
+            B.mode[c] = 3;
+            continue;
+        }
         if (fast_ok && fast_class_side(c) == B.class_side[c]) {
             e = configure_fast(B, c, n_sm);
             if (e != cudaSuccess) return e;
@@ -585,16 +650,16 @@ cudaError_t configure_step_kernels(StepBuffers& B) {
         if (sp > mp) mp = sp;
         if (sc > mc) mc = sc;
     }
-    if (mp > 0) {
-        e = cudaFuncSetAttribute(k_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp);
-        if (e != cudaSuccess) return e;
-    }
-    if (mc > 0) {
-        e = cudaFuncSetAttribute(k_correct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mc);
+    // the attribute is process-wide: set it to the device limit (never to a
+    // context's own need, which would cap another context's launches)
+    if (mp > 0 && (e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_predict))) != cudaSuccess) return e;
+    if (mc > 0 && (e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_correct))) != cudaSuccess) return e;
+    if (passes) {
+        e = configure_passes(B);
         if (e != cudaSuccess) return e;
     }
     for (int c = 0; c < kNumClasses; ++c) {
-        if (B.mode[c] == 0) continue;
+        if (B.mode[c] == 0 || B.mode[c] == 3) continue;
         if (B.mode[c] == 2) {
             B.grid[0][c] = B.grid[1][c] = (n_sm + 3) / 4;
             continue;
@@ -625,56 +690,91 @@ cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream
 
 cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,
                         const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev, const StepStreams* ss,
-                        cudaEvent_t* cls_ev) {
+                        cudaEvent_t* cls_ev, cudaEvent_t* pass_ev) {
     long long ncell = (long long)B.dom.nx * B.dom.ny * B.dom.nz;
+    cudaEvent_t* bin_ev = pass_ev ? pass_ev + 6 * kTiers : nullptr;
     if (ev) cudaEventRecord(ev[0], s);
-    cudaError_t e = cudaMemsetAsync(B.T, 0, (size_t)ncell * 16, s);
+    cudaError_t e;
+    if (B.use_passes) {                 // the field pass stores every cell of T: no clear
+        if (bin_ev) cudaEventRecord(bin_ev[0], s);
+        e = traced(launch_bin(B, s), "tile binning");
+        if (bin_ev) cudaEventRecord(bin_ev[1], s);
+    } else {
+        e = traced(cudaMemsetAsync(B.T, 0, (size_t)ncell * 16, s), "field clear");
+    }
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
     DebugOut d{};
     if (dbg) d = *dbg;
     if (phys.kind == LSGG_PHYSICS_READ_SHOCKLEY) {
-        e = launch_collect_neighbours(B, phys, s);
+        e = traced(launch_collect_neighbours(B, phys, s), "neighbour tables");
         if (e != cudaSuccess) return e;
     }
+    // Each phase forks the size classes (and the pass-path tiers, on the side
+    // streams of tiers' indices, whose classes are then pass-path classes) off
+    // the step's stream and joins them back.
     auto run_phase = [&](int which) -> cudaError_t {
+        bool joined[kNumClasses] = {};
         if (ss) {
-            cudaError_t r = cudaEventRecord(ss->fork, s);
+            cudaError_t r = traced(cudaEventRecord(ss->fork, s), "fork record");
             if (r != cudaSuccess) return r;
         }
-        for (int c = 0; c < kNumClasses; ++c) {
-            cudaStream_t cs = s;
-            if (ss) {
-                cs = ss->side[c];
-                cudaError_t r = cudaStreamWaitEvent(cs, ss->fork, 0);
+        auto stream_for = [&](int k, cudaStream_t* cs) -> cudaError_t {
+            *cs = s;
+            if (!ss) return cudaSuccess;
+            *cs = ss->side[k];
+            return traced(cudaStreamWaitEvent(*cs, ss->fork, 0), "fork wait");
+        };
+        auto join = [&](int k, cudaStream_t cs) -> cudaError_t {
+            if (!ss) return cudaSuccess;
+            joined[k] = true;
+            return traced(cudaEventRecord(ss->join[k], cs), "join record");
+        };
+        if (B.use_passes)
+            for (int t = 0; t < kTiers; ++t) {
+                cudaStream_t cs;
+                cudaError_t r = stream_for(t, &cs);
+                if (r != cudaSuccess) return r;
+                r = traced(launch_passes(B, which, t, taps, phys, d, cs, pass_ev ? pass_ev + t * 6 + (which ? 3 : 0) : nullptr),
+                           "pass kernels");
+                if (r != cudaSuccess) return r;
+                r = join(t, cs);
                 if (r != cudaSuccess) return r;
             }
-            cudaError_t r;
+        for (int c = 0; c < kNumClasses; ++c) {
+            if (B.mode[c] == 3) continue;
+            cudaStream_t cs;
+            cudaError_t r = stream_for(c, &cs);
+            if (r != cudaSuccess) return r;
             if (cls_ev) cudaEventRecord(cls_ev[(which * kNumClasses + c) * 2], cs);
             if (B.mode[c] == 0) r = launch_fast(B, which, c, taps, phys, d, cs);
             else if (which == 0) { k_predict<<<B.grid[0][c], kThreads, B.smem[0][c], cs>>>(B, taps, phys, c); r = cudaGetLastError(); }
             else { k_correct<<<B.grid[1][c], kThreads, B.smem[1][c], cs>>>(B, phys, d, c); r = cudaGetLastError(); }
-            if (r != cudaSuccess) return r;
+            if (r != cudaSuccess) return traced(r, "box-streaming kernels");
             if (cls_ev) cudaEventRecord(cls_ev[(which * kNumClasses + c) * 2 + 1], cs);
-            if (ss) {
-                r = cudaEventRecord(ss->join[c], cs);
-                if (r != cudaSuccess) return r;
-            }
+            r = join(c, cs);
+            if (r != cudaSuccess) return r;
         }
-        if (ss)
-            for (int c = 0; c < kNumClasses; ++c) {
-                cudaError_t r = cudaStreamWaitEvent(s, ss->join[c], 0);
+        for (int c = 0; c < kNumClasses; ++c)
+            if (joined[c]) {
+                cudaError_t r = traced(cudaStreamWaitEvent(s, ss->join[c], 0), "join wait");
                 if (r != cudaSuccess) return r;
             }
         return cudaSuccess;
     };
     e = run_phase(0);
     if (e != cudaSuccess) return e;
+    if (B.use_passes) {
+        if (bin_ev) cudaEventRecord(bin_ev[2], s);
+        e = traced(launch_field(B, phys, d, s), "field pass");
+        if (e != cudaSuccess) return e;
+        if (bin_ev) cudaEventRecord(bin_ev[3], s);
+    }
     if (ev) cudaEventRecord(ev[2], s);
     e = run_phase(1);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[3], s);
-    e = launch_box_update(B, false, s);
+    e = traced(launch_box_update(B, false, s), "box update");
     if (ev) cudaEventRecord(ev[4], s);
     return e;
 }

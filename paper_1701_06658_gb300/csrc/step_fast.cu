@@ -1,6 +1,7 @@
 // Host side of the register-ring kernels: variant table, configuration and launch.
 #include "lsgg_internal.cuh"
 #include "step_fast.cuh"
+#include "../../include/lsgg.h"
 
 namespace lsgg {
 
@@ -52,4 +53,33 @@ cudaError_t launch_fast(const StepBuffers& B, int which, int cls, const Taps& ta
     return cudaLaunchKernel(k.fn, dim3(B.grid[1][cls]), dim3(k.threads), args, k.smem, s);
 }
 
+// An mbarrier with one expected arrival that never comes: the poll loop must
+// give up after `iterations` tries and report it.
+__global__ void k_wait_timeout(int iterations, int* out) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        fast::mbar_init(&bar, 1);
+        fast::fence_mbar_init();
+    }
+    __syncthreads();
+    bool done = false;
+    for (int i = 0; i < iterations && !done; ++i) done = fast::mbar_test(&bar, 0u);
+    if (threadIdx.x == 0) *out = done ? 0 : 1;
+}
+
 }  // namespace lsgg
+
+extern "C" int lsgg_debug_wait_timeout(int32_t device, int32_t iterations, int32_t* timed_out) {
+    if (!timed_out || iterations < 1 || iterations > (1 << 24)) return LSGG_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return LSGG_ERR_CUDA; }
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return LSGG_ERR_OUT_OF_MEMORY; }
+    lsgg::k_wait_timeout<<<1, 32>>>(iterations, d);
+    int h = -1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return LSGG_ERR_CUDA;
+    *timed_out = h;
+    return LSGG_OK;
+}

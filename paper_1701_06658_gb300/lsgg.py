@@ -30,7 +30,7 @@ ERR_UNSUPPORTED = -8
 INIT_VORONOI, INIT_LAGUERRE = 0, 1
 PHYSICS_IDEAL, PHYSICS_READ_SHOCKLEY, PHYSICS_MAGNETIC = 0, 1, 2
 STORAGE_FP32, STORAGE_BF16 = 0, 1
-EXEC_BATCHED, EXEC_PLAIN = 0, 1
+EXEC_BATCHED, EXEC_PLAIN, EXEC_STREAMED = 0, 1, 2
 MOBILITY_STEP, MOBILITY_EQ20 = 0, 1
 
 _dp = C.POINTER(C.c_double)
@@ -60,6 +60,7 @@ class Stats(C.Structure):
         ("steps_done", C.c_int64), ("cell_updates", C.c_int64), ("alive", C.c_int64), ("box_cells", C.c_int64),
         ("arena_capacity", C.c_int64), ("superimposition", C.c_double),
         ("device_bytes", C.c_int64), ("n_classes", C.c_int32), ("class_count", C.c_int32 * 8),
+        ("pass_cells", C.c_int64 * 2),
     ]
 
 
@@ -104,8 +105,11 @@ _SIGS = {
     "lsgg_server_destroy": (C.c_int, [C.c_void_p]),
     "lsgg_grain_neighbours": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32]),
     "lsgg_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_int32)]),
+    "lsgg_debug_set_capacity": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lsgg_debug_wait_timeout": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
+    "lsgg_pass_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
 }
 
 
@@ -200,6 +204,16 @@ def autotune(ctx, steps_per_trial: int = 2, dt: float = 1.0) -> dict:
     return {"k_predict": chosen[0:5].tolist(), "k_correct": chosen[5:10].tolist()}
 
 
+def debug_set_capacity(ctx, capacity: int):
+    _check("debug_set_capacity", lib().lsgg_debug_set_capacity(ctx, int(capacity)))
+
+
+def debug_wait_timeout(device: int, iterations: int) -> bool:
+    out = C.c_int32(-1)
+    _check("debug_wait_timeout", lib().lsgg_debug_wait_timeout(device, iterations, C.byref(out)))
+    return out.value == 1
+
+
 def profile(ctx, enable: bool):
     _check("profile", lib().lsgg_profile(ctx, 1 if enable else 0))
 
@@ -213,6 +227,21 @@ def kernel_times(ctx):
     cnt = np.zeros(4, np.int64)
     _check("kernel_times", lib().lsgg_kernel_times(ctx, _ptr(ms, C.c_double), _ptr(cnt, C.c_int64)))
     return dict(zip(KERNEL_GROUPS, ms.tolist())), dict(zip(KERNEL_GROUPS, cnt.tolist()))
+
+
+PASS_NAMES = ("p_conv_xy", "p_conv_z", "p_redist_xy", "p_redist_z")
+
+
+def pass_times(ctx):
+    """{name: (ms, launches)} of the pass path since the previous call: the
+    per-tier passes as "name[tierT]", plus "k_bin" and "p_field"."""
+    ms = np.zeros(10, np.float64)
+    cnt = np.zeros(10, np.int64)
+    _check("pass_times", lib().lsgg_pass_times(ctx, _ptr(ms, C.c_double), _ptr(cnt, C.c_int64)))
+    out = {f"{PASS_NAMES[k]}[tier{t}]": (float(ms[t * 4 + k]), int(cnt[t * 4 + k])) for t in range(2) for k in range(4)}
+    out["k_bin"] = (float(ms[8]), int(cnt[8]))
+    out["p_field"] = (float(ms[9]), int(cnt[9]))
+    return out
 
 
 class Box(C.Structure):

@@ -272,11 +272,11 @@ def test_autotune_keeps_results_bitwise(L):
     run (3 x 2 tuning steps) equals an untuned run of as many steps."""
     N, G = 64, 50
     seeds = I.voronoi_seeds(24, G, (N, N, N))
-    with L.Microstructure(N, N, N, G, seeds=seeds) as a:
+    with L.Microstructure(N, N, N, G, seeds=seeds, exec_mode=L.EXEC_STREAMED) as a:
         a.step(6, 1.0)
         pa = L.get_phi(a.ctx)
         ba = a.boxes()
-    with L.Microstructure(N, N, N, G, seeds=seeds) as b:
+    with L.Microstructure(N, N, N, G, seeds=seeds, exec_mode=L.EXEC_STREAMED) as b:
         chosen = L.autotune(b.ctx, 2, 1.0)
         assert b.stats().steps_done == 6
         pb = L.get_phi(b.ctx)
@@ -284,3 +284,59 @@ def test_autotune_keeps_results_bitwise(L):
     assert any(v >= 0 for v in chosen["k_predict"])
     assert np.array_equal(ba, bb)
     assert np.array_equal(pa, pb)
+
+
+@pytest.mark.parametrize("shape,G,seed", [((64, 64, 64), 50, 31), ((40, 72, 56), 30, 32), ((24, 24, 24), 5, 33),
+                                          ((96, 96, 96), 12, 34)])
+def test_pass_path_matches_box_streaming(L, shape, G, seed):
+    """The pass path (five passes over plane / column work items) and the
+    box-streaming kernels compute the same step: same boxes, phi within 1e-5
+    over 6 steps, on cubic, non-cubic, full-axis (few grains in a small
+    domain) and large-box (x, y sides above 64) cases."""
+    nx, ny, nz = shape
+    seeds = I.voronoi_seeds(seed, G, (nx, ny, nz))
+    out = {}
+    for mode in (L.EXEC_BATCHED, L.EXEC_STREAMED):
+        with L.Microstructure(nx, ny, nz, G, seeds=seeds, exec_mode=mode) as ms:
+            ms.step(6, 1.0)
+            ms.sync()
+            out[mode] = (ms.boxes(), L.get_phi(ms.ctx), ms.grain_volumes())
+    a, b = out[L.EXEC_BATCHED], out[L.EXEC_STREAMED]
+    assert np.array_equal(a[0], b[0])
+    assert np.max(np.abs(a[1] - b[1])) <= 1e-5
+    assert np.max(np.abs(a[2] - b[2])) <= 1e-3
+
+
+def test_pass_times_cover_every_pass(L):
+    """Profiled steps on the pass path report each pass of each tier once per step."""
+    N, G = 64, 50
+    seeds = I.voronoi_seeds(35, G, (N, N, N))
+    with L.Microstructure(N, N, N, G, seeds=seeds) as ms:
+        L.profile(ms.ctx, True)
+        ms.step(3, 1.0)
+        L.kernel_times(ms.ctx)
+        pt = L.pass_times(ms.ctx)
+        L.profile(ms.ctx, False)
+    assert len(pt) == 10
+    for name, (ms_, n) in pt.items():
+        assert n == 3, (name, n)
+        assert ms_ >= 0.0
+
+
+def test_field_pass_with_overflowing_tile_lists(L):
+    """Dense small grains put more boxes on a domain tile than its list holds
+    (over 128): the field pass then tests every box for those tiles, and the
+    step still equals the box-streaming kernels' step."""
+    N, G = 64, 2000
+    seeds = I.voronoi_seeds(36, G, (N, N, N))
+    out = {}
+    for mode in (L.EXEC_BATCHED, L.EXEC_STREAMED):
+        with L.Microstructure(N, N, N, G, seeds=seeds, exec_mode=mode) as ms:
+            s = ms.stats()
+            assert s.superimposition > 20          # about 260 boxes per 32 x 8 x 16 tile
+            ms.step(2, 1.0)
+            ms.sync()
+            out[mode] = (ms.boxes(), L.get_phi(ms.ctx))
+    a, b = out[L.EXEC_BATCHED], out[L.EXEC_STREAMED]
+    assert np.array_equal(a[0], b[0])
+    assert np.max(np.abs(a[1] - b[1])) <= 1e-5
