@@ -132,11 +132,37 @@ __device__ __forceinline__ float line_min(const float* in, int i, int n, int str
     return s ? best : -best;
 }
 
-__device__ __forceinline__ void opp_delta(float a, bool pos, float nbv, float& dmin) {
-    if ((nbv > 0.0f) != pos) {
-        float d = a / (a + fabsf(nbv));
-        dmin = fminf(dmin, d);
-    }
+// Reference cells of the re-initialisation (Sec. 2.1.6): a cell with a face
+// neighbour of the opposite sign.  On an axis whose opposite-sign neighbours
+// have largest magnitude n, linear interpolation puts the zero crossing at
+// a / (a + n) cells (a = |phi|); the distance to the plane through the
+// crossings of all such axes is 1 / sqrt(sum over them of ((a + n) / a)^2).
+// opp_max: n for one axis' two neighbours, -1 when neither is opposite.
+__device__ __forceinline__ float opp_max(bool pos, float l, float r) {
+    float n = -1.0f;
+    if ((l > 0.0f) != pos) n = fabsf(l);
+    if ((r > 0.0f) != pos) n = fmaxf(n, fabsf(r));
+    return n;
+}
+
+// Magnitude of phi after classification: eps for cells that are not reference
+// cells, else the planar-exact distance (0 when phi = 0).
+__device__ __forceinline__ float ref_magnitude(float a, float n0, float n1, float n2, float eps) {
+    if (n0 < 0.0f && n1 < 0.0f && n2 < 0.0f) return eps;
+    const float ra = 1.0f / a;                  // a = 0: inf, and the distance is 0
+    float s = 0.0f;
+    if (n0 >= 0.0f) { const float r = fmaf(n0, ra, 1.0f); s = fmaf(r, r, s); }
+    if (n1 >= 0.0f) { const float r = fmaf(n1, ra, 1.0f); s = fmaf(r, r, s); }
+    if (n2 >= 0.0f) { const float r = fmaf(n2, ra, 1.0f); s = fmaf(r, r, s); }
+    return rsqrtf(s);
+}
+
+// Signed classified value of a cell from its six face neighbours.
+__device__ __forceinline__ float classify_cell(float v, float xl, float xr, float yl, float yr, float zl, float zr,
+                                               float eps) {
+    const bool pos = v > 0.0f;
+    const float mag = ref_magnitude(fabsf(v), opp_max(pos, xl, xr), opp_max(pos, yl, yr), opp_max(pos, zl, zr), eps);
+    return pos ? mag : -mag;
 }
 
 // Pull the next box of class `cls` for kernel `which`; -1 when the queue is empty.

@@ -30,7 +30,7 @@ constexpr int kNumClasses = 5;          // box side <= 32, 40, 48, 64, larger (g
 constexpr int kRedistReach = 6;         // taxicab steps below eps = 7 (exact fixed point)
 constexpr int kTiers = 2;               // pass path: boxes with x, y sides <= 32 and <= 64
 constexpr int kPassChunk = 256;         // columns per column item of the pass path
-constexpr int kTileX = 32, kTileY = 8, kTileZ = 16;   // domain tiles of the field pass
+constexpr int kTileX = 32, kTileY = 8, kTileZ = 8;    // domain tiles of the field pass
 constexpr int kTileCap = 128;           // boxes listed per tile (more: the tile scans all boxes)
 
 struct Box {
@@ -164,9 +164,8 @@ struct StepBuffers {
     long long chunk_item_cap;       // entries (n_boxes * 64 * 64 / kPassChunk)
     int use_passes;
     int tier_side[kTiers];
-    int tier_threads[kTiers];       // threads per CTA of the plane passes
+    int tier_threads[kTiers];       // threads per CTA of the plane passes (= tier side)
     int pgrid[kTiers][5];           // persistent grid per tier and pass (conv_xy, conv_z, -, redist_xy, redist_z)
-    size_t psmem[kTiers][2];        // dynamic shared memory of the two plane passes
     // field pass: boxes overlapping each domain tile of kTileX x kTileY x kTileZ cells
     int* tile_cnt;                  // [n_tiles]
     int* tile_list;                 // [n_tiles * kTileCap]

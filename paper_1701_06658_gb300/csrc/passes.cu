@@ -34,11 +34,8 @@
 
 namespace lsgg {
 
-constexpr int kPVX = 4;              // convolution x-pass outputs per task
-constexpr int kPVD = 8;              // taxicab x-pass outputs per task
-constexpr int kPVY = 8;              // taxicab y-pass outputs per task
-constexpr int kPCY = 4;              // convolution y-pass outputs per task
 constexpr int kZB = 8;               // planes loaded ahead by the column passes
+constexpr int kStageU = 8;           // loads in flight per thread when staging a plane
 constexpr int kReachP = kRedistReach;
 constexpr int kColThreads = kPassChunk;
 
@@ -59,21 +56,23 @@ __device__ __forceinline__ float conv_xy_of_const(const float (&g)[2 * R + 1], f
 // ---------------------------------------------------------------------------
 // pass 1: xy convolution of one plane
 // ---------------------------------------------------------------------------
-template <int R>
-__global__ void __launch_bounds__(256)
+// A CTA of SIDE threads takes one (box, plane) item at a time: the plane of
+// phi is staged row by row (old box -> new box, -eps outside), then thread x
+// walks down column x, convolving each padded row along x from shared memory
+// and keeping the last 2R + 1 row results in registers for the y convolution.
+template <int R, int SIDE>
+__global__ void __launch_bounds__(SIDE)
 p_conv_xy(StepBuffers B, Taps taps, int tier) {
     constexpr int W = 2 * R + 1;
-    extern __shared__ __align__(16) float sm[];
+    constexpr int PS = SIDE + 2 * R;
+    __shared__ float P[(PS + W) * PS];      // W spare rows: the unrolled row loop may read past the plane
+    __shared__ int mapx[PS], mapy[PS];
     if (halted(B)) return;
     const Domain D = B.dom;
     float g[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) g[k] = taps.g[k];
-    const int side = B.tier_side[tier];
-    float* P = sm;                                          // (side+2R)^2 staged plane
-    float* Xp = P + (side + 2 * R) * (side + 2 * R);        // (side+2R) rows x side after the x pass
-    int* mapx = reinterpret_cast<int*>(Xp + side * (side + 2 * R));
-    int* mapy = mapx + side + 2 * R;
+    const int t = threadIdx.x;
     const int n_items = B.st->n_planes[tier];
     const int2* items = B.plane_items + B.st->plane_base[tier];
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -84,7 +83,7 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         const bool fx = nx == D.nx, fy = ny == D.ny;
         const int PXa = nx + 2 * R, PYa = ny + 2 * R;
         __syncthreads();                                    // previous item done with the buffers
-        for (int i = threadIdx.x; i < PXa; i += blockDim.x) {
+        for (int i = t; i < PXa; i += SIDE) {
             int xl = i - R, v = -1;
             if (fx || (xl >= 0 && xl < nx)) {
                 if (fx) xl = pmod(xl, nx);
@@ -93,7 +92,7 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
             }
             mapx[i] = v;
         }
-        for (int i = threadIdx.x; i < PYa; i += blockDim.x) {
+        for (int i = t; i < PYa; i += SIDE) {
             int yl = i - R, v = -1;
             if (fy || (yl >= 0 && yl < ny)) {
                 if (fy) yl = pmod(yl, ny);
@@ -105,47 +104,48 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         const int ozl = pmod(nb.oz + z - ob.oz, D.nz);
         const int zold = ozl < ob.nz ? ozl : -1;
         const float* src = B.X + ob.off + (long long)(zold < 0 ? 0 : zold) * plane_stride(ob.nx, ob.ny);
-        const Div16 dPX(PXa);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < PXa * PYa; idx += blockDim.x) {
-            const int yp = dPX(idx), xp = idx - yp * PXa;
-            const int mx = mapx[xp], my = mapy[yp];
-            P[idx] = (zold >= 0 && mx >= 0 && my >= 0) ? src[my * ob.nx + mx] : -D.eps;
-        }
-        __syncthreads();
-        const int nxs = (nx + kPVX - 1) / kPVX;
-        const Div16 dXS(nxs);
-        for (int t = threadIdx.x; t < PYa * nxs; t += blockDim.x) {
-            const int yp = dXS(t), x0 = (t - yp * nxs) * kPVX;
-            const float* row = P + yp * PXa + x0;
-            float in[kPVX + 2 * R];
+        {   // stage the padded plane, kStageU loads in flight per thread
+            const int n = PXa * PYa;
+            const Div16 dPX(PXa);
+            for (int i0 = t; i0 < n; i0 += SIDE * kStageU) {
+                float v[kStageU];
 #pragma unroll
-            for (int j = 0; j < kPVX + 2 * R; ++j) in[j] = x0 + j < PXa ? row[j] : 0.0f;
+                for (int u = 0; u < kStageU; ++u) {
+                    const int i = i0 + u * SIDE;
+                    v[u] = -D.eps;
+                    if (i < n && zold >= 0) {
+                        const int yp = dPX(i), xp = i - yp * PXa;
+                        const int mx = mapx[xp], my = mapy[yp];
+                        if (mx >= 0 && my >= 0) v[u] = src[my * ob.nx + mx];
+                    }
+                }
 #pragma unroll
-            for (int v = 0; v < kPVX; ++v) {
-                float acc = 0.0f;
-#pragma unroll
-                for (int k = 0; k < W; ++k) acc = fmaf(g[k], in[v + k], acc);
-                if (x0 + v < nx) Xp[yp * nx + x0 + v] = acc;
+                for (int u = 0; u < kStageU; ++u)
+                    if (i0 + u * SIDE < n) P[i0 + u * SIDE] = v[u];
             }
         }
         __syncthreads();
-        float* dst = B.Z + nb.off + (long long)z * plane_stride(nx, ny);
-        const Div16 dNX(nx);
-        const int nys = (ny + kPCY - 1) / kPCY;
-        for (int t = threadIdx.x; t < nx * nys; t += blockDim.x) {
-            const int ys = dNX(t), x = t - ys * nx;
-            const int y0 = ys * kPCY;
-            const float* col = Xp + y0 * nx + x;
-            float in[kPCY + 2 * R];
+        if (t < nx) {
+            float* dst = B.Z + nb.off + (long long)z * plane_stride(nx, ny) + t;
+            const float* prow = P + t;
+            float win[W];                                   // x-convolved rows, slot = row mod W
+            for (int yb = 0; yb < PYa; yb += W) {
+                // W rows per trip without branches, so that their independent FMA
+                // chains interleave; rows past the plane are computed and dropped
 #pragma unroll
-            for (int j = 0; j < kPCY + 2 * R; ++j) in[j] = y0 + j < PYa ? col[j * nx] : 0.0f;
+                for (int s = 0; s < W; ++s) {
+                    const int yp = yb + s;
+                    const float* r = prow + yp * PXa;
+                    float acc = 0.0f;
 #pragma unroll
-            for (int v = 0; v < kPCY; ++v) {
-                float acc = 0.0f;
+                    for (int k = 0; k < W; ++k) acc = fmaf(g[k], r[k], acc);
+                    win[s] = acc;
+                    float o = 0.0f;                         // output row y = yp - 2R: rows y .. yp
 #pragma unroll
-                for (int k = 0; k < W; ++k) acc = fmaf(g[k], in[v + k], acc);
-                if (y0 + v < ny) dst[(y0 + v) * nx + x] = acc;
+                    for (int k = 0; k < W; ++k) o = fmaf(g[k], win[(s + 1 + k) % W], o);
+                    if (yp >= 2 * R && yp < PYa) dst[(yp - 2 * R) * nx] = o;
+                }
             }
         }
     }
@@ -328,7 +328,7 @@ __device__ __forceinline__ void stage_tile_box(const StepBuffers& B, int b, int 
     t.zmask = m;
 }
 
-__global__ void __launch_bounds__(kTileX * kTileY, 2)
+__global__ void __launch_bounds__(kTileX * kTileY, 3)
 p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
     __shared__ TileBox s_tb[kTileCap];
     if (halted(B)) return;
@@ -420,133 +420,105 @@ p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
 // ---------------------------------------------------------------------------
 // pass 4: classification + x / y taxicab passes of one plane
 // ---------------------------------------------------------------------------
-template <int N>
-__device__ __forceinline__ void sweep_window(float (&w)[N], const bool (&valid)[N]) {
-    float f[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        float a = fabsf(w[j]);
-        if (j > 0 && valid[j] && valid[j - 1] && sgn_pos(w[j]) == sgn_pos(w[j - 1])) a = fminf(a, f[j - 1] + 1.0f);
-        f[j] = a;
+// Sign-blocked min-plus along one line of n cells, in place (stride st):
+// f_j = min(|v_j|, f_{j-1} + 1) over a run of one sign, forward then backward.
+// A periodic line is swept twice around in each direction.  Cells further
+// than 6 apart add at least 7 >= eps, so this equals the 6-step window of
+// the box-streaming kernels.  `out` (optional) receives the final values.
+__device__ __forceinline__ void line_sweep(float* L, int n, int st, bool wrap, float* out, int out_st) {
+    const int laps = wrap ? 2 : 1;
+    float fp = 0.0f;
+    bool sp = false;
+    for (int j = 0; j < laps * n; ++j) {
+        const int i = j < n ? j : j - n;
+        const float v = L[i * st];
+        const bool sv = sgn_pos(v);
+        float a = fabsf(v);
+        if (j > 0 && sv == sp) a = fminf(a, fp + 1.0f);
+        L[i * st] = sv ? a : -a;
+        fp = a;
+        sp = sv;
     }
-#pragma unroll
-    for (int j = N - 2; j >= 0; --j)
-        if (valid[j] && valid[j + 1] && sgn_pos(w[j]) == sgn_pos(w[j + 1])) f[j] = fminf(f[j], f[j + 1] + 1.0f);
-#pragma unroll
-    for (int j = 0; j < N; ++j) w[j] = sgn_pos(w[j]) ? f[j] : -f[j];
+    for (int j = laps * n - 2; j >= 0; --j) {
+        const int i = j < n ? j : j - n;
+        const float v = L[i * st];
+        const bool sv = sgn_pos(v);
+        float a = fabsf(v);
+        if (sv == sp) a = fminf(a, fp + 1.0f);
+        const float f = sv ? a : -a;
+        L[i * st] = f;
+        if (out && j < n) out[i * out_st] = f;
+        fp = a;
+        sp = sv;
+    }
+    if (out) {                                       // the last cell is final after the forward sweep
+        const int i = n - 1;
+        if (laps == 1) out[i * out_st] = L[i * st];
+    }
 }
 
-__device__ __forceinline__ void axis_inv2(float a, bool pos, float l, float r, float& inv2, bool& zero) {
-    float dmin = FLT_MAX;
-    opp_delta(a, pos, l, dmin);
-    opp_delta(a, pos, r, dmin);
-    if (dmin < FLT_MAX) { if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
-}
-
-__global__ void __launch_bounds__(256)
+template <int SIDE>
+__global__ void __launch_bounds__(SIDE)
 p_redist_xy(StepBuffers B, int tier) {
-    extern __shared__ __align__(16) float sm[];
+    constexpr int PG = SIDE + 1;                      // odd pitch: row sweeps hit distinct banks
+    constexpr int U = 4;                              // rows classified per trip
+    __shared__ float G[(SIDE + U) * PG];              // U spare rows for the unrolled trip
     if (halted(B)) return;
     const Domain D = B.dom;
     const float eps = D.eps;
-    const int side = B.tier_side[tier];
-    float* C0 = sm;
-    float* G = C0 + side * side;
-    float* H = G + side * side;
+    const int t = threadIdx.x;
     const int n_items = B.st->n_planes[tier];
     const int2* items = B.plane_items + B.st->plane_base[tier];
-    constexpr int NXW = kPVD + 2 * kReachP;
-    constexpr int NYW = kPVY + 2 * kReachP;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int2 it = items[item];
         const int b = it.x, z = it.y;
         const Box nb = B.cur[b];
-        const int nx = nb.nx, ny = nb.ny, nz = nb.nz, A = nx * ny;
+        const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
         const bool fx = nx == D.nx, fy = ny == D.ny, fz = nz == D.nz;
         const int ps = plane_stride(nx, ny);
         const float* zb = B.Z + nb.off;
-        __syncthreads();                                    // previous item done with the buffers
-        for (int i = threadIdx.x; i < A; i += blockDim.x) C0[i] = zb[(long long)z * ps + i];
         const int zm = fz ? pmod(z - 1, nz) : z - 1, zp = fz ? pmod(z + 1, nz) : z + 1;
         const bool has_m = zm >= 0, has_p = zp < nz;
-        const Div16 dNX(nx);
-        __syncthreads();
-        // reference cells (a neighbour of opposite sign) get the planar-exact
-        // distance 1 / sqrt(sum over such axes of 1 / d^2); others eps
-        for (int i = threadIdx.x; i < A; i += blockDim.x) {
-            const int y = dNX(i), x = i - y * nx;
-            const float val = C0[i];
-            const bool pos = val > 0.0f;
-            const float xl = x > 0 ? C0[i - 1] : (fx ? C0[i + nx - 1] : -eps);
-            const float xr = x < nx - 1 ? C0[i + 1] : (fx ? C0[i - nx + 1] : -eps);
-            const float yl = y > 0 ? C0[i - nx] : (fy ? C0[i + (ny - 1) * nx] : -eps);
-            const float yr = y < ny - 1 ? C0[i + nx] : (fy ? C0[i - (ny - 1) * nx] : -eps);
-            const float zl = has_m ? zb[(long long)zm * ps + i] : -eps;
-            const float zr = has_p ? zb[(long long)zp * ps + i] : -eps;
-            const bool any = ((xl > 0.0f) != pos) | ((xr > 0.0f) != pos) | ((yl > 0.0f) != pos) |
-                             ((yr > 0.0f) != pos) | ((zl > 0.0f) != pos) | ((zr > 0.0f) != pos);
-            float mag = eps;
-            if (any) {
-                const float a = fabsf(val);
-                float inv2 = 0.0f;
-                bool zero = false;
-                axis_inv2(a, pos, xl, xr, inv2, zero);
-                axis_inv2(a, pos, yl, yr, inv2, zero);
-                axis_inv2(a, pos, zl, zr, inv2, zero);
-                mag = zero ? 0.0f : 1.0f / sqrtf(inv2);
-            }
-            G[i] = pos ? mag : -mag;
-        }
-        __syncthreads();
-        // x pass G -> H
-        const int nxs = (nx + kPVD - 1) / kPVD;
-        const Div16 dXS(nxs);
-        for (int t = threadIdx.x; t < ny * nxs; t += blockDim.x) {
-            const int y = dXS(t), x0 = (t - y * nxs) * kPVD;
-            const float* row = G + y * nx;
-            float w[NXW];
-            bool valid[NXW];
-            if (!fx) {
+        __syncthreads();                                    // previous item done with G
+        if (t < nx) {                                       // classification, thread = column
+            // phi_c of plane z and of its z neighbours, read through L1: row y of
+            // the plane is loaded by the whole CTA, so the x neighbours hit L1
+            const int x = t;
+            const float* c = zb + (long long)z * ps;
+            const float* cm = zb + (long long)(has_m ? zm : 0) * ps;
+            const float* cp = zb + (long long)(has_p ? zp : 0) * ps;
+            const int xl_i = x > 0 ? x - 1 : (fx ? nx - 1 : -1);
+            const int xr_i = x < nx - 1 ? x + 1 : (fx ? 0 : -1);
+            float c_prev = fy ? __ldg(c + (ny - 1) * nx + x) : -eps;
+            float c_cur = __ldg(c + x);
+            for (int y0 = 0; y0 < ny; y0 += U) {
+                float cv[U + 1], xl[U], xr[U], zl[U], zr[U];
+                cv[0] = c_cur;
 #pragma unroll
-                for (int j = 0; j < NXW; ++j) {
-                    const int x = x0 - kReachP + j;
-                    valid[j] = x >= 0 && x < nx;
-                    w[j] = valid[j] ? row[x] : 0.0f;
+                for (int u = 0; u < U; ++u) {
+                    const int y = y0 + u;
+                    const bool in = y < ny;
+                    const int yn = y + 1 < ny ? y + 1 : (fy ? 0 : -1);
+                    cv[u + 1] = in && yn >= 0 ? __ldg(c + yn * nx + x) : -eps;
+                    xl[u] = in && xl_i >= 0 ? __ldg(c + y * nx + xl_i) : -eps;
+                    xr[u] = in && xr_i >= 0 ? __ldg(c + y * nx + xr_i) : -eps;
+                    zl[u] = in && has_m ? __ldg(cm + y * nx + x) : -eps;
+                    zr[u] = in && has_p ? __ldg(cp + y * nx + x) : -eps;
                 }
-            } else {
 #pragma unroll
-                for (int j = 0; j < NXW; ++j) { valid[j] = true; w[j] = row[pmod(x0 - kReachP + j, nx)]; }
+                for (int u = 0; u < U; ++u) {
+                    const float yl = u ? cv[u - 1] : c_prev;
+                    G[(y0 + u) * PG + x] = classify_cell(cv[u], xl[u], xr[u], yl, cv[u + 1], zl[u], zr[u], eps);
+                }
+                c_prev = cv[U - 1];
+                c_cur = cv[U];
             }
-            sweep_window<NXW>(w, valid);
-#pragma unroll
-            for (int v = 0; v < kPVD; ++v)
-                if (x0 + v < nx) H[y * nx + x0 + v] = w[kReachP + v];
         }
         __syncthreads();
-        // y pass H -> Y
-        const int nys = (ny + kPVY - 1) / kPVY;
-        float* out = B.Y + nb.off + (long long)z * ps;
-        for (int t = threadIdx.x; t < nx * nys; t += blockDim.x) {
-            const int ys = dNX(t), x = t - ys * nx;
-            const int y0 = ys * kPVY;
-            float w[NYW];
-            bool valid[NYW];
-            if (!fy) {
-#pragma unroll
-                for (int j = 0; j < NYW; ++j) {
-                    const int y = y0 - kReachP + j;
-                    valid[j] = y >= 0 && y < ny;
-                    w[j] = valid[j] ? H[y * nx + x] : 0.0f;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < NYW; ++j) { valid[j] = true; w[j] = H[pmod(y0 - kReachP + j, ny) * nx + x]; }
-            }
-            sweep_window<NYW>(w, valid);
-#pragma unroll
-            for (int v = 0; v < kPVY; ++v)
-                if (y0 + v < ny) out[(y0 + v) * nx + x] = w[kReachP + v];
-        }
+        if (t < ny) line_sweep(G + t * PG, nx, 1, fx, nullptr, 0);      // x pass, thread = row
+        __syncthreads();
+        if (t < nx)                                         // y pass, thread = column -> Y
+            line_sweep(G + t, ny, PG, fy, B.Y + nb.off + (long long)z * ps + t, nx);
     }
 }
 
@@ -648,60 +620,52 @@ p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// The radius-specialised convolution kernels (R = 1 .. kMaxRadius); the z pass
-// with or without the velocity correction of Eq. (10).
+// The radius-specialised convolution kernels (R = 1 .. kMaxRadius) per tier
+// side; the z pass with or without the velocity correction of Eq. (10).
+constexpr int kTierSide[kTiers] = {32, 64};
+
 struct PassFns {
-    const void* conv_xy;
+    const void* conv_xy[kTiers];
     const void* conv_z;
+    const void* redist_xy[kTiers];
 };
 
 template <int R>
 static PassFns pass_fns_r(bool phys) {
-    return PassFns{reinterpret_cast<const void*>(p_conv_xy<R>),
-                   phys ? reinterpret_cast<const void*>(p_conv_z<R, true>)
-                        : reinterpret_cast<const void*>(p_conv_z<R, false>)};
+    static_assert(kTiers == 2, "one instantiation per tier side");
+    PassFns f;
+    f.conv_xy[0] = reinterpret_cast<const void*>(p_conv_xy<R, 32>);
+    f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 64>);
+    f.conv_z = phys ? reinterpret_cast<const void*>(p_conv_z<R, true>) : reinterpret_cast<const void*>(p_conv_z<R, false>);
+    f.redist_xy[0] = reinterpret_cast<const void*>(p_redist_xy<32>);
+    f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<64>);
+    return f;
 }
 
-static PassFns pass_fns(int R, bool phys) {
+static bool pass_fns(int R, bool phys, PassFns* f) {
     switch (R) {
-        case 1: return pass_fns_r<1>(phys);
-        case 2: return pass_fns_r<2>(phys);
-        case 3: return pass_fns_r<3>(phys);
-        case 4: return pass_fns_r<4>(phys);
-        case 5: return pass_fns_r<5>(phys);
-        case 6: return pass_fns_r<6>(phys);
-        case 7: return pass_fns_r<7>(phys);
-        default: return PassFns{nullptr, nullptr};
+        case 1: *f = pass_fns_r<1>(phys); return true;
+        case 2: *f = pass_fns_r<2>(phys); return true;
+        case 3: *f = pass_fns_r<3>(phys); return true;
+        case 4: *f = pass_fns_r<4>(phys); return true;
+        case 5: *f = pass_fns_r<5>(phys); return true;
+        case 6: *f = pass_fns_r<6>(phys); return true;
+        case 7: *f = pass_fns_r<7>(phys); return true;
+        default: return false;
     }
 }
-
-static size_t pass_smem_conv(int side, int R) {
-    return sizeof(float) * ((size_t)(side + 2 * R) * (side + 2 * R) + (size_t)side * (side + 2 * R)) +
-           sizeof(int) * 2 * (size_t)(side + 2 * R);
-}
-static size_t pass_smem_redist(int side) { return sizeof(float) * 3 * (size_t)side * side; }
 
 cudaError_t configure_passes(StepBuffers& B) {
-    const int sides[kTiers] = {32, 64};
-    const int threads[kTiers] = {128, 256};
+    PassFns fn;
+    if (!pass_fns(B.dom.radius, true, &fn)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
     for (int t = 0; t < kTiers; ++t) {
-        B.tier_side[t] = sides[t];
-        B.tier_threads[t] = threads[t];
-        B.psmem[t][0] = pass_smem_conv(sides[t], B.dom.radius);
-        B.psmem[t][1] = pass_smem_redist(sides[t]);
-    }
-    const PassFns fn = pass_fns(B.dom.radius, true);
-    if (!fn.conv_xy) return cudaErrorInvalidValue;
-    cudaError_t e = allow_max_dynamic_smem(fn.conv_xy);
-    if (e != cudaSuccess) return e;
-    e = allow_max_dynamic_smem(reinterpret_cast<const void*>(p_redist_xy));
-    if (e != cudaSuccess) return e;
-    for (int t = 0; t < kTiers; ++t) {
+        B.tier_side[t] = kTierSide[t];
+        B.tier_threads[t] = kTierSide[t];
         int o[5] = {0, 0, 1, 0, 0};
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], fn.conv_xy, threads[t], B.psmem[t][0]);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], fn.conv_xy[t], kTierSide[t], 0);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], fn.conv_z, kColThreads, 0);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], p_redist_xy, threads[t], B.psmem[t][1]);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], fn.redist_xy[t], kTierSide[t], 0);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[4], p_redist_z, kColThreads, 0);
         if (e != cudaSuccess) return e;
         for (int k = 0; k < 5; ++k) B.pgrid[t][k] = B.n_sm * (o[k] < 1 ? 1 : o[k]);
@@ -722,19 +686,21 @@ cudaError_t configure_passes(StepBuffers& B) {
 // pass_ev (optional): one event before the first kernel and one after each.
 cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps& taps, const PhysicsDev& phys,
                           const DebugOut& dbg, cudaStream_t s, cudaEvent_t* pass_ev) {
+    PassFns fn;
+    if (!pass_fns(taps.radius, phys.kind != LSGG_PHYSICS_IDEAL, &fn)) return cudaErrorInvalidValue;
     const int nt = B.tier_threads[tier];
     const int* g = B.pgrid[tier];
+    StepBuffers bb = B;
+    Taps tp = taps;
+    PhysicsDev ph = phys;
+    DebugOut db = dbg;
+    int tr = tier;
     int k = 0;
+    cudaError_t e;
     if (pass_ev) cudaEventRecord(pass_ev[k++], s);
     if (which == 0) {
-        const PassFns fn = pass_fns(taps.radius, phys.kind != LSGG_PHYSICS_IDEAL);
-        if (!fn.conv_xy) return cudaErrorInvalidValue;
-        Taps tp = taps;
-        StepBuffers bb = B;
-        int tr = tier;
-        PhysicsDev ph = phys;
         void* a0[] = {&bb, &tp, &tr};
-        cudaError_t e = cudaLaunchKernel(fn.conv_xy, dim3(g[0]), dim3(nt), a0, B.psmem[tier][0], s);
+        e = cudaLaunchKernel(fn.conv_xy[tier], dim3(g[0]), dim3(nt), a0, 0, s);
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
         void* a1[] = {&bb, &tp, &ph, &tr};
@@ -742,9 +708,13 @@ cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps&
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
     } else {
-        p_redist_xy<<<g[3], nt, B.psmem[tier][1], s>>>(B, tier);
+        void* a3[] = {&bb, &tr};
+        e = cudaLaunchKernel(fn.redist_xy[tier], dim3(g[3]), dim3(nt), a3, 0, s);
+        if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
-        p_redist_z<<<g[4], kColThreads, 0, s>>>(B, dbg, tier);
+        void* a4[] = {&bb, &db, &tr};
+        e = cudaLaunchKernel(reinterpret_cast<const void*>(p_redist_z), dim3(g[4]), dim3(kColThreads), a4, 0, s);
+        if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
     }
     return cudaGetLastError();

@@ -145,19 +145,14 @@ __global__ void kp_classify(Domain D, PlainBox p, const float* __restrict__ Cc, 
         int x = (int)(i % nb.nx);
         int y = (int)((i / nb.nx) % nb.ny);
         int z = (int)(i / A);
-        float v = box_value(D, nb, Cc, x, y, z);
-        bool pos = v > 0.0f;
-        float a = fabsf(v), inv2 = 0.0f;
-        bool ref = false, zero = false;
+        const float v = box_value(D, nb, Cc, x, y, z);
+        const bool pos = v > 0.0f;
+        float n[3] = {-1.0f, -1.0f, -1.0f};
         for (int ax = 0; ax < D.dim; ++ax) {
-            float dmin = 3.4e38f;
-            int dx = ax == 0, dy = ax == 1, dz = ax == 2;
-            opp_delta(a, pos, box_value(D, nb, Cc, x - dx, y - dy, z - dz), dmin);
-            opp_delta(a, pos, box_value(D, nb, Cc, x + dx, y + dy, z + dz), dmin);
-            if (dmin < 3.4e38f) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
+            const int dx = ax == 0, dy = ax == 1, dz = ax == 2;
+            n[ax] = opp_max(pos, box_value(D, nb, Cc, x - dx, y - dy, z - dz), box_value(D, nb, Cc, x + dx, y + dy, z + dz));
         }
-        float mag = D.eps;
-        if (ref) mag = zero ? 0.0f : 1.0f / sqrtf(inv2);
+        const float mag = ref_magnitude(fabsf(v), n[0], n[1], n[2], D.eps);
         Gg[nb.off + (long long)z * ps + (long long)y * nb.nx + x] = pos ? mag : -mag;
     }
 }

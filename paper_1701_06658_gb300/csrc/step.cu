@@ -279,36 +279,13 @@ __device__ void correct_box(const StepBuffers& B, const PhysicsDev& phys, const 
             const float* Cp = C + (size_t)pmod(zb + 1, 3) * A;
             for (int i = threadIdx.x; i < A; i += blockDim.x) {
                 int y = i / nx, x = i - y * nx;
-                float v = C0[i];
-                bool pos = v > 0.0f;
-                float a = fabsf(v);
-                float inv2 = 0.0f;
-                bool ref = false, zero = false;
-                {   // x axis
-                    float dmin = FLT_MAX;
-                    float l = x > 0 ? C0[i - 1] : (fx ? C0[i + nx - 1] : -eps);
-                    float r = x < nx - 1 ? C0[i + 1] : (fx ? C0[i - nx + 1] : -eps);
-                    opp_delta(a, pos, l, dmin);
-                    opp_delta(a, pos, r, dmin);
-                    if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
-                }
-                {   // y axis
-                    float dmin = FLT_MAX;
-                    float l = y > 0 ? C0[i - nx] : (fy ? C0[i + (ny - 1) * nx] : -eps);
-                    float r = y < ny - 1 ? C0[i + nx] : (fy ? C0[i - (ny - 1) * nx] : -eps);
-                    opp_delta(a, pos, l, dmin);
-                    opp_delta(a, pos, r, dmin);
-                    if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
-                }
-                if (is3d) {
-                    float dmin = FLT_MAX;
-                    opp_delta(a, pos, Cm[i], dmin);
-                    opp_delta(a, pos, Cp[i], dmin);
-                    if (dmin < FLT_MAX) { ref = true; if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
-                }
-                float mag = eps;
-                if (ref) mag = zero ? 0.0f : 1.0f / sqrtf(inv2);
-                G[i] = pos ? mag : -mag;
+                const float xl = x > 0 ? C0[i - 1] : (fx ? C0[i + nx - 1] : -eps);
+                const float xr = x < nx - 1 ? C0[i + 1] : (fx ? C0[i - nx + 1] : -eps);
+                const float yl = y > 0 ? C0[i - nx] : (fy ? C0[i + (ny - 1) * nx] : -eps);
+                const float yr = y < ny - 1 ? C0[i + nx] : (fy ? C0[i - (ny - 1) * nx] : -eps);
+                // 2D: no z neighbours (on the z axis nothing is opposite)
+                const float zl = is3d ? Cm[i] : C0[i], zr = is3d ? Cp[i] : C0[i];
+                G[i] = classify_cell(C0[i], xl, xr, yl, yr, zl, zr, eps);
             }
             __syncthreads();
             // ---- C: x pass G -> H, y pass H -> forward z sweep into F ----
@@ -413,6 +390,57 @@ k_correct(StepBuffers B, PhysicsDev phys, DebugOut dbg, int cls) {
 // box update (single CTA)
 // ---------------------------------------------------------------------------
 
+// Block-wide exclusive scan of N ints per thread (thread order): pre = the sum
+// over lower threads, tot = the block total.  s: (blockDim / 32) * N ints.
+template <int N>
+__device__ __forceinline__ void block_exclusive_scan(const int (&v)[N], int (&pre)[N], int (&tot)[N], int* s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int inc[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        int x = v[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        inc[k] = x;
+        if (lane == 31) s[warp * N + k] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            int x = lane < nw ? s[lane * N + k] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < nw) s[lane * N + k] = x;          // inclusive prefix over warps
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        pre[k] = inc[k] - v[k] + (warp ? s[(warp - 1) * N + k] : 0);
+        tot[k] = s[(nw - 1) * N + k];
+    }
+    __syncthreads();
+}
+
+// Block-wide sum (s: blockDim long longs), the same value on every thread.
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    return t;
+}
+
 // Size class of a box: the smallest class whose side holds the x and y extents
 // of both its new layout and the layout its state is read from.
 __device__ __forceinline__ int box_class(const StepBuffers& B, const Box& b, const Box& p) {
@@ -430,16 +458,10 @@ __device__ __forceinline__ int pass_tier(const StepBuffers& B, int c) {
 __global__ void __launch_bounds__(kBoxUpdateThreads)
 k_box_update(StepBuffers B, int layout_only) {
     __shared__ long long s_part[kBoxUpdateThreads];
-    __shared__ int s_cnt[kNumClasses];
-    __shared__ long long s_alive;
-    __shared__ int s_np[kTiers], s_nc[kTiers], s_wp[kTiers], s_wc[kTiers];
-    __shared__ unsigned long long s_tc[kTiers];
+    __shared__ int s_scan[(kBoxUpdateThreads / 32) * (kNumClasses + 2 * kTiers)];
     const int G = B.n_boxes;
     const Domain D = B.dom;
     if (*(volatile int*)&B.st->halt && !layout_only) return;
-    if (threadIdx.x < kNumClasses) s_cnt[threadIdx.x] = 0;
-    if (threadIdx.x < kTiers) { s_np[threadIdx.x] = 0; s_nc[threadIdx.x] = 0; s_tc[threadIdx.x] = 0; }
-    if (threadIdx.x == 0) s_alive = 0;
     const int per = (G + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * per, b1 = min(G, b0 + per);
     long long sum = 0, done = 0;
@@ -500,73 +522,76 @@ k_box_update(StepBuffers B, int layout_only) {
         return;
     }
     long long off = s_part[threadIdx.x] - sum;
-    long long cells = 0, alive = 0;
+    // per-thread counts: boxes per class (work lists), pass-path planes and
+    // column chunks per tier; their block-wide exclusive scans place every
+    // box's entries in box order
+    constexpr int NV = kNumClasses + 2 * kTiers;
+    int cnt[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) cnt[k] = 0;
+    long long cells = 0, alive = 0, tcell[kTiers] = {};
     for (int b = b0; b < b1; ++b) {
         Box cb = B.cur[b];
         cb.off = off;
         off += box_elems(cb);
         B.cur[b] = cb;
         if (cb.nx > 0) {
-            int c = box_class(B, cb, B.prev[b]);
-            int w = atomicAdd(&s_cnt[c], 1);
+            const int c = box_class(B, cb, B.prev[b]);
+            const long long vol = (long long)cb.nx * cb.ny * cb.nz;
+            cnt[c] += 1;
             if (B.mode[c] == 3) {
                 const int t = pass_tier(B, c);
-                atomicAdd(&s_np[t], cb.nz);
-                atomicAdd(&s_nc[t], (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk);
-                atomicAdd(&s_tc[t], (unsigned long long)cb.nx * cb.ny * cb.nz);
-            } else {
-                B.worklist[c * G + w] = b;
+                cnt[kNumClasses + t] += cb.nz;
+                cnt[kNumClasses + kTiers + t] += (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
+                tcell[t] += vol;
             }
-            cells += (long long)cb.nx * cb.ny * cb.nz;
+            cells += vol;
             alive += 1;
         }
     }
-    // pass-path work items: tier 0 first, then tier 1, each box's in a block
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_wp[0] = 0; s_wp[1] = s_np[0];
-        s_wc[0] = 0; s_wc[1] = s_nc[0];
-    }
-    __syncthreads();
-    const bool items_fit = (long long)s_np[0] + s_np[1] <= B.plane_item_cap &&
-                           (long long)s_nc[0] + s_nc[1] <= B.chunk_item_cap;
-    for (int b = b0; b < b1 && items_fit; ++b) {
+    int pre[NV], tot[NV];
+    block_exclusive_scan<NV>(cnt, pre, tot, s_scan);
+    const bool items_fit = (long long)tot[kNumClasses] + tot[kNumClasses + 1] <= B.plane_item_cap &&
+                           (long long)tot[kNumClasses + kTiers] + tot[kNumClasses + kTiers + 1] <= B.chunk_item_cap;
+    for (int b = b0; b < b1; ++b) {
         const Box cb = B.cur[b];
         if (cb.nx <= 0) continue;
         const int c = box_class(B, cb, B.prev[b]);
-        if (B.mode[c] != 3) continue;
+        if (B.mode[c] != 3) {
+            B.worklist[c * G + pre[c]++] = b;
+            continue;
+        }
+        if (!items_fit) continue;
         const int t = pass_tier(B, c);
         const int nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
-        const int p0 = atomicAdd(&s_wp[t], cb.nz), c0 = atomicAdd(&s_wc[t], nch);
+        const int p0 = (t ? tot[kNumClasses] : 0) + pre[kNumClasses + t];
+        const int c0 = (t ? tot[kNumClasses + kTiers] : 0) + pre[kNumClasses + kTiers + t];
+        pre[kNumClasses + t] += cb.nz;
+        pre[kNumClasses + kTiers + t] += nch;
         for (int z = 0; z < cb.nz; ++z) B.plane_items[p0 + z] = make_int2(b, z);
         for (int k = 0; k < nch; ++k) B.chunk_items[c0 + k] = make_int2(b, k);
     }
-    // reduce cells / alive
-    __syncthreads();
-    s_part[threadIdx.x] = cells;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < (unsigned)o) s_part[threadIdx.x] += s_part[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) B.st->box_cells = s_part[0];
-    atomicAdd((unsigned long long*)&s_alive, (unsigned long long)alive);
-    __syncthreads();
+    // reduce cells / alive / tier cells
+    const long long r_cells = block_sum_ll(cells, s_part);
+    const long long r_alive = block_sum_ll(alive, s_part);
+    long long r_tc[kTiers];
+    for (int t = 0; t < kTiers; ++t) r_tc[t] = block_sum_ll(tcell[t], s_part);
+    if (threadIdx.x == 0) B.st->box_cells = r_cells;
     if (threadIdx.x < kNumClasses) {
-        B.st->class_count[threadIdx.x] = s_cnt[threadIdx.x];
+        B.st->class_count[threadIdx.x] = tot[threadIdx.x];
         B.st->queue[0][threadIdx.x] = 0;
         B.st->queue[1][threadIdx.x] = 0;
     }
     if (threadIdx.x < kTiers) {
         const int t = threadIdx.x;
-        B.st->n_planes[t] = items_fit ? s_np[t] : 0;
-        B.st->n_chunks[t] = items_fit ? s_nc[t] : 0;
-        B.st->plane_base[t] = t ? s_np[0] : 0;
-        B.st->chunk_base[t] = t ? s_nc[0] : 0;
-        B.st->tier_cells[t] = (long long)s_tc[t];
+        B.st->n_planes[t] = items_fit ? tot[kNumClasses + t] : 0;
+        B.st->n_chunks[t] = items_fit ? tot[kNumClasses + kTiers + t] : 0;
+        B.st->plane_base[t] = t ? tot[kNumClasses] : 0;
+        B.st->chunk_base[t] = t ? tot[kNumClasses + kTiers] : 0;
+        B.st->tier_cells[t] = r_tc[t];
     }
     if (threadIdx.x == 0) {
-        B.st->alive = s_alive;
+        B.st->alive = r_alive;
         if (!items_fit) { B.st->status = LSGG_ERR_UNSUPPORTED; B.st->halt = 1; }   // not reached: caps are bounds
     }
 }
@@ -710,9 +735,8 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
         e = traced(launch_collect_neighbours(B, phys, s), "neighbour tables");
         if (e != cudaSuccess) return e;
     }
-    // Each phase forks the size classes (and the pass-path tiers, on the side
-    // streams of tiers' indices, whose classes are then pass-path classes) off
-    // the step's stream and joins them back.
+    // Each phase forks the box-streaming size classes off the step's stream
+    // onto their side streams and joins them back.
     auto run_phase = [&](int which) -> cudaError_t {
         bool joined[kNumClasses] = {};
         if (ss) {
@@ -730,15 +754,13 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
             joined[k] = true;
             return traced(cudaEventRecord(ss->join[k], cs), "join record");
         };
+        // pass-path tiers run one after the other on the step's stream: each
+        // pass is a persistent grid that fills the GPU by itself
         if (B.use_passes)
             for (int t = 0; t < kTiers; ++t) {
-                cudaStream_t cs;
-                cudaError_t r = stream_for(t, &cs);
-                if (r != cudaSuccess) return r;
-                r = traced(launch_passes(B, which, t, taps, phys, d, cs, pass_ev ? pass_ev + t * 6 + (which ? 3 : 0) : nullptr),
-                           "pass kernels");
-                if (r != cudaSuccess) return r;
-                r = join(t, cs);
+                cudaError_t r = traced(
+                    launch_passes(B, which, t, taps, phys, d, s, pass_ev ? pass_ev + t * 6 + (which ? 3 : 0) : nullptr),
+                    "pass kernels");
                 if (r != cudaSuccess) return r;
             }
         for (int c = 0; c < kNumClasses; ++c) {

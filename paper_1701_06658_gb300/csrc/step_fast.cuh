@@ -487,34 +487,11 @@ k_correct_fast(StepBuffers B, PhysicsDev phys, DebugOut dbg, int cls) {
                     if (y >= ny) continue;
                     const int i = y * nx + sx;
                     const float val = c_0[v];
-                    const bool pos = val > 0.0f;
                     const float xl = sx > 0 ? C0[i - 1] : (fx ? C0[i + nx - 1] : -eps);
                     const float xr = sx < nx - 1 ? C0[i + 1] : (fx ? C0[i - nx + 1] : -eps);
                     const float yl = y > 0 ? C0[i - nx] : (fy ? C0[i + (ny - 1) * nx] : -eps);
                     const float yr = y < ny - 1 ? C0[i + nx] : (fy ? C0[i - (ny - 1) * nx] : -eps);
-                    const float zl2 = c_m[v], zr = c_p[v];
-                    const bool any = ((xl > 0.0f) != pos) | ((xr > 0.0f) != pos) | ((yl > 0.0f) != pos) |
-                                     ((yr > 0.0f) != pos) | ((zl2 > 0.0f) != pos) | ((zr > 0.0f) != pos);
-                    float mag = eps;
-                    if (any) {   // reference cell: planar-exact distance from the linear crossings
-                        const float a = fabsf(val);
-                        float inv2 = 0.0f;
-                        bool zero = false;
-                        float dmin = FLT_MAX;
-                        opp_delta(a, pos, xl, dmin);
-                        opp_delta(a, pos, xr, dmin);
-                        if (dmin < FLT_MAX) { if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
-                        dmin = FLT_MAX;
-                        opp_delta(a, pos, yl, dmin);
-                        opp_delta(a, pos, yr, dmin);
-                        if (dmin < FLT_MAX) { if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
-                        dmin = FLT_MAX;
-                        opp_delta(a, pos, zl2, dmin);
-                        opp_delta(a, pos, zr, dmin);
-                        if (dmin < FLT_MAX) { if (dmin > 0.0f) inv2 += 1.0f / (dmin * dmin); else zero = true; }
-                        mag = zero ? 0.0f : 1.0f / sqrtf(inv2);
-                    }
-                    G[i] = pos ? mag : -mag;
+                    G[i] = classify_cell(val, xl, xr, yl, yr, c_m[v], c_p[v], eps);
                 }
             }
             load_t(zin + 1);
