@@ -259,6 +259,26 @@ def gpu_arm(args):
         e2e_s = time.perf_counter() - t0
         e2e_cells = se.cell_updates
 
+    # ---------------- comparison paths on the same workload ----------------
+    # the plain path (one launch per grain per sub-step, the comparator the
+    # metric is quoted against) and the box-streaming kernels, a few steps each
+    compare = None
+    if not args.no_compare and rank == 0:
+        compare = {}
+        for name, mode, steps in (("plain_gpu", L.EXEC_PLAIN, 3), ("box_streaming_gpu", L.EXEC_STREAMED, 10)):
+            with L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=mode) as cm:
+                cm.step(2, dt)
+                cm.sync()
+                c0 = cm.stats().cell_updates
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                cm.step(steps, dt)
+                cm.sync()
+                el = time.perf_counter() - t0
+                rate = (cm.stats().cell_updates - c0) / el
+            compare[name] = {"value": rate, "unit": UNIT, "steps": steps, "ms_per_step": 1e3 * el / steps,
+                             "timing": "host wall clock around the steps (synchronised)"}
+
     # ---------------- serving: continuous batching under an HBM budget ----------------
     serving = None
     if args.serve_requests > 0 and rank == 0:
@@ -335,6 +355,8 @@ def gpu_arm(args):
                       f"density ({SAMPLE['grains']} grains), {cpu_s:.1f} s"},
         "clocks": clk.summary(),
         "serving": serving,
+        "compare": compare,
+        "speedup_vs_plain_gpu": None if not compare else value / compare["plain_gpu"]["value"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -388,6 +410,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
     ap.add_argument("--no-tune", action="store_true", help="skip the tile autotuner")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain / box-streaming comparison runs")
     ap.add_argument("--exec", default="batched", choices=["batched", "streamed"],
                     help="batched: pass path for boxes of side <= 64; streamed: box-streaming kernels only")
     ap.add_argument("--serve-requests", type=int, default=24,

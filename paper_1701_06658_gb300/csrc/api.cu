@@ -17,7 +17,7 @@
 #include "../../include/lsgg.h"
 
 namespace lsgg {
-cudaError_t launch_init(const Domain& D, int G, const double* d_seeds, const double* d_weights, int* d_labels,
+cudaError_t launch_init(const Domain& D, int G, const SeedBins& bins, const double* d_seeds, const double* d_weights, int* d_labels,
                         unsigned* d_bits, long long words_per_row, int* d_bb, Box* d_cur, cudaStream_t s);
 cudaError_t launch_sdf(const Domain& D, int G, const Box* d_cur, const double* d_seeds, const double* d_weights,
                        const unsigned* d_bits, long long words_per_row, float* X, int* IDF, int* d_status,
@@ -497,7 +497,59 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
         c->have_ss = true;
     }
 
-    if (launch_init(D, G, c->d_seeds, c->d_weights, d_labels, d_bits, wpr, d_bb, c->B.cur, c->stream) != cudaSuccess)
+    // seeds binned on a uniform grid of about one seed per bin (labelling search)
+    SeedBins bins{};
+    long long bin_bytes = 0;
+    float4* d_bpts = nullptr;
+    int *d_bids = nullptr, *d_bstart = nullptr;
+    {
+        const int Ns[3] = {D.nx, D.ny, D.nz};
+        const double spacing = std::pow((double)ncell / G, 1.0 / D.dim);
+        for (int a = 0; a < 3; ++a) {
+            int nb = Ns[a] == 1 ? 1 : (int)(Ns[a] / spacing);
+            bins.nb[a] = std::max(1, std::min(Ns[a], nb));
+            bins.size[a] = (float)Ns[a] / (float)bins.nb[a];
+        }
+        const long long n_bins = (long long)bins.nb[0] * bins.nb[1] * bins.nb[2];
+        std::vector<int> bin_of(G), start(n_bins + 1, 0), ids(G);
+        std::vector<float4> pts(G);
+        float wmax = 0.0f;
+        for (int i = 0; i < G; ++i) {
+            int bc[3];
+            float w[3];
+            for (int a = 0; a < 3; ++a) {
+                const double sw = seeds[3 * (size_t)i + a] - Ns[a] * std::floor(seeds[3 * (size_t)i + a] / Ns[a]);
+                w[a] = std::min((float)sw, std::nextafter((float)Ns[a], 0.0f));
+                bc[a] = std::min(bins.nb[a] - 1, (int)(w[a] / bins.size[a]));
+            }
+            const float wt = weights.empty() ? 0.0f : (float)weights[i];
+            wmax = std::max(wmax, wt);
+            pts[i] = make_float4(w[0], w[1], w[2], wt);
+            bin_of[i] = (bc[2] * bins.nb[1] + bc[1]) * bins.nb[0] + bc[0];
+            start[bin_of[i] + 1] += 1;
+        }
+        for (long long b = 0; b < n_bins; ++b) start[b + 1] += start[b];
+        std::vector<int> fill(start.begin(), start.end() - 1);
+        std::vector<float4> spts(G);
+        for (int i = 0; i < G; ++i) {
+            const int q = fill[bin_of[i]]++;
+            spts[q] = pts[i];
+            ids[q] = i;
+        }
+        bins.wmax = wmax;
+        if ((r = dalloc(c, &d_bpts, (size_t)G)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &d_bids, (size_t)G)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &d_bstart, (size_t)n_bins + 1)) != LSGG_OK) return bail(r);
+        if (cudaMemcpy(d_bpts, spts.data(), (size_t)G * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d_bids, ids.data(), (size_t)G * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d_bstart, start.data(), (size_t)(n_bins + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(CUDA_FAIL());
+        bins.pts = d_bpts;
+        bins.ids = d_bids;
+        bins.start = d_bstart;
+        bin_bytes = (long long)G * (sizeof(float4) + 4) + (n_bins + 1) * 4;
+    }
+    if (launch_init(D, G, bins, c->d_seeds, c->d_weights, d_labels, d_bits, wpr, d_bb, c->B.cur, c->stream) != cudaSuccess)
         return bail(CUDA_FAIL());
     // size the arena from the initial boxes
     std::vector<Box> hb(G);
@@ -536,7 +588,10 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     dfree(c, d_labels);
     dfree(c, d_bits);
     dfree(c, d_bb);
-    c->device_bytes -= (long long)ncell * 4 + (long long)G * wpr * 4 + 6LL * G * 4;
+    dfree(c, d_bpts);
+    dfree(c, d_bids);
+    dfree(c, d_bstart);
+    c->device_bytes -= (long long)ncell * 4 + (long long)G * wpr * 4 + 6LL * G * 4 + bin_bytes;
     c->phys.kind = cfg_in->physics;
     c->phys.energy = c->d_energy;
     c->phys.quats = c->d_quats;

@@ -30,7 +30,7 @@ constexpr int kNumClasses = 5;          // box side <= 32, 40, 48, 64, larger (g
 constexpr int kRedistReach = 6;         // taxicab steps below eps = 7 (exact fixed point)
 constexpr int kTiers = 2;               // pass path: boxes with x, y sides <= 32 and <= 64
 constexpr int kPassChunk = 256;         // columns per column item of the pass path
-constexpr int kTileX = 32, kTileY = 8, kTileZ = 8;    // domain tiles of the field pass
+constexpr int kTileX = 8, kTileY = 32, kTileZ = 8;    // domain tiles of the field pass
 constexpr int kTileCap = 128;           // boxes listed per tile (more: the tile scans all boxes)
 
 struct Box {
@@ -195,6 +195,17 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
                         const StepStreams* ss = nullptr, cudaEvent_t* cls_ev = nullptr,
                         cudaEvent_t* pass_ev = nullptr);
 cudaError_t launch_box_update(const StepBuffers& B, bool commit_only_layout, cudaStream_t s);
+
+// Seeds sorted into a uniform grid of bins (built on the host) for the
+// labelling search of the initialisation.
+struct SeedBins {
+    const float4* pts;     // per sorted seed: x, y, z wrapped into [0, N), weight (FP32)
+    const int* ids;        // per sorted seed: its grain id
+    const int* start;      // per bin (x fastest): first sorted seed; [n_bins] = G
+    int nb[3];             // bins per axis
+    float size[3];         // bin side (cells) per axis
+    float wmax;            // largest weight (0 without weights)
+};
 cudaError_t configure_step_kernels(StepBuffers& B);
 // Let `fn` take up to the device's opt-in shared memory per CTA (process-wide).
 cudaError_t allow_max_dynamic_smem(const void* fn);
