@@ -10,12 +10,34 @@ namespace lsgg {
 __device__ __forceinline__ bool sgn_pos(float v) { return !(__float_as_uint(v) >> 31); }
 
 // Division of non-negative ints below 2^16 by a divisor d set once: q = (t *
-// ceil(2^32 / d)) >> 32 is exact in that range (two instructions).
+// ceil(2^32 / d)) >> 32 is exact in that range (two instructions).  The
+// multiplier of every divisor up to kDivTable comes from a table in constant
+// memory (one load, uniform across the warp); larger divisors compute it.
+constexpr int kDivTable = 160;
+struct DivMagic {
+    unsigned m[kDivTable + 1];
+};
+constexpr DivMagic make_div_magic() {
+    DivMagic t{};
+    for (int d = 1; d <= kDivTable; ++d) t.m[d] = (unsigned)((0x100000000ULL + d - 1) / d);
+    return t;
+}
+static __constant__ DivMagic c_div_magic = make_div_magic();
+
 struct Div16 {
     unsigned m;
-    __device__ __forceinline__ explicit Div16(int d) : m((unsigned)((0x100000000ULL + d - 1) / d)) {}
+    __device__ __forceinline__ explicit Div16(int d)
+        : m(d <= kDivTable ? c_div_magic.m[d] : (unsigned)((0x100000000ULL + d - 1) / d)) {}
     __device__ __forceinline__ int operator()(int t) const { return (int)__umulhi((unsigned)t, m); }
 };
+
+// a mod n for a within one period of [0, n) (the usual case of box and
+// domain offsets), falling back to the general form otherwise.
+__device__ __forceinline__ int wrap_near(int a, int n) {
+    if (a < 0) a += n;
+    else if (a >= n) a -= n;
+    return (unsigned)a < (unsigned)n ? a : pmod(a, n);
+}
 
 // Disorientation angle (radians) of two cubic crystals: with q = conj(qa) qb
 // and |q| components sorted c0 >= c1 >= c2 >= c3, the largest |w| over the 24
@@ -149,7 +171,7 @@ __device__ __forceinline__ float opp_max(bool pos, float l, float r) {
 // cells, else the planar-exact distance (0 when phi = 0).
 __device__ __forceinline__ float ref_magnitude(float a, float n0, float n1, float n2, float eps) {
     if (n0 < 0.0f && n1 < 0.0f && n2 < 0.0f) return eps;
-    const float ra = 1.0f / a;                  // a = 0: inf, and the distance is 0
+    const float ra = __frcp_rn(a);              // = 1 / a rounded to nearest; a = 0: inf, distance 0
     float s = 0.0f;
     if (n0 >= 0.0f) { const float r = fmaf(n0, ra, 1.0f); s = fmaf(r, r, s); }
     if (n1 >= 0.0f) { const float r = fmaf(n1, ra, 1.0f); s = fmaf(r, r, s); }

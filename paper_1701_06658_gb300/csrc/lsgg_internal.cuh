@@ -15,8 +15,9 @@
 //              path; aliases IDF when the physics needs no ID-field.
 //   classes    per size class a work list of box indices and a queue counter
 //              per kernel; persistent CTAs pull boxes from the queue.
-//   items      pass path: per tier a list of (box, plane) and of (box, column
-//              chunk) work items, rebuilt by every box update.
+//   items      pass path: per tier a list of (box, plane), of (box, slab of
+//              kSlab planes) and of (box, column chunk) work items, rebuilt by
+//              every box update.
 #pragma once
 
 #include <cstdint>
@@ -30,6 +31,7 @@ constexpr int kNumClasses = 5;          // box side <= 32, 40, 48, 64, larger (g
 constexpr int kRedistReach = 6;         // taxicab steps below eps = 7 (exact fixed point)
 constexpr int kTiers = 2;               // pass path: boxes with x, y sides <= 32 and <= 64
 constexpr int kPassChunk = 256;         // columns per column item of the pass path
+constexpr int kSlab = 8;                // planes per slab item of the pass path
 constexpr int kTileX = 8, kTileY = 32, kTileZ = 8;    // domain tiles of the field pass
 constexpr int kTileCap = 128;           // boxes listed per tile (more: the tile scans all boxes)
 
@@ -100,6 +102,8 @@ struct StepState {                  // device-resident control block
     int plane_base[kTiers];
     int chunk_base[kTiers];
     long long tier_cells[kTiers];   // box cells per tier in `cur`
+    int n_slabs[kTiers];            // pass path: slab items (kSlab planes) per tier
+    int slab_base[kTiers];
 };
 
 __host__ __device__ inline int plane_stride(int nx, int ny) { return (nx * ny + 3) & ~3; }
@@ -160,7 +164,9 @@ struct StepBuffers {
     float* Z;
     int2* plane_items;              // (box, local z), tier 0 then tier 1
     int2* chunk_items;              // (box, column chunk of kPassChunk columns)
+    int2* slab_items;               // (box, first plane of a slab of kSlab planes)
     long long plane_item_cap;       // entries (n_boxes * domain nz: a bound on sum nz)
+    long long slab_item_cap;        // entries (n_boxes * ceil(domain nz / kSlab))
     long long chunk_item_cap;       // entries (n_boxes * 64 * 64 / kPassChunk)
     int use_passes;
     int tier_side[kTiers];

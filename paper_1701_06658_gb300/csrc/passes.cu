@@ -30,12 +30,12 @@
 #include <cfloat>
 #include <climits>
 
+#include "bulk_copy.cuh"
 #include "kernels_common.cuh"
 
 namespace lsgg {
 
 constexpr int kZB = 8;               // planes loaded ahead by the column passes
-constexpr int kStageU = 8;           // loads in flight per thread when staging a plane
 constexpr int kReachP = kRedistReach;
 constexpr int kColThreads = kPassChunk;
 
@@ -56,25 +56,84 @@ __device__ __forceinline__ float conv_xy_of_const(const float (&g)[2 * R + 1], f
 // ---------------------------------------------------------------------------
 // pass 1: xy convolution of one plane
 // ---------------------------------------------------------------------------
-// A CTA of SIDE threads takes one (box, plane) item at a time: the plane of
-// phi is staged row by row (old box -> new box, -eps outside), then thread x
-// walks down column x, convolving each padded row along x from shared memory
-// and keeping the last 2R + 1 row results in registers for the y convolution.
+// A CTA of NT threads takes one (box, plane) item at a time:
+//   fetch   the plane of phi in the box's previous layout (contiguous,
+//           16-byte aligned) arrives in a raw slot by a bulk copy, issued
+//           while the CTA still works on the item before;
+//   stage   raw -> padded grid P in the new layout (-eps outside the old
+//           box), warps over rows and lanes along x;
+//   x pass  each thread convolves 4 consecutive cells of one padded row from
+//           16-byte shared loads -> grid XC (all padded rows);
+//   y pass  each thread convolves 4 consecutive rows of one column from
+//           shared loads of XC and stores them (lanes along x: coalesced).
+// The FMA order of both passes is the one conv_xy_of_const repeats.  Every
+// wait on a copy is bounded (LSGG_ERR_TIMEOUT, halt, drain, return).
 template <int R, int SIDE>
-__global__ void __launch_bounds__(SIDE)
+struct ConvXYLayout {
+    static constexpr int PYR = SIDE + 2 * R;                  // padded rows
+    static constexpr int NQ = (2 * R + 1 + 6) / 4;            // 16-byte loads per x window of 4 outputs
+    static constexpr int PX = ((SIDE + 3) & ~3) + 4 * NQ;     // pitch of P: room for the last group's window
+    static constexpr int XP = (SIDE + 3) & ~3;                // pitch of XC
+    static constexpr int XR = PYR + 3;                        // rows of XC (3 spare for the last 4-row group)
+    static constexpr size_t raw = 128;                        // after the barrier
+    static constexpr size_t P = raw + sizeof(float) * SIDE * SIDE;
+    static constexpr size_t XC = P + sizeof(float) * PYR * PX;
+    static constexpr size_t maps = XC + sizeof(float) * XR * XP;
+    static constexpr size_t bytes = maps + sizeof(int) * 2 * PYR;
+};
+
+// The plane of item `item` in the box's previous layout: source address and
+// bytes (0 when the new plane lies outside the old box).
+__device__ __forceinline__ void conv_source(const StepBuffers& B, int2 it, const float** src, uint32_t* bytes) {
+    const Box nb = B.cur[it.x], ob = B.prev[it.x];
+    const int ozl = pmod(nb.oz + it.y - ob.oz, B.dom.nz);
+    const int ps = plane_stride(ob.nx, ob.ny);
+    *src = B.X + ob.off + (long long)(ozl < ob.nz ? ozl : 0) * ps;
+    *bytes = ozl < ob.nz ? (uint32_t)ps * 4u : 0u;
+}
+
+template <int R, int SIDE, int NT>
+__global__ void __launch_bounds__(NT)
 p_conv_xy(StepBuffers B, Taps taps, int tier) {
     constexpr int W = 2 * R + 1;
-    constexpr int PS = SIDE + 2 * R;
-    __shared__ float P[(PS + W) * PS];      // W spare rows: the unrolled row loop may read past the plane
-    __shared__ int mapx[PS], mapy[PS];
-    if (halted(B)) return;
+    using LY = ConvXYLayout<R, SIDE>;
+    extern __shared__ __align__(128) unsigned char smc[];   // ConvXYLayout::bytes
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smc);
+    float* const raw = reinterpret_cast<float*>(smc + LY::raw);
+    float* const P = reinterpret_cast<float*>(smc + LY::P);
+    float* const XC = reinterpret_cast<float*>(smc + LY::XC);
+    int* const mapx = reinterpret_cast<int*>(smc + LY::maps);
+    int* const mapy = mapx + LY::PYR;
+    __shared__ int s_flag;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        s_flag = halted(B);
+    }
+    __syncthreads();
+    if (s_flag) return;
     const Domain D = B.dom;
     float g[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) g[k] = taps.g[k];
-    const int t = threadIdx.x;
     const int n_items = B.st->n_planes[tier];
     const int2* items = B.plane_items + B.st->plane_base[tier];
+    uint32_t phase = 0;
+    // the first item's plane
+    bool pending = false;
+    if (blockIdx.x < n_items) {
+        const float* src;
+        uint32_t bytes;
+        conv_source(B, items[blockIdx.x], &src, &bytes);
+        if (bytes) {
+            if (t == 0) {
+                mbar_expect(bar, bytes);
+                bulk_load(raw, src, bytes, bar);
+            }
+            pending = true;
+        }
+    }
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int2 it = items[item];
         const int b = it.x, z = it.y;
@@ -82,72 +141,106 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         const int nx = nb.nx, ny = nb.ny;
         const bool fx = nx == D.nx, fy = ny == D.ny;
         const int PXa = nx + 2 * R, PYa = ny + 2 * R;
-        __syncthreads();                                    // previous item done with the buffers
-        for (int i = t; i < PXa; i += SIDE) {
-            int xl = i - R, v = -1;
-            if (fx || (xl >= 0 && xl < nx)) {
-                if (fx) xl = pmod(xl, nx);
-                const int ol = pmod(nb.ox + xl - ob.ox, D.nx);
-                v = ol < ob.nx ? ol : -1;
+        const bool have = pending;
+        for (int i = t; i < PXa + PYa; i += NT) {
+            const bool isx = i < PXa;
+            const int ip = isx ? i : i - PXa;
+            const int n = isx ? nx : ny, N = isx ? D.nx : D.ny;
+            const int o_new = isx ? nb.ox : nb.oy, o_old = isx ? ob.ox : ob.oy, n_old = isx ? ob.nx : ob.ny;
+            const bool full = isx ? fx : fy;
+            int l = ip - R, v = -1;
+            if (full || (l >= 0 && l < n)) {
+                if (full) l = wrap_near(l, n);
+                const int ol = wrap_near(o_new + l - o_old, N);
+                v = ol < n_old ? ol : -1;
             }
-            mapx[i] = v;
+            if (isx) mapx[ip] = v; else mapy[ip] = v;
         }
-        for (int i = t; i < PYa; i += SIDE) {
-            int yl = i - R, v = -1;
-            if (fy || (yl >= 0 && yl < ny)) {
-                if (fy) yl = pmod(yl, ny);
-                const int ol = pmod(nb.oy + yl - ob.oy, D.ny);
-                v = ol < ob.ny ? ol : -1;
+        bool ok = true;
+        if (pending) {
+            ok = mbar_wait(bar, phase);
+            if (ok) phase ^= 1u;
+        }
+        if (!__syncthreads_and(ok)) {                       // also publishes the maps
+            if (t == 0) {
+                atomicExch(&B.st->status, LSGG_ERR_TIMEOUT);
+                atomicExch(&B.st->halt, 1);
+                mbar_wait(bar, phase);
             }
-            mapy[i] = v;
+            __syncthreads();
+            return;
         }
-        const int ozl = pmod(nb.oz + z - ob.oz, D.nz);
-        const int zold = ozl < ob.nz ? ozl : -1;
-        const float* src = B.X + ob.off + (long long)(zold < 0 ? 0 : zold) * plane_stride(ob.nx, ob.ny);
-        __syncthreads();
-        {   // stage the padded plane, kStageU loads in flight per thread
-            const int n = PXa * PYa;
-            const Div16 dPX(PXa);
-            for (int i0 = t; i0 < n; i0 += SIDE * kStageU) {
-                float v[kStageU];
-#pragma unroll
-                for (int u = 0; u < kStageU; ++u) {
-                    const int i = i0 + u * SIDE;
-                    v[u] = -D.eps;
-                    if (i < n && zold >= 0) {
-                        const int yp = dPX(i), xp = i - yp * PXa;
-                        const int mx = mapx[xp], my = mapy[yp];
-                        if (mx >= 0 && my >= 0) v[u] = src[my * ob.nx + mx];
-                    }
+        pending = false;
+        // stage: raw (old layout) -> P (new layout), warp per padded row
+        for (int yp = warp; yp < PYa; yp += NT / 32) {
+            const int my = mapy[yp];
+            const float* rrow = raw + (my < 0 ? 0 : my) * ob.nx;
+            float* prow = P + yp * LY::PX;
+            for (int xp = lane; xp < PXa; xp += 32) {
+                const int mx = mapx[xp];
+                prow[xp] = (have && my >= 0 && mx >= 0) ? rrow[mx] : -D.eps;
+            }
+        }
+        __syncthreads();                                    // raw is free: fetch the next item's plane
+        if (item + (int)gridDim.x < n_items) {
+            const float* src;
+            uint32_t bytes;
+            conv_source(B, items[item + gridDim.x], &src, &bytes);
+            if (bytes) {
+                if (t == 0) {
+                    fence_async_smem();
+                    mbar_expect(bar, bytes);
+                    bulk_load(raw, src, bytes, bar);
                 }
-#pragma unroll
-                for (int u = 0; u < kStageU; ++u)
-                    if (i0 + u * SIDE < n) P[i0 + u * SIDE] = v[u];
+                pending = true;
             }
         }
-        __syncthreads();
-        if (t < nx) {
-            float* dst = B.Z + nb.off + (long long)z * plane_stride(nx, ny) + t;
-            const float* prow = P + t;
-            float win[W];                                   // x-convolved rows, slot = row mod W
-            for (int yb = 0; yb < PYa; yb += W) {
-                // W rows per trip without branches, so that their independent FMA
-                // chains interleave; rows past the plane are computed and dropped
+        // x pass: (padded row, group of 4 outputs)
+        const int ngx = (nx + 3) >> 2;
+        {
+            const Div16 dgx(ngx);
+            for (int j = t; j < PYa * ngx; j += NT) {
+                const int yp = dgx(j), x0 = 4 * (j - yp * ngx);
+                const float4* r4 = reinterpret_cast<const float4*>(P + yp * LY::PX + x0);
+                float v[4 * LY::NQ];
 #pragma unroll
-                for (int s = 0; s < W; ++s) {
-                    const int yp = yb + s;
-                    const float* r = prow + yp * PXa;
+                for (int q = 0; q < LY::NQ; ++q) {
+                    const float4 a = r4[q];
+                    v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+                }
+                float o[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
                     float acc = 0.0f;
 #pragma unroll
-                    for (int k = 0; k < W; ++k) acc = fmaf(g[k], r[k], acc);
-                    win[s] = acc;
-                    float o = 0.0f;                         // output row y = yp - 2R: rows y .. yp
+                    for (int k = 0; k < W; ++k) acc = fmaf(g[k], v[u + k], acc);
+                    o[u] = acc;
+                }
+                *reinterpret_cast<float4*>(XC + yp * LY::XP + x0) = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+        __syncthreads();
+        // y pass: (group of 4 rows, column), lanes along x
+        {
+            float* dst = B.Z + nb.off + (long long)z * plane_stride(nx, ny);
+            const int ngy = (ny + 3) >> 2;
+            const Div16 dnx(nx);
+            for (int j = t; j < ngy * nx; j += NT) {
+                const int gy = dnx(j), x = j - gy * nx, y0 = 4 * gy;
+                const float* col = XC + y0 * LY::XP + x;
+                float v[W + 3];
 #pragma unroll
-                    for (int k = 0; k < W; ++k) o = fmaf(g[k], win[(s + 1 + k) % W], o);
-                    if (yp >= 2 * R && yp < PYa) dst[(yp - 2 * R) * nx] = o;
+                for (int k = 0; k < W + 3; ++k) v[k] = col[k * LY::XP];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < W; ++k) acc = fmaf(g[k], v[u + k], acc);
+                    if (y0 + u < ny) dst[(y0 + u) * nx + x] = acc;
                 }
             }
         }
+        __syncthreads();                                    // XC and the maps are free
     }
 }
 
@@ -192,8 +285,8 @@ p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
         bool in_old_xy = false;
         if (PHYS) {
             const int y = c / nx, x = c - y * nx;
-            oxl = pmod(nb.ox + x - ob.ox, D.nx);
-            oyl = pmod(nb.oy + y - ob.oy, D.ny);
+            oxl = wrap_near(nb.ox + x - ob.ox, D.nx);
+            oyl = wrap_near(nb.oy + y - ob.oy, D.ny);
             in_old_xy = oxl < ob.nx && oyl < ob.ny;
         }
         const int ps_old = plane_stride(ob.nx, ob.ny);
@@ -225,7 +318,7 @@ p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
                 for (int k = 0; k < W; ++k) acc = fmaf(g[k], win[k], acc);
                 float val = acc;
                 if (PHYS) {
-                    const int ozl = pmod(nb.oz + zo - ob.oz, D.nz);
+                    const int ozl = wrap_near(nb.oz + zo - ob.oz, D.nz);
                     float phi0 = -D.eps;
                     int j = -1;
                     if (in_old_xy && ozl < ob.nz) {
@@ -315,9 +408,9 @@ __device__ __forceinline__ void stage_tile_box(const StepBuffers& B, int b, int 
     t.ny = bx.ny;
     t.id = b;
     t.ps = plane_stride(bx.nx, bx.ny);
-    t.dx = pmod(tx0 - bx.ox, D.nx);
-    t.dy = pmod(ty0 - bx.oy, D.ny);
-    t.dz = pmod(z0 - bx.oz, D.nz);
+    t.dx = wrap_near(tx0 - bx.ox, D.nx);
+    t.dy = wrap_near(ty0 - bx.oy, D.ny);
+    t.dz = wrap_near(z0 - bx.oz, D.nz);
     unsigned m = 0;
     if (bx.nx > 0)
         for (int zz = 0; zz < nzt; ++zz) {
@@ -418,114 +511,278 @@ p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
 }
 
 // ---------------------------------------------------------------------------
-// pass 4: classification + x / y taxicab passes of one plane
+// pass 4: classification + y / x taxicab passes of one plane
 // ---------------------------------------------------------------------------
-// Sign-blocked min-plus along one line of n cells, in place (stride st):
-// f_j = min(|v_j|, f_{j-1} + 1) over a run of one sign, forward then backward.
-// A periodic line is swept twice around in each direction.  Cells further
-// than 6 apart add at least 7 >= eps, so this equals the 6-step window of
-// the box-streaming kernels.  `out` (optional) receives the final values.
-__device__ __forceinline__ void line_sweep(float* L, int n, int st, bool wrap, float* out, int out_st) {
-    const int laps = wrap ? 2 : 1;
-    float fp = 0.0f;
-    bool sp = false;
-    for (int j = 0; j < laps * n; ++j) {
+// After classification every cell holds eps or, at a reference cell, its
+// planar-exact distance, which is at most 1.  A sign change along a line
+// lies between two reference cells, and a value carried across it (at least
+// 1 after the crossing) never undercuts the reference value on the far side:
+// restricting the taxicab propagation to same-sign neighbours changes
+// nothing.  The fixed point of Sec. 2.1.6 is therefore the plain taxicab
+// distance transform of the magnitudes with each cell's own sign put back.
+// That transform is separable -- a forward and a backward scan
+// f_j = min(m_j, f_{j-1} + 1) along x, y and z, in any order -- and a scan of
+// the whole line equals the 6-step window because no magnitude exceeds
+// eps = 7.
+
+// Forward and backward min-plus scan of N registers.  Entries past the end
+// of the line start at eps (not below any magnitude): they only ever carry a
+// line value plus a distance, which never undercuts the line's own values.
+template <int N>
+__device__ __forceinline__ void scan_regs(float (&r)[N]) {
+#pragma unroll
+    for (int j = 1; j < N; ++j) r[j] = fminf(r[j], r[j - 1] + 1.0f);
+#pragma unroll
+    for (int j = N - 2; j >= 0; --j) r[j] = fminf(r[j], r[j + 1] + 1.0f);
+}
+
+// The scan of n <= N magnitudes in shared memory (stride st) through registers.
+template <int N>
+__device__ __forceinline__ void scan_line_regs(float* L, int n, int st, float pad) {
+    float r[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) r[j] = j < n ? L[j * st] : pad;
+    scan_regs(r);
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (j < n) L[j * st] = r[j];
+}
+
+// The scan of a periodic line of n magnitudes in shared memory: twice around
+// in each direction.
+__device__ __forceinline__ void scan_line_wrap(float* L, int n, int st) {
+    float f = L[0];
+    for (int j = 1; j < 2 * n; ++j) {
         const int i = j < n ? j : j - n;
-        const float v = L[i * st];
-        const bool sv = sgn_pos(v);
-        float a = fabsf(v);
-        if (j > 0 && sv == sp) a = fminf(a, fp + 1.0f);
-        L[i * st] = sv ? a : -a;
-        fp = a;
-        sp = sv;
-    }
-    for (int j = laps * n - 2; j >= 0; --j) {
-        const int i = j < n ? j : j - n;
-        const float v = L[i * st];
-        const bool sv = sgn_pos(v);
-        float a = fabsf(v);
-        if (sv == sp) a = fminf(a, fp + 1.0f);
-        const float f = sv ? a : -a;
+        f = fminf(L[i * st], f + 1.0f);
         L[i * st] = f;
-        if (out && j < n) out[i * out_st] = f;
-        fp = a;
-        sp = sv;
     }
-    if (out) {                                       // the last cell is final after the forward sweep
-        const int i = n - 1;
-        if (laps == 1) out[i * out_st] = L[i * st];
+    for (int j = 2 * n - 2; j >= 0; --j) {
+        const int i = j < n ? j : j - n;
+        f = fminf(L[i * st], f + 1.0f);
+        L[i * st] = f;
     }
 }
 
-template <int SIDE>
-__global__ void __launch_bounds__(SIDE)
+// Segmented scan of a line of n <= 4 * L cells (stride st in shared memory)
+// by the 4 consecutive lanes that share it: lane `seg` scans cells
+// [seg * L, seg * L + L) in registers, then takes the boundary value of its
+// neighbour segment (forward: the previous segment's last cell, backward: the
+// next segment's first) and lowers its first / last cells by it.  With L > 6
+// a segment's boundary cells do not depend on the carry coming into it, so
+// one exchange per direction suffices.  All 4 lanes of a group must call.
+template <int L>
+__device__ __forceinline__ void scan_line_seg(float* line, int n, int st, int seg, bool active, float eps) {
+    static_assert(L > kRedistReach, "one exchange per direction needs segments longer than the reach");
+    float r[L];
+    const int j0 = seg * L;
+#pragma unroll
+    for (int j = 0; j < L; ++j) r[j] = active && j0 + j < n ? line[(j0 + j) * st] : eps;
+#pragma unroll
+    for (int j = 1; j < L; ++j) r[j] = fminf(r[j], r[j - 1] + 1.0f);
+    float cf = __shfl_up_sync(0xffffffffu, r[L - 1], 1);
+    if (seg == 0) cf = eps;
+#pragma unroll
+    for (int j = 0; j < kRedistReach; ++j) r[j] = fminf(r[j], cf + (float)(j + 1));
+#pragma unroll
+    for (int j = L - 2; j >= 0; --j) r[j] = fminf(r[j], r[j + 1] + 1.0f);
+    float cb = __shfl_down_sync(0xffffffffu, r[0], 1);
+    if (seg == 3) cb = eps;
+#pragma unroll
+    for (int j = 0; j < kRedistReach; ++j) r[L - 1 - j] = fminf(r[L - 1 - j], cb + (float)(j + 1));
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+        if (active && j0 + j < n) line[(j0 + j) * st] = r[j];
+}
+
+// Plane pass of the re-initialisation: a CTA of NT threads takes one (box,
+// slab of kSlab planes) item at a time and walks its planes in z order.
+// Planes of phi_c stream into a 3-slot shared-memory ring by bulk copies
+// (a box plane is contiguous and 16-byte aligned), plane z + 2 being fetched
+// while plane z is processed.  For plane z every thread classifies cells
+// from the slots of z - 1, z, z + 1; the magnitudes go to a grid G (odd
+// pitch); the y and x scans run with 4 lanes per line; the signs of plane z
+// are put back as the plane is stored with 16-byte stores.  Every wait on a
+// copy is bounded: on expiry the CTA records LSGG_ERR_TIMEOUT, halts the step,
+// drains its copies (bounded) and returns.
+template <int SIDE, int NT>
+__global__ void __launch_bounds__(NT)
 p_redist_xy(StepBuffers B, int tier) {
-    constexpr int PG = SIDE + 1;                      // odd pitch: row sweeps hit distinct banks
-    constexpr int U = 4;                              // rows classified per trip
-    __shared__ float G[(SIDE + U) * PG];              // U spare rows for the unrolled trip
-    if (halted(B)) return;
+    constexpr int PA = SIDE * SIDE;                   // floats per plane slot
+    constexpr int PG = SIDE + 1;                      // pitch of G
+    constexpr int L = SIDE / 4;                       // segment of a scan lane
+    constexpr int KC = PA / NT;                       // cells classified per thread
+    static_assert(PA % NT == 0 && NT / 4 >= SIDE, "4 lanes per line of the plane");
+    extern __shared__ __align__(128) unsigned char smraw[];    // redist_smem_bytes(SIDE)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+    float* const slots = reinterpret_cast<float*>(smraw + 128);
+    float* const G = slots + 3 * PA;
+    __shared__ int s_flag;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        for (int k = 0; k < 3; ++k) mbar_init(&bar[k], 1);
+        fence_mbar_init();
+        s_flag = halted(B);
+    }
+    __syncthreads();
+    if (s_flag) return;
     const Domain D = B.dom;
     const float eps = D.eps;
-    const int t = threadIdx.x;
-    const int n_items = B.st->n_planes[tier];
-    const int2* items = B.plane_items + B.st->plane_base[tier];
+    const float4 fill = make_float4(-eps, -eps, -eps, -eps);
+    uint32_t phase = 0;                               // bit k: parity of slot k's next completion
+    uint32_t pending = 0;                             // bit k: a copy into slot k is in flight
+    const int n_items = B.st->n_slabs[tier];
+    const int2* items = B.slab_items + B.st->slab_base[tier];
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int2 it = items[item];
-        const int b = it.x, z = it.y;
+        const int b = it.x, z0 = it.y;
         const Box nb = B.cur[b];
         const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
         const bool fx = nx == D.nx, fy = ny == D.ny, fz = nz == D.nz;
         const int ps = plane_stride(nx, ny);
+        const int n = nx * ny;
         const float* zb = B.Z + nb.off;
-        const int zm = fz ? pmod(z - 1, nz) : z - 1, zp = fz ? pmod(z + 1, nz) : z + 1;
-        const bool has_m = zm >= 0, has_p = zp < nz;
-        __syncthreads();                                    // previous item done with G
-        if (t < nx) {                                       // classification, thread = column
-            // phi_c of plane z and of its z neighbours, read through L1: row y of
-            // the plane is loaded by the whole CTA, so the x neighbours hit L1
-            const int x = t;
-            const float* c = zb + (long long)z * ps;
-            const float* cm = zb + (long long)(has_m ? zm : 0) * ps;
-            const float* cp = zb + (long long)(has_p ? zp : 0) * ps;
-            const int xl_i = x > 0 ? x - 1 : (fx ? nx - 1 : -1);
-            const int xr_i = x < nx - 1 ? x + 1 : (fx ? 0 : -1);
-            float c_prev = fy ? __ldg(c + (ny - 1) * nx + x) : -eps;
-            float c_cur = __ldg(c + x);
-            for (int y0 = 0; y0 < ny; y0 += U) {
-                float cv[U + 1], xl[U], xr[U], zl[U], zr[U];
-                cv[0] = c_cur;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int y = y0 + u;
-                    const bool in = y < ny;
-                    const int yn = y + 1 < ny ? y + 1 : (fy ? 0 : -1);
-                    cv[u + 1] = in && yn >= 0 ? __ldg(c + yn * nx + x) : -eps;
-                    xl[u] = in && xl_i >= 0 ? __ldg(c + y * nx + xl_i) : -eps;
-                    xr[u] = in && xr_i >= 0 ? __ldg(c + y * nx + xr_i) : -eps;
-                    zl[u] = in && has_m ? __ldg(cm + y * nx + x) : -eps;
-                    zr[u] = in && has_p ? __ldg(cp + y * nx + x) : -eps;
+        const int z1 = min(z0 + kSlab, nz);
+        // plane zz (z0 - 1 <= zz <= z1) lives in slot (zz - z0 + 1) mod 3; a
+        // plane outside a non-periodic box is the -eps fill
+        auto request = [&](int zz) {
+            const int k = (zz - z0 + 1) % 3;
+            const int src = fz ? pmod(zz, nz) : zz;
+            if (src >= 0 && src < nz) {
+                if (t == 0) {
+                    fence_async_smem();                 // earlier generic accesses to the slot come first
+                    mbar_expect(&bar[k], (uint32_t)ps * 4u);
+                    bulk_load(slots + k * PA, zb + (long long)src * ps, (uint32_t)ps * 4u, &bar[k]);
                 }
+                pending |= 1u << k;
+            } else {
+                float4* d = reinterpret_cast<float4*>(slots + k * PA);
+                for (int q = t; q < ps / 4; q += NT) d[q] = fill;
+            }
+        };
+        __syncthreads();                                    // previous item done with the slots and G
+        request(z0 - 1);
+        request(z0);
+        request(z0 + 1);
+        for (int z = z0; z < z1; ++z) {
+            bool ok = true;
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const float yl = u ? cv[u - 1] : c_prev;
-                    G[(y0 + u) * PG + x] = classify_cell(cv[u], xl[u], xr[u], yl, cv[u + 1], zl[u], zr[u], eps);
+            for (int k = 0; k < 3; ++k)
+                if ((pending >> k) & 1u) {
+                    if (mbar_wait(&bar[k], (phase >> k) & 1u)) {
+                        phase ^= 1u << k;
+                        pending &= ~(1u << k);
+                    } else {
+                        ok = false;
+                    }
                 }
-                c_prev = cv[U - 1];
-                c_cur = cv[U];
+            if (!__syncthreads_and(ok)) {                   // also publishes the fills
+                if (t == 0) {
+                    atomicExch(&B.st->status, LSGG_ERR_TIMEOUT);
+                    atomicExch(&B.st->halt, 1);
+                    for (int k = 0; k < 3; ++k)
+                        if ((pending >> k) & 1u) mbar_wait(&bar[k], (phase >> k) & 1u);
+                }
+                __syncthreads();
+                return;
+            }
+            const float* Pm = slots + ((z - z0) % 3) * PA;
+            const float* Pc = slots + ((z - z0 + 1) % 3) * PA;
+            const float* Pp = slots + ((z - z0 + 2) % 3) * PA;
+            // classification: cells t, t + NT, ... up to the plane's last cell
+            float mag[KC];
+            const Div16 dnx(nx);
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                const int i = t + k * NT;
+                if (i >= n) break;
+                const int y = dnx(i), x = i - y * nx;
+                const float v = Pc[i];
+                const bool pos = v > 0.0f;
+                const float xl = x > 0 ? Pc[i - 1] : (fx ? Pc[i + nx - 1] : -eps);
+                const float xr = x < nx - 1 ? Pc[i + 1] : (fx ? Pc[i - nx + 1] : -eps);
+                const float yl = y > 0 ? Pc[i - nx] : (fy ? Pc[i + n - nx] : -eps);
+                const float yr = y < ny - 1 ? Pc[i + nx] : (fy ? Pc[i - n + nx] : -eps);
+                mag[k] = ref_magnitude(fabsf(v), opp_max(pos, xl, xr), opp_max(pos, yl, yr),
+                                       opp_max(pos, Pm[i], Pp[i]), eps);
+            }
+            __syncthreads();                                // the slot of z - 1 is free
+            if (z + 1 < z1) request(z + 2);
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                const int i = t + k * NT;
+                if (i >= n) break;
+                const int y = dnx(i), x = i - y * nx;
+                G[y * PG + x] = mag[k];
+            }
+            __syncthreads();
+            // scans: 4 lanes per line; a warp holds 8 lines and skips as a
+            // whole when all of them lie past the plane
+            const int line = t >> 2, seg = t & 3, warp_line0 = (t >> 5) * 8;
+            if (fy) {                                       // periodic y: one lane per column
+                if (seg == 0 && line < nx) scan_line_wrap(G + line, ny, PG);
+            } else if (warp_line0 < nx) {
+                scan_line_seg<L>(G + line, ny, PG, seg, line < nx, eps);
+            }
+            __syncthreads();
+            if (fx) {
+                if (seg == 0 && line < ny) scan_line_wrap(G + line * PG, nx, 1);
+            } else if (warp_line0 < ny) {
+                scan_line_seg<L>(G + line * PG, nx, 1, seg, line < ny, eps);
+            }
+            __syncthreads();
+            // signs of plane z back, 16-byte stores (the plane's tail padding is scratch)
+            float4* dst = reinterpret_cast<float4*>(B.Y + nb.off + (long long)z * ps);
+            for (int q = t; q < ps / 4; q += NT) {
+                float o[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = 4 * q + u;
+                    o[u] = 0.0f;
+                    if (i < n) {
+                        const int y = dnx(i), x = i - y * nx;
+                        const float m = G[y * PG + x];
+                        o[u] = Pc[i] > 0.0f ? m : -m;
+                    }
+                }
+                dst[q] = make_float4(o[0], o[1], o[2], o[3]);
             }
         }
-        __syncthreads();
-        if (t < ny) line_sweep(G + t * PG, nx, 1, fx, nullptr, 0);      // x pass, thread = row
-        __syncthreads();
-        if (t < nx)                                         // y pass, thread = column -> Y
-            line_sweep(G + t, ny, PG, fy, B.Y + nb.off + (long long)z * ps + t, nx);
     }
 }
 
 // ---------------------------------------------------------------------------
 // pass 5: z taxicab pass per column, clamp, bounding box of the positive set
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kColThreads)
+// Column of nz <= NZ cells on a non-periodic axis, held in registers: the
+// magnitudes are scanned forward and backward and the signs put back.
+// Returns the mask of positive cells (bit z).
+template <int NZ>
+__device__ __forceinline__ unsigned long long redist_column(const float* hc, float* xc, float* dc, int nz, int ps,
+                                                            float eps) {
+    float r[NZ];
+    unsigned long long pm = 0;
+    // unconditional loads (cells past the column re-read its last cell), so
+    // that all of them are in flight at once
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) r[z] = __ldg(hc + (long long)min(z, nz - 1) * ps);
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) {
+        if (z < nz && sgn_pos(r[z])) pm |= 1ull << z;
+        r[z] = z < nz ? fabsf(r[z]) : eps;
+    }
+    scan_regs(r);
+#pragma unroll
+    for (int z = 0; z < NZ; ++z)
+        if (z < nz) {
+            const float out = (pm >> z) & 1ull ? r[z] : -r[z];
+            xc[(long long)z * ps] = out;
+            if (dc) dc[(long long)z * ps] = out;
+        }
+    return pm;
+}
+
+__global__ void __launch_bounds__(kColThreads, 2)
 p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
     if (halted(B)) return;
     const Domain D = B.dom;
@@ -546,56 +803,72 @@ p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
             const int ps = plane_stride(nx, ny);
             const float* hc = B.Y + nb.off + c;
             float* xc = B.X + nb.off + c;
-            float fr[ZR];                                  // forward-swept planes zb-6 .. zb
-#pragma unroll
-            for (int k = 0; k < ZR; ++k) fr[k] = -eps;
-            // periodic z: the sweep starts 6 planes early so that plane 0 sees its wrapped predecessors
-            const int zb_first = fz ? -kReachP : 0;
-            const int n_zb = nz + kReachP - zb_first;      // zb = zb_first .. nz-1+6
-            for (int base = 0; base < n_zb; base += kZB) {
-                float v[kZB];
-#pragma unroll
-                for (int u = 0; u < kZB; ++u) {
-                    const int zb = zb_first + base + u;
-                    v[u] = 0.0f;
-                    if (base + u < n_zb && (fz || zb < nz)) v[u] = hc[(long long)(fz ? pmod(zb, nz) : zb) * ps];
+            if (!fz && nz <= 64) {                         // uniform across the CTA (one box per item)
+                float* dc = dbg.phin ? dbg.phin + nb.off + c : nullptr;
+                const unsigned long long pm = nz <= 16   ? redist_column<16>(hc, xc, dc, nz, ps, eps)
+                                              : nz <= 32 ? redist_column<32>(hc, xc, dc, nz, ps, eps)
+                                              : nz <= 48 ? redist_column<48>(hc, xc, dc, nz, ps, eps)
+                                                         : redist_column<64>(hc, xc, dc, nz, ps, eps);
+                if (pm) {
+                    lo[0] = hi[0] = x;
+                    lo[1] = hi[1] = y;
+                    lo[2] = __ffsll((long long)pm) - 1;
+                    hi[2] = 63 - __clzll((long long)pm);
                 }
+            } else {
+                // periodic or long column: forward scan over a register ring,
+                // backward over a 6-plane window
+                float fr[ZR];                              // forward-swept planes zb-6 .. zb
 #pragma unroll
-                for (int u = 0; u < kZB; ++u) {
-                    if (base + u >= n_zb) break;
-                    const int zb = zb_first + base + u;
+                for (int k = 0; k < ZR; ++k) fr[k] = -eps;
+                // periodic z: the sweep starts 6 planes early so that plane 0 sees its wrapped predecessors
+                const int zb_first = fz ? -kReachP : 0;
+                const int n_zb = nz + kReachP - zb_first;  // zb = zb_first .. nz-1+6
+                for (int base = 0; base < n_zb; base += kZB) {
+                    float v[kZB];
 #pragma unroll
-                    for (int k = 0; k < ZR - 1; ++k) fr[k] = fr[k + 1];
-                    if (fz || zb < nz) {
-                        float val = v[u];
-                        const float p = fr[ZR - 2];
-                        if (zb != zb_first && sgn_pos(p) == sgn_pos(val)) {
-                            const float mm = fminf(fabsf(val), fabsf(p) + 1.0f);
-                            val = sgn_pos(val) ? mm : -mm;
+                    for (int u = 0; u < kZB; ++u) {
+                        const int zb = zb_first + base + u;
+                        v[u] = 0.0f;
+                        if (base + u < n_zb && (fz || zb < nz)) v[u] = hc[(long long)(fz ? pmod(zb, nz) : zb) * ps];
+                    }
+#pragma unroll
+                    for (int u = 0; u < kZB; ++u) {
+                        if (base + u >= n_zb) break;
+                        const int zb = zb_first + base + u;
+#pragma unroll
+                        for (int k = 0; k < ZR - 1; ++k) fr[k] = fr[k + 1];
+                        if (fz || zb < nz) {
+                            float val = v[u];
+                            const float p = fr[ZR - 2];
+                            if (zb != zb_first && sgn_pos(p) == sgn_pos(val)) {
+                                const float mm = fminf(fabsf(val), fabsf(p) + 1.0f);
+                                val = sgn_pos(val) ? mm : -mm;
+                            }
+                            fr[ZR - 1] = val;
                         }
-                        fr[ZR - 1] = val;
-                    }
-                    const int zo = zb - kReachP;
-                    if (zo < 0) continue;
-                    const int ztop = fz ? zb : min(zb, nz - 1);
-                    const float v0 = fr[0];
-                    const bool sg = sgn_pos(v0);
-                    float best = fabsf(v0);
-                    bool go = true;
+                        const int zo = zb - kReachP;
+                        if (zo < 0) continue;
+                        const int ztop = fz ? zb : min(zb, nz - 1);
+                        const float v0 = fr[0];
+                        const bool sg = sgn_pos(v0);
+                        float best = fabsf(v0);
+                        bool go = true;
 #pragma unroll
-                    for (int k = 1; k <= kReachP; ++k) {
-                        const float w = fr[k];
-                        go = go && (zo + k <= ztop) && (sgn_pos(w) == sg);
-                        if (go) best = fminf(best, fabsf(w) + (float)k);
-                    }
-                    best = fminf(best, eps);
-                    const float out = sg ? best : -best;
-                    xc[(long long)zo * ps] = out;
-                    if (dbg.phin) dbg.phin[nb.off + (long long)zo * ps + c] = out;
-                    if (out > 0.0f) {
-                        lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);
-                        lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
-                        lo[2] = min(lo[2], zo); hi[2] = max(hi[2], zo);
+                        for (int k = 1; k <= kReachP; ++k) {
+                            const float w = fr[k];
+                            go = go && (zo + k <= ztop) && (sgn_pos(w) == sg);
+                            if (go) best = fminf(best, fabsf(w) + (float)k);
+                        }
+                        best = fminf(best, eps);
+                        const float out = sg ? best : -best;
+                        xc[(long long)zo * ps] = out;
+                        if (dbg.phin) dbg.phin[nb.off + (long long)zo * ps + c] = out;
+                        if (out > 0.0f) {
+                            lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);
+                            lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
+                            lo[2] = min(lo[2], zo); hi[2] = max(hi[2], zo);
+                        }
                     }
                 }
             }
@@ -616,13 +889,22 @@ p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
         }
     }
 }
-
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 // The radius-specialised convolution kernels (R = 1 .. kMaxRadius) per tier
 // side; the z pass with or without the velocity correction of Eq. (10).
 constexpr int kTierSide[kTiers] = {32, 64};
+constexpr int kRedistThreads[kTiers] = {128, 256};   // threads per CTA of p_redist_xy (4 lanes per line)
+constexpr int kConvThreads[kTiers] = {128, 256};     // threads per CTA of p_conv_xy
+static size_t conv_smem_bytes(int side, int R) {       // ConvXYLayout<R, side>::bytes
+    const int pyr = side + 2 * R, px = ((side + 3) & ~3) + 4 * ((2 * R + 1 + 6) / 4), xp = (side + 3) & ~3;
+    return 128 + sizeof(float) * ((size_t)side * side + (size_t)pyr * px + (size_t)(pyr + 3) * xp) +
+           sizeof(int) * 2 * pyr;
+}
+constexpr size_t redist_smem_bytes(int side) {
+    return 128 + (size_t)(3 * side * side + side * (side + 1)) * sizeof(float);   // barriers, 3 slots, G
+}
 
 struct PassFns {
     const void* conv_xy[kTiers];
@@ -634,11 +916,11 @@ template <int R>
 static PassFns pass_fns_r(bool phys) {
     static_assert(kTiers == 2, "one instantiation per tier side");
     PassFns f;
-    f.conv_xy[0] = reinterpret_cast<const void*>(p_conv_xy<R, 32>);
-    f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 64>);
+    f.conv_xy[0] = reinterpret_cast<const void*>(p_conv_xy<R, 32, kConvThreads[0]>);
+    f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 64, kConvThreads[1]>);
     f.conv_z = phys ? reinterpret_cast<const void*>(p_conv_z<R, true>) : reinterpret_cast<const void*>(p_conv_z<R, false>);
-    f.redist_xy[0] = reinterpret_cast<const void*>(p_redist_xy<32>);
-    f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<64>);
+    f.redist_xy[0] = reinterpret_cast<const void*>(p_redist_xy<32, kRedistThreads[0]>);
+    f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<64, kRedistThreads[1]>);
     return f;
 }
 
@@ -663,9 +945,15 @@ cudaError_t configure_passes(StepBuffers& B) {
         B.tier_side[t] = kTierSide[t];
         B.tier_threads[t] = kTierSide[t];
         int o[5] = {0, 0, 1, 0, 0};
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], fn.conv_xy[t], kTierSide[t], 0);
+        e = allow_max_dynamic_smem(fn.conv_xy[t]);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], fn.conv_xy[t], kConvThreads[t],
+                                                              conv_smem_bytes(kTierSide[t], B.dom.radius));
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], fn.conv_z, kColThreads, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], fn.redist_xy[t], kTierSide[t], 0);
+        if (e == cudaSuccess) e = allow_max_dynamic_smem(fn.redist_xy[t]);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], fn.redist_xy[t], kRedistThreads[t],
+                                                              redist_smem_bytes(kTierSide[t]));
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[4], p_redist_z, kColThreads, 0);
         if (e != cudaSuccess) return e;
         for (int k = 0; k < 5; ++k) B.pgrid[t][k] = B.n_sm * (o[k] < 1 ? 1 : o[k]);
@@ -688,7 +976,6 @@ cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps&
                           const DebugOut& dbg, cudaStream_t s, cudaEvent_t* pass_ev) {
     PassFns fn;
     if (!pass_fns(taps.radius, phys.kind != LSGG_PHYSICS_IDEAL, &fn)) return cudaErrorInvalidValue;
-    const int nt = B.tier_threads[tier];
     const int* g = B.pgrid[tier];
     StepBuffers bb = B;
     Taps tp = taps;
@@ -700,7 +987,8 @@ cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps&
     if (pass_ev) cudaEventRecord(pass_ev[k++], s);
     if (which == 0) {
         void* a0[] = {&bb, &tp, &tr};
-        e = cudaLaunchKernel(fn.conv_xy[tier], dim3(g[0]), dim3(nt), a0, 0, s);
+        e = cudaLaunchKernel(fn.conv_xy[tier], dim3(g[0]), dim3(kConvThreads[tier]), a0,
+                             conv_smem_bytes(kTierSide[tier], taps.radius), s);
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
         void* a1[] = {&bb, &tp, &ph, &tr};
@@ -709,7 +997,8 @@ cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps&
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
     } else {
         void* a3[] = {&bb, &tr};
-        e = cudaLaunchKernel(fn.redist_xy[tier], dim3(g[3]), dim3(nt), a3, 0, s);
+        e = cudaLaunchKernel(fn.redist_xy[tier], dim3(g[3]), dim3(kRedistThreads[tier]), a3,
+                             redist_smem_bytes(kTierSide[tier]), s);
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
         void* a4[] = {&bb, &db, &tr};

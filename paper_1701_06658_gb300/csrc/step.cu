@@ -458,7 +458,7 @@ __device__ __forceinline__ int pass_tier(const StepBuffers& B, int c) {
 __global__ void __launch_bounds__(kBoxUpdateThreads)
 k_box_update(StepBuffers B, int layout_only) {
     __shared__ long long s_part[kBoxUpdateThreads];
-    __shared__ int s_scan[(kBoxUpdateThreads / 32) * (kNumClasses + 2 * kTiers)];
+    __shared__ int s_scan[(kBoxUpdateThreads / 32) * (kNumClasses + 3 * kTiers)];
     const int G = B.n_boxes;
     const Domain D = B.dom;
     if (*(volatile int*)&B.st->halt && !layout_only) return;
@@ -522,10 +522,10 @@ k_box_update(StepBuffers B, int layout_only) {
         return;
     }
     long long off = s_part[threadIdx.x] - sum;
-    // per-thread counts: boxes per class (work lists), pass-path planes and
-    // column chunks per tier; their block-wide exclusive scans place every
-    // box's entries in box order
-    constexpr int NV = kNumClasses + 2 * kTiers;
+    // per-thread counts: boxes per class (work lists), pass-path planes,
+    // column chunks and slabs per tier; their block-wide exclusive scans place
+    // every box's entries in box order
+    constexpr int NV = kNumClasses + 3 * kTiers;
     int cnt[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) cnt[k] = 0;
@@ -543,6 +543,7 @@ k_box_update(StepBuffers B, int layout_only) {
                 const int t = pass_tier(B, c);
                 cnt[kNumClasses + t] += cb.nz;
                 cnt[kNumClasses + kTiers + t] += (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
+                cnt[kNumClasses + 2 * kTiers + t] += (cb.nz + kSlab - 1) / kSlab;
                 tcell[t] += vol;
             }
             cells += vol;
@@ -552,7 +553,8 @@ k_box_update(StepBuffers B, int layout_only) {
     int pre[NV], tot[NV];
     block_exclusive_scan<NV>(cnt, pre, tot, s_scan);
     const bool items_fit = (long long)tot[kNumClasses] + tot[kNumClasses + 1] <= B.plane_item_cap &&
-                           (long long)tot[kNumClasses + kTiers] + tot[kNumClasses + kTiers + 1] <= B.chunk_item_cap;
+                           (long long)tot[kNumClasses + kTiers] + tot[kNumClasses + kTiers + 1] <= B.chunk_item_cap &&
+                           (long long)tot[kNumClasses + 2 * kTiers] + tot[kNumClasses + 2 * kTiers + 1] <= B.slab_item_cap;
     for (int b = b0; b < b1; ++b) {
         const Box cb = B.cur[b];
         if (cb.nx <= 0) continue;
@@ -566,10 +568,14 @@ k_box_update(StepBuffers B, int layout_only) {
         const int nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
         const int p0 = (t ? tot[kNumClasses] : 0) + pre[kNumClasses + t];
         const int c0 = (t ? tot[kNumClasses + kTiers] : 0) + pre[kNumClasses + kTiers + t];
+        const int nsl = (cb.nz + kSlab - 1) / kSlab;
+        const int s0 = (t ? tot[kNumClasses + 2 * kTiers] : 0) + pre[kNumClasses + 2 * kTiers + t];
         pre[kNumClasses + t] += cb.nz;
         pre[kNumClasses + kTiers + t] += nch;
+        pre[kNumClasses + 2 * kTiers + t] += nsl;
         for (int z = 0; z < cb.nz; ++z) B.plane_items[p0 + z] = make_int2(b, z);
         for (int k = 0; k < nch; ++k) B.chunk_items[c0 + k] = make_int2(b, k);
+        for (int k = 0; k < nsl; ++k) B.slab_items[s0 + k] = make_int2(b, k * kSlab);
     }
     // reduce cells / alive / tier cells
     const long long r_cells = block_sum_ll(cells, s_part);
@@ -588,6 +594,8 @@ k_box_update(StepBuffers B, int layout_only) {
         B.st->n_chunks[t] = items_fit ? tot[kNumClasses + kTiers + t] : 0;
         B.st->plane_base[t] = t ? tot[kNumClasses] : 0;
         B.st->chunk_base[t] = t ? tot[kNumClasses + kTiers] : 0;
+        B.st->n_slabs[t] = items_fit ? tot[kNumClasses + 2 * kTiers + t] : 0;
+        B.st->slab_base[t] = t ? tot[kNumClasses + 2 * kTiers] : 0;
         B.st->tier_cells[t] = r_tc[t];
     }
     if (threadIdx.x == 0) {

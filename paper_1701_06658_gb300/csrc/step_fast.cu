@@ -58,12 +58,12 @@ cudaError_t launch_fast(const StepBuffers& B, int which, int cls, const Taps& ta
 __global__ void k_wait_timeout(int iterations, int* out) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
-        fast::mbar_init(&bar, 1);
-        fast::fence_mbar_init();
+        mbar_init(&bar, 1);
+        fence_mbar_init();
     }
     __syncthreads();
     bool done = false;
-    for (int i = 0; i < iterations && !done; ++i) done = fast::mbar_test(&bar, 0u);
+    for (int i = 0; i < iterations && !done; ++i) done = mbar_test(&bar, 0u);
     if (threadIdx.x == 0) *out = done ? 0 : 1;
 }
 

@@ -20,42 +20,11 @@
 #include <cfloat>
 #include <climits>
 
+#include "bulk_copy.cuh"
 #include "kernels_common.cuh"
 
 namespace lsgg {
 namespace fast {
-
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t sa(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(r)
-        : "r"(sa(b)), "r"(parity)
-        : "memory");
-    return r != 0;
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     sa(dst)),
-                 "l"(src), "r"(bytes), "r"(sa(b))
-                 : "memory");
-}
-constexpr int kWaitIters = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (int i = 0; i < kWaitIters; ++i)
-        if (mbar_test(b, parity)) return true;
-    return false;
-}
 
 // Division of small non-negative ints (< 2^16) by a per-box divisor d:
 // q = (t * ceil(2^32 / d)) >> 32 is exact in that range, two instructions

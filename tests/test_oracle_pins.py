@@ -255,6 +255,33 @@ def test_redistance_fixed_point_is_shortest_path(oracle, shape, full):
         assert np.array_equal(got > 0, phic > 0)
 
 
+@pytest.mark.parametrize("shape,full", [((5, 6, 7), (False,) * 3), ((4, 6, 5), (True, True, False)),
+                                         ((1, 11, 9), (False, False, True))])
+def test_same_sign_restriction_is_immaterial(oracle, shape, full):
+    """Every sign change lies between two reference cells, whose values are at
+    most 1, so the same-sign fixed point equals the unrestricted taxicab
+    distance transform of the classified magnitudes: min over all cells k of
+    m_k + |x - k|_1 (minimum image on periodic axes), capped at eps, with the
+    cell's own sign.  The pass kernels compute that transform with separable
+    scans that ignore signs."""
+    rng = np.random.default_rng(17)
+    axes = oracle.spatial_axes(shape)
+    idx = np.stack(np.meshgrid(*[np.arange(n) for n in shape], indexing="ij"), -1).reshape(-1, 3)
+    for trial in range(4):
+        phic = rng.uniform(-3, 3, size=shape) + rng.uniform(-1, 1)
+        phic[rng.uniform(size=shape) < 0.05] = 0.0
+        is_ref, dref = oracle.reference_values(phic, full, 7.0, axes)
+        m = np.where(is_ref, dref, 7.0).reshape(-1)
+        d = np.abs(idx[:, None, :] - idx[None, :, :])
+        for a in range(3):
+            if full[a]:
+                d[..., a] = np.minimum(d[..., a], shape[a] - d[..., a])
+        brute = np.minimum(7.0, (m[None, :] + d.sum(-1)).min(axis=1)).reshape(shape)
+        want = np.where(phic > 0, brute, -brute)
+        got = oracle.redistance(phic, full, 7.0, axes)
+        assert np.max(np.abs(got - want)) < 1e-12
+
+
 def test_redistance_axis_plane_is_exact(oracle):
     """Taxicab propagation reproduces an axis-aligned planar SDF exactly
     (within eps) and caps it at eps."""
