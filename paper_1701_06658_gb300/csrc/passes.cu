@@ -1,5 +1,6 @@
 // Pass path of the batched step for 3D boxes whose x and y sides are at most
-// 64: passes over (box, plane), (box, column chunk) and domain-tile work items.
+// 64: passes over (box, plane), (box, slab), (box, column chunk) and
+// domain-tile work items.
 //
 // Same arithmetic as the box-streaming kernels (Sec. 2.1.4 predictor, Eq. (16)
 // comparison, Sec. 2.1.6 taxicab re-initialisation), arranged so that every
@@ -8,17 +9,18 @@
 // serialised a whole box along z.  The fields between passes go through HBM:
 //   k_bin       per box: list it in every domain tile it overlaps; reset its
 //               positive bounding box
-//   p_conv_xy   (box, plane): stage the plane of phi (old box -> new box, -eps
-//               outside), x and y passes in shared memory   -> Z = xy-convolved
+//   p_conv_xy   (box, plane): bulk copy of the plane of phi in the old layout,
+//               staged into the new layout (-eps outside), x and y passes in
+//               shared memory                                     -> Z = xy-convolved
 //   p_conv_z    (box, columns): z pass over a register window, velocity
-//               correction, clamp                                -> Y = phi_p
+//               correction, clamp                                 -> Y = phi_p
 //   p_field     (domain tile): top-2 keys (phi_p, -id) over the tile's boxes
 //               in registers -> T; then phi_c = (phi_p - m) / 2 and the
-//               ID-field for every box cell of the tile          -> Z = phi_c
-//   p_redist_xy (box, plane): reference cells with their planar-exact
-//               distances, x and y sign-blocked taxicab passes   -> Y
-//   p_redist_z  (box, columns): forward sweep + 6-plane backward window along
-//               z, clamp, positive bounding box                  -> X = phi
+//               ID-field for every box cell of the tile           -> Z = phi_c
+//   p_redist_xy (box, slab): plane ring filled by bulk copies; reference cells
+//               with their planar-exact distances, y and x taxicab scans -> Y
+//   p_redist_z  (box, columns): the column in registers, z taxicab scans,
+//               signs, positive bounding box                      -> X = phi
 // The field pass replaces the box-streaming kernels' atomic scatter: each
 // domain cell's top-2 is built by the one thread that owns the cell, so the
 // step has no atomics on the field.  The work-item lists are written by the
@@ -564,16 +566,17 @@ __device__ __forceinline__ void scan_line_wrap(float* L, int n, int st) {
     }
 }
 
-// Segmented scan of a line of n <= 4 * L cells (stride st in shared memory)
-// by the 4 consecutive lanes that share it: lane `seg` scans cells
+// Segmented scan of a line of n <= LANES * L cells (stride st in shared
+// memory) by the LANES consecutive lanes that share it: lane `seg` scans cells
 // [seg * L, seg * L + L) in registers, then takes the boundary value of its
 // neighbour segment (forward: the previous segment's last cell, backward: the
 // next segment's first) and lowers its first / last cells by it.  With L > 6
 // a segment's boundary cells do not depend on the carry coming into it, so
-// one exchange per direction suffices.  All 4 lanes of a group must call.
-template <int L>
+// one exchange per direction suffices.  All lanes of a group must call.
+template <int L, int LANES>
 __device__ __forceinline__ void scan_line_seg(float* line, int n, int st, int seg, bool active, float eps) {
     static_assert(L > kRedistReach, "one exchange per direction needs segments longer than the reach");
+    static_assert(LANES > 1 && 32 % LANES == 0, "a group of lanes lies within one warp");
     float r[L];
     const int j0 = seg * L;
 #pragma unroll
@@ -587,7 +590,7 @@ __device__ __forceinline__ void scan_line_seg(float* line, int n, int st, int se
 #pragma unroll
     for (int j = L - 2; j >= 0; --j) r[j] = fminf(r[j], r[j + 1] + 1.0f);
     float cb = __shfl_down_sync(0xffffffffu, r[0], 1);
-    if (seg == 3) cb = eps;
+    if (seg == LANES - 1) cb = eps;
 #pragma unroll
     for (int j = 0; j < kRedistReach; ++j) r[L - 1 - j] = fminf(r[L - 1 - j], cb + (float)(j + 1));
 #pragma unroll
@@ -601,7 +604,8 @@ __device__ __forceinline__ void scan_line_seg(float* line, int n, int st, int se
 // (a box plane is contiguous and 16-byte aligned), plane z + 2 being fetched
 // while plane z is processed.  For plane z every thread classifies cells
 // from the slots of z - 1, z, z + 1; the magnitudes go to a grid G (odd
-// pitch); the y and x scans run with 4 lanes per line; the signs of plane z
+// pitch); the y and x scans run with NT / SIDE lanes per line; the signs of
+// plane z
 // are put back as the plane is stored with 16-byte stores.  Every wait on a
 // copy is bounded: on expiry the CTA records LSGG_ERR_TIMEOUT, halts the step,
 // drains its copies (bounded) and returns.
@@ -610,9 +614,10 @@ __global__ void __launch_bounds__(NT)
 p_redist_xy(StepBuffers B, int tier) {
     constexpr int PA = SIDE * SIDE;                   // floats per plane slot
     constexpr int PG = SIDE + 1;                      // pitch of G
-    constexpr int L = SIDE / 4;                       // segment of a scan lane
+    constexpr int LANES = NT / SIDE;                  // scan lanes per line
+    constexpr int L = SIDE / LANES;                   // segment of a scan lane
     constexpr int KC = PA / NT;                       // cells classified per thread
-    static_assert(PA % NT == 0 && NT / 4 >= SIDE, "4 lanes per line of the plane");
+    static_assert(PA % NT == 0 && NT % SIDE == 0, "LANES lanes per line of the plane");
     extern __shared__ __align__(128) unsigned char smraw[];    // redist_smem_bytes(SIDE)
     uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
     float* const slots = reinterpret_cast<float*>(smraw + 128);
@@ -716,19 +721,19 @@ p_redist_xy(StepBuffers B, int tier) {
                 G[y * PG + x] = mag[k];
             }
             __syncthreads();
-            // scans: 4 lanes per line; a warp holds 8 lines and skips as a
-            // whole when all of them lie past the plane
-            const int line = t >> 2, seg = t & 3, warp_line0 = (t >> 5) * 8;
+            // scans: LANES lanes per line; a warp holds 32 / LANES lines and
+            // skips as a whole when all of them lie past the plane
+            const int line = t / LANES, seg = t % LANES, warp_line0 = (t >> 5) * (32 / LANES);
             if (fy) {                                       // periodic y: one lane per column
                 if (seg == 0 && line < nx) scan_line_wrap(G + line, ny, PG);
             } else if (warp_line0 < nx) {
-                scan_line_seg<L>(G + line, ny, PG, seg, line < nx, eps);
+                scan_line_seg<L, LANES>(G + line, ny, PG, seg, line < nx, eps);
             }
             __syncthreads();
             if (fx) {
                 if (seg == 0 && line < ny) scan_line_wrap(G + line * PG, nx, 1);
             } else if (warp_line0 < ny) {
-                scan_line_seg<L>(G + line * PG, nx, 1, seg, line < ny, eps);
+                scan_line_seg<L, LANES>(G + line * PG, nx, 1, seg, line < ny, eps);
             }
             __syncthreads();
             // signs of plane z back, 16-byte stores (the plane's tail padding is scratch)
