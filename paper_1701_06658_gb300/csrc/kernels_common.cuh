@@ -13,7 +13,7 @@ __device__ __forceinline__ bool sgn_pos(float v) { return !(__float_as_uint(v) >
 // ceil(2^32 / d)) >> 32 is exact in that range (two instructions).  The
 // multiplier of every divisor up to kDivTable comes from a table in constant
 // memory (one load, uniform across the warp); larger divisors compute it.
-constexpr int kDivTable = 160;
+constexpr int kDivTable = 256;
 struct DivMagic {
     unsigned m[kDivTable + 1];
 };
@@ -28,7 +28,8 @@ struct Div16 {
     unsigned m;
     __device__ __forceinline__ explicit Div16(int d)
         : m(d <= kDivTable ? c_div_magic.m[d] : (unsigned)((0x100000000ULL + d - 1) / d)) {}
-    __device__ __forceinline__ int operator()(int t) const { return (int)__umulhi((unsigned)t, m); }
+    // d = 1: the multiplier 2^32 does not fit and is stored as 0
+    __device__ __forceinline__ int operator()(int t) const { return m ? (int)__umulhi((unsigned)t, m) : t; }
 };
 
 // a mod n for a within one period of [0, n) (the usual case of box and
