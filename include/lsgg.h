@@ -148,6 +148,7 @@ void* lsgg_get_stream(lsgg_ctx* ctx);
 size_t lsgg_abi_config_size(void);
 
 /* ------------------------------------------------------------- inspection */
+#define LSGG_PASS_TIERS 3      /* pass-path tiers: boxes of x, y side <= 32, <= 48, <= 64 */
 typedef struct lsgg_stats {
     int64_t steps_done;        /* steps completed since creation */
     int64_t cell_updates;      /* box cells advanced, summed over completed steps */
@@ -158,8 +159,8 @@ typedef struct lsgg_stats {
     int64_t device_bytes;      /* device memory held by the context */
     int32_t n_classes;         /* box-size classes of the batched path */
     int32_t class_count[8];    /* boxes per class at the last box update */
-    int64_t pass_cells[2];     /* box cells on the pass path per tier (x, y side <= 32,
-                                  <= 64) at the last box update; 0 off the pass path */
+    int64_t pass_cells[LSGG_PASS_TIERS];  /* box cells on the pass path per tier (x, y side
+                                  <= 32, <= 48, <= 64) at the last box update; 0 off the pass path */
 } lsgg_stats;
 
 int lsgg_get_stats(lsgg_ctx* ctx, lsgg_stats* out);
@@ -191,11 +192,12 @@ int lsgg_autotune(lsgg_ctx* ctx, int32_t steps_per_trial, double dt, int32_t* ch
 int lsgg_kernel_times(lsgg_ctx* ctx, double* out_ms, int64_t* out_count);
 
 /* Per-pass timing of the pass path (LSGG_EXEC_BATCHED, 3D), from the same
- * profiled steps as lsgg_kernel_times (arrays of 10; NULL allowed):
- * out_ms[t * 4 + k] / out_count[t * 4 + k] for tier t = 0 (boxes of x, y side
- * <= 32), 1 (<= 64) and pass k = 0 p_conv_xy, 1 p_conv_z, 2 p_redist_xy,
- * 3 p_redist_z; [8] the tile binning (k_bin), [9] the field pass (p_field,
- * all boxes).  In lsgg_kernel_times the binning is group 0 and the field
+ * profiled steps as lsgg_kernel_times (arrays of 4 * LSGG_PASS_TIERS + 2;
+ * NULL allowed): out_ms[t * 4 + k] / out_count[t * 4 + k] for tier t = 0
+ * (boxes of x, y side <= 32), 1 (<= 48), 2 (<= 64) and pass k = 0 p_conv_xy,
+ * 1 p_conv_z, 2 p_redist_xy, 3 p_redist_z; [4 * LSGG_PASS_TIERS] the tile
+ * binning (k_bin), [4 * LSGG_PASS_TIERS + 1] the field pass (p_field, all
+ * boxes).  In lsgg_kernel_times the binning is group 0 and the field
  * pass belongs to group 1.  Synchronises, then resets the sums. */
 int lsgg_pass_times(lsgg_ctx* ctx, double* out_ms, int64_t* out_count);
 

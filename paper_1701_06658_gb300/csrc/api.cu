@@ -16,6 +16,8 @@
 #include "lsgg_internal.cuh"
 #include "../../include/lsgg.h"
 
+static_assert(lsgg::kTiers == LSGG_PASS_TIERS, "pass-path tiers of the library and of the ABI");
+
 namespace lsgg {
 cudaError_t launch_init(const Domain& D, int G, const SeedBins& bins, const double* d_seeds, const double* d_weights, int* d_labels,
                         unsigned* d_bits, long long words_per_row, int* d_bb, Box* d_cur, cudaStream_t s);

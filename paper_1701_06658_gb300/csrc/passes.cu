@@ -24,9 +24,9 @@
 // The field pass replaces the box-streaming kernels' atomic scatter: each
 // domain cell's top-2 is built by the one thread that owns the cell, so the
 // step has no atomics on the field.  The work-item lists are written by the
-// box update; boxes of x, y side <= 32 (tier 0) and <= 64 (tier 1) have their
-// own lists and launches, so the plane passes of small boxes run with small
-// CTAs and high occupancy.  A non-periodic box's planes outside it are -eps;
+// box update; boxes of x, y side <= 32, <= 48 and <= 64 (tiers 0, 1, 2) have
+// their own lists and launches, so the plane passes of smaller boxes run with
+// smaller shared-memory grids and higher occupancy.  A non-periodic box's planes outside it are -eps;
 // their xy convolution is the constant that p_conv_z recomputes with the FMA
 // sequence p_conv_xy would use.
 #include <cfloat>
@@ -144,6 +144,11 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         const bool fx = nx == D.nx, fy = ny == D.ny;
         const int PXa = nx + 2 * R, PYa = ny + 2 * R;
         const bool have = pending;
+        if (max(max(nx, ny), max(ob.nx, ob.ny)) > SIDE) {    // not this tier's box: refuse, never overrun
+            if (t == 0) { atomicExch(&B.st->status, LSGG_ERR_UNSUPPORTED); atomicExch(&B.st->halt, 1); }
+            if (have) { if (t == 0) mbar_wait(bar, phase); }
+            return;
+        }
         for (int i = t; i < PXa + PYa; i += NT) {
             const bool isx = i < PXa;
             const int ip = isx ? i : i - PXa;
@@ -648,6 +653,10 @@ p_redist_xy(StepBuffers B, int tier) {
         const int n = nx * ny;
         const float* zb = B.Z + nb.off;
         const int z1 = min(z0 + kSlab, nz);
+        if (max(nx, ny) > SIDE) {                           // not this tier's box: refuse, never overrun
+            if (t == 0) { atomicExch(&B.st->status, LSGG_ERR_UNSUPPORTED); atomicExch(&B.st->halt, 1); }
+            return;                                         // no copy is in flight between items
+        }
         // plane zz (z0 - 1 <= zz <= z1) lives in slot (zz - z0 + 1) mod 3; a
         // plane outside a non-periodic box is the -eps fill
         auto request = [&](int zz) {
@@ -899,9 +908,9 @@ p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
 // ---------------------------------------------------------------------------
 // The radius-specialised convolution kernels (R = 1 .. kMaxRadius) per tier
 // side; the z pass with or without the velocity correction of Eq. (10).
-constexpr int kTierSide[kTiers] = {32, 64};
-constexpr int kRedistThreads[kTiers] = {128, 256};   // threads per CTA of p_redist_xy (4 lanes per line)
-constexpr int kConvThreads[kTiers] = {128, 256};     // threads per CTA of p_conv_xy
+constexpr int kTierSide[kTiers] = {32, 48, 64};
+constexpr int kRedistThreads[kTiers] = {128, 192, 256};   // threads per CTA of p_redist_xy (4 lanes per line)
+constexpr int kConvThreads[kTiers] = {128, 192, 256};     // threads per CTA of p_conv_xy
 static size_t conv_smem_bytes(int side, int R) {       // ConvXYLayout<R, side>::bytes
     const int pyr = side + 2 * R, px = ((side + 3) & ~3) + 4 * ((2 * R + 1 + 6) / 4), xp = (side + 3) & ~3;
     return 128 + sizeof(float) * ((size_t)side * side + (size_t)pyr * px + (size_t)(pyr + 3) * xp) +
@@ -919,13 +928,15 @@ struct PassFns {
 
 template <int R>
 static PassFns pass_fns_r(bool phys) {
-    static_assert(kTiers == 2, "one instantiation per tier side");
+    static_assert(kTiers == 3, "one instantiation per tier side");
     PassFns f;
     f.conv_xy[0] = reinterpret_cast<const void*>(p_conv_xy<R, 32, kConvThreads[0]>);
-    f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 64, kConvThreads[1]>);
+    f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 48, kConvThreads[1]>);
+    f.conv_xy[2] = reinterpret_cast<const void*>(p_conv_xy<R, 64, kConvThreads[2]>);
     f.conv_z = phys ? reinterpret_cast<const void*>(p_conv_z<R, true>) : reinterpret_cast<const void*>(p_conv_z<R, false>);
     f.redist_xy[0] = reinterpret_cast<const void*>(p_redist_xy<32, kRedistThreads[0]>);
-    f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<64, kRedistThreads[1]>);
+    f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<48, kRedistThreads[1]>);
+    f.redist_xy[2] = reinterpret_cast<const void*>(p_redist_xy<64, kRedistThreads[2]>);
     return f;
 }
 

@@ -452,7 +452,9 @@ __device__ __forceinline__ int box_class(const StepBuffers& B, const Box& b, con
 
 // Tier of a pass-path class: the smallest tier whose side holds the class's side.
 __device__ __forceinline__ int pass_tier(const StepBuffers& B, int c) {
-    return B.class_side[c] <= B.tier_side[0] ? 0 : 1;
+    for (int t = 0; t < kTiers - 1; ++t)
+        if (B.class_side[c] <= B.tier_side[t]) return t;
+    return kTiers - 1;
 }
 
 __global__ void __launch_bounds__(kBoxUpdateThreads)
@@ -552,9 +554,20 @@ k_box_update(StepBuffers B, int layout_only) {
     }
     int pre[NV], tot[NV];
     block_exclusive_scan<NV>(cnt, pre, tot, s_scan);
-    const bool items_fit = (long long)tot[kNumClasses] + tot[kNumClasses + 1] <= B.plane_item_cap &&
-                           (long long)tot[kNumClasses + kTiers] + tot[kNumClasses + kTiers + 1] <= B.chunk_item_cap &&
-                           (long long)tot[kNumClasses + 2 * kTiers] + tot[kNumClasses + 2 * kTiers + 1] <= B.slab_item_cap;
+    // first entry of each tier's items in the shared lists (kind 0 planes,
+    // 1 column chunks, 2 slabs): the totals of the tiers before it
+    int tier_base[3][kTiers];
+    long long kind_total[3];
+    for (int kd = 0; kd < 3; ++kd) {
+        long long acc = 0;
+        for (int t = 0; t < kTiers; ++t) {
+            tier_base[kd][t] = (int)acc;
+            acc += tot[kNumClasses + kd * kTiers + t];
+        }
+        kind_total[kd] = acc;
+    }
+    const bool items_fit = kind_total[0] <= B.plane_item_cap && kind_total[1] <= B.chunk_item_cap &&
+                           kind_total[2] <= B.slab_item_cap;
     for (int b = b0; b < b1; ++b) {
         const Box cb = B.cur[b];
         if (cb.nx <= 0) continue;
@@ -566,10 +579,10 @@ k_box_update(StepBuffers B, int layout_only) {
         if (!items_fit) continue;
         const int t = pass_tier(B, c);
         const int nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
-        const int p0 = (t ? tot[kNumClasses] : 0) + pre[kNumClasses + t];
-        const int c0 = (t ? tot[kNumClasses + kTiers] : 0) + pre[kNumClasses + kTiers + t];
+        const int p0 = tier_base[0][t] + pre[kNumClasses + t];
+        const int c0 = tier_base[1][t] + pre[kNumClasses + kTiers + t];
         const int nsl = (cb.nz + kSlab - 1) / kSlab;
-        const int s0 = (t ? tot[kNumClasses + 2 * kTiers] : 0) + pre[kNumClasses + 2 * kTiers + t];
+        const int s0 = tier_base[2][t] + pre[kNumClasses + 2 * kTiers + t];
         pre[kNumClasses + t] += cb.nz;
         pre[kNumClasses + kTiers + t] += nch;
         pre[kNumClasses + 2 * kTiers + t] += nsl;
@@ -592,10 +605,10 @@ k_box_update(StepBuffers B, int layout_only) {
         const int t = threadIdx.x;
         B.st->n_planes[t] = items_fit ? tot[kNumClasses + t] : 0;
         B.st->n_chunks[t] = items_fit ? tot[kNumClasses + kTiers + t] : 0;
-        B.st->plane_base[t] = t ? tot[kNumClasses] : 0;
-        B.st->chunk_base[t] = t ? tot[kNumClasses + kTiers] : 0;
+        B.st->plane_base[t] = tier_base[0][t];
+        B.st->chunk_base[t] = tier_base[1][t];
         B.st->n_slabs[t] = items_fit ? tot[kNumClasses + 2 * kTiers + t] : 0;
-        B.st->slab_base[t] = t ? tot[kNumClasses + 2 * kTiers] : 0;
+        B.st->slab_base[t] = tier_base[2][t];
         B.st->tier_cells[t] = r_tc[t];
     }
     if (threadIdx.x == 0) {

@@ -60,7 +60,7 @@ class Stats(C.Structure):
         ("steps_done", C.c_int64), ("cell_updates", C.c_int64), ("alive", C.c_int64), ("box_cells", C.c_int64),
         ("arena_capacity", C.c_int64), ("superimposition", C.c_double),
         ("device_bytes", C.c_int64), ("n_classes", C.c_int32), ("class_count", C.c_int32 * 8),
-        ("pass_cells", C.c_int64 * 2),
+        ("pass_cells", C.c_int64 * 3),
     ]
 
 
@@ -230,17 +230,19 @@ def kernel_times(ctx):
 
 
 PASS_NAMES = ("p_conv_xy", "p_conv_z", "p_redist_xy", "p_redist_z")
+PASS_TIERS = 3          # LSGG_PASS_TIERS: boxes of x, y side <= 32, <= 48, <= 64
 
 
 def pass_times(ctx):
     """{name: (ms, launches)} of the pass path since the previous call: the
     per-tier passes as "name[tierT]", plus "k_bin" and "p_field"."""
-    ms = np.zeros(10, np.float64)
-    cnt = np.zeros(10, np.int64)
+    ms = np.zeros(4 * PASS_TIERS + 2, np.float64)
+    cnt = np.zeros(4 * PASS_TIERS + 2, np.int64)
     _check("pass_times", lib().lsgg_pass_times(ctx, _ptr(ms, C.c_double), _ptr(cnt, C.c_int64)))
-    out = {f"{PASS_NAMES[k]}[tier{t}]": (float(ms[t * 4 + k]), int(cnt[t * 4 + k])) for t in range(2) for k in range(4)}
-    out["k_bin"] = (float(ms[8]), int(cnt[8]))
-    out["p_field"] = (float(ms[9]), int(cnt[9]))
+    out = {f"{PASS_NAMES[k]}[tier{t}]": (float(ms[t * 4 + k]), int(cnt[t * 4 + k]))
+           for t in range(PASS_TIERS) for k in range(4)}
+    out["k_bin"] = (float(ms[4 * PASS_TIERS]), int(cnt[4 * PASS_TIERS]))
+    out["p_field"] = (float(ms[4 * PASS_TIERS + 1]), int(cnt[4 * PASS_TIERS + 1]))
     return out
 
 

@@ -317,7 +317,7 @@ def test_pass_times_cover_every_pass(L):
         L.kernel_times(ms.ctx)
         pt = L.pass_times(ms.ctx)
         L.profile(ms.ctx, False)
-    assert len(pt) == 10
+    assert len(pt) == 4 * L.PASS_TIERS + 2
     for name, (ms_, n) in pt.items():
         assert n == 3, (name, n)
         assert ms_ >= 0.0
