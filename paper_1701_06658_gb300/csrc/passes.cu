@@ -254,6 +254,32 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
 // ---------------------------------------------------------------------------
 // pass 2: z convolution per column, velocity correction, clamp
 // ---------------------------------------------------------------------------
+// z pass of one column of nz <= NZ cells on a non-periodic axis, ideal
+// growth: the column in registers (unconditional loads: cells past the column
+// re-read its last cell, so all of them are in flight at once), planes
+// outside the box are the constant xy convolution of -eps.
+template <int R, int NZ>
+__device__ __forceinline__ void conv_column(const float* zc, float* yc, int nz, int ps, const float (&g)[2 * R + 1],
+                                            float cconst, float eps) {
+    constexpr int W = 2 * R + 1;
+    float r[NZ + 2 * R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) r[k] = cconst;
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) r[R + z] = __ldg(zc + (long long)min(z, nz - 1) * ps);
+#pragma unroll
+    for (int z = 0; z < NZ + R; ++z)
+        if (z >= nz) r[R + z] = cconst;
+#pragma unroll
+    for (int z = 0; z < NZ; ++z)
+        if (z < nz) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < W; ++k) acc = fmaf(g[k], r[z + k], acc);
+            yc[(long long)z * ps] = fminf(fmaxf(acc, -eps), eps);
+        }
+}
+
 template <int R, bool PHYS>
 __global__ void __launch_bounds__(kColThreads)
 p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
@@ -295,6 +321,13 @@ p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
             oxl = wrap_near(nb.ox + x - ob.ox, D.nx);
             oyl = wrap_near(nb.oy + y - ob.oy, D.ny);
             in_old_xy = oxl < ob.nx && oyl < ob.ny;
+        }
+        if (!PHYS && !fz && nz <= 64) {                    // uniform across the CTA (one box per item)
+            if (nz <= 16) conv_column<R, 16>(zc, yc, nz, ps, g, cconst, D.eps);
+            else if (nz <= 32) conv_column<R, 32>(zc, yc, nz, ps, g, cconst, D.eps);
+            else if (nz <= 48) conv_column<R, 48>(zc, yc, nz, ps, g, cconst, D.eps);
+            else conv_column<R, 64>(zc, yc, nz, ps, g, cconst, D.eps);
+            continue;
         }
         const int ps_old = plane_stride(ob.nx, ob.ny);
         float win[W];                                      // planes zo-R .. zo+R
