@@ -279,6 +279,35 @@ def gpu_arm(args):
             compare[name] = {"value": rate, "unit": UNIT, "steps": steps, "ms_per_step": 1e3 * el / steps,
                              "timing": "host wall clock around the steps (synchronised)"}
 
+    # ---------------- BF16 state storage on the same workload ----------------
+    # phi stored in BF16 between steps (FP32 arithmetic): device-timed steps and
+    # the per-grain volume error against FP32 after the same number of steps
+    bf16 = None
+    if not args.no_compare and rank == 0:
+        steps_b = 10
+        vols = {}
+        for st in (L.STORAGE_FP32, L.STORAGE_BF16):
+            with L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=exec_mode, storage=st) as bm:
+                bm.step(2, dt)
+                bm.sync()
+                c0 = bm.stats().cell_updates
+                bstream = torch.cuda.ExternalStream(bm.stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(bstream)
+                bm.step(steps_b, dt)
+                e1.record(bstream)
+                bm.sync()
+                torch.cuda.synchronize()
+                vols[st] = (bm.grain_volumes(), (bm.stats().cell_updates - c0) / (e0.elapsed_time(e1) * 1e-3),
+                            e0.elapsed_time(e1) / steps_b)
+        v32, v16 = vols[L.STORAGE_FP32][0], vols[L.STORAGE_BF16][0]
+        alive = v32 > 50.0
+        rel = np.abs(v16[alive] - v32[alive]) / v32[alive]
+        bf16 = {"value": vols[L.STORAGE_BF16][1], "unit": UNIT, "ms_per_step": vols[L.STORAGE_BF16][2],
+                "fp32_same_run": vols[L.STORAGE_FP32][1], "steps": 2 + steps_b,
+                "volume_rel_error_vs_fp32": {"max": float(rel.max()), "mean": float(rel.mean())}}
+
     # ---------------- serving: continuous batching under an HBM budget ----------------
     serving = None
     if args.serve_requests > 0 and rank == 0:
@@ -356,6 +385,7 @@ def gpu_arm(args):
         "clocks": clk.summary(),
         "serving": serving,
         "compare": compare,
+        "bf16_storage": bf16,
         "speedup_vs_plain_gpu": None if not compare else value / compare["plain_gpu"]["value"],
     }
     print(json.dumps(line), flush=True)

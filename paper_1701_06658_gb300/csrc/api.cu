@@ -214,6 +214,14 @@ int grow_arena(lsgg_ctx* c, long long need) {
     return r;
 }
 
+// The state as FP32: X itself, or (BF16 storage) its conversion into Y,
+// which is free between steps.
+cudaError_t state_as_f32(lsgg_ctx* c, const float** out) {
+    if (!c->B.bf16) { *out = c->B.X; return cudaSuccess; }
+    *out = c->B.Y;
+    return launch_state_to_f32(c->B.X, c->B.Y, c->B.cap, c->stream);
+}
+
 // Assign arena offsets / classes for the `cur` boxes (no resize), growing if needed.
 int relayout(lsgg_ctx* c) {
     for (int attempt = 0; attempt < 4; ++attempt) {
@@ -340,7 +348,10 @@ static int validate(const lsgg_config* cfg) {
     if (cfg->init_kind != LSGG_INIT_VORONOI && cfg->init_kind != LSGG_INIT_LAGUERRE) return LSGG_ERR_INVALID_ARG;
     if (cfg->physics < LSGG_PHYSICS_IDEAL || cfg->physics > LSGG_PHYSICS_MAGNETIC) return LSGG_ERR_INVALID_ARG;
     if (cfg->storage != LSGG_STORAGE_FP32 && cfg->storage != LSGG_STORAGE_BF16) return LSGG_ERR_INVALID_ARG;
-    if (cfg->storage == LSGG_STORAGE_BF16) return LSGG_ERR_UNSUPPORTED;
+    // BF16 state storage: the batched path's kernels (pass path, shared /
+    // global-ring box streaming) read and write it; the comparator and the
+    // register-ring kernels keep FP32 only
+    if (cfg->storage == LSGG_STORAGE_BF16 && cfg->exec != LSGG_EXEC_BATCHED) return LSGG_ERR_UNSUPPORTED;
     if (cfg->exec != LSGG_EXEC_BATCHED && cfg->exec != LSGG_EXEC_PLAIN && cfg->exec != LSGG_EXEC_STREAMED)
         return LSGG_ERR_INVALID_ARG;
     if (cfg->physics == LSGG_PHYSICS_READ_SHOCKLEY &&
@@ -481,7 +492,11 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->B.prev = c->d_boxes;
     c->B.cur = c->d_boxes + G;
     c->B.use_passes = cfg_in->exec == LSGG_EXEC_BATCHED ? 1 : 0;
+    c->B.bf16 = cfg_in->storage == LSGG_STORAGE_BF16 ? 1 : 0;
     if (configure_step_kernels(c->B) != cudaSuccess) return bail(CUDA_FAIL());
+    if (c->B.bf16)
+        for (int k = 0; k < kNumClasses; ++k)
+            if (c->B.mode[k] == 0) return bail(LSGG_ERR_UNSUPPORTED);   // register-ring kernels are FP32-only
     if (c->B.use_passes) {
         c->B.plane_item_cap = (long long)G * D.nz;
         c->B.chunk_item_cap = (long long)G * ((64 * 64 + kPassChunk - 1) / kPassChunk);
@@ -582,9 +597,10 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
         if ((r = dalloc(c, &c->B.scratch, (size_t)std::max(total, 32LL))) != LSGG_OK) return bail(r);
     }
     if ((r = relayout(c)) != LSGG_OK) return bail(r);
-    if (launch_sdf(D, G, c->B.cur, c->d_seeds, c->d_weights, d_bits, wpr, c->B.X,
+    if (launch_sdf(D, G, c->B.cur, c->d_seeds, c->d_weights, d_bits, wpr, c->B.bf16 ? c->B.Y : c->B.X,
                    c->B.IDF, &c->B.st->status, c->stream) != cudaSuccess)
         return bail(CUDA_FAIL());
+    if (c->B.bf16 && launch_f32_to_state(c->B.Y, c->B.X, c->B.cap, c->stream) != cudaSuccess) return bail(CUDA_FAIL());
     if (cudaMemcpyAsync(c->B.prev, c->B.cur, (size_t)G * sizeof(Box), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
         return bail(CUDA_FAIL());
     if ((r = read_state(c)) != LSGG_OK) return bail(r);
@@ -894,7 +910,9 @@ int lsgg_get_phi(lsgg_ctx* c, float* out, int64_t cap, int64_t* n_out) {
     if (!out || cap < off[c->G]) return LSGG_ERR_CAPACITY;
     float* d = nullptr;
     if ((r = dalloc(c, &d, (size_t)off[c->G])) != LSGG_OK) return r;
-    cudaError_t e = launch_pack_state(c->dom, c->G, c->B.cur, c->B.prev, c->B.X, c->d_packed_off, d, c->stream);
+    const float* x = nullptr;
+    cudaError_t e = state_as_f32(c, &x);
+    if (e == cudaSuccess) e = launch_pack_state(c->dom, c->G, c->B.cur, c->B.prev, x, c->d_packed_off, d, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)off[c->G] * 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     c->device_bytes -= off[c->G] * 4;
@@ -933,7 +951,9 @@ int lsgg_set_state(lsgg_ctx* c, const int32_t* boxes, const float* phi, const in
     CK(cudaMemcpy(c->d_packed_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(dphi, phi, (size_t)off[c->G] * 4, cudaMemcpyHostToDevice));
     if (idf) CK(cudaMemcpy(didf, idf, (size_t)off[c->G] * 4, cudaMemcpyHostToDevice));
-    CK(launch_unpack_state(c->G, c->B.cur, dphi, didf, c->d_packed_off, c->B.X, c->B.IDF, c->stream));
+    CK(launch_unpack_state(c->G, c->B.cur, dphi, didf, c->d_packed_off, c->B.bf16 ? c->B.Y : c->B.X, c->B.IDF,
+                           c->stream));
+    if (c->B.bf16) CK(launch_f32_to_state(c->B.Y, c->B.X, c->B.cap, c->stream));
     CK(cudaMemcpyAsync(c->B.prev, c->B.cur, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->field_valid = false;
@@ -987,7 +1007,9 @@ int lsgg_grain_volumes(lsgg_ctx* c, double* out, int64_t cap, int64_t* n_out) {
     if (!out || cap < c->G) return LSGG_ERR_CAPACITY;
     int r = lsgg_sync(c, -1);
     if (r != LSGG_OK) return r;
-    CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, c->B.X, c->d_vol, c->stream));
+    const float* x = nullptr;
+    CK(state_as_f32(c, &x));
+    CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, x, c->d_vol, c->stream));
     CK(cudaMemcpyAsync(out, c->d_vol, (size_t)c->G * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LSGG_OK;
@@ -1001,7 +1023,9 @@ int lsgg_voxel_owner(lsgg_ctx* c, int32_t* out, int64_t n_cells) {
     if (r != LSGG_OK) return r;
     int* d = nullptr;
     if ((r = dalloc(c, &d, (size_t)n)) != LSGG_OK) return r;
-    cudaError_t e = launch_owner(c->dom, c->G, c->B.cur, c->B.prev, c->B.X, c->B.T, d, c->stream);
+    const float* x = nullptr;
+    cudaError_t e = state_as_f32(c, &x);
+    if (e == cudaSuccess) e = launch_owner(c->dom, c->G, c->B.cur, c->B.prev, x, c->B.T, d, c->stream);
     c->field_valid = false;        // the owner map reused the field's memory
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -3,9 +3,12 @@
 // Data layout in HBM (one context):
 //   boxes      Box[G] x 2 tables: `prev` = layout of the state arena X,
 //              `cur` = layout the next step writes (bbox of {phi > 0} + halo).
-//   X, Y       FP32 (or BF16) box arenas, `cap` elements each.  Box b's plane z
-//              starts at off + z * ps with ps = round_up(nx * ny, 4) so that a
-//              plane is one 16-byte aligned bulk copy; off is a multiple of 32.
+//   X          state arena: phi between steps, `cap` elements of FP32, or of
+//              BF16 with LSGG_STORAGE_BF16 (the allocation keeps the FP32
+//              size).  Box b's plane z starts at off + z * ps with ps =
+//              round_up(nx * ny, 8), so that a plane is one 16-byte aligned bulk
+//              copy in either type; off is a multiple of 32.
+//   Y          FP32 box arena (same layout): phi_p and the passes' results.
 //   T          neighbour-max field, 2 x u64 per domain cell: key1 = the largest
 //              (phi_p, -id) over the boxes covering the cell, key2 = the second.
 //              Box-streaming kernels build it with 64-bit atomicMax; the pass
@@ -21,6 +24,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace lsgg {
@@ -106,7 +110,7 @@ struct StepState {                  // device-resident control block
     int slab_base[kTiers];
 };
 
-__host__ __device__ inline int plane_stride(int nx, int ny) { return (nx * ny + 3) & ~3; }
+__host__ __device__ inline int plane_stride(int nx, int ny) { return (nx * ny + 7) & ~7; }
 __host__ __device__ inline long long box_elems(const Box& b) {
     if (b.nx <= 0) return 0;
     long long s = (long long)plane_stride(b.nx, b.ny) * b.nz;
@@ -137,6 +141,7 @@ __device__ __forceinline__ float key_val(unsigned long long k, float eps) {
 struct StepBuffers {
     Domain dom;
     int n_boxes;
+    int bf16;                       // X holds BF16 (LSGG_STORAGE_BF16); arithmetic stays FP32
     Box* prev;
     Box* cur;
     Bounds* bounds;
@@ -180,6 +185,17 @@ struct StepBuffers {
     int field_grid, bin_grid;
 };
 
+// Element i of the state arena X as FP32, and its store (round to nearest
+// even when the arena holds BF16).
+__device__ __forceinline__ float ld_state(const StepBuffers& B, long long i) {
+    return B.bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(B.X)[i]) : B.X[i];
+}
+__device__ __forceinline__ void st_state(const StepBuffers& B, long long i, float v) {
+    if (B.bf16) reinterpret_cast<__nv_bfloat16*>(B.X)[i] = __float2bfloat16_rn(v);
+    else B.X[i] = v;
+}
+__host__ __device__ inline int state_bytes(const StepBuffers& B) { return B.bf16 ? 2 : 4; }
+
 // Side streams on which the size-class kernels of one phase run concurrently
 // (forked from and joined back into the step's stream by events).
 struct StepStreams {
@@ -216,6 +232,9 @@ cudaError_t configure_step_kernels(StepBuffers& B);
 // Let `fn` take up to the device's opt-in shared memory per CTA (process-wide).
 cudaError_t allow_max_dynamic_smem(const void* fn);
 cudaError_t configure_passes(StepBuffers& B);
+// Whole-arena conversions of the state between BF16 and FP32 (n elements).
+cudaError_t launch_state_to_f32(const void* bf16_in, float* out, long long n, cudaStream_t s);
+cudaError_t launch_f32_to_state(const float* in, void* bf16_out, long long n, cudaStream_t s);
 cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps& taps, const PhysicsDev& phys,
                           const DebugOut& dbg, cudaStream_t s, cudaEvent_t* pass_ev);
 cudaError_t launch_bin(const StepBuffers& B, cudaStream_t s);

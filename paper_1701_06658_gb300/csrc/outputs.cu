@@ -9,6 +9,8 @@
 //   k_remap     the state phi (stored in the `prev` layout) resampled on the
 //               current boxes with -eps where the old box did not reach: the
 //               grain functions as they enter the next step (Sec. 3.1 box update).
+#include <algorithm>
+
 #include "lsgg_internal.cuh"
 
 namespace lsgg {
@@ -179,6 +181,29 @@ cudaError_t launch_pack_cur(int G, const Box* cur, const void* arena, const long
 cudaError_t launch_unpack_state(int G, const Box* cur, const float* packed, const int* packed_idf,
                                 const long long* packed_off, float* X, int* IDF, cudaStream_t s) {
     k_unpack_state<<<G, 256, 0, s>>>(cur, packed, packed_idf, packed_off, X, IDF);
+    return cudaGetLastError();
+}
+
+// Whole-arena conversions of the BF16 state (LSGG_STORAGE_BF16) to and from
+// FP32: the outputs and the test hooks read and write FP32 through them.
+__global__ void __launch_bounds__(256) k_state_to_f32(const __nv_bfloat16* __restrict__ in, float* __restrict__ out,
+                                                      long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __bfloat162float(in[i]);
+}
+__global__ void __launch_bounds__(256) k_f32_to_state(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
+                                                      long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(in[i]);
+}
+cudaError_t launch_state_to_f32(const void* bf16_in, float* out, long long n, cudaStream_t s) {
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    k_state_to_f32<<<(int)std::max<long long>(blocks, 1), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(bf16_in), out, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_f32_to_state(const float* in, void* bf16_out, long long n, cudaStream_t s) {
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    k_f32_to_state<<<(int)std::max<long long>(blocks, 1), 256, 0, s>>>(in, static_cast<__nv_bfloat16*>(bf16_out), n);
     return cudaGetLastError();
 }
 

@@ -90,8 +90,9 @@ __device__ __forceinline__ void conv_source(const StepBuffers& B, int2 it, const
     const Box nb = B.cur[it.x], ob = B.prev[it.x];
     const int ozl = pmod(nb.oz + it.y - ob.oz, B.dom.nz);
     const int ps = plane_stride(ob.nx, ob.ny);
-    *src = B.X + ob.off + (long long)(ozl < ob.nz ? ozl : 0) * ps;
-    *bytes = ozl < ob.nz ? (uint32_t)ps * 4u : 0u;
+    const long long e = ob.off + (long long)(ozl < ob.nz ? ozl : 0) * ps;
+    *src = reinterpret_cast<const float*>(reinterpret_cast<const char*>(B.X) + e * state_bytes(B));
+    *bytes = ozl < ob.nz ? (uint32_t)(ps * state_bytes(B)) : 0u;
 }
 
 template <int R, int SIDE, int NT>
@@ -178,14 +179,17 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
             return;
         }
         pending = false;
-        // stage: raw (old layout) -> P (new layout), warp per padded row
+        // stage: raw (old layout, FP32 or BF16) -> P (new layout), warp per padded row
         for (int yp = warp; yp < PYa; yp += NT / 32) {
             const int my = mapy[yp];
-            const float* rrow = raw + (my < 0 ? 0 : my) * ob.nx;
+            const int r0 = (my < 0 ? 0 : my) * ob.nx;
             float* prow = P + yp * LY::PX;
             for (int xp = lane; xp < PXa; xp += 32) {
                 const int mx = mapx[xp];
-                prow[xp] = (have && my >= 0 && mx >= 0) ? rrow[mx] : -D.eps;
+                float v = -D.eps;
+                if (have && my >= 0 && mx >= 0)
+                    v = B.bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(raw)[r0 + mx]) : raw[r0 + mx];
+                prow[xp] = v;
             }
         }
         __syncthreads();                                    // raw is free: fetch the next item's plane
@@ -363,7 +367,7 @@ p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
                     int j = -1;
                     if (in_old_xy && ozl < ob.nz) {
                         const long long o = ob.off + (long long)ozl * ps_old + (long long)oyl * ob.nx + oxl;
-                        phi0 = B.X[o];
+                        phi0 = ld_state(B, o);
                         j = B.IDF[o];
                     }
                     val = pair_blend(phys, tab, b, j, phi0, acc);
@@ -805,8 +809,8 @@ p_redist_xy(StepBuffers B, int tier) {
 // magnitudes are scanned forward and backward and the signs put back.
 // Returns the mask of positive cells (bit z).
 template <int NZ>
-__device__ __forceinline__ unsigned long long redist_column(const float* hc, float* xc, float* dc, int nz, int ps,
-                                                            float eps) {
+__device__ __forceinline__ unsigned long long redist_column(const StepBuffers& B, const float* hc, long long xo,
+                                                            float* dc, int nz, int ps, float eps) {
     float r[NZ];
     unsigned long long pm = 0;
     // unconditional loads (cells past the column re-read its last cell), so
@@ -823,7 +827,7 @@ __device__ __forceinline__ unsigned long long redist_column(const float* hc, flo
     for (int z = 0; z < NZ; ++z)
         if (z < nz) {
             const float out = (pm >> z) & 1ull ? r[z] : -r[z];
-            xc[(long long)z * ps] = out;
+            st_state(B, xo + (long long)z * ps, out);
             if (dc) dc[(long long)z * ps] = out;
         }
     return pm;
@@ -849,13 +853,13 @@ p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
             const int y = c / nx, x = c - y * nx;
             const int ps = plane_stride(nx, ny);
             const float* hc = B.Y + nb.off + c;
-            float* xc = B.X + nb.off + c;
+            const long long xo = nb.off + c;
             if (!fz && nz <= 64) {                         // uniform across the CTA (one box per item)
                 float* dc = dbg.phin ? dbg.phin + nb.off + c : nullptr;
-                const unsigned long long pm = nz <= 16   ? redist_column<16>(hc, xc, dc, nz, ps, eps)
-                                              : nz <= 32 ? redist_column<32>(hc, xc, dc, nz, ps, eps)
-                                              : nz <= 48 ? redist_column<48>(hc, xc, dc, nz, ps, eps)
-                                                         : redist_column<64>(hc, xc, dc, nz, ps, eps);
+                const unsigned long long pm = nz <= 16   ? redist_column<16>(B, hc, xo, dc, nz, ps, eps)
+                                              : nz <= 32 ? redist_column<32>(B, hc, xo, dc, nz, ps, eps)
+                                              : nz <= 48 ? redist_column<48>(B, hc, xo, dc, nz, ps, eps)
+                                                         : redist_column<64>(B, hc, xo, dc, nz, ps, eps);
                 if (pm) {
                     lo[0] = hi[0] = x;
                     lo[1] = hi[1] = y;
@@ -909,7 +913,7 @@ p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
                         }
                         best = fminf(best, eps);
                         const float out = sg ? best : -best;
-                        xc[(long long)zo * ps] = out;
+                        st_state(B, xo + (long long)zo * ps, out);
                         if (dbg.phin) dbg.phin[nb.off + (long long)zo * ps + c] = out;
                         if (out > 0.0f) {
                             lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);

@@ -99,12 +99,12 @@ __device__ void predict_box(const StepBuffers& B, const Taps& taps, const Physic
                 zold = ol < ob.nz ? ol : -1;
             }
         }
-        const float* src = B.X + ob.off + (long long)(zold < 0 ? 0 : zold) * ps_old;
+        const long long src = ob.off + (long long)(zold < 0 ? 0 : zold) * ps_old;
         for (int idx = threadIdx.x; idx < px * py; idx += blockDim.x) {
             int yp = idx / px, xp = idx - yp * px;
             int mx = sm.mapx[xp], my = sm.mapy[yp];
             float v = -eps;
-            if (zold >= 0 && mx >= 0 && my >= 0) v = src[my * ob.nx + mx];
+            if (zold >= 0 && mx >= 0 && my >= 0) v = ld_state(B, src + my * ob.nx + mx);
             P[idx] = v;
         }
         __syncthreads();
@@ -156,7 +156,7 @@ __device__ void predict_box(const StepBuffers& B, const Taps& taps, const Physic
                 int j = -1;
                 if (zo_old < ob.nz && mx >= 0 && my >= 0) {
                     long long o = ob.off + (long long)zo_old * ps_old + my * ob.nx + mx;
-                    phi0 = B.X[o];
+                    phi0 = ld_state(B, o);
                     j = B.IDF[o];
                 }
                 v = pair_blend(phys, tab, b, j, phi0, c);
@@ -315,7 +315,7 @@ __device__ void correct_box(const StepBuffers& B, const PhysicsDev& phys, const 
         const int zo = is3d ? zb - kRedistReach : zb;
         if (zo >= 0 && zo < nz && (is3d || zin == 0)) {
             const int ztop = is3d ? (fz ? zb : min(zb, nz - 1)) : zo;
-            float* dst = B.X + nb.off + (long long)zo * ps;
+            const long long dst = nb.off + (long long)zo * ps;
             for (int i = threadIdx.x; i < A; i += blockDim.x) {
                 float v = F[(size_t)(is3d ? pmod(zo, 7) : 0) * A + i];
                 const bool s = sgn_pos(v);
@@ -331,7 +331,7 @@ __device__ void correct_box(const StepBuffers& B, const PhysicsDev& phys, const 
                 }
                 best = fminf(best, eps);
                 float out = s ? best : -best;
-                dst[i] = out;
+                st_state(B, dst + i, out);
                 if (dbg.phin) dbg.phin[nb.off + (long long)zo * ps + i] = out;
                 if (out > 0.0f) {
                     int y = i / nx, x = i - y * nx;

@@ -85,3 +85,15 @@ def test_no_cpu_fallback_without_a_device():
     with pytest.raises(L.LsggError) as e:
         L.Microstructure(16, 16, 16, 4)
     assert e.value.code == L.ERR_CUDA
+
+
+@pytest.mark.parametrize("exec_mode", ["EXEC_PLAIN", "EXEC_STREAMED"])
+def test_bf16_storage_only_on_the_batched_path(exec_mode):
+    """BF16 state storage is refused before any device work on the execution
+    modes whose kernels keep FP32 only."""
+    L = _lib()
+    cfg = L.config_default()
+    cfg.storage = L.STORAGE_BF16
+    cfg.exec = getattr(L, exec_mode)
+    ctx = ctypes.c_void_p()
+    assert L.lib().lsgg_create_microstructure(ctypes.byref(cfg), None, ctypes.byref(ctx)) == L.ERR_UNSUPPORTED

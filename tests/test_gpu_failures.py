@@ -43,7 +43,7 @@ def _need(boxes):
     n = 0
     for b in boxes:
         if b[0]:
-            ps = (int(b[4]) * int(b[5]) + 3) & ~3
+            ps = (int(b[4]) * int(b[5]) + 7) & ~7
             n += (ps * int(b[6]) + 31) & ~31
     return n
 
