@@ -37,6 +37,13 @@ WORKLOADS = {
     "256": {"n": 256, "grains": 5000, "seed": 2, "dt": 1.0},
     # small case for ncu captures: same grain density, state still larger than L2
     "160": {"n": 160, "grains": 1221, "seed": 2, "dt": 1.0},
+    # non-ideal growth: Laguerre tessellation with lognormal radii (sigma 0.5) and
+    # 1 % of grains with 5x volume, random cubic orientations, Read-Shockley
+    # boundary energy (theta_max 15 deg) and mobility 0.1 below 15 deg
+    "512rs": {"n": 512, "grains": 40000, "seed": 3, "dt": 1.0, "physics": "read_shockley", "init": "laguerre"},
+    # magnetically driven growth: random c-axes, field (0, cos 32, sin 32), bulk
+    # energy B^2 dchi cos^2 / (2 mu0) in grid units (4.07e-3 at cos^2 = 1)
+    "384mag": {"n": 384, "grains": 10000, "seed": 4, "dt": 1.0, "physics": "magnetic", "energy_scale": 4.07e-3},
 }
 WORKLOAD = dict(WORKLOADS["256"])
 SAMPLE = {"n": 64, "grains": 78, "seed": 2}     # same density: 64^3 / 78 = 3361 cells per grain
@@ -175,11 +182,30 @@ def reference_arm(args):
     return 0
 
 
+def workload_kwargs(L):
+    """Microstructure keyword arguments of the workload's physics and tessellation."""
+    kw = {}
+    ph = WORKLOAD.get("physics", "ideal")
+    if ph == "read_shockley":
+        kw["physics"] = L.PHYSICS_READ_SHOCKLEY
+    elif ph == "magnetic":
+        kw["physics"] = L.PHYSICS_MAGNETIC
+        kw["energy_scale"] = WORKLOAD["energy_scale"]
+    if WORKLOAD.get("init") == "laguerre":
+        kw["init_kind"] = L.INIT_LAGUERRE
+    return kw
+
+
 def workload_config():
-    return {"workload": f"{WORKLOAD['n']}^3 periodic, {WORKLOAD['grains']} Voronoi grains (seed {WORKLOAD['seed']}), "
-                        f"ideal growth, dt={WORKLOAD['dt']}, box halo 5, eps 7, FP32",
+    ph = {"ideal": "ideal growth", "read_shockley": "Read-Shockley energy and step mobility, random cubic orientations",
+          "magnetic": "magnetic driving force, random c-axes"}[WORKLOAD.get("physics", "ideal")]
+    tess = ("Laguerre grains, lognormal radii sigma 0.5, 1 % at 5x volume" if WORKLOAD.get("init") == "laguerre"
+            else "Voronoi grains")
+    return {"workload": f"{WORKLOAD['n']}^3 periodic, {WORKLOAD['grains']} {tess} (seed {WORKLOAD['seed']}), "
+                        f"{ph}, dt={WORKLOAD['dt']}, box halo 5, eps 7, FP32",
             "domain": [WORKLOAD["n"]] * 3, "grains": WORKLOAD["grains"], "dt": WORKLOAD["dt"],
-            "l2": "inputs larger than L2: box arena ~0.8 GB per buffer and 268 MB field vs 129 MB L2"}
+            "l2": f"inputs larger than L2: box arenas of ~{WORKLOAD['n'] ** 3 * 8.5 * 4 / 1e9:.1f} GB each and a "
+                  f"{16 * WORKLOAD['n'] ** 3 / 1e6:.0f} MB field vs 129 MB L2"}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -206,7 +232,7 @@ def gpu_arm(args):
 
     # ---------------- device-resident timing ----------------
     exec_mode = {"batched": L.EXEC_BATCHED, "streamed": L.EXEC_STREAMED}[args.exec]
-    ms = L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=exec_mode)
+    ms = L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=exec_mode, **workload_kwargs(L))
     stream = torch.cuda.ExternalStream(ms.stream)
     ms.step(args.warmup, dt)
     ms.sync()
@@ -247,7 +273,7 @@ def gpu_arm(args):
     if not args.no_e2e:
         t0 = time.perf_counter()
         e2e = L.Microstructure(n, n, n, g, seeds=seeds, device=local,    # H2D of the seeds, init
-                               exec_mode=exec_mode)
+                               exec_mode=exec_mode, **workload_kwargs(L))
         for _ in range(args.steps):
             e2e.step(1, dt)
             vol = e2e.grain_volumes()                                      # D2H of the step's result
@@ -266,7 +292,7 @@ def gpu_arm(args):
     if not args.no_compare and rank == 0:
         compare = {}
         for name, mode, steps in (("plain_gpu", L.EXEC_PLAIN, 3), ("box_streaming_gpu", L.EXEC_STREAMED, 10)):
-            with L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=mode) as cm:
+            with L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=mode, **workload_kwargs(L)) as cm:
                 cm.step(2, dt)
                 cm.sync()
                 c0 = cm.stats().cell_updates
@@ -287,7 +313,8 @@ def gpu_arm(args):
         steps_b = 10
         vols = {}
         for st in (L.STORAGE_FP32, L.STORAGE_BF16):
-            with L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=exec_mode, storage=st) as bm:
+            with L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=exec_mode, storage=st,
+                                  **workload_kwargs(L)) as bm:
                 bm.step(2, dt)
                 bm.sync()
                 c0 = bm.stats().cell_updates
@@ -446,7 +473,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving measurement (0: skip; 256: the full serving workload)")
     ap.add_argument("--workload", default="256", choices=sorted(WORKLOADS),
-                    help="256: the benchmark workload; 160: a small case of the same density for profilers")
+                    help="256: the benchmark workload; 160: a small case of the same density for profilers; "
+                         "512rs, 384mag: the non-ideal and magnetic workloads")
     args = ap.parse_args()
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])

@@ -189,6 +189,8 @@ int replace_z(lsgg_ctx* c, long long cap) {
     return LSGG_OK;
 }
 
+int ensure_chunk_cap(lsgg_ctx* c);
+
 // Grow the arenas to hold `need` elements, keeping the state (prev layout).
 int grow_arena(lsgg_ctx* c, long long need) {
     long long cap = std::max<long long>(need + need / 4, c->B.cap * 2);
@@ -210,8 +212,26 @@ int grow_arena(lsgg_ctx* c, long long need) {
     c->B.IDF = I2;
     r = replace_z(c, cap);
     c->B.cap = cap;
+    if (r == LSGG_OK) r = ensure_chunk_cap(c);
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     return r;
+}
+
+// Column-chunk work items of the pass path: a box of plane area A has
+// ceil(A / kPassChunk) <= A / kPassChunk + 1 chunks and the plane areas sum to
+// at most the box cells, which the arena capacity bounds.  Reallocated (not
+// copied: the next box update rebuilds them) when the arena grows.
+int ensure_chunk_cap(lsgg_ctx* c) {
+    if (!c->B.use_passes) return LSGG_OK;
+    const long long need = (long long)c->G + c->B.cap / kPassChunk + 64;
+    if (c->B.chunk_items && c->B.chunk_item_cap >= need) return LSGG_OK;
+    if (c->B.chunk_items) {
+        c->device_bytes -= c->B.chunk_item_cap * (long long)sizeof(int2);
+        dfree(c, c->B.chunk_items);
+        c->B.chunk_items = nullptr;
+    }
+    c->B.chunk_item_cap = need;
+    return dalloc(c, &c->B.chunk_items, (size_t)need);
 }
 
 // The state as FP32: X itself, or (BF16 storage) its conversion into Y,
@@ -499,9 +519,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
             if (c->B.mode[k] == 0) return bail(LSGG_ERR_UNSUPPORTED);   // register-ring kernels are FP32-only
     if (c->B.use_passes) {
         c->B.plane_item_cap = (long long)G * D.nz;
-        c->B.chunk_item_cap = (long long)G * ((64 * 64 + kPassChunk - 1) / kPassChunk);
         if ((r = dalloc(c, &c->B.plane_items, (size_t)c->B.plane_item_cap)) != LSGG_OK) return bail(r);
-        if ((r = dalloc(c, &c->B.chunk_items, (size_t)c->B.chunk_item_cap)) != LSGG_OK) return bail(r);
         c->B.slab_item_cap = (long long)G * ((D.nz + kSlab - 1) / kSlab);
         if ((r = dalloc(c, &c->B.slab_items, (size_t)c->B.slab_item_cap)) != LSGG_OK) return bail(r);
         if ((r = dalloc(c, &c->B.tile_cnt, (size_t)c->B.n_tiles)) != LSGG_OK) return bail(r);
@@ -586,6 +604,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->separate_z = c->B.use_passes && cfg_in->physics != LSGG_PHYSICS_IDEAL;
     if (c->separate_z && (r = dalloc(c, &c->B.Z, (size_t)cap)) != LSGG_OK) return bail(r);
     if (c->B.use_passes && !c->separate_z) c->B.Z = reinterpret_cast<float*>(c->B.IDF);
+    if ((r = ensure_chunk_cap(c)) != LSGG_OK) return bail(r);
     c->B.scratch_per_cta = large_class_scratch_floats(D);
     {
         long long total = 0;
@@ -850,6 +869,7 @@ int lsgg_debug_set_capacity(lsgg_ctx* c, int64_t capacity) {
     c->B.IDF = I2;
     if ((r = replace_z(c, capacity)) != LSGG_OK) return r;
     c->B.cap = capacity;
+    if ((r = ensure_chunk_cap(c)) != LSGG_OK) return r;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     return relayout(c);
 }

@@ -89,11 +89,11 @@ struct PairTable {
     int n;
 };
 
-// Eq. (10): phi + w (c - phi) + M (e_j - e_i) dt; w = 1, no bulk term when j < 0.
-__device__ __forceinline__ float pair_blend(const PhysicsDev& phys, const PairTable& tab, int gid, int j, float phi,
-                                            float c) {
-    if (j < 0) return c;
-    float w = 1.0f, m = 1.0f;
+// Pair weight w and mobility M of grain gid against neighbour j (j >= 0).
+__device__ __forceinline__ void pair_weights(const PhysicsDev& phys, const PairTable& tab, int gid, int j, float& w,
+                                             float& m) {
+    w = 1.0f;
+    m = 1.0f;
     if (phys.kind == LSGG_PHYSICS_READ_SHOCKLEY) {
         int lo = 0, hi = tab.n - 1;
         bool hit = false;
@@ -105,9 +105,37 @@ __device__ __forceinline__ float pair_blend(const PhysicsDev& phys, const PairTa
         }
         if (!hit) rs_pair(phys, gid, j, w, m);
     }
+}
+
+// Eq. (10): phi + w (c - phi) + M (e_j - e_i) dt; w = 1, no bulk term when j < 0.
+__device__ __forceinline__ float pair_blend(const PhysicsDev& phys, const PairTable& tab, int gid, int j, float phi,
+                                            float c) {
+    if (j < 0) return c;
+    float w, m;
+    pair_weights(phys, tab, gid, j, w, m);
     float bulk = 0.0f;
     if (phys.energy) bulk = m * (phys.energy[j] - phys.energy[gid]) * phys.dt;
     return phi + w * (c - phi) + bulk;
+}
+
+// pair_blend with the last neighbour's weights and energy kept: along a
+// column the neighbour seldom changes, so the table search and the energy
+// load run once per run of equal j.  Same arithmetic as pair_blend.
+struct PairCache {
+    int j = -1;
+    float w = 1.0f, m = 1.0f, ej = 0.0f;
+};
+__device__ __forceinline__ float pair_blend_cached(const PhysicsDev& phys, const PairTable& tab, int gid, int j,
+                                                   float phi, float c, float ei, PairCache& pc) {
+    if (j < 0) return c;
+    if (j != pc.j) {
+        pair_weights(phys, tab, gid, j, pc.w, pc.m);
+        pc.ej = phys.energy ? phys.energy[j] : 0.0f;
+        pc.j = j;
+    }
+    float bulk = 0.0f;
+    if (phys.energy) bulk = pc.m * (pc.ej - ei) * phys.dt;
+    return phi + pc.w * (c - phi) + bulk;
 }
 
 // Load box `gid`'s neighbour table into shared memory and evaluate its pair

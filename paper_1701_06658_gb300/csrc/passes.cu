@@ -84,6 +84,25 @@ struct ConvXYLayout {
     static constexpr size_t bytes = maps + sizeof(int) * 2 * PYR;
 };
 
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// raw plane (old layout) -> padded grid P (new layout), warp per padded row.
+template <int NT, int PX, class T>
+__device__ __forceinline__ void stage_plane(const T* raw, float* P, const int* mapx, const int* mapy, int PXa, int PYa,
+                                            int onx, bool have, float fill, int warp, int lane) {
+    for (int yp = warp; yp < PYa; yp += NT / 32) {
+        const int my = mapy[yp];
+        const T* rrow = raw + (my < 0 ? 0 : my) * onx;
+        const bool row_in = have && my >= 0;
+        float* prow = P + yp * PX;
+        for (int xp = lane; xp < PXa; xp += 32) {
+            const int mx = mapx[xp];
+            prow[xp] = row_in && mx >= 0 ? to_f32(rrow[mx]) : fill;
+        }
+    }
+}
+
 // The plane of item `item` in the box's previous layout: source address and
 // bytes (0 when the new plane lies outside the old box).
 __device__ __forceinline__ void conv_source(const StepBuffers& B, int2 it, const float** src, uint32_t* bytes) {
@@ -180,18 +199,9 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         }
         pending = false;
         // stage: raw (old layout, FP32 or BF16) -> P (new layout), warp per padded row
-        for (int yp = warp; yp < PYa; yp += NT / 32) {
-            const int my = mapy[yp];
-            const int r0 = (my < 0 ? 0 : my) * ob.nx;
-            float* prow = P + yp * LY::PX;
-            for (int xp = lane; xp < PXa; xp += 32) {
-                const int mx = mapx[xp];
-                float v = -D.eps;
-                if (have && my >= 0 && mx >= 0)
-                    v = B.bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(raw)[r0 + mx]) : raw[r0 + mx];
-                prow[xp] = v;
-            }
-        }
+        if (B.bf16) stage_plane<NT, LY::PX>(reinterpret_cast<const __nv_bfloat16*>(raw), P, mapx, mapy, PXa, PYa,
+                                            ob.nx, have, -D.eps, warp, lane);
+        else stage_plane<NT, LY::PX>(raw, P, mapx, mapy, PXa, PYa, ob.nx, have, -D.eps, warp, lane);
         __syncthreads();                                    // raw is free: fetch the next item's plane
         if (item + (int)gridDim.x < n_items) {
             const float* src;
@@ -334,6 +344,8 @@ p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
             continue;
         }
         const int ps_old = plane_stride(ob.nx, ob.ny);
+        PairCache pcache;
+        const float ei = PHYS && phys.energy ? phys.energy[b] : 0.0f;
         float win[W];                                      // planes zo-R .. zo+R
 #pragma unroll
         for (int k = 0; k < W; ++k) win[k] = cconst;
@@ -349,6 +361,23 @@ p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
                     else if (zin >= 0 && zin < nz) v[u] = zc[(long long)zin * ps];
                 }
             }
+            // the previous step's phi and ID-field of this batch's output planes
+            float phi0[PHYS ? kZB : 1];
+            int jn[PHYS ? kZB : 1];
+            if (PHYS) {
+#pragma unroll
+                for (int u = 0; u < kZB; ++u) {
+                    const int zo = base + u - 2 * R;
+                    const int ozl = wrap_near(nb.oz + zo - ob.oz, D.nz);
+                    phi0[u] = -D.eps;
+                    jn[u] = -1;
+                    if (zo >= 0 && zo < nz && in_old_xy && ozl < ob.nz) {
+                        const long long o = ob.off + (long long)ozl * ps_old + (long long)oyl * ob.nx + oxl;
+                        phi0[u] = ld_state(B, o);
+                        jn[u] = B.IDF[o];
+                    }
+                }
+            }
 #pragma unroll
             for (int u = 0; u < kZB; ++u) {
                 if (base + u >= n_in) break;
@@ -361,17 +390,7 @@ p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
 #pragma unroll
                 for (int k = 0; k < W; ++k) acc = fmaf(g[k], win[k], acc);
                 float val = acc;
-                if (PHYS) {
-                    const int ozl = wrap_near(nb.oz + zo - ob.oz, D.nz);
-                    float phi0 = -D.eps;
-                    int j = -1;
-                    if (in_old_xy && ozl < ob.nz) {
-                        const long long o = ob.off + (long long)ozl * ps_old + (long long)oyl * ob.nx + oxl;
-                        phi0 = ld_state(B, o);
-                        j = B.IDF[o];
-                    }
-                    val = pair_blend(phys, tab, b, j, phi0, acc);
-                }
+                if (PHYS) val = pair_blend_cached(phys, tab, b, jn[u], phi0[u], acc, ei, pcache);
                 val = fminf(fmaxf(val, -D.eps), D.eps);
                 yc[(long long)zo * ps] = val;
             }
@@ -941,19 +960,175 @@ p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
     }
 }
 // ---------------------------------------------------------------------------
+// general-size tier: plane passes through global memory
+// ---------------------------------------------------------------------------
+// Boxes with an x or y side above 64 (the lognormal tail of a power-diagram
+// tessellation, grains grown large) exceed every shared-memory plane grid.
+// Their plane passes keep one CTA per (box, plane) item and work through
+// global memory (L1 / L2) instead: the x pass writes the plane's x-convolved
+// rows into its own region of Y, the y pass reads them back after a barrier;
+// the re-initialisation classifies into Y, scans rows (a thread per row) and
+// columns (a thread per column) in place and puts the signs back.  Same
+// arithmetic and FMA order as p_conv_xy; scans as scan_line_wrap without the
+// wrap.  The column passes are the shared ones.
+
+// Forward and backward min-plus scan of n magnitudes (stride st), in place.
+__device__ __forceinline__ void scan_line_serial(float* L, int n, int st) {
+    float f = L[0];
+    for (int j = 1; j < n; ++j) {
+        f = fminf(L[(long long)j * st], f + 1.0f);
+        L[(long long)j * st] = f;
+    }
+    for (int j = n - 2; j >= 0; --j) {
+        f = fminf(L[(long long)j * st], f + 1.0f);
+        L[(long long)j * st] = f;
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256)
+p_conv_xy_big(StepBuffers B, Taps taps, int tier) {
+    constexpr int W = 2 * R + 1;
+    __shared__ int s_flag;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) s_flag = halted(B);
+    __syncthreads();
+    if (s_flag) return;
+    const Domain D = B.dom;
+    float g[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) g[k] = taps.g[k];
+    float aconst = 0.0f;                              // x convolution of a row of -eps
+#pragma unroll
+    for (int k = 0; k < W; ++k) aconst = fmaf(g[k], -D.eps, aconst);
+    const int n_items = B.st->n_planes[tier];
+    const int2* items = B.plane_items + B.st->plane_base[tier];
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int2 it = items[item];
+        const int b = it.x, z = it.y;
+        const Box nb = B.cur[b], ob = B.prev[b];
+        const int nx = nb.nx, ny = nb.ny;
+        const bool fx = nx == D.nx, fy = ny == D.ny;
+        const int ps = plane_stride(nx, ny);
+        const int ozl = wrap_near(nb.oz + z - ob.oz, D.nz);
+        const bool zin = ozl < ob.nz;
+        const long long obase = ob.off + (long long)(zin ? ozl : 0) * plane_stride(ob.nx, ob.ny);
+        float* rows = B.Y + nb.off + (long long)z * ps;  // x-convolved rows of this plane (scratch)
+        for (int y = warp; y < ny; y += 8) {               // x pass: warp per row, lanes along x
+            const int oy = wrap_near(nb.oy + y - ob.oy, D.ny);
+            const bool rin = zin && oy < ob.ny;
+            const long long rbase = obase + (long long)oy * ob.nx;
+            for (int x = lane; x < nx; x += 32) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    int xl = x + k - R;
+                    float v = -D.eps;
+                    if (fx || (xl >= 0 && xl < nx)) {
+                        if (fx) xl = wrap_near(xl, nx);
+                        const int ox = wrap_near(nb.ox + xl - ob.ox, D.nx);
+                        if (rin && ox < ob.nx) v = ld_state(B, rbase + ox);
+                    }
+                    acc = fmaf(g[k], v, acc);
+                }
+                rows[(long long)y * nx + x] = acc;
+            }
+        }
+        __syncthreads();
+        float* dst = B.Z + nb.off + (long long)z * ps;
+        for (int y = warp; y < ny; y += 8) {               // y pass
+            for (int x = lane; x < nx; x += 32) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    int yl = y + k - R;
+                    float v = aconst;
+                    if (fy || (yl >= 0 && yl < ny)) {
+                        if (fy) yl = wrap_near(yl, ny);
+                        v = rows[(long long)yl * nx + x];
+                    }
+                    acc = fmaf(g[k], v, acc);
+                }
+                dst[(long long)y * nx + x] = acc;
+            }
+        }
+        __syncthreads();                                    // rows are read before the next item
+    }
+}
+
+__global__ void __launch_bounds__(256)
+p_redist_xy_big(StepBuffers B, int tier) {
+    __shared__ int s_flag;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) s_flag = halted(B);
+    __syncthreads();
+    if (s_flag) return;
+    const Domain D = B.dom;
+    const float eps = D.eps;
+    const int n_items = B.st->n_planes[tier];
+    const int2* items = B.plane_items + B.st->plane_base[tier];
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int2 it = items[item];
+        const int b = it.x, z = it.y;
+        const Box nb = B.cur[b];
+        const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
+        const bool fx = nx == D.nx, fy = ny == D.ny, fz = nz == D.nz;
+        const int ps = plane_stride(nx, ny);
+        const int n = nx * ny;
+        const float* c = B.Z + nb.off + (long long)z * ps;
+        const int zm = fz ? pmod(z - 1, nz) : z - 1, zp = fz ? pmod(z + 1, nz) : z + 1;
+        const float* cm = zm >= 0 ? B.Z + nb.off + (long long)zm * ps : nullptr;
+        const float* cp = zp < nz ? B.Z + nb.off + (long long)zp * ps : nullptr;
+        float* G = B.Y + nb.off + (long long)z * ps;        // magnitudes, then the result
+        for (int y = warp; y < ny; y += 8) {               // classification: warp per row
+            for (int x = lane; x < nx; x += 32) {
+                const long long i = (long long)y * nx + x;
+                const float v = __ldg(c + i);
+                const bool pos = v > 0.0f;
+                const float xl = x > 0 ? __ldg(c + i - 1) : (fx ? __ldg(c + i + nx - 1) : -eps);
+                const float xr = x < nx - 1 ? __ldg(c + i + 1) : (fx ? __ldg(c + i - nx + 1) : -eps);
+                const float yl = y > 0 ? __ldg(c + i - nx) : (fy ? __ldg(c + i + n - nx) : -eps);
+                const float yr = y < ny - 1 ? __ldg(c + i + nx) : (fy ? __ldg(c + i - n + nx) : -eps);
+                const float zl = cm ? __ldg(cm + i) : -eps, zr = cp ? __ldg(cp + i) : -eps;
+                G[i] = ref_magnitude(fabsf(v), opp_max(pos, xl, xr), opp_max(pos, yl, yr), opp_max(pos, zl, zr), eps);
+            }
+        }
+        __syncthreads();
+        for (int y = t; y < ny; y += blockDim.x) {         // x scans: thread per row
+            if (fx) scan_line_wrap(G + (long long)y * nx, nx, 1);
+            else scan_line_serial(G + (long long)y * nx, nx, 1);
+        }
+        __syncthreads();
+        for (int x = t; x < nx; x += blockDim.x) {         // y scans: thread per column, then the signs
+            if (fy) scan_line_wrap(G + x, ny, nx);
+            else scan_line_serial(G + x, ny, nx);
+            for (int y = 0; y < ny; ++y) {
+                const long long i = (long long)y * nx + x;
+                const float m = G[i];
+                G[i] = __ldg(c + i) > 0.0f ? m : -m;
+            }
+        }
+        __syncthreads();                                    // G is final before the next item
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 // The radius-specialised convolution kernels (R = 1 .. kMaxRadius) per tier
 // side; the z pass with or without the velocity correction of Eq. (10).
-constexpr int kTierSide[kTiers] = {32, 48, 64};
-constexpr int kRedistThreads[kTiers] = {128, 192, 256};   // threads per CTA of p_redist_xy (4 lanes per line)
-constexpr int kConvThreads[kTiers] = {128, 192, 256};     // threads per CTA of p_conv_xy
+constexpr int kTierSide[kTiers] = {32, 48, 64, 1 << 30};  // the last tier: any size (global-memory plane passes)
+constexpr int kRedistThreads[kTiers] = {128, 192, 256, 256};   // threads per CTA of p_redist_xy (4 lanes per line)
+constexpr int kConvThreads[kTiers] = {128, 192, 256, 256};     // threads per CTA of p_conv_xy
+constexpr int kBigTier = kTiers - 1;
 static size_t conv_smem_bytes(int side, int R) {       // ConvXYLayout<R, side>::bytes
+    if (side > 64) return 0;                              // general-size tier: static shared memory only
     const int pyr = side + 2 * R, px = ((side + 3) & ~3) + 4 * ((2 * R + 1 + 6) / 4), xp = (side + 3) & ~3;
     return 128 + sizeof(float) * ((size_t)side * side + (size_t)pyr * px + (size_t)(pyr + 3) * xp) +
            sizeof(int) * 2 * pyr;
 }
 constexpr size_t redist_smem_bytes(int side) {
+    if (side > 64) return 0;
     return 128 + (size_t)(3 * side * side + side * (side + 1)) * sizeof(float);   // barriers, 3 slots, G
 }
 
@@ -965,15 +1140,17 @@ struct PassFns {
 
 template <int R>
 static PassFns pass_fns_r(bool phys) {
-    static_assert(kTiers == 3, "one instantiation per tier side");
+    static_assert(kTiers == 4, "one instantiation per tier side");
     PassFns f;
     f.conv_xy[0] = reinterpret_cast<const void*>(p_conv_xy<R, 32, kConvThreads[0]>);
     f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 48, kConvThreads[1]>);
     f.conv_xy[2] = reinterpret_cast<const void*>(p_conv_xy<R, 64, kConvThreads[2]>);
+    f.conv_xy[3] = reinterpret_cast<const void*>(p_conv_xy_big<R>);
     f.conv_z = phys ? reinterpret_cast<const void*>(p_conv_z<R, true>) : reinterpret_cast<const void*>(p_conv_z<R, false>);
     f.redist_xy[0] = reinterpret_cast<const void*>(p_redist_xy<32, kRedistThreads[0]>);
     f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<48, kRedistThreads[1]>);
     f.redist_xy[2] = reinterpret_cast<const void*>(p_redist_xy<64, kRedistThreads[2]>);
+    f.redist_xy[3] = reinterpret_cast<const void*>(p_redist_xy_big);
     return f;
 }
 
@@ -998,12 +1175,12 @@ cudaError_t configure_passes(StepBuffers& B) {
         B.tier_side[t] = kTierSide[t];
         B.tier_threads[t] = kTierSide[t];
         int o[5] = {0, 0, 1, 0, 0};
-        e = allow_max_dynamic_smem(fn.conv_xy[t]);
+        e = t == kBigTier ? cudaSuccess : allow_max_dynamic_smem(fn.conv_xy[t]);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], fn.conv_xy[t], kConvThreads[t],
                                                               conv_smem_bytes(kTierSide[t], B.dom.radius));
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], fn.conv_z, kColThreads, 0);
-        if (e == cudaSuccess) e = allow_max_dynamic_smem(fn.redist_xy[t]);
+        if (e == cudaSuccess && t != kBigTier) e = allow_max_dynamic_smem(fn.redist_xy[t]);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], fn.redist_xy[t], kRedistThreads[t],
                                                               redist_smem_bytes(kTierSide[t]));

@@ -668,7 +668,7 @@ cudaError_t configure_step_kernels(StepBuffers& B) {
     B.use_passes = passes ? 1 : 0;
     for (int c = 0; c < kNumClasses; ++c) {
         B.block[c] = kThreads;
-        if (passes && c < kNumClasses - 1) {      // x, y sides <= 64: pass path
+        if (passes) {                             // pass path (the largest boxes: its general-size tier)
             B.mode[c] = 3;
             continue;
         }
