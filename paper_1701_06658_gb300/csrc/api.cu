@@ -59,6 +59,8 @@ struct lsgg_ctx {
     double* d_quats = nullptr;
     int* d_nb_tab = nullptr;
     int* d_nb_cnt = nullptr;
+    float* d_nb_w = nullptr;
+    float* d_nb_m = nullptr;
     double* d_vol = nullptr;
     long long* d_packed_off = nullptr;
     StepState* h_st = nullptr;       // pinned mirror for status reads
@@ -498,6 +500,8 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
         if ((r = dalloc(c, &c->d_quats, quats.size())) != LSGG_OK) return bail(r);
         if ((r = dalloc(c, &c->d_nb_tab, (size_t)G * kNbCap)) != LSGG_OK) return bail(r);
         if ((r = dalloc(c, &c->d_nb_cnt, (size_t)G)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &c->d_nb_w, (size_t)G * kNbCap)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &c->d_nb_m, (size_t)G * kNbCap)) != LSGG_OK) return bail(r);
         if (cudaMemcpy(c->d_quats, quats.data(), quats.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemset(c->d_nb_cnt, 0, (size_t)G * 4) != cudaSuccess)
             return bail(CUDA_FAIL());
@@ -636,6 +640,8 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->phys.quats = c->d_quats;
     c->phys.nb_tab = c->d_nb_tab;
     c->phys.nb_cnt = c->d_nb_cnt;
+    c->phys.nb_w = c->d_nb_w;
+    c->phys.nb_m = c->d_nb_m;
     c->phys.theta_max = cfg_in->theta_max_deg * M_PI / 180.0;
     c->phys.mob_low = cfg_in->mob_low;
     c->phys.mob_law = cfg_in->mobility_law;

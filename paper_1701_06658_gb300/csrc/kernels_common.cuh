@@ -138,20 +138,19 @@ __device__ __forceinline__ float pair_blend_cached(const PhysicsDev& phys, const
     return phi + pc.w * (c - phi) + bulk;
 }
 
-// Load box `gid`'s neighbour table into shared memory and evaluate its pair
-// weights (all threads of the CTA; caller synchronises afterwards).
+// Load box `gid`'s neighbour table and its pair weights (evaluated once per
+// step when the table is rebuilt) into shared memory (all threads of the CTA;
+// caller synchronises afterwards).
 __device__ __forceinline__ PairTable load_pair_table(const PhysicsDev& phys, int gid, int* tj, float* tw, float* tm) {
     PairTable t{tj, tw, tm, 0};
     if (phys.kind != LSGG_PHYSICS_READ_SHOCKLEY) return t;
     int n = phys.nb_cnt[gid];
     if (n > kNbCap) n = kNbCap;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int j = phys.nb_tab[(size_t)gid * kNbCap + k];
-        float w, m;
-        rs_pair(phys, gid, j, w, m);
-        tj[k] = j;
-        tw[k] = w;
-        tm[k] = m;
+        const size_t e = (size_t)gid * kNbCap + k;
+        tj[k] = phys.nb_tab[e];
+        tw[k] = phys.nb_w[e];
+        tm[k] = phys.nb_m[e];
     }
     t.n = n;
     return t;

@@ -78,6 +78,8 @@ struct PhysicsDev {
     const double* quats;            // per grain unit quaternion (w, x, y, z) (READ_SHOCKLEY)
     const int* nb_tab;              // per grain: ascending ids of the grains in its ID-field
     const int* nb_cnt;              // per grain: entries (kNbCap + 1: the table overflowed)
+    const float* nb_w;              // per grain and entry: pair weight w (READ_SHOCKLEY, refreshed with nb_tab)
+    const float* nb_m;              // per grain and entry: pair mobility M
     double theta_max;               // radians
     double mob_low;
     int mob_law;                    // LSGG_MOBILITY_*

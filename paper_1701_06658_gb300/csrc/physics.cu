@@ -6,15 +6,15 @@
 // pairs the next predictor can meet.  k_collect_neighbours rebuilds it from the
 // state's ID-field before every predictor of a READ_SHOCKLEY run; the
 // predictor evaluates the pair weights of a box once from it.
-#include "lsgg_internal.cuh"
+#include "kernels_common.cuh"
 
 namespace lsgg {
 
 constexpr int kHashSlots = 512;
 
 __global__ void __launch_bounds__(256)
-k_collect_neighbours(const Box* __restrict__ prev, const int* __restrict__ IDF, int* __restrict__ tab,
-                     int* __restrict__ cnt) {
+k_collect_neighbours(PhysicsDev phys, const Box* __restrict__ prev, const int* __restrict__ IDF, int* __restrict__ tab,
+                     int* __restrict__ cnt, float* __restrict__ tw, float* __restrict__ tm) {
     __shared__ int keys[kHashSlots];
     __shared__ int n_keys, overflow;
     const int b = blockIdx.x;
@@ -55,6 +55,15 @@ k_collect_neighbours(const Box* __restrict__ prev, const int* __restrict__ IDF, 
         if (rank < kNbCap) tab[(size_t)b * kNbCap + rank] = j;
     }
     if (threadIdx.x == 0) cnt[b] = (overflow || n_keys > kNbCap) ? kNbCap + 1 : n_keys;
+    __syncthreads();
+    // the pair weights of the table (FP64 disorientation), once per grain and step
+    const int n = min(n_keys, kNbCap);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        float w, m;
+        rs_pair(phys, b, tab[(size_t)b * kNbCap + k], w, m);
+        tw[(size_t)b * kNbCap + k] = w;
+        tm[(size_t)b * kNbCap + k] = m;
+    }
 }
 
 // Contact neighbours of each box from the neighbour-max field of the last step:
@@ -117,8 +126,9 @@ cudaError_t launch_field_neighbours(const StepBuffers& B, const Box* boxes, int 
 }
 
 cudaError_t launch_collect_neighbours(const StepBuffers& B, const PhysicsDev& phys, cudaStream_t s) {
-    k_collect_neighbours<<<B.n_boxes, 256, 0, s>>>(B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
-                                                     const_cast<int*>(phys.nb_cnt));
+    k_collect_neighbours<<<B.n_boxes, 256, 0, s>>>(phys, B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
+                                                     const_cast<int*>(phys.nb_cnt), const_cast<float*>(phys.nb_w),
+                                                     const_cast<float*>(phys.nb_m));
     return cudaGetLastError();
 }
 
