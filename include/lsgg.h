@@ -126,7 +126,8 @@ int lsgg_step(lsgg_ctx* ctx, int32_t n, double dt);
 int lsgg_sync(lsgg_ctx* ctx, int64_t timeout_ms);
 
 /* Per-grain volume V_i = sum_x H(phi_i(x)), H(phi) = clamp(phi + 1/2, 0, 1),
- * FP64 compensated sums in a fixed order (deterministic); index = grain id,
+ * exact fixed-point partial sums merged with FP64 compensated sums in a fixed
+ * order (deterministic); index = grain id,
  * 0 for extinct grains.  out: host array of cap >= n_grains doubles;
  * *n_out = n_grains.  Synchronises. */
 int lsgg_grain_volumes(lsgg_ctx* ctx, double* out, int64_t cap, int64_t* n_out);
