@@ -504,13 +504,23 @@ p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
         unsigned long long k1[kTileZ], k2[kTileZ];
 #pragma unroll
         for (int zz = 0; zz < kTileZ; ++zz) { k1[zz] = 0ull; k2[zz] = 0ull; }
+        // the top-2 decoded once for sweep 1: the other grains' max is v1 unless
+        // the box is the top one (then v2); absent keys read -eps and id -1
+        float v1[kTileZ], v2[kTileZ];
+        int i1[kTileZ], i2[kTileZ];
         // two sweeps over the tile's boxes: 0 builds the top-2, 1 writes phi_c
+#pragma unroll
         for (int sweep = 0; sweep < 2; ++sweep) {
-            if (sweep == 1 && col) {
+            if (sweep == 1) {
                 ulonglong2* T2 = reinterpret_cast<ulonglong2*>(B.T);
 #pragma unroll
-                for (int zz = 0; zz < kTileZ; ++zz)
-                    if (zz < nzt) T2[((long long)(z0 + zz) * D.ny + y) * D.nx + x] = make_ulonglong2(k1[zz], k2[zz]);
+                for (int zz = 0; zz < kTileZ; ++zz) {
+                    if (col && zz < nzt) T2[((long long)(z0 + zz) * D.ny + y) * D.nx + x] = make_ulonglong2(k1[zz], k2[zz]);
+                    v1[zz] = key_val(k1[zz], eps);
+                    v2[zz] = key_val(k2[zz], eps);
+                    i1[zz] = key_id(k1[zz]);
+                    i2[zz] = key_id(k2[zz]);
+                }
             }
             for (int base = 0; base < n_total; base += kTileCap) {
                 const int nb = min(kTileCap, n_total - base);
@@ -555,11 +565,9 @@ p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
                             int lz = dz + zz;
                             if (lz >= D.nz) lz -= D.nz;
                             const long long o = o0 + (long long)lz * ps;
-                            const int id1 = key_id(k1[zz]);
-                            float m;
-                            int mid;
-                            if (id1 != t.id) { m = key_val(k1[zz], eps); mid = id1; }
-                            else { m = key_val(k2[zz], eps); mid = key_id(k2[zz]); }
+                            const bool top = i1[zz] == t.id;
+                            const float m = top ? v2[zz] : v1[zz];
+                            int mid = top ? i2[zz] : i1[zz];
                             if (!(m > -eps)) mid = -1;
                             const float pc = 0.5f * (v[zz] - m);
                             B.Z[o] = pc;
