@@ -36,6 +36,9 @@ __device__ __forceinline__ float wrap_half(float d, float n) {
     return d > 0.5f * n ? d - n : (d < -0.5f * n ? d + n : d);
 }
 
+// A bin index within one period of [0, nb) (the reach never exceeds a period).
+__device__ __forceinline__ int wrap_bin(int i, int nb) { return i < 0 ? i + nb : (i >= nb ? i - nb : i); }
+
 // Bins of one axis to visit around bin c at reach k: [lo, lo + cnt) cyclically.
 __device__ __forceinline__ void bin_range(int c, int k, int nb, int& lo, int& cnt) {
     if (2 * k + 1 >= nb) { lo = 0; cnt = nb; }
@@ -50,12 +53,12 @@ __device__ __forceinline__ void for_block(const SeedBins& S, int cx, int cy, int
     bin_range(cy, ky, S.nb[1], ly, ny_);
     bin_range(cz, kz, S.nb[2], lz, nz_);
     for (int iz = 0; iz < nz_; ++iz) {
-        const int bz = pmod(lz + iz, S.nb[2]);
+        const int bz = wrap_bin(lz + iz, S.nb[2]);
         for (int iy = 0; iy < ny_; ++iy) {
-            const int by = pmod(ly + iy, S.nb[1]);
+            const int by = wrap_bin(ly + iy, S.nb[1]);
             const int row = (bz * S.nb[1] + by) * S.nb[0];
             for (int ix = 0; ix < nx_; ++ix) {
-                const int bin = row + pmod(lx + ix, S.nb[0]);
+                const int bin = row + wrap_bin(lx + ix, S.nb[0]);
                 for (int q = S.start[bin]; q < S.start[bin + 1]; ++q) f(q);
             }
         }
@@ -92,13 +95,27 @@ k_labels(Domain D, int G, SeedBins S, const double* __restrict__ seeds, const do
         const float r = sqrtf(fmaxf(0.0f, bound + margin(bound) + S.wmax)) + 1.0f;   // + 1: bin-edge rounding
         for (int a = 0; a < 3; ++a) k[a] = (int)ceilf(r / S.size[a]) + 1;
     }
+    // one pass: the FP32 minimum and the seeds within the margin of the running
+    // minimum (a superset of those within the margin of the final one); a
+    // full candidate list falls back to a second pass
+    constexpr int kCand = 8;
+    int cand[kCand];
+    float cand_d[kCand];
+    int n_cand = 0;
+    bool rescan = false;
     float best32 = FLT_MAX;
-    for_block(S, cx, cy, cz, k[0], k[1], k[2], [&](int q) { best32 = fminf(best32, d32(q)); });
+    for_block(S, cx, cy, cz, k[0], k[1], k[2], [&](int q) {
+        const float d = d32(q);
+        best32 = fminf(best32, d);
+        if (d <= best32 + margin(best32)) {
+            if (n_cand < kCand) { cand[n_cand] = q; cand_d[n_cand] = d; ++n_cand; }
+            else rescan = true;
+        }
+    });
     const float lim = best32 + margin(best32);
     double best = DBL_MAX;
     int arg = -1;
-    for_block(S, cx, cy, cz, k[0], k[1], k[2], [&](int q) {
-        if (d32(q) > lim) return;
+    auto exact = [&](int q) {
         const int i = S.ids[q];
         const double ex = min_image(__dsub_rn((double)x, seeds[3 * i]), (double)D.nx);
         const double ey = min_image(__dsub_rn((double)y, seeds[3 * i + 1]), (double)D.ny);
@@ -106,7 +123,15 @@ k_labels(Domain D, int G, SeedBins S, const double* __restrict__ seeds, const do
         double rr = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
         if (weights) rr = __dsub_rn(rr, weights[i]);
         if (rr < best || (rr == best && i < arg)) { best = rr; arg = i; }
-    });
+    };
+    if (!rescan) {
+        for (int c = 0; c < n_cand; ++c)
+            if (cand_d[c] <= lim) exact(cand[c]);
+    } else {
+        for_block(S, cx, cy, cz, k[0], k[1], k[2], [&](int q) {
+            if (d32(q) <= lim) exact(q);
+        });
+    }
     labels[cell] = arg;
 }
 
@@ -201,8 +226,11 @@ __device__ __forceinline__ double power_dist(const double* p, const double* s, d
 // with D = s_i - s_j (minimum image), p - s_j = a + D up to one period per
 // axis; with d = (p - s_j) - a the bisector distance is
 // (d . (d + 2a) - (w_j - w_i)) / (2 |d|).  An FP32 pass over the neighbours
-// finds the candidates within a margin of the minimum; those are evaluated
-// exactly as in the FP64 definition (explicitly rounded operations).
+// finds the candidates within a margin of the minimum; those are evaluated in
+// FP64 in that well-conditioned form (a reciprocal square root instead of a
+// square root and a division): the same value as the definition's
+// ((p - s_j)^2 - w_j - (p - s_i)^2 + w_i) / (2 |d|) up to FP64 rounding,
+// far below the FP32 result's half unit.
 __global__ void __launch_bounds__(256)
 k_sdf(Domain D, int G, const Box* __restrict__ boxes, const double* __restrict__ seeds,
       const double* __restrict__ weights, const unsigned* __restrict__ bits, long long words_per_row,
@@ -250,7 +278,7 @@ k_sdf(Domain D, int G, const Box* __restrict__ boxes, const double* __restrict__
         const int y = rem / b.nx, x = rem - y * b.nx;
         const double p[3] = {(double)pmod(b.ox + x, D.nx), (double)pmod(b.oy + y, D.ny), (double)pmod(b.oz + z, D.nz)};
         double a0, a1, a2;
-        const double pa = power_dist(p, si, wi, Nd, a0, a1, a2);
+        power_dist(p, si, wi, Nd, a0, a1, a2);
         const float af[3] = {(float)a0, (float)a1, (float)a2};
         // FP32 screen: U bounds the exact minimum from above
         const float asum = fabsf(af[0]) + fabsf(af[1]) + fabsf(af[2]);
@@ -295,12 +323,13 @@ k_sdf(Domain D, int G, const Box* __restrict__ boxes, const double* __restrict__
         int arg = -1;
         auto exact = [&](int k) {
             const int j = s_nb[k];
-            double b0, b1, b2;
-            const double pb = power_dist(p, seeds + 3 * j, weights ? weights[j] : 0.0, Nd, b0, b1, b2);
-            const double d0 = __dsub_rn(b0, a0), d1 = __dsub_rn(b1, a1), d2 = __dsub_rn(b2, a2);
-            const double den2 = __dmul_rn(2.0, __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)),
-                                                                    __dmul_rn(d2, d2))));
-            const double ve = __ddiv_rn(__dsub_rn(pb, pa), den2);
+            const double* sj = seeds + 3 * j;
+            const double d0 = __dsub_rn(min_image(__dsub_rn(p[0], sj[0]), Nd[0]), a0);
+            const double d1 = __dsub_rn(min_image(__dsub_rn(p[1], sj[1]), Nd[1]), a1);
+            const double d2 = __dsub_rn(min_image(__dsub_rn(p[2], sj[2]), Nd[2]), a2);
+            double num = fma(d0, fma(2.0, a0, d0), fma(d1, fma(2.0, a1, d1), d2 * fma(2.0, a2, d2)));
+            if (weights) num -= weights[j] - wi;
+            const double ve = num * (0.5 * rsqrt(fma(d0, d0, fma(d1, d1, d2 * d2))));
             if (ve < best) { best = ve; arg = j; }
         };
         if (!rescan) {
