@@ -524,6 +524,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if (c->B.use_passes) {
         c->B.plane_item_cap = (long long)G * D.nz;
         if ((r = dalloc(c, &c->B.plane_items, (size_t)c->B.plane_item_cap)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &c->B.item_base, (size_t)G)) != LSGG_OK) return bail(r);
         c->B.slab_item_cap = (long long)G * ((D.nz + kSlab - 1) / kSlab);
         if ((r = dalloc(c, &c->B.slab_items, (size_t)c->B.slab_item_cap)) != LSGG_OK) return bail(r);
         if ((r = dalloc(c, &c->B.tile_cnt, (size_t)c->B.n_tiles)) != LSGG_OK) return bail(r);

@@ -172,6 +172,7 @@ struct StepBuffers {
     int2* plane_items;              // (box, local z), tier 0 then tier 1
     int2* chunk_items;              // (box, column chunk of kPassChunk columns)
     int2* slab_items;               // (box, first plane of a slab of kSlab planes)
+    int4* item_base;                // per box: first plane / chunk / slab item, tier (-1: no items)
     long long plane_item_cap;       // entries (n_boxes * domain nz: a bound on sum nz)
     long long slab_item_cap;        // entries (n_boxes * ceil(domain nz / kSlab))
     long long chunk_item_cap;       // entries (n_boxes * 64 * 64 / kPassChunk)

@@ -570,6 +570,7 @@ k_box_update(StepBuffers B, int layout_only) {
                            kind_total[2] <= B.slab_item_cap;
     for (int b = b0; b < b1; ++b) {
         const Box cb = B.cur[b];
+        if (B.use_passes) B.item_base[b] = make_int4(0, 0, 0, -1);
         if (cb.nx <= 0) continue;
         const int c = box_class(B, cb, B.prev[b]);
         if (B.mode[c] != 3) {
@@ -586,9 +587,7 @@ k_box_update(StepBuffers B, int layout_only) {
         pre[kNumClasses + t] += cb.nz;
         pre[kNumClasses + kTiers + t] += nch;
         pre[kNumClasses + 2 * kTiers + t] += nsl;
-        for (int z = 0; z < cb.nz; ++z) B.plane_items[p0 + z] = make_int2(b, z);
-        for (int k = 0; k < nch; ++k) B.chunk_items[c0 + k] = make_int2(b, k);
-        for (int k = 0; k < nsl; ++k) B.slab_items[s0 + k] = make_int2(b, k * kSlab);
+        B.item_base[b] = make_int4(p0, c0, s0, t);    // the items themselves: k_write_items
     }
     // reduce cells / alive / tier cells
     const long long r_cells = block_sum_ll(cells, s_part);
@@ -729,8 +728,30 @@ long long large_class_scratch_floats(const Domain& d) {
     return (m + 31) & ~31LL;
 }
 
+// The pass path's work items of every box, from the bases k_box_update set:
+// a warp per box, lanes along its items (coalesced stores).
+__global__ void __launch_bounds__(256)
+k_write_items(StepBuffers B) {
+    if (*(volatile int*)&B.st->halt) return;         // the box update stopped the step: no fresh bases
+    const int lane = threadIdx.x & 31;
+    const int warps = (blockDim.x >> 5) * gridDim.x;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B.n_boxes; b += warps) {
+        const int4 base = B.item_base[b];
+        if (base.w < 0) continue;
+        const Box cb = B.cur[b];
+        const int nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
+        const int nsl = (cb.nz + kSlab - 1) / kSlab;
+        for (int z = lane; z < cb.nz; z += 32) B.plane_items[base.x + z] = make_int2(b, z);
+        for (int k = lane; k < nch; k += 32) B.chunk_items[base.y + k] = make_int2(b, k);
+        for (int k = lane; k < nsl; k += 32) B.slab_items[base.z + k] = make_int2(b, k * kSlab);
+    }
+}
+
 cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream_t s) {
     k_box_update<<<1, kBoxUpdateThreads, 0, s>>>(B, layout_only ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !B.use_passes) return e;
+    k_write_items<<<B.n_sm * 4, 256, 0, s>>>(B);
     return cudaGetLastError();
 }
 
