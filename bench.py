@@ -182,6 +182,26 @@ def reference_arm(args):
     return 0
 
 
+def replica_seed(rank: int) -> int:
+    """Tessellation seed of a rank's replica: independent replicas, no exchange."""
+    return WORKLOAD["seed"] + 1000 * rank
+
+
+def reduce_over_ranks(dev_ms, cells, e2e_s, e2e_cells, world):
+    """Whole-job timing of independent replicas: the slowest rank's times and
+    the sum of all ranks' cell-updates (a no-op on one rank)."""
+    if world <= 1:
+        return dev_ms, float(cells), e2e_s, float(e2e_cells)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([dev_ms, float(cells), e2e_s, float(e2e_cells)], dtype=torch.float64, device=dev)
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
+
+
 def workload_kwargs(L):
     """Microstructure keyword arguments of the workload's physics and tessellation."""
     kw = {}
@@ -222,7 +242,7 @@ def gpu_arm(args):
     from paper_1701_06658_gb300 import lsgg as L
     L.lib()
     n, g, dt = WORKLOAD["n"], WORKLOAD["grains"], WORKLOAD["dt"]
-    seed = WORKLOAD["seed"] + 1000 * rank          # independent replica per rank
+    seed = replica_seed(rank)                      # independent replica per rank
     seeds = I.voronoi_seeds(seed, g, (n, n, n))
 
     def barrier():
@@ -341,17 +361,7 @@ def gpu_arm(args):
         serving = serving_run(L, I, args.serve_requests, local)
 
     # ---------------- reduce over ranks ----------------
-    vals = [dev_ms, float(cells), e2e_s, float(e2e_cells)]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor(vals, dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        dev_ms, cells_all, e2e_s, e2e_cells_all = mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
-    else:
-        cells_all, e2e_cells_all = float(cells), float(e2e_cells)
+    dev_ms, cells_all, e2e_s, e2e_cells_all = reduce_over_ranks(dev_ms, cells, e2e_s, e2e_cells, world)
     if rank != 0:
         return 0
 

@@ -1,0 +1,61 @@
+"""The multi-GPU bench path without GPUs: two gloo ranks on the CPU run the
+same whole-job reduction bench.py uses (slowest rank's time, summed
+cell-updates) and get independent replica seeds; the reference arm of a
+non-zero rank exits without work."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out = bench.reduce_over_ranks(10.0 + rank, 100 * (rank + 1), 1.0 + 0.5 * rank, 7 * (rank + 1), world)
+        q.put((rank, out, bench.replica_seed(rank)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_like_the_bench():
+    mp = pytest.importorskip("torch.multiprocessing")
+    pytest.importorskip("torch.distributed")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    res.sort()
+    for rank, out, seed in res:
+        assert out == (11.0, 300.0, 1.5, 21.0)         # max time, summed cells over both ranks
+    assert res[0][2] != res[1][2]                        # independent replicas
+
+
+def test_reference_arm_of_a_nonzero_rank_does_nothing(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        steps, warmup, gpus = 1, 3, 2
+    assert bench.reference_arm(A()) == 0
+    assert capsys.readouterr().out == ""
