@@ -52,6 +52,12 @@ code where it applies):
   R7 initial functions (Sec. 2.1.3, "initialized to fulfill Eq. (2)"): the
      minimum over face-adjacent cells of the signed distance to the power
      bisector plane, clamped to [-eps, eps].
+  R11 Godunov variant of R5 (the Euclidean first-order update of Zhao's
+     fast sweeping, selected instead of the paper's taxicab propagation; Sec.
+     6.1 names the metric as the taxicab's weakness): the same reference
+     cells and values; every other cell gets the smallest u with
+     sum over the axes whose neighbour minimum a_k < u of (u - a_k)^2 = 1,
+     capped at eps, iterated (Jacobi) to the fixed point.
 """
 from __future__ import annotations
 
@@ -281,6 +287,51 @@ def redistance(phic: np.ndarray, full, eps, axes) -> np.ndarray:
     return np.where(pos, mag, -mag)
 
 
+def godunov_update(mins) -> np.ndarray:
+    """R11: the upwind solution u of sum_k max(u - a_k, 0)^2 = 1 for the
+    per-axis neighbour minima a_k (inf where an axis has none): with the a_k
+    sorted, u = a_1 + 1 while that is <= a_2, else the root over the two
+    smallest while it is <= a_3, else the root over all three."""
+    a = np.sort(np.stack(mins), axis=0)
+    u = a[0] + 1.0
+    if len(mins) >= 2:
+        s2 = a[0] + a[1]
+        with np.errstate(invalid="ignore"):
+            u2 = 0.5 * (s2 + np.sqrt(np.maximum(2.0 - (a[0] - a[1]) ** 2, 0.0)))
+        u = np.where(u > a[1], u2, u)
+    if len(mins) == 3:
+        s3 = a[0] + a[1] + a[2]
+        with np.errstate(invalid="ignore"):
+            u3 = (s3 + np.sqrt(np.maximum(s3 * s3 - 3.0 * (a[0] ** 2 + a[1] ** 2 + a[2] ** 2 - 1.0), 0.0))) / 3.0
+        u = np.where(u > a[2], u3, u)
+    return u
+
+
+def redistance_godunov(phic: np.ndarray, full, eps, axes) -> np.ndarray:
+    """Reading R11: Euclidean first-order (Godunov upwind) signed distance to
+    the zero level of phic, reference values as in R5 held fixed, the others
+    lowered to the fixed point of the update over same-sign face neighbours."""
+    pos = phic > 0
+    is_ref, dref = reference_values(phic, full, eps, axes)
+    mag = np.where(is_ref, dref, eps)
+    exists = np.ones(phic.shape, dtype=bool)
+    while True:
+        mins = []
+        for ax in axes:
+            m = np.full(phic.shape, np.inf)
+            for k in (1, -1):
+                nb_mag = _shift(mag, ax, k, full[ax], np.inf)
+                nb_pos = _shift(pos, ax, k, full[ax], False)
+                nb_ok = _shift(exists, ax, k, full[ax], False)
+                m = np.where(nb_ok & (nb_pos == pos), np.minimum(m, nb_mag), m)
+            mins.append(m)
+        new = np.where(is_ref, dref, np.minimum(mag, np.minimum(eps, godunov_update(mins))))
+        if np.array_equal(new, mag):
+            break
+        mag = new
+    return np.where(pos, mag, -mag)
+
+
 # --------------------------------------------------------------------------
 # box update: Secs. 2.1.3 and 3.1 (size-adaptive local grids)
 # --------------------------------------------------------------------------
@@ -470,6 +521,7 @@ class Microstructure:
     radius: int = 5
     physics: Physics | None = None
     time: float = 0.0
+    redist: str = "taxicab"      # R5, or "godunov" (R11)
 
 
 def box_candidates(ms: Microstructure):
@@ -513,7 +565,8 @@ def step_parts(ms: Microstructure, dt: float, brute_force: bool = False) -> Step
         parts.m[g.gid] = m
         parts.idm[g.gid] = idm
         parts.phic[g.gid] = compare(phip[g.gid], m)
-        parts.phi[g.gid] = np.clip(redistance(parts.phic[g.gid], full_axes(g, ms.shape), ms.eps, axes),
+        redist = redistance_godunov if ms.redist == "godunov" else redistance
+        parts.phi[g.gid] = np.clip(redist(parts.phic[g.gid], full_axes(g, ms.shape), ms.eps, axes),
                                    -ms.eps, ms.eps)
     return parts
 
@@ -529,7 +582,7 @@ def step(ms: Microstructure, dt: float, brute_force: bool = False) -> Microstruc
         idf = parts.idm[g.gid] if ms.physics is not None else None
         upd = Grain(g.gid, g.origin, parts.phi[g.gid], idf)
         grains.append(box_update(upd, ms.shape, ms.halo, ms.eps))
-    return Microstructure(ms.shape, grains, ms.eps, ms.halo, ms.radius, ms.physics, ms.time + dt)
+    return Microstructure(ms.shape, grains, ms.eps, ms.halo, ms.radius, ms.physics, ms.time + dt, ms.redist)
 
 
 def run(ms: Microstructure, n: int, dt: float) -> Microstructure:

@@ -282,6 +282,68 @@ def test_same_sign_restriction_is_immaterial(oracle, shape, full):
         assert np.max(np.abs(got - want)) < 1e-12
 
 
+def test_godunov_update_solves_the_upwind_equation(oracle):
+    """R11: the closed-form update is the smallest root of
+    sum_k max(u - a_k, 0)^2 = 1, found here by bisection instead."""
+    rng = np.random.default_rng(21)
+    for ndim in (1, 2, 3):
+        a = [rng.uniform(0.0, 3.0, 400) for _ in range(ndim)]
+        a[0][:50] = np.inf if ndim > 1 else a[0][:50]          # an axis without a neighbour
+        u = oracle.godunov_update(a)
+        lo = np.min(np.stack(a), axis=0)
+        hi = lo + 1.0
+        f = lambda v: sum(np.maximum(v - ak, 0.0) ** 2 for ak in a) - 1.0
+        for _ in range(80):
+            mid = 0.5 * (lo + hi)
+            neg = f(mid) < 0
+            lo = np.where(neg, mid, lo)
+            hi = np.where(neg, hi, mid)
+        assert np.max(np.abs(u - 0.5 * (lo + hi))) < 1e-12
+
+
+def test_godunov_redistance_is_euclidean_on_a_sphere(oracle):
+    """R11 vs R5 on a sphere of radius 12 (distorted values, same zero level):
+    the Godunov fixed point is first-order Euclidean (max error 0.38 cells in
+    the band |d| <= 5), the taxicab one overshoots along diagonals (2.9)."""
+    N, c = 40, 19.6
+    z, y, x = np.meshgrid(*[np.arange(N, dtype=float)] * 3, indexing="ij")
+    d = 12.0 - np.sqrt((x - c - 0.3) ** 2 + (y - c + 0.2) ** 2 + (z - c) ** 2)
+    phic = np.clip(6.0 * np.tanh(d / 3.0), -7, 7)
+    g = oracle.redistance_godunov(phic, (False,) * 3, 7.0, (0, 1, 2))
+    t = oracle.redistance(phic, (False,) * 3, 7.0, (0, 1, 2))
+    band = np.abs(d) <= 5.0
+    assert np.abs(g - d)[band].max() < 0.45 and np.abs(g - d)[band].mean() < 0.12
+    assert np.abs(t - d)[band].max() > 2.0
+    assert np.array_equal(g > 0, phic > 0)
+
+
+@pytest.mark.parametrize("shape,full", [((6, 7, 5), (False,) * 3), ((5, 6, 7), (True, False, True))])
+def test_godunov_fixed_point(oracle, shape, full):
+    """The returned magnitudes are a fixed point: reference cells keep their
+    planar values, every other cell equals min(eps, update of its same-sign
+    neighbours); an axis-aligned plane is reproduced exactly like R5."""
+    rng = np.random.default_rng(22)
+    axes = (0, 1, 2)
+    phic = rng.uniform(-2, 2, size=shape) + rng.uniform(-1, 1)
+    g = oracle.redistance_godunov(phic, full, 7.0, axes)
+    is_ref, dref = oracle.reference_values(phic, full, 7.0, axes)
+    mag, pos = np.abs(g), phic > 0
+    mins = []
+    for ax in axes:
+        m = np.full(shape, np.inf)
+        for k in (1, -1):
+            nb = oracle._shift(mag, ax, k, full[ax], np.inf)
+            ok = oracle._shift(np.ones(shape, bool), ax, k, full[ax], False) & (oracle._shift(pos, ax, k, full[ax], False) == pos)
+            m = np.where(ok, np.minimum(m, nb), m)
+        mins.append(m)
+    want = np.where(is_ref, dref, np.minimum(7.0, oracle.godunov_update(mins)))
+    assert np.max(np.abs(mag - want)) < 1e-12
+    x = np.arange(30, dtype=float)
+    d = np.broadcast_to(x - 12.3, (4, 5, 30)).copy()
+    assert np.array_equal(oracle.redistance_godunov(np.clip(1.7 * d, -7, 7), (True, True, False), 7.0, axes),
+                          oracle.redistance(np.clip(1.7 * d, -7, 7), (True, True, False), 7.0, axes))
+
+
 def test_redistance_axis_plane_is_exact(oracle):
     """Taxicab propagation reproduces an axis-aligned planar SDF exactly
     (within eps) and caps it at eps."""
