@@ -213,6 +213,8 @@ def workload_kwargs(L):
         kw["energy_scale"] = WORKLOAD["energy_scale"]
     if WORKLOAD.get("init") == "laguerre":
         kw["init_kind"] = L.INIT_LAGUERRE
+    if WORKLOAD.get("redist") == "godunov":
+        kw["redist"] = L.REDIST_GODUNOV
     return kw
 
 
@@ -221,8 +223,9 @@ def workload_config():
           "magnetic": "magnetic driving force, random c-axes"}[WORKLOAD.get("physics", "ideal")]
     tess = ("Laguerre grains, lognormal radii sigma 0.5, 1 % at 5x volume" if WORKLOAD.get("init") == "laguerre"
             else "Voronoi grains")
+    rd = "" if WORKLOAD.get("redist", "taxicab") == "taxicab" else ", Godunov re-initialisation"
     return {"workload": f"{WORKLOAD['n']}^3 periodic, {WORKLOAD['grains']} {tess} (seed {WORKLOAD['seed']}), "
-                        f"{ph}, dt={WORKLOAD['dt']}, box halo 5, eps 7, FP32",
+                        f"{ph}{rd}, dt={WORKLOAD['dt']}, box halo 5, eps 7, FP32",
             "domain": [WORKLOAD["n"]] * 3, "grains": WORKLOAD["grains"], "dt": WORKLOAD["dt"],
             "l2": f"inputs larger than L2: box arenas of ~{WORKLOAD['n'] ** 3 * 8.5 * 4 / 1e9:.1f} GB each and a "
                   f"{16 * WORKLOAD['n'] ** 3 / 1e6:.0f} MB field vs 129 MB L2"}
@@ -482,12 +485,15 @@ def main():
                     help="batched: pass path for boxes of side <= 64; streamed: box-streaming kernels only")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving measurement (0: skip; 256: the full serving workload)")
+    ap.add_argument("--redist", default="taxicab", choices=["taxicab", "godunov"],
+                    help="re-initialisation metric: the paper's taxicab propagation or the Godunov update")
     ap.add_argument("--workload", default="256", choices=sorted(WORKLOADS),
                     help="256: the benchmark workload; 160: a small case of the same density for profilers; "
                          "512rs, 384mag: the non-ideal and magnetic workloads")
     args = ap.parse_args()
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
+    WORKLOAD["redist"] = args.redist
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

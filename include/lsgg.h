@@ -67,6 +67,10 @@ extern "C" {
 #define LSGG_EXEC_STREAMED 2   /* all boxes by box-streaming kernels: one CTA streams one box
                                   along z (register-ring / shared-memory rings per size class) */
 
+#define LSGG_REDIST_TAXICAB 0  /* Sec. 2.1.6 as printed: taxicab propagation from the reference cells */
+#define LSGG_REDIST_GODUNOV 1  /* the Euclidean first-order (Godunov upwind) update instead, iterated
+                                  (Jacobi, 20 sweeps over the boxes); LSGG_EXEC_BATCHED, 3D only */
+
 #define LSGG_MOBILITY_STEP  0  /* mob_low below theta_max, 1 above */
 #define LSGG_MOBILITY_EQ20  1  /* Eq. (20): 1 - 0.99 exp(-5 (theta / 15 deg)^9) */
 
@@ -83,6 +87,8 @@ typedef struct lsgg_config {
     int32_t exec;              /* LSGG_EXEC_* */
     int32_t mobility_law;      /* LSGG_MOBILITY_* (READ_SHOCKLEY only) */
     int32_t device;            /* CUDA device ordinal */
+    int32_t redist;            /* LSGG_REDIST_* re-initialisation metric (default TAXICAB) */
+    int32_t reserved;          /* 0 */
     double theta_max_deg;      /* Read-Shockley / mobility cut-off angle (default 15) */
     double mob_low;            /* low-angle mobility for LSGG_MOBILITY_STEP (default 0.1) */
     double lognormal_sigma;    /* LAGUERRE: sigma of the lognormal radii (default 0.5) */

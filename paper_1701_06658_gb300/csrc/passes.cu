@@ -968,6 +968,171 @@ p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
     }
 }
 // ---------------------------------------------------------------------------
+// Godunov re-initialisation (LSGG_REDIST_GODUNOV)
+// ---------------------------------------------------------------------------
+// The same reference cells and values as the taxicab scheme; every other cell
+// takes the smallest u with sum over the axes whose neighbour minimum a_k is
+// below u of (u - a_k)^2 = 1 (the Euclidean first-order upwind update of
+// Zhao's fast sweeping), capped at eps.  Non-reference cells have only
+// same-sign face neighbours, so no sign test is needed.  The update is not
+// separable: Jacobi sweeps over all boxes' columns (kGodunovSweeps, even, so
+// the magnitudes end in Y), ping-ponging between Y and X (the state is not
+// read after the predictor).  Reference cells are stored as -(1 + |d|) and
+// held fixed.  All tiers' column items at once: their lists are contiguous.
+constexpr int kGodunovSweeps = 20;     // fixed point to ~1e-8 (FP64 oracle), well inside the 1e-4 tolerance
+
+__device__ __forceinline__ float god_mag(float v) { return v < 0.0f ? -v - 1.0f : v; }
+
+__device__ __forceinline__ float godunov_u(float a, float b, float c) {
+    // sort a <= b <= c
+    float t;
+    if (b < a) { t = a; a = b; b = t; }
+    if (c < b) { t = b; b = c; c = t; }
+    if (b < a) { t = a; a = b; b = t; }
+    float u = a + 1.0f;
+    if (u > b) {
+        const float d = a - b;
+        u = 0.5f * (a + b + sqrtf(2.0f - d * d));
+        if (u > c) {
+            const float s = a + b + c;
+            u = (s + sqrtf(fmaxf(s * s - 3.0f * (a * a + b * b + c * c - 1.0f), 0.0f))) * (1.0f / 3.0f);
+        }
+    }
+    return u;
+}
+
+__device__ __forceinline__ int god_n_items(const StepBuffers& B) {
+    int n = 0;
+#pragma unroll
+    for (int t = 0; t < kTiers; ++t) n += B.st->n_chunks[t];
+    return n;
+}
+
+// classification -> Y (non-reference eps, reference -(1 + distance))
+__global__ void __launch_bounds__(kColThreads)
+p_god_init(StepBuffers B) {
+    if (halted(B)) return;
+    const Domain D = B.dom;
+    const float eps = D.eps;
+    const int n_items = god_n_items(B);
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int2 it = B.chunk_items[item];
+        const Box nb = B.cur[it.x];
+        const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
+        const bool fx = nx == D.nx, fy = ny == D.ny, fz = nz == D.nz;
+        const int c = it.y * kPassChunk + threadIdx.x;
+        if (c >= nx * ny) continue;
+        const int y = c / nx, x = c - y * nx;
+        const int ps = plane_stride(nx, ny);
+        const long long o0 = nb.off + c;
+        const int dxl = x > 0 ? -1 : (fx ? nx - 1 : 0), dxr = x < nx - 1 ? 1 : (fx ? 1 - nx : 0);
+        const int dyl = y > 0 ? -nx : (fy ? (ny - 1) * nx : 0), dyr = y < ny - 1 ? nx : (fy ? (1 - ny) * nx : 0);
+        for (int z = 0; z < nz; ++z) {
+            const long long o = o0 + (long long)z * ps;
+            const float v = __ldg(B.Z + o);
+            const bool pos = v > 0.0f;
+            const float xl = dxl ? __ldg(B.Z + o + dxl) : -eps, xr = dxr ? __ldg(B.Z + o + dxr) : -eps;
+            const float yl = dyl ? __ldg(B.Z + o + dyl) : -eps, yr = dyr ? __ldg(B.Z + o + dyr) : -eps;
+            const int zm = z > 0 ? z - 1 : (fz ? nz - 1 : -1), zp = z < nz - 1 ? z + 1 : (fz ? 0 : -1);
+            const float zl = zm >= 0 ? __ldg(B.Z + o0 + (long long)zm * ps) : -eps;
+            const float zr = zp >= 0 ? __ldg(B.Z + o0 + (long long)zp * ps) : -eps;
+            const float m = ref_magnitude(fabsf(v), opp_max(pos, xl, xr), opp_max(pos, yl, yr), opp_max(pos, zl, zr), eps);
+            B.Y[o] = m < eps ? -(1.0f + m) : eps;
+        }
+    }
+}
+
+// one Jacobi sweep src -> dst
+__global__ void __launch_bounds__(kColThreads)
+p_god_sweep(StepBuffers B, const float* __restrict__ src, float* __restrict__ dst) {
+    if (halted(B)) return;
+    const Domain D = B.dom;
+    const float eps = D.eps;
+    const int n_items = god_n_items(B);
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int2 it = B.chunk_items[item];
+        const Box nb = B.cur[it.x];
+        const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
+        const bool fx = nx == D.nx, fy = ny == D.ny, fz = nz == D.nz;
+        const int c = it.y * kPassChunk + threadIdx.x;
+        if (c >= nx * ny) continue;
+        const int y = c / nx, x = c - y * nx;
+        const int ps = plane_stride(nx, ny);
+        const long long o0 = nb.off + c;
+        const int dxl = x > 0 ? -1 : (fx ? nx - 1 : 0), dxr = x < nx - 1 ? 1 : (fx ? 1 - nx : 0);
+        const int dyl = y > 0 ? -nx : (fy ? (ny - 1) * nx : 0), dyr = y < ny - 1 ? nx : (fy ? (1 - ny) * nx : 0);
+        const float inf = __int_as_float(0x7f800000);
+        for (int z = 0; z < nz; ++z) {
+            const long long o = o0 + (long long)z * ps;
+            const float v = src[o];
+            if (v < 0.0f) { dst[o] = v; continue; }
+            const float ax = fminf(dxl ? god_mag(src[o + dxl]) : inf, dxr ? god_mag(src[o + dxr]) : inf);
+            const float ay = fminf(dyl ? god_mag(src[o + dyl]) : inf, dyr ? god_mag(src[o + dyr]) : inf);
+            const int zm = z > 0 ? z - 1 : (fz ? nz - 1 : -1), zp = z < nz - 1 ? z + 1 : (fz ? 0 : -1);
+            const float az = fminf(zm >= 0 ? god_mag(src[o0 + (long long)zm * ps]) : inf,
+                                   zp >= 0 ? god_mag(src[o0 + (long long)zp * ps]) : inf);
+            dst[o] = fminf(v, fminf(eps, godunov_u(ax, ay, az)));
+        }
+    }
+}
+
+// signs of phi_c back -> X, positive bounding box
+__global__ void __launch_bounds__(kColThreads)
+p_god_final(StepBuffers B, DebugOut dbg) {
+    if (halted(B)) return;
+    const Domain D = B.dom;
+    const int n_items = god_n_items(B);
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int2 it = B.chunk_items[item];
+        const int b = it.x;
+        const Box nb = B.cur[b];
+        const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
+        const int c = it.y * kPassChunk + threadIdx.x;
+        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+        if (c < nx * ny) {
+            const int y = c / nx, x = c - y * nx;
+            const int ps = plane_stride(nx, ny);
+            for (int z = 0; z < nz; ++z) {
+                const long long o = nb.off + c + (long long)z * ps;
+                const float m = god_mag(B.Y[o]);
+                const float out = __ldg(B.Z + o) > 0.0f ? m : -m;
+                st_state(B, o, out);
+                if (dbg.phin) dbg.phin[o] = out;
+                if (out > 0.0f) {
+                    lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);
+                    lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
+                    lo[2] = min(lo[2], z); hi[2] = max(hi[2], z);
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int l = lo[a], h = hi[a];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+                h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+            }
+            if ((threadIdx.x & 31) == 0 && l <= h) {
+                atomicMin(&B.bounds[b].lo[a], l);
+                atomicMax(&B.bounds[b].hi[a], h);
+            }
+        }
+    }
+}
+
+cudaError_t launch_godunov(const StepBuffers& B, const DebugOut& dbg, cudaStream_t s) {
+    const int grid = B.pgrid[0][4];
+    p_god_init<<<grid, kColThreads, 0, s>>>(B);
+    for (int k = 0; k < kGodunovSweeps; ++k) {
+        const bool even = (k & 1) == 0;
+        p_god_sweep<<<grid, kColThreads, 0, s>>>(B, even ? B.Y : B.X, even ? B.X : B.Y);
+    }
+    p_god_final<<<grid, kColThreads, 0, s>>>(B, dbg);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // general-size tier: plane passes through global memory
 // ---------------------------------------------------------------------------
 // Boxes with an x or y side above 64 (the lognormal tail of a power-diagram

@@ -798,13 +798,27 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
         };
         // pass-path tiers run one after the other on the step's stream: each
         // pass is a persistent grid that fills the GPU by itself
-        if (B.use_passes)
+        if (B.use_passes && which == 1 && B.godunov) {
+            // Godunov re-initialisation over all tiers at once; its time is
+            // reported as tier 0's re-initialisation passes
+            cudaEvent_t* pe = pass_ev ? pass_ev + 3 : nullptr;
+            if (pe) cudaEventRecord(pe[0], s);
+            cudaError_t r = traced(launch_godunov(B, d, s), "Godunov re-initialisation");
+            if (r != cudaSuccess) return r;
+            if (pe) {
+                cudaEventRecord(pe[1], s);
+                cudaEventRecord(pe[2], s);
+                for (int t = 1; t < kTiers; ++t)
+                    for (int k = 0; k < 3; ++k) cudaEventRecord(pass_ev[t * 6 + 3 + k], s);
+            }
+        } else if (B.use_passes) {
             for (int t = 0; t < kTiers; ++t) {
                 cudaError_t r = traced(
                     launch_passes(B, which, t, taps, phys, d, s, pass_ev ? pass_ev + t * 6 + (which ? 3 : 0) : nullptr),
                     "pass kernels");
                 if (r != cudaSuccess) return r;
             }
+        }
         for (int c = 0; c < kNumClasses; ++c) {
             if (B.mode[c] == 3) continue;
             cudaStream_t cs;

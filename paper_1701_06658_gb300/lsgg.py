@@ -32,6 +32,7 @@ PHYSICS_IDEAL, PHYSICS_READ_SHOCKLEY, PHYSICS_MAGNETIC = 0, 1, 2
 STORAGE_FP32, STORAGE_BF16 = 0, 1
 EXEC_BATCHED, EXEC_PLAIN, EXEC_STREAMED = 0, 1, 2
 MOBILITY_STEP, MOBILITY_EQ20 = 0, 1
+REDIST_TAXICAB, REDIST_GODUNOV = 0, 1
 
 _dp = C.POINTER(C.c_double)
 
@@ -46,6 +47,7 @@ class Config(C.Structure):
         ("eps", C.c_float),
         ("init_kind", C.c_int32), ("physics", C.c_int32), ("storage", C.c_int32),
         ("exec", C.c_int32), ("mobility_law", C.c_int32), ("device", C.c_int32),
+        ("redist", C.c_int32), ("reserved", C.c_int32),
         ("theta_max_deg", C.c_double), ("mob_low", C.c_double),
         ("lognormal_sigma", C.c_double), ("big_fraction", C.c_double), ("big_volume", C.c_double),
         ("field_dir", C.c_double * 3),
