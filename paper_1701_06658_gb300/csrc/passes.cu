@@ -1062,16 +1062,41 @@ p_god_sweep(StepBuffers B, const float* __restrict__ src, float* __restrict__ ds
         const int dxl = x > 0 ? -1 : (fx ? nx - 1 : 0), dxr = x < nx - 1 ? 1 : (fx ? 1 - nx : 0);
         const int dyl = y > 0 ? -nx : (fy ? (ny - 1) * nx : 0), dyr = y < ny - 1 ? nx : (fy ? (1 - ny) * nx : 0);
         const float inf = __int_as_float(0x7f800000);
-        for (int z = 0; z < nz; ++z) {
-            const long long o = o0 + (long long)z * ps;
-            const float v = src[o];
-            if (v < 0.0f) { dst[o] = v; continue; }
-            const float ax = fminf(dxl ? god_mag(src[o + dxl]) : inf, dxr ? god_mag(src[o + dxr]) : inf);
-            const float ay = fminf(dyl ? god_mag(src[o + dyl]) : inf, dyr ? god_mag(src[o + dyr]) : inf);
-            const int zm = z > 0 ? z - 1 : (fz ? nz - 1 : -1), zp = z < nz - 1 ? z + 1 : (fz ? 0 : -1);
-            const float az = fminf(zm >= 0 ? god_mag(src[o0 + (long long)zm * ps]) : inf,
-                                   zp >= 0 ? god_mag(src[o0 + (long long)zp * ps]) : inf);
-            dst[o] = fminf(v, fminf(eps, godunov_u(ax, ay, az)));
+        // batches of kZB planes: every load of a batch is issued before any use
+        // (indices clamped into the column, the values of absent neighbours
+        // replaced afterwards)
+        for (int z0 = 0; z0 < nz; z0 += kZB) {
+            float col[kZB + 2], xl[kZB], xr[kZB], yl[kZB], yr[kZB];
+#pragma unroll
+            for (int u = 0; u < kZB + 2; ++u) {
+                int z = z0 + u - 1;
+                const bool in = z >= 0 && z < nz;
+                if (!in && fz) z = z < 0 ? z + nz : z - nz;
+                const int zc = min(max(z, 0), nz - 1);
+                col[u] = src[o0 + (long long)zc * ps];
+                if (!in && !fz) col[u] = -16.0f;           // marker: no neighbour (encoded values are >= -2)
+            }
+#pragma unroll
+            for (int u = 0; u < kZB; ++u) {
+                const long long o = o0 + (long long)min(z0 + u, nz - 1) * ps;
+                xl[u] = src[o + dxl];
+                xr[u] = src[o + dxr];
+                yl[u] = src[o + dyl];
+                yr[u] = src[o + dyr];
+            }
+#pragma unroll
+            for (int u = 0; u < kZB; ++u) {
+                const int z = z0 + u;
+                if (z >= nz) break;
+                const float v = col[u + 1];
+                const long long o = o0 + (long long)z * ps;
+                if (v < 0.0f) { dst[o] = v; continue; }
+                const float ax = fminf(dxl ? god_mag(xl[u]) : inf, dxr ? god_mag(xr[u]) : inf);
+                const float ay = fminf(dyl ? god_mag(yl[u]) : inf, dyr ? god_mag(yr[u]) : inf);
+                const float zl = col[u] == -16.0f ? inf : god_mag(col[u]);
+                const float zr = col[u + 2] == -16.0f ? inf : god_mag(col[u + 2]);
+                dst[o] = fminf(v, fminf(eps, godunov_u(ax, ay, fminf(zl, zr))));
+            }
         }
     }
 }
