@@ -138,6 +138,23 @@ int lsgg_sync(lsgg_ctx* ctx, int64_t timeout_ms);
  * *n_out = n_grains.  Synchronises. */
 int lsgg_grain_volumes(lsgg_ctx* ctx, double* out, int64_t cap, int64_t* n_out);
 
+/* Grain statistics of the size analysis (Sec. 5), computed on the device from
+ * the grain volumes: the alive grains (V > 0), their mean volume, the mean,
+ * root-mean-square and largest equivalent radius R = (3 V / 4 pi)^(1/3)
+ * (3D; (V / pi)^(1/2) in 2D), and the distribution of R / <R> as fractions of
+ * the alive grains in n_bins equal bins over [0, r_max_rel) (hist, n_bins
+ * doubles; the fraction at or above r_max_rel in overflow).  Deterministic
+ * (fixed-order FP64 compensated sums, integer bin counts).  Synchronises. */
+typedef struct lsgg_grain_stats {
+    int64_t alive;
+    double mean_volume;
+    double mean_radius;
+    double rms_radius;
+    double max_radius;
+    double overflow;
+} lsgg_grain_stats;
+int lsgg_grain_statistics(lsgg_ctx* ctx, int32_t n_bins, double r_max_rel, lsgg_grain_stats* out, double* hist);
+
 /* owner(x) = argmax_i phi_i(x) over the boxes covering x, lowest id on ties,
  * -1 where no box covers x; x fastest, n_cells = nx*ny*nz int32s.  Synchronises. */
 int lsgg_voxel_owner(lsgg_ctx* ctx, int32_t* out, int64_t n_cells);

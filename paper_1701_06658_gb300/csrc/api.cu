@@ -24,6 +24,8 @@ cudaError_t launch_init(const Domain& D, int G, const SeedBins& bins, const doub
 cudaError_t launch_sdf(const Domain& D, int G, const Box* d_cur, const double* d_seeds, const double* d_weights,
                        const unsigned* d_bits, long long words_per_row, float* X, int* IDF, int* d_status,
                        cudaStream_t s);
+cudaError_t launch_grain_stats(const double* vol, int G, int dim, int n_bins, double r_max, double* out,
+                               double* hist, cudaStream_t s);
 cudaError_t launch_volumes(const Domain& D, int G, const Box* cur, const Box* prev, const float* X, double* out,
                            cudaStream_t s);
 cudaError_t launch_owner(const Domain& D, int G, const Box* cur, const Box* prev, const float* X,
@@ -1044,6 +1046,32 @@ int lsgg_grain_volumes(lsgg_ctx* c, double* out, int64_t cap, int64_t* n_out) {
     CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, x, c->d_vol, c->stream));
     CK(cudaMemcpyAsync(out, c->d_vol, (size_t)c->G * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return LSGG_OK;
+}
+
+int lsgg_grain_statistics(lsgg_ctx* c, int32_t n_bins, double r_max_rel, lsgg_grain_stats* out, double* hist) {
+    if (!c || !out || !hist || n_bins < 1 || n_bins > 4096 || !(r_max_rel > 0.0)) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    const float* x = nullptr;
+    CK(state_as_f32(c, &x));
+    CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, x, c->d_vol, c->stream));
+    double* d = nullptr;
+    if ((r = dalloc(c, &d, (size_t)n_bins + 6)) != LSGG_OK) return r;
+    cudaError_t e = launch_grain_stats(c->d_vol, c->G, c->dom.dim, n_bins, r_max_rel, d, d + 6, c->stream);
+    double h[6];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 6 * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hist, d + 6, (size_t)n_bins * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->device_bytes -= (long long)(n_bins + 6) * 8;
+    dfree(c, d);
+    if (e != cudaSuccess) return LSGG_ERR_CUDA;
+    out->alive = (int64_t)h[0];
+    out->mean_volume = h[1];
+    out->mean_radius = h[2];
+    out->rms_radius = h[3];
+    out->max_radius = h[4];
+    out->overflow = h[5];
     return LSGG_OK;
 }
 

@@ -209,4 +209,84 @@ cudaError_t launch_f32_to_state(const float* in, void* bf16_out, long long n, cu
     return cudaGetLastError();
 }
 
+// Grain statistics (Sec. 5's size analysis) from the volumes, one CTA:
+// per-thread partial sums over grains t, t + blockDim, ... in FP64, merged by
+// compensated additions in a fixed tree order; bins counted with integer
+// atomics (order-free); out = alive, mean V, mean R, rms R, max R, overflow.
+constexpr int kStatsThreads = 1024;
+constexpr int kStatsMaxBins = 4096;
+
+__global__ void __launch_bounds__(kStatsThreads)
+k_grain_stats(const double* __restrict__ vol, int G, int dim, int n_bins, double r_max, double* __restrict__ out,
+              double* __restrict__ hist) {
+    __shared__ double s_s[4][kStatsThreads], s_c[4][kStatsThreads];
+    __shared__ unsigned s_bins[kStatsMaxBins + 1];
+    const int t = threadIdx.x;
+    // 0: count, 1: sum V, 2: sum R, 3: sum R^2 (running compensated per thread)
+    double sum[4] = {0.0, 0.0, 0.0, 0.0}, comp[4] = {0.0, 0.0, 0.0, 0.0}, rmax = 0.0;
+    for (int k = t; k <= n_bins; k += blockDim.x) s_bins[k] = 0u;
+    for (int i = t; i < G; i += blockDim.x) {
+        const double v = vol[i];
+        if (!(v > 0.0)) continue;
+        const double r = dim == 3 ? cbrt(3.0 * v / (4.0 * 3.14159265358979323846)) : sqrt(v / 3.14159265358979323846);
+        const double x[4] = {1.0, v, r, r * r};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double s2, e;
+            two_sum(sum[q], x[q], s2, e);
+            sum[q] = s2;
+            comp[q] = __dadd_rn(comp[q], e);
+        }
+        rmax = fmax(rmax, r);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { s_s[q][t] = sum[q]; s_c[q][t] = comp[q]; }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double s2, e;
+                two_sum(s_s[q][t], s_s[q][t + o], s2, e);
+                s_s[q][t] = s2;
+                s_c[q][t] = __dadd_rn(__dadd_rn(s_c[q][t], s_c[q][t + o]), e);
+            }
+        }
+        __syncthreads();
+    }
+    __shared__ double s_max[kStatsThreads];
+    s_max[t] = rmax;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) s_max[t] = fmax(s_max[t], s_max[t + o]);
+        __syncthreads();
+    }
+    const double n = __dadd_rn(s_s[0][0], s_c[0][0]);
+    const double mean_r = n > 0.0 ? __dadd_rn(s_s[2][0], s_c[2][0]) / n : 0.0;
+    for (int i = t; i < G; i += blockDim.x) {
+        const double v = vol[i];
+        if (!(v > 0.0)) continue;
+        const double r = dim == 3 ? cbrt(3.0 * v / (4.0 * 3.14159265358979323846)) : sqrt(v / 3.14159265358979323846);
+        const double k = floor(r / mean_r / r_max * (double)n_bins);
+        atomicAdd(&s_bins[k < (double)n_bins ? (int)k : n_bins], 1u);
+    }
+    __syncthreads();
+    if (t == 0) {
+        out[0] = n;
+        out[1] = n > 0.0 ? __dadd_rn(s_s[1][0], s_c[1][0]) / n : 0.0;
+        out[2] = mean_r;
+        out[3] = n > 0.0 ? sqrt(__dadd_rn(s_s[3][0], s_c[3][0]) / n) : 0.0;
+        out[4] = s_max[0];
+        out[5] = n > 0.0 ? (double)s_bins[n_bins] / n : 0.0;
+    }
+    for (int k = t; k < n_bins; k += blockDim.x) hist[k] = n > 0.0 ? (double)s_bins[k] / n : 0.0;
+}
+
+cudaError_t launch_grain_stats(const double* vol, int G, int dim, int n_bins, double r_max, double* out,
+                               double* hist, cudaStream_t s) {
+    if (n_bins < 1 || n_bins > kStatsMaxBins) return cudaErrorInvalidValue;
+    k_grain_stats<<<1, kStatsThreads, 0, s>>>(vol, G, dim, n_bins, r_max, out, hist);
+    return cudaGetLastError();
+}
+
 }  // namespace lsgg

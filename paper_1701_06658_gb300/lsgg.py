@@ -66,6 +66,12 @@ class Stats(C.Structure):
     ]
 
 
+class GrainStats(C.Structure):
+    """Mirror of ``lsgg_grain_stats``."""
+    _fields_ = [("alive", C.c_int64), ("mean_volume", C.c_double), ("mean_radius", C.c_double),
+                ("rms_radius", C.c_double), ("max_radius", C.c_double), ("overflow", C.c_double)]
+
+
 class LsggError(RuntimeError):
     def __init__(self, fn: str, code: int):
         self.code = code
@@ -82,6 +88,7 @@ _SIGS = {
     "lsgg_sync": (C.c_int, [C.c_void_p, C.c_int64]),
     "lsgg_grain_volumes": (C.c_int, [C.c_void_p, _dp, C.c_int64, C.POINTER(C.c_int64)]),
     "lsgg_voxel_owner": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
+    "lsgg_grain_statistics": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(GrainStats), _dp]),
     "lsgg_destroy": (C.c_int, [C.c_void_p]),
     "lsgg_status_string": (C.c_char_p, [C.c_int]),
     "lsgg_get_stream": (C.c_void_p, [C.c_void_p]),
@@ -184,6 +191,17 @@ def grain_volumes(ctx, n_grains: int, out=None) -> np.ndarray:
     out = np.zeros(n_grains, dtype=np.float64) if out is None else out
     n = C.c_int64()
     _check("grain_volumes", lib().lsgg_grain_volumes(ctx, _ptr(out, C.c_double), out.size, C.byref(n)))
+    return out
+
+
+def grain_statistics(ctx, n_bins: int = 20, r_max: float = 3.0) -> dict:
+    """Device-computed grain statistics (see lsgg.h): a dict of the struct's
+    fields plus the R / <R> histogram."""
+    st = GrainStats()
+    hist = np.zeros(n_bins, np.float64)
+    _check("grain_statistics", lib().lsgg_grain_statistics(ctx, n_bins, r_max, C.byref(st), _ptr(hist, C.c_double)))
+    out = {f: getattr(st, f) for f, _ in GrainStats._fields_}
+    out["hist"] = hist
     return out
 
 
@@ -396,6 +414,9 @@ class Microstructure:
 
     def voxel_owner(self) -> np.ndarray:
         return voxel_owner(self.ctx, self.shape)
+
+    def grain_statistics(self, n_bins: int = 20, r_max: float = 3.0) -> dict:
+        return grain_statistics(self.ctx, n_bins, r_max)
 
     def boxes(self) -> np.ndarray:
         return get_boxes(self.ctx, self.n_grains)

@@ -383,3 +383,25 @@ def test_godunov_multistep_volumes(L):
     alive = want > 1.0
     assert np.max(np.abs(vol[alive] - want[alive]) / want[alive]) < 1e-3
     assert (own >= 0).all()
+
+
+def test_grain_statistics_on_device(L):
+    """The device statistics equal the oracle's definition evaluated on the
+    device's own volumes (to rounding), and on the oracle's volumes after the
+    20-step run (to the 0.1 % volume tolerance)."""
+    N, G = 64, 50
+    seeds = I.voronoi_seeds(1, G, (N, N, N))
+    with L.Microstructure(N, N, N, G, seeds=seeds) as ms:
+        ms.step(20, 1.0)
+        st = ms.grain_statistics(16, 2.5)
+        vol = ms.grain_volumes()
+    want = O.grain_statistics(vol, 3, 16, 2.5)
+    assert st["alive"] == want["alive"]
+    for k in ("mean_volume", "mean_radius", "rms_radius", "max_radius", "overflow"):
+        assert abs(st[k] - want[k]) <= 1e-12 * max(1.0, abs(want[k])), k
+    assert np.array_equal(st["hist"], want["hist"])
+    ref = O.run(O.tessellate((N, N, N), seeds), 20, 1.0)
+    ow = O.grain_statistics(O.volumes(ref), 3, 16, 2.5)
+    assert st["alive"] == ow["alive"]
+    assert abs(st["mean_radius"] - ow["mean_radius"]) / ow["mean_radius"] < 1e-3
+

@@ -651,3 +651,24 @@ def test_splitmix64_reference_values():
     """SplitMix64 from seed 0: published first outputs of the generator."""
     got = [int(v) for v in I.u64(0, np.arange(3))]
     assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+# ---------------------------------------------------------------- grain statistics
+
+def test_grain_statistics_closed_forms(oracle):
+    """Equal spheres: <R> = R, rms = R, all in the bin of R / <R> = 1; two
+    sizes in 2D: the equivalent radii of the disc areas and their mean; extinct
+    (V = 0) grains are not counted; ratios at or above r_max overflow."""
+    r0 = 4.0
+    v = np.array([4.0 / 3.0 * math.pi * r0 ** 3] * 5 + [0.0, 0.0])
+    st = oracle.grain_statistics(v, 3, 10, 2.0)
+    assert st["alive"] == 5
+    assert abs(st["mean_radius"] - r0) < 1e-12 and abs(st["rms_radius"] - r0) < 1e-12
+    assert st["hist"][5] == 1.0 and st["hist"].sum() == 1.0 and st["overflow"] == 0.0
+    a = np.array([math.pi * 1.0, math.pi * 9.0, 0.0])             # discs of radius 1 and 3
+    st = oracle.grain_statistics(a, 2, 4, 1.4)
+    assert st["alive"] == 2 and abs(st["mean_radius"] - 2.0) < 1e-12
+    assert abs(st["rms_radius"] - math.sqrt(5.0)) < 1e-12 and st["max_radius"] == 3.0
+    assert st["hist"][1] == 0.5 and st["overflow"] == 0.5         # 0.5 in [0.35, 0.7); 1.5 >= 1.4
+    assert abs(st["mean_volume"] - 5.0 * math.pi) < 1e-12
+
