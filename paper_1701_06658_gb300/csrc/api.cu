@@ -977,6 +977,9 @@ int lsgg_set_state(lsgg_ctx* c, const int32_t* boxes, const float* phi, const in
     }
     if (need > c->B.cap && (r = grow_arena(c, need)) != LSGG_OK) return r;
     CK(cudaMemcpy(c->B.cur, hb.data(), (size_t)c->G * sizeof(Box), cudaMemcpyHostToDevice));
+    // the state will live in this layout: `prev` equal to `cur` already for the
+    // size classes the layout assigns (the same as any later relayout's)
+    CK(cudaMemcpy(c->B.prev, hb.data(), (size_t)c->G * sizeof(Box), cudaMemcpyHostToDevice));
     if ((r = relayout(c)) != LSGG_OK) return r;
     float* dphi = nullptr;
     int* didf = nullptr;
