@@ -762,10 +762,21 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
     cudaEvent_t* bin_ev = pass_ev ? pass_ev + 6 * kTiers : nullptr;
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e;
+    // binning reads only the boxes and writes only the tile lists and the
+    // bounds the re-initialisation collects: with side streams it runs beside
+    // the convolution passes and joins before the field pass
+    static_assert(kTiers <= kNumClasses, "a side stream for the binning beside the tiers' ones");
+    cudaStream_t bs = ss && B.use_passes ? ss->side[kTiers - 1] : s;
     if (B.use_passes) {                 // the field pass stores every cell of T: no clear
+        if (bs != s) {
+            e = traced(cudaEventRecord(ss->fork, s), "fork record");
+            if (e == cudaSuccess) e = traced(cudaStreamWaitEvent(bs, ss->fork, 0), "fork wait");
+            if (e != cudaSuccess) return e;
+        }
         if (bin_ev) cudaEventRecord(bin_ev[0], s);
-        e = traced(launch_bin(B, s), "tile binning");
+        e = traced(launch_bin(B, bs), "tile binning");
         if (bin_ev) cudaEventRecord(bin_ev[1], s);
+        if (e == cudaSuccess && bs != s) e = traced(cudaEventRecord(ss->join[kTiers - 1], bs), "join record");
     } else {
         e = traced(cudaMemsetAsync(B.T, 0, (size_t)ncell * 16, s), "field clear");
     }
@@ -796,8 +807,11 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
             joined[k] = true;
             return traced(cudaEventRecord(ss->join[k], cs), "join record");
         };
-        // pass-path tiers run one after the other on the step's stream: each
-        // pass is a persistent grid that fills the GPU by itself
+        // pass-path tiers: a tier's passes touch only its own boxes, so with
+        // side streams (graph replay) tiers 1.. run on side streams beside
+        // tier 0 and the small tiers' launches and every pass's tail overlap
+        // the others; profiled steps (no side streams) run them one after
+        // another so that each event time is one kernel's
         if (B.use_passes && which == 1 && B.godunov) {
             // Godunov re-initialisation over all tiers at once; its time is
             // reported as tier 0's re-initialisation passes
@@ -812,11 +826,23 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
                     for (int k = 0; k < 3; ++k) cudaEventRecord(pass_ev[t * 6 + 3 + k], s);
             }
         } else if (B.use_passes) {
+            static_assert(kTiers - 1 <= kNumClasses, "a side stream per tier beyond the first");
             for (int t = 0; t < kTiers; ++t) {
+                cudaStream_t ts = s;
+                if (ss && t > 0) {
+                    ts = ss->side[t - 1];
+                    cudaError_t r = traced(cudaStreamWaitEvent(ts, ss->fork, 0), "fork wait");
+                    if (r != cudaSuccess) return r;
+                }
                 cudaError_t r = traced(
-                    launch_passes(B, which, t, taps, phys, d, s, pass_ev ? pass_ev + t * 6 + (which ? 3 : 0) : nullptr),
+                    launch_passes(B, which, t, taps, phys, d, ts, pass_ev ? pass_ev + t * 6 + (which ? 3 : 0) : nullptr),
                     "pass kernels");
                 if (r != cudaSuccess) return r;
+                if (ss && t > 0) {
+                    r = traced(cudaEventRecord(ss->join[t - 1], ts), "join record");
+                    if (r == cudaSuccess) r = traced(cudaStreamWaitEvent(s, ss->join[t - 1], 0), "join wait");
+                    if (r != cudaSuccess) return r;
+                }
             }
         }
         for (int c = 0; c < kNumClasses; ++c) {
@@ -843,6 +869,10 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
     e = run_phase(0);
     if (e != cudaSuccess) return e;
     if (B.use_passes) {
+        if (bs != s) {
+            e = traced(cudaStreamWaitEvent(s, ss->join[kTiers - 1], 0), "join wait");
+            if (e != cudaSuccess) return e;
+        }
         if (bin_ev) cudaEventRecord(bin_ev[2], s);
         e = traced(launch_field(B, phys, d, s), "field pass");
         if (e != cudaSuccess) return e;
