@@ -447,26 +447,46 @@ k_bin(StepBuffers B) {
 // ---------------------------------------------------------------------------
 // Thread (x, y) of a tile owns the column of kTileZ cells at (x, y); for each
 // box covering the column it loads the box's phi_p there and keeps the two
-// largest keys (phi_p, -id) per cell in registers -- the same order as the
-// box-streaming kernels' atomicMax field, so m and the ID-field are identical.
-// Per listed box the CTA first stages, in shared memory, the box-local
-// coordinates of the tile's corner and the mask of the tile's planes the box
-// covers, so the per-thread work is a compare per column and a load per cell.
+// largest (phi_p, grain) pairs per cell in registers, ordered by phi_p and,
+// at equal phi_p, by the smaller grain id first -- the order of the
+// box-streaming kernels' 64-bit keys (phi_p, -id) under atomicMax, so m and
+// the ID-field are identical.  Per listed box the CTA first stages, in shared
+// memory, how the tile maps into the box: on an axis where the box's cells
+// in the tile keep one box-local offset (all but boxes spanning nearly the
+// whole domain), the mask of the tile's rows / columns / planes it covers
+// and one arena offset for the tile's corner, so that the per-thread work is
+// a mask test per column and an add per cell; other boxes take the general
+// cyclic path.
 struct TileBox {
-    long long off;            // arena offset of the box
+    long long off;            // affine: arena offset of tile cell (0, 0, 0); general: of the box
     int nx, ny;               // box x, y sides
-    int dx, dy;               // box-local x, y of the tile corner (cyclic)
     int ps;                   // plane stride
     int id;                   // grain id
-    int dz;                   // box-local z of the tile's first plane (cyclic)
-    unsigned zmask;           // bit zz: plane zz of the tile lies in the box
+    unsigned ymask;           // affine: bit ly: row ly of the tile lies in the box
+    unsigned xzm;             // bits 0-7: columns (affine), 8-15: planes (both), bit 31: affine
+    int dx, dy, dz;           // general: box-local coordinates of the tile corner (cyclic)
+    int pad;
 };
 
-__device__ __forceinline__ void stage_tile_box(const StepBuffers& B, int b, int tx0, int ty0, int z0, int nzt,
-                                               TileBox& t) {
+// One axis of the tile -> box map: tile cells l in [0, T) with box-local
+// coordinate l + sh, covered where 0 <= l + sh < n.  False when the box's
+// cells in the tile do not share one offset (the uncovered gap of a box
+// spanning nearly the whole axis lies inside the tile).
+__device__ __forceinline__ bool tile_axis(int t0, int T, int N, int o, int n, int& sh, unsigned& mask) {
+    int d = t0 - o;
+    if (d < 0) d += N;
+    if (d < n && N - d < T) return false;
+    sh = d < n ? d : d - N;
+    const int lo = max(0, -sh), hi = min(T, n - sh);
+    const int w = hi - lo;
+    mask = w <= 0 ? 0u : (w >= 32 ? 0xffffffffu : (1u << w) - 1u) << lo;
+    return true;
+}
+
+__device__ __forceinline__ void stage_tile_box(const StepBuffers& B, int b, int tx0, int ty0, int z0, int ntx, int nty,
+                                               int nzt, TileBox& t) {
     const Domain& D = B.dom;
     const Box bx = B.cur[b];
-    t.off = bx.off;
     t.nx = bx.nx;
     t.ny = bx.ny;
     t.id = b;
@@ -474,16 +494,44 @@ __device__ __forceinline__ void stage_tile_box(const StepBuffers& B, int b, int 
     t.dx = wrap_near(tx0 - bx.ox, D.nx);
     t.dy = wrap_near(ty0 - bx.oy, D.ny);
     t.dz = wrap_near(z0 - bx.oz, D.nz);
+    int sx, sy, sz;
+    unsigned mx, my, mz;
+    if (bx.nx <= 0) {
+        t.off = 0;
+        t.ymask = 0;
+        t.xzm = 1u << 31;                   // affine and empty
+        return;
+    }
+    if (tile_axis(tx0, ntx, D.nx, bx.ox, bx.nx, sx, mx) && tile_axis(ty0, nty, D.ny, bx.oy, bx.ny, sy, my) &&
+        tile_axis(z0, nzt, D.nz, bx.oz, bx.nz, sz, mz)) {
+        t.off = bx.off + (long long)sz * t.ps + (long long)sy * bx.nx + sx;
+        t.ymask = my;
+        t.xzm = (1u << 31) | (mz << 8) | mx;
+        return;
+    }
     unsigned m = 0;
-    if (bx.nx > 0)
-        for (int zz = 0; zz < nzt; ++zz) {
-            int lz = t.dz + zz;
-            if (lz >= D.nz) lz -= D.nz;
-            if (lz < bx.nz) m |= 1u << zz;
-        }
-    t.zmask = m;
+    for (int zz = 0; zz < nzt; ++zz) {
+        int lz = t.dz + zz;
+        if (lz >= D.nz) lz -= D.nz;
+        if (lz < bx.nz) m |= 1u << zz;
+    }
+    t.off = bx.off;
+    t.ymask = 0;
+    t.xzm = m << 8;
 }
 
+// (v, id) enters the top two (v1, i1) >= (v2, i2) of a cell; absent entries
+// are (-inf, -1), and v = -inf never enters.
+__device__ __forceinline__ void top2_insert(float v, int id, float& v1, int& i1, float& v2, int& i2) {
+    const bool c1 = v > v1 || (v == v1 && id < i1);
+    const bool c2 = v > v2 || (v == v2 && id < i2);
+    v2 = c1 ? v1 : (c2 ? v : v2);
+    i2 = c1 ? i1 : (c2 ? id : i2);
+    v1 = c1 ? v : v1;
+    i1 = c1 ? id : i1;
+}
+
+template <bool IDF, bool DBG>
 __global__ void __launch_bounds__(kTileX * kTileY, 3)
 p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
     __shared__ TileBox s_tb[kTileCap];
@@ -497,29 +545,28 @@ p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
         const int tx0 = tx * kTileX, ty0 = ty * kTileY, z0 = tz * kTileZ;
         const int x = tx0 + lx, y = ty0 + ly;
         const bool col = x < D.nx && y < D.ny;
+        const int ext_x = min(kTileX, D.nx - tx0), ext_y = min(kTileY, D.ny - ty0);
         const int nzt = min(kTileZ, D.nz - z0);
         const int cnt = B.tile_cnt[tile];
         const bool all = cnt > kTileCap;            // list overflowed: test every box in batches
         const int n_total = all ? B.n_boxes : cnt;
-        unsigned long long k1[kTileZ], k2[kTileZ];
-#pragma unroll
-        for (int zz = 0; zz < kTileZ; ++zz) { k1[zz] = 0ull; k2[zz] = 0ull; }
-        // the top-2 decoded once for sweep 1: the other grains' max is v1 unless
-        // the box is the top one (then v2); absent keys read -eps and id -1
-        float v1[kTileZ], v2[kTileZ];
+        float v1[kTileZ], v2[kTileZ], w1[kTileZ], w2[kTileZ];
         int i1[kTileZ], i2[kTileZ];
-        // two sweeps over the tile's boxes: 0 builds the top-2, 1 writes phi_c
+#pragma unroll
+        for (int zz = 0; zz < kTileZ; ++zz) { v1[zz] = v2[zz] = -INFINITY; i1[zz] = i2[zz] = -1; }
+        // two sweeps over the tile's boxes: 0 builds the top two, 1 writes phi_c
 #pragma unroll
         for (int sweep = 0; sweep < 2; ++sweep) {
             if (sweep == 1) {
                 ulonglong2* T2 = reinterpret_cast<ulonglong2*>(B.T);
 #pragma unroll
                 for (int zz = 0; zz < kTileZ; ++zz) {
-                    if (col && zz < nzt) T2[((long long)(z0 + zz) * D.ny + y) * D.nx + x] = make_ulonglong2(k1[zz], k2[zz]);
-                    v1[zz] = key_val(k1[zz], eps);
-                    v2[zz] = key_val(k2[zz], eps);
-                    i1[zz] = key_id(k1[zz]);
-                    i2[zz] = key_id(k2[zz]);
+                    if (col && zz < nzt)
+                        T2[((long long)(z0 + zz) * D.ny + y) * D.nx + x] =
+                            make_ulonglong2(i1[zz] >= 0 ? make_key(v1[zz], i1[zz]) : 0ull,
+                                            i2[zz] >= 0 ? make_key(v2[zz], i2[zz]) : 0ull);
+                    w1[zz] = i1[zz] >= 0 ? v1[zz] + 0.0f : -eps;
+                    w2[zz] = i2[zz] >= 0 ? v2[zz] + 0.0f : -eps;
                 }
             }
             for (int base = 0; base < n_total; base += kTileCap) {
@@ -527,52 +574,65 @@ p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
                 __syncthreads();                    // previous batch done with s_tb
                 for (int k = threadIdx.x; k < nb; k += blockDim.x) {
                     const int b = all ? base + k : B.tile_list[(long long)tile * kTileCap + k];
-                    stage_tile_box(B, b, tx0, ty0, z0, nzt, s_tb[k]);
+                    stage_tile_box(B, b, tx0, ty0, z0, ext_x, ext_y, nzt, s_tb[k]);
                 }
                 __syncthreads();
                 if (!col) continue;
                 for (int k = 0; k < nb; ++k) {
                     const TileBox& t = s_tb[k];
-                    if (!t.zmask) continue;
-                    int bxl = t.dx + lx, byl = t.dy + ly;
-                    if (bxl >= D.nx) bxl -= D.nx;
-                    if (byl >= D.ny) byl -= D.ny;
-                    if (bxl >= t.nx || byl >= t.ny) continue;
-                    const long long o0 = t.off + (long long)byl * t.nx + bxl;
-                    const float* src = B.Y + o0;
-                    const unsigned zm = t.zmask;
-                    const int ps = t.ps, dz = t.dz;
-                    float v[kTileZ];
+                    const unsigned xzm = t.xzm;
+                    const unsigned zm = (xzm >> 8) & 0xffu;
+                    const int id = t.id, ps = t.ps;
+                    long long o[kTileZ];                // arena offsets of the column's cells
+                    if (xzm >> 31) {                    // affine (uniform across the CTA)
+                        if (!((xzm >> lx) & (t.ymask >> ly) & 1u)) continue;
+                        const long long oc = t.off + (long long)(ly * t.nx + lx);
 #pragma unroll
-                    for (int zz = 0; zz < kTileZ; ++zz) {
-                        int lz = dz + zz;
-                        if (lz >= D.nz) lz -= D.nz;
-                        v[zz] = (zm >> zz) & 1u ? src[lz * ps] : 0.0f;
-                    }
-                    if (sweep == 0) {
-                        const unsigned lo = 0xffffffffu - (unsigned)t.id;
+                        for (int zz = 0; zz < kTileZ; ++zz) o[zz] = oc + (long long)zz * ps;
+                    } else {
+                        if (!zm) continue;
+                        int bxl = t.dx + lx, byl = t.dy + ly;
+                        if (bxl >= D.nx) bxl -= D.nx;
+                        if (byl >= D.ny) byl -= D.ny;
+                        if (bxl >= t.nx || byl >= t.ny) continue;
+                        const long long oc = t.off + (long long)byl * t.nx + bxl;
 #pragma unroll
                         for (int zz = 0; zz < kTileZ; ++zz) {
-                            if (!((zm >> zz) & 1u)) continue;
-                            const unsigned long long key = ((unsigned long long)ord_float(v[zz]) << 32) | lo;
-                            if (key > k1[zz]) { k2[zz] = k1[zz]; k1[zz] = key; }
-                            else if (key > k2[zz]) k2[zz] = key;
+                            int lz = t.dz + zz;
+                            if (lz >= D.nz) lz -= D.nz;
+                            o[zz] = oc + (long long)lz * ps;
                         }
+                    }
+                    float v[kTileZ];
+                    if (zm == 0xffu) {                  // the whole column (uniform)
+#pragma unroll
+                        for (int zz = 0; zz < kTileZ; ++zz) v[zz] = B.Y[o[zz]];
+                    } else {
+#pragma unroll
+                        for (int zz = 0; zz < kTileZ; ++zz) v[zz] = (zm >> zz) & 1u ? B.Y[o[zz]] : -INFINITY;
+                    }
+                    if (sweep == 0) {
+#pragma unroll
+                        for (int zz = 0; zz < kTileZ; ++zz) top2_insert(v[zz], id, v1[zz], i1[zz], v2[zz], i2[zz]);
                     } else {
 #pragma unroll
                         for (int zz = 0; zz < kTileZ; ++zz) {
                             if (!((zm >> zz) & 1u)) continue;
-                            int lz = dz + zz;
-                            if (lz >= D.nz) lz -= D.nz;
-                            const long long o = o0 + (long long)lz * ps;
-                            const bool top = i1[zz] == t.id;
-                            const float m = top ? v2[zz] : v1[zz];
-                            int mid = top ? i2[zz] : i1[zz];
-                            if (!(m > -eps)) mid = -1;
+                            const bool top = i1[zz] == id;
+                            const float m = top ? w2[zz] : w1[zz];
                             const float pc = 0.5f * (v[zz] - m);
-                            B.Z[o] = pc;
-                            if (phys.kind != LSGG_PHYSICS_IDEAL) B.IDF[o] = mid;
-                            if (dbg.m) { dbg.m[o] = m; dbg.idm[o] = mid; dbg.phic[o] = pc; dbg.phip[o] = v[zz]; }
+                            B.Z[o[zz]] = pc;
+                            if (IDF || DBG) {
+                                int mid = top ? i2[zz] : i1[zz];
+                                if (!(m > -eps)) mid = -1;
+                                if (IDF) B.IDF[o[zz]] = mid;
+                                if (DBG) {
+                                    dbg.m[o[zz]] = m;
+                                    dbg.idm[o[zz]] = mid;
+                                    dbg.phic[o[zz]] = pc;
+                                    dbg.phip[o[zz]] = v[zz];
+                                }
+                            }
                         }
                     }
                 }
@@ -1387,7 +1447,7 @@ cudaError_t configure_passes(StepBuffers& B) {
         for (int k = 0; k < 5; ++k) B.pgrid[t][k] = B.n_sm * (o[k] < 1 ? 1 : o[k]);
     }
     int of = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field, kTileX * kTileY, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field<false, false>, kTileX * kTileY, 0);
     if (e != cudaSuccess) return e;
     B.field_grid = B.n_sm * (of < 1 ? 1 : of);
     B.bin_grid = B.n_sm;
@@ -1445,7 +1505,9 @@ cudaError_t launch_bin(const StepBuffers& B, cudaStream_t s) {
 }
 
 cudaError_t launch_field(const StepBuffers& B, const PhysicsDev& phys, const DebugOut& dbg, cudaStream_t s) {
-    p_field<<<B.field_grid, kTileX * kTileY, 0, s>>>(B, phys, dbg);
+    const bool idf = phys.kind != LSGG_PHYSICS_IDEAL, dg = dbg.m != nullptr;
+    auto k = idf ? (dg ? p_field<true, true> : p_field<true, false>) : (dg ? p_field<false, true> : p_field<false, false>);
+    k<<<B.field_grid, kTileX * kTileY, 0, s>>>(B, phys, dbg);
     return cudaGetLastError();
 }
 
