@@ -186,7 +186,7 @@ struct StepBuffers {
     int* tile_list;                 // [n_tiles * kTileCap]
     int ntile[3];
     int n_tiles;
-    int field_grid, bin_grid;
+    int field_grid[2], bin_grid;      // field grid: plain / ID-field and debug variants
 };
 
 // Element i of the state arena X as FP32, and its store (round to nearest

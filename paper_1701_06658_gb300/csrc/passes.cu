@@ -63,9 +63,11 @@ __device__ __forceinline__ float conv_xy_of_const(const float (&g)[2 * R + 1], f
 //           16-byte aligned) arrives in a raw slot by a bulk copy, issued
 //           while the CTA still works on the item before;
 //   stage   raw -> padded grid P in the new layout (-eps outside the old
-//           box), warps over rows and lanes along x;
+//           box), warps over rows and lanes along x; rows outside the old
+//           box are left unstaged;
 //   x pass  each thread convolves 4 consecutive cells of one padded row from
-//           16-byte shared loads -> grid XC (all padded rows);
+//           16-byte shared loads -> grid XC (all padded rows; a row outside
+//           the old box is the FMA chain over -eps, written directly);
 //   y pass  each thread convolves 4 consecutive rows of one column from
 //           shared loads of XC and stores them (lanes along x: coalesced).
 // The FMA order of both passes is the one conv_xy_of_const repeats.  Every
@@ -95,6 +97,7 @@ __device__ __forceinline__ void stage_plane(const T* raw, float* P, const int* m
         const int my = mapy[yp];
         const T* rrow = raw + (my < 0 ? 0 : my) * onx;
         const bool row_in = have && my >= 0;
+        if (!row_in) continue;                    // a fill row: the x pass writes its result unstaged
         float* prow = P + yp * PX;
         for (int xp = lane; xp < PXa; xp += 32) {
             const int mx = mapx[xp];
@@ -220,8 +223,15 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         const int ngx = (nx + 3) >> 2;
         {
             const Div16 dgx(ngx);
+            float cfill = 0.0f;
+#pragma unroll
+            for (int k = 0; k < W; ++k) cfill = fmaf(g[k], -D.eps, cfill);
             for (int j = t; j < PYa * ngx; j += NT) {
                 const int yp = dgx(j), x0 = 4 * (j - yp * ngx);
+                if (!have || mapy[yp] < 0) {                // a fill row: the chain over -eps, unstaged
+                    *reinterpret_cast<float4*>(XC + yp * LY::XP + x0) = make_float4(cfill, cfill, cfill, cfill);
+                    continue;
+                }
                 const float4* r4 = reinterpret_cast<const float4*>(P + yp * LY::PX + x0);
                 float v[4 * LY::NQ];
 #pragma unroll
@@ -531,8 +541,10 @@ __device__ __forceinline__ void top2_insert(float v, int id, float& v1, int& i1,
     i1 = c1 ? id : i1;
 }
 
+// Four CTAs per SM for the plain field; the ID-field and debug variants keep
+// the registers of three.
 template <bool IDF, bool DBG>
-__global__ void __launch_bounds__(kTileX * kTileY, 3)
+__global__ void __launch_bounds__(kTileX * kTileY, (IDF || DBG) ? 3 : 4)
 p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
     __shared__ TileBox s_tb[kTileCap];
     if (halted(B)) return;
@@ -837,10 +849,18 @@ p_redist_xy(StepBuffers B, int tier) {
                 const int y = dnx(i), x = i - y * nx;
                 const float v = Pc[i];
                 const bool pos = v > 0.0f;
-                const float xl = x > 0 ? Pc[i - 1] : (fx ? Pc[i + nx - 1] : -eps);
-                const float xr = x < nx - 1 ? Pc[i + 1] : (fx ? Pc[i - nx + 1] : -eps);
-                const float yl = y > 0 ? Pc[i - nx] : (fy ? Pc[i + n - nx] : -eps);
-                const float yr = y < ny - 1 ? Pc[i + nx] : (fy ? Pc[i - n + nx] : -eps);
+                float xl = -eps, xr = -eps, yl = -eps, yr = -eps;
+                if (!(fx || fy)) {                          // uniform: the box lies inside the domain
+                    if (x > 0) xl = Pc[i - 1];
+                    if (x < nx - 1) xr = Pc[i + 1];
+                    if (y > 0) yl = Pc[i - nx];
+                    if (y < ny - 1) yr = Pc[i + nx];
+                } else {
+                    xl = x > 0 ? Pc[i - 1] : (fx ? Pc[i + nx - 1] : -eps);
+                    xr = x < nx - 1 ? Pc[i + 1] : (fx ? Pc[i - nx + 1] : -eps);
+                    yl = y > 0 ? Pc[i - nx] : (fy ? Pc[i + n - nx] : -eps);
+                    yr = y < ny - 1 ? Pc[i + nx] : (fy ? Pc[i - n + nx] : -eps);
+                }
                 mag[k] = ref_magnitude(fabsf(v), opp_max(pos, xl, xr), opp_max(pos, yl, yr),
                                        opp_max(pos, Pm[i], Pp[i]), eps);
             }
@@ -1449,7 +1469,10 @@ cudaError_t configure_passes(StepBuffers& B) {
     int of = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field<false, false>, kTileX * kTileY, 0);
     if (e != cudaSuccess) return e;
-    B.field_grid = B.n_sm * (of < 1 ? 1 : of);
+    B.field_grid[0] = B.n_sm * (of < 1 ? 1 : of);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field<true, false>, kTileX * kTileY, 0);
+    if (e != cudaSuccess) return e;
+    B.field_grid[1] = B.n_sm * (of < 1 ? 1 : of);
     B.bin_grid = B.n_sm;
     const int tsz[3] = {kTileX, kTileY, kTileZ};
     const int dn[3] = {B.dom.nx, B.dom.ny, B.dom.nz};
@@ -1507,7 +1530,7 @@ cudaError_t launch_bin(const StepBuffers& B, cudaStream_t s) {
 cudaError_t launch_field(const StepBuffers& B, const PhysicsDev& phys, const DebugOut& dbg, cudaStream_t s) {
     const bool idf = phys.kind != LSGG_PHYSICS_IDEAL, dg = dbg.m != nullptr;
     auto k = idf ? (dg ? p_field<true, true> : p_field<true, false>) : (dg ? p_field<false, true> : p_field<false, false>);
-    k<<<B.field_grid, kTileX * kTileY, 0, s>>>(B, phys, dbg);
+    k<<<B.field_grid[idf || dg ? 1 : 0], kTileX * kTileY, 0, s>>>(B, phys, dbg);
     return cudaGetLastError();
 }
 
