@@ -72,19 +72,44 @@ __device__ __forceinline__ float conv_xy_of_const(const float (&g)[2 * R + 1], f
 //           shared loads of XC and stores them (lanes along x: coalesced).
 // The FMA order of both passes is the one conv_xy_of_const repeats.  Every
 // wait on a copy is bounded (LSGG_ERR_TIMEOUT, halt, drain, return).
+//
+// The sizes below are the one definition of the layout: the kernel's
+// offsets and the launch's dynamic shared-memory size both derive from them.
+// padded rows; 16-byte loads per x window of 4 outputs; pitch of P (room for
+// the last group's window); pitch of XC; rows of XC (3 spare rows)
+__host__ __device__ constexpr int conv_pyr(int R, int side) { return side + 2 * R; }
+__host__ __device__ constexpr int conv_nq(int R) { return (2 * R + 1 + 6) / 4; }
+__host__ __device__ constexpr int conv_px(int R, int side) { return ((side + 3) & ~3) + 4 * conv_nq(R); }
+__host__ __device__ constexpr int conv_xp(int side) { return (side + 3) & ~3; }
+__host__ __device__ constexpr int conv_xr(int R, int side) { return conv_pyr(R, side) + 3; }
+__host__ __device__ constexpr size_t conv_layout_bytes(int R, int side) {
+    return 128 + sizeof(float) * ((size_t)side * side + (size_t)conv_pyr(R, side) * conv_px(R, side) +
+                                  (size_t)conv_xr(R, side) * conv_xp(side)) +
+           sizeof(int) * 2 * (size_t)conv_pyr(R, side);
+}
 template <int R, int SIDE>
 struct ConvXYLayout {
-    static constexpr int PYR = SIDE + 2 * R;                  // padded rows
-    static constexpr int NQ = (2 * R + 1 + 6) / 4;            // 16-byte loads per x window of 4 outputs
-    static constexpr int PX = ((SIDE + 3) & ~3) + 4 * NQ;     // pitch of P: room for the last group's window
-    static constexpr int XP = (SIDE + 3) & ~3;                // pitch of XC
-    static constexpr int XR = PYR + 3;                        // rows of XC (3 spare for the last 4-row group)
+    static constexpr int PYR = conv_pyr(R, SIDE);
+    static constexpr int NQ = conv_nq(R);
+    static constexpr int PX = conv_px(R, SIDE);              // room for the last group's window
+    static constexpr int XP = conv_xp(SIDE);
+    static constexpr int XR = conv_xr(R, SIDE);              // the last 4-row group reads 3 rows past PYR
     static constexpr size_t raw = 128;                        // after the barrier
     static constexpr size_t P = raw + sizeof(float) * SIDE * SIDE;
     static constexpr size_t XC = P + sizeof(float) * PYR * PX;
     static constexpr size_t maps = XC + sizeof(float) * XR * XP;
     static constexpr size_t bytes = maps + sizeof(int) * 2 * PYR;
+    static_assert(bytes == conv_layout_bytes(R, SIDE), "one definition of the layout");
 };
+
+// Dynamic shared memory of the running launch: the plane kernels refuse to
+// run (LSGG_ERR_UNSUPPORTED) rather than index past a launch that got less
+// than their layout.
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
 
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -132,9 +157,15 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
     __shared__ int s_flag;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-        s_flag = halted(B);
+        const bool fits = dyn_smem_bytes() >= LY::bytes;
+        if (fits) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        } else {
+            atomicExch(&B.st->status, LSGG_ERR_UNSUPPORTED);
+            atomicExch(&B.st->halt, 1);
+        }
+        s_flag = !fits || halted(B);
     }
     __syncthreads();
     if (s_flag) return;
@@ -750,6 +781,10 @@ __device__ __forceinline__ void scan_line_seg(float* line, int n, int st, int se
 // are put back as the plane is stored with 16-byte stores.  Every wait on a
 // copy is bounded: on expiry the CTA records LSGG_ERR_TIMEOUT, halts the step,
 // drains its copies (bounded) and returns.
+__host__ __device__ constexpr size_t redist_layout_bytes(int side) {     // barriers, 3 plane slots, G
+    return 128 + (size_t)(3 * side * side + side * (side + 1)) * sizeof(float);
+}
+
 template <int SIDE, int NT>
 __global__ void __launch_bounds__(NT)
 p_redist_xy(StepBuffers B, int tier) {
@@ -759,16 +794,23 @@ p_redist_xy(StepBuffers B, int tier) {
     constexpr int L = SIDE / LANES;                   // segment of a scan lane
     constexpr int KC = PA / NT;                       // cells classified per thread
     static_assert(PA % NT == 0 && NT % SIDE == 0, "LANES lanes per line of the plane");
-    extern __shared__ __align__(128) unsigned char smraw[];    // redist_smem_bytes(SIDE)
+    extern __shared__ __align__(128) unsigned char smraw[];    // redist_layout_bytes(SIDE)
+    static_assert(128 + sizeof(float) * (3 * PA + SIDE * PG) == redist_layout_bytes(SIDE), "one layout");
     uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
     float* const slots = reinterpret_cast<float*>(smraw + 128);
     float* const G = slots + 3 * PA;
     __shared__ int s_flag;
     const int t = threadIdx.x;
     if (t == 0) {
-        for (int k = 0; k < 3; ++k) mbar_init(&bar[k], 1);
-        fence_mbar_init();
-        s_flag = halted(B);
+        const bool fits = dyn_smem_bytes() >= redist_layout_bytes(SIDE);
+        if (fits) {
+            for (int k = 0; k < 3; ++k) mbar_init(&bar[k], 1);
+            fence_mbar_init();
+        } else {
+            atomicExch(&B.st->status, LSGG_ERR_UNSUPPORTED);
+            atomicExch(&B.st->halt, 1);
+        }
+        s_flag = !fits || halted(B);
     }
     __syncthreads();
     if (s_flag) return;
@@ -1400,15 +1442,9 @@ constexpr int kRedistThreads[kTiers] = {128, 192, 256, 256};   // threads per CT
 constexpr int kConvThreads[kTiers] = {128, 192, 256, 256};     // threads per CTA of p_conv_xy
 constexpr int kBigTier = kTiers - 1;
 static size_t conv_smem_bytes(int side, int R) {       // ConvXYLayout<R, side>::bytes
-    if (side > 64) return 0;                              // general-size tier: static shared memory only
-    const int pyr = side + 2 * R, px = ((side + 3) & ~3) + 4 * ((2 * R + 1 + 6) / 4), xp = (side + 3) & ~3;
-    return 128 + sizeof(float) * ((size_t)side * side + (size_t)pyr * px + (size_t)(pyr + 3) * xp) +
-           sizeof(int) * 2 * pyr;
+    return side > 64 ? 0 : conv_layout_bytes(R, side);   // general-size tier: static shared memory only
 }
-constexpr size_t redist_smem_bytes(int side) {
-    if (side > 64) return 0;
-    return 128 + (size_t)(3 * side * side + side * (side + 1)) * sizeof(float);   // barriers, 3 slots, G
-}
+constexpr size_t redist_smem_bytes(int side) { return side > 64 ? 0 : redist_layout_bytes(side); }
 
 struct PassFns {
     const void* conv_xy[kTiers];
