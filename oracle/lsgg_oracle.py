@@ -58,6 +58,19 @@ code where it applies):
      cells and values; every other cell gets the smallest u with
      sum over the axes whose neighbour minimum a_k < u of (u - a_k)^2 = 1,
      capped at eps, iterated (Jacobi) to the fixed point.
+  R12 grid coarsening (Sec. 4.1, sequential optimizations: the spacing grows
+     as the population falls, each function is projected to the coarser grid
+     by trilinear interpolation): the same periodic domain on N' < N cells
+     per axis, one spacing for all axes (N'/N equal).  Coarse cell i' sits at
+     fine index coordinate u = i' N / N' (cell 0 stays in place); its value
+     is the trilinear interpolation of the fine values at floor(u) and
+     floor(u) + 1 per axis (-eps outside the fine box), times N'/N (distances
+     in coarse cells), clamped to [-eps, eps].  The projected function is
+     then re-initialised (R5 / R11) on its coarse box -- the projection
+     leaves a valid band of only eps N'/N coarse cells -- and the box update
+     (R6) follows.  The coarse box of a grain covers every coarse cell whose
+     interpolation corners can meet its fine box.  Time and dt stay in grid
+     units (one step's physical time grows with the spacing squared).
 """
 from __future__ import annotations
 
@@ -589,6 +602,78 @@ def run(ms: Microstructure, n: int, dt: float) -> Microstructure:
     for _ in range(n):
         ms = step(ms, dt)
     return ms
+
+
+# --------------------------------------------------------------------------
+# grid coarsening: Sec. 4.1 (reading R12)
+# --------------------------------------------------------------------------
+
+
+def coarse_axis(o: int, n: int, N: int, N2: int):
+    """Origin and extent on a coarse axis of N2 cells of the box [o, o + n) of
+    a fine axis of N cells: every coarse cell i' with a fine interpolation
+    corner floor(u) or floor(u) + 1 (u = i' N / N2) in the box, i.e.
+    (o - 1) N2 / N <= i' <= (o + n - 1) N2 / N, lies in [floor((o - 1) N2 / N),
+    ceil((o + n) N2 / N)] (R12)."""
+    if n >= N:
+        return (o * N2) // N, N2
+    lo = ((o - 1) * N2) // N
+    hi = -((-(o + n) * N2) // N)
+    n2 = hi - lo + 1
+    if n2 >= N2:
+        return lo % N2, N2
+    return lo % N2, n2
+
+
+def coarse_project(grain: Grain, shape, shape2, eps: float) -> Grain:
+    """The grain's function on its coarse box (R12), before re-initialisation:
+    trilinear interpolation of the fine values (-eps outside the fine box) at
+    u = i' N / N' per axis, times N' / N, clamped to [-eps, eps]."""
+    origin2, dims2 = [], []
+    for a in range(3):
+        o2, n2 = coarse_axis(grain.origin[a], grain.dims[a], shape[a], shape2[a])
+        origin2.append(o2)
+        dims2.append(n2)
+    pos2 = [(origin2[a] + np.arange(dims2[a])) % shape2[a] for a in range(3)]
+    fl, w = [], []
+    for a in range(3):
+        num = pos2[a] * shape[a]
+        fl.append(num // shape2[a])
+        w.append((num % shape2[a]) / shape2[a])
+    val = np.zeros(tuple(dims2))
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                c = (cz, cy, cx)
+                pos = tuple((fl[a] + c[a]) % shape[a] for a in range(3))
+                v, _ = sample(grain, pos, shape, -eps)
+                wt = [w[a] if c[a] else 1.0 - w[a] for a in range(3)]
+                val += wt[0][:, None, None] * wt[1][None, :, None] * wt[2][None, None, :] * v
+    scale = shape2[2] / shape[2]
+    return Grain(grain.gid, tuple(origin2), np.clip(scale * val, -eps, eps))
+
+
+def coarsen(ms: Microstructure, shape2) -> Microstructure:
+    """Every grain projected onto the coarser grid ``shape2`` of the same
+    periodic 3D domain, re-initialised and box-updated (R12)."""
+    shape2 = tuple(int(v) for v in shape2)
+    if any(ms.shape[a] < 2 for a in range(3)):
+        raise ValueError("grid coarsening is defined on 3D domains")
+    if any(shape2[a] * ms.shape[2] != shape2[2] * ms.shape[a] for a in range(3)):
+        raise ValueError("one spacing for all axes: N'/N must be equal")
+    if any(not 1 <= shape2[a] <= ms.shape[a] for a in range(3)):
+        raise ValueError("coarser grid expected")
+    axes = spatial_axes(shape2)
+    redist = redistance_godunov if ms.redist == "godunov" else redistance
+    grains = []
+    for g in ms.grains:
+        if not g.alive:
+            grains.append(Grain(g.gid, g.origin, g.phi, None, alive=False))
+            continue
+        p = coarse_project(g, ms.shape, shape2, ms.eps)
+        p.phi = np.clip(redist(p.phi, full_axes(p, shape2), ms.eps, axes), -ms.eps, ms.eps)
+        grains.append(box_update(p, shape2, ms.halo, ms.eps))
+    return Microstructure(shape2, grains, ms.eps, ms.halo, ms.radius, ms.physics, ms.time, ms.redist)
 
 
 # --------------------------------------------------------------------------

@@ -672,3 +672,101 @@ def test_grain_statistics_closed_forms(oracle):
     assert st["hist"][1] == 0.5 and st["overflow"] == 0.5         # 0.5 in [0.35, 0.7); 1.5 >= 1.4
     assert abs(st["mean_volume"] - 5.0 * math.pi) < 1e-12
 
+
+
+# ---------------------------------------------------------------- grid coarsening (Sec. 4.1, R12)
+
+def _box_grain(oracle, shape, origin, dims, seed, eps=7.0):
+    rng = np.random.default_rng(seed)
+    return oracle.Grain(0, tuple(origin), rng.uniform(-eps, eps, size=tuple(dims)))
+
+
+def test_coarse_project_identity_ratio_pads_with_fill(oracle):
+    """N' = N: u = i', every weight is 0, so the projection is the box's own
+    values, and the coarse box adds one cell of -eps on each side."""
+    shape = (20, 22, 24)
+    g = _box_grain(oracle, shape, (3, 4, 5), (9, 8, 7), 1)
+    p = oracle.coarse_project(g, shape, shape, 7.0)
+    assert p.origin == (2, 3, 4)
+    want = np.pad(g.phi, 1, constant_values=-7.0)
+    assert p.phi.shape == want.shape
+    assert np.array_equal(p.phi, want)
+
+
+def test_coarse_project_half_ratio_takes_even_cells(oracle):
+    """N' = N / 2 on a full-domain box: coarse cell i' sits on fine cell 2 i'
+    exactly, so the projection is half the fine value there."""
+    shape = (16, 20, 24)
+    g = _box_grain(oracle, shape, (0, 0, 0), shape, 2)
+    p = oracle.coarse_project(g, shape, (8, 10, 12), 7.0)
+    assert p.origin == (0, 0, 0)
+    assert np.array_equal(p.phi, 0.5 * g.phi[::2, ::2, ::2])
+
+
+def test_coarse_project_reproduces_affine_functions(oracle):
+    """Trilinear interpolation is exact on affine functions: with N' / N = 2/3
+    (u = 1.5 i'), a box holding a z + b y + c x + d (distinct slopes per axis,
+    so a swapped axis shows) projects to (2/3)(a u_z + b u_y + c u_x + d)
+    wherever all eight corners lie in the box."""
+    shape, shape2, eps = (48, 48, 48), (32, 32, 32), 1e6
+    o, n = (6, 9, 12), (30, 27, 24)
+    a, b, c, d = 0.37, -0.21, 0.113, 1.5
+    z, y, x = np.meshgrid(*[o[k] + np.arange(n[k]) for k in range(3)], indexing="ij")
+    g = oracle.Grain(0, o, a * z + b * y + c * x + d)
+    p = oracle.coarse_project(g, shape, shape2, eps)
+    uz, uy, ux = np.meshgrid(*[(p.origin[k] + np.arange(p.phi.shape[k])) * 1.5 for k in range(3)], indexing="ij")
+    inside = np.ones(p.phi.shape, dtype=bool)
+    for u, k in ((uz, 0), (uy, 1), (ux, 2)):
+        inside &= (np.floor(u) >= o[k]) & (np.floor(u) + 1 <= o[k] + n[k] - 1)
+    assert inside.sum() > 1000
+    want = (2.0 / 3.0) * (a * uz + b * uy + c * ux + d)
+    assert np.max(np.abs(p.phi[inside] - want[inside])) < 1e-12
+
+
+def test_coarse_project_matches_scipy_linear_interpolation(oracle):
+    """The projection equals scipy's periodic linear interpolation
+    (map_coordinates, order 1, grid-wrap) of the fine field (-eps outside the
+    box) at u = i' N / N', times N' / N; and every coarse cell that the box
+    influences lies in the coarse box, which includes boxes crossing the
+    periodic boundary."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    shape, shape2, eps = (30, 36, 42), (20, 24, 28), 7.0
+    for seed, origin, dims in ((3, (25, 2, 30), (11, 13, 17)), (4, (0, 20, 5), (9, 16, 20))):
+        g = _box_grain(oracle, shape, origin, dims, seed)
+        fine = np.full(shape, -eps)
+        idx = np.ix_(*[(origin[k] + np.arange(dims[k])) % shape[k] for k in range(3)])
+        fine[idx] = g.phi
+        coords = np.meshgrid(*[np.arange(shape2[k]) * shape[k] / shape2[k] for k in range(3)], indexing="ij")
+        full = (2.0 / 3.0) * ndimage.map_coordinates(fine, coords, order=1, mode="grid-wrap")
+        p = oracle.coarse_project(g, shape, shape2, eps)
+        pidx = np.ix_(*[(p.origin[k] + np.arange(p.phi.shape[k])) % shape2[k] for k in range(3)])
+        assert np.max(np.abs(p.phi - np.clip(full[pidx], -eps, eps))) < 1e-12
+        outside = np.ones(shape2, dtype=bool)
+        outside[pidx] = False
+        assert np.all(np.abs(full[outside] + (2.0 / 3.0) * eps) < 1e-12)
+
+
+def test_coarsen_halves_a_sphere_exactly(oracle):
+    """A sphere of radius 10 about fine cell (24, 24, 24), coarsened 48 -> 24:
+    coarse cells sit on even fine cells, so the coarse grain's positive set is
+    exactly the lattice sphere of radius 5 about (12, 12, 12); near the
+    surface the re-initialised values are the planar-exact distances (within
+    0.1 of the Euclidean ones), further out taxicab distances (between the
+    Euclidean distance and sqrt(3) times it); the box is the bbox of the
+    positive set (|i' - 12| <= 4) plus the halo of 5."""
+    shape = (48, 48, 48)
+    ms = oracle.single_grain_state(
+        shape, lambda z, y, x: 10.0 - np.sqrt((z - 24) ** 2 + (y - 24) ** 2 + (x - 24) ** 2))
+    c = oracle.coarsen(ms, (24, 24, 24))
+    g = c.grains[0]
+    z, y, x = np.meshgrid(*[np.arange(24)] * 3, indexing="ij")
+    r = np.sqrt((z - 12.0) ** 2 + (y - 12.0) ** 2 + (x - 12.0) ** 2)
+    val, _ = oracle.sample(g, (np.arange(24),) * 3, (24, 24, 24), -7.0)
+    assert np.array_equal(val > 0, r < 5.0)
+    shell = np.abs(r - 5.0) < 0.5
+    assert np.max(np.abs(val[shell] - (5.0 - r[shell]))) < 0.1
+    band = np.abs(r - 5.0) < 3.0
+    e, t = np.abs(5.0 - r[band]), np.abs(val[band])
+    assert np.all(t >= e - 0.1) and np.all(t <= math.sqrt(3.0) * e + 0.1)
+    assert g.origin == (3, 3, 3) and g.dims == (19, 19, 19)
+    assert c.grains[1].dims == (24, 24, 24)       # the complement grain keeps a full box
