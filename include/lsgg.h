@@ -155,6 +155,22 @@ typedef struct lsgg_grain_stats {
 } lsgg_grain_stats;
 int lsgg_grain_statistics(lsgg_ctx* ctx, int32_t n_bins, double r_max_rel, lsgg_grain_stats* out, double* hist);
 
+/* Grid coarsening (Sec. 4.1: as the population falls the spacing grows so a
+ * grain keeps about the same number of cells; each function is projected to
+ * the coarser grid by trilinear interpolation).  The same periodic 3D domain
+ * on nx x ny x nz cells, one spacing: nx / Nx = ny / Ny = nz / Nz, each at
+ * most the current count.  Coarse cell i' of an axis sits at fine index
+ * coordinate u = i' N / N' (cell 0 in place); its value interpolates the fine
+ * values at floor(u), floor(u) + 1 (-eps outside the grain's box), is scaled
+ * by N' / N and clamped to [-eps, eps]; then the step's re-initialisation
+ * (the configured metric) and box update run on the coarse boxes.  No step is
+ * counted.  eps, the halo, the kernel radius and dt stay in grid units, so
+ * one step's physical time grows with the spacing squared, and volumes are
+ * in coarse cells.  Batched execution of a 3D domain with ideal growth only
+ * (else LSGG_ERR_UNSUPPORTED); LSGG_ERR_INVALID_ARG for unequal ratios or a
+ * finer grid.  Waits for enqueued steps first; synchronises. */
+int lsgg_coarsen(lsgg_ctx* ctx, int32_t nx, int32_t ny, int32_t nz);
+
 /* owner(x) = argmax_i phi_i(x) over the boxes covering x, lowest id on ties,
  * -1 where no box covers x; x fastest, n_cells = nx*ny*nz int32s.  Synchronises. */
 int lsgg_voxel_owner(lsgg_ctx* ctx, int32_t* out, int64_t n_cells);

@@ -1078,6 +1078,77 @@ int lsgg_grain_statistics(lsgg_ctx* c, int32_t n_bins, double r_max_rel, lsgg_gr
     return LSGG_OK;
 }
 
+// Coarse origin and extent of a fine box [o, o + n) on an axis coarsened
+// from N to N2 cells: every coarse cell i' whose fine interpolation corners
+// floor(u), floor(u) + 1 (u = i' N / N2) can meet the box, i.e. from
+// floor((o - 1) N2 / N) to ceil((o + n) N2 / N).
+static void coarse_box_axis(int o, int n, int N, int N2, int* o2, int* n2) {
+    if (n >= N) {
+        *o2 = (int)((long long)o * N2 / N);
+        *n2 = N2;
+        return;
+    }
+    auto floor_div = [](long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+    const long long lo = floor_div((long long)(o - 1) * N2, N);
+    const long long hi = -floor_div(-(long long)(o + n) * N2, N);
+    const long long ext = hi - lo + 1;
+    *o2 = (int)(((lo % N2) + N2) % N2);
+    *n2 = ext >= N2 ? N2 : (int)ext;
+}
+
+int lsgg_coarsen(lsgg_ctx* c, int32_t nx, int32_t ny, int32_t nz) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    const Domain fine = c->dom;
+    if (fine.dim != 3 || !c->B.use_passes) return LSGG_ERR_UNSUPPORTED;
+    if (c->phys.kind != LSGG_PHYSICS_IDEAL) return LSGG_ERR_UNSUPPORTED;   // no ID-field on the coarse grid yet
+    if (nx < 1 || ny < 1 || nz < 1 || nx > fine.nx || ny > fine.ny || nz > fine.nz) return LSGG_ERR_INVALID_ARG;
+    if ((long long)nx * fine.ny != (long long)ny * fine.nx || (long long)nx * fine.nz != (long long)nz * fine.nx)
+        return LSGG_ERR_INVALID_ARG;                                       // one spacing on every axis
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    // the grains' boxes on the fine grid (`cur`: the functions the next step
+    // would start from) -> candidate boxes on the coarse grid
+    std::vector<Box> hp((size_t)c->G), hc((size_t)c->G);
+    CK(cudaMemcpy(hp.data(), c->B.cur, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToHost));
+    Box* d_fine = nullptr;
+    if ((r = dalloc(c, &d_fine, (size_t)c->G)) != LSGG_OK) return r;
+    CK(cudaMemcpy(d_fine, hp.data(), (size_t)c->G * sizeof(Box), cudaMemcpyHostToDevice));
+    const int N[3] = {fine.nx, fine.ny, fine.nz}, N2[3] = {nx, ny, nz};
+    for (int b = 0; b < c->G; ++b) {
+        Box o = hp[b], q{};
+        if (o.nx > 0) {
+            const int oo[3] = {o.ox, o.oy, o.oz}, on[3] = {o.nx, o.ny, o.nz};
+            int qo[3], qn[3];
+            for (int a = 0; a < 3; ++a) coarse_box_axis(oo[a], on[a], N[a], N2[a], &qo[a], &qn[a]);
+            q.ox = qo[0]; q.oy = qo[1]; q.oz = qo[2];
+            q.nx = qn[0]; q.ny = qn[1]; q.nz = qn[2];
+        }
+        hc[b] = q;
+    }
+    // the coarse domain, its tiles, the candidate layout
+    c->dom.nx = nx;
+    c->dom.ny = ny;
+    c->dom.nz = nz;
+    c->B.dom = c->dom;
+    CK(configure_passes(c->B));
+    CK(cudaMemcpy(c->B.cur, hc.data(), (size_t)c->G * sizeof(Box), cudaMemcpyHostToDevice));
+    r = relayout(c);
+    // projection into Z, then the re-initialisation and box update of a step
+    const float* x = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (r == LSGG_OK) e = state_as_f32(c, &x);
+    if (r == LSGG_OK && e == cudaSuccess) e = launch_coarsen(c->B, fine, d_fine, x, c->stream);
+    if (r == LSGG_OK && e == cudaSuccess) e = launch_reinit(c->B, make_taps(1.0, c->dom.radius), c->phys, c->stream);
+    if (r == LSGG_OK && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->device_bytes -= (long long)c->G * (long long)sizeof(Box);
+    dfree(c, d_fine);
+    c->field_valid = false;
+    if (r != LSGG_OK) return r;
+    if (e != cudaSuccess) return fail_cuda(e);
+    return lsgg_sync(c, -1);
+}
+
 int lsgg_voxel_owner(lsgg_ctx* c, int32_t* out, int64_t n_cells) {
     if (!c || !out) return LSGG_ERR_INVALID_ARG;
     long long n = (long long)c->dom.nx * c->dom.ny * c->dom.nz;

@@ -220,7 +220,14 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
                         const DebugOut* dbg, cudaStream_t s, cudaEvent_t* ev = nullptr,
                         const StepStreams* ss = nullptr, cudaEvent_t* cls_ev = nullptr,
                         cudaEvent_t* pass_ev = nullptr);
-cudaError_t launch_box_update(const StepBuffers& B, bool commit_only_layout, cudaStream_t s);
+cudaError_t launch_box_update(const StepBuffers& B, bool commit_only_layout, cudaStream_t s, bool count_step = true);
+cudaError_t launch_reinit(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys, cudaStream_t s);
+// grid coarsening (coarsen.cu): every alive grain's function on the domain
+// `fine` (its box `fine_boxes`, values from the FP32 state in the `prev`
+// layout) projected trilinearly into Z in the `cur` layout on B.dom, scaled by
+// the spacing ratio and clamped
+cudaError_t launch_coarsen(const StepBuffers& B, const Domain& fine, const Box* fine_boxes, const float* state,
+                           cudaStream_t s);
 
 // Seeds sorted into a uniform grid of bins (built on the host) for the
 // labelling search of the initialisation.

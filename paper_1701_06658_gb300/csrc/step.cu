@@ -457,8 +457,12 @@ __device__ __forceinline__ int pass_tier(const StepBuffers& B, int c) {
     return kTiers - 1;
 }
 
+// layout_only: offsets and work items for the `cur` boxes as they are;
+// otherwise the boxes follow the bounds collected by the re-initialisation,
+// and count_step adds the step to the step and cell-update counters (not for
+// the re-initialisation of a coarsening).
 __global__ void __launch_bounds__(kBoxUpdateThreads)
-k_box_update(StepBuffers B, int layout_only) {
+k_box_update(StepBuffers B, int layout_only, int count_step) {
     __shared__ long long s_part[kBoxUpdateThreads];
     __shared__ int s_scan[(kBoxUpdateThreads / 32) * (kNumClasses + 3 * kTiers)];
     const int G = B.n_boxes;
@@ -513,8 +517,8 @@ k_box_update(StepBuffers B, int layout_only) {
         __syncthreads();
     }
     const long long total = s_part[blockDim.x - 1];
-    if (!layout_only && done) atomicAdd((unsigned long long*)&B.st->cell_updates, (unsigned long long)done);
-    if (threadIdx.x == 0 && !layout_only) B.st->steps_done += 1;   // the step's fields are complete
+    if (!layout_only && count_step && done) atomicAdd((unsigned long long*)&B.st->cell_updates, (unsigned long long)done);
+    if (threadIdx.x == 0 && !layout_only && count_step) B.st->steps_done += 1;   // the step's fields are complete
     if (total > B.cap) {
         if (threadIdx.x == 0) {
             B.st->status = LSGG_ERR_CAPACITY;
@@ -747,8 +751,8 @@ k_write_items(StepBuffers B) {
     }
 }
 
-cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream_t s) {
-    k_box_update<<<1, kBoxUpdateThreads, 0, s>>>(B, layout_only ? 1 : 0);
+cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream_t s, bool count_step) {
+    k_box_update<<<1, kBoxUpdateThreads, 0, s>>>(B, layout_only ? 1 : 0, count_step ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !B.use_passes) return e;
     k_write_items<<<B.n_sm * 4, 256, 0, s>>>(B);
@@ -885,6 +889,25 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
     e = traced(launch_box_update(B, false, s), "box update");
     if (ev) cudaEventRecord(ev[4], s);
     return e;
+}
+
+// The re-initialisation (pass 3) and box update of a step alone, on the
+// phi_c that Z holds in the `cur` layout: the pass path's binning (which
+// resets the bounds), its re-initialisation passes of every tier and a box
+// update that counts no step.  Used by the grid coarsening.
+cudaError_t launch_reinit(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys, cudaStream_t s) {
+    if (!B.use_passes) return cudaErrorInvalidValue;
+    cudaError_t e = traced(launch_bin(B, s), "tile binning");
+    if (e != cudaSuccess) return e;
+    const DebugOut d{};
+    if (B.godunov) {
+        e = traced(launch_godunov(B, d, s), "Godunov re-initialisation");
+    } else {
+        for (int t = 0; t < kTiers && e == cudaSuccess; ++t)
+            e = traced(launch_passes(B, 1, t, taps, phys, d, s, nullptr), "pass kernels");
+    }
+    if (e != cudaSuccess) return e;
+    return traced(launch_box_update(B, false, s, false), "box update");
 }
 
 }  // namespace lsgg

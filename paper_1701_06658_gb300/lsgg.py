@@ -89,6 +89,7 @@ _SIGS = {
     "lsgg_grain_volumes": (C.c_int, [C.c_void_p, _dp, C.c_int64, C.POINTER(C.c_int64)]),
     "lsgg_voxel_owner": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
     "lsgg_grain_statistics": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(GrainStats), _dp]),
+    "lsgg_coarsen": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "lsgg_destroy": (C.c_int, [C.c_void_p]),
     "lsgg_status_string": (C.c_char_p, [C.c_int]),
     "lsgg_get_stream": (C.c_void_p, [C.c_void_p]),
@@ -203,6 +204,11 @@ def grain_statistics(ctx, n_bins: int = 20, r_max: float = 3.0) -> dict:
     out = {f: getattr(st, f) for f, _ in GrainStats._fields_}
     out["hist"] = hist
     return out
+
+
+def coarsen(ctx, nx: int, ny: int, nz: int):
+    """Grid coarsening onto nx x ny x nz cells of the same domain (see lsgg.h)."""
+    _check("coarsen", lib().lsgg_coarsen(ctx, nx, ny, nz))
 
 
 def voxel_owner(ctx, shape_zyx, out=None) -> np.ndarray:
@@ -417,6 +423,10 @@ class Microstructure:
 
     def grain_statistics(self, n_bins: int = 20, r_max: float = 3.0) -> dict:
         return grain_statistics(self.ctx, n_bins, r_max)
+
+    def coarsen(self, nx: int, ny: int, nz: int):
+        coarsen(self.ctx, nx, ny, nz)
+        self.shape = (nz, ny, nx)
 
     def boxes(self) -> np.ndarray:
         return get_boxes(self.ctx, self.n_grains)
