@@ -358,6 +358,42 @@ def gpu_arm(args):
                 "fp32_same_run": vols[L.STORAGE_FP32][1], "steps": 2 + steps_b,
                 "volume_rel_error_vs_fp32": {"max": float(rel.max()), "mean": float(rel.mean())}}
 
+    # ---------------- grid coarsening (Sec. 4.1) of the same workload ----------------
+    # lsgg_coarsen to half the cells per axis after a few steps (host wall clock
+    # around the synchronising call), then device-timed steps on the coarse grid
+    coarsening = None
+    if not args.no_compare and rank == 0 and WORKLOAD.get("physics", "ideal") == "ideal" and n % 2 == 0:
+        with L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=exec_mode,
+                              **workload_kwargs(L)) as km:
+            km.step(5, dt)
+            km.sync()
+            fine_cells = km.stats().box_cells
+            t0 = time.perf_counter()
+            km.coarsen(n // 2, n // 2, n // 2)
+            el = time.perf_counter() - t0
+            coarse_cells = km.stats().box_cells
+            km.step(2, dt)
+            km.sync()
+            c0 = km.stats().cell_updates
+            kstream = torch.cuda.ExternalStream(km.stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            steps_k = 10
+            torch.cuda.synchronize()
+            e0.record(kstream)
+            km.step(steps_k, dt)
+            e1.record(kstream)
+            km.sync()
+            torch.cuda.synchronize()
+            kms = e0.elapsed_time(e1)
+            k_rate = (km.stats().cell_updates - c0) / (kms * 1e-3)
+        coarsening = {"from": [n, n, n], "to": [n // 2] * 3, "ms": 1e3 * el,
+                      "timing": "host wall clock around lsgg_coarsen (box copies, relayout, projection, "
+                                "re-initialisation, box update; synchronising)",
+                      "fine_box_cells": int(fine_cells), "coarse_box_cells": int(coarse_cells),
+                      "fine_box_cells_per_s": fine_cells / el,
+                      "coarse_steps": {"value": k_rate, "unit": UNIT, "ms_per_step": kms / steps_k,
+                                       "steps": steps_k}}
+
     # ---------------- serving: continuous batching under an HBM budget ----------------
     serving = None
     if args.serve_requests > 0 and rank == 0:
@@ -426,6 +462,7 @@ def gpu_arm(args):
         "serving": serving,
         "compare": compare,
         "bf16_storage": bf16,
+        "coarsening": coarsening,
         "speedup_vs_plain_gpu": None if not compare else value / compare["plain_gpu"]["value"],
     }
     print(json.dumps(line), flush=True)

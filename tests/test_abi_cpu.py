@@ -75,6 +75,9 @@ def test_invalid_arguments_rejected_before_any_device_work():
     assert e.value.code == L.ERR_INVALID_ARG
     with pytest.raises(L.LsggError):
         L.generate_seeds(1, 0, 4, 4, 4)
+    with pytest.raises(L.LsggError) as e:
+        L.coarsen(None, 16, 16, 16)          # no context
+    assert e.value.code == L.ERR_INVALID_ARG
 
 
 def test_no_cpu_fallback_without_a_device():
