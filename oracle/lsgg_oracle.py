@@ -449,7 +449,8 @@ def mobility_step(theta: float, theta_max: float, low: float) -> float:
 
 
 def mobility_eq20(theta: float) -> float:
-    """Eq. (20): mu = 1 - 0.99 exp(-5 (theta / 15 deg)^9)."""
+    """Eq. (20): mu = 1 - 0.99 exp(-5 (theta / 15 deg)^9), as printed (its
+    rise lies between 10 and 15 degrees, where the prose says 8 to 10)."""
     return 1.0 - 0.99 * math.exp(-5.0 * (theta / math.radians(15.0)) ** 9)
 
 

@@ -629,6 +629,25 @@ def test_read_shockley_shape(oracle):
     assert abs(slope) < 1e-4          # energy maximum at theta_max: smooth join to 1
 
 
+def test_mobility_eq20_has_the_described_shape(oracle):
+    """Sec. 4.1's prose around Eq. (20): low- and high-angle boundaries are
+    distinguished, high angle above 15 degrees, with a steep ascent starting at
+    8 degrees (reading R13: the printed formula completes its rise by 15
+    degrees, not 10).  So: values in (0, 1], non-decreasing, a low-angle
+    plateau up to 8 degrees (below 3 % of the high-angle mobility), the
+    high-angle value (within 1 %) from 15 degrees on, and the half-way point
+    of the rise between 8 and 15 degrees."""
+    deg = math.radians(1.0)
+    th = np.linspace(0.0, 62.8, 2000) * deg
+    mu = np.array([oracle.mobility_eq20(t) for t in th])
+    assert np.all(mu > 0.0) and np.all(mu <= 1.0)
+    assert np.all(np.diff(mu) >= 0.0)
+    assert np.all(mu[th <= 8 * deg] < 0.03)
+    assert np.all(mu[th >= 15 * deg] > 0.99)
+    half = th[np.argmax(mu >= 0.5)]
+    assert 8 * deg < half < 15 * deg
+
+
 def test_magnetic_energy_matches_printed_maximum(oracle):
     """P7: Eq. (18) with the printed B = 17 T and dchi = 1.18e-5 gives the
     largest orientation energy; the paper's printed maximum 1351.23 J/m^3
