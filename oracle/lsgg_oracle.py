@@ -69,8 +69,11 @@ code where it applies):
      then re-initialised (R5 / R11) on its coarse box -- the projection
      leaves a valid band of only eps N'/N coarse cells -- and the box update
      (R6) follows.  The coarse box of a grain covers every coarse cell whose
-     interpolation corners can meet its fine box.  Time and dt stay in grid
-     units (one step's physical time grows with the spacing squared).
+     interpolation corners can meet its fine box.  With physics, the ID-field
+     the next step's correction reads (R3) is rebuilt on the coarse grid as
+     R4's argmax over the other grains of the re-initialised functions.  Time
+     and dt stay in grid units (one step's physical time grows with the
+     spacing squared).
 """
 from __future__ import annotations
 
@@ -666,14 +669,22 @@ def coarsen(ms: Microstructure, shape2) -> Microstructure:
         raise ValueError("coarser grid expected")
     axes = spatial_axes(shape2)
     redist = redistance_godunov if ms.redist == "godunov" else redistance
-    grains = []
+    coarse = []
     for g in ms.grains:
         if not g.alive:
-            grains.append(Grain(g.gid, g.origin, g.phi, None, alive=False))
+            coarse.append(Grain(g.gid, g.origin, g.phi, None, alive=False))
             continue
         p = coarse_project(g, ms.shape, shape2, ms.eps)
         p.phi = np.clip(redist(p.phi, full_axes(p, shape2), ms.eps, axes), -ms.eps, ms.eps)
-        grains.append(box_update(p, shape2, ms.halo, ms.eps))
+        coarse.append(p)
+    if ms.physics is not None:
+        cms = Microstructure(shape2, coarse, ms.eps, ms.halo, ms.radius, ms.physics, ms.time, ms.redist)
+        cand = box_candidates(cms)
+        phis = {g.gid: g.phi for g in coarse if g.alive}
+        for g in coarse:
+            if g.alive:
+                _, g.idf = neighbour_max(g.gid, coarse, phis, shape2, ms.eps, cand[g.gid])
+    grains = [box_update(g, shape2, ms.halo, ms.eps) if g.alive else g for g in coarse]
     return Microstructure(shape2, grains, ms.eps, ms.halo, ms.radius, ms.physics, ms.time, ms.redist)
 
 

@@ -789,3 +789,28 @@ def test_coarsen_halves_a_sphere_exactly(oracle):
     assert np.all(t >= e - 0.1) and np.all(t <= math.sqrt(3.0) * e + 0.1)
     assert g.origin == (3, 3, 3) and g.dims == (19, 19, 19)
     assert c.grains[1].dims == (24, 24, 24)       # the complement grain keeps a full box
+
+
+def test_coarsen_rebuilds_the_id_field(oracle):
+    """With physics, coarsening rebuilds the ID-field (R3 / R4) from the coarse
+    functions: in a sphere + complement pair, the sphere's ID-field is the
+    complement (id 1) wherever the complement's coarse value exceeds -eps,
+    -1 elsewhere; it is carried into the new box like phi (-1 in the cells the
+    box update adds beyond the coarse box it was computed on)."""
+    shape = (40, 40, 40)
+    ms = oracle.single_grain_state(
+        shape, lambda z, y, x: 8.0 - np.sqrt((z - 20) ** 2 + (y - 20) ** 2 + (x - 20) ** 2))
+    ms.physics = oracle.isotropic_physics(np.zeros(2))
+    c = oracle.coarsen(ms, (20, 20, 20))
+    g0, g1 = c.grains
+    assert g0.idf is not None and g0.idf.shape == g0.phi.shape
+    pos = oracle.box_positions(g0, (20, 20, 20))
+    other, _ = oracle.sample(g1, pos, (20, 20, 20), -7.0)
+    cb = [oracle.coarse_axis(ms.grains[0].origin[a], ms.grains[0].dims[a], 40, 20) for a in range(3)]
+    inside = np.ones(g0.dims, dtype=bool)
+    for a in range(3):
+        sh = [1, 1, 1]
+        sh[a] = -1
+        inside &= (((pos[a] - cb[a][0]) % 20) < cb[a][1]).reshape(sh)
+    assert np.array_equal(g0.idf, np.where(inside & (other > -7.0), 1, -1))
+    assert (g0.idf == 1).any() and (~inside).any()
