@@ -163,12 +163,14 @@ int lsgg_grain_statistics(lsgg_ctx* ctx, int32_t n_bins, double r_max_rel, lsgg_
  * coordinate u = i' N / N' (cell 0 in place); its value interpolates the fine
  * values at floor(u), floor(u) + 1 (-eps outside the grain's box), is scaled
  * by N' / N and clamped to [-eps, eps]; then the step's re-initialisation
- * (the configured metric) and box update run on the coarse boxes.  No step is
- * counted.  eps, the halo, the kernel radius and dt stay in grid units, so
- * one step's physical time grows with the spacing squared, and volumes are
- * in coarse cells.  Batched execution of a 3D domain with ideal growth only
- * (else LSGG_ERR_UNSUPPORTED); LSGG_ERR_INVALID_ARG for unequal ratios or a
- * finer grid.  Waits for enqueued steps first; synchronises. */
+ * (the configured metric) and box update run on the coarse boxes; with
+ * physics other than ideal growth the ID-field is rebuilt from the coarse
+ * functions (argmax over the other grains).  No step is counted.  eps, the
+ * halo, the kernel radius and dt stay in grid units, so one step's physical
+ * time grows with the spacing squared, and volumes are in coarse cells.
+ * Batched execution of a 3D domain only (else LSGG_ERR_UNSUPPORTED);
+ * LSGG_ERR_INVALID_ARG for unequal ratios or a finer grid.  Waits for
+ * enqueued steps first; synchronises. */
 int lsgg_coarsen(lsgg_ctx* ctx, int32_t nx, int32_t ny, int32_t nz);
 
 /* owner(x) = argmax_i phi_i(x) over the boxes covering x, lowest id on ties,

@@ -1100,7 +1100,6 @@ int lsgg_coarsen(lsgg_ctx* c, int32_t nx, int32_t ny, int32_t nz) {
     if (!c) return LSGG_ERR_INVALID_ARG;
     const Domain fine = c->dom;
     if (fine.dim != 3 || !c->B.use_passes) return LSGG_ERR_UNSUPPORTED;
-    if (c->phys.kind != LSGG_PHYSICS_IDEAL) return LSGG_ERR_UNSUPPORTED;   // no ID-field on the coarse grid yet
     if (nx < 1 || ny < 1 || nz < 1 || nx > fine.nx || ny > fine.ny || nz > fine.nz) return LSGG_ERR_INVALID_ARG;
     if ((long long)nx * fine.ny != (long long)ny * fine.nx || (long long)nx * fine.nz != (long long)nz * fine.nx)
         return LSGG_ERR_INVALID_ARG;                                       // one spacing on every axis
@@ -1139,7 +1138,8 @@ int lsgg_coarsen(lsgg_ctx* c, int32_t nx, int32_t ny, int32_t nz) {
     cudaError_t e = cudaSuccess;
     if (r == LSGG_OK) e = state_as_f32(c, &x);
     if (r == LSGG_OK && e == cudaSuccess) e = launch_coarsen(c->B, fine, d_fine, x, c->stream);
-    if (r == LSGG_OK && e == cudaSuccess) e = launch_reinit(c->B, make_taps(1.0, c->dom.radius), c->phys, c->stream);
+    if (r == LSGG_OK && e == cudaSuccess) e = launch_reinit(c->B, make_taps(1.0, c->dom.radius), c->phys,
+                                                                c->phys.kind != LSGG_PHYSICS_IDEAL, c->stream);
     if (r == LSGG_OK && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     c->device_bytes -= (long long)c->G * (long long)sizeof(Box);
     dfree(c, d_fine);

@@ -221,7 +221,8 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
                         const StepStreams* ss = nullptr, cudaEvent_t* cls_ev = nullptr,
                         cudaEvent_t* pass_ev = nullptr);
 cudaError_t launch_box_update(const StepBuffers& B, bool commit_only_layout, cudaStream_t s, bool count_step = true);
-cudaError_t launch_reinit(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys, cudaStream_t s);
+cudaError_t launch_reinit(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys, bool id_field,
+                          cudaStream_t s);
 // grid coarsening (coarsen.cu): every alive grain's function on the domain
 // `fine` (its box `fine_boxes`, values from the FP32 state in the `prev`
 // layout) projected trilinearly into Z in the `cur` layout on B.dom, scaled by

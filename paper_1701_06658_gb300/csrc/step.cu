@@ -894,8 +894,12 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
 // The re-initialisation (pass 3) and box update of a step alone, on the
 // phi_c that Z holds in the `cur` layout: the pass path's binning (which
 // resets the bounds), its re-initialisation passes of every tier and a box
-// update that counts no step.  Used by the grid coarsening.
-cudaError_t launch_reinit(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys, cudaStream_t s) {
+// update that counts no step.  With id_field, the field pass then runs on the
+// re-initialised state (copied to Y as its phi_p) before the box update, so
+// that the ID-field the next step's correction reads exists in this layout.
+// Used by the grid coarsening.
+cudaError_t launch_reinit(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys, bool id_field,
+                          cudaStream_t s) {
     if (!B.use_passes) return cudaErrorInvalidValue;
     cudaError_t e = traced(launch_bin(B, s), "tile binning");
     if (e != cudaSuccess) return e;
@@ -905,6 +909,11 @@ cudaError_t launch_reinit(const StepBuffers& B, const Taps& taps, const PhysicsD
     } else {
         for (int t = 0; t < kTiers && e == cudaSuccess; ++t)
             e = traced(launch_passes(B, 1, t, taps, phys, d, s, nullptr), "pass kernels");
+    }
+    if (e == cudaSuccess && id_field) {
+        e = B.bf16 ? launch_state_to_f32(B.X, B.Y, B.cap, s)
+                   : cudaMemcpyAsync(B.Y, B.X, (size_t)B.cap * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = traced(launch_field(B, phys, d, s), "field pass");
     }
     if (e != cudaSuccess) return e;
     return traced(launch_box_update(B, false, s, false), "box update");

@@ -158,3 +158,28 @@ def test_coarsen_rejects_unequal_ratios_and_finer_grids(L):
         assert ms.shape == (N, N, N)
         ms.step(1, 1.0)          # the context is unchanged and usable
         ms.sync()
+
+
+def test_coarsen_with_read_shockley_rebuilds_the_id_field(L):
+    """Read-Shockley physics: the coarsening matches the oracle's, and the next
+    step -- whose predictor blends with the pair weights the ID-field selects
+    -- matches the oracle's step from the oracle's coarsened state (its
+    rebuilt ID-field), so the GPU's ID-field is the oracle's."""
+    from tests.test_gpu_physics import _compare_step
+    N, N2, G = 48, 36, 24
+    seeds = I.voronoi_seeds(8, G, (N, N, N))
+    quats = I.random_quaternions(8, G)
+    phys = O.read_shockley_physics(quats)
+    with L.Microstructure(N, N, N, G, seeds=seeds, quats=quats, physics=L.PHYSICS_READ_SHOCKLEY) as ms:
+        ms.step(2, 1.0)
+        ms.sync()
+        ref_ms = oracle_from_gpu((N, N, N), ms.boxes(), ms.phi(), physics=phys)
+        ms.coarsen(N2, N2, N2)
+        boxes2, phi2 = ms.boxes(), ms.phi()
+        ref = O.coarsen(ref_ms, (N2, N2, N2))
+        worst, excluded = _compare(L, (N2, N2, N2), boxes2, phi2, ref_ms, ref)
+        assert worst <= TOL_PHI
+        assert excluded == 0
+        idf = {g: ref.grains[g].idf for g in range(G) if ref.grains[g].alive}
+        nxt = oracle_from_gpu((N2, N2, N2), boxes2, phi2, idf_by_grain=idf, physics=phys)
+        _compare_step(L, ms, nxt)
