@@ -68,12 +68,17 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# the sources the pass kernels are compiled from: their file and every header
+# it includes
+PASS_KERNEL_SOURCES = ("paper_1701_06658_gb300/csrc/passes.cu", "paper_1701_06658_gb300/csrc/bulk_copy.cuh",
+                       "paper_1701_06658_gb300/csrc/kernels_common.cuh",
+                       "paper_1701_06658_gb300/csrc/lsgg_internal.cuh", "include/lsgg.h")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    cs = os.path.join(ROOT, "paper_1701_06658_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(cs, f), "rb").read())
+    for f in PASS_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
