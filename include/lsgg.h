@@ -60,7 +60,7 @@ extern "C" {
 #define LSGG_STORAGE_BF16  1   /* phi stored in BF16 between steps, FP32 arithmetic */
 
 #define LSGG_EXEC_BATCHED  0   /* all boxes at once: 3D boxes by five passes over (box, plane /
-                                  slab / column) work items in size tiers (x, y side <= 32, 48, 64
+                                  slab / column) work items in size tiers (x, y side <= 32, 40, 48, 64
                                   in shared memory, larger through global memory), 2D boxes by
                                   box-streaming kernels; persistent grids, one CUDA graph per step */
 #define LSGG_EXEC_PLAIN    1   /* comparator: separate launches per grain per sub-step */
@@ -191,7 +191,7 @@ void* lsgg_get_stream(lsgg_ctx* ctx);
 size_t lsgg_abi_config_size(void);
 
 /* ------------------------------------------------------------- inspection */
-#define LSGG_PASS_TIERS 4      /* pass-path tiers: boxes of x, y side <= 32, <= 48, <= 64, larger */
+#define LSGG_PASS_TIERS 5      /* pass-path tiers: boxes of x, y side <= 32, <= 40, <= 48, <= 64, larger */
 typedef struct lsgg_stats {
     int64_t steps_done;        /* steps completed since creation */
     int64_t cell_updates;      /* box cells advanced, summed over completed steps */
@@ -203,7 +203,7 @@ typedef struct lsgg_stats {
     int32_t n_classes;         /* box-size classes of the batched path */
     int32_t class_count[8];    /* boxes per class at the last box update */
     int64_t pass_cells[LSGG_PASS_TIERS];  /* box cells on the pass path per tier (x, y side
-                                  <= 32, <= 48, <= 64, larger) at the last box update; 0 off the
+                                  <= 32, <= 40, <= 48, <= 64, larger) at the last box update; 0 off the
                                   pass path */
 } lsgg_stats;
 
@@ -238,8 +238,8 @@ int lsgg_kernel_times(lsgg_ctx* ctx, double* out_ms, int64_t* out_count);
 /* Per-pass timing of the pass path (LSGG_EXEC_BATCHED, 3D), from the same
  * profiled steps as lsgg_kernel_times (arrays of 4 * LSGG_PASS_TIERS + 2;
  * NULL allowed): out_ms[t * 4 + k] / out_count[t * 4 + k] for tier t = 0
- * (boxes of x, y side <= 32), 1 (<= 48), 2 (<= 64), 3 (larger: plane passes
- * through global memory) and pass k = 0 p_conv_xy,
+ * (boxes of x, y side <= 32), 1 (<= 40), 2 (<= 48), 3 (<= 64), 4 (larger:
+ * plane passes through global memory) and pass k = 0 p_conv_xy,
  * 1 p_conv_z, 2 p_redist_xy, 3 p_redist_z; [4 * LSGG_PASS_TIERS] the tile
  * binning (k_bin), [4 * LSGG_PASS_TIERS + 1] the field pass (p_field, all
  * boxes).  In lsgg_kernel_times the binning is group 0 and the field

@@ -33,7 +33,7 @@ constexpr int kMaxRadius = 7;
 constexpr int kMaxTaps = 2 * kMaxRadius + 1;
 constexpr int kNumClasses = 5;          // box side <= 32, 40, 48, 64, larger (global scratch)
 constexpr int kRedistReach = 6;         // taxicab steps below eps = 7 (exact fixed point)
-constexpr int kTiers = 4;               // pass path: boxes with x, y sides <= 32, <= 48, <= 64, larger
+constexpr int kTiers = 5;               // pass path: boxes with x, y sides <= 32, <= 40, <= 48, <= 64, larger
 constexpr int kPassChunk = 256;         // columns per column item of the pass path
 constexpr int kSlab = 8;                // planes per slab item of the pass path
 constexpr int kTileX = 8, kTileY = 32, kTileZ = 8;    // domain tiles of the field pass

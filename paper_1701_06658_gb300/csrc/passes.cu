@@ -1437,9 +1437,9 @@ p_redist_xy_big(StepBuffers B, int tier) {
 // ---------------------------------------------------------------------------
 // The radius-specialised convolution kernels (R = 1 .. kMaxRadius) per tier
 // side; the z pass with or without the velocity correction of Eq. (10).
-constexpr int kTierSide[kTiers] = {32, 48, 64, 1 << 30};  // the last tier: any size (global-memory plane passes)
-constexpr int kRedistThreads[kTiers] = {128, 192, 256, 256};   // threads per CTA of p_redist_xy (4 lanes per line)
-constexpr int kConvThreads[kTiers] = {128, 192, 256, 256};     // threads per CTA of p_conv_xy
+constexpr int kTierSide[kTiers] = {32, 40, 48, 64, 1 << 30};  // the last tier: any size (global-memory plane passes)
+constexpr int kRedistThreads[kTiers] = {128, 160, 192, 256, 256};   // threads per CTA of p_redist_xy (4 lanes per line)
+constexpr int kConvThreads[kTiers] = {128, 160, 192, 256, 256};     // threads per CTA of p_conv_xy
 constexpr int kBigTier = kTiers - 1;
 static size_t conv_smem_bytes(int side, int R) {       // ConvXYLayout<R, side>::bytes
     return side > 64 ? 0 : conv_layout_bytes(R, side);   // general-size tier: static shared memory only
@@ -1454,17 +1454,19 @@ struct PassFns {
 
 template <int R>
 static PassFns pass_fns_r(bool phys) {
-    static_assert(kTiers == 4, "one instantiation per tier side");
+    static_assert(kTiers == 5, "one instantiation per tier side");
     PassFns f;
     f.conv_xy[0] = reinterpret_cast<const void*>(p_conv_xy<R, 32, kConvThreads[0]>);
-    f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 48, kConvThreads[1]>);
-    f.conv_xy[2] = reinterpret_cast<const void*>(p_conv_xy<R, 64, kConvThreads[2]>);
-    f.conv_xy[3] = reinterpret_cast<const void*>(p_conv_xy_big<R>);
+    f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 40, kConvThreads[1]>);
+    f.conv_xy[2] = reinterpret_cast<const void*>(p_conv_xy<R, 48, kConvThreads[2]>);
+    f.conv_xy[3] = reinterpret_cast<const void*>(p_conv_xy<R, 64, kConvThreads[3]>);
+    f.conv_xy[4] = reinterpret_cast<const void*>(p_conv_xy_big<R>);
     f.conv_z = phys ? reinterpret_cast<const void*>(p_conv_z<R, true>) : reinterpret_cast<const void*>(p_conv_z<R, false>);
     f.redist_xy[0] = reinterpret_cast<const void*>(p_redist_xy<32, kRedistThreads[0]>);
-    f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<48, kRedistThreads[1]>);
-    f.redist_xy[2] = reinterpret_cast<const void*>(p_redist_xy<64, kRedistThreads[2]>);
-    f.redist_xy[3] = reinterpret_cast<const void*>(p_redist_xy_big);
+    f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<40, kRedistThreads[1]>);
+    f.redist_xy[2] = reinterpret_cast<const void*>(p_redist_xy<48, kRedistThreads[2]>);
+    f.redist_xy[3] = reinterpret_cast<const void*>(p_redist_xy<64, kRedistThreads[3]>);
+    f.redist_xy[4] = reinterpret_cast<const void*>(p_redist_xy_big);
     return f;
 }
 

@@ -62,7 +62,7 @@ class Stats(C.Structure):
         ("steps_done", C.c_int64), ("cell_updates", C.c_int64), ("alive", C.c_int64), ("box_cells", C.c_int64),
         ("arena_capacity", C.c_int64), ("superimposition", C.c_double),
         ("device_bytes", C.c_int64), ("n_classes", C.c_int32), ("class_count", C.c_int32 * 8),
-        ("pass_cells", C.c_int64 * 4),
+        ("pass_cells", C.c_int64 * 5),
     ]
 
 
@@ -256,7 +256,7 @@ def kernel_times(ctx):
 
 
 PASS_NAMES = ("p_conv_xy", "p_conv_z", "p_redist_xy", "p_redist_z")
-PASS_TIERS = 4          # LSGG_PASS_TIERS: boxes of x, y side <= 32, <= 48, <= 64, larger
+PASS_TIERS = 5          # LSGG_PASS_TIERS: boxes of x, y side <= 32, <= 40, <= 48, <= 64, larger
 
 
 def pass_times(ctx):
