@@ -65,6 +65,35 @@ __device__ __forceinline__ void for_block(const SeedBins& S, int cx, int cy, int
     }
 }
 
+// Visit every seed in the bins that meet [x - r, x + r] on each axis (cyclic;
+// a range of a period or more visits the whole axis once).
+template <class F>
+__device__ __forceinline__ void for_reach(const SeedBins& S, float fx, float fy, float fz, float r, F f) {
+    const float c[3] = {fx, fy, fz};
+    int lo[3], cnt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (2.0f * r + 2.0f * S.size[a] >= (float)S.nb[a] * S.size[a]) { lo[a] = 0; cnt[a] = S.nb[a]; continue; }
+        const int l = (int)floorf((c[a] - r) / S.size[a]);
+        const int h = (int)floorf((c[a] + r) / S.size[a]);
+        cnt[a] = h - l + 1;
+        lo[a] = l;
+        if (cnt[a] >= S.nb[a]) { lo[a] = 0; cnt[a] = S.nb[a]; }
+        else { lo[a] %= S.nb[a]; if (lo[a] < 0) lo[a] += S.nb[a]; }
+    }
+    for (int iz = 0; iz < cnt[2]; ++iz) {
+        const int bz = wrap_bin(lo[2] + iz, S.nb[2]);
+        for (int iy = 0; iy < cnt[1]; ++iy) {
+            const int by = wrap_bin(lo[1] + iy, S.nb[1]);
+            const int row = (bz * S.nb[1] + by) * S.nb[0];
+            for (int ix = 0; ix < cnt[0]; ++ix) {
+                const int bin = row + wrap_bin(lo[0] + ix, S.nb[0]);
+                for (int q = S.start[bin]; q < S.start[bin + 1]; ++q) f(q);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256)
 k_labels(Domain D, int G, SeedBins S, const double* __restrict__ seeds, const double* __restrict__ weights,
          int* __restrict__ labels) {
@@ -90,11 +119,9 @@ k_labels(Domain D, int G, SeedBins S, const double* __restrict__ seeds, const do
     const float nmax = fmaxf(fnx, fmaxf(fny, fnz));
     // margin covering FP32 rounding of |d|^2 <= 3 N^2, of the seeds and of the weights
     auto margin = [&](float v) { return 0.5f + 4e-6f * nmax * nmax + 1e-5f * fabsf(v); };
-    int k[3] = {S.nb[0], S.nb[1], S.nb[2]};
-    if (bound < FLT_MAX) {
-        const float r = sqrtf(fmaxf(0.0f, bound + margin(bound) + S.wmax)) + 1.0f;   // + 1: bin-edge rounding
-        for (int a = 0; a < 3; ++a) k[a] = (int)ceilf(r / S.size[a]) + 1;
-    }
+    // every seed within the margin of the minimum lies within r of the cell
+    const float r = bound < FLT_MAX ? sqrtf(fmaxf(0.0f, bound + margin(bound) + S.wmax)) + 1.0f   // + 1: bin-edge rounding
+                                    : FLT_MAX;
     // one pass: the FP32 minimum and the seeds within the margin of the running
     // minimum (a superset of those within the margin of the final one); a
     // full candidate list falls back to a second pass
@@ -104,7 +131,7 @@ k_labels(Domain D, int G, SeedBins S, const double* __restrict__ seeds, const do
     int n_cand = 0;
     bool rescan = false;
     float best32 = FLT_MAX;
-    for_block(S, cx, cy, cz, k[0], k[1], k[2], [&](int q) {
+    for_reach(S, fx, fy, fz, r, [&](int q) {
         const float d = d32(q);
         best32 = fminf(best32, d);
         if (d <= best32 + margin(best32)) {
@@ -128,7 +155,7 @@ k_labels(Domain D, int G, SeedBins S, const double* __restrict__ seeds, const do
         for (int c = 0; c < n_cand; ++c)
             if (cand_d[c] <= lim) exact(cand[c]);
     } else {
-        for_block(S, cx, cy, cz, k[0], k[1], k[2], [&](int q) {
+        for_reach(S, fx, fy, fz, r, [&](int q) {
             if (d32(q) <= lim) exact(q);
         });
     }
@@ -225,18 +252,28 @@ __device__ __forceinline__ double power_dist(const double* p, const double* s, d
 // For cell p with displacement a = p - s_i (minimum image) and neighbour j
 // with D = s_i - s_j (minimum image), p - s_j = a + D up to one period per
 // axis; with d = (p - s_j) - a the bisector distance is
-// (d . (d + 2a) - (w_j - w_i)) / (2 |d|).  An FP32 pass over the neighbours
-// finds the candidates within a margin of the minimum; those are evaluated in
-// FP64 in that well-conditioned form (a reciprocal square root instead of a
-// square root and a division): the same value as the definition's
-// ((p - s_j)^2 - w_j - (p - s_i)^2 + w_i) / (2 |d|) up to FP64 rounding,
-// far below the FP32 result's half unit.
+// (d . (d + 2a) - (w_j - w_i)) / (2 |d|).  Where p - s_j needs no other
+// period than D's (every cell of a box small against the domain), d = D and
+// the distance is affine in a: n . a + c with n = D / |D| and
+// c = |D| / 2 - (w_j - w_i) / (2 |D|), both per pair, computed once per grain
+// in FP64.  An FP32 pass over the neighbours (3 FMAs each) finds the
+// candidates within a bound of its rounding error of the minimum; those are
+// evaluated in FP64 (3 FMAs): the definition's value
+// ((p - s_j)^2 - w_j - (p - s_i)^2 + w_i) / (2 |d|) up to FP64 rounding, far
+// below the FP32 result's half unit.  Cells where the image of s_j or of s_i
+// is too close to call in FP32 take the general form with a per-cell image.
+struct SdfPair {
+    double n0, n1, n2, c;
+};
+
 __global__ void __launch_bounds__(256)
 k_sdf(Domain D, int G, const Box* __restrict__ boxes, const double* __restrict__ seeds,
       const double* __restrict__ weights, const unsigned* __restrict__ bits, long long words_per_row,
       float* __restrict__ X, int* __restrict__ IDF, int* __restrict__ status) {
     __shared__ int s_nb[kSdfNb];
     __shared__ float4 s_d[kSdfNb];          // D = s_i - s_j (minimum image), w_j - w_i
+    __shared__ float4 s_f[kSdfNb];          // n and c in FP32
+    __shared__ SdfPair s_p[kSdfNb];         // n and c in FP64
     __shared__ int s_cnt;
     const int i = blockIdx.x;
     const Box b = boxes[i];
@@ -261,29 +298,84 @@ k_sdf(Domain D, int G, const Box* __restrict__ boxes, const double* __restrict__
     const double wi = weights ? weights[i] : 0.0;
     const double Nd[3] = {(double)D.nx, (double)D.ny, (double)D.nz};
     const float Nf[3] = {(float)D.nx, (float)D.ny, (float)D.nz};
+    const int Ni[3] = {D.nx, D.ny, D.nz};
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         const int j = s_nb[k];
         const double wj = weights ? weights[j] : 0.0;
-        s_d[k] = make_float4((float)min_image(si[0] - seeds[3 * j], Nd[0]), (float)min_image(si[1] - seeds[3 * j + 1], Nd[1]),
-                             (float)min_image(si[2] - seeds[3 * j + 2], Nd[2]), (float)(wj - wi));
+        const double d0 = min_image(si[0] - seeds[3 * j], Nd[0]), d1 = min_image(si[1] - seeds[3 * j + 1], Nd[1]),
+                     d2 = min_image(si[2] - seeds[3 * j + 2], Nd[2]);
+        s_d[k] = make_float4((float)d0, (float)d1, (float)d2, (float)(wj - wi));
+        const double len = sqrt(fma(d0, d0, fma(d1, d1, d2 * d2)));
+        SdfPair q;
+        q.n0 = d0 / len;
+        q.n1 = d1 / len;
+        q.n2 = d2 / len;
+        q.c = 0.5 * len - 0.5 * (wj - wi) / len;
+        s_p[k] = q;
+        s_f[k] = make_float4((float)q.n0, (float)q.n1, (float)q.n2, (float)q.c);
     }
     __syncthreads();
+    const float sif[3] = {(float)si[0], (float)si[1], (float)si[2]};
+    const float nmax = fmaxf(Nf[0], fmaxf(Nf[1], Nf[2]));
     const int A = b.nx * b.ny;
     const int ps = plane_stride(b.nx, b.ny);
     const int ncell = A * b.nz;
     const double eps = (double)D.eps;
+    const int o[3] = {b.ox, b.oy, b.oz};
     for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
         const int z = idx / A;
         const int rem = idx - z * A;
         const int y = rem / b.nx, x = rem - y * b.nx;
-        const double p[3] = {(double)pmod(b.ox + x, D.nx), (double)pmod(b.oy + y, D.ny), (double)pmod(b.oz + z, D.nz)};
+        const int l[3] = {x, y, z};
+        // the cell's global coordinates g and its displacement from s_i: the
+        // image decided in FP32 (g - (float)s_i is exact), FP64 only for the value
+        int g[3], sh[3];
+        float af[3];
+        bool amb = false;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int gc = o[c] + l[c];
+            if (gc >= Ni[c]) gc -= Ni[c];
+            g[c] = gc;
+            const float raw = (float)gc - sif[c];
+            const float h = 0.5f * Nf[c];
+            amb |= fabsf(fabsf(raw) - h) < 1e-2f;
+            sh[c] = raw > h ? -Ni[c] : (raw < -h ? Ni[c] : 0);
+            af[c] = raw + (float)sh[c];
+        }
         double a0, a1, a2;
-        power_dist(p, si, wi, Nd, a0, a1, a2);
-        const float af[3] = {(float)a0, (float)a1, (float)a2};
-        // FP32 screen: U bounds the exact minimum from above
+        if (amb) {
+            const double p[3] = {(double)g[0], (double)g[1], (double)g[2]};
+            power_dist(p, si, wi, Nd, a0, a1, a2);
+            af[0] = (float)a0;
+            af[1] = (float)a1;
+            af[2] = (float)a2;
+        } else {
+            a0 = __dsub_rn((double)(g[0] + sh[0]), si[0]);
+            a1 = __dsub_rn((double)(g[1] + sh[1]), si[1]);
+            a2 = __dsub_rn((double)(g[2] + sh[2]), si[2]);
+        }
         const float asum = fabsf(af[0]) + fabsf(af[1]) + fabsf(af[2]);
+        // whether neighbour k's image for this cell is D's (then the affine form
+        // holds); near half a period the general form decides
+        auto affine = [&](const float4& dk) {
+            bool ok = !amb;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float t = af[c] + (c == 0 ? dk.x : (c == 1 ? dk.y : dk.z));
+                ok &= fabsf(t) < 0.5f * Nf[c] - 1e-2f;
+            }
+            return ok;
+        };
         auto screen = [&](int k, float& v, float& err) {
             const float4 dk = s_d[k];
+            if (affine(dk)) {
+                const float4 f = s_f[k];
+                v = fmaf(f.x, af[0], fmaf(f.y, af[1], fmaf(f.z, af[2], f.w)));
+                // rounding of s_i, n and c to FP32 and of the three FMAs
+                err = 2.4e-7f * (3.0f * nmax + 2.0f * asum + 2.0f * fabsf(f.w) + 4.0f);
+                return;
+            }
             const float dd[3] = {dk.x, dk.y, dk.z};
             float num = -dk.w, den = 0.0f;
             bool near_half = false;                            // image choice too close to call in FP32
@@ -298,8 +390,8 @@ k_sdf(Domain D, int G, const Box* __restrict__ boxes, const double* __restrict__
             const float rinv = rsqrtf(den);
             v = 0.5f * num * rinv;
             // about 64 FP32 ulps of every term of num / (2 |d|), and of v
-            err = near_half ? FLT_MAX
-                            : 4e-6f * (0.5f * den * rinv + asum + 0.5f * fabsf(dk.w) * rinv + fabsf(v) + 1.0f);
+            err = near_half || amb ? FLT_MAX
+                                   : 4e-6f * (0.5f * den * rinv + asum + 0.5f * fabsf(dk.w) * rinv + fabsf(v) + 1.0f);
         };
         // one screening pass keeps the neighbours that may still be the minimum
         // (v - err <= the running bound U); a full list falls back to a rescan
@@ -323,13 +415,20 @@ k_sdf(Domain D, int G, const Box* __restrict__ boxes, const double* __restrict__
         int arg = -1;
         auto exact = [&](int k) {
             const int j = s_nb[k];
-            const double* sj = seeds + 3 * j;
-            const double d0 = __dsub_rn(min_image(__dsub_rn(p[0], sj[0]), Nd[0]), a0);
-            const double d1 = __dsub_rn(min_image(__dsub_rn(p[1], sj[1]), Nd[1]), a1);
-            const double d2 = __dsub_rn(min_image(__dsub_rn(p[2], sj[2]), Nd[2]), a2);
-            double num = fma(d0, fma(2.0, a0, d0), fma(d1, fma(2.0, a1, d1), d2 * fma(2.0, a2, d2)));
-            if (weights) num -= weights[j] - wi;
-            const double ve = num * (0.5 * rsqrt(fma(d0, d0, fma(d1, d1, d2 * d2))));
+            double ve;
+            if (affine(s_d[k])) {
+                const SdfPair q = s_p[k];
+                ve = fma(q.n0, a0, fma(q.n1, a1, fma(q.n2, a2, q.c)));
+            } else {
+                const double p[3] = {(double)g[0], (double)g[1], (double)g[2]};
+                const double* sj = seeds + 3 * j;
+                const double d0 = __dsub_rn(min_image(__dsub_rn(p[0], sj[0]), Nd[0]), a0);
+                const double d1 = __dsub_rn(min_image(__dsub_rn(p[1], sj[1]), Nd[1]), a1);
+                const double d2 = __dsub_rn(min_image(__dsub_rn(p[2], sj[2]), Nd[2]), a2);
+                double num = fma(d0, fma(2.0, a0, d0), fma(d1, fma(2.0, a1, d1), d2 * fma(2.0, a2, d2)));
+                if (weights) num -= weights[j] - wi;
+                ve = num * (0.5 * rsqrt(fma(d0, d0, fma(d1, d1, d2 * d2))));
+            }
             if (ve < best) { best = ve; arg = j; }
         };
         if (!rescan) {
@@ -343,9 +442,9 @@ k_sdf(Domain D, int G, const Box* __restrict__ boxes, const double* __restrict__
             }
         }
         const double outv = best == DBL_MAX ? eps : (best < -eps ? -eps : (best > eps ? eps : best));
-        const long long o = b.off + (long long)z * ps + rem;
-        X[o] = (float)outv;
-        if (IDF) IDF[o] = arg;
+        const long long off = b.off + (long long)z * ps + rem;
+        X[off] = (float)outv;
+        if (IDF) IDF[off] = arg;
     }
 }
 
