@@ -672,6 +672,10 @@ int lsgg_sync(lsgg_ctx* c, int64_t timeout_ms) {
     if (cudaSetDevice(c->device) != cudaSuccess) return CUDA_FAIL();
     for (int round = 0; round < 64; ++round) {
         auto t0 = std::chrono::steady_clock::now();
+        if (timeout_ms < 0) {
+            // no limit: a blocking wait returns as soon as the stream drains
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) return CUDA_FAIL();
+        }
         for (;;) {
             cudaError_t q = cudaStreamQuery(c->stream);
             if (q == cudaSuccess) break;
@@ -1042,14 +1046,23 @@ int lsgg_grain_volumes(lsgg_ctx* c, double* out, int64_t cap, int64_t* n_out) {
     if (!c) return LSGG_ERR_INVALID_ARG;
     if (n_out) *n_out = c->G;
     if (!out || cap < c->G) return LSGG_ERR_CAPACITY;
-    int r = lsgg_sync(c, -1);
-    if (r != LSGG_OK) return r;
-    const float* x = nullptr;
-    CK(state_as_f32(c, &x));
-    CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, x, c->d_vol, c->stream));
-    CK(cudaMemcpyAsync(out, c->d_vol, (size_t)c->G * 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return LSGG_OK;
+    // enqueued behind the pending steps, read back with their status in one
+    // wait; a step that stopped (arena overflow, error) goes through lsgg_sync
+    // and the volumes are taken again
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (attempt == 1) {
+            int r = lsgg_sync(c, -1);
+            if (r != LSGG_OK) return r;
+        }
+        const float* x = nullptr;
+        CK(state_as_f32(c, &x));
+        CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, x, c->d_vol, c->stream));
+        CK(cudaMemcpyAsync(out, c->d_vol, (size_t)c->G * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->h_st, c->B.st, sizeof(StepState), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->h_st->status == 0 && !c->h_st->halt) return LSGG_OK;
+    }
+    return c->h_st->status ? c->h_st->status : LSGG_ERR_CUDA;
 }
 
 int lsgg_grain_statistics(lsgg_ctx* c, int32_t n_bins, double r_max_rel, lsgg_grain_stats* out, double* hist) {

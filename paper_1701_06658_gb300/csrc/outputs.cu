@@ -49,11 +49,19 @@ k_volumes(Domain D, const Box* __restrict__ cur, const Box* __restrict__ prev, c
     if (cur[b].nx > 0) {
         const Box ob = prev[b];
         const int A = ob.nx * ob.ny, ps = plane_stride(ob.nx, ob.ny);
-        for (int z = 0; z < ob.nz; ++z) {
-            const float* pl = X + ob.off + (long long)z * ps;
+        // four planes per pass: four independent loads in flight per thread
+        for (int z0 = 0; z0 < ob.nz; z0 += 4) {
+            const float* pl = X + ob.off + (long long)z0 * ps;
+            const int nzp = min(4, ob.nz - z0);
             for (int i = threadIdx.x; i < A; i += blockDim.x) {
-                const int q = __float2int_rn(__ldg(pl + i) * kScale);   // |phi| <= eps: no overflow
-                acc += min(max(q + kHalf, 0), kOne);
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = u < nzp ? __ldg(pl + (long long)u * ps + i) : -1.0f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = __float2int_rn(v[u] * kScale);         // |phi| <= eps: no overflow
+                    acc += min(max(q + kHalf, 0), kOne);                 // phi = -1 (no plane): 0
+                }
             }
         }
     }
