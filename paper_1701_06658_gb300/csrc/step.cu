@@ -429,16 +429,55 @@ __device__ __forceinline__ void block_exclusive_scan(const int (&v)[N], int (&pr
     __syncthreads();
 }
 
-// Block-wide sum (s: blockDim long longs), the same value on every thread.
-__device__ __forceinline__ long long block_sum_ll(long long v, long long* s) {
+// Block-wide sums of N long longs per thread, the same values on every
+// thread afterwards (s: 32 * N long longs, free on entry and on return).
+template <int N>
+__device__ __forceinline__ void block_sums_ll(long long (&v)[N], long long* s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) s[warp * N + k] = v[k];
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        long long t = 0;
+        for (int w = 0; w < nw; ++w) t += s[w * N + k];
+        v[k] = t;
+    }
     __syncthreads();
-    long long t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
-    return t;
+}
+
+// Block-wide inclusive scan of one long long per thread in thread order
+// (warp shuffles; warp 0 scans the warp totals); *total = the block's sum
+// (s: 32 long longs, free on entry and on return).
+__device__ __forceinline__ long long block_inclusive_scan_ll(long long v, long long* s, long long* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < nw ? s[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) s[lane] = w;
+    }
+    __syncthreads();
+    const long long r = x + (warp ? s[warp - 1] : 0);
+    *total = s[nw - 1];
+    __syncthreads();
+    return r;
 }
 
 // Size class of a box: the smallest class whose side holds the x and y extents
@@ -463,7 +502,8 @@ __device__ __forceinline__ int pass_tier(const StepBuffers& B, int c) {
 // the re-initialisation of a coarsening).
 __global__ void __launch_bounds__(kBoxUpdateThreads)
 k_box_update(StepBuffers B, int layout_only, int count_step) {
-    __shared__ long long s_part[kBoxUpdateThreads];
+    static_assert(2 + kTiers <= 8 && kBoxUpdateThreads <= 1024, "the scratch holds 8 sums of 32 warps");
+    __shared__ long long s_part[32 * 8];
     __shared__ int s_scan[(kBoxUpdateThreads / 32) * (kNumClasses + 3 * kTiers)];
     const int G = B.n_boxes;
     const Domain D = B.dom;
@@ -507,16 +547,9 @@ k_box_update(StepBuffers B, int layout_only, int count_step) {
         }
         sum += box_elems(cb);
     }
-    s_part[threadIdx.x] = sum;
-    __syncthreads();
-    // inclusive scan of the per-thread sums (Hillis-Steele, fixed order)
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        long long v = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0;
-        __syncthreads();
-        s_part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    const long long total = s_part[blockDim.x - 1];
+    // inclusive scan of the per-thread sums (integer: the order does not matter)
+    long long total = 0;
+    const long long incl = block_inclusive_scan_ll(sum, s_part, &total);
     if (!layout_only && count_step && done) atomicAdd((unsigned long long*)&B.st->cell_updates, (unsigned long long)done);
     if (threadIdx.x == 0 && !layout_only && count_step) B.st->steps_done += 1;   // the step's fields are complete
     if (total > B.cap) {
@@ -527,7 +560,7 @@ k_box_update(StepBuffers B, int layout_only, int count_step) {
         }
         return;
     }
-    long long off = s_part[threadIdx.x] - sum;
+    long long off = incl - sum;
     // per-thread counts: boxes per class (work lists), pass-path planes,
     // column chunks and slabs per tier; their block-wide exclusive scans place
     // every box's entries in box order
@@ -593,11 +626,15 @@ k_box_update(StepBuffers B, int layout_only, int count_step) {
         pre[kNumClasses + 2 * kTiers + t] += nsl;
         B.item_base[b] = make_int4(p0, c0, s0, t);    // the items themselves: k_write_items
     }
-    // reduce cells / alive / tier cells
-    const long long r_cells = block_sum_ll(cells, s_part);
-    const long long r_alive = block_sum_ll(alive, s_part);
+    // reduce cells / alive / tier cells in one pass
+    long long red[2 + kTiers];
+    red[0] = cells;
+    red[1] = alive;
+    for (int t = 0; t < kTiers; ++t) red[2 + t] = tcell[t];
+    block_sums_ll<2 + kTiers>(red, s_part);
+    const long long r_cells = red[0], r_alive = red[1];
     long long r_tc[kTiers];
-    for (int t = 0; t < kTiers; ++t) r_tc[t] = block_sum_ll(tcell[t], s_part);
+    for (int t = 0; t < kTiers; ++t) r_tc[t] = red[2 + t];
     if (threadIdx.x == 0) B.st->box_cells = r_cells;
     if (threadIdx.x < kNumClasses) {
         B.st->class_count[threadIdx.x] = tot[threadIdx.x];
