@@ -74,6 +74,13 @@ code where it applies):
      R4's argmax over the other grains of the re-initialised functions.  Time
      and dt stay in grid units (one step's physical time grows with the
      spacing squared).
+  R14 size analysis (Sec. 5): rho = <R>^2 / <R^2> and Var(R / <R>) =
+     <R^2> / <R>^2 - 1 (= 1 / rho - 1, Eq. (varianz)) from the equivalent
+     radii of the grain volumes; Eq. (Rios) with the garbled factor
+     nu^(H0/2) read as nu^(H/2) (the only reading under which it is a
+     normalised density); the kinetic law is printed as
+     <R>^n - <R_0>^n = k t with exponents n = 0.45-0.46, which only makes
+     sense as <R> ~ t^n: we fit <R>^(1/n) - <R_0>^(1/n) = k t.
 """
 from __future__ import annotations
 
@@ -896,7 +903,7 @@ def grain_statistics(vol: np.ndarray, dim: int, n_bins: int, r_max: float) -> di
     r = (3.0 * v / (4.0 * math.pi)) ** (1.0 / 3.0) if dim == 3 else np.sqrt(v / math.pi)
     n = r.size
     out = {"alive": n, "mean_volume": 0.0, "mean_radius": 0.0, "rms_radius": 0.0, "max_radius": 0.0,
-           "overflow": 0.0, "hist": np.zeros(n_bins)}
+           "overflow": 0.0, "rho": 0.0, "var_z": 0.0, "hist": np.zeros(n_bins)}
     if n == 0:
         return out
     mean = r.mean()
@@ -904,8 +911,86 @@ def grain_statistics(vol: np.ndarray, dim: int, n_bins: int, r_max: float) -> di
     k = np.floor(rel / r_max * n_bins).astype(np.int64)
     for b in k[k < n_bins]:
         out["hist"][b] += 1.0
-    out.update(mean_volume=v.mean(), mean_radius=mean, rms_radius=math.sqrt((r * r).mean()), max_radius=r.max(),
-               overflow=float((k >= n_bins).sum()) / n)
+    msq = (r * r).mean()
+    out.update(mean_volume=v.mean(), mean_radius=mean, rms_radius=math.sqrt(msq), max_radius=r.max(),
+               overflow=float((k >= n_bins).sum()) / n,
+               rho=mean * mean / msq,                  # Sec. 5: rho = <R>^2 / <R^2>
+               var_z=msq / (mean * mean) - 1.0)        # Eq. (varianz): Var(R / <R>) = 1 / rho - 1
     out["hist"] /= n
     return out
 
+
+
+# --------------------------------------------------------------------------
+# size distributions and kinetics of the size analysis (Sec. 5, reading R14)
+# --------------------------------------------------------------------------
+
+
+def rios_pdf(z, nu: float, rho: float, H: float = 3.0):
+    """Eq. (Rios): Rios' distribution of z = R / <R> with H = 3, reading the
+    garbled factor nu^(H0/2) as nu^(H/2), the reading under which p
+    integrates to 1 (R14).  Valid for 0 < nu < 4."""
+    z = np.asarray(z, dtype=np.float64)
+    s = math.sqrt(4.0 * nu - nu * nu)
+    base = rho * rho * z * z - nu * rho * z + nu
+    ang = np.arctan((2.0 * rho * z - nu) / s) + math.atan(nu / s)
+    return z * rho * rho * H * nu ** (H / 2.0) / base ** (1.0 + H / 2.0) * np.exp(-H * nu / s * ang)
+
+
+def hillert_pdf(z):
+    """Hillert's 3D distribution written in z = R / <R>: with u = R / R_cr =
+    rho z and rho = 8/9, P(u) = (2e)^3 3u / (2 - u)^5 exp(-6 / (2 - u)) for
+    u < 2, so p(z) = rho P(rho z) (the nu -> 4 limit of Eq. (Rios))."""
+    z = np.asarray(z, dtype=np.float64)
+    rho = 8.0 / 9.0
+    u = rho * z
+    inside = u < 2.0
+    uu = np.where(inside, u, 0.0)
+    P = (2.0 * math.e) ** 3 * 3.0 * uu / (2.0 - uu) ** 5 * np.exp(-6.0 / (2.0 - uu))
+    return np.where(inside, rho * P, 0.0)
+
+
+def fit_rios_nu(hist: np.ndarray, r_max: float, rho: float) -> float:
+    """nu of Eq. (Rios) closest (least squares over the bins' centres) to a
+    measured distribution of R / <R> given as fractions per bin of
+    [0, r_max), with the measured rho (Sec. 5 fits nu and rho this way)."""
+    from scipy.optimize import minimize_scalar
+    n = len(hist)
+    w = r_max / n
+    zc = (np.arange(n) + 0.5) * w
+    dens = np.asarray(hist, dtype=np.float64) / w
+    res = minimize_scalar(lambda nu: float(((rios_pdf(zc, nu, rho) - dens) ** 2).sum()),
+                          bounds=(1e-3, 4.0 - 1e-6), method="bounded", options={"xatol": 1e-9})
+    return float(res.x)
+
+
+def fit_growth_exponent(t: np.ndarray, mean_r: np.ndarray):
+    """Kinetic exponent of Sec. 5 (R14): <R> ~ t^n, fitted in the printed law's
+    form <R>^(1/n) - <R_0>^(1/n) = k t (parabolic growth: n = 1/2) by least
+    squares over n, with k the least-squares slope through the origin for
+    each n and <R_0> the first sample.  Returns (n, k)."""
+    from scipy.optimize import minimize_scalar
+    t = np.asarray(t, dtype=np.float64)
+    r = np.asarray(mean_r, dtype=np.float64)
+    dt = t - t[0]
+
+    def cost(n):
+        y = r ** (1.0 / n) - r[0] ** (1.0 / n)
+        k = float((dt * y).sum() / (dt * dt).sum())
+        return float(((y - k * dt) ** 2).sum() / (y * y).sum()), k
+
+    res = minimize_scalar(lambda n: cost(n)[0], bounds=(0.05, 2.0), method="bounded", options={"xatol": 1e-10})
+    return float(res.x), cost(res.x)[1]
+
+
+def texture_shares(vol: np.ndarray, grain_class: np.ndarray, n_classes: int) -> np.ndarray:
+    """Volume fraction of each grain class (Sec. 5.3's texture components):
+    the class's summed volume over all grains' volume; grains of a class
+    outside [0, n_classes) count in the total only."""
+    vol = np.asarray(vol, dtype=np.float64)
+    out = np.zeros(n_classes)
+    for v, c in zip(vol, grain_class):
+        if 0 <= c < n_classes:
+            out[c] += v
+    tot = vol[vol > 0].sum()
+    return out / tot if tot > 0 else out

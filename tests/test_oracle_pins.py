@@ -814,3 +814,76 @@ def test_coarsen_rebuilds_the_id_field(oracle):
         inside &= (((pos[a] - cb[a][0]) % 20) < cb[a][1]).reshape(sh)
     assert np.array_equal(g0.idf, np.where(inside & (other > -7.0), 1, -1))
     assert (g0.idf == 1).any() and (~inside).any()
+
+
+# ---------------------------------------------------------------- size analysis (Sec. 5, R14)
+
+def _quad(f, a, b):
+    integrate = pytest.importorskip("scipy.integrate")
+    return integrate.quad(f, a, b, limit=400)[0]
+
+
+def test_rios_is_a_density_with_the_printed_moments(oracle):
+    """Eq. (Rios) with H = 3 integrates to 1 for any 0 < nu < 4 (this fixes
+    the garbled nu exponent, R14), and at the paper's steady state
+    (nu = 3.106, rho = 0.863) has E(z) = 1 and Var(z) = 1/rho - 1
+    (Eq. (varianz)) to the precision the paper's 'approximately' allows."""
+    c = json.load(open(GOLDEN))["size_distribution"]
+    for nu, rho in ((3.106, 0.863), (2.5, 0.8), (3.9, 0.85), (1.0, 0.7)):
+        assert abs(_quad(lambda z: float(oracle.rios_pdf(z, nu, rho)), 0.0, np.inf) - 1.0) < 1e-8
+    nu, rho = c["steady_nu"], c["steady_rho"]
+    m1 = _quad(lambda z: z * float(oracle.rios_pdf(z, nu, rho)), 0.0, np.inf)
+    m2 = _quad(lambda z: z * z * float(oracle.rios_pdf(z, nu, rho)), 0.0, np.inf)
+    assert abs(m1 - 1.0) < 5e-3
+    assert abs((m2 - m1 * m1) - (1.0 / rho - 1.0)) < 0.02 * (1.0 / rho - 1.0)
+
+
+def test_rios_tends_to_hillert(oracle):
+    """Sec. 5: nu -> 4 with rho = 8/9 gives Hillert's distribution; Hillert's
+    density (written independently from its own closed form) integrates to
+    1 with E(z) = 1 and Var(z) = 1/8 = 1/rho - 1."""
+    rho = json.load(open(GOLDEN))["size_distribution"]["hillert_rho"]
+    z = np.linspace(0.02, 2.4, 200)
+    for d in (1e-3, 1e-5, 1e-7):
+        err = np.max(np.abs(oracle.rios_pdf(z, 4.0 - d, rho) - oracle.hillert_pdf(z)))
+        assert err < 30.0 * d, (d, err)
+    top = 2.0 / rho
+    assert abs(_quad(lambda q: float(oracle.hillert_pdf(q)), 0.0, top) - 1.0) < 1e-10
+    assert abs(_quad(lambda q: q * float(oracle.hillert_pdf(q)), 0.0, top) - 1.0) < 1e-10
+    var = _quad(lambda q: q * q * float(oracle.hillert_pdf(q)), 0.0, top) - 1.0
+    assert abs(var - (1.0 / rho - 1.0)) < 1e-10
+
+
+def test_grain_statistics_rho_and_variance(oracle):
+    """Radii 1 and 3: <R> = 2, <R^2> = 5, so rho = 4/5 and Var(z) = 1/4 =
+    1/rho - 1 exactly."""
+    vol = np.array([4.0 / 3.0 * math.pi, 4.0 / 3.0 * math.pi * 27.0, 0.0])
+    st = oracle.grain_statistics(vol, 3, 10, 3.0)
+    assert abs(st["rho"] - 0.8) < 1e-14
+    assert abs(st["var_z"] - 0.25) < 1e-14
+
+
+def test_growth_exponent_fit_recovers_the_law(oracle):
+    """Exact series of <R>^(1/n) - <R_0>^(1/n) = k t: the fit returns (n, k),
+    for the parabolic law (n = 1/2) and for the paper's n = 0.458."""
+    t = np.linspace(0.0, 400.0, 60)
+    for n, k, r0 in ((0.5, 0.7, 3.0), (0.458, 0.21, 5.0)):
+        r = (r0 ** (1.0 / n) + k * t) ** n
+        fn, fk = oracle.fit_growth_exponent(t, r)
+        assert abs(fn - n) < 1e-6 and abs(fk - k) < 1e-5 * k, (n, fn, k, fk)
+
+
+def test_rios_nu_fit_recovers_nu(oracle):
+    """A histogram of Eq. (Rios)'s bin-centre densities at the paper's
+    steady state returns its nu."""
+    c = json.load(open(GOLDEN))["size_distribution"]
+    n_bins, r_max = 30, 3.0
+    zc = (np.arange(n_bins) + 0.5) * (r_max / n_bins)
+    hist = oracle.rios_pdf(zc, c["steady_nu"], c["steady_rho"]) * (r_max / n_bins)
+    assert abs(oracle.fit_rios_nu(hist, r_max, c["steady_rho"]) - c["steady_nu"]) < 1e-5
+
+
+def test_texture_shares_by_hand(oracle):
+    vol = np.array([10.0, 30.0, 0.0, 60.0])
+    cls = np.array([0, 1, 1, -1])
+    assert np.allclose(oracle.texture_shares(vol, cls, 2), [0.1, 0.3], rtol=0, atol=1e-15)
