@@ -152,8 +152,39 @@ typedef struct lsgg_grain_stats {
     double rms_radius;
     double max_radius;
     double overflow;
+    double rho;                /* <R>^2 / <R^2> (Sec. 5) */
+    double var_z;              /* Var(R / <R>) = <R^2> / <R>^2 - 1 = 1 / rho - 1 (Eq. (varianz)) */
 } lsgg_grain_stats;
 int lsgg_grain_statistics(lsgg_ctx* ctx, int32_t n_bins, double r_max_rel, lsgg_grain_stats* out, double* hist);
+
+/* Texture shares (Sec. 5.3's texture components): for each class c in
+ * [0, n_classes), the summed volume of the grains with grain_class[id] == c
+ * over the summed volume of all grains (grains of other classes count in the
+ * total only).  grain_class: host array of n_grains int32; out: host array of
+ * n_classes doubles; 1 <= n_classes <= 4096.  Computed on the device from the
+ * grain volumes with compensated sums in a fixed order (deterministic).
+ * Synchronises. */
+int lsgg_texture_shares(lsgg_ctx* ctx, const int32_t* grain_class, int32_t n_classes, double* out);
+
+/* Size analysis of Sec. 5 on the host (no context, no device).
+ * lsgg_rios_pdf: Rios' distribution of z = R / <R> (Eq. (Rios), H = 3, the
+ * printed factor nu^(H0/2) read as nu^(H/2), under which it integrates to
+ * 1); NaN unless 0 < nu < 4, rho > 0 and z >= 0.
+ * lsgg_hillert_pdf: Hillert's distribution in z, rho P(rho z) with
+ * rho = 8/9 and P(u) = (2e)^3 3u / (2 - u)^5 exp(-6 / (2 - u)) for u < 2 (the
+ * nu -> 4 limit of Rios').
+ * lsgg_fit_rios_nu: the nu in (0, 4) whose Rios density is closest (least
+ * squares at the bin centres) to hist, fractions per bin of [0, r_max_rel)
+ * as lsgg_grain_statistics gives them, for the given rho.
+ * lsgg_fit_growth_exponent: the kinetic exponent n of <R> ~ t^n and k, fitted
+ * as <R>^(1/n) - <R_0>^(1/n) = k t (the printed law <R>^n - <R_0>^n = k t
+ * read with the reported n = 0.45-0.46 as the exponent of <R>) over n
+ * samples (t increasing, <R> > 0; n >= 3), n searched in [0.05, 2].
+ * The fits return LSGG_ERR_INVALID_ARG for invalid input. */
+double lsgg_rios_pdf(double z, double nu, double rho);
+double lsgg_hillert_pdf(double z);
+int lsgg_fit_rios_nu(const double* hist, int32_t n_bins, double r_max_rel, double rho, double* nu);
+int lsgg_fit_growth_exponent(const double* t, const double* mean_r, int32_t n, double* n_out, double* k_out);
 
 /* Grid coarsening (Sec. 4.1: as the population falls the spacing grows so a
  * grain keeps about the same number of cells; each function is projected to

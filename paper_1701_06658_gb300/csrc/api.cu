@@ -1073,13 +1073,14 @@ int lsgg_grain_statistics(lsgg_ctx* c, int32_t n_bins, double r_max_rel, lsgg_gr
     CK(state_as_f32(c, &x));
     CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, x, c->d_vol, c->stream));
     double* d = nullptr;
-    if ((r = dalloc(c, &d, (size_t)n_bins + 6)) != LSGG_OK) return r;
-    cudaError_t e = launch_grain_stats(c->d_vol, c->G, c->dom.dim, n_bins, r_max_rel, d, d + 6, c->stream);
-    double h[6];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 6 * 8, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hist, d + 6, (size_t)n_bins * 8, cudaMemcpyDeviceToHost, c->stream);
+    constexpr int kHead = 8;
+    if ((r = dalloc(c, &d, (size_t)n_bins + kHead)) != LSGG_OK) return r;
+    cudaError_t e = launch_grain_stats(c->d_vol, c->G, c->dom.dim, n_bins, r_max_rel, d, d + kHead, c->stream);
+    double h[kHead];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, kHead * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hist, d + kHead, (size_t)n_bins * 8, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    c->device_bytes -= (long long)(n_bins + 6) * 8;
+    c->device_bytes -= (long long)(n_bins + kHead) * 8;
     dfree(c, d);
     if (e != cudaSuccess) return LSGG_ERR_CUDA;
     out->alive = (int64_t)h[0];
@@ -1088,7 +1089,34 @@ int lsgg_grain_statistics(lsgg_ctx* c, int32_t n_bins, double r_max_rel, lsgg_gr
     out->rms_radius = h[3];
     out->max_radius = h[4];
     out->overflow = h[5];
+    out->rho = h[6];
+    out->var_z = h[7];
     return LSGG_OK;
+}
+
+int lsgg_texture_shares(lsgg_ctx* c, const int32_t* grain_class, int32_t n_classes, double* out) {
+    if (!c || !grain_class || !out || n_classes < 1 || n_classes > 4096) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    const float* x = nullptr;
+    CK(state_as_f32(c, &x));
+    CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, x, c->d_vol, c->stream));
+    int* dc = nullptr;
+    double* d = nullptr;
+    if ((r = dalloc(c, &dc, (size_t)c->G)) != LSGG_OK) return r;
+    if ((r = dalloc(c, &d, (size_t)n_classes + 1)) != LSGG_OK) {
+        c->device_bytes -= (long long)c->G * 4;
+        dfree(c, dc);
+        return r;
+    }
+    cudaError_t e = cudaMemcpyAsync(dc, grain_class, (size_t)c->G * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_texture_shares(c->d_vol, dc, c->G, n_classes, d, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)n_classes * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->device_bytes -= (long long)c->G * 4 + (long long)(n_classes + 1) * 8;
+    dfree(c, dc);
+    dfree(c, d);
+    return e == cudaSuccess ? LSGG_OK : LSGG_ERR_CUDA;
 }
 
 // Coarse origin and extent of a fine box [o, o + n) on an axis coarsened

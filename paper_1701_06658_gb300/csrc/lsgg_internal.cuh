@@ -227,6 +227,8 @@ cudaError_t launch_reinit(const StepBuffers& B, const Taps& taps, const PhysicsD
 // `fine` (its box `fine_boxes`, values from the FP32 state in the `prev`
 // layout) projected trilinearly into Z in the `cur` layout on B.dom, scaled by
 // the spacing ratio and clamped
+cudaError_t launch_texture_shares(const double* vol, const int* cls, int G, int n_classes, double* out,
+                                  cudaStream_t s);
 cudaError_t launch_coarsen(const StepBuffers& B, const Domain& fine, const Box* fine_boxes, const float* state,
                            cudaStream_t s);
 

@@ -283,11 +283,60 @@ k_grain_stats(const double* __restrict__ vol, int G, int dim, int n_bins, double
         out[0] = n;
         out[1] = n > 0.0 ? __dadd_rn(s_s[1][0], s_c[1][0]) / n : 0.0;
         out[2] = mean_r;
-        out[3] = n > 0.0 ? sqrt(__dadd_rn(s_s[3][0], s_c[3][0]) / n) : 0.0;
+        const double msq = n > 0.0 ? __dadd_rn(s_s[3][0], s_c[3][0]) / n : 0.0;
+        out[3] = sqrt(msq);
         out[4] = s_max[0];
         out[5] = n > 0.0 ? (double)s_bins[n_bins] / n : 0.0;
+        out[6] = msq > 0.0 ? mean_r * mean_r / msq : 0.0;            // rho = <R>^2 / <R^2>
+        out[7] = mean_r > 0.0 ? msq / (mean_r * mean_r) - 1.0 : 0.0;  // Var(R / <R>) = 1 / rho - 1
     }
     for (int k = t; k < n_bins; k += blockDim.x) hist[k] = n > 0.0 ? (double)s_bins[k] / n : 0.0;
+}
+
+// Texture shares: per class c < n_classes, the summed volume of its grains
+// over the summed volume of all grains, each sum compensated (TwoSum) per
+// thread and merged in a fixed tree order (deterministic).  One CTA; out:
+// n_classes + 1 doubles (the last: the total volume).
+__global__ void __launch_bounds__(kStatsThreads)
+k_texture_shares(const double* __restrict__ vol, const int* __restrict__ cls, int G, int n_classes,
+                 double* __restrict__ out) {
+    __shared__ double s_s[kStatsThreads], s_c[kStatsThreads];
+    const int t = threadIdx.x;
+    for (int c = -1; c < n_classes; ++c) {            // c = -1: all grains
+        double sum = 0.0, comp = 0.0;
+        for (int i = t; i < G; i += blockDim.x) {
+            const double v = vol[i];
+            if (!(v > 0.0) || (c >= 0 && cls[i] != c)) continue;
+            double s2, e;
+            two_sum(sum, v, s2, e);
+            sum = s2;
+            comp = __dadd_rn(comp, e);
+        }
+        s_s[t] = sum;
+        s_c[t] = comp;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (t < o) {
+                double s2, e;
+                two_sum(s_s[t], s_s[t + o], s2, e);
+                s_s[t] = s2;
+                s_c[t] = __dadd_rn(__dadd_rn(s_c[t], s_c[t + o]), e);
+            }
+            __syncthreads();
+        }
+        if (t == 0) out[c < 0 ? n_classes : c] = __dadd_rn(s_s[0], s_c[0]);
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double tot = out[n_classes];
+        for (int c = 0; c < n_classes; ++c) out[c] = tot > 0.0 ? out[c] / tot : 0.0;
+    }
+}
+
+cudaError_t launch_texture_shares(const double* vol, const int* cls, int G, int n_classes, double* out,
+                                  cudaStream_t s) {
+    k_texture_shares<<<1, kStatsThreads, 0, s>>>(vol, cls, G, n_classes, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_grain_stats(const double* vol, int G, int dim, int n_bins, double r_max, double* out,

@@ -69,7 +69,8 @@ class Stats(C.Structure):
 class GrainStats(C.Structure):
     """Mirror of ``lsgg_grain_stats``."""
     _fields_ = [("alive", C.c_int64), ("mean_volume", C.c_double), ("mean_radius", C.c_double),
-                ("rms_radius", C.c_double), ("max_radius", C.c_double), ("overflow", C.c_double)]
+                ("rms_radius", C.c_double), ("max_radius", C.c_double), ("overflow", C.c_double),
+                ("rho", C.c_double), ("var_z", C.c_double)]
 
 
 class LsggError(RuntimeError):
@@ -90,6 +91,11 @@ _SIGS = {
     "lsgg_voxel_owner": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
     "lsgg_grain_statistics": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(GrainStats), _dp]),
     "lsgg_coarsen": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "lsgg_texture_shares": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, _dp]),
+    "lsgg_rios_pdf": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+    "lsgg_hillert_pdf": (C.c_double, [C.c_double]),
+    "lsgg_fit_rios_nu": (C.c_int, [_dp, C.c_int32, C.c_double, C.c_double, _dp]),
+    "lsgg_fit_growth_exponent": (C.c_int, [_dp, _dp, C.c_int32, _dp, _dp]),
     "lsgg_destroy": (C.c_int, [C.c_void_p]),
     "lsgg_status_string": (C.c_char_p, [C.c_int]),
     "lsgg_get_stream": (C.c_void_p, [C.c_void_p]),
@@ -204,6 +210,39 @@ def grain_statistics(ctx, n_bins: int = 20, r_max: float = 3.0) -> dict:
     out = {f: getattr(st, f) for f, _ in GrainStats._fields_}
     out["hist"] = hist
     return out
+
+
+def texture_shares(ctx, grain_class, n_classes: int) -> np.ndarray:
+    """Volume fraction of each grain class (see lsgg.h)."""
+    cls = np.ascontiguousarray(grain_class, dtype=np.int32)
+    out = np.zeros(n_classes, np.float64)
+    _check("texture_shares", lib().lsgg_texture_shares(ctx, _ptr(cls, C.c_int32), n_classes, _ptr(out, C.c_double)))
+    return out
+
+
+def rios_pdf(z: float, nu: float, rho: float) -> float:
+    return lib().lsgg_rios_pdf(z, nu, rho)
+
+
+def hillert_pdf(z: float) -> float:
+    return lib().lsgg_hillert_pdf(z)
+
+
+def fit_rios_nu(hist, r_max_rel: float, rho: float) -> float:
+    h = np.ascontiguousarray(hist, dtype=np.float64)
+    nu = C.c_double()
+    _check("fit_rios_nu", lib().lsgg_fit_rios_nu(_ptr(h, C.c_double), h.size, r_max_rel, rho, C.byref(nu)))
+    return nu.value
+
+
+def fit_growth_exponent(t, mean_r):
+    """(n, k) of <R> ~ t^n fitted as <R>^(1/n) - <R_0>^(1/n) = k t (see lsgg.h)."""
+    tt = np.ascontiguousarray(t, dtype=np.float64)
+    rr = np.ascontiguousarray(mean_r, dtype=np.float64)
+    n, k = C.c_double(), C.c_double()
+    _check("fit_growth_exponent", lib().lsgg_fit_growth_exponent(_ptr(tt, C.c_double), _ptr(rr, C.c_double),
+                                                                 tt.size, C.byref(n), C.byref(k)))
+    return n.value, k.value
 
 
 def coarsen(ctx, nx: int, ny: int, nz: int):
@@ -423,6 +462,9 @@ class Microstructure:
 
     def grain_statistics(self, n_bins: int = 20, r_max: float = 3.0) -> dict:
         return grain_statistics(self.ctx, n_bins, r_max)
+
+    def texture_shares(self, grain_class, n_classes: int) -> np.ndarray:
+        return texture_shares(self.ctx, grain_class, n_classes)
 
     def coarsen(self, nx: int, ny: int, nz: int):
         coarsen(self.ctx, nx, ny, nz)

@@ -397,7 +397,7 @@ def test_grain_statistics_on_device(L):
         vol = ms.grain_volumes()
     want = O.grain_statistics(vol, 3, 16, 2.5)
     assert st["alive"] == want["alive"]
-    for k in ("mean_volume", "mean_radius", "rms_radius", "max_radius", "overflow"):
+    for k in ("mean_volume", "mean_radius", "rms_radius", "max_radius", "overflow", "rho", "var_z"):
         assert abs(st[k] - want[k]) <= 1e-12 * max(1.0, abs(want[k])), k
     assert np.array_equal(st["hist"], want["hist"])
     ref = O.run(O.tessellate((N, N, N), seeds), 20, 1.0)
@@ -405,3 +405,22 @@ def test_grain_statistics_on_device(L):
     assert st["alive"] == ow["alive"]
     assert abs(st["mean_radius"] - ow["mean_radius"]) / ow["mean_radius"] < 1e-3
 
+
+
+def test_texture_shares_on_device(L):
+    """Volume fractions of grain classes (Sec. 5.3's texture components): the
+    device's compensated sums equal the oracle's shares of the device's own
+    volumes to rounding, and the shares of a partition sum to 1."""
+    N, G = 64, 50
+    seeds = I.voronoi_seeds(2, G, (N, N, N))
+    cls = (np.arange(G) * 7) % 3
+    cls[5] = -1                       # a grain in no class
+    with L.Microstructure(N, N, N, G, seeds=seeds) as ms:
+        ms.step(5, 1.0)
+        sh = ms.texture_shares(cls, 3)
+        vol = ms.grain_volumes()
+        full = ms.texture_shares(np.zeros(G, np.int32), 1)
+    want = O.texture_shares(vol, cls, 3)
+    assert np.max(np.abs(sh - want)) <= 1e-14
+    assert abs(full[0] - 1.0) <= 1e-15
+    assert sh.sum() < 1.0
