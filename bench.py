@@ -366,12 +366,19 @@ def gpu_arm(args):
     # ---------------- grid coarsening (Sec. 4.1) of the same workload ----------------
     # lsgg_coarsen to half the cells per axis after a few steps (host wall clock
     # around the synchronising call), then device-timed steps on the coarse grid
-    coarsening = None
+    coarsening = statistics = None
     if not args.no_compare and rank == 0 and WORKLOAD.get("physics", "ideal") == "ideal" and n % 2 == 0:
         with L.Microstructure(n, n, n, g, seeds=seeds, device=local, exec_mode=exec_mode,
                               **workload_kwargs(L)) as km:
             km.step(5, dt)
             km.sync()
+            # the size analysis on the device (Sec. 5): statistics and texture shares
+            t0 = time.perf_counter()
+            gs = km.grain_statistics(20, 3.0)
+            t_stats = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            km.texture_shares(np.arange(g, dtype=np.int32) % 2, 2)
+            t_tex = time.perf_counter() - t0
             fine_cells = km.stats().box_cells
             t0 = time.perf_counter()
             km.coarsen(n // 2, n // 2, n // 2)
@@ -391,6 +398,9 @@ def gpu_arm(args):
             torch.cuda.synchronize()
             kms = e0.elapsed_time(e1)
             k_rate = (km.stats().cell_updates - c0) / (kms * 1e-3)
+        statistics = {"grain_statistics_ms": 1e3 * t_stats, "texture_shares_ms": 1e3 * t_tex,
+                      "alive": int(gs["alive"]), "rho": gs["rho"], "var_z": gs["var_z"],
+                      "timing": "host wall clock around each synchronising call after 5 steps"}
         coarsening = {"from": [n, n, n], "to": [n // 2] * 3, "ms": 1e3 * el,
                       "timing": "host wall clock around lsgg_coarsen (box copies, relayout, projection, "
                                 "re-initialisation, box update; synchronising)",
@@ -468,6 +478,7 @@ def gpu_arm(args):
         "compare": compare,
         "bf16_storage": bf16,
         "coarsening": coarsening,
+        "size_analysis": statistics,
         "speedup_vs_plain_gpu": None if not compare else value / compare["plain_gpu"]["value"],
     }
     print(json.dumps(line), flush=True)
