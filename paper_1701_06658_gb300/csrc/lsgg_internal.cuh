@@ -180,7 +180,7 @@ struct StepBuffers {
     int use_passes;
     int tier_side[kTiers];
     int tier_threads[kTiers];       // threads per CTA of the plane passes (= tier side)
-    int pgrid[kTiers][5];           // persistent grid per tier and pass (conv_xy, conv_z, -, redist_xy, redist_z)
+    int pgrid[kTiers][5];           // persistent grid per tier and pass (conv_xy, conv_z ideal, conv_z physics, redist_xy, redist_z)
     // field pass: boxes overlapping each domain tile of kTileX x kTileY x kTileZ cells
     int* tile_cnt;                  // [n_tiles]
     int* tile_list;                 // [n_tiles * kTileCap]

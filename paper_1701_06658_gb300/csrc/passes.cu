@@ -1484,18 +1484,19 @@ static bool pass_fns(int R, bool phys, PassFns* f) {
 }
 
 cudaError_t configure_passes(StepBuffers& B) {
-    PassFns fn;
-    if (!pass_fns(B.dom.radius, true, &fn)) return cudaErrorInvalidValue;
+    PassFns fn, fn_ideal;
+    if (!pass_fns(B.dom.radius, true, &fn) || !pass_fns(B.dom.radius, false, &fn_ideal)) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     for (int t = 0; t < kTiers; ++t) {
         B.tier_side[t] = kTierSide[t];
         B.tier_threads[t] = kTierSide[t];
-        int o[5] = {0, 0, 1, 0, 0};
+        int o[5] = {0, 0, 0, 0, 0};       // conv_xy, conv_z (ideal), conv_z (physics), redist_xy, redist_z
         e = t == kBigTier ? cudaSuccess : allow_max_dynamic_smem(fn.conv_xy[t]);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], fn.conv_xy[t], kConvThreads[t],
                                                               conv_smem_bytes(kTierSide[t], B.dom.radius));
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], fn.conv_z, kColThreads, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], fn_ideal.conv_z, kColThreads, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], fn.conv_z, kColThreads, 0);
         if (e == cudaSuccess && t != kBigTier) e = allow_max_dynamic_smem(fn.redist_xy[t]);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], fn.redist_xy[t], kRedistThreads[t],
@@ -1541,7 +1542,7 @@ cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps&
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
         void* a1[] = {&bb, &tp, &ph, &tr};
-        e = cudaLaunchKernel(fn.conv_z, dim3(g[1]), dim3(kColThreads), a1, 0, s);
+        e = cudaLaunchKernel(fn.conv_z, dim3(g[phys.kind != LSGG_PHYSICS_IDEAL ? 2 : 1]), dim3(kColThreads), a1, 0, s);
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
     } else {
