@@ -503,10 +503,9 @@ struct TileBox {
     int nx, ny;               // box x, y sides
     int ps;                   // plane stride
     int id;                   // grain id
-    unsigned ymask;           // affine: bit ly: row ly of the tile lies in the box
-    unsigned xzm;             // bits 0-7: columns (affine), 8-15: planes (both), bit 31: affine
+    unsigned xmask, ymask;    // affine: bit lx / ly: column / row of the tile lies in the box
+    unsigned zm;              // bits 0-7: planes (both paths), bit 31: affine
     int dx, dy, dz;           // general: box-local coordinates of the tile corner (cyclic)
-    int pad;
 };
 
 // One axis of the tile -> box map: tile cells l in [0, T) with box-local
@@ -539,15 +538,16 @@ __device__ __forceinline__ void stage_tile_box(const StepBuffers& B, int b, int 
     unsigned mx, my, mz;
     if (bx.nx <= 0) {
         t.off = 0;
-        t.ymask = 0;
-        t.xzm = 1u << 31;                   // affine and empty
+        t.xmask = t.ymask = 0;
+        t.zm = 1u << 31;                    // affine and empty
         return;
     }
     if (tile_axis(tx0, ntx, D.nx, bx.ox, bx.nx, sx, mx) && tile_axis(ty0, nty, D.ny, bx.oy, bx.ny, sy, my) &&
         tile_axis(z0, nzt, D.nz, bx.oz, bx.nz, sz, mz)) {
         t.off = bx.off + (long long)sz * t.ps + (long long)sy * bx.nx + sx;
+        t.xmask = mx;
         t.ymask = my;
-        t.xzm = (1u << 31) | (mz << 8) | mx;
+        t.zm = (1u << 31) | mz;
         return;
     }
     unsigned m = 0;
@@ -557,8 +557,8 @@ __device__ __forceinline__ void stage_tile_box(const StepBuffers& B, int b, int 
         if (lz < bx.nz) m |= 1u << zz;
     }
     t.off = bx.off;
-    t.ymask = 0;
-    t.xzm = m << 8;
+    t.xmask = t.ymask = 0;
+    t.zm = m;
 }
 
 // (v, id) enters the top two (v1, i1) >= (v2, i2) of a cell; absent entries
@@ -623,12 +623,12 @@ p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
                 if (!col) continue;
                 for (int k = 0; k < nb; ++k) {
                     const TileBox& t = s_tb[k];
-                    const unsigned xzm = t.xzm;
-                    const unsigned zm = (xzm >> 8) & 0xffu;
+                    const unsigned zaff = t.zm;
+                    const unsigned zm = zaff & 0xffu;
                     const int id = t.id, ps = t.ps;
                     long long o[kTileZ];                // arena offsets of the column's cells
-                    if (xzm >> 31) {                    // affine (uniform across the CTA)
-                        if (!((xzm >> lx) & (t.ymask >> ly) & 1u)) continue;
+                    if (zaff >> 31) {                   // affine (uniform across the CTA)
+                        if (!((t.xmask >> lx) & (t.ymask >> ly) & 1u)) continue;
                         const long long oc = t.off + (long long)(ly * t.nx + lx);
 #pragma unroll
                         for (int zz = 0; zz < kTileZ; ++zz) o[zz] = oc + (long long)zz * ps;
