@@ -1151,9 +1151,6 @@ int lsgg_coarsen(lsgg_ctx* c, int32_t nx, int32_t ny, int32_t nz) {
     // would start from) -> candidate boxes on the coarse grid
     std::vector<Box> hp((size_t)c->G), hc((size_t)c->G);
     CK(cudaMemcpy(hp.data(), c->B.cur, (size_t)c->G * sizeof(Box), cudaMemcpyDeviceToHost));
-    Box* d_fine = nullptr;
-    if ((r = dalloc(c, &d_fine, (size_t)c->G)) != LSGG_OK) return r;
-    CK(cudaMemcpy(d_fine, hp.data(), (size_t)c->G * sizeof(Box), cudaMemcpyHostToDevice));
     const int N[3] = {fine.nx, fine.ny, fine.nz}, N2[3] = {nx, ny, nz};
     for (int b = 0; b < c->G; ++b) {
         Box o = hp[b], q{};
@@ -1173,7 +1170,11 @@ int lsgg_coarsen(lsgg_ctx* c, int32_t nx, int32_t ny, int32_t nz) {
     c->B.dom = c->dom;
     CK(configure_passes(c->B));
     CK(cudaMemcpy(c->B.cur, hc.data(), (size_t)c->G * sizeof(Box), cudaMemcpyHostToDevice));
-    r = relayout(c);
+    Box* d_fine = nullptr;                               // the grains' fine boxes, for the projection
+    if ((r = dalloc(c, &d_fine, (size_t)c->G)) != LSGG_OK) return r;
+    r = cudaMemcpy(d_fine, hp.data(), (size_t)c->G * sizeof(Box), cudaMemcpyHostToDevice) == cudaSuccess ? LSGG_OK
+                                                                                                     : LSGG_ERR_CUDA;
+    if (r == LSGG_OK) r = relayout(c);
     // projection into Z, then the re-initialisation and box update of a step
     const float* x = nullptr;
     cudaError_t e = cudaSuccess;
