@@ -183,3 +183,31 @@ def test_coarsen_with_read_shockley_rebuilds_the_id_field(L):
         idf = {g: ref.grains[g].idf for g in range(G) if ref.grains[g].alive}
         nxt = oracle_from_gpu((N2, N2, N2), boxes2, phi2, idf_by_grain=idf, physics=phys)
         _compare_step(L, ms, nxt)
+
+
+def test_coarsen_with_bf16_storage(L):
+    """BF16 state storage: the projection reads the FP32 view of the state and
+    the re-initialisation stores BF16 again.  From the same FP32-exact start
+    the coarsened BF16 state equals the FP32 run's coarsened state up to the
+    storage rounding (2^-8 relative) and a few sign-tie cells, with the same
+    grains alive."""
+    N, G = 64, 40
+    seeds = I.voronoi_seeds(9, G, (N, N, N))
+    out = {}
+    for st in (L.STORAGE_FP32, L.STORAGE_BF16):
+        with L.Microstructure(N, N, N, G, seeds=seeds, storage=st) as ms:
+            ms.coarsen(48, 48, 48)
+            out[st] = (ms.boxes(), ms.phi(), ms.grain_volumes())
+    b32, p32, v32 = out[L.STORAGE_FP32]
+    b16, p16, v16 = out[L.STORAGE_BF16]
+    assert np.array_equal(b32[:, 0], b16[:, 0])
+    same = 0
+    for g in range(G):
+        if not b32[g, 0] or not np.array_equal(b32[g], b16[g]):
+            continue
+        same += 1
+        d = np.abs(p16[g] - p32[g]) - 2.0 ** -7 * np.abs(p32[g]) - 2e-2
+        assert np.mean(d > 0) < 0.01, g
+    assert same >= G - 2
+    alive = v32 > 50
+    assert np.max(np.abs(v16[alive] - v32[alive]) / v32[alive]) < 5e-3
