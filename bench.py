@@ -82,6 +82,25 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def step_roofline(box_cells: float, dom_cells: float, ms_per_step: float, peak_gbs: float, passes: bool):
+    """The whole step against the bytes the method must move at least (one
+    FP32 read and write of phi per box cell, 44 B of top-two field per domain
+    cell: 16 cleared, 16 written, 12 read) and against the bytes of this
+    design's five passes (44 B per box cell: 8 each for the x/y and z
+    convolution and re-initialisation passes, 12 for the field pass; 16 B of
+    field per domain cell), both over the measured step time."""
+    minimum = 8.0 * box_cells + 44.0 * dom_cells
+    design = (44.0 * box_cells + 16.0 * dom_cells) if passes else None
+    t = ms_per_step * 1e-3
+    out = {"minimum_bytes_per_step": minimum, "minimum_bound_ms": minimum / (peak_gbs * 1e9) * 1e3,
+           "achieved_minimum_gbs": minimum / t / 1e9, "frac_minimum": minimum / t / 1e9 / peak_gbs,
+           "peak": peak_gbs, "unit": "GB/s"}
+    if design is not None:
+        out.update(design_bytes_per_step=design, achieved_design_gbs=design / t / 1e9,
+                   frac_design=design / t / 1e9 / peak_gbs)
+    return out
+
+
 def profiled_traffic(kernel: str, units_per_launch: float):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
     to this launch by units processed; None if the kernel changed since."""
@@ -465,6 +484,8 @@ def gpu_arm(args):
                      "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": achieved / peaks.get("hbm_gbs"), "peak_source": src,
                      "algorithmic_bytes_per_launch": alg_bytes, "traffic": traffic},
+        "step_roofline": step_roofline(box_cells_mean, dom_cells, dev_ms / args.steps, peaks.get("hbm_gbs"),
+                                       bool(pass_ms)),
         "e2e": None if args.no_e2e else {"value": e2e_cells_all / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * 3 * g / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "seconds": e2e_s, "includes": "create_microstructure from host seeds, steps, per-step volumes "
