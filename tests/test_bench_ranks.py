@@ -59,3 +59,18 @@ def test_reference_arm_of_a_nonzero_rank_does_nothing(monkeypatch, capsys):
         steps, warmup, gpus = 1, 3, 2
     assert bench.reference_arm(A()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_step_roofline_arithmetic():
+    """The whole-step roofline: the method's minimum bytes (8 B per box cell +
+    44 B per domain cell) and the five-pass design's (44 B per box cell + 16 B
+    per domain cell) over the step time, against the peak."""
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), ".."))
+    import bench
+    r = bench.step_roofline(1.0e8, 1.0e7, 2.0, 5000.0, True)
+    assert r["minimum_bytes_per_step"] == 8.0e8 + 4.4e8
+    assert abs(r["achieved_minimum_gbs"] - 1.24e9 / 2e-3 / 1e9) < 1e-9
+    assert abs(r["frac_minimum"] - r["achieved_minimum_gbs"] / 5000.0) < 1e-15
+    assert abs(r["minimum_bound_ms"] - 1.24e9 / 5e12 * 1e3) < 1e-12
+    assert r["design_bytes_per_step"] == 4.4e9 + 1.6e8
+    assert "design_bytes_per_step" not in bench.step_roofline(1.0e8, 1.0e7, 2.0, 5000.0, False)
