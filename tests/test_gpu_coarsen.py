@@ -73,6 +73,7 @@ def _compare(L, ms_shape2, boxes2, phi2, ref_ms, ref):
     ((64, 64, 64), (48, 48, 48), 50, 1, 3),
     ((64, 64, 64), (32, 32, 32), 40, 2, 2),
     ((40, 60, 80), (30, 45, 60), 30, 3, 2),
+    ((48, 48, 48), (48, 48, 48), 30, 10, 2),       # ratio 1: the projection is the identity
 ])
 def test_coarsen_matches_oracle(L, shape, shape2, G, seed, steps):
     nz, ny, nx = shape
@@ -158,6 +159,12 @@ def test_coarsen_rejects_unequal_ratios_and_finer_grids(L):
         assert ms.shape == (N, N, N)
         ms.step(1, 1.0)          # the context is unchanged and usable
         ms.sync()
+    # a 2D domain (no 3D pass path) is refused
+    seeds2 = I.voronoi_seeds(7, 6, (1, 32, 32))
+    with L.Microstructure(32, 32, 1, 6, seeds=seeds2) as m2:
+        with pytest.raises(L.LsggError) as e:
+            m2.coarsen(16, 16, 1)
+        assert e.value.code == L.ERR_UNSUPPORTED
 
 
 def test_coarsen_with_read_shockley_rebuilds_the_id_field(L):

@@ -424,3 +424,20 @@ def test_texture_shares_on_device(L):
     assert np.max(np.abs(sh - want)) <= 1e-14
     assert abs(full[0] - 1.0) <= 1e-15
     assert sh.sum() < 1.0
+
+
+def test_single_grain_fills_the_domain(L):
+    """Degenerate case: one grain.  No bisector exists, so its function is eps
+    everywhere, its box is the whole periodic domain, the comparison step sees
+    no other grain (m = -eps), and the state is a fixed point: after steps the
+    grain still covers all N^3 cells and matches the oracle."""
+    N = 32
+    seeds = I.voronoi_seeds(12, 1, (N, N, N))
+    ref = O.run(O.tessellate((N, N, N), seeds), 3, 1.0)
+    with L.Microstructure(N, N, N, 1, seeds=seeds) as ms:
+        ms.step(3, 1.0)
+        boxes, phi, vol = ms.boxes(), ms.phi(), ms.grain_volumes()
+    assert boxes[0, 0] == 1 and tuple(boxes[0, 4:7]) == (N, N, N)
+    assert np.max(np.abs(phi[0] - ref.grains[0].phi)) <= 1e-6
+    assert np.all(phi[0] == 7.0)
+    assert vol[0] == N ** 3
