@@ -94,12 +94,9 @@ __device__ __forceinline__ void for_reach(const SeedBins& S, float fx, float fy,
     }
 }
 
-__global__ void __launch_bounds__(256)
-k_labels(Domain D, int G, SeedBins S, const double* __restrict__ seeds, const double* __restrict__ weights,
-         int* __restrict__ labels) {
-    const long long ncell = (long long)D.nx * D.ny * D.nz;
-    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= ncell) return;
+// The label of one cell (see k_labels).
+__device__ __forceinline__ int label_cell(const Domain& D, const SeedBins& S, const double* __restrict__ seeds,
+                                          const double* __restrict__ weights, long long cell) {
     const int x = (int)(cell % D.nx);
     const int y = (int)((cell / D.nx) % D.ny);
     const int z = (int)(cell / ((long long)D.nx * D.ny));
@@ -159,7 +156,37 @@ k_labels(Domain D, int G, SeedBins S, const double* __restrict__ seeds, const do
             if (d32(q) <= lim) exact(q);
         });
     }
-    labels[cell] = arg;
+    return arg;
+}
+
+__global__ void __launch_bounds__(256)
+k_labels(Domain D, int G, SeedBins S, const double* __restrict__ seeds, const double* __restrict__ weights,
+         int* __restrict__ labels) {
+    const long long ncell = (long long)D.nx * D.ny * D.nz;
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= ncell) return;
+    labels[cell] = label_cell(D, S, seeds, weights, cell);
+}
+
+// The same labels from a persistent grid whose CTAs first copy the binned
+// seeds (points and bin starts) into shared memory: the search's dependent
+// loads then come from shared memory instead of L2.
+__global__ void __launch_bounds__(512)
+k_labels_staged(Domain D, int G, SeedBins S, long long n_bins, const double* __restrict__ seeds,
+                const double* __restrict__ weights, int* __restrict__ labels) {
+    extern __shared__ __align__(16) unsigned char sm_labels[];
+    float4* s_pts = reinterpret_cast<float4*>(sm_labels);
+    int* s_start = reinterpret_cast<int*>(s_pts + G);
+    for (int i = threadIdx.x; i < G; i += blockDim.x) s_pts[i] = S.pts[i];
+    for (long long i = threadIdx.x; i <= n_bins; i += blockDim.x) s_start[i] = S.start[i];
+    __syncthreads();
+    SeedBins L = S;
+    L.pts = s_pts;
+    L.start = s_start;
+    const long long ncell = (long long)D.nx * D.ny * D.nz;
+    for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < ncell;
+         cell += (long long)gridDim.x * blockDim.x)
+        labels[cell] = label_cell(D, L, seeds, weights, cell);
 }
 
 __global__ void k_face_pairs(Domain D, int G, const int* __restrict__ labels, unsigned* __restrict__ bits,
@@ -452,8 +479,26 @@ cudaError_t launch_init(const Domain& D, int G, const SeedBins& bins, const doub
                         int* d_labels, unsigned* d_bits, long long words_per_row, int* d_bb,
                         Box* d_cur, cudaStream_t s) {
     const long long ncell = (long long)D.nx * D.ny * D.nz;
-    int blocks = (int)((ncell + 255) / 256);
-    k_labels<<<blocks, 256, 0, s>>>(D, G, bins, d_seeds, d_weights, d_labels);
+    // the binned seeds in shared memory when they fit, else read from global memory
+    const long long n_bins = (long long)bins.nb[0] * bins.nb[1] * bins.nb[2];
+    const size_t staged = (size_t)G * sizeof(float4) + (size_t)(n_bins + 1) * sizeof(int);
+    int dev = 0, n_sm = 0, optin = 0, occ = 0;
+    bool use_staged = cudaGetDevice(&dev) == cudaSuccess &&
+                      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+                      staged <= (size_t)optin &&
+                      cudaFuncSetAttribute(k_labels_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)staged) == cudaSuccess &&
+                      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_labels_staged, 512, staged) ==
+                          cudaSuccess &&
+                      occ > 0;
+    if (use_staged) {
+        k_labels_staged<<<n_sm * occ, 512, staged, s>>>(D, G, bins, n_bins, d_seeds, d_weights, d_labels);
+    } else {
+        cudaGetLastError();                      // a refused attribute leaves no error behind
+        int blocks = (int)((ncell + 255) / 256);
+        k_labels<<<blocks, 256, 0, s>>>(D, G, bins, d_seeds, d_weights, d_labels);
+    }
     cudaError_t e = cudaMemsetAsync(d_bits, 0, (size_t)G * words_per_row * 4, s);
     if (e != cudaSuccess) return e;
     int gs = (int)((ncell + 255) / 256);
