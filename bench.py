@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import statistics
@@ -75,10 +76,19 @@ PASS_KERNEL_SOURCES = ("paper_1701_06658_gb300/csrc/passes.cu", "paper_1701_0665
                        "paper_1701_06658_gb300/csrc/lsgg_internal.cuh", "include/lsgg.h")
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and with whitespace collapsed (string
+    literals in these sources hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash():
+    """Hash of the pass kernels' code (comments and layout ignored)."""
     h = hashlib.sha256()
     for f in PASS_KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

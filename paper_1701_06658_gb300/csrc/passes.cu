@@ -1,6 +1,5 @@
-// Pass path of the batched step for 3D boxes whose x and y sides are at most
-// 64: passes over (box, plane), (box, slab), (box, column chunk) and
-// domain-tile work items.
+// Pass path of the batched step for 3D boxes: passes over (box, plane),
+// (box, slab), (box, column chunk) and domain-tile work items.
 //
 // Same arithmetic as the box-streaming kernels (Sec. 2.1.4 predictor, Eq. (16)
 // comparison, Sec. 2.1.6 taxicab re-initialisation), arranged so that every
@@ -14,9 +13,10 @@
 //               shared memory                                     -> Z = xy-convolved
 //   p_conv_z    (box, columns): z pass over a register window, velocity
 //               correction, clamp                                 -> Y = phi_p
-//   p_field     (domain tile): top-2 keys (phi_p, -id) over the tile's boxes
-//               in registers -> T; then phi_c = (phi_p - m) / 2 and the
-//               ID-field for every box cell of the tile           -> Z = phi_c
+//   p_field     (domain tile): the two largest (phi_p, grain) per cell over
+//               the tile's boxes in registers -> T as (phi_p, -id) keys; then
+//               phi_c = (phi_p - m) / 2 and the ID-field for every box cell of
+//               the tile                                          -> Z = phi_c
 //   p_redist_xy (box, slab): plane ring filled by bulk copies; reference cells
 //               with their planar-exact distances, y and x taxicab scans -> Y
 //   p_redist_z  (box, columns): the column in registers, z taxicab scans,
@@ -24,11 +24,13 @@
 // The field pass replaces the box-streaming kernels' atomic scatter: each
 // domain cell's top-2 is built by the one thread that owns the cell, so the
 // step has no atomics on the field.  The work-item lists are written by the
-// box update; boxes of x, y side <= 32, <= 48 and <= 64 (tiers 0, 1, 2) have
-// their own lists and launches, so the plane passes of smaller boxes run with
-// smaller shared-memory grids and higher occupancy.  A non-periodic box's planes outside it are -eps;
-// their xy convolution is the constant that p_conv_z recomputes with the FMA
-// sequence p_conv_xy would use.
+// box update; boxes of x, y side <= 32, <= 40, <= 48 and <= 64 (tiers 0-3)
+// have their own lists and launches, so the plane passes of smaller boxes run
+// with smaller shared-memory grids and higher occupancy; larger boxes (tier 4)
+// take plane passes through global memory (p_conv_xy_big, p_redist_xy_big).
+// A non-periodic box's planes outside it are -eps; their xy convolution is
+// the constant that p_conv_z recomputes with the FMA sequence p_conv_xy would
+// use.
 #include <cfloat>
 #include <climits>
 

@@ -74,3 +74,15 @@ def test_step_roofline_arithmetic():
     assert abs(r["minimum_bound_ms"] - 1.24e9 / 5e12 * 1e3) < 1e-12
     assert r["design_bytes_per_step"] == 4.4e9 + 1.6e8
     assert "design_bytes_per_step" not in bench.step_roofline(1.0e8, 1.0e7, 2.0, 5000.0, False)
+
+
+def test_traffic_hash_ignores_comments_not_code():
+    """The traffic figures are keyed to the pass kernels' code: a comment or
+    layout change keeps the key, a code change does not."""
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), ".."))
+    import bench
+    a = "int f(int x) { // doubles\n  return 2 * x; /* the\n result */ }\n"
+    b = "int f(int x) {\n    return 2 * x;   // twice x\n}\n"
+    c = "int f(int x) { return 3 * x; }"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
