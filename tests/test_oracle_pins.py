@@ -887,3 +887,113 @@ def test_texture_shares_by_hand(oracle):
     vol = np.array([10.0, 30.0, 0.0, 60.0])
     cls = np.array([0, 1, 1, -1])
     assert np.allclose(oracle.texture_shares(vol, cls, 2), [0.1, 0.3], rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------- anisotropy map (R15)
+
+def _tri_area(T):
+    return 0.5 * np.linalg.norm(np.cross(T[:, 1] - T[:, 0], T[:, 2] - T[:, 0]), axis=1)
+
+
+def test_gb_triangles_of_an_oblique_plane_are_exact(oracle):
+    """A linear function's zero level is triangulated exactly: every vertex
+    lies on the plane, and the area is the plane's section of the box
+    (width (ny-1), length (nx-1)/cos theta for a plane tilted in z-x)."""
+    nz, ny, nx = 12, 7, 9
+    th = 0.35
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi = 5.2 - (z * math.cos(th) + x * math.sin(th))       # crosses x = 0 .. nx-1 inside z's range
+    T, g = oracle.gb_triangles(phi, np.where(phi <= 0, 3, -1))
+    on = T[..., 0] * math.cos(th) + T[..., 2] * math.sin(th) - 5.2
+    assert np.abs(on).max() < 1e-12
+    assert abs(_tri_area(T).sum() - (ny - 1) * (nx - 1) / math.cos(th)) < 1e-9
+    assert set(g.tolist()) == {3}
+
+
+def _sphere(n, r, c):
+    z, y, x = np.meshgrid(*[np.arange(n)] * 3, indexing="ij")
+    return r - np.sqrt((z - c[0]) ** 2 + (y - c[1]) ** 2 + (x - c[2]) ** 2)
+
+
+def test_gb_triangles_of_a_sphere_are_a_closed_sphere(oracle):
+    """The triangulated zero level of a sphere's distance function is a closed
+    2-manifold of Euler characteristic 2 (every edge in exactly two
+    triangles), its vertices within the chord error of radius r, and its area
+    within 1% of 4 pi r^2."""
+    r, c = 8.3, (12.4, 11.7, 12.1)
+    T, _ = oracle.gb_triangles(_sphere(26, r, c), np.zeros((26, 26, 26), dtype=np.int64))
+    rad = np.linalg.norm(T - np.array(c), axis=2)
+    assert np.abs(rad - r).max() < 3.0 / (8.0 * r) + 1e-9      # longest tetrahedron edge sqrt(3)
+    assert abs(_tri_area(T).sum() / (4 * math.pi * r * r) - 1.0) < 0.01
+    key = {}
+    vid = np.array([key.setdefault(tuple(np.round(v, 9)), len(key)) for v in T.reshape(-1, 3)]).reshape(-1, 3)
+    edges = {}
+    for a, b, cc in vid:
+        for e in ((a, b), (b, cc), (cc, a)):
+            e = (min(e), max(e))
+            edges[e] = edges.get(e, 0) + 1
+    assert set(edges.values()) == {2}
+    assert len(key) - len(edges) + len(vid) == 2
+
+
+def test_point_triangle_distance_matches_brute_force(oracle):
+    """Against the minimum over a fine barycentric sample of each triangle:
+    never above it, and below it by at most the sample's spacing; collinear
+    (degenerate) triangles included."""
+    rng = np.random.default_rng(15)
+    tris = rng.uniform(-2, 2, (40, 3, 3))
+    tris[0, 2] = 0.5 * (tris[0, 0] + tris[0, 1])               # degenerate
+    s = np.linspace(0.0, 1.0, 161)
+    a, b = np.meshgrid(s, s, indexing="ij")
+    keep = a + b <= 1.0
+    bary = np.stack([1 - a[keep] - b[keep], a[keep], b[keep]], 1)
+    for p in rng.uniform(-3, 3, (25, 3)):
+        d = oracle.point_triangle_distance(p, tris)
+        for k in range(len(tris)):
+            pts = bary @ tris[k]
+            dmin = np.linalg.norm(pts - p, axis=1).min()
+            diam = max(np.linalg.norm(tris[k, i] - tris[k, j]) for i in range(3) for j in range(3))
+            assert d[k] <= dmin + 1e-12 and d[k] >= dmin - diam / 160.0, (k, d[k], dmin)
+
+
+def test_closest_gb_distance_is_the_sphere_distance(oracle):
+    """Every band cell of a sphere grain lies at distance |r - |p - c|| from
+    the true boundary; the closest triangle gives it within the chord error."""
+    r, c = 7.6, (10.3, 9.8, 10.2)
+    phi = _sphere(21, r, c)
+    T, _ = oracle.gb_triangles(phi, np.zeros(phi.shape, dtype=np.int64))
+    for z, y, x in zip(*np.nonzero(np.abs(phi) < 2.5)):
+        d = oracle.point_triangle_distance(np.array([z, y, x], dtype=np.float64), T).min()
+        assert abs(d - abs(phi[z, y, x])) < 3.0 / (8.0 * (r - 2.5)) + 0.02
+
+
+def test_closest_gb_grains_at_a_triple_junction(oracle):
+    """Grain 0 fills x < 9.5; across its plane boundary grain 1 holds y <= 7
+    and grain 2 y >= 8 (the junction line at y = 7.5).  Every band cell adopts
+    the grain straight across the plane: 1 for y <= 6, 2 for y >= 9, either at
+    the junction.  A sentinel id on grain 0's own side must never be adopted
+    (the label comes from the corners outside the grain)."""
+    nz, ny, nx = 5, 16, 20
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi = np.clip(9.5 - x, -7.0, 7.0).astype(np.float64)
+    across = np.where(y <= 7, 1, 2)
+    idf = np.where(phi <= 0, across, 5)
+    out = oracle.closest_gb_grains(phi, idf, 3.0)
+    band = np.abs(phi) < 3.0
+    assert np.all(out[~band] == idf[~band])
+    assert np.all(out[band & (y <= 6)] == 1) and np.all(out[band & (y >= 9)] == 2)
+    assert set(np.unique(out[band & ((y == 7) | (y == 8))]).tolist()) <= {1, 2}
+
+
+def test_closest_gb_grains_of_a_bicrystal_and_an_isolated_grain(oracle):
+    """A bicrystal: every band cell adopts the one neighbour.  No boundary in
+    the box (all positive) or no neighbour (-1 outside): the map is the
+    ID-field, resp. -1 (w = 1)."""
+    phi = np.clip(4.5 - np.arange(10), -7, 7)[None, None, :] * np.ones((3, 4, 1))
+    idf = np.where(phi <= 0, 4, 4)
+    out = oracle.closest_gb_grains(phi, idf, 2.0)
+    assert np.all(out == 4)
+    assert np.array_equal(oracle.closest_gb_grains(np.full((3, 3, 3), 2.0), np.full((3, 3, 3), 6), 3.0),
+                          np.full((3, 3, 3), 6))
+    out = oracle.closest_gb_grains(phi, np.full(phi.shape, -1), 2.0)
+    assert np.all(out == -1)
