@@ -408,6 +408,37 @@ int lsgg_neighbour_max_noalloc(const lsgg_box* boxes_dev, int32_t n_boxes, const
                                int64_t n_elems, int32_t nx, int32_t ny, int32_t nz, float eps,
                                float* m_dev, int32_t* id_dev, void* stream);
 
+/* Anisotropy map (Sec. 2.1.4: a grid point takes w and M of the closest
+ * point on the grain boundary, found on a marching-cubes triangulation; Sec.
+ * 4.1 accelerates that search).  For every box i of the packed set, its
+ * boundary is the zero level of phi_i on the box's own cells (box-local: a
+ * full periodic axis is not wrapped), triangulated by marching tetrahedra:
+ * each cell cube split into the six tetrahedra around its main diagonal (one
+ * per order of the axes z, y, x), the level linearly interpolated on the edges
+ * between corners of opposite sign (phi > 0 inside); a quad is split along the
+ * diagonal between the edge points of its two positive corners' first edges.
+ * A triangle faces the grain most frequent in idf among its tetrahedron's
+ * corners with phi <= 0 (lowest id on ties, -1 without any).  Then for every
+ * cell c of the box:
+ *   out[c] = the grain of the triangle at the smallest (squared Euclidean
+ *            distance from c, grain) when |phi[c]| < tube and the box has a
+ *            triangle,
+ *   out[c] = idf[c] otherwise (a box with an axis of one cell has none).
+ * The result replaces the per-cell ID-field in Eq. (10)'s pair weights.
+ * Distances are evaluated in FP32, so cells whose two nearest grains lie
+ * within rounding of each other may take either.  All array pointers are
+ * DEVICE pointers: boxes_dev (n_boxes entries, the origin is ignored),
+ * phi_dev (float), idf_dev and out_dev (int32), each of n_elems entries
+ * indexed by the boxes' offsets; out_dev must not overlap phi_dev or idf_dev.
+ * Boxes with dims below 1 or reaching past n_elems are skipped and their
+ * outputs left untouched.  0 < tube <= 16, else LSGG_ERR_INVALID_ARG.  The
+ * search per cell covers the cubes within ceil(tube) + 1 cells and, where the
+ * best distance there does not prove it the box's minimum (a function far
+ * from a distance function), every cube of the box.  Enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default stream); returns after enqueue. */
+int lsgg_closest_gb_map(const lsgg_box* boxes_dev, int32_t n_boxes, const float* phi_dev, const int32_t* idf_dev,
+                        int64_t n_elems, float tube, int32_t* out_dev, void* stream);
+
 /* Test hook: reallocate the context's box arenas to exactly `capacity`
  * elements (at least what the current state needs), so that a later box update
  * overflows and exercises the growth path of lsgg_sync.  Synchronises. */

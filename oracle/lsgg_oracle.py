@@ -92,9 +92,9 @@ code where it applies):
      its tetrahedron's corners with phi_i <= 0 (the lowest id on ties).
      Every cell with |phi_i| < tube adopts the grain of the Euclidean-closest
      triangle; that map replaces R3's per-cell ID-field in Eq. (10)'s
-     weights.  Not built on the device; its oracle functions are pinned by
-     the plane, the sphere, a bicrystal, brute-force distances and an
-     analytic triple junction.
+     weights.  Box-local: the cubes are those between the box's own cells (a
+     full periodic axis is not wrapped; a box with an axis of one cell has
+     none, and then the map is the ID-field).
 """
 from __future__ import annotations
 
@@ -1121,7 +1121,12 @@ def closest_gb_grains(phi: np.ndarray, idf: np.ndarray, tube: float) -> np.ndarr
     if len(tris) == 0:
         return out
     for z, y, x in zip(*np.nonzero(np.abs(phi) < tube)):
-        d = point_triangle_distance(np.array([z, y, x], dtype=np.float64), tris)
-        k = int(np.argmin(d))
-        out[z, y, x] = grains[k]
+        out[z, y, x] = closest_gb_grain_at((z, y, x), tris, grains)
     return out
+
+
+def closest_gb_grain_at(cell, tris: np.ndarray, grains: np.ndarray) -> int:
+    """R15 for one cell (z, y, x) of a box with at least one triangle: the
+    grain of the Euclidean-closest triangle (the first one on exact ties)."""
+    d = point_triangle_distance(np.asarray(cell, dtype=np.float64), tris)
+    return int(grains[int(np.argmin(d))])

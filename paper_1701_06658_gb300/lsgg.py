@@ -111,6 +111,8 @@ _SIGS = {
                                      C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lsgg_neighbour_max_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
                                              C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lsgg_closest_gb_map": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
+                                      C.c_void_p, C.c_void_p]),
     "lsgg_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
     "lsgg_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Config), C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
     "lsgg_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
@@ -337,6 +339,14 @@ def neighbour_max_noalloc(boxes_dev: int, n_boxes: int, phip_dev: int, n_elems: 
     any device allocation (its field is a static array of NOALLOC_MAX_CELLS cells)."""
     _check("neighbour_max_noalloc", lib().lsgg_neighbour_max_noalloc(boxes_dev, n_boxes, phip_dev, n_elems, nx, ny,
                                                                       nz, eps, m_dev, id_dev, stream or None))
+
+
+def closest_gb_map(boxes_dev: int, n_boxes: int, phi_dev: int, idf_dev: int, n_elems: int, tube: float,
+                   out_dev: int, stream: int = 0):
+    """lsgg_closest_gb_map on device pointers: the grain across the closest
+    triangulated boundary point for every cell with |phi| < tube."""
+    _check("closest_gb_map", lib().lsgg_closest_gb_map(boxes_dev, n_boxes, phi_dev, idf_dev, n_elems, tube, out_dev,
+                                                        stream or None))
 
 
 def grain_neighbours(ctx, n_grains: int, cap: int = 96) -> list:

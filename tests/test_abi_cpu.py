@@ -78,6 +78,11 @@ def test_invalid_arguments_rejected_before_any_device_work():
     with pytest.raises(L.LsggError) as e:
         L.coarsen(None, 16, 16, 16)          # no context
     assert e.value.code == L.ERR_INVALID_ARG
+    for args in ((0, 1, 8, 8, 10, 3.0, 8), (8, 1, 8, 8, 10, 0.0, 8), (8, 1, 8, 8, 10, 17.0, 8),
+                 (8, -1, 8, 8, 10, 3.0, 8), (8, 1, 8, 8, 10, float("nan"), 8)):
+        with pytest.raises(L.LsggError) as e:    # checked before any launch: the pointers are never read
+            L.closest_gb_map(*args)
+        assert e.value.code == L.ERR_INVALID_ARG
 
 
 def test_no_cpu_fallback_without_a_device():
