@@ -997,3 +997,61 @@ def test_closest_gb_grains_of_a_bicrystal_and_an_isolated_grain(oracle):
                           np.full((3, 3, 3), 6))
     out = oracle.closest_gb_grains(phi, np.full(phi.shape, -1), 2.0)
     assert np.all(out == -1)
+
+
+# ------------------------------------------------- initial boxes and signs (R6, R7)
+
+def _min_arc(coords, n):
+    """Brute force: the shortest arc (start, length) of the n-cycle that covers
+    every coordinate, the smallest start among the shortest."""
+    occ = {int(c) % n for c in coords}
+    for length in range(1, n + 1):
+        for start in range(n):
+            if occ <= {(start + k) % n for k in range(length)}:
+                return start, length
+
+
+@pytest.mark.parametrize("shape,n,seed", [((20, 24, 28), 18, 21), ((1, 40, 36), 25, 22)])
+def test_initial_boxes_are_tight_periodic_bboxes(oracle, shape, n, seed):
+    """Every grain's initial box is the shortest periodic arc of its label
+    cells per axis, grown by the halo on both sides (the whole axis once that
+    reaches N), found here by brute force over all arcs."""
+    seeds = I.voronoi_seeds(seed, n, (shape[2], shape[1], shape[0]))
+    ms = oracle.tessellate(shape, seeds, halo=3)
+    lab = oracle.labels_of_tessellation(shape, seeds)
+    for g in ms.grains:
+        cells = np.argwhere(lab == g.gid)
+        if len(cells) == 0:
+            assert not g.alive
+            continue
+        for a in range(3):
+            if shape[a] == 1:
+                assert g.dims[a] == 1
+                continue
+            s, length = _min_arc(cells[:, a], shape[a])
+            if length + 6 >= shape[a]:
+                assert g.dims[a] == shape[a]
+            else:
+                assert g.dims[a] == length + 6 and g.origin[a] == (s - 3) % shape[a], (g.gid, a)
+
+
+def test_initial_functions_agree_with_the_labels(oracle):
+    """R7: a grain's initial function is >= 0 on its own label cells (<= its
+    distance to every bisector plane of a face neighbour, all of which it is
+    on the grain's side of) and <= 0 on the cells of its face neighbours."""
+    shape = (18, 22, 20)
+    seeds = I.voronoi_seeds(31, 20, (shape[2], shape[1], shape[0]))
+    ms = oracle.tessellate(shape, seeds)
+    lab = oracle.labels_of_tessellation(shape, seeds)
+    nbs = oracle.face_neighbours(lab, len(seeds))
+    checked = 0
+    for g in ms.grains:
+        if not g.alive:
+            continue
+        pz, py, px = oracle.box_positions(g, shape)
+        L = lab[np.ix_(pz, py, px)]
+        assert np.all(g.phi[L == g.gid] >= -1e-12)
+        nb = np.isin(L, list(nbs[g.gid]))
+        assert np.all(g.phi[nb] <= 1e-12)
+        checked += int(nb.sum())
+    assert checked > 1000
