@@ -415,8 +415,10 @@ int lsgg_neighbour_max_noalloc(const lsgg_box* boxes_dev, int32_t n_boxes, const
  * full periodic axis is not wrapped), triangulated by marching tetrahedra:
  * each cell cube split into the six tetrahedra around its main diagonal (one
  * per order of the axes z, y, x), the level linearly interpolated on the edges
- * between corners of opposite sign (phi > 0 inside); a quad is split along the
- * diagonal between the edge points of its two positive corners' first edges.
+ * between corners of opposite sign (phi > 0 inside); a quad (two positive
+ * corners a < b, two others c < d, in the tetrahedron's corner order: the
+ * cube corner, then one, two and three unit steps) is split along the
+ * diagonal from the point on edge (a, c) to the point on edge (b, d).
  * A triangle faces the grain most frequent in idf among its tetrahedron's
  * corners with phi <= 0 (lowest id on ties, -1 without any).  Then for every
  * cell c of the box:

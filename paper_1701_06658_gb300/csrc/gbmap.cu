@@ -10,8 +10,9 @@
 // the six tetrahedra around its main diagonal, one per order of the axes
 // (z, y, x), the level linearly interpolated on the edges between corners of
 // opposite sign (phi > 0 inside).  A tetrahedron with one corner apart gives a
-// triangle, one with two and two a quad split along the diagonal from the
-// first positive corner's edge point to the second's.  A triangle faces the
+// triangle, one with two and two a quad (positive corners a < b, the others
+// c < d, in the tetrahedron's corner order) split along the diagonal from the
+// point on edge (a, c) to the point on edge (b, d).  A triangle faces the
 // grain most frequent in the ID-field among its tetrahedron's corners with
 // phi <= 0 (lowest id on ties, -1 without any).
 //
