@@ -92,7 +92,7 @@ code where it applies):
      its tetrahedron's corners with phi_i <= 0 (the lowest id on ties).
      Every cell with |phi_i| < tube adopts the grain of the Euclidean-closest
      triangle; that map replaces R3's per-cell ID-field in Eq. (10)'s
-     weights.  Box-local: the cubes are those between the box's own cells (a
+     weights (``Physics.gb_map_tube``).  Box-local: the cubes are those between the box's own cells (a
      full periodic axis is not wrapped; a box with an axis of one cell has
      none, and then the map is the ID-field).
 """
@@ -228,13 +228,17 @@ def convolve(phi: np.ndarray, full, taps: np.ndarray, eps: float, axes) -> np.nd
 def predict(grain: Grain, shape, taps, eps, physics=None, dt=1.0) -> np.ndarray:
     """Predictor of Algorithm 1 (Sec. 2.1.4): convolution with the heat
     kernel (Eq. (9)) and, with physics, the velocity correction of Eq. (10)
-    (reading R3).  Clamped to [-eps, eps] (reading R2)."""
+    (reading R3, or R15 with ``physics.gb_map_tube``).  Clamped to
+    [-eps, eps] (reading R2)."""
     axes = spatial_axes(shape)
     c = convolve(grain.phi, full_axes(grain, shape), taps, eps, axes)
     if physics is None:
         phip = c
     else:
-        w, bulk = physics.blend_terms(grain.gid, grain.idf, dt)
+        pair_ids = grain.idf
+        if physics.gb_map_tube is not None:
+            pair_ids = closest_gb_grains(grain.phi, grain.idf, physics.gb_map_tube)   # R15
+        w, bulk = physics.blend_terms(grain.gid, pair_ids, dt)
         phip = grain.phi + w * (c - grain.phi) + bulk
     return np.clip(phip, -eps, eps)
 
@@ -500,10 +504,14 @@ class Physics:
 
     weight(i, j) -> (w_ij, M_ij): w = M* gamma* in (0, 1] scales the
     curvature flow, M* in (0, 1] the bulk term.  ``energy[i]`` is the bulk
-    energy of grain i in grid units (E_i h / gamma_max, Eq. (13))."""
+    energy of grain i in grid units (E_i h / gamma_max, Eq. (13)).
+    ``gb_map_tube``: None takes the pair per cell from the ID-field (R3); a
+    tube width takes it from the closest grain-boundary point instead (R15)
+    for the cells with |phi| below it."""
     weight: callable
     energy: np.ndarray
     _cache: dict = field(default_factory=dict)
+    gb_map_tube: float | None = None
 
     def pair(self, i, j):
         key = (i, j)

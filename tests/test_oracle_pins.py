@@ -1055,3 +1055,33 @@ def test_initial_functions_agree_with_the_labels(oracle):
         assert np.all(g.phi[nb] <= 1e-12)
         checked += int(nb.sum())
     assert checked > 1000
+
+
+def test_gb_map_takes_the_pair_from_the_closest_boundary(oracle):
+    """R15 in Eq. (10): a cylinder grain whose outside belongs to grain 1
+    (x < c) and grain 2 (x >= c), with w(0, 1) = 1 and w(0, 2) = 0.5, and no
+    ID entry on its own cells (-1: w = 1 under R3).  With the map each band
+    cell blends with the weight of the grain across its closest boundary
+    point: its change is exactly w(map) times the R3 change, 0.5 on the x > c
+    side; isotropic physics is unaffected by the map."""
+    shape, c = (4, 40, 40), 19.6
+    ms = oracle.single_grain_state(shape, lambda z, y, x: 11.0 - np.sqrt((x - c) ** 2 + (y - 19.3) ** 2))
+    g = ms.grains[0]
+    pz, py, px = oracle.box_positions(g, shape)
+    X = np.broadcast_to(px[None, None, :], g.dims)
+    g.idf = np.where(g.phi <= 0, np.where(X < c, 1, 2), -1).astype(np.int64)
+    taps = oracle.heat_kernel_taps(1.0, 5)
+    wts = {1: 1.0, 2: 0.5}
+    r3 = oracle.Physics(weight=lambda i, j: (wts[j], 1.0), energy=np.zeros(3))
+    r15 = oracle.Physics(weight=lambda i, j: (wts[j], 1.0), energy=np.zeros(3), gb_map_tube=3.0)
+    p3 = oracle.predict(g, shape, taps, ms.eps, r3, 1.0)
+    p15 = oracle.predict(g, shape, taps, ms.eps, r15, 1.0)
+    m = oracle.closest_gb_grains(g.phi, g.idf, 3.0)
+    band = (np.abs(g.phi) < 3.0) & (g.phi > 0)
+    assert np.all(m[band & (X > c + 1.5)] == 2) and np.all(m[band & (X < c - 1.5)] == 1)
+    w = np.where(m == 2, 0.5, 1.0)
+    assert np.allclose((p15 - g.phi)[band], (w * (p3 - g.phi))[band], rtol=0, atol=1e-12)
+    assert np.abs((p15 - g.phi)[band & (X > c + 1.5)]).max() > 1e-3
+    iso = lambda tube: oracle.Physics(weight=lambda i, j: (1.0, 1.0), energy=np.zeros(3), gb_map_tube=tube)
+    assert np.array_equal(oracle.predict(g, shape, taps, ms.eps, iso(None), 1.0),
+                          oracle.predict(g, shape, taps, ms.eps, iso(3.0), 1.0))
