@@ -25,6 +25,13 @@ Conventions (grid units, h = 1, M_max * gamma_max = 1):
   * outside its box a grain's function is -eps (Fig. 1 caption: "outside it
     was restricted to eps = -7h").
 
+Pins (tests/test_oracle_pins.py) tie every function here to something other
+than itself.  Parity unpinned: the evolution of many grains over many steps
+(``run``) beyond what those pins fix -- its laws (sphere, circle, von
+Neumann-Mullins), invariants (no voids or overlaps) and stationary cases --
+has no independent reference; there the device path is judged against this
+module alone.
+
 Readings of points where the paper is silent or garbled (each named in the
 code where it applies):
   R1 Eq. (8) prints (4 pi t)^(-1/D) exp(-|x|^2 / 4 pi); we use the heat kernel
