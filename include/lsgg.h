@@ -131,11 +131,14 @@ int lsgg_step(lsgg_ctx* ctx, int32_t n, double dt);
  * LSGG_ERR_TIMEOUT if the wait expired (the work keeps running). */
 int lsgg_sync(lsgg_ctx* ctx, int64_t timeout_ms);
 
-/* Per-grain volume V_i = sum_x H(phi_i(x)), H(phi) = clamp(phi + 1/2, 0, 1),
- * exact fixed-point partial sums merged with FP64 compensated sums in a fixed
- * order (deterministic); index = grain id,
- * 0 for extinct grains.  out: host array of cap >= n_grains doubles;
- * *n_out = n_grains.  Synchronises. */
+/* Per-grain volume V_i = sum_x H(phi_i(x)), H(phi) = clamp(phi + 1/2, 0, 1).
+ * The paper does not define a grain's volume; this is a smooth cell count:
+ * the zero level of phi_i smeared over one cell, so that it moves
+ * continuously with the interface (the volumes the grain-size analysis of
+ * Sec. 5 takes its equivalent radii from).  Computed from exact fixed-point
+ * partial sums merged with FP64 compensated sums in a fixed order
+ * (deterministic); index = grain id, 0 for extinct grains.  out: host array
+ * of cap >= n_grains doubles; *n_out = n_grains.  Synchronises. */
 int lsgg_grain_volumes(lsgg_ctx* ctx, double* out, int64_t cap, int64_t* n_out);
 
 /* Grain statistics of the size analysis (Sec. 5), computed on the device from
@@ -204,9 +207,29 @@ int lsgg_fit_growth_exponent(const double* t, const double* mean_r, int32_t n, d
  * enqueued steps first; synchronises. */
 int lsgg_coarsen(lsgg_ctx* ctx, int32_t nx, int32_t ny, int32_t nz);
 
-/* owner(x) = argmax_i phi_i(x) over the boxes covering x, lowest id on ties,
- * -1 where no box covers x; x fastest, n_cells = nx*ny*nz int32s.  Synchronises. */
+/* Voxel owner map: owner(x) = argmax_i phi_i(x) over the boxes covering x --
+ * the grain whose function is largest at x, i.e. the grain the comparison
+ * step of Eq. (16) leaves positive there and the voxel ID-field of Sec. 3.1
+ * records -- lowest id on ties, -1 where no box covers x; x fastest,
+ * n_cells >= nx*ny*nz int32s.  Synchronises. */
 int lsgg_voxel_owner(lsgg_ctx* ctx, int32_t* out, int64_t n_cells);
+
+/* Device-pointer variants of lsgg_grain_volumes and lsgg_voxel_owner (same
+ * definitions and results, bit for bit) for outputs that stay on the device,
+ * e.g. in a torch tensor's data_ptr().  out_dev: DEVICE array of cap >=
+ * n_grains doubles / n_cells >= nx*ny*nz int32s, owned by the caller.
+ * status_dev (optional DEVICE int32, may be NULL) receives the status of the
+ * steps enqueued before the call, read on the device: 0, their error code, or
+ * LSGG_ERR_CAPACITY when one of them stopped on a full box arena -- then the
+ * output describes the state before that step, and lsgg_sync (which grows the
+ * arena and finishes the steps) followed by another call gives the result.
+ * The work is enqueued on `stream` (a cudaStream_t; NULL = the context's
+ * stream) after the context's enqueued work, and the context's later work
+ * waits for it; the calls do not synchronise and allocate nothing.  The owner
+ * map takes the context's neighbour-max field as scratch, so
+ * lsgg_grain_neighbours needs another step afterwards. */
+int lsgg_grain_volumes_device(lsgg_ctx* ctx, double* out_dev, int64_t cap, int32_t* status_dev, void* stream);
+int lsgg_voxel_owner_device(lsgg_ctx* ctx, int32_t* out_dev, int64_t n_cells, int32_t* status_dev, void* stream);
 
 /* Free all device memory of the context (after finishing its work). */
 int lsgg_destroy(lsgg_ctx* ctx);
@@ -397,11 +420,13 @@ int lsgg_neighbour_max(const lsgg_box* boxes_dev, int32_t n_boxes, const float* 
  * every GPU on which the library's ops module is loaded keeps until the
  * process exits.  The call allocates nothing (no cudaMalloc, no cudaFree,
  * no allocating library routine).  Domains above LSGG_NOALLOC_MAX_CELLS
- * cells return LSGG_ERR_CAPACITY without touching the device.  The first
- * call on a device looks up the array's device address on the current
- * device (cudaGetSymbolAddress) and caches it: make that first call before
- * any stream capture.  Every call shares the one array and leaves the last
- * call's field in it (each call clears it first), so calls whose work
+ * cells return LSGG_ERR_CAPACITY without touching the device.  Every call
+ * looks up the array's device address in the current device's context
+ * (cudaGetSymbolAddress, which allocates nothing), so a context torn down and
+ * recreated in the same process is followed; the first lookup on a device
+ * loads the library's ops module there, so make the first call on a device
+ * before any stream capture.  Every call shares the one array and leaves the
+ * last call's field in it (each call clears it first), so calls whose work
  * overlaps on the GPU (different streams, different host threads) race and
  * must be ordered by the caller. */
 int lsgg_neighbour_max_noalloc(const lsgg_box* boxes_dev, int32_t n_boxes, const float* phip_dev,

@@ -6,8 +6,6 @@
 //                        (value, -index) keys per box cell), in caller scratch.
 //   lsgg_neighbour_max_noalloc  the same kernels with the field in a static
 //                        device array, for callers that cannot allocate.
-#include <mutex>
-
 #include "lsgg_internal.cuh"
 #include "../../include/lsgg.h"
 
@@ -104,24 +102,16 @@ namespace {
 // 2 x u64 per cell: the neighbour-max field of at most LSGG_NOALLOC_MAX_CELLS cells.
 static __device__ __align__(256) unsigned long long g_noalloc_field[2 * (size_t)LSGG_NOALLOC_MAX_CELLS];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kMaxDevices] = {};
-
-// Device address of g_noalloc_field on the current device, looked up once per
-// device.  The host-side name is only a stand-in for the device array.
+// Device address of g_noalloc_field in the current device's context.  The
+// host-side name is only a stand-in for the device array, so the address is
+// looked up on every call: a lookup is not an allocation, and a cached address
+// would outlive the context it belongs to (a device reset or a released
+// primary context reloads the module, possibly at another address).
 int noalloc_field(unsigned long long** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return LSGG_ERR_CUDA; }
-    if (dev < 0 || dev >= kMaxDevices) return LSGG_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_field);
-        if (e != cudaSuccess || !p) { cudaGetLastError(); return LSGG_ERR_CUDA; }
-        g_noalloc_addr[dev] = p;
-    }
-    *out = static_cast<unsigned long long*>(g_noalloc_addr[dev]);
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_field);
+    if (e != cudaSuccess || !p) { cudaGetLastError(); return LSGG_ERR_CUDA; }
+    *out = static_cast<unsigned long long*>(p);
     return LSGG_OK;
 }
 
