@@ -30,6 +30,7 @@ cudaError_t launch_volumes(const Domain& D, int G, const Box* cur, const Box* pr
                            cudaStream_t s);
 cudaError_t launch_owner(const Domain& D, int G, const Box* cur, const Box* prev, const float* X,
                          unsigned long long* F, int* out, cudaStream_t s);
+cudaError_t launch_step_status(const StepState* st, int* out, cudaStream_t s);
 cudaError_t launch_pack_state(const Domain& D, int G, const Box* cur, const Box* prev, const float* X,
                               const long long* packed_off, float* out, cudaStream_t s);
 cudaError_t launch_pack_cur(int G, const Box* cur, const void* arena, const long long* packed_off, void* out,
@@ -67,6 +68,8 @@ struct lsgg_ctx {
     long long* d_packed_off = nullptr;
     StepState* h_st = nullptr;       // pinned mirror for status reads
     bool field_valid = false;        // T holds the field of the last completed step
+    cudaEvent_t join_in = nullptr;   // _device outputs on a caller stream: after the context's work,
+    cudaEvent_t join_out = nullptr;  // and the context's later work after them
     long long steps_target = 0;      // steps requested since creation
     double last_dt = 0.0;
     long long device_bytes = 0;
@@ -240,10 +243,24 @@ int ensure_chunk_cap(lsgg_ctx* c) {
 
 // The state as FP32: X itself, or (BF16 storage) its conversion into Y,
 // which is free between steps.
-cudaError_t state_as_f32(lsgg_ctx* c, const float** out) {
+cudaError_t state_as_f32(lsgg_ctx* c, const float** out, cudaStream_t s = nullptr) {
     if (!c->B.bf16) { *out = c->B.X; return cudaSuccess; }
     *out = c->B.Y;
-    return launch_state_to_f32(c->B.X, c->B.Y, c->B.cap, c->stream);
+    return launch_state_to_f32(c->B.X, c->B.Y, c->B.cap, s ? s : c->stream);
+}
+
+// Run an output on caller stream s (the context's own when null): s waits for
+// the context's enqueued work before, and the context's stream for s after.
+cudaError_t join_caller_stream(lsgg_ctx* c, cudaStream_t s, bool after) {
+    if (s == c->stream) return cudaSuccess;
+    cudaEvent_t& e = after ? c->join_out : c->join_in;
+    if (!e) {
+        cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (r != cudaSuccess) { e = nullptr; return r; }
+    }
+    cudaStream_t from = after ? s : c->stream, to = after ? c->stream : s;
+    cudaError_t r = cudaEventRecord(e, from);
+    return r == cudaSuccess ? cudaStreamWaitEvent(to, e, 0) : r;
 }
 
 // Assign arena offsets / classes for the `cur` boxes (no resize), growing if needed.
@@ -347,6 +364,8 @@ int lsgg_destroy(lsgg_ctx* c) {
     for (auto& v : c->ev_pending)
         for (cudaEvent_t e : v) c->ev_pool.push_back(e);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->join_in) cudaEventDestroy(c->join_in);
+    if (c->join_out) cudaEventDestroy(c->join_out);
     for (void* p : c->allocations) cudaFree(p);
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1208,6 +1227,33 @@ int lsgg_voxel_owner(lsgg_ctx* c, int32_t* out, int64_t n_cells) {
     c->device_bytes -= n * 4;
     dfree(c, d);
     return e == cudaSuccess ? LSGG_OK : LSGG_ERR_CUDA;
+}
+
+int lsgg_grain_volumes_device(lsgg_ctx* c, double* out_dev, int64_t cap, int32_t* status_dev, void* stream) {
+    if (!c || !out_dev) return LSGG_ERR_INVALID_ARG;
+    if (cap < c->G) return LSGG_ERR_CAPACITY;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const float* x = nullptr;
+    CK(join_caller_stream(c, s, false));
+    CK(state_as_f32(c, &x, s));
+    CK(launch_volumes(c->dom, c->G, c->B.cur, c->B.prev, x, out_dev, s));
+    if (status_dev) CK(launch_step_status(c->B.st, status_dev, s));
+    CK(join_caller_stream(c, s, true));
+    return LSGG_OK;
+}
+
+int lsgg_voxel_owner_device(lsgg_ctx* c, int32_t* out_dev, int64_t n_cells, int32_t* status_dev, void* stream) {
+    if (!c || !out_dev) return LSGG_ERR_INVALID_ARG;
+    if (n_cells < (long long)c->dom.nx * c->dom.ny * c->dom.nz) return LSGG_ERR_CAPACITY;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const float* x = nullptr;
+    CK(join_caller_stream(c, s, false));
+    CK(state_as_f32(c, &x, s));
+    c->field_valid = false;        // the owner map takes the field's memory as its scratch
+    CK(launch_owner(c->dom, c->G, c->B.cur, c->B.prev, x, c->B.T, out_dev, s));
+    if (status_dev) CK(launch_step_status(c->B.st, status_dev, s));
+    CK(join_caller_stream(c, s, true));
+    return LSGG_OK;
 }
 
 }  // extern "C"

@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "lsgg_internal.cuh"
+#include "../../include/lsgg.h"
 
 namespace lsgg {
 
@@ -173,6 +174,19 @@ cudaError_t launch_owner(const Domain& D, int G, const Box* cur, const Box* prev
     int blocks = (int)((n + 255) / 256);
     if (blocks > 65535 * 16) blocks = 65535 * 16;
     k_owner_decode<<<blocks, 256, 0, s>>>(n, F, out);
+    return cudaGetLastError();
+}
+
+// The status of the steps enqueued so far, read on the device: their error
+// code, LSGG_ERR_CAPACITY for a step stopped on a full box arena (lsgg_sync
+// grows it and finishes the steps), else 0.
+__global__ void k_step_status(const StepState* __restrict__ st, int* __restrict__ out) {
+    const int status = *(volatile const int*)&st->status, halt = *(volatile const int*)&st->halt;
+    *out = status ? status : (halt ? LSGG_ERR_CAPACITY : 0);
+}
+
+cudaError_t launch_step_status(const StepState* st, int* out, cudaStream_t s) {
+    k_step_status<<<1, 1, 0, s>>>(st, out);
     return cudaGetLastError();
 }
 

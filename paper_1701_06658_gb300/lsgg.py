@@ -89,6 +89,8 @@ _SIGS = {
     "lsgg_sync": (C.c_int, [C.c_void_p, C.c_int64]),
     "lsgg_grain_volumes": (C.c_int, [C.c_void_p, _dp, C.c_int64, C.POINTER(C.c_int64)]),
     "lsgg_voxel_owner": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
+    "lsgg_grain_volumes_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "lsgg_voxel_owner_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "lsgg_grain_statistics": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(GrainStats), _dp]),
     "lsgg_coarsen": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "lsgg_texture_shares": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, _dp]),
@@ -256,6 +258,18 @@ def voxel_owner(ctx, shape_zyx, out=None) -> np.ndarray:
     out = np.zeros(shape_zyx, dtype=np.int32) if out is None else out
     _check("voxel_owner", lib().lsgg_voxel_owner(ctx, _ptr(out, C.c_int32), out.size))
     return out
+
+
+def grain_volumes_device(ctx, out_dev: int, cap: int, status_dev: int = 0, stream: int = 0):
+    """lsgg_grain_volumes_device: device pointers in, enqueued, no synchronisation."""
+    _check("grain_volumes_device", lib().lsgg_grain_volumes_device(ctx, out_dev, cap, status_dev or None,
+                                                                   stream or None))
+
+
+def voxel_owner_device(ctx, out_dev: int, n_cells: int, status_dev: int = 0, stream: int = 0):
+    """lsgg_voxel_owner_device: device pointers in, enqueued, no synchronisation."""
+    _check("voxel_owner_device", lib().lsgg_voxel_owner_device(ctx, out_dev, n_cells, status_dev or None,
+                                                               stream or None))
 
 
 def get_stats(ctx) -> Stats:
