@@ -105,3 +105,22 @@ def test_bf16_storage_only_on_the_batched_path(exec_mode):
     cfg.exec = getattr(L, exec_mode)
     ctx = ctypes.c_void_p()
     assert L.lib().lsgg_create_microstructure(ctypes.byref(cfg), None, ctypes.byref(ctx)) == L.ERR_UNSUPPORTED
+
+
+def test_smoke_exclusion_equals_the_parity_helpers():
+    """smoke() carries its own copy of the parity tests' sign-flip exclusion
+    (it imports nothing from tests/): both give the same cells on random
+    boxes, with and without full periodic axes."""
+    import numpy as np
+
+    import __graft_entry__ as ge
+    from tests.parity import box_full, sign_flip_exclusion
+    rng = np.random.default_rng(5)
+    # (box array shape z, y, x; domain z, y, x): full on every axis, on x and z only, 2D full on y only
+    for shape, dom in (((9, 11, 13), (9, 11, 13)), ((9, 11, 13), (9, 40, 13)), ((1, 12, 10), (1, 12, 30))):
+        box = (1, 0, 0, 0, shape[2], shape[1], shape[0])
+        ref = rng.uniform(-2e-4, 2e-4, shape)
+        gpu = ref + rng.uniform(-1e-4, 1e-4, shape)
+        a = ge._sign_flip_exclusion(ref, gpu, box, dom)
+        b = sign_flip_exclusion(ref, gpu, box_full(box, dom))
+        assert np.array_equal(a, b)
