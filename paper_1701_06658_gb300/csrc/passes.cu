@@ -65,8 +65,8 @@ __device__ __forceinline__ float conv_xy_of_const(const float (&g)[2 * R + 1], f
 //           16-byte aligned) arrives in a raw slot by a bulk copy, issued
 //           while the CTA still works on the item before;
 //   stage   raw -> padded grid P in the new layout (-eps outside the old
-//           box), warps over rows and lanes along x; rows outside the old
-//           box are left unstaged;
+//           box), a thread per group of four cells of a padded row; rows
+//           outside the old box are left unstaged;
 //   x pass  each thread convolves 4 consecutive cells of one padded row from
 //           16-byte shared loads -> grid XC (all padded rows; a row outside
 //           the old box is the FMA chain over -eps, written directly);
@@ -84,10 +84,11 @@ __host__ __device__ constexpr int conv_nq(int R) { return (2 * R + 1 + 6) / 4; }
 __host__ __device__ constexpr int conv_px(int R, int side) { return ((side + 3) & ~3) + 4 * conv_nq(R); }
 __host__ __device__ constexpr int conv_xp(int side) { return (side + 3) & ~3; }
 __host__ __device__ constexpr int conv_xr(int R, int side) { return conv_pyr(R, side) + 3; }
+__host__ __device__ constexpr int conv_mx(int R, int side) { return (conv_pyr(R, side) + 3) & ~3; }
 __host__ __device__ constexpr size_t conv_layout_bytes(int R, int side) {
     return 128 + sizeof(float) * ((size_t)side * side + (size_t)conv_pyr(R, side) * conv_px(R, side) +
                                   (size_t)conv_xr(R, side) * conv_xp(side)) +
-           sizeof(int) * 2 * (size_t)conv_pyr(R, side);
+           sizeof(int) * (size_t)(conv_mx(R, side) + conv_pyr(R, side));
 }
 template <int R, int SIDE>
 struct ConvXYLayout {
@@ -96,11 +97,12 @@ struct ConvXYLayout {
     static constexpr int PX = conv_px(R, SIDE);              // room for the last group's window
     static constexpr int XP = conv_xp(SIDE);
     static constexpr int XR = conv_xr(R, SIDE);              // the last 4-row group reads 3 rows past PYR
+    static constexpr int MX = conv_mx(R, SIDE);               // x map entries: whole 4-cell staging groups
     static constexpr size_t raw = 128;                        // after the barrier
     static constexpr size_t P = raw + sizeof(float) * SIDE * SIDE;
     static constexpr size_t XC = P + sizeof(float) * PYR * PX;
     static constexpr size_t maps = XC + sizeof(float) * XR * XP;
-    static constexpr size_t bytes = maps + sizeof(int) * 2 * PYR;
+    static constexpr size_t bytes = maps + sizeof(int) * (MX + PYR);
     static_assert(bytes == conv_layout_bytes(R, SIDE), "one definition of the layout");
 };
 
@@ -116,20 +118,27 @@ __device__ __forceinline__ unsigned dyn_smem_bytes() {
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// raw plane (old layout) -> padded grid P (new layout), warp per padded row.
+// raw plane (old layout) -> padded grid P (new layout): a thread per group of
+// four padded cells of a row (16-byte stores; the map has -1 past the row's
+// end, so a group's extra cells take the fill).  Rows outside the old box are
+// not staged: the x pass writes their result directly.
 template <int NT, int PX, class T>
 __device__ __forceinline__ void stage_plane(const T* raw, float* P, const int* mapx, const int* mapy, int PXa, int PYa,
-                                            int onx, bool have, float fill, int warp, int lane) {
-    for (int yp = warp; yp < PYa; yp += NT / 32) {
+                                            int onx, float fill, int t) {
+    const int ngp = (PXa + 3) >> 2;
+    const Div16 dg(ngp);
+    for (int j = t; j < PYa * ngp; j += NT) {
+        const int yp = dg(j), xp0 = 4 * (j - yp * ngp);
         const int my = mapy[yp];
-        const T* rrow = raw + (my < 0 ? 0 : my) * onx;
-        const bool row_in = have && my >= 0;
-        if (!row_in) continue;                    // a fill row: the x pass writes its result unstaged
-        float* prow = P + yp * PX;
-        for (int xp = lane; xp < PXa; xp += 32) {
-            const int mx = mapx[xp];
-            prow[xp] = row_in && mx >= 0 ? to_f32(rrow[mx]) : fill;
+        if (my < 0) continue;
+        const T* rrow = raw + my * onx;
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int mx = mapx[xp0 + u];
+            v[u] = mx >= 0 ? to_f32(rrow[mx]) : fill;
         }
+        *reinterpret_cast<float4*>(P + yp * PX + xp0) = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
@@ -155,9 +164,9 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
     float* const P = reinterpret_cast<float*>(smc + LY::P);
     float* const XC = reinterpret_cast<float*>(smc + LY::XC);
     int* const mapx = reinterpret_cast<int*>(smc + LY::maps);
-    int* const mapy = mapx + LY::PYR;
+    int* const mapy = mapx + LY::MX;
     __shared__ int s_flag;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int t = threadIdx.x;
     if (t == 0) {
         const bool fits = dyn_smem_bytes() >= LY::bytes;
         if (fits) {
@@ -205,14 +214,14 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
             if (have) { if (t == 0) mbar_wait(bar, phase); }
             return;
         }
-        for (int i = t; i < PXa + PYa; i += NT) {
-            const bool isx = i < PXa;
-            const int ip = isx ? i : i - PXa;
+        for (int i = t; i < LY::MX + PYa; i += NT) {
+            const bool isx = i < LY::MX;
+            const int ip = isx ? i : i - LY::MX;
             const int n = isx ? nx : ny, N = isx ? D.nx : D.ny;
             const int o_new = isx ? nb.ox : nb.oy, o_old = isx ? ob.ox : ob.oy, n_old = isx ? ob.nx : ob.ny;
             const bool full = isx ? fx : fy;
             int l = ip - R, v = -1;
-            if (full || (l >= 0 && l < n)) {
+            if ((!isx || ip < PXa) && (full || (l >= 0 && l < n))) {
                 if (full) l = wrap_near(l, n);
                 const int ol = wrap_near(o_new + l - o_old, N);
                 v = ol < n_old ? ol : -1;
@@ -235,9 +244,11 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         }
         pending = false;
         // stage: raw (old layout, FP32 or BF16) -> P (new layout), warp per padded row
-        if (B.bf16) stage_plane<NT, LY::PX>(reinterpret_cast<const __nv_bfloat16*>(raw), P, mapx, mapy, PXa, PYa,
-                                            ob.nx, have, -D.eps, warp, lane);
-        else stage_plane<NT, LY::PX>(raw, P, mapx, mapy, PXa, PYa, ob.nx, have, -D.eps, warp, lane);
+        if (have) {
+            if (B.bf16) stage_plane<NT, LY::PX>(reinterpret_cast<const __nv_bfloat16*>(raw), P, mapx, mapy, PXa, PYa,
+                                                ob.nx, -D.eps, t);
+            else stage_plane<NT, LY::PX>(raw, P, mapx, mapy, PXa, PYa, ob.nx, -D.eps, t);
+        }
         __syncthreads();                                    // raw is free: fetch the next item's plane
         if (item + (int)gridDim.x < n_items) {
             const float* src;
@@ -740,21 +751,18 @@ __device__ __forceinline__ void scan_line_wrap(float* L, int n, int st) {
     }
 }
 
-// Segmented scan of a line of n <= LANES * L cells (stride st in shared
-// memory) by the LANES consecutive lanes that share it: lane `seg` scans cells
-// [seg * L, seg * L + L) in registers, then takes the boundary value of its
-// neighbour segment (forward: the previous segment's last cell, backward: the
-// next segment's first) and lowers its first / last cells by it.  With L > 6
-// a segment's boundary cells do not depend on the carry coming into it, so
-// one exchange per direction suffices.  All lanes of a group must call.
+// Segmented min-plus scan of a line held in registers by the LANES
+// consecutive lanes that share it: lane `seg` holds cells [seg * L, seg * L +
+// L) and scans them forward and backward; between the two directions it
+// takes the boundary value of its neighbour segment (forward: the previous
+// segment's last cell, backward: the next segment's first) and lowers its
+// first / last cells by it.  With L > 6 a segment's boundary cells do not
+// depend on the carry coming into it, so one exchange per direction suffices.
+// Cells past the line's end hold eps.  All lanes of the warp must call.
 template <int L, int LANES>
-__device__ __forceinline__ void scan_line_seg(float* line, int n, int st, int seg, bool active, float eps) {
+__device__ __forceinline__ void scan_seg_regs(float (&r)[L], int seg, float eps) {
     static_assert(L > kRedistReach, "one exchange per direction needs segments longer than the reach");
     static_assert(LANES > 1 && 32 % LANES == 0, "a group of lanes lies within one warp");
-    float r[L];
-    const int j0 = seg * L;
-#pragma unroll
-    for (int j = 0; j < L; ++j) r[j] = active && j0 + j < n ? line[(j0 + j) * st] : eps;
 #pragma unroll
     for (int j = 1; j < L; ++j) r[j] = fminf(r[j], r[j - 1] + 1.0f);
     float cf = __shfl_up_sync(0xffffffffu, r[L - 1], 1);
@@ -767,40 +775,54 @@ __device__ __forceinline__ void scan_line_seg(float* line, int n, int st, int se
     if (seg == LANES - 1) cb = eps;
 #pragma unroll
     for (int j = 0; j < kRedistReach; ++j) r[L - 1 - j] = fminf(r[L - 1 - j], cb + (float)(j + 1));
-#pragma unroll
-    for (int j = 0; j < L; ++j)
-        if (active && j0 + j < n) line[(j0 + j) * st] = r[j];
 }
 
-// Plane pass of the re-initialisation: a CTA of NT threads takes one (box,
-// slab of kSlab planes) item at a time and walks its planes in z order.
-// Planes of phi_c stream into a 3-slot shared-memory ring by bulk copies
-// (a box plane is contiguous and 16-byte aligned), plane z + 2 being fetched
-// while plane z is processed.  For plane z every thread classifies cells
-// from the slots of z - 1, z, z + 1; the magnitudes go to a grid G (odd
-// pitch); the y and x scans run with NT / SIDE lanes per line; the signs of
-// plane z
-// are put back as the plane is stored with 16-byte stores.  Every wait on a
-// copy is bounded: on expiry the CTA records LSGG_ERR_TIMEOUT, halts the step,
-// drains its copies (bounded) and returns.
-__host__ __device__ constexpr size_t redist_layout_bytes(int side) {     // barriers, 3 plane slots, G
-    return 128 + (size_t)(3 * side * side + side * (side + 1)) * sizeof(float);
+// Plane pass of the re-initialisation: a CTA of NT = 4 * SIDE threads takes
+// one (box, slab of kSlab planes) item at a time and walks its planes in z
+// order.  Planes of phi_c stream into a 3-slot shared-memory ring by bulk
+// copies (a box plane is contiguous and 16-byte aligned), plane z + 2 being
+// fetched while plane z is processed.  Thread (r, s) owns cells [s L, s L +
+// L) of row r (L = SIDE / 4) and, for every plane entering the ring, records
+// their signs (phi > 0) as an L-bit word W.  A cell is a reference cell when
+// a face neighbour's sign differs (outside the box the neighbour is -eps,
+// negative): shifts and XORs of the words of its row, of the rows above and
+// below and of the same row in planes z - 1 and z + 1 find the reference
+// cells of a segment at once, and only those load their neighbours' values
+// for the planar-exact distance; every other cell starts at eps.  The x scan
+// runs in the owner's registers (one carry exchange between the four lanes
+// of a row) and goes to the grid G; thread (c, s) then scans rows [s L, s L +
+// L) of column c the same way and stores plane z with the signs of phi_c put
+// back.  A full periodic axis takes a serial scan twice around the line by
+// one lane.  Every wait on a copy is bounded: on expiry the CTA records
+// LSGG_ERR_TIMEOUT, halts the step, drains its copies (bounded) and returns.
+constexpr int kRedistLanes = 4;      // lanes per row (x phase) and per column (y phase)
+__host__ __device__ constexpr size_t redist_layout_bytes(int side) {  // barriers, 3 plane slots, G, sign words, lists
+    return 128 + (size_t)(3 * side * side + side * (side + 1)) * sizeof(float) +
+           (size_t)3 * side * kRedistLanes * sizeof(unsigned) + (size_t)side * side * sizeof(unsigned short);
 }
+
+// CTAs per SM the register budget is sized for (shared memory allows them)
+__host__ __device__ constexpr int redist_min_blocks(int side) { return side <= 32 ? 8 : side <= 40 ? 6 : side <= 48 ? 5 : 2; }
 
 template <int SIDE, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, redist_min_blocks(SIDE))
 p_redist_xy(StepBuffers B, int tier) {
     constexpr int PA = SIDE * SIDE;                   // floats per plane slot
     constexpr int PG = SIDE + 1;                      // pitch of G
-    constexpr int LANES = NT / SIDE;                  // scan lanes per line
-    constexpr int L = SIDE / LANES;                   // segment of a scan lane
-    constexpr int KC = PA / NT;                       // cells classified per thread
-    static_assert(PA % NT == 0 && NT % SIDE == 0, "LANES lanes per line of the plane");
+    constexpr int LANES = kRedistLanes;
+    constexpr int L = SIDE / LANES;                   // cells per segment
+    constexpr int WS = SIDE * LANES;                  // sign words per slot
+    static_assert(NT == LANES * SIDE && SIDE % LANES == 0, "four lanes per row of the plane");
+    static_assert(L <= 32, "a segment's signs fit one word");
     extern __shared__ __align__(128) unsigned char smraw[];    // redist_layout_bytes(SIDE)
-    static_assert(128 + sizeof(float) * (3 * PA + SIDE * PG) == redist_layout_bytes(SIDE), "one layout");
+    static_assert(128 + sizeof(float) * (3 * PA + SIDE * PG) + sizeof(unsigned) * 3 * WS +
+                  sizeof(unsigned short) * PA == redist_layout_bytes(SIDE), "one layout");
     uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
     float* const slots = reinterpret_cast<float*>(smraw + 128);
     float* const G = slots + 3 * PA;
+    unsigned* const W = reinterpret_cast<unsigned*>(G + SIDE * PG);
+    // per warp, the reference cells of its rows (row << 8 | x): 32 lanes x L cells
+    unsigned short* const RL = reinterpret_cast<unsigned short*>(W + 3 * WS) + (threadIdx.x >> 5) * (32 * L);
     __shared__ int s_flag;
     const int t = threadIdx.x;
     if (t == 0) {
@@ -819,6 +841,8 @@ p_redist_xy(StepBuffers B, int tier) {
     const Domain D = B.dom;
     const float eps = D.eps;
     const float4 fill = make_float4(-eps, -eps, -eps, -eps);
+    const int r = t / LANES, s = t % LANES;           // x phase: row r; y phase: column r
+    const int x0 = s * L;                             // first cell of the segment
     uint32_t phase = 0;                               // bit k: parity of slot k's next completion
     uint32_t pending = 0;                             // bit k: a copy into slot k is in flight
     const int n_items = B.st->n_slabs[tier];
@@ -837,6 +861,11 @@ p_redist_xy(StepBuffers B, int tier) {
             if (t == 0) { atomicExch(&B.st->status, LSGG_ERR_UNSUPPORTED); atomicExch(&B.st->halt, 1); }
             return;                                         // no copy is in flight between items
         }
+        // cells of this thread's segment inside the row (x phase), its valid bits
+        const int nbits = min(max(nx - x0, 0), L);
+        const unsigned valid = nbits >= 32 ? 0xffffffffu : (1u << nbits) - 1u;
+        // the cell of the last segment holding x = nx - 1, for the periodic wrap
+        const int sl = (nx - 1) / L, jl = (nx - 1) - sl * L;
         // plane zz (z0 - 1 <= zz <= z1) lives in slot (zz - z0 + 1) mod 3; a
         // plane outside a non-periodic box is the -eps fill
         auto request = [&](int zz) {
@@ -854,10 +883,11 @@ p_redist_xy(StepBuffers B, int tier) {
                 for (int q = t; q < ps / 4; q += NT) d[q] = fill;
             }
         };
-        __syncthreads();                                    // previous item done with the slots and G
+        __syncthreads();                                    // previous item done with the slots, G and W
         request(z0 - 1);
         request(z0);
         request(z0 + 1);
+        unsigned fresh = 7u;                                // slots whose sign words are still to be made
         for (int z = z0; z < z1; ++z) {
             bool ok = true;
 #pragma unroll
@@ -880,74 +910,111 @@ p_redist_xy(StepBuffers B, int tier) {
                 __syncthreads();
                 return;
             }
-            const float* Pm = slots + ((z - z0) % 3) * PA;
-            const float* Pc = slots + ((z - z0 + 1) % 3) * PA;
-            const float* Pp = slots + ((z - z0 + 2) % 3) * PA;
-            // classification: cells t, t + NT, ... up to the plane's last cell
-            float mag[KC];
-            const Div16 dnx(nx);
+            const int km = (z - z0) % 3, kc = (z - z0 + 1) % 3, kp = (z - z0 + 2) % 3;
+            const float* Pm = slots + km * PA;
+            const float* Pc = slots + kc * PA;
+            const float* Pp = slots + kp * PA;
+            // sign words of the planes that entered the ring: plane z + 1, and at
+            // the slab's start planes z - 1 and z as well
+            fresh |= 1u << kp;
 #pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                const int i = t + k * NT;
-                if (i >= n) break;
-                const int y = dnx(i), x = i - y * nx;
-                const float v = Pc[i];
-                const bool pos = v > 0.0f;
-                float xl = -eps, xr = -eps, yl = -eps, yr = -eps;
-                if (!(fx || fy)) {                          // uniform: the box lies inside the domain
-                    if (x > 0) xl = Pc[i - 1];
-                    if (x < nx - 1) xr = Pc[i + 1];
-                    if (y > 0) yl = Pc[i - nx];
-                    if (y < ny - 1) yr = Pc[i + nx];
-                } else {
-                    xl = x > 0 ? Pc[i - 1] : (fx ? Pc[i + nx - 1] : -eps);
-                    xr = x < nx - 1 ? Pc[i + 1] : (fx ? Pc[i - nx + 1] : -eps);
-                    yl = y > 0 ? Pc[i - nx] : (fy ? Pc[i + n - nx] : -eps);
-                    yr = y < ny - 1 ? Pc[i + nx] : (fy ? Pc[i - n + nx] : -eps);
+            for (int k = 0; k < 3; ++k)
+                if ((fresh >> k) & 1u) {
+                    // cells past the row's end read a later row or the slot's tail
+                    // (in bounds) and are masked off
+                    const float* row = slots + k * PA + min(r, ny - 1) * nx + x0;
+                    unsigned w = 0u;
+#pragma unroll
+                    for (int j = 0; j < L; ++j) w |= (row[j] > 0.0f ? 1u : 0u) << j;
+                    W[k * WS + t] = r < ny ? w & valid : 0u;
                 }
-                mag[k] = ref_magnitude(fabsf(v), opp_max(pos, xl, xr), opp_max(pos, yl, yr),
-                                       opp_max(pos, Pm[i], Pp[i]), eps);
+            fresh = 0u;
+            __syncthreads();
+            // classification and the x scan of row r, segment s
+            float rr[L];
+            {
+                const unsigned* Wc = W + kc * WS;
+                unsigned ref = 0u;
+                if (r < ny) {
+                    const unsigned m0 = Wc[t];
+                    unsigned lbit, rbit;
+                    if (s > 0) lbit = (Wc[t - 1] >> (L - 1)) & 1u;
+                    else lbit = fx ? (Wc[r * LANES + sl] >> jl) & 1u : 0u;
+                    if (x0 + L < nx) rbit = Wc[t + 1] & 1u;
+                    else rbit = fx ? Wc[r * LANES] & 1u : 0u;
+                    const unsigned mL = (m0 << 1) | lbit;
+                    const unsigned mR = nbits > 0 ? (m0 >> 1) | (rbit << (nbits - 1)) : 0u;
+                    const unsigned mU = r > 0 ? Wc[t - LANES] : (fy ? Wc[(ny - 1) * LANES + s] : 0u);
+                    const unsigned mD = r < ny - 1 ? Wc[t + LANES] : (fy ? Wc[s] : 0u);
+                    const unsigned mZm = W[km * WS + t], mZp = W[kp * WS + t];
+                    ref = ((m0 ^ mL) | (m0 ^ mR) | (m0 ^ mU) | (m0 ^ mD) | (m0 ^ mZm) | (m0 ^ mZp)) & valid;
+                }
+                // the warp's reference cells into its list (lane order), then
+                // spread evenly over its lanes: planar-exact distance from the
+                // opposite-sign neighbours -> G
+                const int lane = t & 31;
+                const int cnt = __popc(ref);
+                int pre = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, pre, o);
+                    if (lane >= o) pre += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, pre, 31);
+                pre -= cnt;
+                for (unsigned m = ref; m; m &= m - 1u) RL[pre++] = (unsigned short)((r << 8) | (x0 + __ffs(m) - 1));
+                __syncwarp();
+                for (int q = lane; q < total; q += 32) {
+                    const unsigned e = RL[q];
+                    const int ry = (int)(e >> 8), x = (int)(e & 0xffu);
+                    const int i = ry * nx + x;
+                    const float v = Pc[i];
+                    const bool pos = v > 0.0f;
+                    const float xl = x > 0 ? Pc[i - 1] : (fx ? Pc[i + nx - 1] : -eps);
+                    const float xr = x < nx - 1 ? Pc[i + 1] : (fx ? Pc[i - nx + 1] : -eps);
+                    const float yl = ry > 0 ? Pc[i - nx] : (fy ? Pc[i + n - nx] : -eps);
+                    const float yr = ry < ny - 1 ? Pc[i + nx] : (fy ? Pc[i - n + nx] : -eps);
+                    G[ry * PG + x] = ref_magnitude(fabsf(v), opp_max(pos, xl, xr), opp_max(pos, yl, yr),
+                                                   opp_max(pos, Pm[i], Pp[i]), eps);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < L; ++j) {
+                    const float g = G[r * PG + x0 + j];            // in bounds; used at reference cells only
+                    rr[j] = (ref >> j) & 1u ? g : eps;
+                }
+                if (!fx) scan_seg_regs<L, LANES>(rr, s, eps);
+                // rows past ny and cells past nx of G are written but never read
+#pragma unroll
+                for (int j = 0; j < L; ++j) G[r * PG + x0 + j] = rr[j];
+                if (fx) {                                   // periodic x: the row twice around, one lane
+                    __syncwarp();
+                    if (s == 0 && r < ny) scan_line_wrap(G + r * PG, nx, 1);
+                }
             }
-            __syncthreads();                                // the slot of z - 1 is free
+            __syncthreads();                                // G holds the x scans; the slot of z - 1 is free
             if (z + 1 < z1) request(z + 2);
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                const int i = t + k * NT;
-                if (i >= n) break;
-                const int y = dnx(i), x = i - y * nx;
-                G[y * PG + x] = mag[k];
-            }
-            __syncthreads();
-            // scans: LANES lanes per line; a warp holds 32 / LANES lines and
-            // skips as a whole when all of them lie past the plane
-            const int line = t / LANES, seg = t % LANES, warp_line0 = (t >> 5) * (32 / LANES);
-            if (fy) {                                       // periodic y: one lane per column
-                if (seg == 0 && line < nx) scan_line_wrap(G + line, ny, PG);
-            } else if (warp_line0 < nx) {
-                scan_line_seg<L, LANES>(G + line, ny, PG, seg, line < nx, eps);
-            }
-            __syncthreads();
-            if (fx) {
-                if (seg == 0 && line < ny) scan_line_wrap(G + line * PG, nx, 1);
-            } else if (warp_line0 < ny) {
-                scan_line_seg<L, LANES>(G + line * PG, nx, 1, seg, line < ny, eps);
-            }
-            __syncthreads();
-            // signs of plane z back, 16-byte stores (the plane's tail padding is scratch)
-            float4* dst = reinterpret_cast<float4*>(B.Y + nb.off + (long long)z * ps);
-            for (int q = t; q < ps / 4; q += NT) {
-                float o[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = 4 * q + u;
-                    o[u] = 0.0f;
-                    if (i < n) {
-                        const int y = dnx(i), x = i - y * nx;
-                        const float m = G[y * PG + x];
-                        o[u] = Pc[i] > 0.0f ? m : -m;
-                    }
+            // y scan of column c = r, rows [s L, s L + L), then the signs of plane z back
+            {
+                const int c = r;
+                if (fy) {                                   // periodic y: the column twice around, one lane
+                    if (s == 0 && c < nx) scan_line_wrap(G + c, ny, PG);
+                    __syncwarp();
                 }
-                dst[q] = make_float4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+                for (int j = 0; j < L; ++j) {
+                    const float g = G[(x0 + j) * PG + c];          // in bounds; rows past ny are eps
+                    rr[j] = x0 + j < ny ? g : eps;
+                }
+                if (!fy) scan_seg_regs<L, LANES>(rr, s, eps);
+                float* dst = B.Y + nb.off + (long long)z * ps + c;
+                const float* pcol = Pc + c;
+#pragma unroll
+                for (int j = 0; j < L; ++j) {
+                    const int y = x0 + j;
+                    const float sgn = pcol[min(y, ny - 1) * nx];   // in bounds; stored only inside the plane
+                    if (c < nx && y < ny) dst[y * nx] = sgn > 0.0f ? rr[j] : -rr[j];
+                }
             }
         }
     }
