@@ -92,23 +92,66 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def step_roofline(box_cells: float, dom_cells: float, ms_per_step: float, peak_gbs: float, passes: bool):
+# Bytes per box cell (per domain cell for the field) the design's five passes
+# must move at least: each reads its input field once and writes its output
+# once.  The state X is FP32 (4 B) or BF16 (2 B); with physics the z pass also
+# reads the previous step's phi and ID-field of each cell.
+def pass_bytes(kernel: str, state_bytes: int, physics: bool):
+    """(bytes per box cell of the launch's tier, bytes per domain cell)."""
+    name = kernel.split("[")[0]
+    if name == "p_conv_xy":
+        return state_bytes + 4.0, 0.0                     # X (old layout) in, Z out
+    if name == "p_conv_z":
+        return 8.0 + ((state_bytes + 4.0) if physics else 0.0), 0.0   # Z in, Y out (+ phi, IDF)
+    if name == "p_field":
+        # phi_p read once (the top two), phi_c written (and the ID-field with
+        # physics); the 16-byte field per domain cell stored
+        return 8.0 + (4.0 if physics else 0.0), 16.0
+    if name == "p_redist_xy":
+        return 8.0, 0.0                                   # phi_c in, x/y-scanned magnitudes out
+    if name == "p_redist_z":
+        return 4.0 + state_bytes, 0.0                     # magnitudes in, phi (X) out
+    raise KeyError(kernel)
+
+
+def step_roofline(box_cells: float, dom_cells: float, ms_per_step: float, peak_gbs: float, passes: bool,
+                  state_bytes: int = 4, physics: bool = False):
     """The whole step against the bytes the method must move at least (one
-    FP32 read and write of phi per box cell, 44 B of top-two field per domain
-    cell: 16 cleared, 16 written, 12 read) and against the bytes of this
-    design's five passes (44 B per box cell: 8 each for the x/y and z
-    convolution and re-initialisation passes, 12 for the field pass; 16 B of
-    field per domain cell), both over the measured step time."""
-    minimum = 8.0 * box_cells + 44.0 * dom_cells
-    design = (44.0 * box_cells + 16.0 * dom_cells) if passes else None
+    read and write of phi per box cell -- the ID-field's too with physics --
+    and 44 B of top-two field per domain cell: 16 cleared, 16 written, 12
+    read) and against the bytes of this design's five passes (the sum of
+    pass_bytes over the passes), both over the measured step time."""
+    idf = 8.0 if physics else 0.0
+    minimum = (2.0 * state_bytes + idf) * box_cells + 44.0 * dom_cells
     t = ms_per_step * 1e-3
     out = {"minimum_bytes_per_step": minimum, "minimum_bound_ms": minimum / (peak_gbs * 1e9) * 1e3,
            "achieved_minimum_gbs": minimum / t / 1e9, "frac_minimum": minimum / t / 1e9 / peak_gbs,
            "peak": peak_gbs, "unit": "GB/s"}
-    if design is not None:
-        out.update(design_bytes_per_step=design, achieved_design_gbs=design / t / 1e9,
-                   frac_design=design / t / 1e9 / peak_gbs)
+    if passes:
+        per_box = sum(pass_bytes(k, state_bytes, physics)[0]
+                      for k in ("p_conv_xy", "p_conv_z", "p_field", "p_redist_xy", "p_redist_z"))
+        design = per_box * box_cells + 16.0 * dom_cells
+        out.update(design_bytes_per_step=design, design_bytes_per_box_cell=per_box,
+                   achieved_design_gbs=design / t / 1e9, frac_design=design / t / 1e9 / peak_gbs)
     return out
+
+
+def kernel_roofline(pass_ms: dict, tier_cells, box_cells: float, dom_cells: float, n_grains: int, peak_gbs: float,
+                    state_bytes: int = 4, physics: bool = False):
+    """Roofline of the pass with the longest time per launch: its algorithmic
+    bytes per launch (pass_bytes x the box cells of its tier, or of all boxes
+    for the field pass) over its CUDA-event time."""
+    dominant = max(pass_ms, key=pass_ms.get)
+    if dominant == "k_bin":
+        units, alg = float(n_grains), 32.0 * n_grains
+    else:
+        per_box, per_dom = pass_bytes(dominant, state_bytes, physics)
+        units = box_cells if dominant == "p_field" else float(tier_cells[int(dominant[-2])])
+        alg = per_box * units + per_dom * dom_cells
+    achieved = alg / (pass_ms[dominant] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+            "frac": achieved / peak_gbs, "algorithmic_bytes_per_launch": alg, "units_per_launch": units,
+            "launch_ms": pass_ms[dominant]}
 
 
 def profiled_traffic(kernel: str, units_per_launch: float):
@@ -181,13 +224,15 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- oracle (CPU)
 
-def oracle_sample_run(steps: int, warmup: int):
+def oracle_sample_run(steps: int, warmup: int, seed: int = SAMPLE["seed"]):
     """The FP64 oracle on the bounded sample: 64^3 periodic domain, 78 Voronoi
-    grains (seed 2), dt = 1; returns (cell-updates/s, seconds, cell-updates)."""
+    grains (seed 2 by default), dt = 1; returns (cell-updates/s, seconds,
+    cell-updates)."""
+    import numpy as np
     from oracle import lsgg_oracle as O
     from paper_1701_06658_gb300 import inputs as I
     n, g = SAMPLE["n"], SAMPLE["grains"]
-    ms = O.tessellate((n, n, n), I.voronoi_seeds(SAMPLE["seed"], g, (n, n, n)))
+    ms = O.tessellate((n, n, n), I.voronoi_seeds(seed, g, (n, n, n)))
     for _ in range(warmup):
         ms = O.step(ms, 1.0)
     cells = 0
@@ -197,6 +242,86 @@ def oracle_sample_run(steps: int, warmup: int):
         ms = O.step(ms, 1.0)
     dt = time.perf_counter() - t0
     return cells / dt, dt, cells
+
+
+def _oracle_worker(steps, seed, barrier, out):
+    """One process of the all-core run: tessellate, wait for the others, then
+    time `steps` oracle steps (wall-clock start and end)."""
+    import numpy as np
+    from oracle import lsgg_oracle as O
+    from paper_1701_06658_gb300 import inputs as I
+    n, g = SAMPLE["n"], SAMPLE["grains"]
+    ms = O.tessellate((n, n, n), I.voronoi_seeds(seed, g, (n, n, n)))
+    barrier.wait()
+    t0 = time.time()
+    cells = 0
+    for _ in range(steps):
+        cells += sum(int(np.prod(gr.dims)) for gr in ms.grains if gr.alive)
+        ms = O.step(ms, 1.0)
+    out.put((cells, t0, time.time()))
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_all_cores(steps: int):
+    """The oracle as it stands on every host core: one spawned process per
+    core, each with its own 64^3 sample (seeds 2, 3, ...); after all have
+    tessellated they start together, and the throughput is all processes'
+    cell-updates over the span from the first start to the last finish."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:                      # one thread per process: the cores are the parallelism
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        barrier, out = ctx.Barrier(cores), ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker, args=(steps, SAMPLE["seed"] + k, barrier, out))
+                 for k in range(cores)]
+        for p in procs:
+            p.start()
+        res = [out.get(timeout=600) for _ in procs]
+        for p in procs:
+            p.join(timeout=60)
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    cells = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": cells / span, "cores": cores, "span_s": span, "cell_updates": cells}
+
+
+def cpu_baseline_block(steps: int = 2):
+    """cpu_baseline of the bench line: the oracle on all host cores (value)
+    and on one core, with the host's core count and CPU model."""
+    one_rate, one_s, _ = oracle_sample_run(steps, 0)
+    allc = oracle_all_cores(steps)
+    sample = (f"{steps} oracle steps of a {SAMPLE['n']}^3 periodic sub-domain at the workload's grain density "
+              f"({SAMPLE['grains']} Voronoi grains) per process, one process per core (seeds "
+              f"{SAMPLE['seed']}..{SAMPLE['seed'] + allc['cores'] - 1}), started together after "
+              f"tessellating; {allc['span_s']:.1f} s from the first start to the last finish")
+    return {"value": allc["value"], "unit": UNIT, "cores": allc["cores"], "kind": "oracle", "sample": sample,
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "single_core": {"value": one_rate, "unit": UNIT, "cores": 1, "seconds": one_s}}
 
 
 def reference_arm(args):
@@ -210,7 +335,8 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(),
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -236,33 +362,88 @@ def reduce_over_ranks(dev_ms, cells, e2e_s, e2e_cells, world):
     return mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
 
 
-def workload_kwargs(L):
-    """Microstructure keyword arguments of the workload's physics and tessellation."""
+def workload_kwargs(L, wl=None):
+    """Microstructure keyword arguments of a workload's physics and tessellation."""
+    wl = WORKLOAD if wl is None else wl
     kw = {}
-    ph = WORKLOAD.get("physics", "ideal")
+    ph = wl.get("physics", "ideal")
     if ph == "read_shockley":
         kw["physics"] = L.PHYSICS_READ_SHOCKLEY
     elif ph == "magnetic":
         kw["physics"] = L.PHYSICS_MAGNETIC
-        kw["energy_scale"] = WORKLOAD["energy_scale"]
-    if WORKLOAD.get("init") == "laguerre":
+        kw["energy_scale"] = wl["energy_scale"]
+    if wl.get("init") == "laguerre":
         kw["init_kind"] = L.INIT_LAGUERRE
-    if WORKLOAD.get("redist") == "godunov":
+    if wl.get("redist") == "godunov":
         kw["redist"] = L.REDIST_GODUNOV
     return kw
 
 
-def workload_config():
+def workload_config(wl=None):
+    wl = WORKLOAD if wl is None else wl
     ph = {"ideal": "ideal growth", "read_shockley": "Read-Shockley energy and step mobility, random cubic orientations",
-          "magnetic": "magnetic driving force, random c-axes"}[WORKLOAD.get("physics", "ideal")]
-    tess = ("Laguerre grains, lognormal radii sigma 0.5, 1 % at 5x volume" if WORKLOAD.get("init") == "laguerre"
+          "magnetic": "magnetic driving force, random c-axes"}[wl.get("physics", "ideal")]
+    tess = ("Laguerre grains, lognormal radii sigma 0.5, 1 % at 5x volume" if wl.get("init") == "laguerre"
             else "Voronoi grains")
-    rd = "" if WORKLOAD.get("redist", "taxicab") == "taxicab" else ", Godunov re-initialisation"
-    return {"workload": f"{WORKLOAD['n']}^3 periodic, {WORKLOAD['grains']} {tess} (seed {WORKLOAD['seed']}), "
-                        f"{ph}{rd}, dt={WORKLOAD['dt']}, box halo 5, eps 7, FP32",
-            "domain": [WORKLOAD["n"]] * 3, "grains": WORKLOAD["grains"], "dt": WORKLOAD["dt"],
-            "l2": f"inputs larger than L2: box arenas of ~{WORKLOAD['n'] ** 3 * 8.5 * 4 / 1e9:.1f} GB each and a "
-                  f"{16 * WORKLOAD['n'] ** 3 / 1e6:.0f} MB field vs 129 MB L2"}
+    rd = "" if wl.get("redist", "taxicab") == "taxicab" else ", Godunov re-initialisation"
+    return {"workload": f"{wl['n']}^3 periodic, {wl['grains']} {tess} (seed {wl['seed']}), "
+                        f"{ph}{rd}, dt={wl['dt']}, box halo 5, eps 7, FP32",
+            "domain": [wl["n"]] * 3, "grains": wl["grains"], "dt": wl["dt"],
+            "l2": f"inputs larger than L2: box arenas of ~{wl['n'] ** 3 * 8.5 * 4 / 1e9:.1f} GB each and a "
+                  f"{16 * wl['n'] ** 3 / 1e6:.0f} MB field vs 129 MB L2"}
+
+
+def device_block(L, I, torch, wl, device, steps, warmup, storage, prof_steps=3):
+    """Device-timed steps of a workload (CUDA events on the library's stream,
+    SM clocks sampled meanwhile), then profiled steps for the per-pass times
+    and the roofline of the longest pass."""
+    n, g, dt = wl["n"], wl["grains"], wl["dt"]
+    seeds = I.voronoi_seeds(wl["seed"], g, (n, n, n))
+    physics = wl.get("physics", "ideal") != "ideal"
+    sb = 2 if storage == L.STORAGE_BF16 else 4
+    t0 = time.perf_counter()
+    with L.Microstructure(n, n, n, g, seeds=seeds, device=device, storage=storage, **workload_kwargs(L, wl)) as ms:
+        create_s = time.perf_counter() - t0
+        stream = torch.cuda.ExternalStream(ms.stream)
+        ms.step(warmup, dt)
+        ms.sync()
+        s0 = ms.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with ClockSampler(device) as clk:
+            e0.record(stream)
+            ms.step(steps, dt)
+            e1.record(stream)
+            ms.sync()
+            torch.cuda.synchronize()
+        dev_ms = e0.elapsed_time(e1)
+        s1 = ms.stats()
+        L.profile(ms.ctx, True)
+        ms.step(prof_steps, dt)
+        L.kernel_times(ms.ctx)
+        ptimes = L.pass_times(ms.ctx)
+        L.profile(ms.ctx, False)
+        s2 = ms.stats()
+    cells = s1.cell_updates - s0.cell_updates
+    box_cells = cells / steps
+    pass_ms = {k: v[0] / max(1, v[1]) for k, v in ptimes.items() if v[1] > 0}
+    peaks, src = measured_peaks()
+    cfg = workload_config(wl)
+    cfg["workload"] = cfg["workload"].replace("FP32", "BF16 state storage, FP32 arithmetic" if sb == 2 else "FP32")
+    out = {"config": cfg, "value": cells / (dev_ms * 1e-3), "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": dev_ms / steps, "box_cells_per_step": box_cells, "superimposition": box_cells / n ** 3,
+           "domain_cell_updates_per_s": n ** 3 * steps / (dev_ms * 1e-3), "create_s": create_s,
+           "pass_ms_per_step": pass_ms, "pass_cells_per_tier": list(s2.pass_cells), "clocks": clk.summary(),
+           "timing": "CUDA events on the library's stream around the timed steps (graph replay)"}
+    if pass_ms:
+        prof_cells = (s2.cell_updates - s1.cell_updates) / prof_steps
+        rl = kernel_roofline(pass_ms, list(s2.pass_cells), prof_cells, float(n) ** 3, g, peaks.get("hbm_gbs"),
+                             sb, physics)
+        rl["peak_source"] = src
+        out["roofline"] = rl
+    out["step_roofline"] = step_roofline(box_cells, float(n) ** 3, dev_ms / steps, peaks.get("hbm_gbs"),
+                                         bool(pass_ms), sb, physics)
+    return out
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -438,6 +619,18 @@ def gpu_arm(args):
                       "coarse_steps": {"value": k_rate, "unit": UNIT, "ms_per_step": kms / steps_k,
                                        "steps": steps_k}}
 
+    # ---------------- the non-ideal and magnetic workloads ----------------
+    # 512^3 / 40000 lognormal Laguerre grains under Read-Shockley physics (FP32
+    # state and BF16 state) and 384^3 / 10000 grains with the magnetic driving
+    # force: device-timed steps of each, with their own rooflines
+    configs = None
+    if not args.no_configs and rank == 0:
+        configs = {}
+        for name, key, st in (("512rs_fp32", "512rs", L.STORAGE_FP32), ("512rs_bf16", "512rs", L.STORAGE_BF16),
+                              ("384mag", "384mag", L.STORAGE_FP32)):
+            torch.cuda.synchronize()
+            configs[name] = device_block(L, I, torch, WORKLOADS[key], local, args.config_steps, 3, st)
+
     # ---------------- serving: continuous batching under an HBM budget ----------------
     serving = None
     if args.serve_requests > 0 and rank == 0:
@@ -449,35 +642,33 @@ def gpu_arm(args):
         return 0
 
     value = cells_all / (dev_ms * 1e-3)
-    # roofline of the dominant kernel (algorithmic bytes: 8 B per box cell + 16 B per domain cell)
+    # roofline of the pass with the longest time per launch (its algorithmic bytes
+    # per launch over its CUDA-event time), against the measured copy bandwidth
     peaks, src = measured_peaks()
     dom_cells = n ** 3
     box_cells_prof = cells_prof / kprof
+    physics = WORKLOAD.get("physics", "ideal") != "ideal"
     pass_ms = {name: v[0] / max(1, v[1]) for name, v in ptimes.items() if v[1] > 0}
     if pass_ms:
-        # pass path: the per-tier passes move 8 B per box cell of their tier (one
-        # FP32 read, one FP32 write); the field pass reads phi_p twice, writes
-        # phi_c (12 B per box cell) and stores the 16-byte field per domain cell
-        dominant = max(pass_ms, key=pass_ms.get)
-        if dominant == "p_field":
-            units = box_cells_prof
-            alg_bytes = 12.0 * units + 16.0 * dom_cells
-        elif dominant == "k_bin":
-            units, alg_bytes = float(g), 32.0 * g
-        else:
-            units = float(tier_cells[int(dominant[-2])])
-            alg_bytes = 8.0 * units
-        dom_ms = pass_ms[dominant]
+        roof = kernel_roofline(pass_ms, tier_cells, box_cells_prof, float(dom_cells), g, peaks.get("hbm_gbs"), 4,
+                               physics)
+        dominant, units = roof["kernel"], roof["units_per_launch"]
     else:
         # box-streaming kernels: 8 B per box cell + the 16-byte field per domain cell
         per_launch_ms = {k: ktimes[k] / max(1, kprof) for k in ("k_predict", "k_correct")}
         dominant = max(per_launch_ms, key=per_launch_ms.get)
         units = box_cells_prof
         alg_bytes = 8.0 * box_cells_prof + 16.0 * dom_cells
-        dom_ms = per_launch_ms[dominant]
-    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(dominant, units)
-    cpu_rate, cpu_s, cpu_cells = oracle_sample_run(steps=2, warmup=0) if not args.no_cpu else (None, 0, 0)
+        achieved = alg_bytes / (per_launch_ms[dominant] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs"), "algorithmic_bytes_per_launch": alg_bytes,
+                "units_per_launch": units, "launch_ms": per_launch_ms[dominant]}
+    roof["peak_source"] = src
+    roof["traffic"] = profiled_traffic(dominant, units)
+    roof["traffic_source"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture in "
+                              "profiles/traffic.json, scaled by units processed" if roof["traffic"] is not None
+                              else "no capture of the current pass kernels")
+    cpu = None if args.no_cpu else cpu_baseline_block(2)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
@@ -490,22 +681,17 @@ def gpu_arm(args):
         "pass_ms_per_step": pass_ms, "pass_cells_per_tier": tier_cells, "exec": args.exec,
         "tile_variants": tiles,
         "gpu_launches": int(sum(kcount.values()) * args.steps / max(1, kprof)),
-        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved,
-                     "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                     "frac": achieved / peaks.get("hbm_gbs"), "peak_source": src,
-                     "algorithmic_bytes_per_launch": alg_bytes, "traffic": traffic},
+        "roofline": roof,
         "step_roofline": step_roofline(box_cells_mean, dom_cells, dev_ms / args.steps, peaks.get("hbm_gbs"),
-                                       bool(pass_ms)),
+                                       bool(pass_ms), 4, physics),
         "e2e": None if args.no_e2e else {"value": e2e_cells_all / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * 3 * g / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "seconds": e2e_s, "includes": "create_microstructure from host seeds, steps, per-step volumes "
                                                "to host, final owner map to host"},
-        "cpu_baseline": None if cpu_rate is None else {
-            "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"2 oracle steps of a {SAMPLE['n']}^3 periodic sub-domain at the workload's grain "
-                      f"density ({SAMPLE['grains']} grains), {cpu_s:.1f} s"},
+        "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "serving": serving,
+        "configs": configs,
         "compare": compare,
         "bf16_storage": bf16,
         "coarsening": coarsening,
@@ -516,23 +702,16 @@ def gpu_arm(args):
     return 0
 
 
-def serving_run(L, I, n_requests, device):
-    """Requests drawn from the serving workload (cubic periodic domains 32..256,
-    grains = N^3/3355 clamped to [20, 5000], 10..200 steps), HBM budget 150 GB.
-    Closed loop first (all submitted at once) to measure capacity in requests/s,
-    then Poisson arrivals at 0.8 x capacity: latency = completion - arrival."""
-    budget = 150 << 30
-    probe = I.serving_requests(min(16, n_requests), 1.0, base_seed=5000)
-    with L.Server(budget, max_active=64, steps_per_round=4, device=device) as srv:
-        t0 = time.perf_counter()
-        tk = [srv.submit(r.n, r.n, r.n, r.n_grains, r.steps, seed=r.seed) for r in probe]
-        infos = [srv.wait(t) for t in tk]
-        closed_s = time.perf_counter() - t0
-        closed_cells = sum(i.cell_updates for i in infos)
-    capacity = len(probe) / closed_s
-    reqs = I.serving_requests(n_requests, 0.8 * capacity, base_seed=1000)
-    lat, cells = [], 0
-    with L.Server(budget, max_active=64, steps_per_round=4, device=device) as srv:
+def _pct(sorted_vals, q):
+    return sorted_vals[min(len(sorted_vals) - 1, max(0, int(math.ceil(q * len(sorted_vals))) - 1))]
+
+
+def serve_stream(L, reqs, device, budget, max_active=64, steps_per_round=4):
+    """Submit requests at their arrival times (seconds from the start) and wait
+    for all: per request latency = completion - arrival, the time queued
+    before admission and the time from admission to completion."""
+    lat, queued, service, cells = [], [], [], 0
+    with L.Server(budget, max_active=max_active, steps_per_round=steps_per_round, device=device) as srv:
         start = time.perf_counter()
         tickets = []
         for r in reqs:
@@ -542,17 +721,48 @@ def serving_run(L, I, n_requests, device):
             tickets.append((r, srv.submit(r.n, r.n, r.n, r.n_grains, r.steps, seed=r.seed)))
         for r, t in tickets:
             info = srv.wait(t)
+            if info.state != 2:
+                raise RuntimeError(f"request {r.index} failed with status {info.state}")
             lat.append(info.t_done - info.t_submit)
+            queued.append(info.t_admit - info.t_submit)
+            service.append(info.t_done - info.t_admit)
             cells += info.cell_updates
         wall = time.perf_counter() - start
         peak = srv.stats().peak_bytes
-    lat = sorted(lat)
-    pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
-    return {"requests": n_requests, "rate_per_s": 0.8 * capacity, "capacity_per_s": capacity,
-            "closed_loop_cell_updates_per_s": closed_cells / closed_s,
-            "p50_s": pct(0.50), "p99_s": pct(0.99), "mean_s": sum(lat) / len(lat),
-            "cell_updates_per_s": cells / wall, "wall_s": wall, "peak_admitted_bytes": peak,
-            "budget_bytes": budget}
+    lat, queued, service = sorted(lat), sorted(queued), sorted(service)
+    return {"p50_s": _pct(lat, 0.5), "p99_s": _pct(lat, 0.99), "mean_s": sum(lat) / len(lat),
+            "queued_p50_s": _pct(queued, 0.5), "queued_p99_s": _pct(queued, 0.99),
+            "service_p50_s": _pct(service, 0.5), "service_p99_s": _pct(service, 0.99),
+            "cell_updates": cells, "cell_updates_per_s": cells / wall, "wall_s": wall, "peak_admitted_bytes": peak}
+
+
+def serving_run(L, I, n_requests, device):
+    """The serving workload: independent simulations with cubic periodic
+    domains N in {32, 48, ..., 256}, grains = N^3 / 3355 clamped to [20,
+    5000], 10 to 200 steps, seeds 1000 + k, under an HBM budget of 150 GB.
+    The closed-loop capacity (requests per second with all of a 32-request
+    sample of the same distribution, seeds 5000 + k, submitted at once) sets
+    the rates; the n_requests then arrive as a Poisson stream at 0.8x and at
+    1.2x (overload) of that capacity.  Latency = completion - arrival."""
+    budget = 150 << 30
+    probe = I.serving_requests(32, 1.0, base_seed=5000)
+    for r in probe:
+        r.arrival = 0.0
+    closed = serve_stream(L, probe, device, budget)
+    capacity = len(probe) / closed["wall_s"]
+    out = {"requests": n_requests, "budget_bytes": budget, "max_active": 64, "capacity_per_s": capacity,
+           "closed_loop": {"requests": len(probe), "cell_updates_per_s": closed["cell_updates_per_s"],
+                           "wall_s": closed["wall_s"], "p50_s": closed["p50_s"], "p99_s": closed["p99_s"]},
+           "rates": {}}
+    for factor in (0.8, 1.2):
+        reqs = I.serving_requests(n_requests, factor * capacity, base_seed=1000)
+        res = serve_stream(L, reqs, device, budget)
+        res["rate_per_s"] = factor * capacity
+        out["rates"][f"{factor:.1f}x"] = res
+    lo = out["rates"]["0.8x"]
+    out.update(p50_s=lo["p50_s"], p99_s=lo["p99_s"], cell_updates_per_s=lo["cell_updates_per_s"],
+               peak_admitted_bytes=max(r["peak_admitted_bytes"] for r in out["rates"].values()))
+    return out
 
 
 def main():
@@ -567,8 +777,11 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain / box-streaming comparison runs")
     ap.add_argument("--exec", default="batched", choices=["batched", "streamed"],
                     help="batched: pass path for boxes of side <= 64; streamed: box-streaming kernels only")
-    ap.add_argument("--serve-requests", type=int, default=24,
-                    help="requests of the serving measurement (0: skip; 256: the full serving workload)")
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="requests of the serving measurement at each of its two rates (0: skip)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 512^3 Read-Shockley (FP32, BF16) and 384^3 magnetic blocks")
+    ap.add_argument("--config-steps", type=int, default=8, help="timed steps of each of those blocks")
     ap.add_argument("--redist", default="taxicab", choices=["taxicab", "godunov"],
                     help="re-initialisation metric: the paper's taxicab propagation or the Godunov update")
     ap.add_argument("--workload", default="256", choices=sorted(WORKLOADS),
