@@ -128,7 +128,11 @@ int lsgg_step(lsgg_ctx* ctx, int32_t n, double dt);
 
 /* Wait for enqueued work, at most timeout_ms (< 0: no limit).  Handles a box
  * arena that ran out of room by growing it and finishing the steps.  Returns
- * LSGG_ERR_TIMEOUT if the wait expired (the work keeps running). */
+ * LSGG_ERR_TIMEOUT if the wait expired (the work keeps running).  A failure
+ * on the device (LSGG_ERR_TIMEOUT from a bounded wait in a kernel,
+ * LSGG_ERR_UNSUPPORTED from a launch that refused its input) is returned
+ * once and cleared; the steps that did not complete are dropped
+ * (lsgg_get_stats' steps_done counts the completed ones). */
 int lsgg_sync(lsgg_ctx* ctx, int64_t timeout_ms);
 
 /* Per-grain volume V_i = sum_x H(phi_i(x)), H(phi) = clamp(phi + 1/2, 0, 1).
@@ -476,6 +480,16 @@ int lsgg_debug_set_capacity(lsgg_ctx* ctx, int64_t capacity);
  * way the step kernels wait for their bulk copies; *timed_out = 1 when the
  * wait gave up (the kernel then returns normally).  Synchronises. */
 int lsgg_debug_wait_timeout(int32_t device, int32_t iterations, int32_t* timed_out);
+
+/* Test hook of the step's own bounded waits: the pass kernels poll the
+ * mbarrier of each bulk copy at most `polls` times (polls < 0 restores the
+ * default of 2^22) before they give up: the CTA records LSGG_ERR_TIMEOUT,
+ * halts the step (the step's remaining launches return at once), waits with
+ * the default bound for its copies in flight and returns.  With polls = 0 the
+ * first plane pass of the next step gives up at its first wait, before any
+ * kernel writes the state, so the state stays that of the last completed
+ * step.  Waits for enqueued work first; the next step is captured anew. */
+int lsgg_debug_set_wait_limit(lsgg_ctx* ctx, int32_t polls);
 
 /* SplitMix64 seed points (host only, no device needed): out[3*i + a] =
  * u01(seed, 3*i + a) * N_a for a = x, y, z with

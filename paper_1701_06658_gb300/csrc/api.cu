@@ -13,6 +13,7 @@
 #include <thread>
 #include <vector>
 
+#include "bulk_copy.cuh"
 #include "lsgg_internal.cuh"
 #include "../../include/lsgg.h"
 
@@ -543,6 +544,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->B.use_passes = cfg_in->exec == LSGG_EXEC_BATCHED ? 1 : 0;
     c->B.bf16 = cfg_in->storage == LSGG_STORAGE_BF16 ? 1 : 0;
     c->B.godunov = cfg_in->redist == LSGG_REDIST_GODUNOV ? 1 : 0;
+    c->B.wait_limit = kWaitIters;
     if (configure_step_kernels(c->B) != cudaSuccess) return bail(CUDA_FAIL());
     if (c->B.bf16)
         for (int k = 0; k < kNumClasses; ++k)
@@ -708,7 +710,16 @@ int lsgg_sync(lsgg_ctx* c, int64_t timeout_ms) {
         int r = read_state(c);
         if (r != LSGG_OK) return r;
         if (c->h_st->status == 0) return LSGG_OK;
-        if (c->h_st->status != LSGG_ERR_CAPACITY) return c->h_st->status;
+        if (c->h_st->status != LSGG_ERR_CAPACITY) {
+            // a device-side failure (an expired wait, a refused launch): report it
+            // once, clear it and drop the steps that did not complete
+            const int st = c->h_st->status;
+            if (cudaMemsetAsync(&c->B.st->status, 0, 2 * sizeof(int), c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return CUDA_FAIL();
+            c->steps_target = c->h_st->steps_done;
+            return st;
+        }
         // arena overflow: grow, lay out the pending boxes, finish the remaining steps
         r = grow_arena(c, c->h_st->box_cells);
         if (r != LSGG_OK) return r;
@@ -909,6 +920,18 @@ int lsgg_debug_set_capacity(lsgg_ctx* c, int64_t capacity) {
     if ((r = ensure_chunk_cap(c)) != LSGG_OK) return r;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     return relayout(c);
+}
+
+int lsgg_debug_set_wait_limit(lsgg_ctx* c, int32_t polls) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    c->B.wait_limit = polls < 0 ? kWaitIters : polls;
+    if (c->graph) {                       // the captured step holds the buffers by value
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return LSGG_OK;
 }
 
 int lsgg_grain_neighbours(lsgg_ctx* c, int32_t* counts, int32_t* ids, int32_t cap_per_grain) {

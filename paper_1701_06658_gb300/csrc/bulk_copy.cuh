@@ -36,8 +36,10 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 constexpr int kWaitIters = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (int i = 0; i < kWaitIters; ++i)
+// At most `limit` polls (the step's own waits take the context's limit, which
+// a test hook can lower; the drains after a failed wait keep kWaitIters).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int limit = kWaitIters) {
+    for (int i = 0; i < limit; ++i)
         if (mbar_test(b, parity)) return true;
     return false;
 }

@@ -159,6 +159,7 @@ struct StepBuffers {
     long long scratch_per_cta;
     long long scratch_class_off[kNumClasses];   // each mode-2 class owns a slice (classes run concurrently)
     int n_sm;
+    int wait_limit;                 // polls of a pass kernel's wait on its bulk copies (test hook lowers it)
     int class_side[kNumClasses];    // largest box side per class (last: whole domain)
     int mode[kNumClasses];          // 0: register-ring kernels, 1: shared-memory ring, 2: global scratch ring,
                                     // 3: pass path

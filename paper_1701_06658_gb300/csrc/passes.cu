@@ -230,7 +230,7 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         }
         bool ok = true;
         if (pending) {
-            ok = mbar_wait(bar, phase);
+            ok = mbar_wait(bar, phase, B.wait_limit);
             if (ok) phase ^= 1u;
         }
         if (!__syncthreads_and(ok)) {                       // also publishes the maps
@@ -893,7 +893,7 @@ p_redist_xy(StepBuffers B, int tier) {
 #pragma unroll
             for (int k = 0; k < 3; ++k)
                 if ((pending >> k) & 1u) {
-                    if (mbar_wait(&bar[k], (phase >> k) & 1u)) {
+                    if (mbar_wait(&bar[k], (phase >> k) & 1u, B.wait_limit)) {
                         phase ^= 1u << k;
                         pending &= ~(1u << k);
                     } else {

@@ -127,6 +127,7 @@ _SIGS = {
     "lsgg_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_int32)]),
     "lsgg_debug_set_capacity": (C.c_int, [C.c_void_p, C.c_int64]),
     "lsgg_debug_wait_timeout": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+    "lsgg_debug_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
     "lsgg_pass_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
@@ -293,6 +294,11 @@ def debug_wait_timeout(device: int, iterations: int) -> bool:
     out = C.c_int32(-1)
     _check("debug_wait_timeout", lib().lsgg_debug_wait_timeout(device, iterations, C.byref(out)))
     return out.value == 1
+
+
+def debug_set_wait_limit(ctx, polls: int):
+    """Test hook: polls of the pass kernels' bounded waits (< 0: the default)."""
+    _check("debug_set_wait_limit", lib().lsgg_debug_set_wait_limit(ctx, polls))
 
 
 def profile(ctx, enable: bool):

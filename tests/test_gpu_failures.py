@@ -80,3 +80,30 @@ def test_host_wait_times_out_while_work_runs(L):
         assert code in (L.OK, L.ERR_TIMEOUT)
         ms.sync()
         assert ms.stats().steps_done == 300
+
+
+def test_step_waits_give_up_and_the_context_recovers(L):
+    """The pass kernels' own bounded waits: with the poll limit lowered to zero
+    every plane pass gives up at its first wait on a bulk copy, records
+    LSGG_ERR_TIMEOUT, halts the step and drains its copies; lsgg_sync reports
+    the timeout once.  Nothing was written to the state, so with the default
+    limit restored the steps run as in a context that never timed out."""
+    from paper_1701_06658_gb300 import inputs as I
+    N, G = 64, 50
+    seeds = I.voronoi_seeds(1, G, (N, N, N))
+    with L.Microstructure(N, N, N, G, seeds=seeds) as a:
+        a.step(3, 1.0)
+        a.sync()
+        want_phi, want_boxes = L.get_phi(a.ctx), a.boxes()
+    with L.Microstructure(N, N, N, G, seeds=seeds) as b:
+        L.debug_set_wait_limit(b.ctx, 0)
+        b.step(2, 1.0)
+        assert L.lib().lsgg_sync(b.ctx, -1) == L.ERR_TIMEOUT
+        assert L.lib().lsgg_sync(b.ctx, -1) == L.OK          # reported once
+        assert b.stats().steps_done == 0
+        L.debug_set_wait_limit(b.ctx, -1)
+        b.step(3, 1.0)
+        b.sync()
+        assert b.stats().steps_done == 3
+        assert np.array_equal(b.boxes(), want_boxes)
+        assert np.array_equal(L.get_phi(b.ctx), want_phi)
