@@ -70,6 +70,12 @@ extern "C" {
 #define LSGG_REDIST_TAXICAB 0  /* Sec. 2.1.6 as printed: taxicab propagation from the reference cells */
 #define LSGG_REDIST_GODUNOV 1  /* the Euclidean first-order (Godunov upwind) update instead, iterated
                                   (Jacobi, 20 sweeps over the boxes); LSGG_EXEC_BATCHED, 3D only */
+#define LSGG_REDIST_HARTMANN 2 /* the constrained reinitialization of Hartmann, Meinke and Schroeder
+                                  (Sec. 2.1.6 names it; its first form): 20 forward-Euler steps of
+                                  phi_tau + S(phi0)(|grad phi| - 1) = beta F, dtau = 1/2, beta = 1/2,
+                                  Godunov upwind gradient, F pulling the cells next to the zero level
+                                  towards the values that keep phi0's interpolated crossings in place;
+                                  LSGG_EXEC_BATCHED, 3D only */
 
 #define LSGG_MOBILITY_STEP  0  /* mob_low below theta_max, 1 above */
 #define LSGG_MOBILITY_EQ20  1  /* Eq. (20): 1 - 0.99 exp(-5 (theta / 15 deg)^9) */

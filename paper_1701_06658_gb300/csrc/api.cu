@@ -396,9 +396,10 @@ static int validate(const lsgg_config* cfg) {
     // global-ring box streaming) read and write it; the comparator and the
     // register-ring kernels keep FP32 only
     if (cfg->storage == LSGG_STORAGE_BF16 && cfg->exec != LSGG_EXEC_BATCHED) return LSGG_ERR_UNSUPPORTED;
-    if (cfg->redist != LSGG_REDIST_TAXICAB && cfg->redist != LSGG_REDIST_GODUNOV) return LSGG_ERR_INVALID_ARG;
-    // the Godunov sweeps run on the pass path's column items (3D, batched)
-    if (cfg->redist == LSGG_REDIST_GODUNOV && (cfg->exec != LSGG_EXEC_BATCHED || cfg->nz == 1))
+    if (cfg->redist != LSGG_REDIST_TAXICAB && cfg->redist != LSGG_REDIST_GODUNOV && cfg->redist != LSGG_REDIST_HARTMANN)
+        return LSGG_ERR_INVALID_ARG;
+    // the Godunov and Hartmann sweeps run on the pass path's column items (3D, batched)
+    if (cfg->redist != LSGG_REDIST_TAXICAB && (cfg->exec != LSGG_EXEC_BATCHED || cfg->nz == 1))
         return LSGG_ERR_UNSUPPORTED;
     if (cfg->exec != LSGG_EXEC_BATCHED && cfg->exec != LSGG_EXEC_PLAIN && cfg->exec != LSGG_EXEC_STREAMED)
         return LSGG_ERR_INVALID_ARG;
@@ -543,7 +544,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->B.cur = c->d_boxes + G;
     c->B.use_passes = cfg_in->exec == LSGG_EXEC_BATCHED ? 1 : 0;
     c->B.bf16 = cfg_in->storage == LSGG_STORAGE_BF16 ? 1 : 0;
-    c->B.godunov = cfg_in->redist == LSGG_REDIST_GODUNOV ? 1 : 0;
+    c->B.redist = cfg_in->redist;
     c->B.wait_limit = kWaitIters;
     if (configure_step_kernels(c->B) != cudaSuccess) return bail(CUDA_FAIL());
     if (c->B.bf16)

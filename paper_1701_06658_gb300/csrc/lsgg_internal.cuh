@@ -144,7 +144,8 @@ struct StepBuffers {
     Domain dom;
     int n_boxes;
     int bf16;                       // X holds BF16 (LSGG_STORAGE_BF16); arithmetic stays FP32
-    int godunov;                    // re-initialisation by the Godunov update (LSGG_REDIST_GODUNOV)
+    int redist;                     // LSGG_REDIST_*: TAXICAB by the pass kernels; GODUNOV and HARTMANN
+                                    // by Jacobi sweeps over the boxes' columns
     Box* prev;
     Box* cur;
     Bounds* bounds;
@@ -253,8 +254,9 @@ cudaError_t launch_f32_to_state(const float* in, void* bf16_out, long long n, cu
 cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps& taps, const PhysicsDev& phys,
                           const DebugOut& dbg, cudaStream_t s, cudaEvent_t* pass_ev);
 cudaError_t launch_bin(const StepBuffers& B, cudaStream_t s);
-// LSGG_REDIST_GODUNOV: classification, Jacobi sweeps and signs over all boxes.
-cudaError_t launch_godunov(const StepBuffers& B, const DebugOut& dbg, cudaStream_t s);
+// LSGG_REDIST_GODUNOV: classification, Jacobi sweeps and signs over all boxes;
+// LSGG_REDIST_HARTMANN: the constrained reinitialization's pseudo-time steps.
+cudaError_t launch_sweep_redist(const StepBuffers& B, const DebugOut& dbg, cudaStream_t s);
 cudaError_t launch_field(const StepBuffers& B, const PhysicsDev& phys, const DebugOut& dbg, cudaStream_t s);
 constexpr int kPassEvents = 6 * kTiers + 4;
 // Error tracing (LSGG_TRACE_ERRORS in the environment): `traced` prints a

@@ -1337,8 +1337,142 @@ p_god_final(StepBuffers B, DebugOut dbg) {
     }
 }
 
-cudaError_t launch_godunov(const StepBuffers& B, const DebugOut& dbg, cudaStream_t s) {
+// ---------------------------------------------------------------------------
+// constrained reinitialization of Hartmann et al. (LSGG_REDIST_HARTMANN)
+// ---------------------------------------------------------------------------
+// Forward-Euler pseudo-time steps of phi_tau + S(phi0) (|grad phi| - 1) =
+// beta F from phi0 = phi_c (which stays in Z): S(phi0) = phi0 / sqrt(phi0^2 +
+// 1), |grad phi| by Godunov's upwind scheme (per axis, with a = phi_i -
+// phi_{i-1} and b = phi_{i+1} - phi_i, max(max(a, 0)^2, min(b, 0)^2) where S >
+// 0 and max(min(a, 0)^2, max(b, 0)^2) otherwise), and on a cell with face
+// neighbours j of the opposite sign in phi0 (and phi0_j != 0) F = mean over
+// them of (phi0_i / phi0_j) phi_j - phi_i, the value that keeps each linearly
+// interpolated zero crossing of phi0 in place; every iterate is clamped to
+// [-eps, eps], values outside the box are -eps.  A thread walks one column of
+// a box along z with the z neighbours of phi and phi0 in registers; the
+// steps ping-pong between Y and X (the state is not read after the
+// predictor), and the last one stores the state and the positive bounding
+// box.  The axes and the neighbours enter the sums in the order z, y, x and
+// +1, -1.
+constexpr int kHcrIters = 20;         // pseudo-time steps
+constexpr float kHcrDtau = 0.5f;      // pseudo-time step (grid units)
+constexpr float kHcrBeta = 0.5f;      // weight of the constraint forcing
+
+__device__ __forceinline__ float hcr_axis(float a, float b, bool sp) {
+    const float p = sp ? fmaxf(a, 0.0f) : fminf(a, 0.0f);
+    const float q = sp ? fminf(b, 0.0f) : fmaxf(b, 0.0f);
+    return fmaxf(p * p, q * q);
+}
+
+__device__ __forceinline__ void hcr_term(float q0, bool pos0, float nb0, float nbv, float& cons, int& cnt) {
+    if ((nb0 > 0.0f) != pos0 && nb0 != 0.0f) {
+        cons += (q0 / nb0) * nbv;
+        ++cnt;
+    }
+}
+
+template <bool LAST>
+__global__ void __launch_bounds__(kColThreads)
+p_hcr_step(StepBuffers B, const float* __restrict__ src, float* __restrict__ dst, DebugOut dbg) {
+    if (halted(B)) return;
+    const Domain D = B.dom;
+    const float eps = D.eps;
+    const float* __restrict__ P0 = B.Z;
+    const int n_items = god_n_items(B);
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int2 it = B.chunk_items[item];
+        const int b = it.x;
+        const Box nb = B.cur[b];
+        const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
+        const bool fx = nx == D.nx, fy = ny == D.ny, fz = nz == D.nz;
+        const int c = it.y * kPassChunk + threadIdx.x;
+        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+        if (c < nx * ny) {
+            const int y = c / nx, x = c - y * nx;
+            const int ps = plane_stride(nx, ny);
+            const long long o0 = nb.off + c;
+            const int dxl = x > 0 ? -1 : (fx ? nx - 1 : 0), dxr = x < nx - 1 ? 1 : (fx ? 1 - nx : 0);
+            const int dyl = y > 0 ? -nx : (fy ? (ny - 1) * nx : 0), dyr = y < ny - 1 ? nx : (fy ? (1 - ny) * nx : 0);
+            // plane zz of a field at this column; -eps outside a non-periodic box
+            auto at = [&](const float* f, int zz) -> float {
+                if (zz < 0 || zz >= nz) {
+                    if (!fz) return -eps;
+                    zz = zz < 0 ? zz + nz : zz - nz;
+                }
+                return f[o0 + (long long)zz * ps];
+            };
+            float pm = at(src, -1), pc = at(src, 0), qm = at(P0, -1), qc = at(P0, 0);
+            for (int z = 0; z < nz; ++z) {
+                const float pp = at(src, z + 1), qp = at(P0, z + 1);
+                const long long o = o0 + (long long)z * ps;
+                const float yl = dyl ? src[o + dyl] : -eps, yr = dyr ? src[o + dyr] : -eps;
+                const float xl = dxl ? src[o + dxl] : -eps, xr = dxr ? src[o + dxr] : -eps;
+                const float qyl = dyl ? P0[o + dyl] : -eps, qyr = dyr ? P0[o + dyr] : -eps;
+                const float qxl = dxl ? P0[o + dxl] : -eps, qxr = dxr ? P0[o + dxr] : -eps;
+                const float s0 = qc / sqrtf(qc * qc + 1.0f);
+                const bool sp = s0 > 0.0f;
+                float g2 = hcr_axis(pc - pm, pp - pc, sp);
+                g2 += hcr_axis(pc - yl, yr - pc, sp);
+                g2 += hcr_axis(pc - xl, xr - pc, sp);
+                const bool pos0 = qc > 0.0f;
+                float cons = 0.0f;
+                int cnt = 0;
+                hcr_term(qc, pos0, qp, pp, cons, cnt);
+                hcr_term(qc, pos0, qm, pm, cons, cnt);
+                hcr_term(qc, pos0, qyr, yr, cons, cnt);
+                hcr_term(qc, pos0, qyl, yl, cons, cnt);
+                hcr_term(qc, pos0, qxr, xr, cons, cnt);
+                hcr_term(qc, pos0, qxl, xl, cons, cnt);
+                const float force = cnt ? cons / (float)cnt - pc : 0.0f;
+                float out = pc - kHcrDtau * s0 * (sqrtf(g2) - 1.0f) + kHcrDtau * kHcrBeta * force;
+                out = fminf(fmaxf(out, -eps), eps);
+                if (LAST) {
+                    st_state(B, o, out);
+                    if (dbg.phin) dbg.phin[o] = out;
+                    if (out > 0.0f) {
+                        lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);
+                        lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
+                        lo[2] = min(lo[2], z); hi[2] = max(hi[2], z);
+                    }
+                } else {
+                    dst[o] = out;
+                }
+                pm = pc; pc = pp;
+                qm = qc; qc = qp;
+            }
+        }
+        if (LAST) {
+            // every thread of the CTA reaches this point for every item
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int l = lo[a], h = hi[a];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+                    h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+                }
+                if ((threadIdx.x & 31) == 0 && l <= h) {
+                    atomicMin(&B.bounds[b].lo[a], l);
+                    atomicMax(&B.bounds[b].hi[a], h);
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_sweep_redist(const StepBuffers& B, const DebugOut& dbg, cudaStream_t s) {
     const int grid = B.pgrid[0][4];
+    if (B.redist == LSGG_REDIST_HARTMANN) {
+        // step k reads Z (k = 0), Y (k odd) or X (k even), writes Y (k even) or X
+        static_assert(kHcrIters % 2 == 0, "the last step reads Y and stores the state");
+        for (int k = 0; k < kHcrIters - 1; ++k) {
+            const float* src = k == 0 ? B.Z : ((k & 1) ? B.Y : B.X);
+            float* dst = (k & 1) ? B.X : B.Y;
+            p_hcr_step<false><<<grid, kColThreads, 0, s>>>(B, src, dst, dbg);
+        }
+        p_hcr_step<true><<<grid, kColThreads, 0, s>>>(B, B.Y, B.X, dbg);
+        return cudaGetLastError();
+    }
     p_god_init<<<grid, kColThreads, 0, s>>>(B);
     for (int k = 0; k < kGodunovSweeps; ++k) {
         const bool even = (k & 1) == 0;

@@ -853,12 +853,12 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
         // tier 0 and the small tiers' launches and every pass's tail overlap
         // the others; profiled steps (no side streams) run them one after
         // another so that each event time is one kernel's
-        if (B.use_passes && which == 1 && B.godunov) {
+        if (B.use_passes && which == 1 && B.redist != LSGG_REDIST_TAXICAB) {
             // Godunov re-initialisation over all tiers at once; its time is
             // reported as tier 0's re-initialisation passes
             cudaEvent_t* pe = pass_ev ? pass_ev + 3 : nullptr;
             if (pe) cudaEventRecord(pe[0], s);
-            cudaError_t r = traced(launch_godunov(B, d, s), "Godunov re-initialisation");
+            cudaError_t r = traced(launch_sweep_redist(B, d, s), "sweep re-initialisation");
             if (r != cudaSuccess) return r;
             if (pe) {
                 cudaEventRecord(pe[1], s);
@@ -941,8 +941,8 @@ cudaError_t launch_reinit(const StepBuffers& B, const Taps& taps, const PhysicsD
     cudaError_t e = traced(launch_bin(B, s), "tile binning");
     if (e != cudaSuccess) return e;
     const DebugOut d{};
-    if (B.godunov) {
-        e = traced(launch_godunov(B, d, s), "Godunov re-initialisation");
+    if (B.redist != LSGG_REDIST_TAXICAB) {
+        e = traced(launch_sweep_redist(B, d, s), "sweep re-initialisation");
     } else {
         for (int t = 0; t < kTiers && e == cudaSuccess; ++t)
             e = traced(launch_passes(B, 1, t, taps, phys, d, s, nullptr), "pass kernels");

@@ -32,7 +32,7 @@ PHYSICS_IDEAL, PHYSICS_READ_SHOCKLEY, PHYSICS_MAGNETIC = 0, 1, 2
 STORAGE_FP32, STORAGE_BF16 = 0, 1
 EXEC_BATCHED, EXEC_PLAIN, EXEC_STREAMED = 0, 1, 2
 MOBILITY_STEP, MOBILITY_EQ20 = 0, 1
-REDIST_TAXICAB, REDIST_GODUNOV = 0, 1
+REDIST_TAXICAB, REDIST_GODUNOV, REDIST_HARTMANN = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 

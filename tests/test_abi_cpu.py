@@ -124,3 +124,24 @@ def test_smoke_exclusion_equals_the_parity_helpers():
         a = ge._sign_flip_exclusion(ref, gpu, box, dom)
         b = sign_flip_exclusion(ref, gpu, box_full(box, dom))
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["plain", "streamed", "2d", "unknown"])
+def test_sweep_reinitialisations_only_on_the_batched_3d_path(case):
+    """The Godunov and Hartmann re-initialisations run as column sweeps of the
+    batched 3D path; other execution modes, 2D domains and unknown schemes
+    are refused before any device work."""
+    L = _lib()
+    cfg = L.config_default()
+    cfg.redist = L.REDIST_HARTMANN
+    if case == "plain":
+        cfg.exec = L.EXEC_PLAIN
+    elif case == "streamed":
+        cfg.exec = L.EXEC_STREAMED
+    elif case == "2d":
+        cfg.nz = 1
+    else:
+        cfg.redist = 3
+    ctx = ctypes.c_void_p()
+    code = L.lib().lsgg_create_microstructure(ctypes.byref(cfg), None, ctypes.byref(ctx))
+    assert code in (L.ERR_INVALID_ARG, L.ERR_UNSUPPORTED)

@@ -441,3 +441,59 @@ def test_single_grain_fills_the_domain(L):
     assert np.max(np.abs(phi[0] - ref.grains[0].phi)) <= 1e-6
     assert np.all(phi[0] == 7.0)
     assert vol[0] == N ** 3
+
+
+def test_hartmann_single_step_matches_oracle(L):
+    """LSGG_REDIST_HARTMANN: one step from the GPU's state equals the oracle's
+    step with the constrained reinitialization (reading R16: 20 pseudo-time
+    steps in FP32 against FP64) to the FP32 tolerance; the predictor and
+    comparison parts are the taxicab run's."""
+    N, G = 64, 50
+    seeds = I.voronoi_seeds(1, G, (N, N, N))
+    with L.Microstructure(N, N, N, G, seeds=seeds, redist=L.REDIST_HARTMANN) as ms:
+        ms.step(3, 1.0)
+        boxes = ms.boxes()
+        phi = ms.phi()
+        ref_ms = oracle_from_gpu((N, N, N), boxes, phi)
+        ref_ms.redist = "hartmann"
+        ref = O.step_parts(ref_ms, 1.0)
+        b2, (phip, m, idm, phic, phin) = ms.debug_step(1.0)
+        after = ms.boxes()
+    assert np.array_equal(b2, boxes)
+    worst = 0.0
+    for g in phin:
+        assert np.max(np.abs(phic[g] - ref.phic[g])) <= 2e-5
+        excl = sign_flip_exclusion(ref.phic[g], phic[g], box_full(boxes[g], (N, N, N)))
+        d = np.abs(phin[g] - ref.phi[g])
+        d[excl] = 0
+        worst = max(worst, float(d.max()))
+    assert worst <= TOL_PHI, worst
+    for g, gr in enumerate(ref_ms.grains):
+        if gr.alive:
+            upd = O.box_update(O.Grain(g, gr.origin, ref.phi[g]), ref_ms.shape, 5, 7.0)
+            assert bool(after[g, 0]) == upd.alive
+            if upd.alive:
+                assert (after[g, 3], after[g, 2], after[g, 1]) == upd.origin
+                assert (after[g, 6], after[g, 5], after[g, 4]) == upd.dims
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_hartmann_multistep_volumes(L, storage):
+    """Six Hartmann steps of a 48^3 / 24-grain microstructure: per-grain volumes
+    within 0.1 % of the oracle's (FP32 state; with BF16 storage within the
+    BF16 variant's 0.5 %), every cell owned."""
+    N, G = 48, 24
+    seeds = I.voronoi_seeds(41, G, (N, N, N))
+    ref = O.tessellate((N, N, N), seeds)
+    ref.redist = "hartmann"
+    ref = O.run(ref, 6, 1.0)
+    st = L.STORAGE_FP32 if storage == "fp32" else L.STORAGE_BF16
+    with L.Microstructure(N, N, N, G, seeds=seeds, redist=L.REDIST_HARTMANN, storage=st) as ms:
+        ms.step(6, 1.0)
+        vol = ms.grain_volumes()
+        own = ms.voxel_owner()
+    want = O.volumes(ref)
+    alive = want > 1.0
+    tol = 1e-3 if storage == "fp32" else 5e-3
+    assert np.max(np.abs(vol[alive] - want[alive]) / want[alive]) < tol
+    assert (own >= 0).all()
