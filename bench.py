@@ -474,7 +474,9 @@ def gpu_arm(args):
     stream = torch.cuda.ExternalStream(ms.stream)
     ms.step(args.warmup, dt)
     ms.sync()
-    tiles = L.autotune(ms.ctx, 2, dt) if not args.no_tune else None   # untimed: 6 real steps
+    tiles = None
+    if not args.no_tune:                          # untimed: real steps under each trial setting
+        tiles = {"register_ring": L.autotune(ms.ctx, 2, dt), "pass_path": L.pass_tuning(ms.ctx)}
     ms.sync()
     s0 = ms.stats()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -104,6 +104,10 @@ typedef struct lsgg_config {
     double energy_scale;       /* MAGNETIC: grid-unit bulk energy of cos^2 = 1, i.e.
                                   B^2 dchi h / (2 mu0 gamma_max) (Eqs. (13), (18)) */
     double arena_slack;        /* device box arena capacity / initial need (default 1.5) */
+    double gb_map_tube;        /* 0 (default): Eq. (10)'s pair (i, j) per cell from the ID-field; > 0
+                                  (physics other than IDEAL, batched 3D, below eps): every cell with
+                                  |phi_i| < gb_map_tube takes j from the closest point of grain i's
+                                  triangulated boundary (Sec. 2.1.4; lsgg_closest_gb_map) */
     const double* seeds;       /* optional n_grains x 3 (x, y, z) seed points in cells */
     const double* weights;     /* optional n_grains power weights (LAGUERRE) */
     const double* quats;       /* optional n_grains x 4 unit quaternions (w, x, y, z) */
@@ -288,15 +292,28 @@ int lsgg_get_stats(lsgg_ctx* ctx, lsgg_stats* out);
  * over the steps since the previous call; then resets the sums. */
 int lsgg_profile(lsgg_ctx* ctx, int32_t enable);
 
-/* Tile autotuner of the batched path: for every box-size class served by the
- * register-ring kernels, runs steps_per_trial real steps with each tile
+/* Tile autotuner of the batched path.  On the pass path (3D boxes) it runs
+ * four trials of steps_per_trial profiled steps each -- every persistent grid
+ * at the CTAs per SM that fit, every grid at half of that, and slab items of
+ * 4 and 16 planes for the re-initialisation's plane pass instead of 8 -- and
+ * keeps per tier and pass the faster grid and the slab with the least plane
+ * pass time (read back with lsgg_pass_tuning); chosen (optional, 2 x 8
+ * int32) is then all -1.  Otherwise, for every box-size class served by the
+ * register-ring kernels, it runs steps_per_trial real steps with each tile
  * variant (cells per thread, threads per CTA), times each class's kernels
- * with CUDA events on its stream, and keeps the fastest variant per class and
- * kernel.  Variants give bit-identical results, so the tuning steps are
- * ordinary steps of the simulation (3 * steps_per_trial of them, time dt).
- * chosen (optional, 2 x 8 int32): variant per kernel (predictor, corrector)
- * and class, -1 for classes not served by these kernels.  Synchronises. */
+ * with CUDA events on its stream, and keeps the fastest variant per class
+ * and kernel; chosen: variant per kernel (predictor, corrector) and class,
+ * -1 for classes not served by these kernels.  Every setting gives
+ * bit-identical steps, so the tuning steps are ordinary steps of the
+ * simulation (4 x steps_per_trial on the pass path, 3 x steps_per_trial
+ * otherwise, time dt).  Synchronises. */
 int lsgg_autotune(lsgg_ctx* ctx, int32_t steps_per_trial, double dt, int32_t* chosen);
+
+/* The pass path's current tuning: ctas_per_sm (optional, 4 * LSGG_PASS_TIERS
+ * int32) the CTAs per SM of the persistent grids of p_conv_xy, p_conv_z,
+ * p_redist_xy and p_redist_z of each tier, slab (optional) the planes per slab
+ * item of p_redist_xy; -1 off the pass path. */
+int lsgg_pass_tuning(lsgg_ctx* ctx, int32_t* ctas_per_sm, int32_t* slab);
 int lsgg_kernel_times(lsgg_ctx* ctx, double* out_ms, int64_t* out_count);
 
 /* Per-pass timing of the pass path (LSGG_EXEC_BATCHED, 3D), from the same
@@ -469,10 +486,16 @@ int lsgg_neighbour_max_noalloc(const lsgg_box* boxes_dev, int32_t n_boxes, const
  * indexed by the boxes' offsets; out_dev must not overlap phi_dev or idf_dev.
  * Boxes with dims below 1 or reaching past n_elems are skipped and their
  * outputs left untouched.  0 < tube <= 16, else LSGG_ERR_INVALID_ARG.  The
- * search per cell covers the cubes within ceil(tube) + 1 cells and, where the
- * best distance there does not prove it the box's minimum (a function far
- * from a distance function), every cube of the box.  Enqueued on `stream`
- * (a cudaStream_t, NULL = legacy default stream); returns after enqueue. */
+ * search per cell covers the triangles of the cubes within ceil(tube) + 1
+ * cells and, where the best distance there does not prove it the box's
+ * minimum (a function far from a distance function, or a tube wider than
+ * the function's band, which makes every cell a band cell), every triangle
+ * of the box: the work is bounded by band cells x the box's triangles.
+ * Allocates its scratch in stream order (cudaMallocAsync / cudaFreeAsync on
+ * `stream`: per CTA room for the triangles of a box of up to 2^17 cubes;
+ * larger boxes rebuild their triangles per cell) and returns
+ * LSGG_ERR_OUT_OF_MEMORY if that fails.  Enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream); returns after enqueue. */
 int lsgg_closest_gb_map(const lsgg_box* boxes_dev, int32_t n_boxes, const float* phi_dev, const int32_t* idf_dev,
                         int64_t n_elems, float tube, int32_t* out_dev, void* stream);
 
@@ -486,6 +509,15 @@ int lsgg_debug_set_capacity(lsgg_ctx* ctx, int64_t capacity);
  * way the step kernels wait for their bulk copies; *timed_out = 1 when the
  * wait gave up (the kernel then returns normally).  Synchronises. */
 int lsgg_debug_wait_timeout(int32_t device, int32_t iterations, int32_t* timed_out);
+
+/* Test hook of the anisotropy map (contexts created with gb_map_tube > 0):
+ * the pairs the next step's Eq. (10) blend will use.  idf_out = the ID-field
+ * of the last step resampled onto the current boxes (-1 outside the previous
+ * box), map_out = the map computed from it and the state on those boxes
+ * (lsgg_closest_gb_map's definition, box-local to the current box); both
+ * packed like lsgg_get_phi, cap >= that count.  LSGG_ERR_UNSUPPORTED without
+ * the map.  Synchronises. */
+int lsgg_debug_pair_ids(lsgg_ctx* ctx, int32_t* idf_out, int32_t* map_out, int64_t cap);
 
 /* Test hook of the step's own bounded waits: the pass kernels poll the
  * mbarrier of each bulk copy at most `polls` times (polls < 0 restores the

@@ -1206,18 +1206,45 @@ def point_triangle_distance(p: np.ndarray, tris: np.ndarray) -> np.ndarray:
     return np.where(inside, np.minimum(best, dplane), best)
 
 
-def closest_gb_grains(phi: np.ndarray, idf: np.ndarray, tube: float) -> np.ndarray:
+def point_triangle_distances(pts: np.ndarray, tris: np.ndarray) -> np.ndarray:
+    """point_triangle_distance for several points at once: row k holds the
+    distances from pts[k] to every triangle, by the same operations in the
+    same order."""
+    p = pts[:, None, :]
+    a, b, c = tris[None, :, 0], tris[None, :, 1], tris[None, :, 2]
+    best = np.full((len(pts), len(tris)), np.inf)
+    for u, v in ((a, b), (b, c), (c, a)):
+        e = v - u
+        t = np.clip(((p - u) * e).sum(2) / np.maximum((e * e).sum(2), 1e-300), 0.0, 1.0)
+        best = np.minimum(best, np.linalg.norm(p - (u + t[:, :, None] * e), axis=2))
+    n = np.cross(b - a, c - a)
+    nn = (n * n).sum(2)
+    ok = nn > 1e-24
+    foot = p - (((p - a) * n).sum(2) / np.where(ok, nn, 1.0))[:, :, None] * n
+    inside = np.broadcast_to(ok, best.shape).copy()
+    for u, v in ((a, b), (b, c), (c, a)):
+        inside &= (np.cross(v - u, foot - u) * n).sum(2) >= 0.0
+    dplane = np.linalg.norm(p - foot, axis=2)
+    return np.where(inside, np.minimum(best, dplane), best)
+
+
+def closest_gb_grains(phi: np.ndarray, idf: np.ndarray, tube: float, block: int = 128) -> np.ndarray:
     """The anisotropy map (R15): every cell of the box within `tube` of the
     zero level (|phi| < tube) adopts the grain across the closest triangle of
     the grain boundary (Sec. 2.1.4: each grid point takes the energy and
     mobility of the closest GB point); the other cells keep their ID-field.
-    The result replaces the per-cell ID-field of R3 in Eq. (10)'s weights."""
+    The result replaces the per-cell ID-field of R3 in Eq. (10)'s weights.
+    Cells are taken `block` at a time; each takes its first closest triangle,
+    as closest_gb_grain_at does."""
     tris, grains = gb_triangles(phi, idf)
     out = idf.astype(np.int64).copy()
     if len(tris) == 0:
         return out
-    for z, y, x in zip(*np.nonzero(np.abs(phi) < tube)):
-        out[z, y, x] = closest_gb_grain_at((z, y, x), tris, grains)
+    cells = np.argwhere(np.abs(phi) < tube)
+    for k in range(0, len(cells), block):
+        blk = cells[k:k + block]
+        d = point_triangle_distances(blk.astype(np.float64), tris)
+        out[tuple(blk.T)] = grains[np.argmin(d, axis=1)]
     return out
 
 

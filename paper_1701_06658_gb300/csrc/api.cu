@@ -199,6 +199,20 @@ int replace_z(lsgg_ctx* c, long long cap) {
 
 int ensure_chunk_cap(lsgg_ctx* c);
 
+// The anisotropy map's arena at `cap` elements (its content is rebuilt by
+// every step).
+int replace_map(lsgg_ctx* c, long long cap) {
+    if (!c->B.gb_map) return LSGG_OK;
+    int* M2 = nullptr;
+    int r = dalloc(c, &M2, (size_t)cap);
+    if (r != LSGG_OK) return r;
+    c->device_bytes -= c->B.cap * 4;
+    dfree(c, c->B.gb_map);
+    c->B.gb_map = M2;
+    c->phys.pair_map = M2;
+    return LSGG_OK;
+}
+
 // Grow the arenas to hold `need` elements, keeping the state (prev layout).
 int grow_arena(lsgg_ctx* c, long long need) {
     long long cap = std::max<long long>(need + need / 4, c->B.cap * 2);
@@ -219,6 +233,7 @@ int grow_arena(lsgg_ctx* c, long long need) {
     c->B.Y = Y2;
     c->B.IDF = I2;
     r = replace_z(c, cap);
+    if (r == LSGG_OK) r = replace_map(c, cap);
     c->B.cap = cap;
     if (r == LSGG_OK) r = ensure_chunk_cap(c);
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
@@ -408,6 +423,12 @@ static int validate(const lsgg_config* cfg) {
          (cfg->mobility_law != LSGG_MOBILITY_STEP && cfg->mobility_law != LSGG_MOBILITY_EQ20)))
         return LSGG_ERR_INVALID_ARG;
     if (!(cfg->arena_slack >= 1.0)) return LSGG_ERR_INVALID_ARG;
+    // the anisotropy map: a tube inside the band, physics that reads pairs,
+    // the pass path's z pass
+    if (!(cfg->gb_map_tube >= 0.0) || cfg->gb_map_tube >= cfg->eps) return LSGG_ERR_INVALID_ARG;
+    if (cfg->gb_map_tube > 0.0 &&
+        (cfg->physics == LSGG_PHYSICS_IDEAL || cfg->exec != LSGG_EXEC_BATCHED || cfg->nz == 1))
+        return LSGG_ERR_UNSUPPORTED;
     // taxicab reach is fixed to the default band: eps = 7 gives 6 exact steps
     if (std::fabs(cfg->eps - 7.0f) > 1e-6f) return LSGG_ERR_UNSUPPORTED;
     return LSGG_OK;
@@ -554,7 +575,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
         c->B.plane_item_cap = (long long)G * D.nz;
         if ((r = dalloc(c, &c->B.plane_items, (size_t)c->B.plane_item_cap)) != LSGG_OK) return bail(r);
         if ((r = dalloc(c, &c->B.item_base, (size_t)G)) != LSGG_OK) return bail(r);
-        c->B.slab_item_cap = (long long)G * ((D.nz + kSlab - 1) / kSlab);
+        c->B.slab_item_cap = (long long)G * ((D.nz + kMinSlab - 1) / kMinSlab);
         if ((r = dalloc(c, &c->B.slab_items, (size_t)c->B.slab_item_cap)) != LSGG_OK) return bail(r);
         if ((r = dalloc(c, &c->B.tile_cnt, (size_t)c->B.n_tiles)) != LSGG_OK) return bail(r);
         if ((r = dalloc(c, &c->B.tile_list, (size_t)c->B.n_tiles * kTileCap)) != LSGG_OK) return bail(r);
@@ -639,6 +660,19 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if (c->separate_z && (r = dalloc(c, &c->B.Z, (size_t)cap)) != LSGG_OK) return bail(r);
     if (c->B.use_passes && !c->separate_z) c->B.Z = reinterpret_cast<float*>(c->B.IDF);
     if ((r = ensure_chunk_cap(c)) != LSGG_OK) return bail(r);
+    if (cfg_in->gb_map_tube > 0.0) {
+        // the map per cell (arena layout) and the map kernel's scratch: per CTA
+        // the triangles of a box of up to 2^16 cubes (larger boxes rebuild theirs)
+        c->B.gb_tube = (float)cfg_in->gb_map_tube;
+        c->B.gb_grid = 2 * c->B.n_sm;
+        c->B.gb_cap_cubes = 1 << 16;
+        c->B.gb_cap_tris = 1 << 14;
+        if ((r = dalloc(c, &c->B.gb_map, (size_t)cap)) != LSGG_OK) return bail(r);
+        const size_t sb = gb_map_scratch_bytes(c->B.gb_grid, c->B.gb_cap_cubes, c->B.gb_cap_tris);
+        unsigned char* sc = nullptr;
+        if ((r = dalloc(c, &sc, sb)) != LSGG_OK) return bail(r);
+        c->B.gb_scratch = sc;
+    }
     c->B.scratch_per_cta = large_class_scratch_floats(D);
     {
         long long total = 0;
@@ -675,6 +709,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->phys.theta_max = cfg_in->theta_max_deg * M_PI / 180.0;
     c->phys.mob_low = cfg_in->mob_low;
     c->phys.mob_law = cfg_in->mobility_law;
+    c->phys.pair_map = c->B.gb_map;
     *out = c;
     return LSGG_OK;
 }
@@ -753,10 +788,79 @@ int lsgg_get_stats(lsgg_ctx* c, lsgg_stats* out) {
     return LSGG_OK;
 }
 
+// The pass path's tunables: per tier and pass the CTAs per SM of its
+// persistent grid (pgrid index 0 conv_xy, 1 / 2 conv_z ideal / physics, 3
+// redist_xy, 4 redist_z) and the slab depth of p_redist_xy.  Re-lays the work
+// items out for the slab; the step graph is captured anew.
+static int apply_pass_tuning(lsgg_ctx* c, const int (&ctas)[kTiers][5], int slab) {
+    for (int t = 0; t < kTiers; ++t)
+        for (int k = 0; k < 5; ++k) c->B.pgrid[t][k] = c->B.n_sm * std::max(1, std::min(ctas[t][k], c->B.pocc[t][k]));
+    c->B.slab = slab;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return relayout(c);
+}
+
+// Autotuner of the pass path: trials of steps_per_trial profiled steps each
+// with (a) every grid at its resident maximum and the default slab, (b) every
+// grid at half of it, (c, d) slabs of 4 and 16 planes; per tier and pass the
+// faster grid of (a, b), and the slab with the least re-initialisation
+// plane-pass time over the tiers.  All settings give bit-identical steps.
+static int autotune_passes(lsgg_ctx* c, int32_t steps_per_trial, double dt) {
+    int full[kTiers][5], half[kTiers][5];
+    for (int t = 0; t < kTiers; ++t)
+        for (int k = 0; k < 5; ++k) { full[t][k] = c->B.pocc[t][k]; half[t][k] = std::max(1, c->B.pocc[t][k] / 2); }
+    const int slabs[4] = {kSlab, kSlab, kMinSlab, 2 * kSlab};
+    double ms[4][kTiers * 4 + 2] = {};
+    c->profiling = true;
+    for (int trial = 0; trial < 4; ++trial) {
+        int r = apply_pass_tuning(c, trial == 1 ? half : full, slabs[trial]);
+        if (r == LSGG_OK) r = lsgg_step(c, steps_per_trial, dt);
+        if (r == LSGG_OK) r = lsgg_pass_times(c, ms[trial], nullptr);
+        if (r != LSGG_OK) { c->profiling = false; return r; }
+    }
+    c->profiling = false;
+    // pass index of lsgg_pass_times (conv_xy, conv_z, redist_xy, redist_z) -> pgrid index
+    const int pk[4][2] = {{0, 0}, {1, 2}, {3, 3}, {4, 4}};
+    int best[kTiers][5];
+    for (int t = 0; t < kTiers; ++t)
+        for (int q = 0; q < 4; ++q)
+            for (int j = 0; j < 2; ++j) {
+                const int k = pk[q][j];
+                best[t][k] = ms[1][t * 4 + q] < ms[0][t * 4 + q] ? half[t][k] : full[t][k];
+            }
+    int slab = kSlab;
+    double slab_ms = 0.0;
+    for (int trial : {0, 2, 3}) {
+        double tot = 0.0;
+        for (int t = 0; t < kTiers; ++t) tot += ms[trial][t * 4 + 2];
+        if (trial == 0 || tot < slab_ms) { slab_ms = tot; slab = slabs[trial]; }
+    }
+    return apply_pass_tuning(c, best, slab);
+}
+
+int lsgg_pass_tuning(lsgg_ctx* c, int32_t* ctas_per_sm, int32_t* slab) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    if (ctas_per_sm)
+        for (int t = 0; t < kTiers; ++t) {
+            const int k4[4] = {0, c->phys.kind != LSGG_PHYSICS_IDEAL ? 2 : 1, 3, 4};
+            for (int q = 0; q < 4; ++q) ctas_per_sm[t * 4 + q] = c->B.use_passes ? c->B.pgrid[t][k4[q]] / c->B.n_sm : -1;
+        }
+    if (slab) *slab = c->B.use_passes ? c->B.slab : -1;
+    return LSGG_OK;
+}
+
 int lsgg_autotune(lsgg_ctx* c, int32_t steps_per_trial, double dt, int32_t* chosen) {
     if (!c || steps_per_trial < 1 || !(dt > 0.0) || dt > 4.0) return LSGG_ERR_INVALID_ARG;
     int r = lsgg_sync(c, -1);
     if (r != LSGG_OK) return r;
+    if (c->B.use_passes) {
+        if (chosen)
+            for (int k = 0; k < 2 * kNumClasses; ++k) chosen[k] = -1;
+        r = autotune_passes(c, steps_per_trial, dt);
+        c->field_valid = true;
+        c->last_dt = dt;
+        return r;
+    }
     if (cudaSetDevice(c->device) != cudaSuccess) return CUDA_FAIL();
     const int nv = StepBuffers::kVariants;
     const int ne = 4 * kNumClasses;
@@ -917,6 +1021,7 @@ int lsgg_debug_set_capacity(lsgg_ctx* c, int64_t capacity) {
     c->B.Y = Y2;
     c->B.IDF = I2;
     if ((r = replace_z(c, capacity)) != LSGG_OK) return r;
+    if ((r = replace_map(c, capacity)) != LSGG_OK) return r;
     c->B.cap = capacity;
     if ((r = ensure_chunk_cap(c)) != LSGG_OK) return r;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
@@ -998,6 +1103,29 @@ int lsgg_get_phi(lsgg_ctx* c, float* out, int64_t cap, int64_t* n_out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     c->device_bytes -= off[c->G] * 4;
     dfree(c, d);
+    return e == cudaSuccess ? LSGG_OK : LSGG_ERR_CUDA;
+}
+
+int lsgg_debug_pair_ids(lsgg_ctx* c, int32_t* idf_out, int32_t* map_out, int64_t cap) {
+    if (!c || !idf_out || !map_out) return LSGG_ERR_INVALID_ARG;
+    if (!c->B.gb_map) return LSGG_ERR_UNSUPPORTED;
+    int r = lsgg_sync(c, -1);
+    if (r != LSGG_OK) return r;
+    std::vector<long long> off;
+    if ((r = packed_offsets(c, c->B.cur, off)) != LSGG_OK) return r;
+    if (cap < off[c->G]) return LSGG_ERR_CAPACITY;
+    int* tmp = nullptr;
+    if ((r = dalloc(c, &tmp, (size_t)off[c->G] + 1)) != LSGG_OK) return r;
+    cudaError_t e = launch_gb_map_step(c->B, c->stream);
+    const void* src[2] = {c->B.Z, c->B.gb_map};      // the resampled ID-field, the map
+    int32_t* dst[2] = {idf_out, map_out};
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = launch_pack_cur(c->G, c->B.cur, src[k], c->d_packed_off, tmp, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst[k], tmp, (size_t)off[c->G] * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    c->device_bytes -= (off[c->G] + 1) * 4;
+    dfree(c, tmp);
     return e == cudaSuccess ? LSGG_OK : LSGG_ERR_CUDA;
 }
 

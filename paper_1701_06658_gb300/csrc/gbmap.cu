@@ -349,19 +349,50 @@ k_gb_map(const lsgg_box* __restrict__ boxes, int n_boxes, const float* __restric
     }
 }
 
-// the step: every alive box in the state's own layout (`prev`), into map
-template <class T>
+// The state and its ID-field on the current boxes (the boxes the step writes),
+// in their layout: a cell outside the previous box is -eps and -1 (the
+// grain's function and ID-field as they enter the step, Sec. 3.1).
+__global__ void __launch_bounds__(256)
+k_gb_resample(StepBuffers B, float* __restrict__ phi, int* __restrict__ idf) {
+    const Domain D = B.dom;
+    for (int b = blockIdx.x; b < B.n_boxes; b += gridDim.x) {
+        const Box nb = B.cur[b], ob = B.prev[b];
+        if (nb.nx <= 0) continue;
+        const int A = nb.nx * nb.ny, ps = plane_stride(nb.nx, nb.ny), ops = plane_stride(ob.nx, ob.ny);
+        const long long n = (long long)A * nb.nz;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+            const int z = (int)(i / A), rem = (int)(i - (long long)z * A);
+            const int y = rem / nb.nx, x = rem - y * nb.nx;
+            const int lx = pmod(nb.ox + x - ob.ox, D.nx), ly = pmod(nb.oy + y - ob.oy, D.ny);
+            const int lz = pmod(nb.oz + z - ob.oz, D.nz);
+            float v = -D.eps;
+            int j = -1;
+            if (lx < ob.nx && ly < ob.ny && lz < ob.nz) {
+                const long long o = ob.off + (long long)lz * ops + (long long)ly * ob.nx + lx;
+                v = ld_state(B, o);
+                j = B.IDF[o];
+            }
+            const long long d = nb.off + (long long)z * ps + rem;
+            phi[d] = v;
+            idf[d] = j;
+        }
+    }
+}
+
+// the step: every alive box on its current box, phi and ID-field resampled
+// into the layout of `cur`, the map into `map` (same layout)
 __global__ void __launch_bounds__(kGbThreads)
-k_gb_map_state(StepBuffers B, const T* __restrict__ X, float tube, int r, int* __restrict__ map,
-               int* __restrict__ scratch_off, float4* __restrict__ scratch_tri, int cap_cubes, int cap_tris) {
+k_gb_map_step(StepBuffers B, const float* __restrict__ phi, const int* __restrict__ idf, float tube, int r,
+              int* __restrict__ map, int* __restrict__ scratch_off, float4* __restrict__ scratch_tri, int cap_cubes,
+              int cap_tris) {
     if (*(volatile int*)&B.st->halt) return;
     int* off = scratch_off + (long long)blockIdx.x * (cap_cubes + 1);
     float4* tri = scratch_tri + (long long)blockIdx.x * 3 * cap_tris;
     for (int b = blockIdx.x; b < B.n_boxes; b += gridDim.x) {
-        const Box ob = B.prev[b];
-        if (ob.nx <= 0 || B.cur[b].nx <= 0) continue;
-        const GbBox g{ob.off, ob.nx, ob.ny, ob.nz, plane_stride(ob.nx, ob.ny)};
-        gb_map_box(g, X, B.IDF, map, tube, r, off, tri, cap_cubes, cap_tris);
+        const Box nb = B.cur[b];
+        if (nb.nx <= 0) continue;
+        const GbBox g{nb.off, nb.nx, nb.ny, nb.nz, plane_stride(nb.nx, nb.ny)};
+        gb_map_box(g, phi, idf, map, tube, r, off, tri, cap_cubes, cap_tris);
         __syncthreads();
     }
 }
@@ -379,17 +410,18 @@ static void gb_scratch(void* scratch, int grid, int cap_tris, int** off, float4*
     *off = reinterpret_cast<int*>(*tri + (size_t)grid * 3 * cap_tris);
 }
 
-cudaError_t launch_gb_map_state(const StepBuffers& B, float tube, int* map, void* scratch, int grid, int cap_cubes,
-                                int cap_tris, cudaStream_t s) {
+// The anisotropy map of the step into B.gb_map (layout of `cur`): the state
+// and ID-field resampled onto the current boxes into Y and Z (free before the
+// predictor's passes write them), then the map.
+cudaError_t launch_gb_map_step(const StepBuffers& B, cudaStream_t s) {
     int* off = nullptr;
     float4* tri = nullptr;
-    gb_scratch(scratch, grid, cap_tris, &off, &tri);
-    const int r = (int)ceilf(tube) + 1;
-    if (B.bf16)
-        k_gb_map_state<__nv_bfloat16><<<grid, kGbThreads, 0, s>>>(B, reinterpret_cast<const __nv_bfloat16*>(B.X), tube,
-                                                                   r, map, off, tri, cap_cubes, cap_tris);
-    else
-        k_gb_map_state<float><<<grid, kGbThreads, 0, s>>>(B, B.X, tube, r, map, off, tri, cap_cubes, cap_tris);
+    gb_scratch(B.gb_scratch, B.gb_grid, B.gb_cap_tris, &off, &tri);
+    int* idf = reinterpret_cast<int*>(B.Z);
+    k_gb_resample<<<B.n_sm * 4, 256, 0, s>>>(B, B.Y, idf);
+    const int r = (int)ceilf(B.gb_tube) + 1;
+    k_gb_map_step<<<B.gb_grid, kGbThreads, 0, s>>>(B, B.Y, idf, B.gb_tube, r, B.gb_map, off, tri, B.gb_cap_cubes,
+                                                   B.gb_cap_tris);
     return cudaGetLastError();
 }
 

@@ -35,7 +35,8 @@ constexpr int kNumClasses = 5;          // box side <= 32, 40, 48, 64, larger (g
 constexpr int kRedistReach = 6;         // taxicab steps below eps = 7 (exact fixed point)
 constexpr int kTiers = 5;               // pass path: boxes with x, y sides <= 32, <= 40, <= 48, <= 64, larger
 constexpr int kPassChunk = 256;         // columns per column item of the pass path
-constexpr int kSlab = 8;                // planes per slab item of the pass path
+constexpr int kSlab = 8;                // planes per slab item of the pass path (default; autotuned)
+constexpr int kMinSlab = 4;             // the smallest slab the autotuner tries (sizes the slab item list)
 constexpr int kTileX = 8, kTileY = 32, kTileZ = 8;    // domain tiles of the field pass
 constexpr int kTileCap = 128;           // boxes listed per tile (more: the tile scans all boxes)
 
@@ -76,6 +77,8 @@ struct PhysicsDev {
     int kind;                       // LSGG_PHYSICS_*
     const float* energy;            // per grain bulk energy, grid units (MAGNETIC)
     const double* quats;            // per grain unit quaternion (w, x, y, z) (READ_SHOCKLEY)
+    const int* pair_map;            // per cell of `cur` the pair's j (the anisotropy map), or null: the
+                                    // previous step's ID-field (`prev` layout) gives j
     const int* nb_tab;              // per grain: ascending ids of the grains in its ID-field
     const int* nb_cnt;              // per grain: entries (kNbCap + 1: the table overflowed)
     const float* nb_w;              // per grain and entry: pair weight w (READ_SHOCKLEY, refreshed with nb_tab)
@@ -160,6 +163,12 @@ struct StepBuffers {
     long long scratch_per_cta;
     long long scratch_class_off[kNumClasses];   // each mode-2 class owns a slice (classes run concurrently)
     int n_sm;
+    // anisotropy map of Eq. (10)'s pairs (gb_tube > 0): per cell of `cur`, and
+    // the map kernel's per-CTA scratch
+    float gb_tube;
+    int* gb_map;
+    void* gb_scratch;
+    int gb_grid, gb_cap_cubes, gb_cap_tris;
     int wait_limit;                 // polls of a pass kernel's wait on its bulk copies (test hook lowers it)
     int class_side[kNumClasses];    // largest box side per class (last: whole domain)
     int mode[kNumClasses];          // 0: register-ring kernels, 1: shared-memory ring, 2: global scratch ring,
@@ -183,6 +192,8 @@ struct StepBuffers {
     int tier_side[kTiers];
     int tier_threads[kTiers];       // threads per CTA of the plane passes (= tier side)
     int pgrid[kTiers][5];           // persistent grid per tier and pass (conv_xy, conv_z ideal, conv_z physics, redist_xy, redist_z)
+    int pocc[kTiers][5];            // resident CTAs per SM of those kernels (the grids' upper bound)
+    int slab;                       // planes per slab item of p_redist_xy (kSlab unless autotuned)
     // field pass: boxes overlapping each domain tile of kTileX x kTileY x kTileZ cells
     int* tile_cnt;                  // [n_tiles]
     int* tile_list;                 // [n_tiles * kTileCap]
@@ -258,6 +269,10 @@ cudaError_t launch_bin(const StepBuffers& B, cudaStream_t s);
 // LSGG_REDIST_HARTMANN: the constrained reinitialization's pseudo-time steps.
 cudaError_t launch_sweep_redist(const StepBuffers& B, const DebugOut& dbg, cudaStream_t s);
 cudaError_t launch_field(const StepBuffers& B, const PhysicsDev& phys, const DebugOut& dbg, cudaStream_t s);
+// Anisotropy map (gbmap.cu): the step's map into B.gb_map, and the scratch its
+// kernel needs for `grid` CTAs.
+cudaError_t launch_gb_map_step(const StepBuffers& B, cudaStream_t s);
+size_t gb_map_scratch_bytes(int grid, int cap_cubes, int cap_tris);
 constexpr int kPassEvents = 6 * kTiers + 4;
 // Error tracing (LSGG_TRACE_ERRORS in the environment): `traced` prints a
 // failing call's message and `what` on stderr and returns the error.

@@ -430,6 +430,7 @@ p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
                         phi0[u] = ld_state(B, o);
                         jn[u] = B.IDF[o];
                     }
+                    if (phys.pair_map && zo >= 0 && zo < nz) jn[u] = phys.pair_map[nb.off + (long long)zo * ps + c];
                 }
             }
 #pragma unroll
@@ -856,7 +857,7 @@ p_redist_xy(StepBuffers B, int tier) {
         const int ps = plane_stride(nx, ny);
         const int n = nx * ny;
         const float* zb = B.Z + nb.off;
-        const int z1 = min(z0 + kSlab, nz);
+        const int z1 = min(z0 + B.slab, nz);
         if (max(nx, ny) > SIDE) {                           // not this tier's box: refuse, never overrun
             if (t == 0) { atomicExch(&B.st->status, LSGG_ERR_UNSUPPORTED); atomicExch(&B.st->halt, 1); }
             return;                                         // no copy is in flight between items
@@ -1706,7 +1707,10 @@ cudaError_t configure_passes(StepBuffers& B) {
                                                               redist_smem_bytes(kTierSide[t]));
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[4], p_redist_z, kColThreads, 0);
         if (e != cudaSuccess) return e;
-        for (int k = 0; k < 5; ++k) B.pgrid[t][k] = B.n_sm * (o[k] < 1 ? 1 : o[k]);
+        for (int k = 0; k < 5; ++k) {
+            B.pocc[t][k] = o[k] < 1 ? 1 : o[k];
+            B.pgrid[t][k] = B.n_sm * B.pocc[t][k];
+        }
     }
     int of = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field<false, false>, kTileX * kTileY, 0);
@@ -1716,6 +1720,7 @@ cudaError_t configure_passes(StepBuffers& B) {
     if (e != cudaSuccess) return e;
     B.field_grid[1] = B.n_sm * (of < 1 ? 1 : of);
     B.bin_grid = B.n_sm;
+    if (B.slab < kMinSlab) B.slab = kSlab;
     const int tsz[3] = {kTileX, kTileY, kTileZ};
     const int dn[3] = {B.dom.nx, B.dom.ny, B.dom.nz};
     for (int a = 0; a < 3; ++a) B.ntile[a] = (dn[a] + tsz[a] - 1) / tsz[a];

@@ -582,7 +582,7 @@ k_box_update(StepBuffers B, int layout_only, int count_step) {
                 const int t = pass_tier(B, c);
                 cnt[kNumClasses + t] += cb.nz;
                 cnt[kNumClasses + kTiers + t] += (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
-                cnt[kNumClasses + 2 * kTiers + t] += (cb.nz + kSlab - 1) / kSlab;
+                cnt[kNumClasses + 2 * kTiers + t] += (cb.nz + B.slab - 1) / B.slab;
                 tcell[t] += vol;
             }
             cells += vol;
@@ -619,7 +619,7 @@ k_box_update(StepBuffers B, int layout_only, int count_step) {
         const int nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
         const int p0 = tier_base[0][t] + pre[kNumClasses + t];
         const int c0 = tier_base[1][t] + pre[kNumClasses + kTiers + t];
-        const int nsl = (cb.nz + kSlab - 1) / kSlab;
+        const int nsl = (cb.nz + B.slab - 1) / B.slab;
         const int s0 = tier_base[2][t] + pre[kNumClasses + 2 * kTiers + t];
         pre[kNumClasses + t] += cb.nz;
         pre[kNumClasses + kTiers + t] += nch;
@@ -781,10 +781,10 @@ k_write_items(StepBuffers B) {
         if (base.w < 0) continue;
         const Box cb = B.cur[b];
         const int nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
-        const int nsl = (cb.nz + kSlab - 1) / kSlab;
+        const int nsl = (cb.nz + B.slab - 1) / B.slab;
         for (int z = lane; z < cb.nz; z += 32) B.plane_items[base.x + z] = make_int2(b, z);
         for (int k = lane; k < nch; k += 32) B.chunk_items[base.y + k] = make_int2(b, k);
-        for (int k = lane; k < nsl; k += 32) B.slab_items[base.z + k] = make_int2(b, k * kSlab);
+        for (int k = lane; k < nsl; k += 32) B.slab_items[base.z + k] = make_int2(b, k * B.slab);
     }
 }
 
@@ -827,6 +827,10 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
     if (dbg) d = *dbg;
     if (phys.kind == LSGG_PHYSICS_READ_SHOCKLEY) {
         e = traced(launch_collect_neighbours(B, phys, s), "neighbour tables");
+        if (e != cudaSuccess) return e;
+    }
+    if (phys.pair_map) {                // Eq. (10)'s pairs from the closest boundary point (Sec. 2.1.4)
+        e = traced(launch_gb_map_step(B, s), "anisotropy map");
         if (e != cudaSuccess) return e;
     }
     // Each phase forks the box-streaming size classes off the step's stream

@@ -53,6 +53,7 @@ class Config(C.Structure):
         ("field_dir", C.c_double * 3),
         ("energy_scale", C.c_double),
         ("arena_slack", C.c_double),
+        ("gb_map_tube", C.c_double),
         ("seeds", _dp), ("weights", _dp), ("quats", _dp), ("energy", _dp),
     ]
 
@@ -125,9 +126,11 @@ _SIGS = {
     "lsgg_server_destroy": (C.c_int, [C.c_void_p]),
     "lsgg_grain_neighbours": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32]),
     "lsgg_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_int32)]),
+    "lsgg_pass_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lsgg_debug_set_capacity": (C.c_int, [C.c_void_p, C.c_int64]),
     "lsgg_debug_wait_timeout": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "lsgg_debug_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lsgg_debug_pair_ids": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int64]),
     "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
     "lsgg_pass_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
@@ -286,6 +289,15 @@ def autotune(ctx, steps_per_trial: int = 2, dt: float = 1.0) -> dict:
     return {"k_predict": chosen[0:5].tolist(), "k_correct": chosen[5:10].tolist()}
 
 
+def pass_tuning(ctx) -> dict:
+    """The pass path's tuning: CTAs per SM per tier and pass, and the slab depth."""
+    ctas = np.zeros(4 * PASS_TIERS, np.int32)
+    slab = C.c_int32()
+    _check("pass_tuning", lib().lsgg_pass_tuning(ctx, _ptr(ctas, C.c_int32), C.byref(slab)))
+    return {f"{PASS_NAMES[k]}[tier{t}]": int(ctas[t * 4 + k]) for t in range(PASS_TIERS) for k in range(4)} | {
+        "slab": int(slab.value)}
+
+
 def debug_set_capacity(ctx, capacity: int):
     _check("debug_set_capacity", lib().lsgg_debug_set_capacity(ctx, int(capacity)))
 
@@ -294,6 +306,16 @@ def debug_wait_timeout(device: int, iterations: int) -> bool:
     out = C.c_int32(-1)
     _check("debug_wait_timeout", lib().lsgg_debug_wait_timeout(device, iterations, C.byref(out)))
     return out.value == 1
+
+
+def debug_pair_ids(ctx, boxes: np.ndarray):
+    """Test hook: (ID-field, anisotropy map) per grain on the current boxes, as
+    dicts of box-shaped int32 arrays (see lsgg.h)."""
+    n = packed_size(boxes)
+    idf = np.zeros(max(n, 1), np.int32)
+    mp = np.zeros(max(n, 1), np.int32)
+    _check("debug_pair_ids", lib().lsgg_debug_pair_ids(ctx, _ptr(idf, C.c_int32), _ptr(mp, C.c_int32), n))
+    return unpack(boxes, idf), unpack(boxes, mp)
 
 
 def debug_set_wait_limit(ctx, polls: int):

@@ -47,7 +47,7 @@ def test_config_layout_and_defaults():
     assert L.lib().lsgg_abi_config_size() == ctypes.sizeof(L.Config)
     cfg = L.config_default()
     assert (cfg.nx, cfg.ny, cfg.nz, cfg.n_grains, cfg.halo, cfg.radius) == (64, 64, 64, 50, 5, 5)
-    assert cfg.eps == 7.0 and cfg.arena_slack == 1.5
+    assert cfg.eps == 7.0 and cfg.arena_slack == 1.5 and cfg.gb_map_tube == 0.0
 
 
 @pytest.mark.parametrize("seed,n,shape", [(1, 50, (64, 64, 64)), (2, 5000, (256, 256, 256)),
@@ -142,6 +142,28 @@ def test_sweep_reinitialisations_only_on_the_batched_3d_path(case):
         cfg.nz = 1
     else:
         cfg.redist = 3
+    ctx = ctypes.c_void_p()
+    code = L.lib().lsgg_create_microstructure(ctypes.byref(cfg), None, ctypes.byref(ctx))
+    assert code in (L.ERR_INVALID_ARG, L.ERR_UNSUPPORTED)
+
+
+@pytest.mark.parametrize("case", ["ideal", "wide", "negative", "streamed"])
+def test_anisotropy_map_configuration_is_checked(case):
+    """The in-step anisotropy map needs physics that reads pairs, a tube
+    inside the band and the batched path; anything else is refused before any
+    device work."""
+    L = _lib()
+    cfg = L.config_default()
+    cfg.physics = L.PHYSICS_READ_SHOCKLEY
+    cfg.gb_map_tube = 3.0
+    if case == "ideal":
+        cfg.physics = L.PHYSICS_IDEAL
+    elif case == "wide":
+        cfg.gb_map_tube = 7.0
+    elif case == "negative":
+        cfg.gb_map_tube = -1.0
+    else:
+        cfg.exec = L.EXEC_STREAMED
     ctx = ctypes.c_void_p()
     code = L.lib().lsgg_create_microstructure(ctypes.byref(cfg), None, ctypes.byref(ctx))
     assert code in (L.ERR_INVALID_ARG, L.ERR_UNSUPPORTED)

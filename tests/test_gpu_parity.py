@@ -497,3 +497,28 @@ def test_hartmann_multistep_volumes(L, storage):
     tol = 1e-3 if storage == "fp32" else 5e-3
     assert np.max(np.abs(vol[alive] - want[alive]) / want[alive]) < tol
     assert (own >= 0).all()
+
+
+def test_pass_path_autotune_keeps_results_bitwise(L):
+    """The pass path's autotuner (grid sizes per tier and pass, slab depth)
+    runs 4 x 2 real steps under different settings; the result equals an
+    untuned run of 8 steps bit for bit, and the chosen settings are within
+    their ranges."""
+    N, G = 64, 50
+    seeds = I.voronoi_seeds(24, G, (N, N, N))
+    with L.Microstructure(N, N, N, G, seeds=seeds) as a:
+        a.step(8, 1.0)
+        a.sync()
+        pa, ba = L.get_phi(a.ctx), a.boxes()
+    with L.Microstructure(N, N, N, G, seeds=seeds) as b:
+        chosen = L.autotune(b.ctx, 2, 1.0)
+        assert b.stats().steps_done == 8
+        assert all(v == -1 for v in chosen["k_predict"])
+        tune = L.pass_tuning(b.ctx)
+        pb, bb = L.get_phi(b.ctx), b.boxes()
+        b.step(2, 1.0)                        # the tuned settings step on
+        b.sync()
+    assert np.array_equal(ba, bb)
+    assert np.array_equal(pa, pb)
+    assert tune["slab"] in (4, 8, 16)
+    assert all(1 <= v <= 32 for k, v in tune.items() if k != "slab")

@@ -1198,3 +1198,27 @@ def test_hartmann_without_a_zero_level_keeps_the_clamp(oracle):
     -eps function stays as it is."""
     neg = np.full((8, 9, 10), -7.0)
     assert np.array_equal(oracle.redistance_hartmann(neg, (False,) * 3, 7.0, (0, 1, 2)), neg)
+
+
+def test_point_triangle_distances_equal_the_single_point_form(oracle):
+    """The block form of the point-triangle distance (used by the map over many
+    cells) equals the single-point form row by row, bit for bit, on random
+    points and triangles, degenerate ones included; and the map's blocked
+    search equals a cell-by-cell search on a tessellation box."""
+    rng = np.random.default_rng(3)
+    tris = rng.uniform(-2, 2, (60, 3, 3))
+    tris[5, 2] = tris[5, 1]                           # a segment
+    tris[6, 1] = tris[6, 0]
+    tris[6, 2] = tris[6, 0]                           # a point
+    tris[7, 2] = tris[7, 0] + 2.0 * (tris[7, 1] - tris[7, 0])   # collinear
+    pts = rng.uniform(-3, 3, (40, 3))
+    block = oracle.point_triangle_distances(pts, tris)
+    for k, p in enumerate(pts):
+        assert np.array_equal(block[k], oracle.point_triangle_distance(p, tris))
+    seeds = I.voronoi_seeds(4, 6, (14, 14, 14))
+    ms = oracle.tessellate((14, 14, 14), seeds, with_idf=True)
+    g = ms.grains[0]
+    tr, gr = oracle.gb_triangles(g.phi, g.idf)
+    fast = oracle.closest_gb_grains(g.phi, g.idf, 2.5, block=7)
+    for z, y, x in np.argwhere(np.abs(g.phi) < 2.5):
+        assert fast[z, y, x] == oracle.closest_gb_grain_at((z, y, x), tr, gr)
