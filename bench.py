@@ -767,6 +767,30 @@ def serving_run(L, I, n_requests, device):
     return out
 
 
+def profile_step(args):
+    """The profilers' case: create the workload, run the warm-up steps, print
+    the box cells each tier's passes will process in the next step (one JSON
+    line), run that one step and stop.  An ncu capture of the kernels of the
+    last step (-s = warm-up launches) then has exact units for its bytes."""
+    import torch
+    from paper_1701_06658_gb300 import inputs as I
+    from paper_1701_06658_gb300 import lsgg as L
+    L.lib()
+    n, g, dt = WORKLOAD["n"], WORKLOAD["grains"], WORKLOAD["dt"]
+    seeds = I.voronoi_seeds(WORKLOAD["seed"], g, (n, n, n))
+    with L.Microstructure(n, n, n, g, seeds=seeds, **workload_kwargs(L)) as ms:
+        ms.step(args.warmup, dt)
+        ms.sync()
+        st = ms.stats()
+        print(json.dumps({"workload": workload_config()["workload"], "warmup_steps": args.warmup,
+                          "pass_cells_per_tier": list(st.pass_cells), "box_cells": st.box_cells,
+                          "domain_cells": n ** 3}), flush=True)
+        ms.step(1, dt)
+        ms.sync()
+        torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -784,6 +808,8 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 512^3 Read-Shockley (FP32, BF16) and 384^3 magnetic blocks")
     ap.add_argument("--config-steps", type=int, default=8, help="timed steps of each of those blocks")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profilers' case: warm-up steps, the next step's tier cells as JSON, one step")
     ap.add_argument("--redist", default="taxicab", choices=["taxicab", "godunov"],
                     help="re-initialisation metric: the paper's taxicab propagation or the Godunov update")
     ap.add_argument("--workload", default="256", choices=sorted(WORKLOADS),
@@ -797,6 +823,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_step:
+        return profile_step(args)
     return gpu_arm(args)
 
 
