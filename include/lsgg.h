@@ -145,6 +145,39 @@ int lsgg_step(lsgg_ctx* ctx, int32_t n, double dt);
  * (lsgg_get_stats' steps_done counts the completed ones). */
 int lsgg_sync(lsgg_ctx* ctx, int64_t timeout_ms);
 
+/* ------------------------------------------------------------ step groups
+ * Several microstructures advanced by one set of launches per step
+ * (Algorithm 1's loop body over the boxes of every member at once, Sec. 3.1's
+ * per-grain work spread over all of them): each pass kernel walks the
+ * concatenation of the members' work items, so that many small simulations
+ * share the GPU's SMs instead of each occupying it with its own launches.
+ * Each member keeps its own domain, grains, arenas and field; the results of a
+ * member are bit for bit those of stepping it alone with lsgg_step.
+ *
+ * lsgg_group_create: members = n (1 <= n <= LSGG_MAX_GROUP) contexts created on
+ * the same device with exec LSGG_EXEC_BATCHED, a 3D domain, physics
+ * LSGG_PHYSICS_IDEAL, redist LSGG_REDIST_TAXICAB, radius 5, no anisotropy map
+ * and kernel timing off; anything else is LSGG_ERR_UNSUPPORTED, a NULL or
+ * repeated member LSGG_ERR_INVALID_ARG.  The group holds the pointers, not
+ * the contexts: destroy the group before any of its members.  The call
+ * allocates the group's device array and streams; *out owns them. */
+#define LSGG_MAX_GROUP 64
+typedef struct lsgg_group lsgg_group;
+int lsgg_group_create(lsgg_ctx* const* members, int32_t n, lsgg_group** out);
+
+/* n steps with time dt of every member, enqueued on the group's stream after
+ * the work already enqueued on each member's stream; each member's stream
+ * then waits for them, so that its later calls (lsgg_sync, outputs) see the
+ * steps.  step_limits (optional, n_members entries): member k takes part only
+ * while its completed steps are below step_limits[k] (an absolute count since
+ * its creation), so members needing different step counts share the chunk.
+ * A member whose box arena runs out of room halts; lsgg_sync on it grows the
+ * arena and finishes its steps alone.  Returns after enqueue. */
+int lsgg_group_step(lsgg_group* g, int32_t n, double dt, const int64_t* step_limits);
+
+/* Waits for the group's work and frees the group (not its members). */
+int lsgg_group_destroy(lsgg_group* g);
+
 /* Per-grain volume V_i = sum_x H(phi_i(x)), H(phi) = clamp(phi + 1/2, 0, 1).
  * The paper does not define a grain's volume; this is a smooth cell count:
  * the zero level of phi_i smeared over one cell, so that it moves

@@ -5,6 +5,7 @@
 // outputs.cu and plain.cu.
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -768,6 +769,163 @@ int lsgg_sync(lsgg_ctx* c, int64_t timeout_ms) {
         }
     }
     return LSGG_ERR_OUT_OF_MEMORY;
+}
+
+}  // extern "C"
+
+static_assert(LSGG_MAX_GROUP == kMaxGroup, "group size of the library and of the ABI");
+
+struct lsgg_group {
+    std::vector<lsgg_ctx*> m;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    StepStreams ss{};
+    bool have_ss = false;
+    StepBuffers* d_B = nullptr;          // members' StepBuffers (device copy)
+    long long* d_lim = nullptr;          // members' step limits
+    std::vector<unsigned char> h_B;      // the members' StepBuffers bytes last sent
+    std::vector<long long> h_lim;
+    cudaEvent_t done = nullptr;          // after the group's latest steps
+    std::vector<cudaEvent_t> ready;      // per member: after its enqueued work
+    cudaGraphExec_t graph = nullptr;
+    double graph_dt = -1.0;
+};
+
+namespace {
+
+void group_free(lsgg_group* g) {
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    if (g->have_ss) {
+        for (int k = 0; k < kNumClasses; ++k) {
+            cudaStreamDestroy(g->ss.side[k]);
+            cudaEventDestroy(g->ss.join[k]);
+        }
+        cudaEventDestroy(g->ss.fork);
+    }
+    for (cudaEvent_t e : g->ready) cudaEventDestroy(e);
+    if (g->done) cudaEventDestroy(g->done);
+    if (g->d_B) cudaFree(g->d_B);
+    if (g->d_lim) cudaFree(g->d_lim);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+// One group step captured as a graph on the group's stream (the kernels read
+// the members' buffers from the device array, so the graph stays valid while
+// only their contents change).
+int group_graph(lsgg_group* g, double dt) {
+    if (g->graph && g->graph_dt == dt) return LSGG_OK;
+    if (g->graph) { cudaGraphExecDestroy(g->graph); g->graph = nullptr; }
+    const Taps taps = make_taps(dt, kGroupRadius);
+    const GroupRef grp{g->d_B, (int)g->m.size()};
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_group_step(g->m[0]->B, grp, taps, g->stream, &g->ss);
+    cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail_cuda(e != cudaSuccess ? e : e2);
+    }
+    e = cudaGraphInstantiate(&g->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { g->graph = nullptr; return fail_cuda(e); }
+    g->graph_dt = dt;
+    return LSGG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lsgg_group_create(lsgg_ctx* const* members, int32_t n, lsgg_group** out) {
+    if (!members || !out || n < 1 || n > kMaxGroup) return LSGG_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        lsgg_ctx* c = members[k];
+        if (!c) return LSGG_ERR_INVALID_ARG;
+        for (int j = 0; j < k; ++j)
+            if (members[j] == c) return LSGG_ERR_INVALID_ARG;
+        if (c->device != members[0]->device || !c->B.use_passes || c->dom.dim != 3 ||
+            c->cfg.physics != LSGG_PHYSICS_IDEAL || c->B.redist != LSGG_REDIST_TAXICAB ||
+            c->dom.radius != kGroupRadius || c->B.gb_map || c->profiling)
+            return LSGG_ERR_UNSUPPORTED;
+    }
+    lsgg_group* g = new (std::nothrow) lsgg_group();
+    if (!g) return LSGG_ERR_OUT_OF_MEMORY;
+    g->m.assign(members, members + n);
+    g->device = members[0]->device;
+    auto bail = [&](int code) { group_free(g); return code; };
+    if (cudaSetDevice(g->device) != cudaSuccess) return bail(CUDA_FAIL());
+    if (configure_group_kernels() != cudaSuccess) return bail(CUDA_FAIL());
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(CUDA_FAIL());
+    bool ok = cudaEventCreateWithFlags(&g->ss.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kNumClasses && ok; ++k)
+        ok = cudaStreamCreateWithFlags(&g->ss.side[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&g->ss.join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return bail(CUDA_FAIL());
+    g->have_ss = true;
+    if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) return bail(CUDA_FAIL());
+    g->ready.resize(n, nullptr);
+    for (int k = 0; k < n; ++k)
+        if (cudaEventCreateWithFlags(&g->ready[k], cudaEventDisableTiming) != cudaSuccess) return bail(CUDA_FAIL());
+    if (cudaMalloc(&g->d_B, sizeof(StepBuffers) * n) != cudaSuccess ||
+        cudaMalloc(&g->d_lim, sizeof(long long) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(LSGG_ERR_OUT_OF_MEMORY);
+    }
+    *out = g;
+    return LSGG_OK;
+}
+
+int lsgg_group_step(lsgg_group* g, int32_t n, double dt, const int64_t* step_limits) {
+    if (!g || n < 0 || !(dt > 0.0) || dt > 4.0) return LSGG_ERR_INVALID_ARG;
+    if (n == 0) return LSGG_OK;
+    if (cudaSetDevice(g->device) != cudaSuccess) return CUDA_FAIL();
+    const int nm = (int)g->m.size();
+    // the members' buffers as they are now (an arena may have grown since),
+    // compared byte for byte with the copy on the device
+    std::vector<unsigned char> now(sizeof(StepBuffers) * nm);
+    for (int k = 0; k < nm; ++k) std::memcpy(now.data() + sizeof(StepBuffers) * k, &g->m[k]->B, sizeof(StepBuffers));
+    const bool fresh = now != g->h_B;
+    std::vector<long long> lim(nm);
+    for (int k = 0; k < nm; ++k) lim[k] = step_limits ? (long long)step_limits[k] : LLONG_MAX;
+    // every member's enqueued work first
+    for (int k = 0; k < nm; ++k) {
+        CK(cudaEventRecord(g->ready[k], g->m[k]->stream));
+        CK(cudaStreamWaitEvent(g->stream, g->ready[k], 0));
+    }
+    if (fresh) {
+        g->h_B.swap(now);
+        CK(cudaMemcpyAsync(g->d_B, g->h_B.data(), sizeof(StepBuffers) * nm, cudaMemcpyHostToDevice, g->stream));
+        if (g->graph) { cudaGraphExecDestroy(g->graph); g->graph = nullptr; }   // launch shapes may differ
+    }
+    if (lim != g->h_lim) {
+        g->h_lim = lim;
+        CK(cudaMemcpyAsync(g->d_lim, g->h_lim.data(), sizeof(long long) * nm, cudaMemcpyHostToDevice, g->stream));
+    }
+    CK(launch_group_limits(GroupRef{g->d_B, nm}, g->d_lim, g->stream));
+    int r = group_graph(g, dt);
+    if (r != LSGG_OK) return r;
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(g->graph, g->stream));
+    CK(cudaEventRecord(g->done, g->stream));
+    for (int k = 0; k < nm; ++k) {
+        lsgg_ctx* c = g->m[k];
+        CK(cudaStreamWaitEvent(c->stream, g->done, 0));
+        long long target = c->steps_target + n;
+        if (step_limits) target = std::min(target, std::max(c->steps_target, (long long)step_limits[k]));
+        c->steps_target = target;
+        c->last_dt = dt;
+        c->field_valid = true;
+    }
+    return LSGG_OK;
+}
+
+int lsgg_group_destroy(lsgg_group* g) {
+    if (!g) return LSGG_ERR_INVALID_ARG;
+    cudaSetDevice(g->device);
+    group_free(g);
+    return LSGG_OK;
 }
 
 int lsgg_get_stats(lsgg_ctx* c, lsgg_stats* out) {

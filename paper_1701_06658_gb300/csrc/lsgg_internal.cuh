@@ -113,6 +113,7 @@ struct StepState {                  // device-resident control block
     long long tier_cells[kTiers];   // box cells per tier in `cur`
     int n_slabs[kTiers];            // pass path: slab items (kSlab planes) per tier
     int slab_base[kTiers];
+    long long step_limit;           // step groups: the member takes part while steps_done < step_limit
 };
 
 __host__ __device__ inline int plane_stride(int nx, int ny) { return (nx * ny + 7) & ~7; }
@@ -202,6 +203,17 @@ struct StepBuffers {
     int field_grid[2], bin_grid;      // field grid: plain / ID-field and debug variants
 };
 
+// A step group: the StepBuffers of several contexts (one GPU, the pass path,
+// ideal growth, taxicab re-initialisation), whose steps run as one set of
+// launches.  Each work item finds its context through a per-CTA prefix of the
+// members' item counts; a member takes part while it is not halted and its
+// steps_done is below its step_limit.
+constexpr int kMaxGroup = 64;
+struct GroupRef {
+    const StepBuffers* B;           // device array of n members
+    int n;
+};
+
 // Element i of the state arena X as FP32, and its store (round to nearest
 // even when the arena holds BF16).
 __device__ __forceinline__ float ld_state(const StepBuffers& B, long long i) {
@@ -265,6 +277,19 @@ cudaError_t launch_f32_to_state(const float* in, void* bf16_out, long long n, cu
 cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps& taps, const PhysicsDev& phys,
                           const DebugOut& dbg, cudaStream_t s, cudaEvent_t* pass_ev);
 cudaError_t launch_bin(const StepBuffers& B, cudaStream_t s);
+// Step groups (radius 5 only): the pass kernels of one tier / the binning /
+// the field pass over every member of `grp`; B0 (a member) gives the launch
+// shapes.  launch_group_step enqueues a whole step.
+constexpr int kGroupRadius = 5;
+cudaError_t configure_group_kernels();   // shared-memory limits of the group kernels (host, once per process)
+cudaError_t launch_passes_group(const StepBuffers& B0, const GroupRef& grp, int which, int tier, const Taps& taps,
+                                cudaStream_t s);
+cudaError_t launch_bin_group(const StepBuffers& B0, const GroupRef& grp, cudaStream_t s);
+cudaError_t launch_field_group(const StepBuffers& B0, const GroupRef& grp, cudaStream_t s);
+cudaError_t launch_group_step(const StepBuffers& B0, const GroupRef& grp, const Taps& taps, cudaStream_t s,
+                              const StepStreams* ss);
+// member k's step limit := lim[k] (device array of grp.n entries)
+cudaError_t launch_group_limits(const GroupRef& grp, const long long* lim, cudaStream_t s);
 // LSGG_REDIST_GODUNOV: classification, Jacobi sweeps and signs over all boxes;
 // LSGG_REDIST_HARTMANN: the constrained reinitialization's pseudo-time steps.
 cudaError_t launch_sweep_redist(const StepBuffers& B, const DebugOut& dbg, cudaStream_t s);

@@ -35,6 +35,7 @@
 #include <climits>
 
 #include "bulk_copy.cuh"
+#include "group.cuh"
 #include "kernels_common.cuh"
 
 namespace lsgg {
@@ -44,6 +45,21 @@ constexpr int kReachP = kRedistReach;
 constexpr int kColThreads = kPassChunk;
 
 __device__ __forceinline__ bool halted(const StepBuffers& B) { return *(volatile int*)&B.st->halt != 0; }
+
+// A launch that cannot run records LSGG_ERR_UNSUPPORTED and halts its
+// context, or every member of its group.
+template <bool GRP>
+__device__ __forceinline__ void refuse_launch(const StepBuffers& B1, const GroupRef& g) {
+    if constexpr (GRP) {
+        for (int k = 0; k < g.n; ++k) {
+            atomicExch(&g.B[k].st->status, LSGG_ERR_UNSUPPORTED);
+            atomicExch(&g.B[k].st->halt, 1);
+        }
+    } else {
+        atomicExch(&B1.st->status, LSGG_ERR_UNSUPPORTED);
+        atomicExch(&B1.st->halt, 1);
+    }
+}
 
 // xy convolution of a plane that is -eps everywhere (the W-tap FMA chains of p_conv_xy)
 template <int R>
@@ -153,9 +169,9 @@ __device__ __forceinline__ void conv_source(const StepBuffers& B, int2 it, const
     *bytes = ozl < ob.nz ? (uint32_t)(ps * state_bytes(B)) : 0u;
 }
 
-template <int R, int SIDE, int NT>
+template <int R, int SIDE, int NT, bool GRP>
 __global__ void __launch_bounds__(NT)
-p_conv_xy(StepBuffers B, Taps taps, int tier) {
+p_conv_xy(StepBuffers B1, GroupRef grp, Taps taps, int tier) {
     constexpr int W = 2 * R + 1;
     using LY = ConvXYLayout<R, SIDE>;
     extern __shared__ __align__(128) unsigned char smc[];   // ConvXYLayout::bytes
@@ -166,6 +182,7 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
     int* const mapx = reinterpret_cast<int*>(smc + LY::maps);
     int* const mapy = mapx + LY::MX;
     __shared__ int s_flag;
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
     const int t = threadIdx.x;
     if (t == 0) {
         const bool fits = dyn_smem_bytes() >= LY::bytes;
@@ -173,26 +190,27 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
             mbar_init(bar, 1);
             fence_mbar_init();
         } else {
-            atomicExch(&B.st->status, LSGG_ERR_UNSUPPORTED);
-            atomicExch(&B.st->halt, 1);
+            refuse_launch<GRP>(B1, grp);
         }
-        s_flag = !fits || halted(B);
+        s_flag = !fits || (!GRP && halted(B1));
     }
     __syncthreads();
     if (s_flag) return;
-    const Domain D = B.dom;
+    const Domain D1 = B1.dom;
     float g[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) g[k] = taps.g[k];
-    const int n_items = B.st->n_planes[tier];
-    const int2* items = B.plane_items + B.st->plane_base[tier];
+    const int n_items = GRP ? group_scan(grp, kItemPlanes, tier, true, s_gb) : B1.st->n_planes[tier];
+    const int2* items = GRP ? nullptr : B1.plane_items + B1.st->plane_base[tier];
     uint32_t phase = 0;
     // the first item's plane
     bool pending = false;
     if (blockIdx.x < n_items) {
         const float* src;
         uint32_t bytes;
-        conv_source(B, items[blockIdx.x], &src, &bytes);
+        int lf;
+        const StepBuffers& Bf = member<GRP>(B1, grp, s_gb, blockIdx.x, lf);
+        conv_source(Bf, list_item<GRP>(Bf, items, kItemPlanes, tier, blockIdx.x, lf), &src, &bytes);
         if (bytes) {
             if (t == 0) {
                 mbar_expect(bar, bytes);
@@ -202,7 +220,10 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         }
     }
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int2 it = items[item];
+        int local;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, item, local);
+        const Domain D = GRP ? B.dom : D1;
+        const int2 it = list_item<GRP>(B, items, kItemPlanes, tier, item, local);
         const int b = it.x, z = it.y;
         const Box nb = B.cur[b], ob = B.prev[b];
         const int nx = nb.nx, ny = nb.ny;
@@ -253,7 +274,14 @@ p_conv_xy(StepBuffers B, Taps taps, int tier) {
         if (item + (int)gridDim.x < n_items) {
             const float* src;
             uint32_t bytes;
-            conv_source(B, items[item + gridDim.x], &src, &bytes);
+            if constexpr (GRP) {
+                const int nxt = item + gridDim.x;
+                int ln;
+                const StepBuffers& Bn = member<GRP>(B1, grp, s_gb, nxt, ln);
+                conv_source(Bn, list_item<GRP>(Bn, items, kItemPlanes, tier, nxt, ln), &src, &bytes);
+            } else {
+                conv_source(B1, items[item + gridDim.x], &src, &bytes);
+            }
             if (bytes) {
                 if (t == 0) {
                     fence_async_smem();
@@ -348,25 +376,30 @@ __device__ __forceinline__ void conv_column(const float* zc, float* yc, int nz, 
         }
 }
 
-template <int R, bool PHYS>
+template <int R, bool PHYS, bool GRP>
 __global__ void __launch_bounds__(kColThreads)
-p_conv_z(StepBuffers B, Taps taps, PhysicsDev phys, int tier) {
+p_conv_z(StepBuffers B1, GroupRef grp, Taps taps, PhysicsDev phys, int tier) {
+    static_assert(!(GRP && PHYS), "step groups run ideal growth");
     constexpr int W = 2 * R + 1;
     __shared__ int s_tj[PHYS ? kNbCap : 1];
     __shared__ float s_tw[PHYS ? kNbCap : 1], s_tm[PHYS ? kNbCap : 1];
-    if (halted(B)) return;
-    const Domain D = B.dom;
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
+    if (!GRP && halted(B1)) return;
     float g[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) g[k] = taps.g[k];
-    const float cconst = conv_xy_of_const<R>(g, -D.eps);
-    const int n_items = B.st->n_chunks[tier];
-    const int2* items = B.chunk_items + B.st->chunk_base[tier];
+    const float cconst1 = GRP ? 0.0f : conv_xy_of_const<R>(g, -B1.dom.eps);
+    const int n_items = GRP ? group_scan(grp, kItemChunks, tier, true, s_gb) : B1.st->n_chunks[tier];
+    const int2* items = GRP ? nullptr : B1.chunk_items + B1.st->chunk_base[tier];
     const bool rs = PHYS && phys.kind == LSGG_PHYSICS_READ_SHOCKLEY;
     int last_b = -1;
     PairTable tab{s_tj, s_tw, s_tm, 0};
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int2 it = items[item];
+        int local;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, item, local);
+        const Domain D = B.dom;
+        const float cconst = GRP ? conv_xy_of_const<R>(g, -D.eps) : cconst1;
+        const int2 it = list_item<GRP>(B, items, kItemChunks, tier, item, local);
         const int b = it.x;
         if (rs && b != last_b) {                           // uniform across the CTA
             __syncthreads();
@@ -468,13 +501,18 @@ __device__ __forceinline__ void axis_tiles(int o, int n, int N, int T, int nt, i
     tc = te >= ts ? te - ts + 1 : te + nt - ts + 1;
 }
 
+template <bool GRP>
 __global__ void __launch_bounds__(256)
-k_bin(StepBuffers B) {
-    if (halted(B)) return;
-    const Domain D = B.dom;
+k_bin(StepBuffers B1, GroupRef grp) {
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
+    if (!GRP && halted(B1)) return;
+    const int n_all = GRP ? group_scan(grp, kItemBoxes, 0, true, s_gb) : B1.n_boxes;
     const int lane = threadIdx.x & 31;
     const int warps = (blockDim.x >> 5) * gridDim.x;
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B.n_boxes; b += warps) {
+    for (int gb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gb < n_all; gb += warps) {
+        int b;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, gb, b);
+        const Domain D = B.dom;
         const Box bx = B.cur[b];
         if (bx.nx <= 0) continue;
         if (lane == 0) {
@@ -494,6 +532,19 @@ k_bin(StepBuffers B) {
             const int slot = atomicAdd(&B.tile_cnt[t], 1);
             if (slot < kTileCap) B.tile_list[(long long)t * kTileCap + slot] = b;
         }
+    }
+}
+
+// The tile counters of every live member cleared (the group's counterpart of
+// the single context's memset before k_bin).
+__global__ void __launch_bounds__(256)
+k_clear_tiles_group(GroupRef grp) {
+    __shared__ int s_gb[kMaxGroup + 1];
+    const int n_all = group_scan(grp, kItemTiles, 0, true, s_gb);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_all; i += gridDim.x * blockDim.x) {
+        int local;
+        const StepBuffers& B = member<true>(grp.B[0], grp, s_gb, i, local);
+        B.tile_cnt[local] = 0;
     }
 }
 
@@ -588,16 +639,21 @@ __device__ __forceinline__ void top2_insert(float v, int id, float& v1, int& i1,
 
 // Four CTAs per SM for the plain field; the ID-field and debug variants keep
 // the registers of three.
-template <bool IDF, bool DBG>
+template <bool IDF, bool DBG, bool GRP>
 __global__ void __launch_bounds__(kTileX * kTileY, (IDF || DBG) ? 3 : 4)
-p_field(StepBuffers B, PhysicsDev phys, DebugOut dbg) {
+p_field(StepBuffers B1, GroupRef grp, PhysicsDev phys, DebugOut dbg) {
+    static_assert(!(GRP && (IDF || DBG)), "step groups run ideal growth without intermediates");
     __shared__ TileBox s_tb[kTileCap];
-    if (halted(B)) return;
-    const Domain D = B.dom;
-    const float eps = D.eps;
-    const int ntx = B.ntile[0], nty = B.ntile[1];
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
+    if (!GRP && halted(B1)) return;
+    const int n_all = GRP ? group_scan(grp, kItemTiles, 0, true, s_gb) : B1.n_tiles;
     const int lx = threadIdx.x % kTileX, ly = threadIdx.x / kTileX;
-    for (int tile = blockIdx.x; tile < B.n_tiles; tile += gridDim.x) {
+    for (int gtile = blockIdx.x; gtile < n_all; gtile += gridDim.x) {
+        int tile;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, gtile, tile);
+        const Domain D = B.dom;
+        const float eps = D.eps;
+        const int ntx = B.ntile[0], nty = B.ntile[1];
         const int tx = tile % ntx, tyz = tile / ntx, ty = tyz % nty, tz = tyz / nty;
         const int tx0 = tx * kTileX, ty0 = ty * kTileY, z0 = tz * kTileZ;
         const int x = tx0 + lx, y = ty0 + ly;
@@ -805,9 +861,9 @@ __host__ __device__ constexpr size_t redist_layout_bytes(int side) {  // barrier
 // CTAs per SM the register budget is sized for (shared memory allows them)
 __host__ __device__ constexpr int redist_min_blocks(int side) { return side <= 32 ? 8 : side <= 40 ? 6 : side <= 48 ? 5 : 2; }
 
-template <int SIDE, int NT>
+template <int SIDE, int NT, bool GRP>
 __global__ void __launch_bounds__(NT, redist_min_blocks(SIDE))
-p_redist_xy(StepBuffers B, int tier) {
+p_redist_xy(StepBuffers B1, GroupRef grp, int tier) {
     constexpr int PA = SIDE * SIDE;                   // floats per plane slot
     constexpr int PG = SIDE + 1;                      // pitch of G
     constexpr int LANES = kRedistLanes;
@@ -825,6 +881,7 @@ p_redist_xy(StepBuffers B, int tier) {
     // per warp, the reference cells of its rows (row << 8 | x): 32 lanes x L cells
     unsigned short* const RL = reinterpret_cast<unsigned short*>(W + 3 * WS) + (threadIdx.x >> 5) * (32 * L);
     __shared__ int s_flag;
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
     const int t = threadIdx.x;
     if (t == 0) {
         const bool fits = dyn_smem_bytes() >= redist_layout_bytes(SIDE);
@@ -832,24 +889,25 @@ p_redist_xy(StepBuffers B, int tier) {
             for (int k = 0; k < 3; ++k) mbar_init(&bar[k], 1);
             fence_mbar_init();
         } else {
-            atomicExch(&B.st->status, LSGG_ERR_UNSUPPORTED);
-            atomicExch(&B.st->halt, 1);
+            refuse_launch<GRP>(B1, grp);
         }
-        s_flag = !fits || halted(B);
+        s_flag = !fits || (!GRP && halted(B1));
     }
     __syncthreads();
     if (s_flag) return;
-    const Domain D = B.dom;
-    const float eps = D.eps;
-    const float4 fill = make_float4(-eps, -eps, -eps, -eps);
     const int r = t / LANES, s = t % LANES;           // x phase: row r; y phase: column r
     const int x0 = s * L;                             // first cell of the segment
     uint32_t phase = 0;                               // bit k: parity of slot k's next completion
     uint32_t pending = 0;                             // bit k: a copy into slot k is in flight
-    const int n_items = B.st->n_slabs[tier];
-    const int2* items = B.slab_items + B.st->slab_base[tier];
+    const int n_items = GRP ? group_scan(grp, kItemSlabs, tier, true, s_gb) : B1.st->n_slabs[tier];
+    const int2* items = GRP ? nullptr : B1.slab_items + B1.st->slab_base[tier];
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int2 it = items[item];
+        int local;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, item, local);
+        const Domain D = B.dom;
+        const float eps = D.eps;
+        const float4 fill = make_float4(-eps, -eps, -eps, -eps);
+        const int2 it = list_item<GRP>(B, items, kItemSlabs, tier, item, local);
         const int b = it.x, z0 = it.y;
         const Box nb = B.cur[b];
         const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
@@ -1052,16 +1110,20 @@ __device__ __forceinline__ unsigned long long redist_column(const StepBuffers& B
     return pm;
 }
 
+template <bool GRP>
 __global__ void __launch_bounds__(kColThreads, 2)
-p_redist_z(StepBuffers B, DebugOut dbg, int tier) {
-    if (halted(B)) return;
-    const Domain D = B.dom;
-    const float eps = D.eps;
+p_redist_z(StepBuffers B1, GroupRef grp, DebugOut dbg, int tier) {
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
+    if (!GRP && halted(B1)) return;
     constexpr int ZR = kReachP + 1;
-    const int n_items = B.st->n_chunks[tier];
-    const int2* items = B.chunk_items + B.st->chunk_base[tier];
+    const int n_items = GRP ? group_scan(grp, kItemChunks, tier, true, s_gb) : B1.st->n_chunks[tier];
+    const int2* items = GRP ? nullptr : B1.chunk_items + B1.st->chunk_base[tier];
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int2 it = items[item];
+        int local;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, item, local);
+        const Domain D = B.dom;
+        const float eps = D.eps;
+        const int2 it = list_item<GRP>(B, items, kItemChunks, tier, item, local);
         const int b = it.x;
         const Box nb = B.cur[b];
         const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
@@ -1509,26 +1571,29 @@ __device__ __forceinline__ void scan_line_serial(float* L, int n, int st) {
     }
 }
 
-template <int R>
+template <int R, bool GRP>
 __global__ void __launch_bounds__(256)
-p_conv_xy_big(StepBuffers B, Taps taps, int tier) {
+p_conv_xy_big(StepBuffers B1, GroupRef grp, Taps taps, int tier) {
     constexpr int W = 2 * R + 1;
     __shared__ int s_flag;
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (t == 0) s_flag = halted(B);
+    if (t == 0) s_flag = !GRP && halted(B1);
     __syncthreads();
     if (s_flag) return;
-    const Domain D = B.dom;
     float g[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) g[k] = taps.g[k];
-    float aconst = 0.0f;                              // x convolution of a row of -eps
-#pragma unroll
-    for (int k = 0; k < W; ++k) aconst = fmaf(g[k], -D.eps, aconst);
-    const int n_items = B.st->n_planes[tier];
-    const int2* items = B.plane_items + B.st->plane_base[tier];
+    const int n_items = GRP ? group_scan(grp, kItemPlanes, tier, true, s_gb) : B1.st->n_planes[tier];
+    const int2* items = GRP ? nullptr : B1.plane_items + B1.st->plane_base[tier];
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int2 it = items[item];
+        int local;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, item, local);
+        const Domain D = B.dom;
+        float aconst = 0.0f;                              // x convolution of a row of -eps
+#pragma unroll
+        for (int k = 0; k < W; ++k) aconst = fmaf(g[k], -D.eps, aconst);
+        const int2 it = list_item<GRP>(B, items, kItemPlanes, tier, item, local);
         const int b = it.x, z = it.y;
         const Box nb = B.cur[b], ob = B.prev[b];
         const int nx = nb.nx, ny = nb.ny;
@@ -1580,19 +1645,24 @@ p_conv_xy_big(StepBuffers B, Taps taps, int tier) {
     }
 }
 
+template <bool GRP>
 __global__ void __launch_bounds__(256)
-p_redist_xy_big(StepBuffers B, int tier) {
+p_redist_xy_big(StepBuffers B1, GroupRef grp, int tier) {
     __shared__ int s_flag;
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (t == 0) s_flag = halted(B);
+    if (t == 0) s_flag = !GRP && halted(B1);
     __syncthreads();
     if (s_flag) return;
-    const Domain D = B.dom;
-    const float eps = D.eps;
-    const int n_items = B.st->n_planes[tier];
-    const int2* items = B.plane_items + B.st->plane_base[tier];
+    const Domain D1 = B1.dom;
+    const int n_items = GRP ? group_scan(grp, kItemPlanes, tier, true, s_gb) : B1.st->n_planes[tier];
+    const int2* items = GRP ? nullptr : B1.plane_items + B1.st->plane_base[tier];
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int2 it = items[item];
+        int local;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, item, local);
+        const Domain D = GRP ? B.dom : D1;
+        const float eps = D.eps;
+        const int2 it = list_item<GRP>(B, items, kItemPlanes, tier, item, local);
         const int b = it.x, z = it.y;
         const Box nb = B.cur[b];
         const int nx = nb.nx, ny = nb.ny, nz = nb.nz;
@@ -1656,21 +1726,23 @@ struct PassFns {
     const void* redist_xy[kTiers];
 };
 
-template <int R>
+template <int R, bool GRP = false>
 static PassFns pass_fns_r(bool phys) {
     static_assert(kTiers == 5, "one instantiation per tier side");
     PassFns f;
-    f.conv_xy[0] = reinterpret_cast<const void*>(p_conv_xy<R, 32, kConvThreads[0]>);
-    f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 40, kConvThreads[1]>);
-    f.conv_xy[2] = reinterpret_cast<const void*>(p_conv_xy<R, 48, kConvThreads[2]>);
-    f.conv_xy[3] = reinterpret_cast<const void*>(p_conv_xy<R, 64, kConvThreads[3]>);
-    f.conv_xy[4] = reinterpret_cast<const void*>(p_conv_xy_big<R>);
-    f.conv_z = phys ? reinterpret_cast<const void*>(p_conv_z<R, true>) : reinterpret_cast<const void*>(p_conv_z<R, false>);
-    f.redist_xy[0] = reinterpret_cast<const void*>(p_redist_xy<32, kRedistThreads[0]>);
-    f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<40, kRedistThreads[1]>);
-    f.redist_xy[2] = reinterpret_cast<const void*>(p_redist_xy<48, kRedistThreads[2]>);
-    f.redist_xy[3] = reinterpret_cast<const void*>(p_redist_xy<64, kRedistThreads[3]>);
-    f.redist_xy[4] = reinterpret_cast<const void*>(p_redist_xy_big);
+    f.conv_xy[0] = reinterpret_cast<const void*>(p_conv_xy<R, 32, kConvThreads[0], GRP>);
+    f.conv_xy[1] = reinterpret_cast<const void*>(p_conv_xy<R, 40, kConvThreads[1], GRP>);
+    f.conv_xy[2] = reinterpret_cast<const void*>(p_conv_xy<R, 48, kConvThreads[2], GRP>);
+    f.conv_xy[3] = reinterpret_cast<const void*>(p_conv_xy<R, 64, kConvThreads[3], GRP>);
+    f.conv_xy[4] = reinterpret_cast<const void*>(p_conv_xy_big<R, GRP>);
+    if constexpr (GRP) f.conv_z = reinterpret_cast<const void*>(p_conv_z<R, false, true>);
+    else f.conv_z = phys ? reinterpret_cast<const void*>(p_conv_z<R, true, false>)
+                         : reinterpret_cast<const void*>(p_conv_z<R, false, false>);
+    f.redist_xy[0] = reinterpret_cast<const void*>(p_redist_xy<32, kRedistThreads[0], GRP>);
+    f.redist_xy[1] = reinterpret_cast<const void*>(p_redist_xy<40, kRedistThreads[1], GRP>);
+    f.redist_xy[2] = reinterpret_cast<const void*>(p_redist_xy<48, kRedistThreads[2], GRP>);
+    f.redist_xy[3] = reinterpret_cast<const void*>(p_redist_xy<64, kRedistThreads[3], GRP>);
+    f.redist_xy[4] = reinterpret_cast<const void*>(p_redist_xy_big<GRP>);
     return f;
 }
 
@@ -1705,7 +1777,7 @@ cudaError_t configure_passes(StepBuffers& B) {
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], fn.redist_xy[t], kRedistThreads[t],
                                                               redist_smem_bytes(kTierSide[t]));
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[4], p_redist_z, kColThreads, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[4], p_redist_z<false>, kColThreads, 0);
         if (e != cudaSuccess) return e;
         for (int k = 0; k < 5; ++k) {
             B.pocc[t][k] = o[k] < 1 ? 1 : o[k];
@@ -1713,10 +1785,10 @@ cudaError_t configure_passes(StepBuffers& B) {
         }
     }
     int of = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field<false, false>, kTileX * kTileY, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field<false, false, false>, kTileX * kTileY, 0);
     if (e != cudaSuccess) return e;
     B.field_grid[0] = B.n_sm * (of < 1 ? 1 : of);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field<true, false>, kTileX * kTileY, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field<true, false, false>, kTileX * kTileY, 0);
     if (e != cudaSuccess) return e;
     B.field_grid[1] = B.n_sm * (of < 1 ? 1 : of);
     B.bin_grid = B.n_sm;
@@ -1742,25 +1814,26 @@ cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps&
     int tr = tier;
     int k = 0;
     cudaError_t e;
+    GroupRef none{nullptr, 0};
     if (pass_ev) cudaEventRecord(pass_ev[k++], s);
     if (which == 0) {
-        void* a0[] = {&bb, &tp, &tr};
+        void* a0[] = {&bb, &none, &tp, &tr};
         e = cudaLaunchKernel(fn.conv_xy[tier], dim3(g[0]), dim3(kConvThreads[tier]), a0,
                              conv_smem_bytes(kTierSide[tier], taps.radius), s);
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
-        void* a1[] = {&bb, &tp, &ph, &tr};
+        void* a1[] = {&bb, &none, &tp, &ph, &tr};
         e = cudaLaunchKernel(fn.conv_z, dim3(g[phys.kind != LSGG_PHYSICS_IDEAL ? 2 : 1]), dim3(kColThreads), a1, 0, s);
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
     } else {
-        void* a3[] = {&bb, &tr};
+        void* a3[] = {&bb, &none, &tr};
         e = cudaLaunchKernel(fn.redist_xy[tier], dim3(g[3]), dim3(kRedistThreads[tier]), a3,
                              redist_smem_bytes(kTierSide[tier]), s);
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
-        void* a4[] = {&bb, &db, &tr};
-        e = cudaLaunchKernel(reinterpret_cast<const void*>(p_redist_z), dim3(g[4]), dim3(kColThreads), a4, 0, s);
+        void* a4[] = {&bb, &none, &db, &tr};
+        e = cudaLaunchKernel(reinterpret_cast<const void*>(p_redist_z<false>), dim3(g[4]), dim3(kColThreads), a4, 0, s);
         if (e != cudaSuccess) return e;
         if (pass_ev) cudaEventRecord(pass_ev[k++], s);
     }
@@ -1770,14 +1843,72 @@ cudaError_t launch_passes(const StepBuffers& B, int which, int tier, const Taps&
 cudaError_t launch_bin(const StepBuffers& B, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(B.tile_cnt, 0, sizeof(int) * (size_t)B.n_tiles, s);
     if (e != cudaSuccess) return e;
-    k_bin<<<B.bin_grid, 256, 0, s>>>(B);
+    k_bin<false><<<B.bin_grid, 256, 0, s>>>(B, GroupRef{nullptr, 0});
     return cudaGetLastError();
 }
 
 cudaError_t launch_field(const StepBuffers& B, const PhysicsDev& phys, const DebugOut& dbg, cudaStream_t s) {
     const bool idf = phys.kind != LSGG_PHYSICS_IDEAL, dg = dbg.m != nullptr;
-    auto k = idf ? (dg ? p_field<true, true> : p_field<true, false>) : (dg ? p_field<false, true> : p_field<false, false>);
-    k<<<B.field_grid[idf || dg ? 1 : 0], kTileX * kTileY, 0, s>>>(B, phys, dbg);
+    auto k = idf ? (dg ? p_field<true, true, false> : p_field<true, false, false>)
+                 : (dg ? p_field<false, true, false> : p_field<false, false, false>);
+    k<<<B.field_grid[idf || dg ? 1 : 0], kTileX * kTileY, 0, s>>>(B, GroupRef{nullptr, 0}, phys, dbg);
+    return cudaGetLastError();
+}
+
+// ---- step groups ----
+// The group kernels are instantiated for radius kGroupRadius only; their
+// launch shapes are the member B0's (the same device: the same occupancy).
+cudaError_t launch_passes_group(const StepBuffers& B0, const GroupRef& grp, int which, int tier, const Taps& taps,
+                                cudaStream_t s) {
+    if (taps.radius != kGroupRadius) return cudaErrorInvalidValue;
+    const PassFns fn = pass_fns_r<kGroupRadius, true>(false);
+    const int* g = B0.pgrid[tier];
+    StepBuffers bb = B0;
+    GroupRef gr = grp;
+    Taps tp = taps;
+    PhysicsDev ph{};
+    DebugOut db{};
+    int tr = tier;
+    cudaError_t e;
+    if (which == 0) {
+        void* a0[] = {&bb, &gr, &tp, &tr};
+        e = cudaLaunchKernel(fn.conv_xy[tier], dim3(g[0]), dim3(kConvThreads[tier]), a0,
+                             conv_smem_bytes(kTierSide[tier], taps.radius), s);
+        if (e != cudaSuccess) return e;
+        void* a1[] = {&bb, &gr, &tp, &ph, &tr};
+        e = cudaLaunchKernel(fn.conv_z, dim3(g[1]), dim3(kColThreads), a1, 0, s);
+    } else {
+        void* a3[] = {&bb, &gr, &tr};
+        e = cudaLaunchKernel(fn.redist_xy[tier], dim3(g[3]), dim3(kRedistThreads[tier]), a3,
+                             redist_smem_bytes(kTierSide[tier]), s);
+        if (e != cudaSuccess) return e;
+        void* a4[] = {&bb, &gr, &db, &tr};
+        e = cudaLaunchKernel(reinterpret_cast<const void*>(p_redist_z<true>), dim3(g[4]), dim3(kColThreads), a4, 0, s);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t configure_group_kernels() {
+    const PassFns fn = pass_fns_r<kGroupRadius, true>(false);
+    for (int t = 0; t + 1 < kTiers; ++t) {
+        cudaError_t e = allow_max_dynamic_smem(fn.conv_xy[t]);
+        if (e == cudaSuccess) e = allow_max_dynamic_smem(fn.redist_xy[t]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_bin_group(const StepBuffers& B0, const GroupRef& grp, cudaStream_t s) {
+    k_clear_tiles_group<<<B0.n_sm, 256, 0, s>>>(grp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bin<true><<<B0.bin_grid, 256, 0, s>>>(B0, grp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_group(const StepBuffers& B0, const GroupRef& grp, cudaStream_t s) {
+    p_field<false, false, true><<<B0.field_grid[0], kTileX * kTileY, 0, s>>>(B0, grp, PhysicsDev{}, DebugOut{});
     return cudaGetLastError();
 }
 

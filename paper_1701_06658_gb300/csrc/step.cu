@@ -23,6 +23,7 @@
 #include <climits>
 
 #include "lsgg_internal.cuh"
+#include "group.cuh"
 #include "kernels_common.cuh"
 #include "../../include/lsgg.h"
 
@@ -499,12 +500,16 @@ __device__ __forceinline__ int pass_tier(const StepBuffers& B, int c) {
 // layout_only: offsets and work items for the `cur` boxes as they are;
 // otherwise the boxes follow the bounds collected by the re-initialisation,
 // and count_step adds the step to the step and cell-update counters (not for
-// the re-initialisation of a coarsening).
+// the re-initialisation of a coarsening).  In a step group, CTA k updates
+// member k (if it took part in the step).
+template <bool GRP>
 __global__ void __launch_bounds__(kBoxUpdateThreads)
-k_box_update(StepBuffers B, int layout_only, int count_step) {
+k_box_update(StepBuffers B1, GroupRef grp, int layout_only, int count_step) {
     static_assert(2 + kTiers <= 8 && kBoxUpdateThreads <= 1024, "the scratch holds 8 sums of 32 warps");
     __shared__ long long s_part[32 * 8];
     __shared__ int s_scan[(kBoxUpdateThreads / 32) * (kNumClasses + 3 * kTiers)];
+    const StepBuffers& B = GRP ? grp.B[blockIdx.x] : B1;
+    if (GRP && !group_live(B, true)) return;
     const int G = B.n_boxes;
     const Domain D = B.dom;
     if (*(volatile int*)&B.st->halt && !layout_only) return;
@@ -771,12 +776,19 @@ long long large_class_scratch_floats(const Domain& d) {
 
 // The pass path's work items of every box, from the bases k_box_update set:
 // a warp per box, lanes along its items (coalesced stores).
+// The members of a step group whose box update ran: not halted (a member at
+// its step limit after this step still writes its items).
+template <bool GRP>
 __global__ void __launch_bounds__(256)
-k_write_items(StepBuffers B) {
-    if (*(volatile int*)&B.st->halt) return;         // the box update stopped the step: no fresh bases
+k_write_items(StepBuffers B1, GroupRef grp) {
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
+    if (!GRP && *(volatile int*)&B1.st->halt) return;   // the box update stopped the step: no fresh bases
+    const int n_all = GRP ? group_scan(grp, kItemBoxes, 0, false, s_gb) : B1.n_boxes;
     const int lane = threadIdx.x & 31;
     const int warps = (blockDim.x >> 5) * gridDim.x;
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B.n_boxes; b += warps) {
+    for (int gb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gb < n_all; gb += warps) {
+        int b;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, gb, b);
         const int4 base = B.item_base[b];
         if (base.w < 0) continue;
         const Box cb = B.cur[b];
@@ -789,11 +801,77 @@ k_write_items(StepBuffers B) {
 }
 
 cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream_t s, bool count_step) {
-    k_box_update<<<1, kBoxUpdateThreads, 0, s>>>(B, layout_only ? 1 : 0, count_step ? 1 : 0);
+    const GroupRef none{nullptr, 0};
+    k_box_update<false><<<1, kBoxUpdateThreads, 0, s>>>(B, none, layout_only ? 1 : 0, count_step ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !B.use_passes) return e;
-    k_write_items<<<B.n_sm * 4, 256, 0, s>>>(B);
+    k_write_items<false><<<B.n_sm * 4, 256, 0, s>>>(B, none);
     return cudaGetLastError();
+}
+
+// Each member's step limit (steps_done at which it stops taking part).
+__global__ void k_group_limits(GroupRef grp, const long long* __restrict__ lim) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < grp.n) grp.B[k].st->step_limit = lim[k];
+}
+
+cudaError_t launch_group_limits(const GroupRef& grp, const long long* lim, cudaStream_t s) {
+    k_group_limits<<<1, kMaxGroup, 0, s>>>(grp, lim);
+    return cudaGetLastError();
+}
+
+// One step of every member of a step group (ideal growth, taxicab
+// re-initialisation, the pass path): the same kernels as launch_step's pass
+// path, each launched once over all members.  With side streams the binning
+// runs beside the convolution passes and tiers 1.. beside tier 0.
+cudaError_t launch_group_step(const StepBuffers& B0, const GroupRef& grp, const Taps& taps, cudaStream_t s,
+                              const StepStreams* ss) {
+    cudaStream_t bs = ss ? ss->side[kTiers - 1] : s;
+    cudaError_t e = cudaSuccess;
+    if (bs != s) {
+        e = traced(cudaEventRecord(ss->fork, s), "fork record");
+        if (e == cudaSuccess) e = traced(cudaStreamWaitEvent(bs, ss->fork, 0), "fork wait");
+        if (e != cudaSuccess) return e;
+    }
+    e = traced(launch_bin_group(B0, grp, bs), "group binning");
+    if (e == cudaSuccess && bs != s) e = traced(cudaEventRecord(ss->join[kTiers - 1], bs), "join record");
+    if (e != cudaSuccess) return e;
+    auto tiers = [&](int which) -> cudaError_t {
+        if (ss) {
+            cudaError_t r = traced(cudaEventRecord(ss->fork, s), "fork record");
+            if (r != cudaSuccess) return r;
+        }
+        for (int t = 0; t < kTiers; ++t) {
+            cudaStream_t ts = s;
+            if (ss && t > 0) {
+                ts = ss->side[t - 1];
+                cudaError_t r = traced(cudaStreamWaitEvent(ts, ss->fork, 0), "fork wait");
+                if (r != cudaSuccess) return r;
+            }
+            cudaError_t r = traced(launch_passes_group(B0, grp, which, t, taps, ts), "group pass kernels");
+            if (r != cudaSuccess) return r;
+            if (ss && t > 0) {
+                r = traced(cudaEventRecord(ss->join[t - 1], ts), "join record");
+                if (r == cudaSuccess) r = traced(cudaStreamWaitEvent(s, ss->join[t - 1], 0), "join wait");
+                if (r != cudaSuccess) return r;
+            }
+        }
+        return cudaSuccess;
+    };
+    e = tiers(0);
+    if (e != cudaSuccess) return e;
+    if (bs != s) {
+        e = traced(cudaStreamWaitEvent(s, ss->join[kTiers - 1], 0), "join wait");
+        if (e != cudaSuccess) return e;
+    }
+    e = traced(launch_field_group(B0, grp, s), "group field pass");
+    if (e == cudaSuccess) e = tiers(1);
+    if (e != cudaSuccess) return e;
+    k_box_update<true><<<grp.n, kBoxUpdateThreads, 0, s>>>(B0, grp, 0, 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return traced(e, "group box update");
+    k_write_items<true><<<B0.n_sm * 4, 256, 0, s>>>(B0, grp);
+    return traced(cudaGetLastError(), "group work items");
 }
 
 cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev& phys,

@@ -131,6 +131,9 @@ _SIGS = {
     "lsgg_debug_wait_timeout": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "lsgg_debug_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_debug_pair_ids": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int64]),
+    "lsgg_group_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "lsgg_group_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
+    "lsgg_group_destroy": (C.c_int, [C.c_void_p]),
     "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
     "lsgg_pass_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
@@ -457,6 +460,51 @@ def unpack(boxes: np.ndarray, packed: np.ndarray) -> dict:
 def pack(boxes: np.ndarray, arrays: dict, dtype=np.float32) -> np.ndarray:
     parts = [np.asarray(arrays[g], dtype=dtype).ravel() for g, b in enumerate(boxes) if b[0]]
     return np.concatenate(parts) if parts else np.zeros(0, dtype)
+
+
+MAX_GROUP = 64
+
+
+def group_create(ctxs) -> int:
+    """A step group over contexts (handles); returns the group handle."""
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    g = C.c_void_p()
+    _check("group_create", lib().lsgg_group_create(arr, len(ctxs), C.byref(g)))
+    return g.value
+
+
+def group_step(group, n: int, dt: float, step_limits=None):
+    lim = None
+    if step_limits is not None:
+        keep = np.ascontiguousarray(step_limits, dtype=np.int64)
+        lim = _ptr(keep, C.c_int64)
+    _check("group_step", lib().lsgg_group_step(group, n, dt, lim))
+
+
+def group_destroy(group):
+    _check("group_destroy", lib().lsgg_group_destroy(group))
+
+
+class Group:
+    """Several microstructures stepped by one set of launches per step."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        self.handle = group_create([m.ctx for m in self.members])
+
+    def step(self, n: int, dt: float, step_limits=None):
+        group_step(self.handle, n, dt, step_limits)
+
+    def close(self):
+        if self.handle:
+            group_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Microstructure:

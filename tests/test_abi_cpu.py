@@ -167,3 +167,17 @@ def test_anisotropy_map_configuration_is_checked(case):
     ctx = ctypes.c_void_p()
     code = L.lib().lsgg_create_microstructure(ctypes.byref(cfg), None, ctypes.byref(ctx))
     assert code in (L.ERR_INVALID_ARG, L.ERR_UNSUPPORTED)
+
+
+def test_group_arguments_checked_before_any_device_work():
+    """Step groups: no members, too many members or a NULL member are refused
+    without touching a device; a NULL group is refused by the step and the
+    destroy calls."""
+    L = _lib()
+    h = ctypes.c_void_p()
+    assert L.lib().lsgg_group_create(None, 0, ctypes.byref(h)) == L.ERR_INVALID_ARG
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.lib().lsgg_group_create(arr, 2, ctypes.byref(h)) == L.ERR_INVALID_ARG
+    assert L.lib().lsgg_group_create(arr, L.MAX_GROUP + 1, ctypes.byref(h)) == L.ERR_INVALID_ARG
+    assert L.lib().lsgg_group_step(None, 1, 1.0, None) == L.ERR_INVALID_ARG
+    assert L.lib().lsgg_group_destroy(None) == L.ERR_INVALID_ARG
