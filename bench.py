@@ -708,12 +708,13 @@ def _pct(sorted_vals, q):
     return sorted_vals[min(len(sorted_vals) - 1, max(0, int(math.ceil(q * len(sorted_vals))) - 1))]
 
 
-def serve_stream(L, reqs, device, budget, max_active=64, steps_per_round=4):
+def serve_stream(L, reqs, device, budget, max_active=64, steps_per_round=4, mode=None):
     """Submit requests at their arrival times (seconds from the start) and wait
     for all: per request latency = completion - arrival, the time queued
     before admission and the time from admission to completion."""
     lat, queued, service, cells = [], [], [], 0
-    with L.Server(budget, max_active=max_active, steps_per_round=steps_per_round, device=device) as srv:
+    mode = L.SERVE_SHARED if mode is None else mode
+    with L.Server(budget, max_active=max_active, steps_per_round=steps_per_round, device=device, mode=mode) as srv:
         start = time.perf_counter()
         tickets = []
         for r in reqs:
@@ -745,14 +746,18 @@ def serving_run(L, I, n_requests, device):
     The closed-loop capacity (requests per second with all of a 32-request
     sample of the same distribution, seeds 5000 + k, submitted at once) sets
     the rates; the n_requests then arrive as a Poisson stream at 0.8x and at
-    1.2x (overload) of that capacity.  Latency = completion - arrival."""
+    1.2x (overload) of that capacity.  Latency = completion - arrival.  The
+    server runs with shared launches (one step group over the running
+    requests); the same closed loop and the 0.8x stream are repeated with a
+    stream per request (per_context) for comparison."""
     budget = 150 << 30
     probe = I.serving_requests(32, 1.0, base_seed=5000)
     for r in probe:
         r.arrival = 0.0
     closed = serve_stream(L, probe, device, budget)
     capacity = len(probe) / closed["wall_s"]
-    out = {"requests": n_requests, "budget_bytes": budget, "max_active": 64, "capacity_per_s": capacity,
+    out = {"requests": n_requests, "budget_bytes": budget, "max_active": 64, "mode": "shared launches",
+           "capacity_per_s": capacity,
            "closed_loop": {"requests": len(probe), "cell_updates_per_s": closed["cell_updates_per_s"],
                            "wall_s": closed["wall_s"], "p50_s": closed["p50_s"], "p99_s": closed["p99_s"]},
            "rates": {}}
@@ -764,6 +769,22 @@ def serving_run(L, I, n_requests, device):
     lo = out["rates"]["0.8x"]
     out.update(p50_s=lo["p50_s"], p99_s=lo["p99_s"], cell_updates_per_s=lo["cell_updates_per_s"],
                peak_admitted_bytes=max(r["peak_admitted_bytes"] for r in out["rates"].values()))
+    pc_closed = serve_stream(L, probe, device, budget, mode=L.SERVE_PER_CONTEXT)
+    pc = serve_stream(L, I.serving_requests(n_requests, 0.8 * capacity, base_seed=1000), device, budget,
+                      mode=L.SERVE_PER_CONTEXT)
+    out["per_context"] = {"closed_loop": {"cell_updates_per_s": pc_closed["cell_updates_per_s"],
+                                          "wall_s": pc_closed["wall_s"], "capacity_per_s": len(probe) / pc_closed["wall_s"]},
+                          "0.8x": {k: pc[k] for k in ("p50_s", "p99_s", "mean_s", "cell_updates_per_s", "wall_s")}}
+    # small domains only (N in {32, 48, ..., 128}: the requests the step group
+    # takes), 64 submitted at once, in both modes
+    small = I.serving_requests(64, 1.0, base_seed=7000, sizes=tuple(range(32, 129, 16)))
+    for r in small:
+        r.arrival = 0.0
+    sm = {m: serve_stream(L, small, device, budget, mode=mv)
+          for m, mv in (("shared", L.SERVE_SHARED), ("per_context", L.SERVE_PER_CONTEXT))}
+    out["small_domains_closed_loop"] = {"requests": len(small), "sizes": "32^3 to 128^3",
+                                        **{m: {k: v[k] for k in ("cell_updates_per_s", "wall_s", "p50_s", "p99_s")}
+                                           for m, v in sm.items()}}
     return out
 
 

@@ -175,6 +175,12 @@ int lsgg_group_create(lsgg_ctx* const* members, int32_t n, lsgg_group** out);
  * arena and finishes its steps alone.  Returns after enqueue. */
 int lsgg_group_step(lsgg_group* g, int32_t n, double dt, const int64_t* step_limits);
 
+/* Replace the group's members (same rules as lsgg_group_create) without any
+ * allocation or synchronisation: the next lsgg_group_step advances the new
+ * members, after the steps already enqueued for the old ones.  A server
+ * changes the membership whenever a request joins or completes. */
+int lsgg_group_set_members(lsgg_group* g, lsgg_ctx* const* members, int32_t n);
+
 /* Waits for the group's work and frees the group (not its members). */
 int lsgg_group_destroy(lsgg_group* g);
 
@@ -397,13 +403,23 @@ int lsgg_debug_step(lsgg_ctx* ctx, double dt, float* phip, float* m, int32_t* id
  * (the paper has no serving layer; this is a request loop around Algorithm 1).
  * Requests wait in FIFO order; a scheduler thread admits the head request when
  * a slot is free and the HBM estimates of the running requests plus its own
- * fit in budget_bytes, creates its microstructure (boxes resident on the
- * device), and feeds every running request's stream with chunks of
- * steps_per_round steps, so requests overlap on the device.  Finished requests
+ * fit in budget_bytes and creates its microstructure (boxes resident on the
+ * device).  With shared launches (LSGG_SERVE_SHARED, the default of
+ * lsgg_server_create) the running requests of at most 128^3 domain cells that
+ * a step group accepts (lsgg_group_create: batched 3D, ideal growth, taxicab,
+ * radius 5) and share one dt advance together: one group over all of them (up
+ * to LSGG_MAX_GROUP) takes chunks of steps_per_round steps, each request
+ * stopping at its own step count; the group's members are replaced whenever a
+ * request joins or completes, with at most two chunks queued ahead.  Larger
+ * requests fill the GPU with their own launches.  Other requests, and every
+ * request with LSGG_SERVE_PER_CONTEXT, get their own stream fed with chunks of
+ * their own steps, so that requests overlap on the device.  Finished requests
  * keep their grain volumes on the host and release their device memory.
  * Results are those of lsgg_create_microstructure + lsgg_step(n_steps, dt) +
  * lsgg_grain_volumes run alone.  Times are seconds since lsgg_server_create. */
 typedef struct lsgg_server lsgg_server;
+#define LSGG_SERVE_PER_CONTEXT 0
+#define LSGG_SERVE_SHARED 1
 
 typedef struct lsgg_request_info {
     int32_t state;             /* 0 queued, 1 running, 2 done, < 0 failed with that status */
@@ -421,6 +437,10 @@ typedef struct lsgg_server_stats {
 
 int lsgg_server_create(int64_t budget_bytes, int32_t max_active, int32_t steps_per_round, int32_t device,
                        lsgg_server** out);
+/* lsgg_server_create with the scheduling mode: LSGG_SERVE_SHARED or
+ * LSGG_SERVE_PER_CONTEXT (anything else: LSGG_ERR_INVALID_ARG). */
+int lsgg_server_create_mode(int64_t budget_bytes, int32_t max_active, int32_t steps_per_round, int32_t device,
+                            int32_t mode, lsgg_server** out);
 /* Queue a request; cfg (and its arrays) are copied.  *ticket identifies it.
  * A request whose estimate exceeds the whole budget fails with
  * LSGG_ERR_OVER_BUDGET when it reaches the head of the queue. */

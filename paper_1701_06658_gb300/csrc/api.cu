@@ -814,9 +814,8 @@ void group_free(lsgg_group* g) {
 // One group step captured as a graph on the group's stream (the kernels read
 // the members' buffers from the device array, so the graph stays valid while
 // only their contents change).
-int group_graph(lsgg_group* g, double dt) {
-    if (g->graph && g->graph_dt == dt) return LSGG_OK;
-    if (g->graph) { cudaGraphExecDestroy(g->graph); g->graph = nullptr; }
+int group_graph(lsgg_group* g, double dt, bool stale) {
+    if (g->graph && g->graph_dt == dt && !stale) return LSGG_OK;
     const Taps taps = make_taps(dt, kGroupRadius);
     const GroupRef grp{g->d_B, (int)g->m.size()};
     cudaGraph_t graph = nullptr;
@@ -827,9 +826,21 @@ int group_graph(lsgg_group* g, double dt) {
         if (graph) cudaGraphDestroy(graph);
         return fail_cuda(e != cudaSuccess ? e : e2);
     }
-    e = cudaGraphInstantiate(&g->graph, graph, 0);
+    // the same launches with other parameters (member count, taps, shapes):
+    // update the executable graph in place, else instantiate anew
+    if (g->graph) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(g->graph, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(g->graph);
+            g->graph = nullptr;
+        }
+    }
+    if (!g->graph) {
+        e = cudaGraphInstantiate(&g->graph, graph, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(graph); g->graph = nullptr; return fail_cuda(e); }
+    }
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) { g->graph = nullptr; return fail_cuda(e); }
     g->graph_dt = dt;
     return LSGG_OK;
 }
@@ -838,26 +849,37 @@ int group_graph(lsgg_group* g, double dt) {
 
 extern "C" {
 
-int lsgg_group_create(lsgg_ctx* const* members, int32_t n, lsgg_group** out) {
-    if (!members || !out || n < 1 || n > kMaxGroup) return LSGG_ERR_INVALID_ARG;
-    *out = nullptr;
+// lsgg_group_create's rules for a member list.
+static int check_members(lsgg_ctx* const* members, int32_t n) {
+    if (!members || n < 1 || n > kMaxGroup) return LSGG_ERR_INVALID_ARG;
     for (int k = 0; k < n; ++k) {
         lsgg_ctx* c = members[k];
         if (!c) return LSGG_ERR_INVALID_ARG;
         for (int j = 0; j < k; ++j)
             if (members[j] == c) return LSGG_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < n; ++k) {
+        lsgg_ctx* c = members[k];
         if (c->device != members[0]->device || !c->B.use_passes || c->dom.dim != 3 ||
             c->cfg.physics != LSGG_PHYSICS_IDEAL || c->B.redist != LSGG_REDIST_TAXICAB ||
             c->dom.radius != kGroupRadius || c->B.gb_map || c->profiling)
             return LSGG_ERR_UNSUPPORTED;
     }
+    return LSGG_OK;
+}
+
+int lsgg_group_create(lsgg_ctx* const* members, int32_t n, lsgg_group** out) {
+    if (!out) return LSGG_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int chk = check_members(members, n);
+    if (chk != LSGG_OK) return chk;
     lsgg_group* g = new (std::nothrow) lsgg_group();
     if (!g) return LSGG_ERR_OUT_OF_MEMORY;
     g->m.assign(members, members + n);
     g->device = members[0]->device;
     auto bail = [&](int code) { group_free(g); return code; };
     if (cudaSetDevice(g->device) != cudaSuccess) return bail(CUDA_FAIL());
-    if (configure_group_kernels() != cudaSuccess) return bail(CUDA_FAIL());
+    if (configure_group_kernels(members[0]->B.n_sm) != cudaSuccess) return bail(CUDA_FAIL());
     if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(CUDA_FAIL());
     bool ok = cudaEventCreateWithFlags(&g->ss.fork, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; k < kNumClasses && ok; ++k)
@@ -866,11 +888,11 @@ int lsgg_group_create(lsgg_ctx* const* members, int32_t n, lsgg_group** out) {
     if (!ok) return bail(CUDA_FAIL());
     g->have_ss = true;
     if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) return bail(CUDA_FAIL());
-    g->ready.resize(n, nullptr);
-    for (int k = 0; k < n; ++k)
+    g->ready.resize(kMaxGroup, nullptr);
+    for (int k = 0; k < kMaxGroup; ++k)
         if (cudaEventCreateWithFlags(&g->ready[k], cudaEventDisableTiming) != cudaSuccess) return bail(CUDA_FAIL());
-    if (cudaMalloc(&g->d_B, sizeof(StepBuffers) * n) != cudaSuccess ||
-        cudaMalloc(&g->d_lim, sizeof(long long) * n) != cudaSuccess) {
+    if (cudaMalloc(&g->d_B, sizeof(StepBuffers) * kMaxGroup) != cudaSuccess ||
+        cudaMalloc(&g->d_lim, sizeof(long long) * kMaxGroup) != cudaSuccess) {
         cudaGetLastError();
         return bail(LSGG_ERR_OUT_OF_MEMORY);
     }
@@ -898,14 +920,13 @@ int lsgg_group_step(lsgg_group* g, int32_t n, double dt, const int64_t* step_lim
     if (fresh) {
         g->h_B.swap(now);
         CK(cudaMemcpyAsync(g->d_B, g->h_B.data(), sizeof(StepBuffers) * nm, cudaMemcpyHostToDevice, g->stream));
-        if (g->graph) { cudaGraphExecDestroy(g->graph); g->graph = nullptr; }   // launch shapes may differ
     }
     if (lim != g->h_lim) {
         g->h_lim = lim;
         CK(cudaMemcpyAsync(g->d_lim, g->h_lim.data(), sizeof(long long) * nm, cudaMemcpyHostToDevice, g->stream));
     }
     CK(launch_group_limits(GroupRef{g->d_B, nm}, g->d_lim, g->stream));
-    int r = group_graph(g, dt);
+    int r = group_graph(g, dt, fresh);       // member count and launch shapes may have changed
     if (r != LSGG_OK) return r;
     for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(g->graph, g->stream));
     CK(cudaEventRecord(g->done, g->stream));
@@ -919,6 +940,15 @@ int lsgg_group_step(lsgg_group* g, int32_t n, double dt, const int64_t* step_lim
         c->field_valid = true;
     }
     return LSGG_OK;
+}
+
+int lsgg_group_set_members(lsgg_group* g, lsgg_ctx* const* members, int32_t n) {
+    if (!g) return LSGG_ERR_INVALID_ARG;
+    const int chk = check_members(members, n);
+    if (chk != LSGG_OK) return chk;
+    if (members[0]->device != g->device) return LSGG_ERR_UNSUPPORTED;
+    g->m.assign(members, members + n);
+    return LSGG_OK;     // the next step sends the new buffers and updates the graph
 }
 
 int lsgg_group_destroy(lsgg_group* g) {

@@ -281,7 +281,8 @@ cudaError_t launch_bin(const StepBuffers& B, cudaStream_t s);
 // the field pass over every member of `grp`; B0 (a member) gives the launch
 // shapes.  launch_group_step enqueues a whole step.
 constexpr int kGroupRadius = 5;
-cudaError_t configure_group_kernels();   // shared-memory limits of the group kernels (host, once per process)
+// shared-memory limits and persistent grids of the group kernels on a GPU of n_sm SMs
+cudaError_t configure_group_kernels(int n_sm);
 cudaError_t launch_passes_group(const StepBuffers& B0, const GroupRef& grp, int which, int tier, const Taps& taps,
                                 cudaStream_t s);
 cudaError_t launch_bin_group(const StepBuffers& B0, const GroupRef& grp, cudaStream_t s);

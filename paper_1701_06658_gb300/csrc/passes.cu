@@ -640,7 +640,7 @@ __device__ __forceinline__ void top2_insert(float v, int id, float& v1, int& i1,
 // Four CTAs per SM for the plain field; the ID-field and debug variants keep
 // the registers of three.
 template <bool IDF, bool DBG, bool GRP>
-__global__ void __launch_bounds__(kTileX * kTileY, (IDF || DBG) ? 3 : 4)
+__global__ void __launch_bounds__(kTileX * kTileY, (IDF || DBG || GRP) ? 3 : 4)
 p_field(StepBuffers B1, GroupRef grp, PhysicsDev phys, DebugOut dbg) {
     static_assert(!(GRP && (IDF || DBG)), "step groups run ideal growth without intermediates");
     __shared__ TileBox s_tb[kTileCap];
@@ -862,7 +862,8 @@ __host__ __device__ constexpr size_t redist_layout_bytes(int side) {  // barrier
 __host__ __device__ constexpr int redist_min_blocks(int side) { return side <= 32 ? 8 : side <= 40 ? 6 : side <= 48 ? 5 : 2; }
 
 template <int SIDE, int NT, bool GRP>
-__global__ void __launch_bounds__(NT, redist_min_blocks(SIDE))
+__global__ void __launch_bounds__(NT, GRP ? (redist_min_blocks(SIDE) > 2 ? redist_min_blocks(SIDE) - 1 : 2)
+                                          : redist_min_blocks(SIDE))
 p_redist_xy(StepBuffers B1, GroupRef grp, int tier) {
     constexpr int PA = SIDE * SIDE;                   // floats per plane slot
     constexpr int PG = SIDE + 1;                      // pitch of G
@@ -1856,13 +1857,21 @@ cudaError_t launch_field(const StepBuffers& B, const PhysicsDev& phys, const Deb
 }
 
 // ---- step groups ----
+// Persistent grids of the group kernels (their own occupancy: the group
+// variants keep more registers than the single-context ones).
+struct GroupShapes {
+    int pgrid[kTiers][5];             // as StepBuffers::pgrid (index 2 unused)
+    int field, bin, n_sm;
+};
+static GroupShapes g_group_shapes{};
+
 // The group kernels are instantiated for radius kGroupRadius only; their
 // launch shapes are the member B0's (the same device: the same occupancy).
 cudaError_t launch_passes_group(const StepBuffers& B0, const GroupRef& grp, int which, int tier, const Taps& taps,
                                 cudaStream_t s) {
     if (taps.radius != kGroupRadius) return cudaErrorInvalidValue;
     const PassFns fn = pass_fns_r<kGroupRadius, true>(false);
-    const int* g = B0.pgrid[tier];
+    const int* g = g_group_shapes.pgrid[tier];
     StepBuffers bb = B0;
     GroupRef gr = grp;
     Taps tp = taps;
@@ -1889,26 +1898,47 @@ cudaError_t launch_passes_group(const StepBuffers& B0, const GroupRef& grp, int 
     return cudaGetLastError();
 }
 
-cudaError_t configure_group_kernels() {
+cudaError_t configure_group_kernels(int n_sm) {
     const PassFns fn = pass_fns_r<kGroupRadius, true>(false);
-    for (int t = 0; t + 1 < kTiers; ++t) {
-        cudaError_t e = allow_max_dynamic_smem(fn.conv_xy[t]);
-        if (e == cudaSuccess) e = allow_max_dynamic_smem(fn.redist_xy[t]);
+    GroupShapes sh{};
+    sh.n_sm = n_sm;
+    for (int t = 0; t < kTiers; ++t) {
+        cudaError_t e = cudaSuccess;
+        if (t + 1 < kTiers) {
+            e = allow_max_dynamic_smem(fn.conv_xy[t]);
+            if (e == cudaSuccess) e = allow_max_dynamic_smem(fn.redist_xy[t]);
+        }
+        int o[5] = {0, 0, 0, 0, 0};
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], fn.conv_xy[t], kConvThreads[t],
+                                                              conv_smem_bytes(kTierSide[t], kGroupRadius));
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], fn.conv_z, kColThreads, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], fn.redist_xy[t], kRedistThreads[t],
+                                                              redist_smem_bytes(kTierSide[t]));
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[4], p_redist_z<true>, kColThreads, 0);
         if (e != cudaSuccess) return e;
+        for (int k = 0; k < 5; ++k) sh.pgrid[t][k] = n_sm * (o[k] < 1 ? 1 : o[k]);
     }
+    int of = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, p_field<false, false, true>, kTileX * kTileY, 0);
+    if (e != cudaSuccess) return e;
+    sh.field = n_sm * (of < 1 ? 1 : of);
+    sh.bin = n_sm;
+    g_group_shapes = sh;
     return cudaSuccess;
 }
 
 cudaError_t launch_bin_group(const StepBuffers& B0, const GroupRef& grp, cudaStream_t s) {
-    k_clear_tiles_group<<<B0.n_sm, 256, 0, s>>>(grp);
+    k_clear_tiles_group<<<g_group_shapes.n_sm, 256, 0, s>>>(grp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_bin<true><<<B0.bin_grid, 256, 0, s>>>(B0, grp);
+    k_bin<true><<<g_group_shapes.bin, 256, 0, s>>>(B0, grp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_field_group(const StepBuffers& B0, const GroupRef& grp, cudaStream_t s) {
-    p_field<false, false, true><<<B0.field_grid[0], kTileX * kTileY, 0, s>>>(B0, grp, PhysicsDev{}, DebugOut{});
+    p_field<false, false, true><<<g_group_shapes.field, kTileX * kTileY, 0, s>>>(B0, grp, PhysicsDev{}, DebugOut{});
     return cudaGetLastError();
 }
 

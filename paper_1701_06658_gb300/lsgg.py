@@ -117,6 +117,8 @@ _SIGS = {
     "lsgg_closest_gb_map": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
                                       C.c_void_p, C.c_void_p]),
     "lsgg_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
+    "lsgg_server_create_mode": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                          C.POINTER(C.c_void_p)]),
     "lsgg_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Config), C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
     "lsgg_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
     "lsgg_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]),
@@ -133,6 +135,7 @@ _SIGS = {
     "lsgg_debug_pair_ids": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int64]),
     "lsgg_group_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "lsgg_group_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
+    "lsgg_group_set_members": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.c_int32]),
     "lsgg_group_destroy": (C.c_int, [C.c_void_p]),
     "lsgg_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
@@ -463,6 +466,7 @@ def pack(boxes: np.ndarray, arrays: dict, dtype=np.float32) -> np.ndarray:
 
 
 MAX_GROUP = 64
+SERVE_PER_CONTEXT, SERVE_SHARED = 0, 1
 
 
 def group_create(ctxs) -> int:
@@ -481,6 +485,11 @@ def group_step(group, n: int, dt: float, step_limits=None):
     _check("group_step", lib().lsgg_group_step(group, n, dt, lim))
 
 
+def group_set_members(group, ctxs):
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    _check("group_set_members", lib().lsgg_group_set_members(group, arr, len(ctxs)))
+
+
 def group_destroy(group):
     _check("group_destroy", lib().lsgg_group_destroy(group))
 
@@ -494,6 +503,10 @@ class Group:
 
     def step(self, n: int, dt: float, step_limits=None):
         group_step(self.handle, n, dt, step_limits)
+
+    def set_members(self, members):
+        group_set_members(self.handle, [m.ctx for m in members])
+        self.members = list(members)
 
     def close(self):
         if self.handle:
@@ -627,10 +640,11 @@ class ServerStats(C.Structure):
 class Server:
     """lsgg_server_*: continuous batching of independent simulations under an HBM budget."""
 
-    def __init__(self, budget_bytes: int, max_active: int = 64, steps_per_round: int = 4, device: int = 0):
+    def __init__(self, budget_bytes: int, max_active: int = 64, steps_per_round: int = 4, device: int = 0,
+                 mode: int = SERVE_SHARED):
         h = C.c_void_p()
-        _check("server_create", lib().lsgg_server_create(int(budget_bytes), max_active, steps_per_round, device,
-                                                          C.byref(h)))
+        _check("server_create", lib().lsgg_server_create_mode(int(budget_bytes), max_active, steps_per_round, device,
+                                                               mode, C.byref(h)))
         self.h = h
         self._n_grains = {}
 

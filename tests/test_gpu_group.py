@@ -157,3 +157,32 @@ def test_group_refuses_other_configurations(L):
     finally:
         a.close()
         rs.close()
+
+
+def test_membership_changes_between_steps(L):
+    """One group whose members are replaced between steps (members leaving,
+    joining and coming back) gives every microstructure the result of its
+    steps alone."""
+    mem = [MEMBERS[0], MEMBERS[1], MEMBERS[2], MEMBERS[5]]
+    plan = [[0, 1], [0, 1, 2], [2, 3], [1, 3, 0]]      # members of each group step of 2 steps
+    counts = [0] * len(mem)
+    for grp in plan:
+        for k in grp:
+            counts[k] += 2
+    want = []
+    for m, c in zip(mem, counts):
+        with _make(L, m) as ms:
+            ms.step(c, 1.0)
+            want.append(_snapshot(L, ms))
+    mss = [_make(L, m) for m in mem]
+    try:
+        with L.Group([mss[k] for k in plan[0]]) as g:
+            for i, grp in enumerate(plan):
+                if i:
+                    g.set_members([mss[k] for k in grp])
+                g.step(2, 1.0)
+        for ms, w in zip(mss, want):
+            _assert_same(_snapshot(L, ms), w)
+    finally:
+        for ms in mss:
+            ms.close()

@@ -32,10 +32,15 @@ def _direct(L, n, g, seed, steps):
         return ms.grain_volumes()
 
 
-def test_result_alone_equals_result_in_the_mix(L):
+@pytest.mark.parametrize("mode", ["shared", "per_context"])
+def test_result_alone_equals_result_in_the_mix(L, mode):
+    """Shared launches (one step group over the running requests, rebuilt as
+    they join and finish) and per-context streams give every request the
+    result of running it alone."""
     n, g, seed, steps = MIX[0]
     seeds = I.voronoi_seeds(seed, g, (n, n, n))
-    with L.Server(budget_bytes=8 << 30, max_active=8, steps_per_round=3) as srv:
+    m = L.SERVE_SHARED if mode == "shared" else L.SERVE_PER_CONTEXT
+    with L.Server(budget_bytes=8 << 30, max_active=8, steps_per_round=3, mode=m) as srv:
         t = srv.submit(n, n, n, g, steps, seeds=seeds)
         srv.wait(t)
         alone = srv.volumes(t)
@@ -48,7 +53,7 @@ def test_result_alone_equals_result_in_the_mix(L):
         assert min(i.t_done for i in infos) > max(i.t_admit for i in infos[:3])
         assert np.array_equal(alone, mixed)
         assert np.array_equal(alone, _direct(L, n, g, seed, steps))
-        for (nn, gg, sd, st), tk in zip(MIX[1:3], tickets[1:3]):
+        for (nn, gg, sd, st), tk in zip(MIX[1:], tickets[1:]):
             assert np.array_equal(srv.volumes(tk), _direct(L, nn, gg, sd, st))
         s = srv.stats()
         assert s.completed == len(MIX) + 1 and s.active == 0 and s.queued == 0
@@ -69,3 +74,21 @@ def test_budget_serialises_and_refuses(L):
         with pytest.raises(L.LsggError) as e:
             srv.wait(big)
         assert e.value.code == L.ERR_OVER_BUDGET
+
+
+def test_shared_launches_with_requests_outside_the_group(L):
+    """A server with shared launches runs requests the step group does not
+    take (Read-Shockley physics; another dt; a domain above 128^3 cells) on
+    their own streams beside the group; every result equals the request run
+    alone."""
+    reqs = [(40, 25, 21, 9, 1.0, {}), (48, 30, 22, 7, 1.0, {"physics": L.PHYSICS_READ_SHOCKLEY}),
+            (32, 20, 23, 11, 0.5, {}), (36, 24, 24, 8, 1.0, {}), (132, 690, 25, 3, 1.0, {})]
+    with L.Server(budget_bytes=8 << 30, max_active=8, steps_per_round=4, mode=L.SERVE_SHARED) as srv:
+        tks = [srv.submit(n, n, n, g, st, dt=dt, seeds=I.voronoi_seeds(sd, g, (n, n, n)), **kw)
+               for (n, g, sd, st, dt, kw) in reqs]
+        for tk in tks:
+            srv.wait(tk)
+        for (n, g, sd, st, dt, kw), tk in zip(reqs, tks):
+            with L.Microstructure(n, n, n, g, seeds=I.voronoi_seeds(sd, g, (n, n, n)), **kw) as ms:
+                ms.step(st, dt)
+                assert np.array_equal(srv.volumes(tk), ms.grain_volumes())
