@@ -633,6 +633,11 @@ def gpu_arm(args):
             torch.cuda.synchronize()
             configs[name] = device_block(L, I, torch, WORKLOADS[key], local, args.config_steps, 3, st)
 
+    # ---------------- step groups: many microstructures in one set of launches ----------------
+    group = None
+    if not args.no_compare and rank == 0:
+        group = group_block(L, I, torch, local)
+
     # ---------------- serving: continuous batching under an HBM budget ----------------
     serving = None
     if args.serve_requests > 0 and rank == 0:
@@ -695,6 +700,7 @@ def gpu_arm(args):
         "serving": serving,
         "configs": configs,
         "compare": compare,
+        "step_group": group,
         "bf16_storage": bf16,
         "coarsening": coarsening,
         "size_analysis": statistics,
@@ -702,6 +708,53 @@ def gpu_arm(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def group_block(L, I, torch, device, steps=20):
+    """Microstructures of one size advanced as one step group against the same
+    ones on their own streams (all enqueued before waiting), CUDA events
+    around each pass (a stream waiting for the others' work): 48 of 48^3 / 33
+    grains, 16 of 96^3 / 263, 6 of 160^3 / 1221 (seeds 10 + k)."""
+    out = {}
+    for n, g, cnt in ((48, 33, 48), (96, 263, 16), (160, 1221, 6)):
+        ms = [L.Microstructure(n, n, n, g, seeds=I.voronoi_seeds(10 + k, g, (n, n, n)), device=device)
+              for k in range(cnt)]
+        try:
+            for m in ms:
+                m.step(2, 1.0)
+            for m in ms:
+                m.sync()
+            cells = sum(m.stats().box_cells for m in ms)
+
+            def timed(run):
+                torch.cuda.synchronize()
+                s = torch.cuda.Stream()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                run()
+                for m in ms:                       # s waits for every member's stream
+                    e = torch.cuda.Event()
+                    e.record(torch.cuda.ExternalStream(m.stream))
+                    s.wait_event(e)
+                b.record(s)
+                b.synchronize()
+                return a.elapsed_time(b)
+
+            streams_ms = timed(lambda: [m.step(steps, 1.0) for m in ms])
+            with L.Group(ms) as grp:
+                grp.step(1, 1.0)
+                for m in ms:
+                    m.sync()
+                group_ms = timed(lambda: grp.step(steps, 1.0))
+            out[f"{cnt}x{n}^3"] = {"members": cnt, "box_cells_per_step": cells,
+                                   "own_streams_ms_per_step": streams_ms / steps,
+                                   "group_ms_per_step": group_ms / steps,
+                                   "group_cell_updates_per_s": cells * steps / (group_ms * 1e-3),
+                                   "speedup": streams_ms / group_ms}
+        finally:
+            for m in ms:
+                m.close()
+    return out
 
 
 def _pct(sorted_vals, q):
