@@ -96,7 +96,7 @@ def kernel_source_hash():
 # must move at least: each reads its input field once and writes its output
 # once.  The state X is FP32 (4 B) or BF16 (2 B); with physics the z pass also
 # reads the previous step's phi and ID-field of each cell.
-def pass_bytes(kernel: str, state_bytes: int, physics: bool):
+def pass_bytes(kernel: str, state_bytes: int, physics: bool, keep_field: bool = False):
     """(bytes per box cell of the launch's tier, bytes per domain cell)."""
     name = kernel.split("[")[0]
     if name == "p_conv_xy":
@@ -105,8 +105,9 @@ def pass_bytes(kernel: str, state_bytes: int, physics: bool):
         return 8.0 + ((state_bytes + 4.0) if physics else 0.0), 0.0   # Z in, Y out (+ phi, IDF)
     if name == "p_field":
         # phi_p read once (the top two), phi_c written (and the ID-field with
-        # physics); the 16-byte field per domain cell stored
-        return 8.0 + (4.0 if physics else 0.0), 16.0
+        # physics); the top-two field is consumed in registers, its 16 B per
+        # domain cell stored only on request (lsgg_keep_field)
+        return 8.0 + (4.0 if physics else 0.0), 16.0 if keep_field else 0.0
     if name == "p_redist_xy":
         return 8.0, 0.0                                   # phi_c in, x/y-scanned magnitudes out
     if name == "p_redist_z":
@@ -115,7 +116,7 @@ def pass_bytes(kernel: str, state_bytes: int, physics: bool):
 
 
 def step_roofline(box_cells: float, dom_cells: float, ms_per_step: float, peak_gbs: float, passes: bool,
-                  state_bytes: int = 4, physics: bool = False):
+                  state_bytes: int = 4, physics: bool = False, keep_field: bool = False):
     """The whole step against the bytes the method must move at least (one
     read and write of phi per box cell -- the ID-field's too with physics --
     and 44 B of top-two field per domain cell: 16 cleared, 16 written, 12
@@ -130,14 +131,14 @@ def step_roofline(box_cells: float, dom_cells: float, ms_per_step: float, peak_g
     if passes:
         per_box = sum(pass_bytes(k, state_bytes, physics)[0]
                       for k in ("p_conv_xy", "p_conv_z", "p_field", "p_redist_xy", "p_redist_z"))
-        design = per_box * box_cells + 16.0 * dom_cells
+        design = per_box * box_cells + pass_bytes("p_field", state_bytes, physics, keep_field)[1] * dom_cells
         out.update(design_bytes_per_step=design, design_bytes_per_box_cell=per_box,
                    achieved_design_gbs=design / t / 1e9, frac_design=design / t / 1e9 / peak_gbs)
     return out
 
 
 def kernel_roofline(pass_ms: dict, tier_cells, box_cells: float, dom_cells: float, n_grains: int, peak_gbs: float,
-                    state_bytes: int = 4, physics: bool = False):
+                    state_bytes: int = 4, physics: bool = False, keep_field: bool = False):
     """Roofline of the pass with the longest time per launch: its algorithmic
     bytes per launch (pass_bytes x the box cells of its tier, or of all boxes
     for the field pass) over its CUDA-event time."""
@@ -145,7 +146,7 @@ def kernel_roofline(pass_ms: dict, tier_cells, box_cells: float, dom_cells: floa
     if dominant == "k_bin":
         units, alg = float(n_grains), 32.0 * n_grains
     else:
-        per_box, per_dom = pass_bytes(dominant, state_bytes, physics)
+        per_box, per_dom = pass_bytes(dominant, state_bytes, physics, keep_field)
         units = box_cells if dominant == "p_field" else float(tier_cells[int(dominant[-2])])
         alg = per_box * units + per_dom * dom_cells
     achieved = alg / (pass_ms[dominant] * 1e-3) / 1e9

@@ -371,9 +371,18 @@ int lsgg_pass_times(lsgg_ctx* ctx, double* out_ms, int64_t* out_count);
  * are the largest other function somewhere in grain i's box with a value above
  * -eps -- the ids of its ID-field.  counts[i] = number of neighbours (at most
  * cap_per_grain are stored, ascending, at ids[i * cap_per_grain ...]; a count
- * above cap_per_grain means the list was cut).  Needs a step since creation
- * or lsgg_set_state (else LSGG_ERR_NOT_READY).  Synchronises. */
+ * above cap_per_grain means the list was cut).  Reads the neighbour-max field
+ * of the last step, which the pass path stores only while lsgg_keep_field is
+ * on: needs such a step since creation or lsgg_set_state (else
+ * LSGG_ERR_NOT_READY).  Synchronises. */
 int lsgg_grain_neighbours(lsgg_ctx* ctx, int32_t* counts, int32_t* ids, int32_t cap_per_grain);
+
+/* The pass path's field pass consumes each domain cell's two largest
+ * (phi_p, grain) pairs (the neighbour-max field of Eq. (16)) in registers;
+ * with on != 0 it also stores them (16 bytes per domain cell and step) for
+ * lsgg_grain_neighbours.  Off by default.  The box-streaming and plain modes
+ * always build the field in device memory. */
+int lsgg_keep_field(lsgg_ctx* ctx, int32_t on);
 
 /* Boxes of all grains: out[7*i .. 7*i+6] = alive, ox, oy, oz, nx, ny, nz
  * (origin in [0, N) per axis).  cap in int32s, >= 7 * n_grains.  Synchronises. */

@@ -307,6 +307,10 @@ int relayout(lsgg_ctx* c) {
 
 int enqueue_steps(lsgg_ctx* c, long long n, double dt, const DebugOut* dbg);
 
+// Steps leave the neighbour-max field in T: always off the pass path, on it
+// while lsgg_keep_field is on.
+bool field_stored(const lsgg_ctx* c) { return !c->B.use_passes || c->B.keep_field; }
+
 }  // namespace
 
 extern "C" {
@@ -721,7 +725,7 @@ int lsgg_step(lsgg_ctx* c, int32_t n, double dt) {
     if (cudaSetDevice(c->device) != cudaSuccess) return CUDA_FAIL();
     c->steps_target += n;
     c->last_dt = dt;
-    c->field_valid = true;
+    c->field_valid = field_stored(c);
     return enqueue_steps(c, n, dt, nullptr);
 }
 
@@ -937,7 +941,7 @@ int lsgg_group_step(lsgg_group* g, int32_t n, double dt, const int64_t* step_lim
         if (step_limits) target = std::min(target, std::max(c->steps_target, (long long)step_limits[k]));
         c->steps_target = target;
         c->last_dt = dt;
-        c->field_valid = true;
+        c->field_valid = field_stored(c);
     }
     return LSGG_OK;
 }
@@ -1045,7 +1049,7 @@ int lsgg_autotune(lsgg_ctx* c, int32_t steps_per_trial, double dt, int32_t* chos
         if (chosen)
             for (int k = 0; k < 2 * kNumClasses; ++k) chosen[k] = -1;
         r = autotune_passes(c, steps_per_trial, dt);
-        c->field_valid = true;
+        c->field_valid = field_stored(c);
         c->last_dt = dt;
         return r;
     }
@@ -1094,7 +1098,7 @@ int lsgg_autotune(lsgg_ctx* c, int32_t steps_per_trial, double dt, int32_t* chos
             if (chosen) chosen[w * kNumClasses + k] = c->B.mode[k] == 0 ? best_v[w][k] : -1;
         }
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-    c->field_valid = true;
+    c->field_valid = field_stored(c);
     c->last_dt = dt;
     return status;
 }
@@ -1225,6 +1229,15 @@ int lsgg_debug_set_wait_limit(lsgg_ctx* c, int32_t polls) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
     }
+    return LSGG_OK;
+}
+
+int lsgg_keep_field(lsgg_ctx* c, int32_t on) {
+    if (!c) return LSGG_ERR_INVALID_ARG;
+    const int v = on ? 1 : 0;
+    if (c->B.keep_field == v) return LSGG_OK;
+    c->B.keep_field = v;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }   // the field pass's parameters changed
     return LSGG_OK;
 }
 
@@ -1377,7 +1390,7 @@ int lsgg_debug_step(lsgg_ctx* c, double dt, float* phip, float* m, int32_t* idm,
     dbg.phin = base + 4 * c->B.cap;
     c->steps_target += 1;
     c->last_dt = dt;
-    c->field_valid = true;
+    c->field_valid = field_stored(c);
     r = enqueue_steps(c, 1, dt, &dbg);
     if (r == LSGG_OK) r = lsgg_sync(c, -1);
     if (r == LSGG_OK) {

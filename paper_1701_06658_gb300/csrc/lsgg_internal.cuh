@@ -171,6 +171,7 @@ struct StepBuffers {
     void* gb_scratch;
     int gb_grid, gb_cap_cubes, gb_cap_tris;
     int wait_limit;                 // polls of a pass kernel's wait on its bulk copies (test hook lowers it)
+    int keep_field;                 // pass path: the field pass also stores the top-two field in T
     int class_side[kNumClasses];    // largest box side per class (last: whole domain)
     int mode[kNumClasses];          // 0: register-ring kernels, 1: shared-memory ring, 2: global scratch ring,
                                     // 3: pass path

@@ -14,7 +14,8 @@
 //   p_conv_z    (box, columns): z pass over a register window, velocity
 //               correction, clamp                                 -> Y = phi_p
 //   p_field     (domain tile): the two largest (phi_p, grain) per cell over
-//               the tile's boxes in registers -> T as (phi_p, -id) keys; then
+//               the tile's boxes in registers (stored in T as (phi_p, -id)
+//               keys only on request, B.keep_field); then
 //               phi_c = (phi_p - m) / 2 and the ID-field for every box cell of
 //               the tile                                          -> Z = phi_c
 //   p_redist_xy (box, slab): plane ring filled by bulk copies; reference cells
@@ -672,9 +673,10 @@ p_field(StepBuffers B1, GroupRef grp, PhysicsDev phys, DebugOut dbg) {
         for (int sweep = 0; sweep < 2; ++sweep) {
             if (sweep == 1) {
                 ulonglong2* T2 = reinterpret_cast<ulonglong2*>(B.T);
+                const bool keep = B.keep_field != 0;
 #pragma unroll
                 for (int zz = 0; zz < kTileZ; ++zz) {
-                    if (col && zz < nzt)
+                    if (keep && col && zz < nzt)
                         T2[((long long)(z0 + zz) * D.ny + y) * D.nx + x] =
                             make_ulonglong2(i1[zz] >= 0 ? make_key(v1[zz], i1[zz]) : 0ull,
                                             i2[zz] >= 0 ? make_key(v2[zz], i2[zz]) : 0ull);

@@ -530,6 +530,7 @@ k_box_update(StepBuffers B1, GroupRef grp, int layout_only, int count_step) {
                     int os[3] = {cb.ox, cb.oy, cb.oz};
                     int ns[3] = {cb.nx, cb.ny, cb.nz};
                     int no[3], nn[3];
+#pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         if (a == 2 && D.dim == 2) { no[a] = 0; nn[a] = 1; continue; }
                         int ext = bd.hi[a] - bd.lo[a] + 1 + 2 * D.halo;
@@ -555,8 +556,14 @@ k_box_update(StepBuffers B1, GroupRef grp, int layout_only, int count_step) {
     // inclusive scan of the per-thread sums (integer: the order does not matter)
     long long total = 0;
     const long long incl = block_inclusive_scan_ll(sum, s_part, &total);
-    if (!layout_only && count_step && done) atomicAdd((unsigned long long*)&B.st->cell_updates, (unsigned long long)done);
-    if (threadIdx.x == 0 && !layout_only && count_step) B.st->steps_done += 1;   // the step's fields are complete
+    if (!layout_only && count_step) {
+        long long dn[1] = {done};
+        block_sums_ll<1>(dn, s_part);
+        if (threadIdx.x == 0) {
+            B.st->cell_updates += dn[0];
+            B.st->steps_done += 1;                  // the step's fields are complete
+        }
+    }
     if (total > B.cap) {
         if (threadIdx.x == 0) {
             B.st->status = LSGG_ERR_CAPACITY;
@@ -569,7 +576,15 @@ k_box_update(StepBuffers B1, GroupRef grp, int layout_only, int count_step) {
     // per-thread counts: boxes per class (work lists), pass-path planes,
     // column chunks and slabs per tier; their block-wide exclusive scans place
     // every box's entries in box order
+    // (every array below is indexed by unrolled constants only, so that it
+    // stays in registers: a class or tier picks its entries by predicates)
     constexpr int NV = kNumClasses + 3 * kTiers;
+    int cls_pass[kNumClasses], cls_tier[kNumClasses];
+#pragma unroll
+    for (int q = 0; q < kNumClasses; ++q) {
+        cls_pass[q] = B.mode[q] == 3;
+        cls_tier[q] = pass_tier(B, q);
+    }
     int cnt[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) cnt[k] = 0;
@@ -582,13 +597,25 @@ k_box_update(StepBuffers B1, GroupRef grp, int layout_only, int count_step) {
         if (cb.nx > 0) {
             const int c = box_class(B, cb, B.prev[b]);
             const long long vol = (long long)cb.nx * cb.ny * cb.nz;
-            cnt[c] += 1;
-            if (B.mode[c] == 3) {
-                const int t = pass_tier(B, c);
-                cnt[kNumClasses + t] += cb.nz;
-                cnt[kNumClasses + kTiers + t] += (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
-                cnt[kNumClasses + 2 * kTiers + t] += (cb.nz + B.slab - 1) / B.slab;
-                tcell[t] += vol;
+            int pass = 0, t = 0;
+#pragma unroll
+            for (int q = 0; q < kNumClasses; ++q)
+                if (q == c) {
+                    cnt[q] += 1;
+                    pass = cls_pass[q];
+                    t = cls_tier[q];
+                }
+            if (pass) {
+                const int nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
+                const int nsl = (cb.nz + B.slab - 1) / B.slab;
+#pragma unroll
+                for (int u = 0; u < kTiers; ++u)
+                    if (u == t) {
+                        cnt[kNumClasses + u] += cb.nz;
+                        cnt[kNumClasses + kTiers + u] += nch;
+                        cnt[kNumClasses + 2 * kTiers + u] += nsl;
+                        tcell[u] += vol;
+                    }
             }
             cells += vol;
             alive += 1;
@@ -600,8 +627,10 @@ k_box_update(StepBuffers B1, GroupRef grp, int layout_only, int count_step) {
     // 1 column chunks, 2 slabs): the totals of the tiers before it
     int tier_base[3][kTiers];
     long long kind_total[3];
+#pragma unroll
     for (int kd = 0; kd < 3; ++kd) {
         long long acc = 0;
+#pragma unroll
         for (int t = 0; t < kTiers; ++t) {
             tier_base[kd][t] = (int)acc;
             acc += tot[kNumClasses + kd * kTiers + t];
@@ -615,20 +644,32 @@ k_box_update(StepBuffers B1, GroupRef grp, int layout_only, int count_step) {
         if (B.use_passes) B.item_base[b] = make_int4(0, 0, 0, -1);
         if (cb.nx <= 0) continue;
         const int c = box_class(B, cb, B.prev[b]);
-        if (B.mode[c] != 3) {
-            B.worklist[c * G + pre[c]++] = b;
+        int pass = 0, t = 0, wl = 0;
+#pragma unroll
+        for (int q = 0; q < kNumClasses; ++q)
+            if (q == c) {
+                pass = cls_pass[q];
+                t = cls_tier[q];
+                if (!pass) wl = pre[q]++;
+            }
+        if (!pass) {
+            B.worklist[c * G + wl] = b;
             continue;
         }
         if (!items_fit) continue;
-        const int t = pass_tier(B, c);
         const int nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
-        const int p0 = tier_base[0][t] + pre[kNumClasses + t];
-        const int c0 = tier_base[1][t] + pre[kNumClasses + kTiers + t];
         const int nsl = (cb.nz + B.slab - 1) / B.slab;
-        const int s0 = tier_base[2][t] + pre[kNumClasses + 2 * kTiers + t];
-        pre[kNumClasses + t] += cb.nz;
-        pre[kNumClasses + kTiers + t] += nch;
-        pre[kNumClasses + 2 * kTiers + t] += nsl;
+        int p0 = 0, c0 = 0, s0 = 0;
+#pragma unroll
+        for (int u = 0; u < kTiers; ++u)
+            if (u == t) {
+                p0 = tier_base[0][u] + pre[kNumClasses + u];
+                c0 = tier_base[1][u] + pre[kNumClasses + kTiers + u];
+                s0 = tier_base[2][u] + pre[kNumClasses + 2 * kTiers + u];
+                pre[kNumClasses + u] += cb.nz;
+                pre[kNumClasses + kTiers + u] += nch;
+                pre[kNumClasses + 2 * kTiers + u] += nsl;
+            }
         B.item_base[b] = make_int4(p0, c0, s0, t);    // the items themselves: k_write_items
     }
     // reduce cells / alive / tier cells in one pass

@@ -127,6 +127,7 @@ _SIGS = {
     "lsgg_server_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lsgg_server_destroy": (C.c_int, [C.c_void_p]),
     "lsgg_grain_neighbours": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32]),
+    "lsgg_keep_field": (C.c_int, [C.c_void_p, C.c_int32]),
     "lsgg_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_int32)]),
     "lsgg_pass_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lsgg_debug_set_capacity": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -395,6 +396,10 @@ def closest_gb_map(boxes_dev: int, n_boxes: int, phi_dev: int, idf_dev: int, n_e
     triangulated boundary point for every cell with |phi| < tube."""
     _check("closest_gb_map", lib().lsgg_closest_gb_map(boxes_dev, n_boxes, phi_dev, idf_dev, n_elems, tube, out_dev,
                                                         stream or None))
+
+
+def keep_field(ctx, on: bool = True):
+    _check("keep_field", lib().lsgg_keep_field(ctx, 1 if on else 0))
 
 
 def grain_neighbours(ctx, n_grains: int, cap: int = 96) -> list:

@@ -65,8 +65,8 @@ def test_step_roofline_arithmetic():
     """The whole-step roofline: the method's minimum bytes (8 B per box cell +
     44 B per domain cell in FP32; BF16 halves the state's bytes; physics adds
     the ID-field's read and write) and the five-pass design's (the pass bytes
-    summed: 8 + 8 + 8 + 8 + 8 = 40 B per box cell + 16 B per domain cell),
-    over the step time, against the peak."""
+    summed: 8 + 8 + 8 + 8 + 8 = 40 B per box cell, + 16 B per domain cell
+    when the top-two field is stored), over the step time, against the peak."""
     sys.path.insert(0, os.path.join(os.path.dirname(__file__), ".."))
     import bench
     r = bench.step_roofline(1.0e8, 1.0e7, 2.0, 5000.0, True)
@@ -75,7 +75,8 @@ def test_step_roofline_arithmetic():
     assert abs(r["frac_minimum"] - r["achieved_minimum_gbs"] / 5000.0) < 1e-15
     assert abs(r["minimum_bound_ms"] - 1.24e9 / 5e12 * 1e3) < 1e-12
     assert r["design_bytes_per_box_cell"] == 40.0
-    assert r["design_bytes_per_step"] == 4.0e9 + 1.6e8
+    assert r["design_bytes_per_step"] == 4.0e9
+    assert bench.step_roofline(1.0e8, 1.0e7, 2.0, 5000.0, True, keep_field=True)["design_bytes_per_step"] == 4.0e9 + 1.6e8
     assert "design_bytes_per_step" not in bench.step_roofline(1.0e8, 1.0e7, 2.0, 5000.0, False)
     assert bench.step_roofline(1.0e8, 0.0, 2.0, 5000.0, False, state_bytes=2)["minimum_bytes_per_step"] == 4.0e8
     assert bench.step_roofline(1.0e8, 0.0, 2.0, 5000.0, False, physics=True)["minimum_bytes_per_step"] == 1.6e9
@@ -84,14 +85,17 @@ def test_step_roofline_arithmetic():
 def test_kernel_roofline_takes_the_longest_launch():
     """The dominant pass is the one with the longest time per launch; the
     field pass counts one read of phi_p and one write of phi_c per box cell
-    plus 16 B per domain cell, a tier pass 8 B per box cell of its tier."""
+    (plus 16 B per domain cell when it stores the top-two field), a tier pass
+    8 B per box cell of its tier."""
     sys.path.insert(0, os.path.join(os.path.dirname(__file__), ".."))
     import bench
     tiers = [4.0e7, 6.0e7, 0, 0, 0]
     r = bench.kernel_roofline({"p_field": 0.5, "p_redist_xy[tier1]": 0.4, "k_bin": 0.01}, tiers, 1.0e8, 1.6e7,
                               5000, 6800.0)
     assert r["kernel"] == "p_field"
-    assert r["algorithmic_bytes_per_launch"] == 8.0 * 1.0e8 + 16.0 * 1.6e7
+    assert r["algorithmic_bytes_per_launch"] == 8.0 * 1.0e8
+    rk = bench.kernel_roofline({"p_field": 0.5}, tiers, 1.0e8, 1.6e7, 5000, 6800.0, keep_field=True)
+    assert rk["algorithmic_bytes_per_launch"] == 8.0 * 1.0e8 + 16.0 * 1.6e7
     assert abs(r["frac"] - r["algorithmic_bytes_per_launch"] / 0.5e-3 / 1e9 / 6800.0) < 1e-12
     r = bench.kernel_roofline({"p_field": 0.3, "p_redist_xy[tier1]": 0.4}, tiers, 1.0e8, 1.6e7, 5000, 6800.0)
     assert r["kernel"] == "p_redist_xy[tier1]" and r["units_per_launch"] == 6.0e7

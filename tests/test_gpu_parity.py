@@ -256,6 +256,10 @@ def test_grain_neighbours_are_the_id_field(L):
     seeds = I.voronoi_seeds(23, G, (N, N, N))
     with L.Microstructure(N, N, N, G, seeds=seeds) as ms:
         ms.step(2, 1.0)
+        with pytest.raises(L.LsggError) as e:      # the pass path keeps the field only on request
+            L.grain_neighbours(ms.ctx, G)
+        assert e.value.code == L.ERR_NOT_READY
+        L.keep_field(ms.ctx, True)
         _, (phip, m, idm, phic, phin) = ms.debug_step(1.0)
         nb = L.grain_neighbours(ms.ctx, G)
     for g in phin:
