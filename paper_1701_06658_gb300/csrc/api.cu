@@ -538,6 +538,8 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if ((r = dalloc(c, &c->B.bounds, (size_t)G)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.st, 1)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.worklist, (size_t)kNumClasses * G)) != LSGG_OK) return bail(r);
+    if ((r = dalloc(c, &c->B.bu_part, ((size_t)(G + kBuChunk - 1) / kBuChunk + 1) * kBuVals)) != LSGG_OK)
+        return bail(r);
     if ((r = dalloc(c, &c->d_vol, (size_t)G)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->d_packed_off, (size_t)G + 1)) != LSGG_OK) return bail(r);
     if ((r = dalloc(c, &c->B.T, 2 * (size_t)ncell)) != LSGG_OK) return bail(r);

@@ -11,7 +11,8 @@ namespace lsgg {
 
 // The lists a kernel walks: plane, column-chunk or slab items of a tier, the
 // boxes, the domain tiles.
-enum : int { kItemPlanes = 0, kItemChunks = 1, kItemSlabs = 2, kItemBoxes = 3, kItemTiles = 4 };
+enum : int { kItemPlanes = 0, kItemChunks = 1, kItemSlabs = 2, kItemBoxes = 3, kItemTiles = 4, kItemBoxChunks = 5,
+             kItemBoxChunksGo = 6 };
 
 __device__ __forceinline__ int list_count(const StepBuffers& B, int list, int tier) {
     switch (list) {
@@ -19,6 +20,8 @@ __device__ __forceinline__ int list_count(const StepBuffers& B, int list, int ti
         case kItemChunks: return B.st->n_chunks[tier];
         case kItemSlabs: return B.st->n_slabs[tier];
         case kItemBoxes: return B.n_boxes;
+        case kItemBoxChunks: return (B.n_boxes + kBuChunk - 1) / kBuChunk;
+        case kItemBoxChunksGo: return B.st->bu_go ? (B.n_boxes + kBuChunk - 1) / kBuChunk : 0;
         default: return B.n_tiles;
     }
 }

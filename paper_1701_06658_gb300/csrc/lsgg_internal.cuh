@@ -114,7 +114,15 @@ struct StepState {                  // device-resident control block
     int n_slabs[kTiers];            // pass path: slab items (kSlab planes) per tier
     int slab_base[kTiers];
     long long step_limit;           // step groups: the member takes part while steps_done < step_limit
+    int bu_go;                      // the step's box update places offsets and items (set by its scan)
 };
+
+// The step's box update runs as three grid launches over chunks of
+// kBuChunk boxes: new boxes and per-chunk sums of kBuVals values, a scan of
+// the chunk sums (one CTA per context), then every box's arena offset and
+// work-item bases.
+constexpr int kBuChunk = 256;
+constexpr int kBuVals = 4 + kNumClasses + 4 * kTiers;
 
 __host__ __device__ inline int plane_stride(int nx, int ny) { return (nx * ny + 7) & ~7; }
 __host__ __device__ inline long long box_elems(const Box& b) {
@@ -196,6 +204,7 @@ struct StepBuffers {
     int pgrid[kTiers][5];           // persistent grid per tier and pass (conv_xy, conv_z ideal, conv_z physics, redist_xy, redist_z)
     int pocc[kTiers][5];            // resident CTAs per SM of those kernels (the grids' upper bound)
     int slab;                       // planes per slab item of p_redist_xy (kSlab unless autotuned)
+    long long* bu_part;             // box update: per chunk of kBuChunk boxes kBuVals sums, then their bases
     // field pass: boxes overlapping each domain tile of kTileX x kTileY x kTileZ cells
     int* tile_cnt;                  // [n_tiles]
     int* tile_list;                 // [n_tiles * kTileCap]

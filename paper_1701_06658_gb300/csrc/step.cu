@@ -497,6 +497,38 @@ __device__ __forceinline__ int pass_tier(const StepBuffers& B, int c) {
     return kTiers - 1;
 }
 
+// The box after a step (Secs. 2.1.3, 3.1, reading R6): the bbox of the
+// positive cells the re-initialisation collected (box-local bounds bd), grown
+// by the halo; an axis reaching the domain becomes full and keeps its origin
+// while full; no positive cell: extinct (nx = 0).
+__device__ __forceinline__ Box updated_box(const Box& cb, const Bounds& bd, const Domain& D) {
+    Box n = cb;
+    if (bd.hi[0] < bd.lo[0]) {
+        n.nx = n.ny = n.nz = 0;
+        return n;
+    }
+    const int Ns[3] = {D.nx, D.ny, D.nz};
+    const int os[3] = {cb.ox, cb.oy, cb.oz};
+    const int ns[3] = {cb.nx, cb.ny, cb.nz};
+    int no[3], nn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a == 2 && D.dim == 2) { no[a] = 0; nn[a] = 1; continue; }
+        const int ext = bd.hi[a] - bd.lo[a] + 1 + 2 * D.halo;
+        const bool was_full = ns[a] == Ns[a];
+        if (ext >= Ns[a]) {
+            nn[a] = Ns[a];
+            no[a] = was_full ? os[a] : pmod(os[a] + bd.lo[a] - D.halo, Ns[a]);
+        } else {
+            nn[a] = ext;
+            no[a] = pmod(os[a] + bd.lo[a] - D.halo, Ns[a]);
+        }
+    }
+    n.ox = no[0]; n.oy = no[1]; n.oz = no[2];
+    n.nx = nn[0]; n.ny = nn[1]; n.nz = nn[2];
+    return n;
+}
+
 // layout_only: offsets and work items for the `cur` boxes as they are;
 // otherwise the boxes follow the bounds collected by the re-initialisation,
 // and count_step adds the step to the step and cell-update counters (not for
@@ -520,33 +552,7 @@ k_box_update(StepBuffers B1, GroupRef grp, int layout_only, int count_step) {
         Box cb = B.cur[b];
         if (cb.nx > 0) done += (long long)cb.nx * cb.ny * cb.nz;
         if (!layout_only) {
-            Box n = cb;
-            if (cb.nx > 0) {
-                Bounds bd = B.bounds[b];
-                if (bd.hi[0] < bd.lo[0]) {
-                    n.nx = n.ny = n.nz = 0;          // extinct: no positive cell
-                } else {
-                    int Ns[3] = {D.nx, D.ny, D.nz};
-                    int os[3] = {cb.ox, cb.oy, cb.oz};
-                    int ns[3] = {cb.nx, cb.ny, cb.nz};
-                    int no[3], nn[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        if (a == 2 && D.dim == 2) { no[a] = 0; nn[a] = 1; continue; }
-                        int ext = bd.hi[a] - bd.lo[a] + 1 + 2 * D.halo;
-                        bool was_full = ns[a] == Ns[a];
-                        if (ext >= Ns[a]) {
-                            nn[a] = Ns[a];
-                            no[a] = was_full ? os[a] : pmod(os[a] + bd.lo[a] - D.halo, Ns[a]);
-                        } else {
-                            nn[a] = ext;
-                            no[a] = pmod(os[a] + bd.lo[a] - D.halo, Ns[a]);
-                        }
-                    }
-                    n.ox = no[0]; n.oy = no[1]; n.oz = no[2];
-                    n.nx = nn[0]; n.ny = nn[1]; n.nz = nn[2];
-                }
-            }
+            const Box n = cb.nx > 0 ? updated_box(cb, B.bounds[b], D) : cb;
             B.prev[b] = cb;
             B.cur[b] = n;
             cb = n;
@@ -841,10 +847,270 @@ k_write_items(StepBuffers B1, GroupRef grp) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// the step's box update over the whole GPU
+// ---------------------------------------------------------------------------
+// The values a box contributes (kBuVals): arena elements of its new box, its
+// cells before the update (the step's cell-updates), its cells and 1 if
+// alive, one box for its size class, and on the pass path its planes, column
+// chunks, slabs and cells for its tier.
+enum : int { kVElems = 0, kVDone = 1, kVCells = 2, kVAlive = 3, kVCls = 4, kVPl = kVCls + kNumClasses,
+             kVCh = kVPl + kTiers, kVSl = kVCh + kTiers, kVTc = kVSl + kTiers };
+static_assert(kVTc + kTiers == kBuVals, "one layout of the box update's values");
+
+__device__ __forceinline__ void box_values(const StepBuffers& B, const Box& cb, const Box& pb, long long done,
+                                           long long (&v)[kBuVals], int& cls, int& pass, int& tier) {
+#pragma unroll
+    for (int q = 0; q < kBuVals; ++q) v[q] = 0;
+    v[kVElems] = box_elems(cb);
+    v[kVDone] = done;
+    cls = 0; pass = 0; tier = 0;
+    if (cb.nx <= 0) return;
+    const long long vol = (long long)cb.nx * cb.ny * cb.nz;
+    v[kVCells] = vol;
+    v[kVAlive] = 1;
+    cls = box_class(B, cb, pb);
+#pragma unroll
+    for (int q = 0; q < kNumClasses; ++q)
+        if (q == cls) {
+            v[kVCls + q] = 1;
+            pass = B.mode[q] == 3;
+            tier = pass_tier(B, q);
+        }
+    if (!pass) return;
+    const long long nch = (cb.nx * cb.ny + kPassChunk - 1) / kPassChunk;
+    const long long nsl = (cb.nz + B.slab - 1) / B.slab;
+#pragma unroll
+    for (int u = 0; u < kTiers; ++u)
+        if (u == tier) {
+            v[kVPl + u] = cb.nz;
+            v[kVCh + u] = nch;
+            v[kVSl + u] = nsl;
+            v[kVTc + u] = vol;
+        }
+}
+
+// Block-wide exclusive scan of N long longs per thread (thread order):
+// pre = sum over lower threads; s: (blockDim / 32) * N long longs.
+template <int N>
+__device__ __forceinline__ void block_exclusive_scan_ll(const long long (&v)[N], long long (&pre)[N], long long* s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        long long x = v[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        pre[k] = x - v[k];
+        if (lane == 31) s[warp * N + k] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            long long x = lane < nw ? s[lane * N + k] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < nw) s[lane * N + k] = x;       // inclusive prefix over warps
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) pre[k] += warp ? s[(warp - 1) * N + k] : 0;
+    __syncthreads();
+}
+
+// 1. New boxes and per-chunk sums (a CTA per chunk of kBuChunk boxes).
+template <bool GRP>
+__global__ void __launch_bounds__(kBuChunk)
+k_bu_new(StepBuffers B1, GroupRef grp) {
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
+    __shared__ long long s_red[32 * kBuVals];
+    const int n_all = GRP ? group_scan(grp, kItemBoxChunks, 0, true, s_gb)
+                          : (*(volatile int*)&B1.st->halt ? 0 : (B1.n_boxes + kBuChunk - 1) / kBuChunk);
+    for (int gc = blockIdx.x; gc < n_all; gc += gridDim.x) {
+        int k;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, gc, k);
+        const int b = k * kBuChunk + threadIdx.x;
+        long long v[kBuVals];
+        int cls, pass, tier;
+        if (b < B.n_boxes) {
+            const Box cb = B.cur[b];
+            const Box n = cb.nx > 0 ? updated_box(cb, B.bounds[b], B.dom) : cb;
+            B.prev[b] = cb;
+            B.cur[b] = n;
+            box_values(B, n, cb, cb.nx > 0 ? (long long)cb.nx * cb.ny * cb.nz : 0, v, cls, pass, tier);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kBuVals; ++q) v[q] = 0;
+        }
+        block_sums_ll<kBuVals>(v, s_red);
+#pragma unroll
+        for (int q = 0; q < kBuVals; ++q)
+            if (threadIdx.x == q) B.bu_part[(long long)k * kBuVals + q] = v[q];
+    }
+}
+
+// 2. The chunk sums scanned into chunk bases (in place), the totals checked
+// against the arena and the work-item lists, the step's counters (one CTA per
+// context; in a group, CTA k for member k).
+constexpr int kBuScanThreads = 128;     // the chunk sums of a context are few (one per 256 boxes)
+
+template <bool GRP>
+__global__ void __launch_bounds__(kBuScanThreads)
+k_bu_scan(StepBuffers B1, GroupRef grp, int count_step) {
+    __shared__ long long s_red[32 * kBuVals];
+    const StepBuffers& B = GRP ? grp.B[blockIdx.x] : B1;
+    const bool live = GRP ? group_live(B, true) : *(volatile int*)&B.st->halt == 0;
+    if (!live) {
+        if (threadIdx.x == 0) B.st->bu_go = 0;
+        return;
+    }
+    const int nch = (B.n_boxes + kBuChunk - 1) / kBuChunk;
+    const int per = (nch + blockDim.x - 1) / blockDim.x;
+    const int c0 = min(nch, (int)threadIdx.x * per), c1 = min(nch, c0 + per);
+    long long v[kBuVals], pre[kBuVals];
+#pragma unroll
+    for (int q = 0; q < kBuVals; ++q) v[q] = 0;
+    for (int c = c0; c < c1; ++c)
+#pragma unroll
+        for (int q = 0; q < kBuVals; ++q) v[q] += B.bu_part[(long long)c * kBuVals + q];
+    block_exclusive_scan_ll<kBuVals>(v, pre, s_red);
+    for (int c = c0; c < c1; ++c)                    // chunk sums -> chunk bases
+#pragma unroll
+        for (int q = 0; q < kBuVals; ++q) {
+            long long* e = B.bu_part + (long long)c * kBuVals + q;
+            const long long x = *e;
+            *e = pre[q];
+            pre[q] += x;
+        }
+    // totals: the last thread's running prefix
+    __shared__ long long s_tot[kBuVals];
+    if (threadIdx.x == blockDim.x - 1)
+#pragma unroll
+        for (int q = 0; q < kBuVals; ++q) s_tot[q] = pre[q];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    StepState* st = B.st;
+    if (count_step) {
+        st->cell_updates += s_tot[kVDone];
+        st->steps_done += 1;                          // the step's fields are complete
+    }
+    if (s_tot[kVElems] > B.cap) {
+        st->status = LSGG_ERR_CAPACITY;
+        st->halt = 1;
+        st->box_cells = s_tot[kVElems];
+        st->bu_go = 0;
+        return;
+    }
+    long long kind_total[3];
+#pragma unroll
+    for (int kd = 0; kd < 3; ++kd) {
+        long long acc = 0;
+#pragma unroll
+        for (int t = 0; t < kTiers; ++t) {
+            if (kd == 0) st->plane_base[t] = (int)acc;
+            if (kd == 1) st->chunk_base[t] = (int)acc;
+            if (kd == 2) st->slab_base[t] = (int)acc;
+            acc += s_tot[kVPl + kd * kTiers + t];
+        }
+        kind_total[kd] = acc;
+    }
+    const bool items_fit = kind_total[0] <= B.plane_item_cap && kind_total[1] <= B.chunk_item_cap &&
+                           kind_total[2] <= B.slab_item_cap;
+    st->box_cells = s_tot[kVCells];
+    st->alive = s_tot[kVAlive];
+#pragma unroll
+    for (int q = 0; q < kNumClasses; ++q) {
+        st->class_count[q] = (int)s_tot[kVCls + q];
+        st->queue[0][q] = 0;
+        st->queue[1][q] = 0;
+    }
+#pragma unroll
+    for (int t = 0; t < kTiers; ++t) {
+        st->n_planes[t] = items_fit ? (int)s_tot[kVPl + t] : 0;
+        st->n_chunks[t] = items_fit ? (int)s_tot[kVCh + t] : 0;
+        st->n_slabs[t] = items_fit ? (int)s_tot[kVSl + t] : 0;
+        st->tier_cells[t] = s_tot[kVTc + t];
+    }
+    if (!items_fit) { st->status = LSGG_ERR_UNSUPPORTED; st->halt = 1; }   // not reached: caps are bounds
+    st->bu_go = items_fit ? 1 : 0;
+}
+
+// 3. Every box's arena offset, work-list entry and work-item bases: the
+// chunk base plus the box's exclusive prefix within its chunk.
+template <bool GRP>
+__global__ void __launch_bounds__(kBuChunk)
+k_bu_place(StepBuffers B1, GroupRef grp) {
+    __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
+    __shared__ long long s_scan[(kBuChunk / 32) * kBuVals];
+    const int n_all = GRP ? group_scan(grp, kItemBoxChunksGo, 0, false, s_gb)
+                          : (B1.st->bu_go ? (B1.n_boxes + kBuChunk - 1) / kBuChunk : 0);
+    for (int gc = blockIdx.x; gc < n_all; gc += gridDim.x) {
+        int k;
+        const StepBuffers& B = member<GRP>(B1, grp, s_gb, gc, k);
+        const int b = k * kBuChunk + threadIdx.x;
+        long long v[kBuVals], pre[kBuVals];
+        int cls = 0, pass = 0, tier = 0;
+        Box cb{};
+        if (b < B.n_boxes) {
+            cb = B.cur[b];
+            box_values(B, cb, B.prev[b], 0, v, cls, pass, tier);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kBuVals; ++q) v[q] = 0;
+        }
+        block_exclusive_scan_ll<kBuVals>(v, pre, s_scan);
+        if (b >= B.n_boxes) continue;
+        const long long* base = B.bu_part + (long long)k * kBuVals;
+        B.cur[b].off = base[kVElems] + pre[kVElems];
+        if (cb.nx <= 0) {
+            if (B.use_passes) B.item_base[b] = make_int4(0, 0, 0, -1);
+            continue;
+        }
+        if (!pass) {
+            long long pos = 0;
+#pragma unroll
+            for (int q = 0; q < kNumClasses; ++q)
+                if (q == cls) pos = base[kVCls + q] + pre[kVCls + q];
+            B.worklist[cls * B.n_boxes + pos] = b;
+            if (B.use_passes) B.item_base[b] = make_int4(0, 0, 0, -1);
+            continue;
+        }
+        int p0 = 0, c0 = 0, s0 = 0;
+#pragma unroll
+        for (int u = 0; u < kTiers; ++u)
+            if (u == tier) {
+                p0 = B.st->plane_base[u] + (int)(base[kVPl + u] + pre[kVPl + u]);
+                c0 = B.st->chunk_base[u] + (int)(base[kVCh + u] + pre[kVCh + u]);
+                s0 = B.st->slab_base[u] + (int)(base[kVSl + u] + pre[kVSl + u]);
+            }
+        B.item_base[b] = make_int4(p0, c0, s0, tier);   // the items themselves: k_write_items
+    }
+}
+
 cudaError_t launch_box_update(const StepBuffers& B, bool layout_only, cudaStream_t s, bool count_step) {
     const GroupRef none{nullptr, 0};
-    k_box_update<false><<<1, kBoxUpdateThreads, 0, s>>>(B, none, layout_only ? 1 : 0, count_step ? 1 : 0);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (layout_only) {
+        k_box_update<false><<<1, kBoxUpdateThreads, 0, s>>>(B, none, 1, 0);
+    } else {
+        const int nch = (B.n_boxes + kBuChunk - 1) / kBuChunk;
+        const int grid = nch < 4 * B.n_sm ? nch : 4 * B.n_sm;
+        k_bu_new<false><<<grid, kBuChunk, 0, s>>>(B, none);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_bu_scan<false><<<1, kBuScanThreads, 0, s>>>(B, none, count_step ? 1 : 0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_bu_place<false><<<grid, kBuChunk, 0, s>>>(B, none);
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess || !B.use_passes) return e;
     k_write_items<false><<<B.n_sm * 4, 256, 0, s>>>(B, none);
     return cudaGetLastError();
@@ -908,8 +1174,16 @@ cudaError_t launch_group_step(const StepBuffers& B0, const GroupRef& grp, const 
     e = traced(launch_field_group(B0, grp, s), "group field pass");
     if (e == cudaSuccess) e = tiers(1);
     if (e != cudaSuccess) return e;
-    k_box_update<true><<<grp.n, kBoxUpdateThreads, 0, s>>>(B0, grp, 0, 1);
+    k_bu_new<true><<<4 * B0.n_sm, kBuChunk, 0, s>>>(B0, grp);
     e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_bu_scan<true><<<grp.n, kBuScanThreads, 0, s>>>(B0, grp, 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_bu_place<true><<<4 * B0.n_sm, kBuChunk, 0, s>>>(B0, grp);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return traced(e, "group box update");
     k_write_items<true><<<B0.n_sm * 4, 256, 0, s>>>(B0, grp);
     return traced(cudaGetLastError(), "group work items");
