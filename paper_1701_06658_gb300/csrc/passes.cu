@@ -201,41 +201,48 @@ p_conv_xy(StepBuffers B1, GroupRef grp, Taps taps, int tier) {
     float g[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) g[k] = taps.g[k];
-    const int n_items = GRP ? group_scan(grp, kItemPlanes, tier, true, s_gb) : B1.st->n_planes[tier];
-    const int2* items = GRP ? nullptr : B1.plane_items + B1.st->plane_base[tier];
+    const int n_items = GRP ? group_scan(grp, kItemSlabs, tier, true, s_gb) : B1.st->n_slabs[tier];
+    const int2* items = GRP ? nullptr : B1.slab_items + B1.st->slab_base[tier];
     uint32_t phase = 0;
-    // the first item's plane
     bool pending = false;
-    if (blockIdx.x < n_items) {
+    // bulk copy of plane z of box it.x in its previous layout into raw (none
+    // when the plane lies outside the old box)
+    auto fetch = [&](const StepBuffers& Bx, int2 itx, int z) {
         const float* src;
         uint32_t bytes;
-        int lf;
-        const StepBuffers& Bf = member<GRP>(B1, grp, s_gb, blockIdx.x, lf);
-        conv_source(Bf, list_item<GRP>(Bf, items, kItemPlanes, tier, blockIdx.x, lf), &src, &bytes);
+        conv_source(Bx, make_int2(itx.x, z), &src, &bytes);
         if (bytes) {
             if (t == 0) {
+                fence_async_smem();                     // earlier generic accesses to raw come first
                 mbar_expect(bar, bytes);
                 bulk_load(raw, src, bytes, bar);
             }
             pending = true;
         }
+    };
+    if (blockIdx.x < n_items) {                         // the first item's first plane
+        int lf;
+        const StepBuffers& Bf = member<GRP>(B1, grp, s_gb, blockIdx.x, lf);
+        const int2 itf = list_item<GRP>(Bf, items, kItemSlabs, tier, blockIdx.x, lf);
+        fetch(Bf, itf, itf.y);
     }
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         int local;
         const StepBuffers& B = member<GRP>(B1, grp, s_gb, item, local);
         const Domain D = GRP ? B.dom : D1;
-        const int2 it = list_item<GRP>(B, items, kItemPlanes, tier, item, local);
-        const int b = it.x, z = it.y;
+        const int2 it = list_item<GRP>(B, items, kItemSlabs, tier, item, local);
+        const int b = it.x, z0 = it.y;
         const Box nb = B.cur[b], ob = B.prev[b];
         const int nx = nb.nx, ny = nb.ny;
         const bool fx = nx == D.nx, fy = ny == D.ny;
         const int PXa = nx + 2 * R, PYa = ny + 2 * R;
-        const bool have = pending;
+        const int z1 = min(z0 + B.slab, nb.nz);
         if (max(max(nx, ny), max(ob.nx, ob.ny)) > SIDE) {    // not this tier's box: refuse, never overrun
             if (t == 0) { atomicExch(&B.st->status, LSGG_ERR_UNSUPPORTED); atomicExch(&B.st->halt, 1); }
-            if (have) { if (t == 0) mbar_wait(bar, phase); }
+            if (pending) { if (t == 0) mbar_wait(bar, phase); }
             return;
         }
+        // the new-to-old layout maps of the item's box (the same for all its planes)
         for (int i = t; i < LY::MX + PYa; i += NT) {
             const bool isx = i < LY::MX;
             const int ip = isx ? i : i - LY::MX;
@@ -250,101 +257,94 @@ p_conv_xy(StepBuffers B1, GroupRef grp, Taps taps, int tier) {
             }
             if (isx) mapx[ip] = v; else mapy[ip] = v;
         }
-        bool ok = true;
-        if (pending) {
-            ok = mbar_wait(bar, phase, B.wait_limit);
-            if (ok) phase ^= 1u;
-        }
-        if (!__syncthreads_and(ok)) {                       // also publishes the maps
-            if (t == 0) {
-                atomicExch(&B.st->status, LSGG_ERR_TIMEOUT);
-                atomicExch(&B.st->halt, 1);
-                mbar_wait(bar, phase);
+        __syncthreads();                                    // the maps are published
+        for (int z = z0; z < z1; ++z) {
+            const bool have = pending;
+            bool ok = true;
+            if (pending) {
+                ok = mbar_wait(bar, phase, B.wait_limit);
+                if (ok) phase ^= 1u;
             }
-            __syncthreads();
-            return;
-        }
-        pending = false;
-        // stage: raw (old layout, FP32 or BF16) -> P (new layout), warp per padded row
-        if (have) {
-            if (B.bf16) stage_plane<NT, LY::PX>(reinterpret_cast<const __nv_bfloat16*>(raw), P, mapx, mapy, PXa, PYa,
-                                                ob.nx, -D.eps, t);
-            else stage_plane<NT, LY::PX>(raw, P, mapx, mapy, PXa, PYa, ob.nx, -D.eps, t);
-        }
-        __syncthreads();                                    // raw is free: fetch the next item's plane
-        if (item + (int)gridDim.x < n_items) {
-            const float* src;
-            uint32_t bytes;
-            if constexpr (GRP) {
+            if (!__syncthreads_and(ok)) {
+                if (t == 0) {
+                    atomicExch(&B.st->status, LSGG_ERR_TIMEOUT);
+                    atomicExch(&B.st->halt, 1);
+                    mbar_wait(bar, phase);
+                }
+                __syncthreads();
+                return;
+            }
+            pending = false;
+            // stage: raw (old layout, FP32 or BF16) -> P (new layout), warp per padded row
+            if (have) {
+                if (B.bf16) stage_plane<NT, LY::PX>(reinterpret_cast<const __nv_bfloat16*>(raw), P, mapx, mapy, PXa, PYa,
+                                                    ob.nx, -D.eps, t);
+                else stage_plane<NT, LY::PX>(raw, P, mapx, mapy, PXa, PYa, ob.nx, -D.eps, t);
+            }
+            __syncthreads();                                // raw is free: fetch the next plane
+            if (z + 1 < z1) {
+                fetch(B, it, z + 1);
+            } else if (item + (int)gridDim.x < n_items) {
                 const int nxt = item + gridDim.x;
                 int ln;
                 const StepBuffers& Bn = member<GRP>(B1, grp, s_gb, nxt, ln);
-                conv_source(Bn, list_item<GRP>(Bn, items, kItemPlanes, tier, nxt, ln), &src, &bytes);
-            } else {
-                conv_source(B1, items[item + gridDim.x], &src, &bytes);
+                const int2 itn = list_item<GRP>(Bn, items, kItemSlabs, tier, nxt, ln);
+                fetch(Bn, itn, itn.y);
             }
-            if (bytes) {
-                if (t == 0) {
-                    fence_async_smem();
-                    mbar_expect(bar, bytes);
-                    bulk_load(raw, src, bytes, bar);
+            // x pass: (padded row, group of 4 outputs)
+            const int ngx = (nx + 3) >> 2;
+            {
+                const Div16 dgx(ngx);
+                float cfill = 0.0f;
+    #pragma unroll
+                for (int k = 0; k < W; ++k) cfill = fmaf(g[k], -D.eps, cfill);
+                for (int j = t; j < PYa * ngx; j += NT) {
+                    const int yp = dgx(j), x0 = 4 * (j - yp * ngx);
+                    if (!have || mapy[yp] < 0) {                // a fill row: the chain over -eps, unstaged
+                        *reinterpret_cast<float4*>(XC + yp * LY::XP + x0) = make_float4(cfill, cfill, cfill, cfill);
+                        continue;
+                    }
+                    const float4* r4 = reinterpret_cast<const float4*>(P + yp * LY::PX + x0);
+                    float v[4 * LY::NQ];
+    #pragma unroll
+                    for (int q = 0; q < LY::NQ; ++q) {
+                        const float4 a = r4[q];
+                        v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+                    }
+                    float o[4];
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float acc = 0.0f;
+    #pragma unroll
+                        for (int k = 0; k < W; ++k) acc = fmaf(g[k], v[u + k], acc);
+                        o[u] = acc;
+                    }
+                    *reinterpret_cast<float4*>(XC + yp * LY::XP + x0) = make_float4(o[0], o[1], o[2], o[3]);
                 }
-                pending = true;
             }
+            __syncthreads();
+            // y pass: (group of 4 rows, column), lanes along x
+            {
+                float* dst = B.Z + nb.off + (long long)z * plane_stride(nx, ny);
+                const int ngy = (ny + 3) >> 2;
+                const Div16 dnx(nx);
+                for (int j = t; j < ngy * nx; j += NT) {
+                    const int gy = dnx(j), x = j - gy * nx, y0 = 4 * gy;
+                    const float* col = XC + y0 * LY::XP + x;
+                    float v[W + 3];
+    #pragma unroll
+                    for (int k = 0; k < W + 3; ++k) v[k] = col[k * LY::XP];
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float acc = 0.0f;
+    #pragma unroll
+                        for (int k = 0; k < W; ++k) acc = fmaf(g[k], v[u + k], acc);
+                        if (y0 + u < ny) dst[(y0 + u) * nx + x] = acc;
+                    }
+                }
+            }
+            __syncthreads();                                // XC is free
         }
-        // x pass: (padded row, group of 4 outputs)
-        const int ngx = (nx + 3) >> 2;
-        {
-            const Div16 dgx(ngx);
-            float cfill = 0.0f;
-#pragma unroll
-            for (int k = 0; k < W; ++k) cfill = fmaf(g[k], -D.eps, cfill);
-            for (int j = t; j < PYa * ngx; j += NT) {
-                const int yp = dgx(j), x0 = 4 * (j - yp * ngx);
-                if (!have || mapy[yp] < 0) {                // a fill row: the chain over -eps, unstaged
-                    *reinterpret_cast<float4*>(XC + yp * LY::XP + x0) = make_float4(cfill, cfill, cfill, cfill);
-                    continue;
-                }
-                const float4* r4 = reinterpret_cast<const float4*>(P + yp * LY::PX + x0);
-                float v[4 * LY::NQ];
-#pragma unroll
-                for (int q = 0; q < LY::NQ; ++q) {
-                    const float4 a = r4[q];
-                    v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
-                }
-                float o[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < W; ++k) acc = fmaf(g[k], v[u + k], acc);
-                    o[u] = acc;
-                }
-                *reinterpret_cast<float4*>(XC + yp * LY::XP + x0) = make_float4(o[0], o[1], o[2], o[3]);
-            }
-        }
-        __syncthreads();
-        // y pass: (group of 4 rows, column), lanes along x
-        {
-            float* dst = B.Z + nb.off + (long long)z * plane_stride(nx, ny);
-            const int ngy = (ny + 3) >> 2;
-            const Div16 dnx(nx);
-            for (int j = t; j < ngy * nx; j += NT) {
-                const int gy = dnx(j), x = j - gy * nx, y0 = 4 * gy;
-                const float* col = XC + y0 * LY::XP + x;
-                float v[W + 3];
-#pragma unroll
-                for (int k = 0; k < W + 3; ++k) v[k] = col[k * LY::XP];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < W; ++k) acc = fmaf(g[k], v[u + k], acc);
-                    if (y0 + u < ny) dst[(y0 + u) * nx + x] = acc;
-                }
-            }
-        }
-        __syncthreads();                                    // XC and the maps are free
     }
 }
 
