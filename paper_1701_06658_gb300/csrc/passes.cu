@@ -686,12 +686,15 @@ p_field(StepBuffers B1, GroupRef grp, PhysicsDev phys, DebugOut dbg) {
             }
             for (int base = 0; base < n_total; base += kTileCap) {
                 const int nb = min(kTileCap, n_total - base);
-                __syncthreads();                    // previous batch done with s_tb
-                for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-                    const int b = all ? base + k : B.tile_list[(long long)tile * kTileCap + k];
-                    stage_tile_box(B, b, tx0, ty0, z0, ext_x, ext_y, nzt, s_tb[k]);
+                // one batch (the tile's whole list): the first sweep's staging serves both
+                if (sweep == 0 || n_total > kTileCap) {
+                    __syncthreads();                // previous batch done with s_tb
+                    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+                        const int b = all ? base + k : B.tile_list[(long long)tile * kTileCap + k];
+                        stage_tile_box(B, b, tx0, ty0, z0, ext_x, ext_y, nzt, s_tb[k]);
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
                 if (!col) continue;
                 for (int k = 0; k < nb; ++k) {
                     const TileBox& t = s_tb[k];
