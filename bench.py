@@ -45,6 +45,8 @@ WORKLOADS = {
     # magnetically driven growth: random c-axes, field (0, cos 32, sin 32), bulk
     # energy B^2 dchi cos^2 / (2 mu0) in grid units (4.07e-3 at cos^2 = 1)
     "384mag": {"n": 384, "grains": 10000, "seed": 4, "dt": 1.0, "physics": "magnetic", "energy_scale": 4.07e-3},
+    # small case of the magnetic workload for profilers (the grain density of the 256^3 workload)
+    "160mag": {"n": 160, "grains": 1221, "seed": 4, "dt": 1.0, "physics": "magnetic", "energy_scale": 4.07e-3},
 }
 WORKLOAD = dict(WORKLOADS["256"])
 SAMPLE = {"n": 64, "grains": 78, "seed": 2}     # same density: 64^3 / 78 = 3361 cells per grain
@@ -888,7 +890,7 @@ def main():
     ap.add_argument("--redist", default="taxicab", choices=["taxicab", "godunov"],
                     help="re-initialisation metric: the paper's taxicab propagation or the Godunov update")
     ap.add_argument("--workload", default="256", choices=sorted(WORKLOADS),
-                    help="256: the benchmark workload; 160: a small case of the same density for profilers; "
+                    help="256: the benchmark workload; 160, 160mag: small cases for profilers; "
                          "512rs, 384mag: the non-ideal and magnetic workloads")
     args = ap.parse_args()
     WORKLOAD.clear()
