@@ -74,7 +74,7 @@ def measured_peaks():
 # the sources the pass kernels are compiled from: their file and every header
 # it includes
 PASS_KERNEL_SOURCES = ("paper_1701_06658_gb300/csrc/passes.cu", "paper_1701_06658_gb300/csrc/bulk_copy.cuh",
-                       "paper_1701_06658_gb300/csrc/kernels_common.cuh",
+                       "paper_1701_06658_gb300/csrc/kernels_common.cuh", "paper_1701_06658_gb300/csrc/group.cuh",
                        "paper_1701_06658_gb300/csrc/lsgg_internal.cuh", "include/lsgg.h")
 
 
