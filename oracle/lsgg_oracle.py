@@ -116,6 +116,16 @@ code where it applies):
      weights (``Physics.gb_map_tube``).  Box-local: the cubes are those between the box's own cells (a
      full periodic axis is not wrapped; a box with an axis of one cell has
      none, and then the map is the ID-field).
+  R17 initialisation from a label field (a tessellation read from a file,
+     the paper's input form, Sec. 3.1; the paper gives no rule for it): grain
+     i's box is, per axis, the shortest cyclic interval of [0, N) holding
+     every label cell of i -- the complement of the longest run of positions
+     without one, the first such run counted from 0 on ties -- grown by the
+     halo (dims capped at N); its function is R5's re-initialisation of +1/2
+     on its label cells and -1/2 on the box's other cells (the zero level on
+     the faces between labels, reference cells at 1/2 / sqrt(crossings),
+     taxicab distances beyond).  The initial ID-field is, per cell, the other
+     grain with the largest function there above -eps (lowest id on ties).
 """
 from __future__ import annotations
 
@@ -982,6 +992,71 @@ def tessellate(shape, seeds, weights=None, eps=7.0, halo=5, radius=5, physics=No
 def labels_of_tessellation(shape, seeds, weights=None) -> np.ndarray:
     Nz, Ny, Nx = shape
     return labels_at(domain_cells(shape), np.asarray(seeds, dtype=np.float64), weights, (Nx, Ny, Nz))
+
+
+def label_arc(coords, n: int):
+    """Reading R17: the shortest cyclic interval of [0, n) that holds every
+    coordinate in ``coords`` -- the complement of the longest run of
+    positions holding none (the first such run counted from 0 on ties);
+    returns (start, length)."""
+    occ = np.zeros(n, dtype=bool)
+    occ[np.asarray(coords, dtype=np.int64) % n] = True
+    if occ.all():
+        return 0, n
+    best_start, best_len = 0, -1
+    for s in range(n):
+        if occ[s] or not occ[(s - 1) % n]:
+            continue                               # not the first position of an empty run
+        length = 0
+        while not occ[(s + length) % n]:
+            length += 1
+        if length > best_len:
+            best_start, best_len = s, length
+    return (best_start + best_len) % n, n - best_len
+
+
+def label_box(cells_zyx: np.ndarray, shape, halo: int):
+    """Reading R17: per axis the label arc of the grain's cells grown by the
+    halo (dims capped at the domain); returns origin and dims (z, y, x)."""
+    origin, dims = [0, 0, 0], [1, 1, 1]
+    for a in range(3):
+        n = int(shape[a])
+        if n == 1:
+            continue
+        start, length = label_arc(cells_zyx[:, a], n)
+        dims[a] = min(length + 2 * halo, n)
+        origin[a] = (start - halo) % n
+    return tuple(origin), tuple(dims)
+
+
+def tessellate_labels(labels: np.ndarray, n_grains: int, eps=7.0, halo=5, radius=5, physics=None,
+                      with_idf=False) -> Microstructure:
+    """Initialisation from a label field (reading R17): grain i (label i) on
+    its label box, its function the re-initialisation (R5) of +1/2 on its
+    label cells and -1/2 elsewhere in the box; grains without a cell are
+    extinct.  With physics (or with_idf), the ID-field of every box cell is
+    the other grain whose function is largest there above -eps."""
+    labels = np.asarray(labels)
+    shape = labels.shape
+    axes = spatial_axes(shape)
+    grains = []
+    for i in range(n_grains):
+        sel = labels == i
+        if not sel.any():
+            grains.append(Grain(i, (0, 0, 0), np.full((1, 1, 1), -eps), None, alive=False))
+            continue
+        origin, dims = label_box(np.argwhere(sel), shape, halo)
+        g = Grain(i, origin, np.zeros(dims))
+        pz, py, px = box_positions(g, shape)
+        mine = labels[np.ix_(pz, py, px)] == i
+        g.phi = redistance(np.where(mine, 0.5, -0.5), full_axes(g, shape), eps, axes)
+        grains.append(g)
+    if with_idf or physics is not None:
+        phis = {g.gid: g.phi for g in grains if g.alive}
+        for g in grains:
+            if g.alive:
+                _, g.idf = neighbour_max(g.gid, grains, phis, shape, eps)
+    return Microstructure(tuple(shape), grains, eps, halo, radius, physics)
 
 
 def single_grain_state(shape, phi_fn, eps=7.0, halo=5, radius=5):

@@ -1222,3 +1222,73 @@ def test_point_triangle_distances_equal_the_single_point_form(oracle):
     fast = oracle.closest_gb_grains(g.phi, g.idf, 2.5, block=7)
     for z, y, x in np.argwhere(np.abs(g.phi) < 2.5):
         assert fast[z, y, x] == oracle.closest_gb_grain_at((z, y, x), tr, gr)
+
+
+def test_label_arc_is_the_shortest_covering_interval(oracle):
+    """R17: against brute force over every cyclic interval on random
+    occupancies (a few cells, runs of them, everything), the arc covers every
+    coordinate, no shorter interval does, and among the shortest the one
+    whose empty complement starts first is taken."""
+    rng = np.random.default_rng(7)
+    for n in (1, 2, 5, 9, 16):
+        for trial in range(40):
+            k = int(rng.integers(1, n + 1))
+            coords = rng.choice(n, size=k, replace=False)
+            if trial % 7 == 0:
+                coords = (int(rng.integers(0, n)) + np.arange(k)) % n    # one run, maybe wrapping
+            occ = np.zeros(n, bool)
+            occ[coords] = True
+            covering = [(s, L) for L in range(1, n + 1) for s in range(n)
+                        if all(((c - s) % n) < L for c in coords)]
+            best = min(L for _, L in covering)
+            start, length = oracle.label_arc(coords, n)
+            assert length == best
+            assert all(((c - start) % n) < length for c in coords)
+            if length < n:
+                # the gap left out starts at (start + length) mod n: the first of the longest
+                gaps = sorted(((s + L) % n for s, L in covering if L == best))
+                assert (start + length) % n == gaps[0]
+
+
+def test_label_init_of_a_planar_bicrystal_is_exact(oracle):
+    """R17 on two slabs (x < 10 and x >= 10 of a periodic 24-cell axis, full
+    in y and z): each grain's function is the distance to its two faces
+    (x = -0.5 and x = 9.5 for grain 0), +1/2 at the cells next to them, taxicab
+    beyond and clamped at eps; the boxes are the slabs grown by the halo, the
+    full axes wrapping; the ID-field names the other grain wherever its box
+    reaches (-1 beyond: no other function above -eps)."""
+    lab = np.zeros((6, 7, 24), dtype=np.int64)
+    lab[:, :, 10:] = 1
+    ms = oracle.tessellate_labels(lab, 2, eps=7.0, halo=5, with_idf=True)
+    g0, g1 = ms.grains
+    assert g0.dims == (6, 7, 20) and g0.origin[2] == 19
+    assert g1.dims == (6, 7, 24)                       # 14 + 10 cells reach the domain: full
+    x = (g0.origin[2] + np.arange(20)) % 24
+    d0 = np.minimum(np.abs(x - (-0.5)), np.abs(x - 9.5))
+    d0 = np.minimum(d0, np.abs(x - 23.5))
+    want0 = np.clip(np.where(x < 10, d0, -d0), -7, 7)
+    assert np.array_equal(g0.phi, np.broadcast_to(want0, g0.phi.shape))
+    assert np.all(g0.idf == 1)
+    x1 = (g1.origin[2] + np.arange(24)) % 24
+    in0 = ((x1 - g0.origin[2]) % 24) < g0.dims[2]
+    assert np.array_equal(g1.idf, np.broadcast_to(np.where(in0, 0, -1), g1.idf.shape))
+
+
+def test_label_init_signs_are_the_labels(oracle):
+    """R17 on a periodic Voronoi label field: every grain's function is
+    positive exactly on its own label cells inside its box and its box holds
+    all of them; the ID-field never names the grain itself."""
+    shape = (14, 16, 18)
+    seeds = I.voronoi_seeds(31, 9, (18, 16, 14))
+    lab = oracle.labels_of_tessellation(shape, seeds)
+    ms = oracle.tessellate_labels(lab, 9, with_idf=True)
+    for g in ms.grains:
+        if not g.alive:
+            assert not (lab == g.gid).any()
+            continue
+        pz, py, px = oracle.box_positions(g, shape)
+        mine = lab[np.ix_(pz, py, px)] == g.gid
+        assert np.array_equal(g.phi > 0, mine)
+        assert mine.sum() == (lab == g.gid).sum()
+        assert not np.any(g.idf == g.gid)
+        assert np.all(np.abs(g.phi) >= 0.5 / np.sqrt(3) - 1e-12)
