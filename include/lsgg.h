@@ -51,6 +51,7 @@ extern "C" {
 /* ---------------------------------------------------------------- config */
 #define LSGG_INIT_VORONOI   0   /* Voronoi tessellation of the seeds */
 #define LSGG_INIT_LAGUERRE  1   /* power diagram: seeds plus weights */
+#define LSGG_INIT_LABELS    2   /* a label field: every cell's grain id (a tessellation read from a file) */
 
 #define LSGG_PHYSICS_IDEAL          0  /* w = 1, no bulk term: phi_p = G * phi */
 #define LSGG_PHYSICS_READ_SHOCKLEY  1  /* per-pair w = M* gamma*(theta), cubic disorientation (Sec. 4.3) */
@@ -112,6 +113,11 @@ typedef struct lsgg_config {
     const double* weights;     /* optional n_grains power weights (LAGUERRE) */
     const double* quats;       /* optional n_grains x 4 unit quaternions (w, x, y, z) */
     const double* energy;      /* optional n_grains bulk energies in grid units (MAGNETIC) */
+    const int32_t* labels;     /* LABELS: nx*ny*nz grain ids in [0, n_grains), x fastest (host memory,
+                                  read during creation); grain i starts on its box (per axis the
+                                  shortest periodic arc of its cells grown by the halo) with the
+                                  re-initialisation of +1/2 on its cells and -1/2 elsewhere; a label
+                                  without a cell is an extinct grain.  Batched 3D only */
 } lsgg_config;
 
 /* Fill *cfg with the defaults above (64^3, 50 grains, seed 1, ideal, FP32, batched). */

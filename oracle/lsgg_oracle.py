@@ -1030,12 +1030,13 @@ def label_box(cells_zyx: np.ndarray, shape, halo: int):
 
 
 def tessellate_labels(labels: np.ndarray, n_grains: int, eps=7.0, halo=5, radius=5, physics=None,
-                      with_idf=False) -> Microstructure:
+                      with_idf=False, redist: str = "taxicab") -> Microstructure:
     """Initialisation from a label field (reading R17): grain i (label i) on
-    its label box, its function the re-initialisation (R5) of +1/2 on its
-    label cells and -1/2 elsewhere in the box; grains without a cell are
-    extinct.  With physics (or with_idf), the ID-field of every box cell is
-    the other grain whose function is largest there above -eps."""
+    its label box, its function the re-initialisation (R5, or the scheme
+    named by ``redist``: R11, R16) of +1/2 on its label cells and -1/2
+    elsewhere in the box; grains without a cell are extinct.  With physics
+    (or with_idf), the ID-field of every box cell is the other grain whose
+    function is largest there above -eps."""
     labels = np.asarray(labels)
     shape = labels.shape
     axes = spatial_axes(shape)
@@ -1049,14 +1050,14 @@ def tessellate_labels(labels: np.ndarray, n_grains: int, eps=7.0, halo=5, radius
         g = Grain(i, origin, np.zeros(dims))
         pz, py, px = box_positions(g, shape)
         mine = labels[np.ix_(pz, py, px)] == i
-        g.phi = redistance(np.where(mine, 0.5, -0.5), full_axes(g, shape), eps, axes)
+        g.phi = redistancer(redist)(np.where(mine, 0.5, -0.5), full_axes(g, shape), eps, axes)
         grains.append(g)
     if with_idf or physics is not None:
         phis = {g.gid: g.phi for g in grains if g.alive}
         for g in grains:
             if g.alive:
                 _, g.idf = neighbour_max(g.gid, grains, phis, shape, eps)
-    return Microstructure(tuple(shape), grains, eps, halo, radius, physics)
+    return Microstructure(tuple(shape), grains, eps, halo, radius, physics, redist=redist)
 
 
 def single_grain_state(shape, phi_fn, eps=7.0, halo=5, radius=5):

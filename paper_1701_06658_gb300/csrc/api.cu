@@ -23,6 +23,9 @@ static_assert(lsgg::kTiers == LSGG_PASS_TIERS, "pass-path tiers of the library a
 namespace lsgg {
 cudaError_t launch_init(const Domain& D, int G, const SeedBins& bins, const double* d_seeds, const double* d_weights, int* d_labels,
                         unsigned* d_bits, long long words_per_row, int* d_bb, Box* d_cur, cudaStream_t s);
+cudaError_t launch_label_boxes(const Domain& D, int G, const int* d_labels, unsigned* d_occ, int words, Box* d_cur,
+                               cudaStream_t s);
+cudaError_t launch_label_phi(const Domain& D, int G, const Box* d_cur, const int* d_labels, float* Z, cudaStream_t s);
 cudaError_t launch_sdf(const Domain& D, int G, const Box* d_cur, const double* d_seeds, const double* d_weights,
                        const unsigned* d_bits, long long words_per_row, float* X, int* IDF, int* d_status,
                        cudaStream_t s);
@@ -409,7 +412,17 @@ static int validate(const lsgg_config* cfg) {
     if (cfg->n_grains < 1 || cfg->n_grains > (1 << 24)) return LSGG_ERR_INVALID_ARG;
     if (cfg->halo < 1 || cfg->radius < 1 || cfg->radius > kMaxRadius) return LSGG_ERR_INVALID_ARG;
     if (!(cfg->eps > 1.0f) || cfg->eps > 64.0f) return LSGG_ERR_INVALID_ARG;
-    if (cfg->init_kind != LSGG_INIT_VORONOI && cfg->init_kind != LSGG_INIT_LAGUERRE) return LSGG_ERR_INVALID_ARG;
+    if (cfg->init_kind != LSGG_INIT_VORONOI && cfg->init_kind != LSGG_INIT_LAGUERRE &&
+        cfg->init_kind != LSGG_INIT_LABELS)
+        return LSGG_ERR_INVALID_ARG;
+    if (cfg->init_kind == LSGG_INIT_LABELS) {
+        // the label field starts through the pass path's re-initialisation (3D, batched)
+        if (!cfg->labels) return LSGG_ERR_INVALID_ARG;
+        if (cfg->exec != LSGG_EXEC_BATCHED || cfg->nz == 1) return LSGG_ERR_UNSUPPORTED;
+        const long long n = (long long)cfg->nx * cfg->ny * cfg->nz;
+        for (long long k = 0; k < n; ++k)
+            if (cfg->labels[k] < 0 || cfg->labels[k] >= cfg->n_grains) return LSGG_ERR_INVALID_ARG;
+    }
     if (cfg->physics < LSGG_PHYSICS_IDEAL || cfg->physics > LSGG_PHYSICS_MAGNETIC) return LSGG_ERR_INVALID_ARG;
     if (cfg->storage != LSGG_STORAGE_FP32 && cfg->storage != LSGG_STORAGE_BF16) return LSGG_ERR_INVALID_ARG;
     // BF16 state storage: the batched path's kernels (pass path, shared /
@@ -449,6 +462,7 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     if (!c) return LSGG_ERR_OUT_OF_MEMORY;
     c->cfg = *cfg_in;
     c->cfg.seeds = c->cfg.weights = c->cfg.quats = c->cfg.energy = nullptr;
+    c->cfg.labels = nullptr;
     c->device = cfg_in->device;
     auto bail = [&](int code) { lsgg_destroy(c); return code; };
     if (cudaSetDevice(c->device) != cudaSuccess) return bail(CUDA_FAIL());
@@ -469,9 +483,10 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     D.radius = cfg_in->radius;
 
     // ---- seeds / weights / energies (host marshalling of given or generated inputs) ----
+    const bool from_labels = cfg_in->init_kind == LSGG_INIT_LABELS;
     std::vector<double> seeds(3 * (size_t)G), weights, energy;
     if (cfg_in->seeds) std::memcpy(seeds.data(), cfg_in->seeds, seeds.size() * 8);
-    else lsgg_generate_seeds(cfg_in->seed, G, D.nx, D.ny, D.nz, seeds.data());
+    else if (!from_labels) lsgg_generate_seeds(cfg_in->seed, G, D.nx, D.ny, D.nz, seeds.data());
     if (cfg_in->init_kind == LSGG_INIT_LAGUERRE) {
         weights.resize(G);
         if (cfg_in->weights) std::memcpy(weights.data(), cfg_in->weights, (size_t)G * 8);
@@ -601,7 +616,9 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     long long bin_bytes = 0;
     float4* d_bpts = nullptr;
     int *d_bids = nullptr, *d_bstart = nullptr;
-    {
+    unsigned* d_occ = nullptr;                   // label field: per grain and axis the positions it holds
+    const int occ_words = (std::max(D.nx, std::max(D.ny, D.nz)) + 31) / 32;
+    if (!from_labels) {
         const int Ns[3] = {D.nx, D.ny, D.nz};
         const double spacing = std::pow((double)ncell / G, 1.0 / D.dim);
         for (int a = 0; a < 3; ++a) {
@@ -648,8 +665,17 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
         bins.start = d_bstart;
         bin_bytes = (long long)G * (sizeof(float4) + 4) + (n_bins + 1) * 4;
     }
-    if (launch_init(D, G, bins, c->d_seeds, c->d_weights, d_labels, d_bits, wpr, d_bb, c->B.cur, c->stream) != cudaSuccess)
+    if (from_labels) {
+        // the given labels, every grain's box from the arcs of its cells
+        if (cudaMemcpy(d_labels, cfg_in->labels, (size_t)ncell * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(CUDA_FAIL());
+        if ((r = dalloc(c, &d_occ, (size_t)G * 3 * occ_words)) != LSGG_OK) return bail(r);
+        if (launch_label_boxes(D, G, d_labels, d_occ, occ_words, c->B.cur, c->stream) != cudaSuccess)
+            return bail(CUDA_FAIL());
+    } else if (launch_init(D, G, bins, c->d_seeds, c->d_weights, d_labels, d_bits, wpr, d_bb, c->B.cur, c->stream) !=
+               cudaSuccess) {
         return bail(CUDA_FAIL());
+    }
     // size the arena from the initial boxes
     std::vector<Box> hb(G);
     if (cudaMemcpyAsync(hb.data(), c->B.cur, (size_t)G * sizeof(Box), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -691,21 +717,6 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
         if ((r = dalloc(c, &c->B.scratch, (size_t)std::max(total, 32LL))) != LSGG_OK) return bail(r);
     }
     if ((r = relayout(c)) != LSGG_OK) return bail(r);
-    if (launch_sdf(D, G, c->B.cur, c->d_seeds, c->d_weights, d_bits, wpr, c->B.bf16 ? c->B.Y : c->B.X,
-                   c->B.IDF, &c->B.st->status, c->stream) != cudaSuccess)
-        return bail(CUDA_FAIL());
-    if (c->B.bf16 && launch_f32_to_state(c->B.Y, c->B.X, c->B.cap, c->stream) != cudaSuccess) return bail(CUDA_FAIL());
-    if (cudaMemcpyAsync(c->B.prev, c->B.cur, (size_t)G * sizeof(Box), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-        return bail(CUDA_FAIL());
-    if ((r = read_state(c)) != LSGG_OK) return bail(r);
-    if (c->h_st->status != 0) return bail(c->h_st->status);
-    dfree(c, d_labels);
-    dfree(c, d_bits);
-    dfree(c, d_bb);
-    dfree(c, d_bpts);
-    dfree(c, d_bids);
-    dfree(c, d_bstart);
-    c->device_bytes -= (long long)ncell * 4 + (long long)G * wpr * 4 + 6LL * G * 4 + bin_bytes;
     c->phys.kind = cfg_in->physics;
     c->phys.energy = c->d_energy;
     c->phys.quats = c->d_quats;
@@ -717,6 +728,37 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->phys.mob_low = cfg_in->mob_low;
     c->phys.mob_law = cfg_in->mobility_law;
     c->phys.pair_map = c->B.gb_map;
+    if (from_labels) {
+        // +-1/2 by membership, then the step's re-initialisation and box
+        // update (with physics the field pass of the result gives the
+        // ID-field the first step reads)
+        if (launch_label_phi(D, G, c->B.cur, d_labels, c->B.Z, c->stream) != cudaSuccess ||
+            launch_reinit(c->B, make_taps(1.0, D.radius), c->phys, cfg_in->physics != LSGG_PHYSICS_IDEAL,
+                          c->stream) != cudaSuccess)
+            return bail(CUDA_FAIL());
+    } else {
+        if (launch_sdf(D, G, c->B.cur, c->d_seeds, c->d_weights, d_bits, wpr, c->B.bf16 ? c->B.Y : c->B.X,
+                       c->B.IDF, &c->B.st->status, c->stream) != cudaSuccess)
+            return bail(CUDA_FAIL());
+        if (c->B.bf16 && launch_f32_to_state(c->B.Y, c->B.X, c->B.cap, c->stream) != cudaSuccess)
+            return bail(CUDA_FAIL());
+        if (cudaMemcpyAsync(c->B.prev, c->B.cur, (size_t)G * sizeof(Box), cudaMemcpyDeviceToDevice, c->stream) !=
+            cudaSuccess)
+            return bail(CUDA_FAIL());
+    }
+    if ((r = read_state(c)) != LSGG_OK) return bail(r);
+    if (c->h_st->status != 0) return bail(c->h_st->status);
+    if (d_occ) {
+        dfree(c, d_occ);
+        c->device_bytes -= (long long)G * 3 * occ_words * 4;
+    }
+    dfree(c, d_labels);
+    dfree(c, d_bits);
+    dfree(c, d_bb);
+    dfree(c, d_bpts);
+    dfree(c, d_bids);
+    dfree(c, d_bstart);
+    c->device_bytes -= (long long)ncell * 4 + (long long)G * wpr * 4 + 6LL * G * 4 + bin_bytes;
     *out = c;
     return LSGG_OK;
 }

@@ -510,6 +510,101 @@ cudaError_t launch_init(const Domain& D, int G, const SeedBins& bins, const doub
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// initialisation from a label field
+// ---------------------------------------------------------------------------
+// Per grain and axis, the positions holding one of its cells, as bits
+// (words of 32 positions per (grain, axis)).
+__global__ void k_label_occupancy(Domain D, const int* __restrict__ labels, unsigned* __restrict__ occ, int words) {
+    const long long ncell = (long long)D.nx * D.ny * D.nz;
+    const int N[3] = {D.nx, D.ny, D.nz};
+    for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < ncell;
+         cell += (long long)gridDim.x * blockDim.x) {
+        const int c[3] = {(int)(cell % D.nx), (int)((cell / D.nx) % D.ny), (int)(cell / ((long long)D.nx * D.ny))};
+        const long long i = labels[cell];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (N[a] > 1) atomicOr(&occ[(i * 3 + a) * words + (c[a] >> 5)], 1u << (c[a] & 31));
+    }
+}
+
+// Grain i's box from its label cells: per axis the shortest cyclic interval
+// holding every occupied position -- the complement of the longest run of
+// empty positions, the first such run (smallest start) on ties -- grown by
+// the halo and capped at the axis; no cell: extinct.
+__global__ void k_label_boxes(Domain D, int G, const unsigned* __restrict__ occ, int words, Box* __restrict__ cur) {
+    const int N[3] = {D.nx, D.ny, D.nz};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G; i += gridDim.x * blockDim.x) {
+        const unsigned* ox = occ + ((long long)i * 3) * words;
+        bool any = false;
+        for (int w = 0; w < words; ++w) any = any || ox[w] != 0u;
+        Box b{};
+        if (!any) {
+            cur[i] = b;
+            continue;
+        }
+        int o[3], n[3];
+        for (int a = 0; a < 3; ++a) {
+            const int na = N[a];
+            if (na == 1) { o[a] = 0; n[a] = 1; continue; }
+            const unsigned* bits = occ + ((long long)i * 3 + a) * words;
+            auto at = [&](int p) { return (bits[p >> 5] >> (p & 31)) & 1u; };
+            int best_start = 0, best_len = -1;
+            for (int p = 0; p < na; ++p) {
+                if (at(p) || !at(p == 0 ? na - 1 : p - 1)) continue;   // not the first empty position of a run
+                int len = 0;
+                while (len < na && !at((p + len) % na)) ++len;
+                if (len > best_len) { best_start = p; best_len = len; }
+            }
+            int start = 0, length = na;                            // every position held
+            if (best_len > 0) {
+                start = (best_start + best_len) % na;
+                length = na - best_len;
+            }
+            n[a] = length + 2 * D.halo < na ? length + 2 * D.halo : na;
+            o[a] = pmod(start - D.halo, na);
+        }
+        b.ox = o[0]; b.oy = o[1]; b.oz = o[2];
+        b.nx = n[0]; b.ny = n[1]; b.nz = n[2];
+        cur[i] = b;
+    }
+}
+
+// The starting function before the re-initialisation: +1/2 on the grain's
+// label cells and -1/2 on the other cells of its box (`cur` layout, FP32).
+__global__ void k_label_phi(Domain D, const Box* __restrict__ cur, const int* __restrict__ labels,
+                            float* __restrict__ Z) {
+    const int i = blockIdx.x;
+    const Box b = cur[i];
+    if (b.nx <= 0) return;
+    const int ps = plane_stride(b.nx, b.ny);
+    const int A = b.nx * b.ny;
+    const long long n = (long long)A * b.nz;
+    for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+        const int z = (int)(k / A), rem = (int)(k - (long long)z * A);
+        const int y = rem / b.nx, x = rem - y * b.nx;
+        const long long g = ((long long)pmod(b.oz + z, D.nz) * D.ny + pmod(b.oy + y, D.ny)) * D.nx + pmod(b.ox + x, D.nx);
+        Z[b.off + (long long)z * ps + rem] = labels[g] == i ? 0.5f : -0.5f;
+    }
+}
+
+cudaError_t launch_label_boxes(const Domain& D, int G, const int* d_labels, unsigned* d_occ, int words, Box* d_cur,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_occ, 0, (size_t)G * 3 * words * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const long long ncell = (long long)D.nx * D.ny * D.nz;
+    long long gs = (ncell + 255) / 256;
+    if (gs > 65535 * 8) gs = 65535 * 8;
+    k_label_occupancy<<<(int)gs, 256, 0, s>>>(D, d_labels, d_occ, words);
+    k_label_boxes<<<(G + 127) / 128, 128, 0, s>>>(D, G, d_occ, words, d_cur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_label_phi(const Domain& D, int G, const Box* d_cur, const int* d_labels, float* Z, cudaStream_t s) {
+    k_label_phi<<<G, 256, 0, s>>>(D, d_cur, d_labels, Z);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sdf(const Domain& D, int G, const Box* d_cur, const double* d_seeds, const double* d_weights,
                        const unsigned* d_bits, long long words_per_row, float* X, int* IDF, int* d_status,
                        cudaStream_t s) {

@@ -27,7 +27,7 @@ ERR_NOT_READY = -6
 ERR_CAPACITY = -7
 ERR_UNSUPPORTED = -8
 
-INIT_VORONOI, INIT_LAGUERRE = 0, 1
+INIT_VORONOI, INIT_LAGUERRE, INIT_LABELS = 0, 1, 2
 PHYSICS_IDEAL, PHYSICS_READ_SHOCKLEY, PHYSICS_MAGNETIC = 0, 1, 2
 STORAGE_FP32, STORAGE_BF16 = 0, 1
 EXEC_BATCHED, EXEC_PLAIN, EXEC_STREAMED = 0, 1, 2
@@ -55,6 +55,7 @@ class Config(C.Structure):
         ("arena_slack", C.c_double),
         ("gb_map_tube", C.c_double),
         ("seeds", _dp), ("weights", _dp), ("quats", _dp), ("energy", _dp),
+        ("labels", C.POINTER(C.c_int32)),
     ]
 
 
@@ -531,7 +532,8 @@ class Microstructure:
     def __init__(self, nx: int, ny: int, nz: int, n_grains: int, seed: int = 1, seeds=None, weights=None,
                  quats=None, energy=None, physics: int = PHYSICS_IDEAL, exec_mode: int = EXEC_BATCHED,
                  storage: int = STORAGE_FP32, halo: int = 5, radius: int = 5, eps: float = 7.0,
-                 init_kind: int | None = None, stream=None, device: int = 0, arena_slack: float = 1.5, **extra):
+                 init_kind: int | None = None, stream=None, device: int = 0, arena_slack: float = 1.5,
+                 labels=None, **extra):
         cfg = config_default()
         cfg.nx, cfg.ny, cfg.nz, cfg.n_grains, cfg.seed = nx, ny, nz, n_grains, seed
         cfg.halo, cfg.radius, cfg.eps = halo, radius, eps
@@ -553,6 +555,11 @@ class Microstructure:
             self._keep.append(w)
             cfg.weights = _ptr(w, C.c_double)
         cfg.init_kind = (INIT_LAGUERRE if weights is not None else INIT_VORONOI) if init_kind is None else init_kind
+        if labels is not None:                       # (z, y, x) grain ids: the label-field initialisation
+            lab = np.ascontiguousarray(labels, dtype=np.int32)
+            self._keep.append(lab)
+            cfg.labels = _ptr(lab, C.c_int32)
+            cfg.init_kind = INIT_LABELS
         if quats is not None:
             q = np.ascontiguousarray(quats, dtype=np.float64)
             self._keep.append(q)

@@ -181,3 +181,30 @@ def test_group_arguments_checked_before_any_device_work():
     assert L.lib().lsgg_group_create(arr, L.MAX_GROUP + 1, ctypes.byref(h)) == L.ERR_INVALID_ARG
     assert L.lib().lsgg_group_step(None, 1, 1.0, None) == L.ERR_INVALID_ARG
     assert L.lib().lsgg_group_destroy(None) == L.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("case", ["null", "low", "high", "streamed", "2d"])
+def test_label_field_configuration_is_checked(case):
+    """A label-field start needs the labels, every label in [0, n_grains) and
+    the batched 3D path; anything else is refused before any device work."""
+    L = _lib()
+    cfg = L.config_default()
+    cfg.nx, cfg.ny, cfg.nz, cfg.n_grains = 8, 8, 8, 4
+    cfg.init_kind = L.INIT_LABELS
+    lab = np.zeros(8 * 8 * 8, dtype=np.int32)
+    lab[::3] = 3
+    want = L.ERR_INVALID_ARG
+    if case == "low":
+        lab[17] = -1
+    elif case == "high":
+        lab[-1] = 4
+    elif case == "streamed":
+        cfg.exec = L.EXEC_STREAMED
+        want = L.ERR_UNSUPPORTED
+    elif case == "2d":
+        cfg.nz = 1
+        want = L.ERR_UNSUPPORTED
+    if case != "null":
+        cfg.labels = lab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    ctx = ctypes.c_void_p()
+    assert L.lib().lsgg_create_microstructure(ctypes.byref(cfg), None, ctypes.byref(ctx)) == want
