@@ -42,6 +42,8 @@ WORKLOADS = {
     # 1 % of grains with 5x volume, random cubic orientations, Read-Shockley
     # boundary energy (theta_max 15 deg) and mobility 0.1 below 15 deg
     "512rs": {"n": 512, "grains": 40000, "seed": 3, "dt": 1.0, "physics": "read_shockley", "init": "laguerre"},
+    # small case of the Read-Shockley workload for profilers (the same grain density)
+    "160rs": {"n": 160, "grains": 1221, "seed": 3, "dt": 1.0, "physics": "read_shockley", "init": "laguerre"},
     # magnetically driven growth: random c-axes, field (0, cos 32, sin 32), bulk
     # energy B^2 dchi cos^2 / (2 mu0) in grid units (4.07e-3 at cos^2 = 1)
     "384mag": {"n": 384, "grains": 10000, "seed": 4, "dt": 1.0, "physics": "magnetic", "energy_scale": 4.07e-3},

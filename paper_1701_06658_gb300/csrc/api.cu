@@ -728,6 +728,14 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
     c->phys.mob_low = cfg_in->mob_low;
     c->phys.mob_law = cfg_in->mobility_law;
     c->phys.pair_map = c->B.gb_map;
+    if (cfg_in->physics == LSGG_PHYSICS_READ_SHOCKLEY && c->B.use_passes && !c->B.gb_map) {
+        // the pass path's neighbour-list pool: about 64 pairs per grain (a
+        // box that finds no room looks its pairs up per cell)
+        const long long cap = std::min(std::max(64LL * G, 4096LL), (long long)INT_MAX / 2);
+        if ((r = dalloc(c, &c->phys.pool_ent, (size_t)cap)) != LSGG_OK) return bail(r);
+        if ((r = dalloc(c, &c->phys.pool_box, (size_t)G)) != LSGG_OK) return bail(r);
+        c->phys.pool_cap = (int)cap;
+    }
     if (from_labels) {
         // +-1/2 by membership, then the step's re-initialisation and box
         // update (with physics the field pass of the result gives the

@@ -72,6 +72,7 @@ struct PairEntry {        // neighbour j of grain i: weight w_ij and mobility M_
 };
 
 constexpr int kNbCap = 96;          // neighbour-table entries per grain
+constexpr int kPoolKeys = 512;      // pool list entries per box at most (the collection's hash slots)
 
 struct PhysicsDev {
     int kind;                       // LSGG_PHYSICS_*
@@ -83,6 +84,14 @@ struct PhysicsDev {
     const int* nb_cnt;              // per grain: entries (kNbCap + 1: the table overflowed)
     const float* nb_w;              // per grain and entry: pair weight w (READ_SHOCKLEY, refreshed with nb_tab)
     const float* nb_m;              // per grain and entry: pair mobility M
+    // the pass path's complete neighbour lists of a READ_SHOCKLEY run (every
+    // grain of a box's ID-field, ascending, up to kPoolKeys), refreshed
+    // before each predictor into one pool: entry {j, w, M, 0} (w, M as float
+    // bits); per box {first entry, count} with count -1 when the list did
+    // not fit
+    int4* pool_ent;                 // null: no pool (the z pass looks pairs up per cell)
+    int2* pool_box;
+    int pool_cap;                   // entries
     double theta_max;               // radians
     double mob_low;
     int mob_law;                    // LSGG_MOBILITY_*
@@ -115,6 +124,7 @@ struct StepState {                  // device-resident control block
     int slab_base[kTiers];
     long long step_limit;           // step groups: the member takes part while steps_done < step_limit
     int bu_go;                      // the step's box update places offsets and items (set by its scan)
+    int pool_used;                  // neighbour-list pool entries taken by this step's lists
 };
 
 // The step's box update runs as three grid launches over chunks of

@@ -377,13 +377,113 @@ __device__ __forceinline__ void conv_column(const float* zc, float* yc, int nz, 
         }
 }
 
+// The z pass's per-box pair hash (Read-Shockley): the box's pool list (every
+// grain of its ID-field with w and M) in kZHash open-addressing slots, at
+// most half full, so a cell finds its pair's weights with one or two shared
+// loads.
+constexpr int kZHash = 2 * kPoolKeys;
+static_assert((kZHash & (kZHash - 1)) == 0, "pair hash slots: a power of two");
+__device__ __forceinline__ unsigned zhash(int j) { return ((unsigned)j * 2654435761u) >> 22; }
+static_assert((1u << 10) == kZHash, "zhash yields the slot bits of kZHash");
+__device__ __forceinline__ int zslot(const int* hk, int j) {
+    unsigned h = zhash(j);
+#pragma unroll 1
+    for (int p = 0; p < kZHash; ++p) {
+        const int k = hk[h];
+        if (k == j) return (int)h;
+        if (k < 0) return -1;
+        h = (h + 1) & (kZHash - 1);
+    }
+    return -1;
+}
+
+constexpr int kColumnRadius = 5;   // the physics z pass keeps its column in registers at this radius
+
+// Read-Shockley weights of a pair missing from the box's hash (a list that
+// did not fit the pool): out of line, so that the unrolled column below
+// keeps one call per cell instead of the FP64 evaluation.
+__device__ __noinline__ void rs_pair_out_of_line(const PhysicsDev& phys, int i, int j, float& w, float& m) {
+    rs_pair(phys, i, j, w, m);
+}
+
+// z pass with the velocity correction of Eq. (10) for one column of nz <= NZ
+// cells on a non-periodic axis: the z convolution from the column in
+// registers (as conv_column), then per group of eight cells the previous
+// step's phi and pair ids (old layout; -eps and no pair outside the old box)
+// loaded together, the bulk energies e_j loaded together, and the blend
+// phi + w (c - phi) + M (e_j - e_i) dt with w and M from the box's pair hash
+// (Read-Shockley) or 1 (magnetic); cells without a pair take c.
+template <int R, int NZ>
+__device__ __forceinline__ void conv_column_phys(const StepBuffers& B, const PhysicsDev& phys, const float* zc, float* yc,
+                                                 int nz, int ps, const float (&g)[2 * R + 1], float cconst, float eps,
+                                                 long long o_old, int ps_old, int ozl0, int onz, int dnz, bool in_old,
+                                                 int b, float ei, bool rs, const int* hk, const float* hw,
+                                                 const float* hm) {
+    constexpr int W = 2 * R + 1;
+    constexpr int G8 = 8;
+    float r[NZ + 2 * R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) r[k] = cconst;
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) r[R + z] = __ldg(zc + (long long)min(z, nz - 1) * ps);
+#pragma unroll
+    for (int z = 0; z < NZ + R; ++z)
+        if (z >= nz) r[R + z] = cconst;
+#pragma unroll
+    for (int z0 = 0; z0 < NZ; z0 += G8) {
+        if (z0 >= nz) break;                               // uniform: one box per CTA item
+        float p0[G8], ej[G8];
+        int jj[G8];
+#pragma unroll
+        for (int u = 0; u < G8; ++u) {
+            const int z = z0 + u;
+            int ozl = ozl0 + z;                            // ozl0 + z < 2 N_z
+            if (ozl >= dnz) ozl -= dnz;
+            const bool ok = z < nz && in_old && ozl < onz;
+            const long long o = o_old + (long long)(ok ? ozl : 0) * ps_old;
+            p0[u] = ok ? ld_state(B, o) : -eps;
+            jj[u] = ok ? B.IDF[o] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < G8; ++u) ej[u] = phys.energy && jj[u] >= 0 ? __ldg(phys.energy + jj[u]) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < G8; ++u) {
+            const int z = z0 + u;
+            if (z >= nz) break;
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < W; ++k) acc = fmaf(g[k], r[z + k], acc);
+            float val = acc;
+            const int j = jj[u];
+            if (j >= 0) {
+                float w = 1.0f, m = 1.0f;
+                if (rs) {
+                    const int h = zslot(hk, j);
+                    if (h >= 0) {
+                        w = hw[h];
+                        m = hm[h];
+                    } else {
+                        rs_pair_out_of_line(phys, b, j, w, m);
+                    }
+                }
+                float bulk = 0.0f;
+                if (phys.energy) bulk = m * (ej[u] - ei) * phys.dt;
+                val = p0[u] + w * (acc - p0[u]) + bulk;
+            }
+            yc[(long long)z * ps] = fminf(fmaxf(val, -eps), eps);
+        }
+    }
+}
+
 template <int R, bool PHYS, bool GRP>
-__global__ void __launch_bounds__(kColThreads)
+__global__ void __launch_bounds__(kColThreads, PHYS ? 2 : (R < 5 ? 4 : 3))
 p_conv_z(StepBuffers B1, GroupRef grp, Taps taps, PhysicsDev phys, int tier) {
     static_assert(!(GRP && PHYS), "step groups run ideal growth");
     constexpr int W = 2 * R + 1;
     __shared__ int s_tj[PHYS ? kNbCap : 1];
     __shared__ float s_tw[PHYS ? kNbCap : 1], s_tm[PHYS ? kNbCap : 1];
+    __shared__ int s_hk[PHYS ? kZHash : 1];
+    __shared__ float s_hw[PHYS ? kZHash : 1], s_hm[PHYS ? kZHash : 1];
     __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
     if (!GRP && halted(B1)) return;
     float g[W];
@@ -393,7 +493,9 @@ p_conv_z(StepBuffers B1, GroupRef grp, Taps taps, PhysicsDev phys, int tier) {
     const int n_items = GRP ? group_scan(grp, kItemChunks, tier, true, s_gb) : B1.st->n_chunks[tier];
     const int2* items = GRP ? nullptr : B1.chunk_items + B1.st->chunk_base[tier];
     const bool rs = PHYS && phys.kind == LSGG_PHYSICS_READ_SHOCKLEY;
+    const bool pooled = PHYS && phys.pool_ent != nullptr && phys.pair_map == nullptr;
     int last_b = -1;
+    int hash_n = -1;                                       // the box's pair hash entries, -1: none
     PairTable tab{s_tj, s_tw, s_tm, 0};
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         int local;
@@ -402,9 +504,28 @@ p_conv_z(StepBuffers B1, GroupRef grp, Taps taps, PhysicsDev phys, int tier) {
         const float cconst = GRP ? conv_xy_of_const<R>(g, -D.eps) : cconst1;
         const int2 it = list_item<GRP>(B, items, kItemChunks, tier, item, local);
         const int b = it.x;
-        if (rs && b != last_b) {                           // uniform across the CTA
+        if (PHYS && (rs || pooled) && b != last_b) {       // uniform across the CTA
             __syncthreads();
-            tab = load_pair_table(phys, b, s_tj, s_tw, s_tm);
+            hash_n = -1;
+            tab.n = 0;
+            if (pooled) {
+                const int2 pb = phys.pool_box[b];
+                if (pb.y >= 0 && pb.y <= kZHash / 2) hash_n = pb.y;
+            }
+            if (hash_n >= 0) {
+                for (int k = threadIdx.x; k < kZHash; k += blockDim.x) s_hk[k] = -1;
+                __syncthreads();
+                const int2 pb = phys.pool_box[b];
+                for (int k = threadIdx.x; k < hash_n; k += blockDim.x) {
+                    const int4 e = phys.pool_ent[pb.x + k];
+                    unsigned h = zhash(e.x);
+                    while (atomicCAS(&s_hk[h], -1, e.x) != -1) h = (h + 1) & (kZHash - 1);
+                    s_hw[h] = __int_as_float(e.y);
+                    s_hm[h] = __int_as_float(e.z);
+                }
+            } else if (rs) {
+                tab = load_pair_table(phys, b, s_tj, s_tw, s_tm);
+            }
             __syncthreads();
         }
         last_b = b;
@@ -432,6 +553,28 @@ p_conv_z(StepBuffers B1, GroupRef grp, Taps taps, PhysicsDev phys, int tier) {
             continue;
         }
         const int ps_old = plane_stride(ob.nx, ob.ny);
+        // the paper's radius (the column code is instantiated for it alone)
+        if constexpr (PHYS && R == kColumnRadius) {
+            if (!fz && nz <= 64 && !phys.pair_map && (!rs || hash_n >= 0)) {
+                // uniform across the CTA
+                const long long o_old = ob.off + (long long)oyl * ob.nx + oxl;
+                const int ozl0 = wrap_near(nb.oz - ob.oz, D.nz);
+                const float ei = phys.energy ? phys.energy[b] : 0.0f;
+                if (nz <= 16)
+                    conv_column_phys<R, 16>(B, phys, zc, yc, nz, ps, g, cconst, D.eps, o_old, ps_old, ozl0, ob.nz, D.nz,
+                                            in_old_xy, b, ei, rs, s_hk, s_hw, s_hm);
+                else if (nz <= 32)
+                    conv_column_phys<R, 32>(B, phys, zc, yc, nz, ps, g, cconst, D.eps, o_old, ps_old, ozl0, ob.nz, D.nz,
+                                            in_old_xy, b, ei, rs, s_hk, s_hw, s_hm);
+                else if (nz <= 48)
+                    conv_column_phys<R, 48>(B, phys, zc, yc, nz, ps, g, cconst, D.eps, o_old, ps_old, ozl0, ob.nz, D.nz,
+                                            in_old_xy, b, ei, rs, s_hk, s_hw, s_hm);
+                else
+                    conv_column_phys<R, 64>(B, phys, zc, yc, nz, ps, g, cconst, D.eps, o_old, ps_old, ozl0, ob.nz, D.nz,
+                                            in_old_xy, b, ei, rs, s_hk, s_hw, s_hm);
+                continue;
+            }
+        }
         PairCache pcache;
         const float ei = PHYS && phys.energy ? phys.energy[b] : 0.0f;
         float win[W];                                      // planes zo-R .. zo+R
@@ -479,7 +622,27 @@ p_conv_z(StepBuffers B1, GroupRef grp, Taps taps, PhysicsDev phys, int tier) {
 #pragma unroll
                 for (int k = 0; k < W; ++k) acc = fmaf(g[k], win[k], acc);
                 float val = acc;
-                if (PHYS) val = pair_blend_cached(phys, tab, b, jn[u], phi0[u], acc, ei, pcache);
+                if (PHYS && hash_n >= 0) {
+                    // Eq. (10) with the pair's w and M from the box's hash
+                    // (the arithmetic of pair_blend)
+                    const int j = jn[u];
+                    if (j >= 0) {
+                        const int h = zslot(s_hk, j);
+                        float w = 1.0f, m = 1.0f;
+                        if (h >= 0) {
+                            w = s_hw[h];
+                            m = s_hm[h];
+                        } else if (rs) {                       // not in the box's list: direct
+                            rs_pair_out_of_line(phys, b, j, w, m);
+                        }
+                        const float ej = phys.energy ? phys.energy[j] : 0.0f;
+                        float bulk = 0.0f;
+                        if (phys.energy) bulk = m * (ej - ei) * phys.dt;
+                        val = phi0[u] + w * (acc - phi0[u]) + bulk;
+                    }
+                } else if (PHYS) {
+                    val = pair_blend_cached(phys, tab, b, jn[u], phi0[u], acc, ei, pcache);
+                }
                 val = fminf(fmaxf(val, -D.eps), D.eps);
                 yc[(long long)zo * ps] = val;
             }

@@ -4,17 +4,21 @@
 // keeps, per cell, the nearest other grain in the ID-field (Sec. 3.1).  Here a
 // grain's table is exactly the set of grain ids present in its ID-field: the
 // pairs the next predictor can meet.  k_collect_neighbours rebuilds it from the
-// state's ID-field before every predictor of a READ_SHOCKLEY run; the
-// predictor evaluates the pair weights of a box once from it.
+// state's ID-field before every predictor: the first kNbCap ids with their
+// Read-Shockley weights in a fixed table per grain, and, on the pass path,
+// every id of the box (up to kPoolKeys) with its weight and mobility in the
+// step's pool, which the z pass turns into a shared-memory hash per box, so
+// that no cell searches or evaluates a pair.
 #include "kernels_common.cuh"
 
 namespace lsgg {
 
-constexpr int kHashSlots = 512;
+constexpr int kHashSlots = kPoolKeys;
+static_assert((kHashSlots & (kHashSlots - 1)) == 0, "hash slots: a power of two");
 
 __global__ void __launch_bounds__(256)
-k_collect_neighbours(PhysicsDev phys, const Box* __restrict__ prev, const int* __restrict__ IDF, int* __restrict__ tab,
-                     int* __restrict__ cnt, float* __restrict__ tw, float* __restrict__ tm) {
+k_collect_neighbours(PhysicsDev phys, StepState* st, const Box* __restrict__ prev, const int* __restrict__ IDF,
+                     int* __restrict__ tab, int* __restrict__ cnt, float* __restrict__ tw, float* __restrict__ tm) {
     __shared__ int keys[kHashSlots];
     __shared__ int n_keys, overflow;
     const int b = blockIdx.x;
@@ -46,24 +50,39 @@ k_collect_neighbours(PhysicsDev phys, const Box* __restrict__ prev, const int* _
         }
     }
     __syncthreads();
-    // rank-sort the keys (ascending) and keep the first kNbCap
+    // the box's place in the pool (every key, or none when they overflowed)
+    __shared__ int pool_base;
+    const bool pooled = phys.pool_ent != nullptr && !overflow;
+    if (threadIdx.x == 0) {
+        int base = -1;
+        if (pooled && n_keys > 0) {
+            base = atomicAdd(&st->pool_used, n_keys);
+            if (base > phys.pool_cap - n_keys) base = -1;
+        }
+        pool_base = base;
+        if (phys.pool_ent) phys.pool_box[b] = make_int2(base < 0 ? 0 : base, n_keys == 0 ? 0 : (base < 0 ? -1 : n_keys));
+    }
+    __syncthreads();
+    const bool rs = phys.kind == LSGG_PHYSICS_READ_SHOCKLEY;
+    // rank-sort the keys (ascending): the first kNbCap in the grain's table,
+    // all of them in the pool, each with its pair weights (FP64
+    // disorientation, once per grain, pair and step)
     for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x) {
         const int j = keys[k];
         if (j < 0) continue;
         int rank = 0;
         for (int q = 0; q < kHashSlots; ++q) rank += (unsigned)keys[q] < (unsigned)j && keys[q] >= 0;
-        if (rank < kNbCap) tab[(size_t)b * kNbCap + rank] = j;
+        if (rank >= kNbCap && pool_base < 0) continue;
+        float w = 1.0f, m = 1.0f;
+        if (rs) rs_pair(phys, b, j, w, m);
+        if (rs && rank < kNbCap) {
+            tab[(size_t)b * kNbCap + rank] = j;
+            tw[(size_t)b * kNbCap + rank] = w;
+            tm[(size_t)b * kNbCap + rank] = m;
+        }
+        if (pool_base >= 0) phys.pool_ent[pool_base + rank] = make_int4(j, __float_as_int(w), __float_as_int(m), 0);
     }
-    if (threadIdx.x == 0) cnt[b] = (overflow || n_keys > kNbCap) ? kNbCap + 1 : n_keys;
-    __syncthreads();
-    // the pair weights of the table (FP64 disorientation), once per grain and step
-    const int n = min(n_keys, kNbCap);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        float w, m;
-        rs_pair(phys, b, tab[(size_t)b * kNbCap + k], w, m);
-        tw[(size_t)b * kNbCap + k] = w;
-        tm[(size_t)b * kNbCap + k] = m;
-    }
+    if (threadIdx.x == 0 && rs) cnt[b] = (overflow || n_keys > kNbCap) ? kNbCap + 1 : n_keys;
 }
 
 // Contact neighbours of each box from the neighbour-max field of the last step:
@@ -126,7 +145,11 @@ cudaError_t launch_field_neighbours(const StepBuffers& B, const Box* boxes, int 
 }
 
 cudaError_t launch_collect_neighbours(const StepBuffers& B, const PhysicsDev& phys, cudaStream_t s) {
-    k_collect_neighbours<<<B.n_boxes, 256, 0, s>>>(phys, B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
+    if (phys.pool_ent) {
+        const cudaError_t e = cudaMemsetAsync(&B.st->pool_used, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
+    k_collect_neighbours<<<B.n_boxes, 256, 0, s>>>(phys, B.st, B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
                                                      const_cast<int*>(phys.nb_cnt), const_cast<float*>(phys.nb_w),
                                                      const_cast<float*>(phys.nb_m));
     return cudaGetLastError();
