@@ -732,8 +732,11 @@ static int create_impl(const lsgg_config* cfg_in, void* stream, lsgg_ctx** out) 
         // the pass path's neighbour-list pool: about 64 pairs per grain (a
         // box that finds no room looks its pairs up per cell)
         const long long cap = std::min(std::max(64LL * G, 4096LL), (long long)INT_MAX / 2);
-        if ((r = dalloc(c, &c->phys.pool_ent, (size_t)cap)) != LSGG_OK) return bail(r);
-        if ((r = dalloc(c, &c->phys.pool_box, (size_t)G)) != LSGG_OK) return bail(r);
+        for (int k = 0; k < 2; ++k) {
+            if ((r = dalloc(c, &c->phys.pool_ent[k], (size_t)cap)) != LSGG_OK) return bail(r);
+            if ((r = dalloc(c, &c->phys.pool_box[k], (size_t)G)) != LSGG_OK) return bail(r);
+            if (cudaMemset(c->phys.pool_box[k], 0, (size_t)G * sizeof(int2)) != cudaSuccess) return bail(CUDA_FAIL());
+        }
         c->phys.pool_cap = (int)cap;
     }
     if (from_labels) {

@@ -86,12 +86,13 @@ struct PhysicsDev {
     const float* nb_m;              // per grain and entry: pair mobility M
     // the pass path's complete neighbour lists of a READ_SHOCKLEY run (every
     // grain of a box's ID-field, ascending, up to kPoolKeys), refreshed
-    // before each predictor into one pool: entry {j, w, M, 0} (w, M as float
-    // bits); per box {first entry, count} with count -1 when the list did
-    // not fit
-    int4* pool_ent;                 // null: no pool (the z pass looks pairs up per cell)
-    int2* pool_box;
-    int pool_cap;                   // entries
+    // before each predictor into the pool of the step's parity (steps_done &
+    // 1; the other one holds the previous step's lists, whose weights are
+    // reused): entry {j, w, M, 0} (w, M as float bits); per box {first
+    // entry, count} with count -1 when the list did not fit
+    int4* pool_ent[2];              // null: no pool (the z pass looks pairs up per cell)
+    int2* pool_box[2];
+    int pool_cap;                   // entries per pool
     double theta_max;               // radians
     double mob_low;
     int mob_law;                    // LSGG_MOBILITY_*

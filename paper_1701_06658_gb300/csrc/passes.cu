@@ -493,7 +493,11 @@ p_conv_z(StepBuffers B1, GroupRef grp, Taps taps, PhysicsDev phys, int tier) {
     const int n_items = GRP ? group_scan(grp, kItemChunks, tier, true, s_gb) : B1.st->n_chunks[tier];
     const int2* items = GRP ? nullptr : B1.chunk_items + B1.st->chunk_base[tier];
     const bool rs = PHYS && phys.kind == LSGG_PHYSICS_READ_SHOCKLEY;
-    const bool pooled = PHYS && phys.pool_ent != nullptr && phys.pair_map == nullptr;
+    const bool pooled = PHYS && phys.pool_ent[0] != nullptr && phys.pair_map == nullptr;
+    // this step's pool (the parity of the steps done)
+    const bool odd = pooled && (B1.st->steps_done & 1);
+    const int2* pool_box = PHYS ? (odd ? phys.pool_box[1] : phys.pool_box[0]) : nullptr;
+    const int4* pool_ent = PHYS ? (odd ? phys.pool_ent[1] : phys.pool_ent[0]) : nullptr;
     int last_b = -1;
     int hash_n = -1;                                       // the box's pair hash entries, -1: none
     PairTable tab{s_tj, s_tw, s_tm, 0};
@@ -509,15 +513,15 @@ p_conv_z(StepBuffers B1, GroupRef grp, Taps taps, PhysicsDev phys, int tier) {
             hash_n = -1;
             tab.n = 0;
             if (pooled) {
-                const int2 pb = phys.pool_box[b];
+                const int2 pb = pool_box[b];
                 if (pb.y >= 0 && pb.y <= kZHash / 2) hash_n = pb.y;
             }
             if (hash_n >= 0) {
                 for (int k = threadIdx.x; k < kZHash; k += blockDim.x) s_hk[k] = -1;
                 __syncthreads();
-                const int2 pb = phys.pool_box[b];
+                const int2 pb = pool_box[b];
                 for (int k = threadIdx.x; k < hash_n; k += blockDim.x) {
-                    const int4 e = phys.pool_ent[pb.x + k];
+                    const int4 e = pool_ent[pb.x + k];
                     unsigned h = zhash(e.x);
                     while (atomicCAS(&s_hk[h], -1, e.x) != -1) h = (h + 1) & (kZHash - 1);
                     s_hw[h] = __int_as_float(e.y);

@@ -16,7 +16,66 @@ namespace lsgg {
 constexpr int kHashSlots = kPoolKeys;
 static_assert((kHashSlots & (kHashSlots - 1)) == 0, "hash slots: a power of two");
 
-__global__ void __launch_bounds__(256)
+// Key j enters the box's hash (shared, kHashSlots open-addressing slots);
+// a full table sets the overflow flag.
+__device__ __forceinline__ void collect_key(int* keys, int* n_keys, int* overflow, int j) {
+    unsigned h = ((unsigned)j * 2654435761u) >> 23;   // 9 bits
+    for (int probe = 0; probe < kHashSlots; ++probe) {
+        const int slot = (int)((h + probe) & (kHashSlots - 1));
+        const int cur = keys[slot];
+        if (cur == j) return;
+        if (cur == -1) {
+            const int prevk = atomicCAS(&keys[slot], -1, j);
+            if (prevk == -1) { atomicAdd(n_keys, 1); return; }
+            if (prevk == j) return;
+        }
+    }
+    *overflow = 1;
+}
+
+constexpr int kCollectThreads = 256;
+constexpr int kCollectLoads = 4;     // 16-byte loads in flight per thread
+
+// The box's ID-field as (plane, group of four consecutive cells) items (box
+// planes start on 32-byte boundaries), kCollectLoads items per thread loaded
+// together, each thread skipping repeats of the id it entered last.  I: the
+// index type (32-bit divisions whenever the items fit).
+template <class I>
+__device__ __forceinline__ void collect_walk(const int* base, int A, int ps, int nz, int* keys, int* n_keys,
+                                             int* overflow) {
+    const I nq = (I)((A + 3) >> 2);
+    const I items = nq * (I)nz;
+    int last = -1;
+    for (I i0 = threadIdx.x; i0 < items; i0 += (I)kCollectLoads * blockDim.x) {
+        int v[kCollectLoads][4];
+#pragma unroll
+        for (int k = 0; k < kCollectLoads; ++k) {
+            const I it = i0 + (I)k * blockDim.x;
+            const I z = it < items ? it / nq : 0;
+            const int q = 4 * (int)(it - z * nq);
+            const int* pl = base + (long long)z * ps;
+            if (it < items && q + 3 < A) {
+                const int4 w4 = *reinterpret_cast<const int4*>(pl + q);
+                v[k][0] = w4.x; v[k][1] = w4.y; v[k][2] = w4.z; v[k][3] = w4.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[k][u] = it < items && q + u < A ? pl[q + u] : -1;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kCollectLoads; ++k)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = v[k][u];
+                if (j < 0 || j == last) continue;
+                last = j;
+                collect_key(keys, n_keys, overflow, j);
+            }
+    }
+}
+
+// One CTA per box.
+__global__ void __launch_bounds__(kCollectThreads)
 k_collect_neighbours(PhysicsDev phys, StepState* st, const Box* __restrict__ prev, const int* __restrict__ IDF,
                      int* __restrict__ tab, int* __restrict__ cnt, float* __restrict__ tw, float* __restrict__ tm) {
     __shared__ int keys[kHashSlots];
@@ -27,32 +86,23 @@ k_collect_neighbours(PhysicsDev phys, StepState* st, const Box* __restrict__ pre
     if (threadIdx.x == 0) { n_keys = 0; overflow = 0; }
     __syncthreads();
     if (ob.nx > 0) {
-        const long long A = (long long)ob.nx * ob.ny, n = A * ob.nz;
+        const int A = ob.nx * ob.ny;
         const int ps = plane_stride(ob.nx, ob.ny);
-        int last = -1;
-        for (long long c = threadIdx.x; c < n; c += blockDim.x) {
-            const long long z = c / A, rem = c - z * A;
-            const int j = IDF[ob.off + z * ps + rem];
-            if (j < 0 || j == last) continue;
-            last = j;
-            unsigned h = ((unsigned)j * 2654435761u) >> 23;   // 9 bits
-            for (int probe = 0; probe < kHashSlots; ++probe) {
-                const int slot = (int)((h + probe) & (kHashSlots - 1));
-                const int cur = keys[slot];
-                if (cur == j) break;
-                if (cur == -1) {
-                    const int prevk = atomicCAS(&keys[slot], -1, j);
-                    if (prevk == -1) { atomicAdd(&n_keys, 1); break; }
-                    if (prevk == j) break;
-                }
-                if (probe == kHashSlots - 1) overflow = 1;
-            }
-        }
+        if ((long long)((A + 3) >> 2) * ob.nz < (1LL << 31) - 4LL * kCollectLoads * kCollectThreads)
+            collect_walk<unsigned>(IDF + ob.off, A, ps, ob.nz, keys, &n_keys, &overflow);
+        else
+            collect_walk<long long>(IDF + ob.off, A, ps, ob.nz, keys, &n_keys, &overflow);
     }
     __syncthreads();
-    // the box's place in the pool (every key, or none when they overflowed)
+    // the box's place in this step's pool (every key, or none when they overflowed)
     __shared__ int pool_base;
-    const bool pooled = phys.pool_ent != nullptr && !overflow;
+    // this step's pool and the previous step's (the parity of the steps done)
+    const bool odd = phys.pool_ent[0] && (st->steps_done & 1);
+    int2* const pool_box = odd ? phys.pool_box[1] : phys.pool_box[0];
+    int4* const pool_ent = odd ? phys.pool_ent[1] : phys.pool_ent[0];
+    const int2* const prev_box = odd ? phys.pool_box[0] : phys.pool_box[1];
+    const int4* const prev_pool = odd ? phys.pool_ent[0] : phys.pool_ent[1];
+    const bool pooled = pool_ent != nullptr && !overflow;
     if (threadIdx.x == 0) {
         int base = -1;
         if (pooled && n_keys > 0) {
@@ -60,27 +110,53 @@ k_collect_neighbours(PhysicsDev phys, StepState* st, const Box* __restrict__ pre
             if (base > phys.pool_cap - n_keys) base = -1;
         }
         pool_base = base;
-        if (phys.pool_ent) phys.pool_box[b] = make_int2(base < 0 ? 0 : base, n_keys == 0 ? 0 : (base < 0 ? -1 : n_keys));
+        if (pool_ent) pool_box[b] = make_int2(base < 0 ? 0 : base, n_keys == 0 ? 0 : (base < 0 ? -1 : n_keys));
+    }
+    // the keys in consecutive entries, then ranked (ascending) among
+    // themselves, so that the weights below are evaluated by full warps
+    __shared__ int packed[kHashSlots], sorted[kHashSlots];
+    __shared__ int n_packed;
+    if (threadIdx.x == 0) n_packed = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x)
+        if (keys[k] >= 0) packed[atomicAdd(&n_packed, 1)] = keys[k];
+    __syncthreads();
+    const int np = n_packed;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const int j = packed[k];
+        int rank = 0;
+        for (int q = 0; q < np; ++q) rank += packed[q] < j;
+        sorted[rank] = j;
     }
     __syncthreads();
     const bool rs = phys.kind == LSGG_PHYSICS_READ_SHOCKLEY;
-    // rank-sort the keys (ascending): the first kNbCap in the grain's table,
-    // all of them in the pool, each with its pair weights (FP64
-    // disorientation, once per grain, pair and step)
-    for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x) {
-        const int j = keys[k];
-        if (j < 0) continue;
-        int rank = 0;
-        for (int q = 0; q < kHashSlots; ++q) rank += (unsigned)keys[q] < (unsigned)j && keys[q] >= 0;
-        if (rank >= kNbCap && pool_base < 0) continue;
+    // the first kNbCap in the grain's table, all of them in the pool, each
+    // with its pair weights: the previous step's list of the box (the other
+    // pool) gives those of the pairs it held, the rest are evaluated (FP64
+    // disorientation)
+    const int2 prev_list = pool_ent ? prev_box[b] : make_int2(0, 0);
+    const int4* prev_ent = pool_ent ? prev_pool + prev_list.x : nullptr;
+    const int n_eval = pool_base >= 0 ? n_keys : min(n_keys, kNbCap);
+    for (int rank = threadIdx.x; rank < n_eval; rank += blockDim.x) {
+        const int j = sorted[rank];
         float w = 1.0f, m = 1.0f;
-        if (rs) rs_pair(phys, b, j, w, m);
+        if (rs) {
+            int lo = 0, hi = prev_list.y - 1;             // count -1: no list
+            bool hit = false;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int4 e = prev_ent[mid];
+                if (e.x == j) { w = __int_as_float(e.y); m = __int_as_float(e.z); hit = true; break; }
+                if (e.x < j) lo = mid + 1; else hi = mid - 1;
+            }
+            if (!hit) rs_pair(phys, b, j, w, m);
+        }
         if (rs && rank < kNbCap) {
             tab[(size_t)b * kNbCap + rank] = j;
             tw[(size_t)b * kNbCap + rank] = w;
             tm[(size_t)b * kNbCap + rank] = m;
         }
-        if (pool_base >= 0) phys.pool_ent[pool_base + rank] = make_int4(j, __float_as_int(w), __float_as_int(m), 0);
+        if (pool_base >= 0) pool_ent[pool_base + rank] = make_int4(j, __float_as_int(w), __float_as_int(m), 0);
     }
     if (threadIdx.x == 0 && rs) cnt[b] = (overflow || n_keys > kNbCap) ? kNbCap + 1 : n_keys;
 }
@@ -145,11 +221,11 @@ cudaError_t launch_field_neighbours(const StepBuffers& B, const Box* boxes, int 
 }
 
 cudaError_t launch_collect_neighbours(const StepBuffers& B, const PhysicsDev& phys, cudaStream_t s) {
-    if (phys.pool_ent) {
+    if (phys.pool_ent[0]) {
         const cudaError_t e = cudaMemsetAsync(&B.st->pool_used, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
-    k_collect_neighbours<<<B.n_boxes, 256, 0, s>>>(phys, B.st, B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
+    k_collect_neighbours<<<B.n_boxes, kCollectThreads, 0, s>>>(phys, B.st, B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
                                                      const_cast<int*>(phys.nb_cnt), const_cast<float*>(phys.nb_w),
                                                      const_cast<float*>(phys.nb_m));
     return cudaGetLastError();

@@ -1218,7 +1218,7 @@ cudaError_t launch_step(const StepBuffers& B, const Taps& taps, const PhysicsDev
     if (ev) cudaEventRecord(ev[1], s);
     DebugOut d{};
     if (dbg) d = *dbg;
-    if (phys.kind == LSGG_PHYSICS_READ_SHOCKLEY || phys.pool_ent) {
+    if (phys.kind == LSGG_PHYSICS_READ_SHOCKLEY || phys.pool_ent[0]) {
         e = traced(launch_collect_neighbours(B, phys, s), "neighbour tables");
         if (e != cudaSuccess) return e;
     }
