@@ -105,3 +105,40 @@ def test_laguerre_init_matches_oracle(L):
             assert (boxes[g, 3], boxes[g, 2], boxes[g, 1]) == gr.origin
             assert (boxes[g, 6], boxes[g, 5], boxes[g, 4]) == gr.dims
             assert np.max(np.abs(phi[g] - gr.phi.astype(np.float32))) <= 1e-6
+
+
+@pytest.mark.parametrize("G,seed,min_ids", [(600, 71, 400), (900, 72, 600)])
+def test_read_shockley_box_with_hundreds_of_neighbours(L, G, seed, min_ids):
+    """A power-diagram grain of weight 420 takes about half of a 48^3 domain
+    among G - 1 small grains; after one oracle step its box (the whole
+    domain) holds hundreds of grains in its ID-field (the largest other grain
+    of every cell).  From that state, with that ID-field, one Read-Shockley
+    step matches the oracle stage by stage: with 600 grains the box's pairs
+    pass the 96-entry table and fit the per-box pair list and hash; with 900
+    they also pass the collection's 512 keys, and the z pass takes the fixed
+    table and direct FP64 evaluations."""
+    from tests.parity import oracle_from_gpu
+    N = 48
+    seeds = I.voronoi_seeds(seed, G, (N, N, N))
+    w = np.zeros(G)
+    w[0] = 420.0
+    quats = I.random_quaternions(seed, G)
+    phys = O.read_shockley_physics(quats)
+    ref0 = O.run(O.tessellate((N, N, N), seeds, weights=w, physics=phys), 1, 1.0)
+    g0 = ref0.grains[0]
+    assert g0.dims == (N, N, N)
+    assert len(np.unique(g0.idf[g0.idf >= 0])) >= min_ids
+    boxes = np.zeros((G, 7), np.int32)
+    phi, idf = {}, {}
+    for g in ref0.grains:
+        if not g.alive:
+            continue
+        oz, oy, ox = g.origin
+        nz, ny, nx = g.dims
+        boxes[g.gid] = (1, ox, oy, oz, nx, ny, nz)
+        phi[g.gid] = g.phi.astype(np.float32)
+        idf[g.gid] = g.idf.astype(np.int32)
+    with L.Microstructure(N, N, N, G, seeds=seeds, weights=w, quats=quats, physics=L.PHYSICS_READ_SHOCKLEY) as ms:
+        ms.set_state(boxes, phi, idf)
+        ref_ms = oracle_from_gpu((N, N, N), ms.boxes(), ms.phi(), idf, physics=phys)
+        _compare_step(L, ms, ref_ms)
