@@ -38,21 +38,25 @@ constexpr int kCollectLoads = 4;     // 16-byte loads in flight per thread
 
 // The box's ID-field as (plane, group of four consecutive cells) items (box
 // planes start on 32-byte boundaries), kCollectLoads items per thread loaded
-// together, each thread skipping repeats of the id it entered last.  I: the
-// index type (32-bit divisions whenever the items fit).
+// together; a cell probes the hash only where a run of equal ids starts and
+// its thread has not entered that id last.  I: the index type (32-bit
+// divisions whenever the items fit).
 template <class I>
 __device__ __forceinline__ void collect_walk(const int* base, int A, int ps, int nz, int* keys, int* n_keys,
                                              int* overflow) {
     const I nq = (I)((A + 3) >> 2);
     const I items = nq * (I)nz;
     int last = -1;
-    for (I i0 = threadIdx.x; i0 < items; i0 += (I)kCollectLoads * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    // the loop is uniform across each warp (its lanes exchange values below)
+    for (I w0 = threadIdx.x - lane; w0 < items; w0 += (I)kCollectLoads * blockDim.x) {
+        const I i0 = w0 + lane;
         int v[kCollectLoads][4];
 #pragma unroll
         for (int k = 0; k < kCollectLoads; ++k) {
             const I it = i0 + (I)k * blockDim.x;
             const I z = it < items ? it / nq : 0;
-            const int q = 4 * (int)(it - z * nq);
+            const int q = it < items ? 4 * (int)(it - z * nq) : 0;
             const int* pl = base + (long long)z * ps;
             if (it < items && q + 3 < A) {
                 const int4 w4 = *reinterpret_cast<const int4*>(pl + q);
@@ -62,15 +66,22 @@ __device__ __forceinline__ void collect_walk(const int* base, int A, int ps, int
                 for (int u = 0; u < 4; ++u) v[k][u] = it < items && q + u < A ? pl[q + u] : -1;
             }
         }
+        // a value equal to the cell before it (the lane's own previous cell, or
+        // the previous lane's last one: lanes hold consecutive groups) is
+        // already entered or being entered: only the starts of runs probe
 #pragma unroll
-        for (int k = 0; k < kCollectLoads; ++k)
+        for (int k = 0; k < kCollectLoads; ++k) {
+            int before = __shfl_up_sync(0xffffffffu, v[k][3], 1);
+            if (lane == 0) before = -1;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int j = v[k][u];
-                if (j < 0 || j == last) continue;
+                const bool run_start = j != (u == 0 ? before : v[k][u - 1]);
+                if (j < 0 || !run_start || j == last) continue;
                 last = j;
                 collect_key(keys, n_keys, overflow, j);
             }
+        }
     }
 }
 
