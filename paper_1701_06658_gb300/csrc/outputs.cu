@@ -1,12 +1,16 @@
 // Outputs of a microstructure.
 //
 //   k_volumes   V_i = sum_x H(phi_i(x)), H(phi) = clamp(phi + 1/2, 0, 1): one CTA
-//               per box over the state's own layout (`prev`).  Each thread sums
-//               its cells in fixed point (H in units of 2^-28 is an integer,
-//               exactly for every |phi| >= 2^-5 and to 2^-29 below, so the
-//               64-bit sum is exact); the threads' partials are merged in FP64
-//               with compensated (TwoSum) additions in a fixed tree order, so
-//               the result is the same on every run.
+//               per box over the state's own layout (`prev`), 16-byte loads,
+//               four in flight per thread.  Each thread sums its cells in
+//               fixed point (H in units of 2^-28 is an integer, exactly for
+//               every |phi| >= 2^-5 and to 2^-29 below, so the 64-bit sum is
+//               exact); the threads' partials are merged in FP64 with
+//               compensated (TwoSum) additions in a fixed tree order.  For a
+//               box of fewer than 2^25 cells every partial sum is an integer
+//               multiple of 2^-28 below 2^25, exact in FP64, so the result is
+//               the exact sum whatever the cells' order; larger boxes keep the
+//               compensated sum's rounding, the same on every run.
 //   k_owner_*   owner(x) = argmax_i phi_i(x) over boxes covering x, lowest id on
 //               ties (64-bit atomicMax of (phi, -id) keys), -1 where uncovered.
 //   k_remap     the state phi (stored in the `prev` layout) resampled on the
@@ -36,6 +40,51 @@ __device__ __forceinline__ float state_value(const Domain& D, const Box& nb, con
     return X[ob.off + (long long)lz * plane_stride(ob.nx, ob.ny) + ly * ob.nx + lx];
 }
 
+// H of one cell in units of 2^-28 (an integer: exact for every |phi| >=
+// 2^-5 and to 2^-29 below); no cell (phi = -1 here) gives 0.
+__device__ __forceinline__ long long vol_units(float v) {
+    constexpr float kScale = 268435456.0f;           // 2^28
+    constexpr int kHalf = 1 << 27, kOne = 1 << 28;
+    const int q = __float2int_rn(v * kScale);        // |phi| <= eps: no overflow
+    return min(max(q + kHalf, 0), kOne);
+}
+
+constexpr int kVolLoads = 4;     // 16-byte loads in flight per thread
+
+// Sum of H over one box in its layout (planes of A cells at stride ps, each
+// starting on a 32-byte boundary), as (plane, group of four cells) items,
+// kVolLoads of them per thread loaded together.  The sum is of integers:
+// the same in any order.  I: the index type (32-bit divisions whenever the
+// items fit).
+template <class I>
+__device__ __forceinline__ long long volume_walk(const float* base, int A, int ps, int nz) {
+    const I nq = (I)((A + 3) >> 2);
+    const I items = nq * (I)nz;
+    long long acc = 0;
+    for (I i0 = threadIdx.x; i0 < items; i0 += (I)kVolLoads * blockDim.x) {
+        float v[kVolLoads][4];
+#pragma unroll
+        for (int k = 0; k < kVolLoads; ++k) {
+            const I it = i0 + (I)k * blockDim.x;
+            const I z = it < items ? it / nq : 0;
+            const int q = it < items ? 4 * (int)(it - z * nq) : 0;
+            const float* pl = base + (long long)z * ps;
+            if (it < items && q + 3 < A) {
+                const float4 w4 = __ldg(reinterpret_cast<const float4*>(pl + q));
+                v[k][0] = w4.x; v[k][1] = w4.y; v[k][2] = w4.z; v[k][3] = w4.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[k][u] = it < items && q + u < A ? __ldg(pl + q + u) : -1.0f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kVolLoads; ++k)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc += vol_units(v[k][u]);
+    }
+    return acc;
+}
+
 // The state lives in the `prev` layout; a cell of the prev box outside the
 // current box is at least halo + 1 cells from every positive cell, so its
 // phi <= -halo and H = 0: summing the prev box is summing the current box.
@@ -44,27 +93,15 @@ k_volumes(Domain D, const Box* __restrict__ cur, const Box* __restrict__ prev, c
           double* __restrict__ out) {
     __shared__ double s_s[256], s_c[256];
     const int b = blockIdx.x;
-    constexpr float kScale = 268435456.0f;           // 2^28
-    constexpr int kHalf = 1 << 27, kOne = 1 << 28;
+    constexpr int kOne = 1 << 28;
     long long acc = 0;
     if (cur[b].nx > 0) {
         const Box ob = prev[b];
         const int A = ob.nx * ob.ny, ps = plane_stride(ob.nx, ob.ny);
-        // four planes per pass: four independent loads in flight per thread
-        for (int z0 = 0; z0 < ob.nz; z0 += 4) {
-            const float* pl = X + ob.off + (long long)z0 * ps;
-            const int nzp = min(4, ob.nz - z0);
-            for (int i = threadIdx.x; i < A; i += blockDim.x) {
-                float v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = u < nzp ? __ldg(pl + (long long)u * ps + i) : -1.0f;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = __float2int_rn(v[u] * kScale);         // |phi| <= eps: no overflow
-                    acc += min(max(q + kHalf, 0), kOne);                 // phi = -1 (no plane): 0
-                }
-            }
-        }
+        if ((long long)((A + 3) >> 2) * ob.nz < (1LL << 31) - 4LL * kVolLoads * 256)
+            acc = volume_walk<unsigned>(X + ob.off, A, ps, ob.nz);
+        else
+            acc = volume_walk<long long>(X + ob.off, A, ps, ob.nz);
     }
     s_s[threadIdx.x] = (double)acc / (double)kOne;   // exact: acc < 2^53
     s_c[threadIdx.x] = 0.0;

@@ -579,11 +579,13 @@ class Microstructure:
     def sync(self, timeout_ms: int = -1):
         sync(self.ctx, timeout_ms)
 
-    def grain_volumes(self) -> np.ndarray:
-        return grain_volumes(self.ctx, self.n_grains)
+    def grain_volumes(self, out=None) -> np.ndarray:
+        """Volumes into `out` (n_grains float64, e.g. a view of pinned memory) or a new array."""
+        return grain_volumes(self.ctx, self.n_grains, out)
 
-    def voxel_owner(self) -> np.ndarray:
-        return voxel_owner(self.ctx, self.shape)
+    def voxel_owner(self, out=None) -> np.ndarray:
+        """Owner map into `out` ((nz, ny, nx) int32, e.g. a view of pinned memory) or a new array."""
+        return voxel_owner(self.ctx, self.shape, out)
 
     def grain_statistics(self, n_bins: int = 20, r_max: float = 3.0) -> dict:
         return grain_statistics(self.ctx, n_bins, r_max)
