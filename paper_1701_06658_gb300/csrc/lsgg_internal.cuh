@@ -80,8 +80,8 @@ struct PhysicsDev {
     const double* quats;            // per grain unit quaternion (w, x, y, z) (READ_SHOCKLEY)
     const int* pair_map;            // per cell of `cur` the pair's j (the anisotropy map), or null: the
                                     // previous step's ID-field (`prev` layout) gives j
-    const int* nb_tab;              // per grain: ascending ids of the grains in its ID-field
-    const int* nb_cnt;              // per grain: entries (kNbCap + 1: the table overflowed)
+    const int* nb_tab;              // per grain: the first kNbCap ascending ids of the grains in its ID-field
+    const int* nb_cnt;              // per grain: entries (kNbCap + 1: more ids than the table holds)
     const float* nb_w;              // per grain and entry: pair weight w (READ_SHOCKLEY, refreshed with nb_tab)
     const float* nb_m;              // per grain and entry: pair mobility M
     // the pass path's complete neighbour lists of a READ_SHOCKLEY run (every

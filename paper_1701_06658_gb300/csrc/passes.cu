@@ -11,8 +11,9 @@
 //   p_conv_xy   (box, plane): bulk copy of the plane of phi in the old layout,
 //               staged into the new layout (-eps outside), x and y passes in
 //               shared memory                                     -> Z = xy-convolved
-//   p_conv_z    (box, columns): z pass over a register window, velocity
-//               correction, clamp                                 -> Y = phi_p
+//   p_conv_z    (box, columns): z pass from the column in registers, velocity
+//               correction (Read-Shockley pairs from a per-box hash of the
+//               step's neighbour list), clamp                     -> Y = phi_p
 //   p_field     (domain tile): the two largest (phi_p, grain) per cell over
 //               the tile's boxes in registers (stored in T as (phi_p, -id)
 //               keys only on request, B.keep_field); then
