@@ -1749,6 +1749,8 @@ template <int R, bool GRP>
 __global__ void __launch_bounds__(256)
 p_conv_xy_big(StepBuffers B1, GroupRef grp, Taps taps, int tier) {
     constexpr int W = 2 * R + 1;
+    constexpr int kChunk = 128;                            // x outputs per staged row segment
+    __shared__ float s_row[8][kChunk + 2 * R];             // per warp: the segment's inputs (old layout, -eps outside)
     __shared__ int s_flag;
     __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -1781,20 +1783,27 @@ p_conv_xy_big(StepBuffers B1, GroupRef grp, Taps taps, int tier) {
             const int oy = wrap_near(nb.oy + y - ob.oy, D.ny);
             const bool rin = zin && oy < ob.ny;
             const long long rbase = obase + (long long)oy * ob.nx;
-            for (int x = lane; x < nx; x += 32) {
-                float acc = 0.0f;
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    int xl = x + k - R;
+            float* sr = s_row[warp];
+            for (int x0 = 0; x0 < nx; x0 += kChunk) {      // segments: inputs staged once per warp
+                const int nout = min(kChunk, nx - x0);
+                for (int q = lane; q < nout + 2 * R; q += 32) {
+                    int xl = x0 + q - R;
                     float v = -D.eps;
                     if (fx || (xl >= 0 && xl < nx)) {
                         if (fx) xl = wrap_near(xl, nx);
                         const int ox = wrap_near(nb.ox + xl - ob.ox, D.nx);
                         if (rin && ox < ob.nx) v = ld_state(B, rbase + ox);
                     }
-                    acc = fmaf(g[k], v, acc);
+                    sr[q] = v;
                 }
-                rows[(long long)y * nx + x] = acc;
+                __syncwarp();
+                for (int x = lane; x < nout; x += 32) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < W; ++k) acc = fmaf(g[k], sr[x + k], acc);
+                    rows[(long long)y * nx + x0 + x] = acc;
+                }
+                __syncwarp();                               // the segment is read before the next one
             }
         }
         __syncthreads();
@@ -1822,6 +1831,11 @@ p_conv_xy_big(StepBuffers B1, GroupRef grp, Taps taps, int tier) {
 template <bool GRP>
 __global__ void __launch_bounds__(256)
 p_redist_xy_big(StepBuffers B1, GroupRef grp, int tier) {
+    constexpr int R = kRedistReach;
+    constexpr int kChunk = 128;                            // x outputs per staged row segment
+    constexpr int kTY = 64;                                // rows per staged column tile
+    __shared__ float s_row[8][kChunk + 2 * R];             // per warp: a row segment's magnitudes
+    __shared__ float s_col[kTY + 2 * R][33];               // a tile of 32 columns (padded)
     __shared__ int s_flag;
     __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -1862,21 +1876,56 @@ p_redist_xy_big(StepBuffers B1, GroupRef grp, int tier) {
             }
         }
         __syncthreads();
-        for (int y = t; y < ny; y += blockDim.x) {         // x scans: thread per row
-            if (fx) scan_line_wrap(G + (long long)y * nx, nx, 1);
-            else scan_line_serial(G + (long long)y * nx, nx, 1);
-        }
-        __syncthreads();
-        for (int x = t; x < nx; x += blockDim.x) {         // y scans: thread per column, then the signs
-            if (fy) scan_line_wrap(G + x, ny, nx);
-            else scan_line_serial(G + x, ny, nx);
-            for (int y = 0; y < ny; ++y) {
-                const long long i = (long long)y * nx + x;
-                const float m = G[i];
-                G[i] = __ldg(c + i) > 0.0f ? m : -m;
+        // The line transforms as windows: no magnitude exceeds eps = 7, so a
+        // cell's taxicab distance along a line is min over |k| <= R = 6 of
+        // m(x + k) + |k| (past the ends of a non-periodic line: eps, which
+        // never undercuts), and a window over values already transformed
+        // gives the same distance.
+        for (int y = warp; y < ny; y += 8) {               // x: warp per row, segments staged per warp
+            float* row = G + (long long)y * nx;
+            float* sr = s_row[warp];
+            for (int x0 = 0; x0 < nx; x0 += kChunk) {
+                const int nout = min(kChunk, nx - x0);
+                for (int q = lane; q < nout + 2 * R; q += 32) {
+                    const int xl = x0 + q - R;
+                    sr[q] = fx ? row[pmod(xl, nx)] : (xl >= 0 && xl < nx ? row[xl] : eps);
+                }
+                __syncwarp();
+                for (int x = lane; x < nout; x += 32) {
+                    float d = sr[x + R];
+#pragma unroll
+                    for (int k = 1; k <= R; ++k) d = fminf(d, fminf(sr[x + R - k], sr[x + R + k]) + (float)k);
+                    row[x0 + x] = d;
+                }
+                __syncwarp();                               // the segment is read before the next one
             }
         }
-        __syncthreads();                                    // G is final before the next item
+        __syncthreads();
+        for (int x0 = 0; x0 < nx; x0 += 32) {              // y: tiles of 32 columns x kTY rows, then the signs
+            const int xc = x0 + lane;
+            for (int y0 = 0; y0 < ny; y0 += kTY) {
+                const int nrow = min(kTY, ny - y0);
+                for (int r = warp; r < nrow + 2 * R; r += 8) {
+                    const int yl = y0 + r - R;
+                    float v = eps;
+                    if (xc < nx) {
+                        if (fy) v = fabsf(G[(long long)pmod(yl, ny) * nx + xc]);
+                        else if (yl >= 0 && yl < ny) v = fabsf(G[(long long)yl * nx + xc]);
+                    }
+                    s_col[r][lane] = v;
+                }
+                __syncthreads();
+                for (int r = warp; r < nrow; r += 8) {
+                    if (xc >= nx) continue;
+                    float d = s_col[r + R][lane];
+#pragma unroll
+                    for (int k = 1; k <= R; ++k) d = fminf(d, fminf(s_col[r + R - k][lane], s_col[r + R + k][lane]) + (float)k);
+                    const long long i = (long long)(y0 + r) * nx + xc;
+                    G[i] = __ldg(c + i) > 0.0f ? d : -d;
+                }
+                __syncthreads();                            // the tile is read before the next one
+            }
+        }
     }
 }
 
