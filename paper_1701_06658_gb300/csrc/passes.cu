@@ -1750,7 +1750,9 @@ __global__ void __launch_bounds__(256)
 p_conv_xy_big(StepBuffers B1, GroupRef grp, Taps taps, int tier) {
     constexpr int W = 2 * R + 1;
     constexpr int kChunk = 128;                            // x outputs per staged row segment
+    constexpr int kTY = 64;                                // rows per staged column tile
     __shared__ float s_row[8][kChunk + 2 * R];             // per warp: the segment's inputs (old layout, -eps outside)
+    __shared__ float s_col[kTY + 2 * R][33];               // a tile of 32 columns of the x-convolved rows (padded)
     __shared__ int s_flag;
     __shared__ int s_gb[GRP ? kMaxGroup + 1 : 1];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -1808,23 +1810,30 @@ p_conv_xy_big(StepBuffers B1, GroupRef grp, Taps taps, int tier) {
         }
         __syncthreads();
         float* dst = B.Z + nb.off + (long long)z * ps;
-        for (int y = warp; y < ny; y += 8) {               // y pass
-            for (int x = lane; x < nx; x += 32) {
-                float acc = 0.0f;
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    int yl = y + k - R;
-                    float v = aconst;
-                    if (fy || (yl >= 0 && yl < ny)) {
+        for (int x0 = 0; x0 < nx; x0 += 32) {              // y pass: tiles of 32 columns x kTY rows
+            const int xc = x0 + lane;
+            for (int y0 = 0; y0 < ny; y0 += kTY) {
+                const int nrow = min(kTY, ny - y0);
+                for (int r = warp; r < nrow + 2 * R; r += 8) {
+                    int yl = y0 + r - R;
+                    float v = aconst;                       // a row outside the box: the x convolution of -eps
+                    if (xc < nx && (fy || (yl >= 0 && yl < ny))) {
                         if (fy) yl = wrap_near(yl, ny);
-                        v = rows[(long long)yl * nx + x];
+                        v = rows[(long long)yl * nx + xc];
                     }
-                    acc = fmaf(g[k], v, acc);
+                    s_col[r][lane] = v;
                 }
-                dst[(long long)y * nx + x] = acc;
+                __syncthreads();
+                for (int r = warp; r < nrow; r += 8) {
+                    if (xc >= nx) continue;
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < W; ++k) acc = fmaf(g[k], s_col[r + k][lane], acc);
+                    dst[(long long)(y0 + r) * nx + xc] = acc;
+                }
+                __syncthreads();                            // the tile is read before the next one
             }
         }
-        __syncthreads();                                    // rows are read before the next item
     }
 }
 
