@@ -282,6 +282,50 @@ def test_same_sign_restriction_is_immaterial(oracle, shape, full):
         assert np.max(np.abs(got - want)) < 1e-12
 
 
+@pytest.mark.parametrize("shape,full", [((6, 13, 17), (False,) * 3), ((5, 16, 9), (True, True, False)),
+                                         ((1, 21, 14), (False, False, True))])
+def test_separable_windows_equal_the_transform(oracle, shape, full):
+    """The kernels' form of that transform: one line at a time (x, then y,
+    then z), each cell taking min over |k| <= 6 of m(x + k) + |k| (past the
+    end of a non-periodic line eps, on a periodic one the wrapped cell).  As
+    no magnitude exceeds eps = 7, a window of 6 steps is the whole line, and
+    the three windowed passes give the unrestricted transform exactly."""
+    rng = np.random.default_rng(23)
+    axes = oracle.spatial_axes(shape)
+    idx = np.stack(np.meshgrid(*[np.arange(n) for n in shape], indexing="ij"), -1).reshape(-1, 3)
+    for trial in range(3):
+        phic = rng.uniform(-3, 3, size=shape) + rng.uniform(-1, 1)
+        is_ref, dref = oracle.reference_values(phic, full, 7.0, axes)
+        m = np.where(is_ref, dref, 7.0)
+        d = np.abs(idx[:, None, :] - idx[None, :, :])
+        for a in range(3):
+            if full[a]:
+                d[..., a] = np.minimum(d[..., a], shape[a] - d[..., a])
+        brute = np.minimum(7.0, (m.reshape(-1)[None, :] + d.sum(-1)).min(axis=1)).reshape(shape)
+        f = m.copy()
+        for a in (2, 1, 0):                                 # x, y, z (array axes z, y, x)
+            n = shape[a]
+            if n == 1:
+                continue
+            out = f.copy()
+            for k in range(1, 7):
+                for sgn in (1, -1):
+                    if full[a]:
+                        nb = np.roll(f, -sgn * k, axis=a)
+                    else:
+                        nb = np.full_like(f, 7.0)
+                        src = [slice(None)] * 3
+                        dst = [slice(None)] * 3
+                        if sgn > 0:
+                            src[a], dst[a] = slice(k, None), slice(0, n - k)
+                        else:
+                            src[a], dst[a] = slice(0, n - k), slice(k, None)
+                        nb[tuple(dst)] = f[tuple(src)]
+                    out = np.minimum(out, nb + k)
+            f = out
+        assert np.max(np.abs(np.minimum(f, 7.0) - brute)) < 1e-12
+
+
 def test_godunov_update_solves_the_upwind_equation(oracle):
     """R11: the closed-form update is the smallest root of
     sum_k max(u - a_k, 0)^2 = 1, found here by bisection instead."""
