@@ -546,27 +546,30 @@ class Microstructure:
             else:
                 setattr(cfg, k, v)
         self._keep = []
+
+        def _sized(a, n, what):
+            # the C ABI reads the arrays through plain pointers: their sizes are checked here
+            if a.size != n:
+                raise ValueError(f"{what}: {a.size} values where {n} are read")
+            self._keep.append(a)
+            return a
+
         if seeds is not None:
-            s = np.ascontiguousarray(seeds, dtype=np.float64)
-            self._keep.append(s)
+            s = _sized(np.ascontiguousarray(seeds, dtype=np.float64), 3 * n_grains, "seeds")
             cfg.seeds = _ptr(s, C.c_double)
         if weights is not None:
-            w = np.ascontiguousarray(weights, dtype=np.float64)
-            self._keep.append(w)
+            w = _sized(np.ascontiguousarray(weights, dtype=np.float64), n_grains, "weights")
             cfg.weights = _ptr(w, C.c_double)
         cfg.init_kind = (INIT_LAGUERRE if weights is not None else INIT_VORONOI) if init_kind is None else init_kind
         if labels is not None:                       # (z, y, x) grain ids: the label-field initialisation
-            lab = np.ascontiguousarray(labels, dtype=np.int32)
-            self._keep.append(lab)
+            lab = _sized(np.ascontiguousarray(labels, dtype=np.int32), nx * ny * nz, "labels")
             cfg.labels = _ptr(lab, C.c_int32)
             cfg.init_kind = INIT_LABELS
         if quats is not None:
-            q = np.ascontiguousarray(quats, dtype=np.float64)
-            self._keep.append(q)
+            q = _sized(np.ascontiguousarray(quats, dtype=np.float64), 4 * n_grains, "quats")
             cfg.quats = _ptr(q, C.c_double)
         if energy is not None:
-            e = np.ascontiguousarray(energy, dtype=np.float64)
-            self._keep.append(e)
+            e = _sized(np.ascontiguousarray(energy, dtype=np.float64), n_grains, "energy")
             cfg.energy = _ptr(e, C.c_double)
         self.shape = (nz, ny, nx)
         self.n_grains = n_grains

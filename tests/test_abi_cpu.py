@@ -208,3 +208,14 @@ def test_label_field_configuration_is_checked(case):
         cfg.labels = lab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     ctx = ctypes.c_void_p()
     assert L.lib().lsgg_create_microstructure(ctypes.byref(cfg), None, ctypes.byref(ctx)) == want
+
+
+@pytest.mark.parametrize("kw", [{"labels": np.zeros(100, dtype=np.int32)}, {"seeds": np.zeros((3, 3))},
+                                {"weights": np.zeros(5)}, {"quats": np.zeros((4, 3))}, {"energy": np.zeros(2)}])
+def test_input_array_sizes_are_checked_by_the_binding(kw):
+    """The C ABI reads the config's arrays through plain pointers (3 n_grains
+    seeds, n_grains weights and energies, 4 n_grains quaternions, nx ny nz
+    labels); the binding refuses an array of another size before calling it."""
+    L = _lib()
+    with pytest.raises(ValueError):
+        L.Microstructure(8, 8, 8, 4, **kw)
