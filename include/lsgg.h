@@ -456,7 +456,8 @@ int lsgg_server_create(int64_t budget_bytes, int32_t max_active, int32_t steps_p
  * LSGG_SERVE_PER_CONTEXT (anything else: LSGG_ERR_INVALID_ARG). */
 int lsgg_server_create_mode(int64_t budget_bytes, int32_t max_active, int32_t steps_per_round, int32_t device,
                             int32_t mode, lsgg_server** out);
-/* Queue a request; cfg (and its arrays) are copied.  *ticket identifies it.
+/* Queue a request; cfg and its arrays (seeds, weights, quats, energy, labels)
+ * are copied before the call returns.  *ticket identifies it.
  * A request whose estimate exceeds the whole budget fails with
  * LSGG_ERR_OVER_BUDGET when it reaches the head of the queue. */
 int lsgg_server_submit(lsgg_server* s, const lsgg_config* cfg, int32_t n_steps, double dt, int64_t* ticket);

@@ -39,6 +39,7 @@ struct Request {
     int64_t ticket = 0;
     lsgg_config cfg{};
     std::vector<double> seeds, weights, quats, energy;
+    std::vector<int32_t> labels;
     int32_t n_steps = 0;
     double dt = 1.0;
     int64_t estimate = 0;
@@ -209,6 +210,7 @@ bool lsgg_server::admit_one(std::unique_lock<std::mutex>& lk) {
     cfg.weights = r->weights.empty() ? nullptr : r->weights.data();
     cfg.quats = r->quats.empty() ? nullptr : r->quats.data();
     cfg.energy = r->energy.empty() ? nullptr : r->energy.data();
+    cfg.labels = r->labels.empty() ? nullptr : r->labels.data();
     cfg.device = device;
     lk.unlock();
     lsgg_ctx* ctx = nullptr;
@@ -339,6 +341,7 @@ int lsgg_server_submit(lsgg_server* s, const lsgg_config* cfg, int32_t n_steps, 
     if (cfg->weights) r->weights.assign(cfg->weights, cfg->weights + g);
     if (cfg->quats) r->quats.assign(cfg->quats, cfg->quats + 4 * g);
     if (cfg->energy) r->energy.assign(cfg->energy, cfg->energy + g);
+    if (cfg->labels) r->labels.assign(cfg->labels, cfg->labels + (size_t)cfg->nx * cfg->ny * cfg->nz);
     r->n_steps = n_steps;
     r->dt = dt;
     r->estimate = estimate_bytes(*cfg);

@@ -666,15 +666,26 @@ class Server:
         self._n_grains = {}
 
     def submit(self, nx: int, ny: int, nz: int, n_grains: int, n_steps: int, dt: float = 1.0, seed: int = 1,
-               seeds=None, **fields) -> int:
+               seeds=None, labels=None, **fields) -> int:
+        """Queue a request (the library copies the config and its arrays)."""
         cfg = config_default()
         cfg.nx, cfg.ny, cfg.nz, cfg.n_grains, cfg.seed = nx, ny, nz, n_grains, seed
         for k, v in fields.items():
             setattr(cfg, k, v)
-        keep = None
+        keep = []
         if seeds is not None:
-            keep = np.ascontiguousarray(seeds, dtype=np.float64)
-            cfg.seeds = _ptr(keep, C.c_double)
+            s = np.ascontiguousarray(seeds, dtype=np.float64)
+            if s.size != 3 * n_grains:
+                raise ValueError(f"seeds: {s.size} values where {3 * n_grains} are read")
+            keep.append(s)
+            cfg.seeds = _ptr(s, C.c_double)
+        if labels is not None:
+            lab = np.ascontiguousarray(labels, dtype=np.int32)
+            if lab.size != nx * ny * nz:
+                raise ValueError(f"labels: {lab.size} values where {nx * ny * nz} are read")
+            keep.append(lab)
+            cfg.labels = _ptr(lab, C.c_int32)
+            cfg.init_kind = INIT_LABELS
         t = C.c_int64()
         _check("server_submit", lib().lsgg_server_submit(self.h, C.byref(cfg), int(n_steps), float(dt), C.byref(t)))
         self._n_grains[t.value] = n_grains

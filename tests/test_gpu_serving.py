@@ -92,3 +92,21 @@ def test_shared_launches_with_requests_outside_the_group(L):
             with L.Microstructure(n, n, n, g, seeds=I.voronoi_seeds(sd, g, (n, n, n)), **kw) as ms:
                 ms.step(st, dt)
                 assert np.array_equal(srv.volumes(tk), ms.grain_volumes())
+
+
+def test_label_request_is_copied_at_submit(L):
+    """A request starting from a label field holds its own copy of the
+    labels from submission on (the caller's array is overwritten right after
+    submit), and ends with the volumes of the same start stepped alone."""
+    from oracle import lsgg_oracle as O
+    n, g, steps = 40, 20, 6
+    lab = O.labels_of_tessellation((n, n, n), I.voronoi_seeds(81, g, (n, n, n))).astype(np.int32)
+    with L.Microstructure(n, n, n, g, labels=lab) as ms:
+        ms.step(steps, 1.0)
+        want = ms.grain_volumes()
+    with L.Server(budget_bytes=8 << 30, max_active=8, steps_per_round=3) as srv:
+        buf = lab.copy()
+        t = srv.submit(n, n, n, g, steps, labels=buf)
+        buf[:] = -5
+        srv.wait(t)
+        assert np.array_equal(srv.volumes(t), want)
