@@ -9,9 +9,13 @@
 // every id of the box (up to kPoolKeys) with its weight and mobility in the
 // step's pool, which the z pass turns into a shared-memory hash per box, so
 // that no cell searches or evaluates a pair.
+#include <cooperative_groups.h>
+
 #include "kernels_common.cuh"
 
 namespace lsgg {
+
+namespace cg = cooperative_groups;
 
 constexpr int kHashSlots = kPoolKeys;
 static_assert((kHashSlots & (kHashSlots - 1)) == 0, "hash slots: a power of two");
@@ -42,14 +46,16 @@ constexpr int kCollectLoads = 4;     // 16-byte loads in flight per thread
 // its thread has not entered that id last.  I: the index type (32-bit
 // divisions whenever the items fit).
 template <class I>
-__device__ __forceinline__ void collect_walk(const int* base, int A, int ps, int nz, int* keys, int* n_keys,
-                                             int* overflow) {
+__device__ __forceinline__ void collect_walk(const int* base, int A, int ps, int nz, int part, int parts, int* keys,
+                                             int* n_keys, int* overflow) {
     const I nq = (I)((A + 3) >> 2);
-    const I items = nq * (I)nz;
+    const I all = nq * (I)nz;
+    const I first = all / (I)parts * (I)part + min((I)part, all % (I)parts);     // this part's items
+    const I items = first + all / (I)parts + ((I)part < all % (I)parts ? 1 : 0);
     int last = -1;
     const int lane = threadIdx.x & 31;
     // the loop is uniform across each warp (its lanes exchange values below)
-    for (I w0 = threadIdx.x - lane; w0 < items; w0 += (I)kCollectLoads * blockDim.x) {
+    for (I w0 = first + threadIdx.x - lane; w0 < items; w0 += (I)kCollectLoads * blockDim.x) {
         const I i0 = w0 + lane;
         int v[kCollectLoads][4];
 #pragma unroll
@@ -85,26 +91,38 @@ __device__ __forceinline__ void collect_walk(const int* base, int A, int ps, int
     }
 }
 
-// One CTA per box.
-__global__ void __launch_bounds__(kCollectThreads)
+constexpr int kCollectCluster = 4;    // CTAs per box: a thread-block cluster
+
+// A cluster of kCollectCluster CTAs per box: each walks a part of the box's
+// ID-field and enters its ids into the hash in the shared memory of the
+// cluster's first CTA (distributed shared memory), which then does the rest.
+__global__ void __cluster_dims__(kCollectCluster, 1, 1) __launch_bounds__(kCollectThreads)
 k_collect_neighbours(PhysicsDev phys, StepState* st, const Box* __restrict__ prev, const int* __restrict__ IDF,
                      int* __restrict__ tab, int* __restrict__ cnt, float* __restrict__ tw, float* __restrict__ tm) {
     __shared__ int keys[kHashSlots];
     __shared__ int n_keys, overflow;
-    const int b = blockIdx.x;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int part = (int)cluster.block_rank();
+    const int b = blockIdx.x / kCollectCluster;
     const Box ob = prev[b];
-    for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x) keys[k] = -1;
-    if (threadIdx.x == 0) { n_keys = 0; overflow = 0; }
-    __syncthreads();
+    if (part == 0) {
+        for (int k = threadIdx.x; k < kHashSlots; k += blockDim.x) keys[k] = -1;
+        if (threadIdx.x == 0) { n_keys = 0; overflow = 0; }
+    }
+    cluster.sync();                                  // the first CTA's hash is clear before any entry
     if (ob.nx > 0) {
+        int* const k0 = cluster.map_shared_rank(keys, 0);
+        int* const n0 = cluster.map_shared_rank(&n_keys, 0);
+        int* const o0 = cluster.map_shared_rank(&overflow, 0);
         const int A = ob.nx * ob.ny;
         const int ps = plane_stride(ob.nx, ob.ny);
         if ((long long)((A + 3) >> 2) * ob.nz < (1LL << 31) - 4LL * kCollectLoads * kCollectThreads)
-            collect_walk<unsigned>(IDF + ob.off, A, ps, ob.nz, keys, &n_keys, &overflow);
+            collect_walk<unsigned>(IDF + ob.off, A, ps, ob.nz, part, kCollectCluster, k0, n0, o0);
         else
-            collect_walk<long long>(IDF + ob.off, A, ps, ob.nz, keys, &n_keys, &overflow);
+            collect_walk<long long>(IDF + ob.off, A, ps, ob.nz, part, kCollectCluster, k0, n0, o0);
     }
-    __syncthreads();
+    cluster.sync();                                  // every entry is in; the other CTAs are done
+    if (part != 0) return;
     // the box's place in this step's pool (every key, or none when they overflowed)
     __shared__ int pool_base;
     // this step's pool and the previous step's (the parity of the steps done)
@@ -236,7 +254,7 @@ cudaError_t launch_collect_neighbours(const StepBuffers& B, const PhysicsDev& ph
         const cudaError_t e = cudaMemsetAsync(&B.st->pool_used, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
-    k_collect_neighbours<<<B.n_boxes, kCollectThreads, 0, s>>>(phys, B.st, B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
+    k_collect_neighbours<<<B.n_boxes * kCollectCluster, kCollectThreads, 0, s>>>(phys, B.st, B.prev, B.IDF, const_cast<int*>(phys.nb_tab),
                                                      const_cast<int*>(phys.nb_cnt), const_cast<float*>(phys.nb_w),
                                                      const_cast<float*>(phys.nb_m));
     return cudaGetLastError();
